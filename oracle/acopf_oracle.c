@@ -1,0 +1,313 @@
+/*
+ * Plain FP64 CPU oracle for the polar AC optimal power flow model evaluation.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the benchmark's CPU
+ * baseline may load this file's library.  It shares no code, header, table or helper with the
+ * CUDA evaluator; the two meet only in the seeded input generator.
+ *
+ * What it computes (ExaGO, arXiv 2203.10587, Sec. III, eqs. (7)-(10)): for one state x of the
+ * compact model  min f(x)  s.t.  g(x) = 0,  h- <= h(x) <= h+,  x- <= x <= x+  it returns
+ *   f(x), grad f(x), g(x) | h(x), the values of the Jacobian of [g; h], and the values of the
+ *   lower triangle of the Lagrangian Hessian  sigma*grad^2 f + sum_i lam_i grad^2 g_i
+ *   + sum_l mu_l grad^2 h_l.
+ * The paper leaves the formulation to its references (Sec. III: the full formulation is omitted
+ * for space); the model is the "power-balance-polar" one it names, written here as the textbook
+ * pi-model in polar coordinates:
+ *   variables      x = [Va (nb) | Vm (nb) | Pg (ng) | Qg (ng)]
+ *   equalities     g = [P balance (nb) | Q balance (nb)]
+ *   inequalities   h = [|S_from|^2 (nl) | |S_to|^2 (nl)]   (squared apparent power)
+ *   multipliers    lam = [lamP (nb) | lamQ (nb) | muF (nl) | muT (nl)]
+ * Contingencies (Sec. V-A, eqs. (16)-(20)) enter as a per-branch in-service mask: an out-of-service
+ * branch contributes zero to every output, and its two h rows evaluate to zero.  Load scenarios
+ * (Sec. VI-A, eqs. (27)-(31)) enter as a per-bus load scale, and the scenario weight pi_s as a
+ * factor on the objective.
+ *
+ * Everything is evaluated directly, in plain loops, in the order: branches by ascending index
+ * (from side, then to side), then bus shunts and loads, then generators.  Derivatives are the
+ * chain rule through the branch angle theta = Va_u - Va_v, written out per side.  J and the
+ * Hessian are produced as coordinate triplets (every structural dependency is emitted, even when
+ * its value is zero) and summed into sorted CSR by oracle_coo_to_csr.
+ * Compile with -ffp-contract=off so that every product and sum is rounded on its own.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int nb, nl, ng;
+    const double *Gs, *Bs, *Pd, *Qd;     /* per bus, p.u. */
+    const int *f, *t;                    /* per branch, bus indices */
+    const double *r, *x, *b, *tap;       /* per branch, p.u.; tap 0 means 1 */
+    const int *gbus;                     /* per generator */
+    const double *c2, *c1, *c0;          /* cost in MW terms: c2*MW^2 + c1*MW + c0 */
+    double baseMVA;
+} oracle_net;
+
+typedef struct {
+    int64_t n;        /* triplets written */
+    int64_t cap;      /* capacity of the arrays */
+    int *row, *col;
+    double *val;
+} oracle_coo;
+
+/* ---- pi-model two-port of one branch (textbook; MATPOWER's branch model without phase shift) ----
+ * series admittance ys = 1/(r + j x) = gs + j bs, line charging b split half per end, off-nominal
+ * tap tau on the from side.  Y = [[(ys + j b/2)/tau^2, -ys/tau], [-ys/tau, ys + j b/2]].
+ * Out: Y[0..7] = Gff, Bff, Gft, Bft, Gtf, Btf, Gtt, Btt.  Returns 0, or -1 if r = x = 0. */
+int oracle_pi_model(double r, double x, double b, double tap, double *Y)
+{
+    double z2 = r * r + x * x;
+    double tau = (tap == 0.0) ? 1.0 : tap;
+    double gs, bs;
+    if (z2 == 0.0) return -1;
+    gs = r / z2;
+    bs = -x / z2;
+    Y[0] = gs / (tau * tau);
+    Y[1] = (bs + 0.5 * b) / (tau * tau);
+    Y[2] = -gs / tau;
+    Y[3] = -bs / tau;
+    Y[4] = -gs / tau;
+    Y[5] = -bs / tau;
+    Y[6] = gs;
+    Y[7] = bs + 0.5 * b;
+    return 0;
+}
+
+/* ---- one end of a branch, seen from its own bus u towards the other bus v ----
+ *   P = Gss Vu^2 + Vu Vv (Gm cos th + Bm sin th)
+ *   Q = -Bss Vu^2 + Vu Vv (Gm sin th - Bm cos th),      th = Va_u - Va_v
+ * Local variable order (Va_u, Va_v, Vu, Vv).  dP[4], dQ[4] are gradients, HP[16], HQ[16] the full
+ * symmetric Hessians (row-major 4x4).  The angle enters only through th, with d th / d Va_u = 1
+ * and d th / d Va_v = -1, so every angle derivative is a th-derivative times those signs. */
+static void side_terms(double Gss, double Bss, double Gm, double Bm,
+                       double Vau, double Vav, double Vu, double Vv,
+                       double *P, double *Q, double *dP, double *dQ, double *HP, double *HQ)
+{
+    const double e[2] = {1.0, -1.0};          /* d th / d (Va_u, Va_v) */
+    double th = Vau - Vav;
+    double cs = cos(th), sn = sin(th);
+    double a = Gm * cs + Bm * sn;             /* d a / d th = -c */
+    double c = Gm * sn - Bm * cs;             /* d c / d th =  a */
+    double VV = Vu * Vv;
+    int i, j;
+
+    *P = Gss * Vu * Vu + VV * a;
+    *Q = -Bss * Vu * Vu + VV * c;
+
+    /* gradients */
+    for (i = 0; i < 2; i++) {
+        dP[i] = VV * (-c) * e[i];
+        dQ[i] = VV * a * e[i];
+    }
+    dP[2] = 2.0 * Gss * Vu + Vv * a;
+    dP[3] = Vu * a;
+    dQ[2] = -2.0 * Bss * Vu + Vv * c;
+    dQ[3] = Vu * c;
+
+    /* Hessians */
+    for (i = 0; i < 2; i++) {
+        for (j = 0; j < 2; j++) {
+            HP[i * 4 + j] = VV * (-a) * e[i] * e[j];   /* d2 a / d th2 = -a */
+            HQ[i * 4 + j] = VV * (-c) * e[i] * e[j];   /* d2 c / d th2 = -c */
+        }
+        /* mixed angle / magnitude: d/dVu and d/dVv of the angle gradient */
+        HP[i * 4 + 2] = HP[2 * 4 + i] = Vv * (-c) * e[i];
+        HP[i * 4 + 3] = HP[3 * 4 + i] = Vu * (-c) * e[i];
+        HQ[i * 4 + 2] = HQ[2 * 4 + i] = Vv * a * e[i];
+        HQ[i * 4 + 3] = HQ[3 * 4 + i] = Vu * a * e[i];
+    }
+    HP[2 * 4 + 2] = 2.0 * Gss;
+    HP[2 * 4 + 3] = HP[3 * 4 + 2] = a;
+    HP[3 * 4 + 3] = 0.0;
+    HQ[2 * 4 + 2] = -2.0 * Bss;
+    HQ[2 * 4 + 3] = HQ[3 * 4 + 2] = c;
+    HQ[3 * 4 + 3] = 0.0;
+}
+
+static int push(oracle_coo *c, int row, int col, double v)
+{
+    if (c->n >= c->cap) return -1;
+    c->row[c->n] = row;
+    c->col[c->n] = col;
+    c->val[c->n] = v;
+    c->n++;
+    return 0;
+}
+
+/* Lower-triangle triplet (row >= col) of a symmetric entry. */
+static int push_sym(oracle_coo *c, int gi, int gj, double v)
+{
+    return gi >= gj ? push(c, gi, gj, v) : push(c, gj, gi, v);
+}
+
+/* Capacity the triplet arrays need for one evaluation. */
+void oracle_coo_capacity(const oracle_net *net, int64_t *capJ, int64_t *capH)
+{
+    *capJ = 24 * (int64_t)net->nl + 4 * (int64_t)net->nb + 2 * (int64_t)net->ng;
+    *capH = 20 * (int64_t)net->nl + 3 * (int64_t)net->nb + (int64_t)net->ng;
+}
+
+/*
+ * One evaluation (Sec. III, eqs. (7)-(10); objective weight pi_s of eq. (27)).
+ *   x[n], lam[m]; mask[nl] (1 in service, 0 out; NULL = all in service);
+ *   pd_scale[nb] (NULL = 1); w = objective weight; sigma = objective factor in the Hessian.
+ * Outputs: *fval, grad[n], gh[m]; J and H triplets appended to *J, *H (either may be NULL).
+ * Returns 0, -1 on a bad branch (r = x = 0) or bus index, -2 when a triplet array is full.
+ */
+int oracle_eval(const oracle_net *net, const double *x, const double *lam, const uint8_t *mask,
+                const double *pd_scale, double w, double sigma,
+                double *fval, double *grad, double *gh, oracle_coo *J, oracle_coo *H)
+{
+    const int nb = net->nb, nl = net->nl, ng = net->ng;
+    const int n = 2 * nb + 2 * ng;
+    const double *Va = x, *Vm = x + nb, *Pg = x + 2 * nb, *Qg = x + 2 * nb + ng;
+    const double *lamP = lam, *lamQ = lam + nb, *muF = lam + 2 * nb, *muT = lam + 2 * nb + nl;
+    double *gP = gh, *gQ = gh + nb, *hF = gh + 2 * nb, *hT = gh + 2 * nb + nl;
+    const double base = net->baseMVA;
+    int i, l, k, a, bb;
+
+    for (i = 0; i < 2 * nb + 2 * nl; i++) gh[i] = 0.0;
+    for (i = 0; i < n; i++) grad[i] = 0.0;
+
+    /* branches */
+    for (l = 0; l < nl; l++) {
+        double Y[8];
+        int fb = net->f[l], tb = net->t[l];
+        double m = (mask == NULL || mask[l]) ? 1.0 : 0.0;
+        double P[2], Q[2], dP[2][4], dQ[2][4], HP[2][16], HQ[2][16];
+        int gidx[2][4];
+        int s;
+        if (fb < 0 || fb >= nb || tb < 0 || tb >= nb || fb == tb) return -1;
+        if (oracle_pi_model(net->r[l], net->x[l], net->b[l], net->tap[l], Y) != 0) return -1;
+        /* from side: u = f, v = t; to side: u = t, v = f */
+        side_terms(Y[0], Y[1], Y[2], Y[3], Va[fb], Va[tb], Vm[fb], Vm[tb],
+                   &P[0], &Q[0], dP[0], dQ[0], HP[0], HQ[0]);
+        side_terms(Y[6], Y[7], Y[4], Y[5], Va[tb], Va[fb], Vm[tb], Vm[fb],
+                   &P[1], &Q[1], dP[1], dQ[1], HP[1], HQ[1]);
+        gidx[0][0] = fb; gidx[0][1] = tb; gidx[0][2] = nb + fb; gidx[0][3] = nb + tb;
+        gidx[1][0] = tb; gidx[1][1] = fb; gidx[1][2] = nb + tb; gidx[1][3] = nb + fb;
+
+        for (s = 0; s < 2; s++) {
+            int u = s == 0 ? fb : tb;
+            double mu = s == 0 ? muF[l] : muT[l];
+            double Hs[16];
+            P[s] *= m;
+            Q[s] *= m;
+            for (a = 0; a < 4; a++) { dP[s][a] *= m; dQ[s][a] *= m; }
+            for (a = 0; a < 16; a++) { HP[s][a] *= m; HQ[s][a] *= m; }
+
+            /* g: this end's injection enters the balance of its own bus u */
+            gP[u] += P[s];
+            gQ[u] += Q[s];
+            /* h: squared apparent power at this end */
+            (s == 0 ? hF : hT)[l] = P[s] * P[s] + Q[s] * Q[s];
+
+            if (J) {
+                int hrow = 2 * nb + (s == 0 ? l : nl + l);
+                for (a = 0; a < 4; a++) {
+                    if (push(J, u, gidx[s][a], dP[s][a])) return -2;
+                    if (push(J, nb + u, gidx[s][a], dQ[s][a])) return -2;
+                }
+                for (a = 0; a < 4; a++) /* grad |S|^2 = 2 P grad P + 2 Q grad Q */
+                    if (push(J, hrow, gidx[s][a], 2.0 * P[s] * dP[s][a] + 2.0 * Q[s] * dQ[s][a]))
+                        return -2;
+            }
+            if (H) {
+                /* lamP_u grad^2 P + lamQ_u grad^2 Q
+                   + mu * grad^2 (P^2 + Q^2),  grad^2 (P^2+Q^2) = 2 (dP dP' + P HP + dQ dQ' + Q HQ) */
+                for (a = 0; a < 4; a++)
+                    for (bb = 0; bb < 4; bb++)
+                        Hs[a * 4 + bb] = lamP[u] * HP[s][a * 4 + bb] + lamQ[u] * HQ[s][a * 4 + bb]
+                            + mu * 2.0 * (dP[s][a] * dP[s][bb] + P[s] * HP[s][a * 4 + bb]
+                                          + dQ[s][a] * dQ[s][bb] + Q[s] * HQ[s][a * 4 + bb]);
+                for (a = 0; a < 4; a++)
+                    for (bb = a; bb < 4; bb++)
+                        if (push_sym(H, gidx[s][a], gidx[s][bb], Hs[a * 4 + bb])) return -2;
+            }
+        }
+    }
+
+    /* bus shunts and loads: Gs Vm^2 + Pd and -Bs Vm^2 + Qd */
+    for (i = 0; i < nb; i++) {
+        double sc = pd_scale ? pd_scale[i] : 1.0;
+        gP[i] += net->Gs[i] * Vm[i] * Vm[i] + net->Pd[i] * sc;
+        gQ[i] += -net->Bs[i] * Vm[i] * Vm[i] + net->Qd[i] * sc;
+        if (J) {
+            if (push(J, i, i, 0.0)) return -2;                              /* dP_i/dVa_i */
+            if (push(J, i, nb + i, 2.0 * net->Gs[i] * Vm[i])) return -2;     /* dP_i/dVm_i */
+            if (push(J, nb + i, i, 0.0)) return -2;                         /* dQ_i/dVa_i */
+            if (push(J, nb + i, nb + i, -2.0 * net->Bs[i] * Vm[i])) return -2;
+        }
+        if (H) {
+            if (push(H, i, i, 0.0)) return -2;
+            if (push(H, nb + i, i, 0.0)) return -2;
+            if (push(H, nb + i, nb + i,
+                     lamP[i] * 2.0 * net->Gs[i] - lamQ[i] * 2.0 * net->Bs[i])) return -2;
+        }
+    }
+
+    /* generators: injection -Pg, -Qg at their bus; cost in MW */
+    *fval = 0.0;
+    for (k = 0; k < ng; k++) {
+        int gb = net->gbus[k];
+        double MW = base * Pg[k];
+        if (gb < 0 || gb >= nb) return -1;
+        gP[gb] -= Pg[k];
+        gQ[gb] -= Qg[k];
+        *fval += w * (net->c2[k] * MW * MW + net->c1[k] * MW + net->c0[k]);
+        grad[2 * nb + k] = w * (2.0 * net->c2[k] * base * base * Pg[k] + net->c1[k] * base);
+        if (J) {
+            if (push(J, gb, 2 * nb + k, -1.0)) return -2;
+            if (push(J, nb + gb, 2 * nb + ng + k, -1.0)) return -2;
+        }
+        if (H) {
+            if (push(H, 2 * nb + k, 2 * nb + k, sigma * w * 2.0 * net->c2[k] * base * base)) return -2;
+        }
+    }
+    return 0;
+}
+
+/* ---- sum duplicate triplets into CSR with ascending columns ---- */
+typedef struct { int row, col; int64_t idx; } key_t_;
+
+static int cmp_key(const void *pa, const void *pb)
+{
+    const key_t_ *a = (const key_t_ *)pa, *b = (const key_t_ *)pb;
+    if (a->row != b->row) return a->row < b->row ? -1 : 1;
+    if (a->col != b->col) return a->col < b->col ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx);
+}
+
+/* Sorts by (row, col, emission order) and sums duplicates in emission order.
+ * rowptr[nrows+1]; col/val need room for c->n entries.  Returns nnz, or -1 on a bad row
+ * or allocation failure. */
+int64_t oracle_coo_to_csr(const oracle_coo *c, int nrows, int64_t *rowptr, int *col, double *val)
+{
+    key_t_ *keys;
+    int64_t i, nnz = 0;
+    int r;
+    keys = (key_t_ *)malloc((size_t)(c->n > 0 ? c->n : 1) * sizeof(key_t_));
+    if (!keys) return -1;
+    for (i = 0; i < c->n; i++) {
+        if (c->row[i] < 0 || c->row[i] >= nrows) { free(keys); return -1; }
+        keys[i].row = c->row[i];
+        keys[i].col = c->col[i];
+        keys[i].idx = i;
+    }
+    qsort(keys, (size_t)c->n, sizeof(key_t_), cmp_key);
+    for (r = 0; r <= nrows; r++) rowptr[r] = 0;
+    for (i = 0; i < c->n; i++) {
+        if (nnz > 0 && i > 0 && keys[i].row == keys[i - 1].row && keys[i].col == keys[i - 1].col) {
+            val[nnz - 1] += c->val[keys[i].idx];
+        } else {
+            col[nnz] = keys[i].col;
+            val[nnz] = c->val[keys[i].idx];
+            rowptr[keys[i].row + 1]++;
+            nnz++;
+        }
+    }
+    for (r = 0; r < nrows; r++) rowptr[r + 1] += rowptr[r];
+    free(keys);
+    return nnz;
+}

@@ -1,0 +1,93 @@
+"""Mutation check of the oracle's pins (CPU only).
+
+Each mutant is a plausible transcription mistake planted in a copy of the C oracle (a flipped sign,
+a dropped term or factor, a wrong or swapped index, a unit slip).  The copy is compiled into a
+temporary library and the pins of test_oracle.py are run against it; every mutant must fail at
+least one pin.  This shows that the pins constrain every part of the oracle's arithmetic.
+"""
+import os
+
+import pytest
+
+from oracle import acopf
+import test_oracle as T
+
+SRC = os.path.join(os.path.dirname(acopf.__file__), "acopf_oracle.c")
+
+MUTANTS = {
+    "reactive_sign": ("double c = Gm * sn - Bm * cs;", "double c = Gm * sn + Bm * cs;"),
+    "active_sign": ("double a = Gm * cs + Bm * sn;", "double a = Gm * cs - Bm * sn;"),
+    "dP_dVu_factor": ("dP[2] = 2.0 * Gss * Vu + Vv * a;", "dP[2] = Gss * Vu + Vv * a;"),
+    "dQ_dVv_index": ("dQ[3] = Vu * c;", "dQ[3] = Vv * c;"),
+    "HP_mixed_index": ("HP[i * 4 + 3] = HP[3 * 4 + i] = Vu * (-c) * e[i];",
+                       "HP[i * 4 + 3] = HP[3 * 4 + i] = Vv * (-c) * e[i];"),
+    "HQ_angle_term": ("HQ[i * 4 + j] = VV * (-c) * e[i] * e[j];",
+                      "HQ[i * 4 + j] = VV * (-a) * e[i] * e[j];"),
+    "HQ_self_sign": ("HQ[2 * 4 + 2] = -2.0 * Bss;", "HQ[2 * 4 + 2] = 2.0 * Bss;"),
+    "hess_dropped_outer": ("+ dQ[s][a] * dQ[s][bb] + Q[s] * HQ[s][a * 4 + bb]);",
+                           "+ Q[s] * HQ[s][a * 4 + bb]);"),
+    "hess_mu_factor": ("+ mu * 2.0 * (dP[s][a]", "+ mu * (dP[s][a]"),
+    "to_side_swapped": ("gidx[1][0] = tb; gidx[1][1] = fb;", "gidx[1][0] = fb; gidx[1][1] = tb;"),
+    "charging_not_halved": ("Y[1] = (bs + 0.5 * b) / (tau * tau);", "Y[1] = (bs + b) / (tau * tau);"),
+    "tap_square_mutual": ("Y[2] = -gs / tau;", "Y[2] = -gs / (tau * tau);"),
+    "tap_on_wrong_end": ("Y[6] = gs;", "Y[6] = gs / (tau * tau);"),
+    "h_jac_factor": ("2.0 * P[s] * dP[s][a] + 2.0 * Q[s] * dQ[s][a]", "P[s] * dP[s][a] + Q[s] * dQ[s][a]"),
+    "cost_units": ("net->c1[k] * MW + net->c0[k]", "net->c1[k] * Pg[k] + net->c0[k]"),
+    "grad_units": ("+ net->c1[k] * base);", "+ net->c1[k]);"),
+    "hess_sigma": ("sigma * w * 2.0 * net->c2[k]", "w * 2.0 * net->c2[k]"),
+    "shunt_hess_sign": ("- lamQ[i] * 2.0 * net->Bs[i]", "+ lamQ[i] * 2.0 * net->Bs[i]"),
+    "shunt_jac_dropped": ("if (push(J, i, nb + i, 2.0 * net->Gs[i] * Vm[i])) return -2;",
+                          "if (push(J, i, nb + i, 0.0)) return -2;"),
+    "load_scale_dropped": ("net->Pd[i] * sc;", "net->Pd[i];"),
+    "mask_ignored": ("P[s] *= m;", "P[s] *= 1.0;"),
+    "gen_q_on_p_row": ("gQ[gb] -= Qg[k];", "gP[gb] -= Qg[k];"),
+}
+
+
+class Bound:
+    """The oracle module's API bound to one compiled library."""
+
+    def __init__(self, lib):
+        self.lib = lib
+        self.OracleNet = acopf.OracleNet
+        self.csr_to_dense = acopf.csr_to_dense
+
+    def evaluate(self, *a, **k):
+        return acopf.evaluate(*a, lib=self.lib, **k)
+
+
+PINS = [
+    ("power_angle", lambda om: T.test_power_angle_equations_lossless_line(om)),
+    ("transformer", lambda om: T.test_transformer_scales_from_voltage(om)),
+    ("flat_start", lambda om: T.test_flat_start(om)),
+    ("objective", lambda om: T.test_objective_hand_numbers(om)),
+    ("nodal_3", lambda om: T.test_matches_complex_nodal_form(om, 21, 3, 3, 1)),
+    ("nodal_30", lambda om: T.test_matches_complex_nodal_form(om, 22, 30, 41, 6)),
+    ("loss", lambda om: T.test_loss_invariant(om)),
+    ("fd", lambda om: T.test_finite_differences(om, 41)),
+    ("fd_sigma0", lambda om: T.test_finite_differences_sigma_zero_and_transformers(om)),
+    ("mask", lambda om: T.test_mask_equals_branch_removed(om)),
+]
+
+
+def test_unmutated_copy_passes_all_pins(tmp_path):
+    lib = acopf.bind_library(acopf.compile_source(SRC, str(tmp_path / "good.so")))
+    for name, pin in PINS:
+        pin(Bound(lib))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    lib = acopf.bind_library(acopf.compile_source(str(path), str(tmp_path / f"{name}.so")))
+    caught = []
+    for pname, pin in PINS:
+        try:
+            pin(Bound(lib))
+        except (AssertionError, ValueError):
+            caught.append(pname)
+    assert caught, f"mutant {name} passed every pin"
