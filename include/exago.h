@@ -1,0 +1,197 @@
+/*
+ * exago.h -- C ABI of the GB300 batched evaluator of the polar AC optimal power flow model.
+ *
+ * The model is the compact ACOPF of ExaGO (arXiv 2203.10587), Sec. III, eqs. (7)-(10):
+ *     min f(x)   s.t.   g(x) = 0,   h- <= h(x) <= h+,   x- <= x <= x+
+ * in the "power-balance-polar" formulation named in Sec. III.  An interior-point solver (Ipopt,
+ * HiOp, TAO; Sec. II-III) calls the model once per iteration for f, grad f, g, h, the Jacobian of
+ * [g; h] and the Hessian of the Lagrangian; this library evaluates those callbacks for a batch of
+ * B independent states on one GPU.  Independent states are the contingencies of SCOPFLOW
+ * (Sec. V-A, eqs. (16)-(20)), the scenarios of SOPFLOW (Sec. VI-A, eqs. (27)-(31)) and the
+ * subproblems of the embarrassingly parallel EMPAR solver (Sec. V-A).
+ *
+ * Conventions (all quantities per unit; angles in radians):
+ *   variables     x      = [Va (nb) | Vm (nb) | Pg (ng) | Qg (ng)],            n = 2 nb + 2 ng
+ *   constraints   g | h  = [P balance (nb) | Q balance (nb) | |S_from|^2 (nl) | |S_to|^2 (nl)],
+ *                                                                                m = 2 nb + 2 nl
+ *   multipliers   lambda = [lamP (nb) | lamQ (nb) | muF (nl) | muT (nl)]
+ *   P balance of bus i:  sum of branch-end injections at i + Gs_i Vm_i^2 + Pd_i s_i - sum Pg at i
+ *   Q balance of bus i:  sum of branch-end injections at i - Bs_i Vm_i^2 + Qd_i s_i - sum Qg at i
+ *   branch model:        pi-model, series 1/(r + jx), charging b split half per end, tap on the
+ *                        from end (tap 0 means 1), no phase shift
+ *   objective:           f = w * sum_k (c2_k (baseMVA Pg_k)^2 + c1_k baseMVA Pg_k + c0_k)
+ *   Lagrangian Hessian:  sigma grad^2 f + sum lam_i grad^2 g_i + sum mu_l grad^2 h_l, lower
+ *                        triangle, row-major CSR, ascending columns
+ *   Jacobian:            rows of g then h, row-major CSR, ascending columns
+ *   out-of-service branch (mask 0): contributes nothing; its two h rows and their Jacobian and
+ *                        Hessian entries evaluate to 0; the sparsity pattern is unchanged.
+ *
+ * Threading and streams: every function may be called from any host thread.  Evaluation calls
+ * are asynchronous on the stream given in the batch; host-side argument errors return at once.
+ * Calls that share one net and no caller workspace must be ordered (one stream, or events):
+ * they share the net's internal workspace.  Errors raised inside kernels (a bounded wait that
+ * timed out) are recorded in a device status word and returned by exago_net_check.
+ * Every function returns EXAGO_OK or an error code; exago_last_error() then describes it.
+ */
+#ifndef EXAGO_GB300_H
+#define EXAGO_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EXAGO_OK = 0,
+    EXAGO_EINVAL = 1,    /* bad argument: null pointer, out-of-range index, r = x = 0, ... */
+    EXAGO_ENOMEM = 2,    /* device or host allocation failed */
+    EXAGO_ECUDA = 3,     /* a CUDA runtime call failed */
+    EXAGO_ETIMEOUT = 4,  /* a bounded device-side wait gave up, or a serve deadline passed */
+    EXAGO_EBUSY = 5,     /* serve queue full */
+    EXAGO_ESTATE = 6     /* call not valid in the object's current state */
+} exago_status;
+
+typedef struct exago_net *exago_net_t;
+
+/* Thread-local description of the last non-OK status returned on this thread. */
+const char *exago_last_error(void);
+
+/* Name of a status code ("EXAGO_EINVAL", ...). */
+const char *exago_status_name(exago_status s);
+
+/*
+ * Builds a network on the current CUDA device (Sec. III model data; the network build happens
+ * once per grid, before the solver's iterations).  Copies every host array; the caller keeps
+ * ownership of its arrays.  Validates indices (0 <= f, t < nb, f != t, 0 <= gbus < nb),
+ * r = x = 0, negative taps, non-finite values and baseMVA <= 0 (EINVAL).  Builds the Jacobian and
+ * Hessian patterns and every output position on the host, uploads them, and evaluates the
+ * pi-model admittances on the device.
+ *   nb, nl, ng >= 0 (nb >= 1).  Gs, Bs, Pd, Qd: [nb] or NULL (zeros).  f, t, r, x, b: [nl].
+ *   tap: [nl] or NULL (all 1); 0 entries mean 1.  rateA: [nl] or NULL; flow limit in p.u., used
+ *   only by exago_net_ineq_bounds (0 means unlimited).  gbus, c2, c1: [ng]; c0: [ng] or NULL.
+ * On success *out owns device memory until exago_net_destroy.
+ */
+exago_status exago_net_create(int nb, const double *Gs, const double *Bs, const double *Pd,
+                              const double *Qd, int nl, const int *f, const int *t,
+                              const double *r, const double *x, const double *b,
+                              const double *tap, const double *rateA, int ng, const int *gbus,
+                              const double *c2, const double *c1, const double *c0,
+                              double baseMVA, exago_net_t *out);
+
+/*
+ * Host-only planning with the same arguments and validation as exago_net_create, without
+ * touching a GPU.  The handle answers exago_net_dims, the pattern, bound and plan-array queries
+ * and exago_net_destroy; evaluation calls on it return EXAGO_ESTATE.  Useful to set up a solver's
+ * symbolic factorisation before any device work, and to check the plan on a machine without GPU.
+ */
+exago_status exago_net_plan(int nb, const double *Gs, const double *Bs, const double *Pd,
+                            const double *Qd, int nl, const int *f, const int *t,
+                            const double *r, const double *x, const double *b,
+                            const double *tap, const double *rateA, int ng, const int *gbus,
+                            const double *c2, const double *c1, const double *c0,
+                            double baseMVA, exago_net_t *out);
+
+/* Frees the network's device and host memory.  NULL is accepted.  The caller must make sure no
+ * work that uses the network is still queued on any stream. */
+exago_status exago_net_destroy(exago_net_t net);
+
+/* Problem dimensions: n variables, m_eq = 2 nb, m_ineq = 2 nl, nonzeros of J and of lower H. */
+exago_status exago_net_dims(exago_net_t net, int *n, int *m_eq, int *m_ineq, int64_t *nnzJ,
+                            int64_t *nnzH);
+
+/* Jacobian pattern into caller host arrays: rowptr[m + 1], col[nnzJ] (eqs. (8)-(9) rows). */
+exago_status exago_net_jac_pattern(exago_net_t net, int64_t *rowptr, int *col);
+
+/* Lower-triangle Lagrangian Hessian pattern into caller host arrays: rowptr[n + 1], col[nnzH]. */
+exago_status exago_net_hess_pattern(exago_net_t net, int64_t *rowptr, int *col);
+
+/* Bounds h- and h+ of eq. (9) into caller host arrays [2 nl]: h- = 0, h+ = rateA^2 (or HUGE_VAL
+ * where rateA = 0). */
+exago_status exago_net_ineq_bounds(exago_net_t net, double *hlo, double *hhi);
+
+/*
+ * Copies one of the plan's integer tables (output positions of each kernel's writes) into a
+ * caller host buffer, for inspection and tests.  name is one of: br_off ([12][nl]), br_slot
+ * ([2][nl]), br_shared, slot_ptr, bus_jP, bus_jQ, bus_k, bus_h ([3][nb]), gen_ptr, gen_ord,
+ * gen_jP, gen_jQ, gen_h, fix_ptr, fix_src, fix_dst (int32) and fix_isH (uint8).  *needed receives
+ * the size in bytes; dst may be NULL to query it.  EINVAL for an unknown name or small buffer.
+ */
+exago_status exago_net_plan_array(exago_net_t net, const char *name, void *dst, size_t bytes,
+                                  size_t *needed);
+
+/*
+ * One batch of B independent evaluation states.  Every pointer is a DEVICE pointer owned by the
+ * caller that must stay valid until the work queued on `stream` completes.
+ *   x          [B][n]    row-major
+ *   lambda     [B][m]    multipliers (needed by the Hessian only; may be NULL otherwise)
+ *   mask       [B][nl]   1 in service, 0 out of service (N-1 contingency, Sec. V-A); NULL = all 1
+ *   pd_scale   [B][nb]   per-bus load scale of a scenario (Sec. VI-A); NULL = 1
+ *   obj_weight [B]       scenario weight pi_s of eq. (27); NULL = 1
+ *   obj_factor           sigma of the Lagrangian Hessian (Ipopt's obj_factor)
+ *   stream               cudaStream_t to queue the work on (NULL = legacy default stream)
+ *   workspace            optional device scratch of at least exago_eval_workspace_size bytes,
+ *                        256-byte aligned; NULL = use the net's internal workspace, grown on
+ *                        demand (a growth calls cudaMalloc; use exago_net_reserve before any
+ *                        stream capture)
+ */
+typedef struct {
+    int B;
+    const double *x;
+    const double *lambda;
+    const uint8_t *mask;
+    const double *pd_scale;
+    const double *obj_weight;
+    double obj_factor;
+    void *stream;
+    void *workspace;
+    size_t workspace_bytes;
+} exago_batch;
+
+/* Scratch bytes one evaluation of B states needs (per branch end partial sums, and the
+ * off-diagonal values of parallel branches). */
+exago_status exago_eval_workspace_size(exago_net_t net, int B, size_t *bytes);
+
+/* Grows the net's internal workspace to hold B states now, so later calls allocate nothing. */
+exago_status exago_net_reserve(exago_net_t net, int B);
+
+/*
+ * Evaluations (Sec. III, eqs. (7)-(10)).  Outputs are caller DEVICE buffers, row-major per state:
+ *   f [B]; grad [B][n]; gh [B][m] (g then h); jval [B][nnzJ] in exago_net_jac_pattern order;
+ *   hval [B][nnzH] in exago_net_hess_pattern order.
+ * exago_eval_all computes any subset in one pass: NULL outputs are skipped.
+ * Errors: EINVAL for a null net or batch, B < 0, a missing x (or lambda when hval is wanted), a
+ * too-small or misaligned workspace; ECUDA if a launch fails.  B = 0 returns OK and does nothing.
+ */
+exago_status exago_eval_obj(exago_net_t net, const exago_batch *batch, double *f);
+exago_status exago_eval_grad(exago_net_t net, const exago_batch *batch, double *grad);
+exago_status exago_eval_cons(exago_net_t net, const exago_batch *batch, double *gh);
+exago_status exago_eval_jac(exago_net_t net, const exago_batch *batch, double *jval);
+exago_status exago_eval_hess(exago_net_t net, const exago_batch *batch, double *hval);
+exago_status exago_eval_all(exago_net_t net, const exago_batch *batch, double *f, double *grad,
+                            double *gh, double *jval, double *hval);
+
+/*
+ * Per-kernel timing of exago_eval_all (tracing and benchmarks).  Runs the same evaluation `reps`
+ * times on batch->stream with a CUDA event recorded on that stream before every kernel launch and
+ * after the last one, waits for each repetition, and returns the mean duration in milliseconds of
+ * each kernel of one evaluation: names[k] (static strings: "branch", "bus", "fixup", "grad",
+ * "obj") and ms[k] for k < *nkernels.  names and ms need room for 16 entries.  Outputs are those
+ * of exago_eval_all.  EINVAL for reps < 1 or null names/ms/nkernels.
+ */
+exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, double *f, double *grad,
+                                double *gh, double *jval, double *hval, int reps, int *nkernels,
+                                const char **names, double *ms);
+
+/*
+ * Waits for `stream` and returns the device status word of the net: EXAGO_OK, or EXAGO_ETIMEOUT
+ * if a bounded device-side wait gave up since the last check (the word is then cleared).
+ */
+exago_status exago_net_check(exago_net_t net, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXAGO_GB300_H */

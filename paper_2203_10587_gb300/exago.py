@@ -1,0 +1,305 @@
+"""Thin ctypes binding of the C ABI in include/exago.h (argument marshalling only).
+
+Function names match the C entry points.  Device buffers are torch CUDA tensors (float64 /
+uint8, contiguous); their data pointers are passed through unchanged and every computation
+happens in the library's CUDA kernels.  There is no fallback: if the compiled library
+(paper_2203_10587_gb300/_build/libexago_gb300.so) is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "_build", "libexago_gb300.so")
+
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "EXAGO_OK", 1: "EXAGO_EINVAL", 2: "EXAGO_ENOMEM", 3: "EXAGO_ECUDA",
+          4: "EXAGO_ETIMEOUT", 5: "EXAGO_EBUSY", 6: "EXAGO_ESTATE"}
+
+# every symbol include/exago.h declares (checked by tests/test_capi_host.py)
+EXPORTS = [
+    "exago_last_error", "exago_status_name", "exago_net_create", "exago_net_plan",
+    "exago_net_destroy", "exago_net_dims", "exago_net_jac_pattern", "exago_net_hess_pattern",
+    "exago_net_ineq_bounds", "exago_net_plan_array", "exago_eval_workspace_size",
+    "exago_net_reserve", "exago_eval_obj", "exago_eval_grad", "exago_eval_cons",
+    "exago_eval_jac", "exago_eval_hess", "exago_eval_all", "exago_eval_profile",
+    "exago_net_check",
+]
+
+
+class ExagoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class exago_batch(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int), ("x", ctypes.c_void_p), ("lambda_", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("pd_scale", ctypes.c_void_p),
+                ("obj_weight", ctypes.c_void_p), ("obj_factor", ctypes.c_double),
+                ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIBPATH):
+                raise RuntimeError(f"{LIBPATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIBPATH)
+            vp, i32, i64p = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
+            net_args = [i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp,
+                        vp, ctypes.c_double, ctypes.POINTER(vp)]
+            sig = {
+                "exago_last_error": ([], ctypes.c_char_p),
+                "exago_status_name": ([i32], ctypes.c_char_p),
+                "exago_net_create": (net_args, i32),
+                "exago_net_plan": (net_args, i32),
+                "exago_net_destroy": ([vp], i32),
+                "exago_net_dims": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32), i64p, i64p], i32),
+                "exago_net_jac_pattern": ([vp, vp, vp], i32),
+                "exago_net_hess_pattern": ([vp, vp, vp], i32),
+                "exago_net_ineq_bounds": ([vp, vp, vp], i32),
+                "exago_net_plan_array": ([vp, ctypes.c_char_p, vp, ctypes.c_size_t,
+                                          ctypes.POINTER(ctypes.c_size_t)], i32),
+                "exago_eval_workspace_size": ([vp, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
+                "exago_net_reserve": ([vp, i32], i32),
+                "exago_eval_obj": ([vp, ctypes.POINTER(exago_batch), vp], i32),
+                "exago_eval_grad": ([vp, ctypes.POINTER(exago_batch), vp], i32),
+                "exago_eval_cons": ([vp, ctypes.POINTER(exago_batch), vp], i32),
+                "exago_eval_jac": ([vp, ctypes.POINTER(exago_batch), vp], i32),
+                "exago_eval_hess": ([vp, ctypes.POINTER(exago_batch), vp], i32),
+                "exago_eval_all": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp], i32),
+                "exago_eval_profile": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp, i32,
+                                        ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_char_p),
+                                        ctypes.POINTER(ctypes.c_double)], i32),
+                "exago_net_check": ([vp, vp], i32),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise ExagoError(rc, lib().exago_last_error().decode())
+
+
+def _np(a, dtype):
+    return None if a is None else np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hp(a):
+    return None if a is None else a.ctypes.data
+
+
+def _dp(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _net_call(fn, nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng, gbus, c2, c1, c0,
+              baseMVA):
+    d = lambda a: _np(a, np.float64)
+    i = lambda a: _np(a, np.int32)
+    keep = [d(Gs), d(Bs), d(Pd), d(Qd), i(f), i(t), d(r), d(x), d(b), d(tap), d(rateA), i(gbus),
+            d(c2), d(c1), d(c0)]
+    h = ctypes.c_void_p()
+    _check(fn(int(nb), *map(_hp, keep[:4]), int(nl), *map(_hp, keep[4:11]), int(ng),
+              *map(_hp, keep[11:]), float(baseMVA), ctypes.byref(h)))
+    return h
+
+
+def exago_net_create(nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng, gbus, c2, c1, c0,
+                     baseMVA):
+    """Host numpy arrays in; returns the opaque net handle (on the current CUDA device)."""
+    return _net_call(lib().exago_net_create, nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA,
+                     ng, gbus, c2, c1, c0, baseMVA)
+
+
+def exago_net_plan(nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng, gbus, c2, c1, c0,
+                   baseMVA):
+    """Host-only plan (no GPU needed)."""
+    return _net_call(lib().exago_net_plan, nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng,
+                     gbus, c2, c1, c0, baseMVA)
+
+
+def exago_net_destroy(h):
+    _check(lib().exago_net_destroy(h))
+
+
+def exago_net_dims(h):
+    n, me, mi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nj, nh = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().exago_net_dims(h, ctypes.byref(n), ctypes.byref(me), ctypes.byref(mi),
+                                ctypes.byref(nj), ctypes.byref(nh)))
+    return n.value, me.value, mi.value, nj.value, nh.value
+
+
+def exago_net_jac_pattern(h):
+    n, me, mi, nj, _ = exago_net_dims(h)
+    rowptr = np.zeros(me + mi + 1, np.int64)
+    col = np.zeros(max(nj, 1), np.int32)
+    _check(lib().exago_net_jac_pattern(h, _hp(rowptr), _hp(col)))
+    return rowptr, col[:nj]
+
+
+def exago_net_hess_pattern(h):
+    n, _, _, _, nh = exago_net_dims(h)
+    rowptr = np.zeros(n + 1, np.int64)
+    col = np.zeros(max(nh, 1), np.int32)
+    _check(lib().exago_net_hess_pattern(h, _hp(rowptr), _hp(col)))
+    return rowptr, col[:nh]
+
+
+def exago_net_ineq_bounds(h):
+    _, _, mi, _, _ = exago_net_dims(h)
+    lo = np.zeros(max(mi, 1))
+    hi = np.zeros(max(mi, 1))
+    _check(lib().exago_net_ineq_bounds(h, _hp(lo), _hp(hi)))
+    return lo[:mi], hi[:mi]
+
+
+def exago_net_plan_array(h, name: str):
+    need = ctypes.c_size_t()
+    _check(lib().exago_net_plan_array(h, name.encode(), None, 0, ctypes.byref(need)))
+    dt = np.uint8 if name == "fix_isH" else np.int32
+    out = np.zeros(need.value // np.dtype(dt).itemsize, dt)
+    _check(lib().exago_net_plan_array(h, name.encode(), _hp(out) if out.size else None,
+                                      need.value, ctypes.byref(need)))
+    return out
+
+
+def exago_eval_workspace_size(h, B: int) -> int:
+    v = ctypes.c_size_t()
+    _check(lib().exago_eval_workspace_size(h, int(B), ctypes.byref(v)))
+    return v.value
+
+
+def exago_net_reserve(h, B: int):
+    _check(lib().exago_net_reserve(h, int(B)))
+
+
+def make_batch(x, lam=None, mask=None, pd_scale=None, obj_weight=None, obj_factor=1.0,
+               stream=None, workspace=None) -> exago_batch:
+    """exago_batch over torch CUDA tensors x [B][n] (float64), lam [B][m], mask [B][nl] (uint8),
+    pd_scale [B][nb], obj_weight [B]; stream is a torch.cuda.Stream or None (current stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    ws_ptr, ws_bytes = (None, 0)
+    if workspace is not None:
+        ws_ptr, ws_bytes = _dp(workspace), workspace.numel() * workspace.element_size()
+    return exago_batch(int(x.shape[0]), _dp(x, torch.float64), _dp(lam, torch.float64),
+                       _dp(mask, torch.uint8), _dp(pd_scale, torch.float64),
+                       _dp(obj_weight, torch.float64), float(obj_factor),
+                       ctypes.c_void_p(stream.cuda_stream), ws_ptr, ws_bytes)
+
+
+def _out(t):
+    import torch
+    return _dp(t, torch.float64)
+
+
+def exago_eval_obj(h, batch: exago_batch, f):
+    _check(lib().exago_eval_obj(h, ctypes.byref(batch), _out(f)))
+
+
+def exago_eval_grad(h, batch: exago_batch, grad):
+    _check(lib().exago_eval_grad(h, ctypes.byref(batch), _out(grad)))
+
+
+def exago_eval_cons(h, batch: exago_batch, gh):
+    _check(lib().exago_eval_cons(h, ctypes.byref(batch), _out(gh)))
+
+
+def exago_eval_jac(h, batch: exago_batch, jval):
+    _check(lib().exago_eval_jac(h, ctypes.byref(batch), _out(jval)))
+
+
+def exago_eval_hess(h, batch: exago_batch, hval):
+    _check(lib().exago_eval_hess(h, ctypes.byref(batch), _out(hval)))
+
+
+def exago_eval_all(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None, hval=None):
+    _check(lib().exago_eval_all(h, ctypes.byref(batch), _out(f), _out(grad), _out(gh), _out(jval),
+                                _out(hval)))
+
+
+def exago_eval_profile(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None, hval=None,
+                       reps: int = 10):
+    """Mean per-kernel milliseconds of one exago_eval_all: list of (name, ms)."""
+    nk = ctypes.c_int()
+    names = (ctypes.c_char_p * 16)()
+    ms = (ctypes.c_double * 16)()
+    _check(lib().exago_eval_profile(h, ctypes.byref(batch), _out(f), _out(grad), _out(gh),
+                                    _out(jval), _out(hval), int(reps), ctypes.byref(nk), names, ms))
+    return [(names[k].decode(), ms[k]) for k in range(nk.value)]
+
+
+def exago_net_check(h, stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().exago_net_check(h, ctypes.c_void_p(stream.cuda_stream)))
+
+
+# ---- convenience ------------------------------------------------------------------------------
+
+def _grid_args(grid):
+    return (grid.nb, grid.Gs, grid.Bs, grid.Pd, grid.Qd, grid.nl, grid.f, grid.t, grid.r, grid.x,
+            grid.b, grid.tap, grid.rateA, grid.ng, grid.gbus, grid.c2, grid.c1, grid.c0,
+            grid.baseMVA)
+
+
+class Net:
+    """Owns a net handle built from a synth.Grid-like object (nb, Gs, ..., baseMVA)."""
+
+    def __init__(self, grid, plan_only: bool = False):
+        self.h = (exago_net_plan if plan_only else exago_net_create)(*_grid_args(grid))
+        self.n, self.m_eq, self.m_ineq, self.nnzJ, self.nnzH = exago_net_dims(self.h)
+        self.m = self.m_eq + self.m_ineq
+        self.nb, self.nl, self.ng = grid.nb, grid.nl, grid.ng
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            exago_net_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, B: int, device="cuda", f=True, grad=True, gh=True, jac=True, hess=True):
+        import torch
+        z = lambda *s: torch.empty(*s, dtype=torch.float64, device=device)
+        return {"f": z(B) if f else None, "grad": z(B, self.n) if grad else None,
+                "gh": z(B, self.m) if gh else None, "jval": z(B, self.nnzJ) if jac else None,
+                "hval": z(B, self.nnzH) if hess else None}
+
+    def eval_all(self, batch: exago_batch, out: dict):
+        exago_eval_all(self.h, batch, out.get("f"), out.get("grad"), out.get("gh"),
+                       out.get("jval"), out.get("hval"))
+        return out
