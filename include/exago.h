@@ -173,6 +173,25 @@ exago_status exago_eval_all(exago_net_t net, const exago_batch *batch, double *f
                             double *gh, double *jval, double *hval);
 
 /*
+ * exago_eval_all without any allocation.  The paper has no counterpart: this serves callers that
+ * may not allocate device memory once running -- for example a solver whose device memory belongs
+ * to a pooling allocator (a raw cudaMalloc would bypass it, and cudaFree synchronises the device),
+ * or a serving loop that reserves everything at start-up.  It takes the same batch and outputs as
+ * exago_eval_all and gives the same results, but its scratch lives in one static device array of
+ * EXAGO_STATIC_SCRATCH_BYTES per GPU, reserved by every GPU that loads the library until the
+ * process exits; batch->workspace is ignored and nothing is allocated.
+ *   - The net's device must be current.  The first call on a device looks up the array's device
+ *     address (cudaGetSymbolAddress) once for that device; make that first call before any stream
+ *     capture.
+ *   - EINVAL if the batch's scratch (exago_eval_workspace_size) exceeds the array: split the batch.
+ *   - All calls share the array: calls that overlap on the GPU race on it, so order them (one
+ *     stream, or events).  Nothing in it needs clearing; each call writes all the scratch it reads.
+ */
+#define EXAGO_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+exago_status exago_eval_all_static(exago_net_t net, const exago_batch *batch, double *f,
+                                   double *grad, double *gh, double *jval, double *hval);
+
+/*
  * Per-kernel timing of exago_eval_all (tracing and benchmarks).  Runs the same evaluation `reps`
  * times on batch->stream with a CUDA event recorded on that stream before every kernel launch and
  * after the last one, waits for each repetition, and returns the mean duration in milliseconds of

@@ -220,6 +220,20 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
 
 }  // namespace
 
+namespace exago {
+
+bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **dev, int *device) {
+    if (!net || !net->on_device) return false;
+    *plan = &net->plan;
+    *dev = &net->dev;
+    *device = net->device;
+    return true;
+}
+
+exago_status set_last_error(exago_status s, const std::string &msg) { return fail(s, msg); }
+
+}  // namespace exago
+
 extern "C" {
 
 const char *exago_last_error(void) { return g_err.c_str(); }

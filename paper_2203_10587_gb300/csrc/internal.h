@@ -122,4 +122,9 @@ int launch_admittance(const double *r, const double *x, const double *b, const d
                       double *Bft, void *stream);
 int launch_eval(const DevNet &net, const EvalReq &req, void *stream, ProfileHook *hook = nullptr);
 
+// Read-only view of a net's plan and device tables (false for NULL or a plan-only net), and the
+// thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.
+bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **dev, int *device);
+exago_status set_last_error(exago_status s, const std::string &msg);
+
 }  // namespace exago

@@ -28,8 +28,8 @@ EXPORTS = [
     "exago_net_destroy", "exago_net_dims", "exago_net_jac_pattern", "exago_net_hess_pattern",
     "exago_net_ineq_bounds", "exago_net_plan_array", "exago_eval_workspace_size",
     "exago_net_reserve", "exago_eval_obj", "exago_eval_grad", "exago_eval_cons",
-    "exago_eval_jac", "exago_eval_hess", "exago_eval_all", "exago_eval_profile",
-    "exago_net_check",
+    "exago_eval_jac", "exago_eval_hess", "exago_eval_all", "exago_eval_all_static",
+    "exago_eval_profile", "exago_net_check",
 ]
 
 
@@ -81,6 +81,8 @@ def lib():
                 "exago_eval_jac": ([vp, ctypes.POINTER(exago_batch), vp], i32),
                 "exago_eval_hess": ([vp, ctypes.POINTER(exago_batch), vp], i32),
                 "exago_eval_all": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp], i32),
+                "exago_eval_all_static": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp],
+                                          i32),
                 "exago_eval_profile": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp, i32,
                                         ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.POINTER(ctypes.c_double)], i32),
@@ -244,6 +246,13 @@ def exago_eval_hess(h, batch: exago_batch, hval):
 def exago_eval_all(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None, hval=None):
     _check(lib().exago_eval_all(h, ctypes.byref(batch), _out(f), _out(grad), _out(gh), _out(jval),
                                 _out(hval)))
+
+
+def exago_eval_all_static(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None,
+                          hval=None):
+    """exago_eval_all with its scratch in the library's static device array (no allocation)."""
+    _check(lib().exago_eval_all_static(h, ctypes.byref(batch), _out(f), _out(grad), _out(gh),
+                                       _out(jval), _out(hval)))
 
 
 def exago_eval_profile(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None, hval=None,

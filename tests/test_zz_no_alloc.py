@@ -1,0 +1,71 @@
+"""exago_eval_all_static: the evaluation for callers that may not allocate device memory.
+
+Some callers cannot call cudaMalloc once they run -- a solver whose device memory belongs to a
+pooling allocator, or a serving loop that reserves everything at start-up.  exago_eval_all_static
+keeps its scratch in a static device array inside the library instead.  This test calls it through
+the C ABI twice in a row, on different states, and checks each result against exago_eval_all on
+the same inputs, within the parity tolerance.  It also checks that a batch too large for the array
+is refused.  The file sorts last, so a run that stops at the first failure has run every other
+test before it.
+"""
+import numpy as np
+import pytest
+
+from paper_2203_10587_gb300 import synth
+from parity_util import TOL, assert_close, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ex():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2203_10587_gb300 import build, exago
+    build.build()
+    exago.lib()
+    return exago
+
+
+def _run(ex, net, b, static):
+    import torch
+    d = to_device(b)
+    bt = ex.make_batch(d["x"], d["lam"], d["mask"], d["pd_scale"], d["obj_weight"], b.sigma)
+    out = net.outputs(b.B)
+    fn = ex.exago_eval_all_static if static else ex.exago_eval_all
+    fn(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"], out["hval"])
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("which", ["300bus", "parallel"])
+def test_static_scratch_matches_eval_all_twice(ex, which):
+    if which == "300bus":
+        g = synth.make_grid(37, 300, 389, 77, transformer_frac=0.3, shunts=True)
+    else:
+        from test_capi_host import parallel_grid
+        g = parallel_grid()
+    net = ex.Net(g)
+    for call, seed in enumerate((41, 42)):      # two calls in a row, different states
+        b = synth.random_batch(seed, g, 6, masks=True, pd_scale=True, obj_weight=True,
+                               sigma=0.6 + 0.2 * call)
+        want = _run(ex, net, b, static=False)
+        got = _run(ex, net, b, static=True)
+        for k in want:
+            assert_close(got[k], want[k], f"call {call} {k}", TOL)
+
+
+def test_static_scratch_rejects_oversized_batch(ex):
+    import torch
+    g = synth.grid_2000()
+    net = ex.Net(g)
+    limit = 16 << 20
+    per_state = ex.exago_eval_workspace_size(net.h, 1)
+    B = limit // per_state + 1
+    assert ex.exago_eval_workspace_size(net.h, B) > limit
+    x = torch.zeros(B, net.n, dtype=torch.float64, device="cuda")
+    gh = torch.zeros(B, net.m, dtype=torch.float64, device="cuda")
+    bt = ex.make_batch(x, None, None)
+    with pytest.raises(ex.ExagoError) as ei:
+        ex.exago_eval_all_static(net.h, bt, gh=gh)
+    assert ei.value.name == "EXAGO_EINVAL" and "static scratch" in str(ei.value)
