@@ -33,17 +33,20 @@ UNIT = "evals/s"
 WORKLOAD = "2000-bus x 512 N-1 contingencies: f, grad f, g|h, J values, Lagrangian Hessian values"
 B_DEFAULT = 512
 N_INPUT_SETS = 4
-# FP64 work of the branch kernel per in-service branch with every output requested, counted from
-# its source (fast sincos path): 136 FP64 instructions = 188 flops (an FMA counts 2).
-BRANCH_FP64_INSTR = 136
-BRANCH_FP64_FLOPS = 188
+# FP64 work per unit with every output requested, counted from the kernel source (an FMA counts
+# 2 flops): (flops, instructions).
+FP64_PER_BRANCH = (188, 136)   # branch terms, fast sincos path
+FP64_PER_SLOT = (9, 9)         # one branch end's 9 partial sums at its bus
+FP64_PER_BUS = (20, 15)        # shunt, load and diagonal terms of one bus
+FP64_PER_GEN = (18, 15)        # balance, cost Hessian, gradient and objective terms of one generator
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 2 FP64 FMA per SM per clock x
 # 2 flops x 2.07 GHz (the probe measured 1.20 TFLOP/s at 1.97 GHz under load).
 SMS, FP64_FMA_PER_SM_CLK, SM_MAX_GHZ = 152, 2, 2.07
 FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ / 1e3
 FP64_PEAK_GINSTR = SMS * FP64_FMA_PER_SM_CLK * SM_MAX_GHZ
-# dram bytes of one branch-kernel launch from the ncu capture, or None until profiled
-BRANCH_TRAFFIC_BYTES = 860.7e6   # 303.6 MB read + 557.1 MB write (profiles/k_branch_2000bus_x512.md)
+# dram bytes per launch of the dominant kernel from its ncu capture, by kernel name; a kernel
+# changed since its capture has no entry
+TRAFFIC_BYTES = {}
 
 
 def parse():
@@ -54,6 +57,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--B", type=int, default=B_DEFAULT)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     return p.parse_args()
 
 
@@ -191,6 +195,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     def step(k):
         net.eval_all(batches[k % N_INPUT_SETS], out)
 
+    tuned = None
+    if not args.no_autotune:
+        tuned = exago.exago_net_autotune(net.h, batches[0], out["f"], out["grad"], out["gh"],
+                                         out["jval"], out["hval"], reps=10)
+    launch_cfg = exago.exago_net_get_config(net.h, B)
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
@@ -232,10 +241,22 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     kernels_per_step = len(prof)
     total_prof = sum(ms for _, ms in prof)
     top_name, top_ms = max(prof, key=lambda kv: kv[1])
-    branch_ms = dict(prof).get("branch", top_ms)
-    units = B * grid.nl
-    achieved_tf = BRANCH_FP64_FLOPS * units / (branch_ms * 1e-3) / 1e12
-    achieved_gi = BRANCH_FP64_INSTR * units / (branch_ms * 1e-3) / 1e9
+    # FP64 work of the dominant kernel per launch: the fused persistent kernel does every stage,
+    # the multi-kernel schedule's top kernel is the branch kernel
+    if top_name == "persistent":
+        work = [(FP64_PER_BRANCH, grid.nl), (FP64_PER_SLOT, 2 * grid.nl), (FP64_PER_BUS, grid.nb),
+                (FP64_PER_GEN, grid.ng)]
+        per_unit = ("per state: %d branches x %d + %d branch ends x %d + %d buses x %d + "
+                    "%d generators x %d FP64 flops" % (grid.nl, FP64_PER_BRANCH[0], 2 * grid.nl,
+                    FP64_PER_SLOT[0], grid.nb, FP64_PER_BUS[0], grid.ng, FP64_PER_GEN[0]))
+    else:
+        work = [(FP64_PER_BRANCH, grid.nl)]
+        per_unit = "per state: %d branches x %d FP64 flops" % (grid.nl, FP64_PER_BRANCH[0])
+    flops_state = sum(w[0] * n for w, n in work)
+    instr_state = sum(w[1] * n for w, n in work)
+    units = B
+    achieved_tf = flops_state * units / (top_ms * 1e-3) / 1e12
+    achieved_gi = instr_state * units / (top_ms * 1e-3) / 1e9
 
     # ---- algorithmic HBM bytes per evaluation (read x, lambda, mask; write every output)
     n, m, nnzJ, nnzH = net.n, net.m, net.nnzJ, net.nnzH
@@ -319,13 +340,14 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "kernel_share": {k: v / total_prof for k, v in prof},
         "roofline": {"kernel": top_name, "bound": "alu", "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": BRANCH_TRAFFIC_BYTES,
-                     "per_unit": f"{BRANCH_FP64_FLOPS} FP64 flops ({BRANCH_FP64_INSTR} FP64 instructions) per branch",
-                     "units_per_launch": units, "launch_ms": branch_ms,
+                     "traffic": TRAFFIC_BYTES.get(top_name),
+                     "per_unit": f"{per_unit} = {flops_state} flops ({instr_state} FP64 instructions)",
+                     "units_per_launch": units, "launch_ms": top_ms,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
                      "fp64_instr": {"achieved_g_per_s": achieved_gi, "peak_g_per_s": FP64_PEAK_GINSTR,
                                     "frac": achieved_gi / FP64_PEAK_GINSTR}},
         "gpu_launches": kernels_per_step * args.steps,
+        "launch_config": {"autotuned": tuned, "used": launch_cfg},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": k_e2e},

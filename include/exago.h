@@ -173,6 +173,21 @@ exago_status exago_eval_all(exago_net_t net, const exago_batch *batch, double *f
                             double *gh, double *jval, double *hval);
 
 /*
+ * Adjoint products of the constraint map c(x) = [g(x); h(x)] of eqs. (8)-(9), for solvers and
+ * automatic differentiation, without forming J or the Hessian.  Batch inputs as for the
+ * evaluations; vectors are caller DEVICE buffers, row-major per state.
+ *   exago_eval_jvp:  out [B][m] = J(x) u,              u [B][n]
+ *   exago_eval_jtv:  out [B][n] = J(x)^T v,            v [B][m]
+ *   exago_eval_hvp:  out [B][n] = H u,  u [B][n], H = obj_factor w grad^2 f + sum_i lambda_i
+ *                    grad^2 c_i -- the Lagrangian Hessian of exago_eval_hess (needs lambda).
+ * Out-of-service branches contribute nothing.  EINVAL for null vectors or a missing lambda
+ * (HVP); otherwise as exago_eval_all.  Results are deterministic (fixed summation order).
+ */
+exago_status exago_eval_jvp(exago_net_t net, const exago_batch *batch, const double *u, double *out);
+exago_status exago_eval_jtv(exago_net_t net, const exago_batch *batch, const double *v, double *out);
+exago_status exago_eval_hvp(exago_net_t net, const exago_batch *batch, const double *u, double *out);
+
+/*
  * exago_eval_all without any allocation.  The paper has no counterpart: this serves callers that
  * may not allocate device memory once running -- for example a solver whose device memory belongs
  * to a pooling allocator (a raw cudaMalloc would bypass it, and cudaFree synchronises the device),
@@ -183,7 +198,9 @@ exago_status exago_eval_all(exago_net_t net, const exago_batch *batch, double *f
  *   - The net's device must be current.  The first call on a device looks up the array's device
  *     address (cudaGetSymbolAddress) once for that device; make that first call before any stream
  *     capture.
- *   - EINVAL if the batch's scratch (exago_eval_workspace_size) exceeds the array: split the batch.
+ *   - EINVAL if the batch's scratch exceeds the array: split the batch.  Each state needs
+ *     9 x ceil(2 nl / 32) x 32 doubles of branch-end partials plus 12 doubles per branch that has
+ *     a parallel twin (each part rounded up to 256 bytes for the whole batch).
  *   - All calls share the array: calls that overlap on the GPU race on it, so order them (one
  *     stream, or events).  Nothing in it needs clearing; each call writes all the scratch it reads.
  */
@@ -202,6 +219,56 @@ exago_status exago_eval_all_static(exago_net_t net, const exago_batch *batch, do
 exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, double *f, double *grad,
                                 double *gh, double *jval, double *hval, int reps, int *nkernels,
                                 const char **names, double *ms);
+
+/*
+ * Launch configuration of a net (zero-initialised = automatic).
+ *   schedule  EXAGO_SCHED_AUTO: the autotuned choice for the batch size if exago_net_autotune ran
+ *             for it, else the persistent schedule.  EXAGO_SCHED_KERNELS: one launch per stage
+ *             (branch, bus, fixup, gradient, objective) over the batch.  EXAGO_SCHED_PERSISTENT:
+ *             one fused launch whose CTAs claim branch and bus tiles of all states from a work
+ *             list (the batched evaluation of SCOPFLOW / SOPFLOW subproblems, Sec. V-A, VI-A).
+ *   block     persistent: threads per CTA and items per tile (64, 128, 256; 0 = 128).
+ *   occupancy persistent: resident warps per SM the kernel's registers must allow (24 or 32;
+ *             0 = the compiler's choice).  Higher occupancy can cost register spills.
+ *   lag       persistent: states by which bus tiles trail branch tiles (0 = derived).
+ *   ring      persistent: scratch ring slots, > lag (0 = derived).
+ *   use_graph persistent: EXAGO_GRAPH_DEFAULT / ON launch through a cached instantiated CUDA
+ *             graph (one per distinct argument set, 8 kept); OFF launches directly.  A call on a
+ *             stream that is being captured always launches directly.
+ *   spin_limit  polls (about 0.4 us each) before a device-side wait gives up and records
+ *             EXAGO_ETIMEOUT in the status word (0 = 2^22).
+ *   test_force_timeout  testing only: bus tiles wait for a count that never arrives, so every
+ *             wait times out; the launch still ends and exago_net_check reports it.
+ */
+enum { EXAGO_SCHED_AUTO = 0, EXAGO_SCHED_KERNELS = 1, EXAGO_SCHED_PERSISTENT = 2 };
+enum { EXAGO_GRAPH_DEFAULT = 0, EXAGO_GRAPH_ON = 1, EXAGO_GRAPH_OFF = 2 };
+typedef struct {
+    int schedule;
+    int block;
+    int occupancy;
+    int lag;
+    int ring;
+    int use_graph;
+    long long spin_limit;
+    int test_force_timeout;
+} exago_config;
+
+/* Sets the net's configuration (validated: EINVAL for unknown values or ring <= lag). */
+exago_status exago_net_set_config(exago_net_t net, const exago_config *cfg);
+
+/* The configuration a batch of B states would run with, every derived field filled in. */
+exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg);
+
+/*
+ * Autotuner: times the multi-kernel schedule and persistent variants (block 128 / 256,
+ * occupancy 0 / 24 / 32 warps, two lags)
+ * on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
+ * fastest for batches of this size (used by EXAGO_SCHED_AUTO).  Outputs are written as by
+ * exago_eval_all.  *best (may be NULL) receives the choice.
+ */
+exago_status exago_net_autotune(exago_net_t net, const exago_batch *batch, double *f, double *grad,
+                                double *gh, double *jval, double *hval, int reps,
+                                exago_config *best);
 
 /*
  * Waits for `stream` and returns the device status word of the net: EXAGO_OK, or EXAGO_ETIMEOUT

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -30,16 +31,30 @@ exago_status cuda_fail(cudaError_t e, const char *what) {
 
 }  // namespace
 
+// One instantiated CUDA graph of the persistent schedule, keyed by every argument it bakes in.
+struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+};
+
 struct exago_net {
     HostPlan plan;
     bool on_device = false;
     int device = -1;
+    int sm_count = 0;
     DevNet dev{};
     std::vector<void *> allocs;
     int *status_host = nullptr;   // host-mapped device status word
     void *ws = nullptr;           // internal workspace
     size_t ws_bytes = 0;
-    std::mutex mu;                // guards workspace growth
+    std::mutex mu;                // guards the workspace, the graph cache and the configuration
+    exago_config cfg{};           // user configuration (zeros = automatic)
+    std::map<int, exago_config> tuned;   // autotuned configuration per batch size
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_clock = 0;
+    cudaStream_t cap_stream = nullptr;
+    int occ[9] = {0};             // resident persistent CTAs per SM by (block, occupancy target)
 };
 
 namespace {
@@ -70,6 +85,11 @@ exago_status alloc_dev(exago_net *net, size_t bytes, double **out) {
 }
 
 void free_device(exago_net *net) {
+    if (!net->graphs.empty() || net->cap_stream) cudaDeviceSynchronize();
+    for (auto &g : net->graphs) cudaGraphExecDestroy(g.exec);
+    net->graphs.clear();
+    if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
+    net->cap_stream = nullptr;
     for (void *p : net->allocs) cudaFree(p);
     net->allocs.clear();
     if (net->ws) cudaFree(net->ws);
@@ -86,6 +106,8 @@ exago_status do_upload(exago_net *net) {
     exago_status s;
     cudaError_t e = cudaGetDevice(&net->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&net->sm_count, cudaDevAttrMultiProcessorCount, net->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     d = DevNet{};
     d.nb = p.nb; d.nl = p.nl; d.ng = p.ng; d.n = p.n; d.m = p.m;
     d.nslot = p.nslot;
@@ -158,6 +180,75 @@ exago_status plan_only(int nb, const double *Gs, const double *Bs, const double 
     return EXAGO_OK;
 }
 
+// Launch settings of one call, resolved from the net's configuration and the batch size.
+struct Resolved {
+    int schedule;          // EXAGO_SCHED_KERNELS or EXAGO_SCHED_PERSISTENT
+    int block, occ_warps, grid, lag, ring, use_graph, force_timeout;
+    long long spin_limit;
+};
+
+constexpr long long kDefaultSpinLimit = 1ll << 22;   // polls of ~0.4 us: about 1.7 s
+
+int occ_index(int block, int occ_warps) {
+    return (block == 64 ? 0 : block == 256 ? 2 : 1) * 3 + (occ_warps == 24 ? 1 : occ_warps == 32 ? 2 : 0);
+}
+
+Resolved resolve(exago_net *net, int B) {
+    exago_config c = net->cfg;
+    if (c.schedule == EXAGO_SCHED_AUTO) {
+        auto it = net->tuned.find(B);
+        if (it != net->tuned.end()) {
+            exago_config t = it->second;
+            t.spin_limit = c.spin_limit;
+            t.test_force_timeout = c.test_force_timeout;
+            c = t;
+        }
+    }
+    Resolved r{};
+    r.schedule = c.schedule == EXAGO_SCHED_KERNELS ? EXAGO_SCHED_KERNELS : EXAGO_SCHED_PERSISTENT;
+    r.block = (c.block == 64 || c.block == 256) ? c.block : 128;
+    r.occ_warps = (c.occupancy == 24 || c.occupancy == 32) ? c.occupancy : 0;
+    int &occ = net->occ[occ_index(r.block, r.occ_warps)];
+    if (occ == 0) occ = persist_blocks_per_sm(r.block, r.occ_warps);
+    r.grid = net->sm_count * occ;
+    const int Tbr = (net->plan.nl + r.block - 1) / r.block;
+    // bus tiles trail by the states the resident CTAs can hold in branch work, plus margin
+    int lag = c.lag > 0 ? c.lag : (Tbr > 0 ? (r.grid + Tbr - 1) / Tbr : 1) + 2;
+    if (lag > B) lag = B;
+    if (lag < 1) lag = 1;
+    int ring = c.ring > 0 ? c.ring : 2 * lag + 2;
+    if (ring <= lag) ring = lag + 1;
+    if (ring > B + 1) ring = B + 1 > lag ? B + 1 : lag + 1;
+    r.lag = lag;
+    r.ring = ring;
+    r.use_graph = c.use_graph != EXAGO_GRAPH_OFF;
+    r.spin_limit = c.spin_limit > 0 ? c.spin_limit : kDefaultSpinLimit;
+    r.force_timeout = c.test_force_timeout ? 1 : 0;
+    return r;
+}
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t slot_bytes(const exago_net *net) {
+    return (size_t)NCOMP * (size_t)net->dev.nslot_pad * sizeof(double);
+}
+
+size_t off_bytes(const exago_net *net) { return (size_t)NOFF * (size_t)net->plan.nshared * sizeof(double); }
+
+// Workspace of the persistent schedule: ring scratch, ring parallel-branch scratch, counters.
+size_t persist_bytes(const exago_net *net, const Resolved &r, int B) {
+    return round256(r.ring * slot_bytes(net)) + round256(r.ring * off_bytes(net)) +
+           round256((size_t)(1 + 2 * (size_t)B) * sizeof(int));
+}
+
+size_t need_bytes(exago_net *net, int B) {
+    size_t k = workspace_bytes(net->plan, B);
+    if (!net->on_device) return k;
+    Resolved r = resolve(net, B);
+    size_t p = persist_bytes(net, r, B);
+    return k > p ? k : p;
+}
+
 exago_status check_batch(exago_net *net, const exago_batch *bt, bool need_lam) {
     if (!net) return fail(EXAGO_EINVAL, "net is NULL");
     if (!net->on_device) return fail(EXAGO_ESTATE, "net was planned without a device (exago_net_plan)");
@@ -168,15 +259,15 @@ exago_status check_batch(exago_net *net, const exago_batch *bt, bool need_lam) {
     if (need_lam && !bt->lambda) return fail(EXAGO_EINVAL, "batch lambda is NULL (needed by the Hessian)");
     if (bt->workspace) {
         if (((uintptr_t)bt->workspace & 255) != 0) return fail(EXAGO_EINVAL, "workspace not 256-byte aligned");
-        if (bt->workspace_bytes < workspace_bytes(net->plan, bt->B))
+        std::lock_guard<std::mutex> lk(net->mu);
+        if (bt->workspace_bytes < need_bytes(net, bt->B))
             return fail(EXAGO_EINVAL, "workspace smaller than exago_eval_workspace_size");
     }
     return EXAGO_OK;
 }
 
-exago_status ensure_workspace(exago_net *net, int B) {
-    size_t need = workspace_bytes(net->plan, B);
-    std::lock_guard<std::mutex> lk(net->mu);
+// Caller holds net->mu.
+exago_status ensure_workspace_locked(exago_net *net, size_t need) {
     if (net->ws_bytes >= need) return EXAGO_OK;
     if (net->ws) {
         cudaError_t e = cudaDeviceSynchronize();   // earlier work may still use the old buffer
@@ -191,30 +282,115 @@ exago_status ensure_workspace(exago_net *net, int B) {
     return EXAGO_OK;
 }
 
+exago_status ensure_workspace(exago_net *net, int B) {
+    std::lock_guard<std::mutex> lk(net->mu);
+    return ensure_workspace_locked(net, need_bytes(net, B));
+}
+
+uint64_t bits(double v) {
+    uint64_t u;
+    std::memcpy(&u, &v, sizeof u);
+    return u;
+}
+
+// Launches the persistent schedule through a cached instantiated CUDA graph (memset of the
+// counters + the persistent kernel).  Caller holds net->mu.
+exago_status launch_graph_locked(exago_net *net, const EvalReq &R, const PersistLaunch &pl,
+                                 cudaStream_t stream) {
+    std::vector<uint64_t> key = {
+        (uint64_t)R.x, (uint64_t)R.lam, (uint64_t)R.mask, (uint64_t)R.pd_scale,
+        (uint64_t)R.obj_weight, (uint64_t)R.f, (uint64_t)R.grad, (uint64_t)R.gh,
+        (uint64_t)R.jval, (uint64_t)R.hval, (uint64_t)R.scratch, (uint64_t)R.offscratch,
+        (uint64_t)pl.counters, (uint64_t)R.B, bits(R.sigma), (uint64_t)pl.block,
+        (uint64_t)pl.grid, (uint64_t)pl.lag, (uint64_t)pl.ring, (uint64_t)pl.spin_limit,
+        (uint64_t)pl.occ_warps,
+        (uint64_t)pl.force_timeout};
+    GraphEntry *hit = nullptr;
+    for (auto &g : net->graphs)
+        if (g.key == key) { hit = &g; break; }
+    cudaError_t e;
+    if (!hit) {
+        if (!net->cap_stream) {
+            e = cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate (graph capture)");
+        }
+        e = cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        int le = launch_eval_persistent(net->dev, R, pl, net->cap_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(net->cap_stream, &graph);
+        if (le != 0) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail((cudaError_t)le, "persistent kernel launch (capture)");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        if (net->graphs.size() >= 8) {   // evict the least recently used graph
+            size_t lru = 0;
+            for (size_t i = 1; i < net->graphs.size(); i++)
+                if (net->graphs[i].last_use < net->graphs[lru].last_use) lru = i;
+            cudaDeviceSynchronize();
+            cudaGraphExecDestroy(net->graphs[lru].exec);
+            net->graphs.erase(net->graphs.begin() + lru);
+        }
+        net->graphs.push_back(GraphEntry{key, exec, 0});
+        hit = &net->graphs.back();
+    }
+    hit->last_use = ++net->graph_clock;
+    e = cudaGraphLaunch(hit->exec, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return EXAGO_OK;
+}
+
 exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad, double *gh,
                   double *jval, double *hval, ProfileHook *hook = nullptr) {
     exago_status s = check_batch(net, bt, hval != nullptr);
     if (s != EXAGO_OK || bt->B == 0) return s;
+    std::lock_guard<std::mutex> lk(net->mu);
+    const Resolved rs = resolve(net, bt->B);
     void *ws = bt->workspace;
-    if (!ws && (gh || jval || hval)) {
-        if ((s = ensure_workspace(net, bt->B)) != EXAGO_OK) return s;
+    const bool needs_ws = gh || jval || hval || rs.schedule == EXAGO_SCHED_PERSISTENT;
+    if (!ws && needs_ws) {
+        if ((s = ensure_workspace_locked(net, need_bytes(net, bt->B))) != EXAGO_OK) return s;
         ws = net->ws;
     }
-    const HostPlan &p = net->plan;
     EvalReq R{};
     R.B = bt->B;
     R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask;
     R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
     R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
-    if (ws) {
-        char *w = (char *)ws;
-        const size_t pad = (size_t)net->dev.nslot_pad;
-        R.scratch = (double *)w;
-        w += ((size_t)bt->B * NCOMP * pad * sizeof(double) + 255) / 256 * 256;
-        R.offscratch = (double *)w;
+    cudaStream_t stream = (cudaStream_t)bt->stream;
+    if (rs.schedule == EXAGO_SCHED_KERNELS) {
+        if (ws) {
+            char *w = (char *)ws;
+            R.scratch = (double *)w;
+            w += round256((size_t)bt->B * slot_bytes(net));
+            R.offscratch = (double *)w;
+        }
+        int e = launch_eval(net->dev, R, stream, hook);
+        if (e != 0) return cuda_fail((cudaError_t)e, "evaluation kernel launch");
+        return EXAGO_OK;
     }
-    int e = launch_eval(net->dev, R, bt->stream, hook);
-    if (e != 0) return cuda_fail((cudaError_t)e, "evaluation kernel launch");
+    char *w = (char *)ws;
+    R.scratch = (double *)w;
+    w += round256(rs.ring * slot_bytes(net));
+    R.offscratch = (double *)w;
+    w += round256(rs.ring * off_bytes(net));
+    PersistLaunch pl;
+    pl.block = rs.block; pl.occ_warps = rs.occ_warps; pl.grid = rs.grid; pl.lag = rs.lag;
+    pl.ring = rs.ring;
+    pl.spin_limit = rs.spin_limit; pl.force_timeout = rs.force_timeout;
+    pl.counters = (int *)w;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(stream, &cap);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
+    if (rs.use_graph && !hook && cap == cudaStreamCaptureStatusNone)
+        return launch_graph_locked(net, R, pl, stream);
+    int e = launch_eval_persistent(net->dev, R, pl, stream, hook);
+    if (e != 0) return cuda_fail((cudaError_t)e, "persistent kernel launch");
     return EXAGO_OK;
 }
 
@@ -350,7 +526,8 @@ exago_status exago_net_plan_array(exago_net_t net, const char *name, void *dst, 
 
 exago_status exago_eval_workspace_size(exago_net_t net, int B, size_t *bytes) {
     if (!net || !bytes || B < 0) return fail(EXAGO_EINVAL, "bad argument");
-    *bytes = workspace_bytes(net->plan, B);
+    std::lock_guard<std::mutex> lk(net->mu);
+    *bytes = need_bytes(net, B);
     return EXAGO_OK;
 }
 
@@ -426,6 +603,142 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *bt, double *
     if (s != EXAGO_OK) return s;
     *nkernels = nk;
     for (int k = 0; k < nk; k++) ms[k] = acc[k] / reps;
+    return EXAGO_OK;
+}
+
+namespace {
+
+exago_status adjoint(exago_net *net, const exago_batch *bt, const double *v, double *out,
+                     int mode) {
+    exago_status s = check_batch(net, bt, mode == ADJ_HVP);
+    if (s != EXAGO_OK || bt->B == 0) return s;
+    if (!v || !out) return fail(EXAGO_EINVAL, "input or output vector is NULL");
+    void *ws = bt->workspace;
+    std::lock_guard<std::mutex> lk(net->mu);
+    if (!ws) {
+        if ((s = ensure_workspace_locked(net, need_bytes(net, bt->B))) != EXAGO_OK) return s;
+        ws = net->ws;
+    }
+    AdjReq A{};
+    A.B = bt->B;
+    A.x = bt->x; A.lam = bt->lambda; A.mask = bt->mask; A.obj_weight = bt->obj_weight;
+    A.sigma = bt->obj_factor;
+    A.v = v; A.out = out;
+    A.scratch = (double *)ws;
+    int e = launch_adjoint(net->dev, A, mode, bt->stream);
+    if (e != 0) return cuda_fail((cudaError_t)e, "adjoint kernel launch");
+    return EXAGO_OK;
+}
+
+}  // namespace
+
+exago_status exago_eval_jvp(exago_net_t net, const exago_batch *bt, const double *u, double *out) {
+    return adjoint(net, bt, u, out, ADJ_JVP);
+}
+
+exago_status exago_eval_jtv(exago_net_t net, const exago_batch *bt, const double *v, double *out) {
+    return adjoint(net, bt, v, out, ADJ_JTV);
+}
+
+exago_status exago_eval_hvp(exago_net_t net, const exago_batch *bt, const double *u, double *out) {
+    return adjoint(net, bt, u, out, ADJ_HVP);
+}
+
+exago_status exago_net_set_config(exago_net_t net, const exago_config *cfg) {
+    if (!net || !cfg) return fail(EXAGO_EINVAL, "null argument");
+    if (cfg->schedule < EXAGO_SCHED_AUTO || cfg->schedule > EXAGO_SCHED_PERSISTENT)
+        return fail(EXAGO_EINVAL, "unknown schedule");
+    if (cfg->block != 0 && cfg->block != 64 && cfg->block != 128 && cfg->block != 256)
+        return fail(EXAGO_EINVAL, "block must be 0, 64, 128 or 256");
+    if (cfg->occupancy != 0 && cfg->occupancy != 24 && cfg->occupancy != 32)
+        return fail(EXAGO_EINVAL, "occupancy must be 0, 24 or 32");
+    if (cfg->lag < 0 || cfg->ring < 0 || cfg->spin_limit < 0)
+        return fail(EXAGO_EINVAL, "negative lag, ring or spin limit");
+    if (cfg->ring > 0 && cfg->lag > 0 && cfg->ring <= cfg->lag)
+        return fail(EXAGO_EINVAL, "ring must exceed lag");
+    std::lock_guard<std::mutex> lk(net->mu);
+    net->cfg = *cfg;
+    return EXAGO_OK;
+}
+
+exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg) {
+    if (!net || !cfg || B < 0) return fail(EXAGO_EINVAL, "bad argument");
+    if (!net->on_device) return fail(EXAGO_ESTATE, "net was planned without a device");
+    std::lock_guard<std::mutex> lk(net->mu);
+    const Resolved r = resolve(net, B > 0 ? B : 1);
+    *cfg = net->cfg;
+    cfg->schedule = r.schedule;
+    if (r.schedule == EXAGO_SCHED_PERSISTENT) {
+        cfg->block = r.block;
+        cfg->occupancy = r.occ_warps;
+        cfg->lag = r.lag;
+        cfg->ring = r.ring;
+        cfg->use_graph = r.use_graph;
+    }
+    cfg->spin_limit = r.spin_limit;
+    return EXAGO_OK;
+}
+
+exago_status exago_net_autotune(exago_net_t net, const exago_batch *bt, double *f, double *grad,
+                                double *gh, double *jval, double *hval, int reps,
+                                exago_config *best) {
+    if (reps < 1) return fail(EXAGO_EINVAL, "reps < 1");
+    exago_status s = check_batch(net, bt, hval != nullptr);
+    if (s != EXAGO_OK) return s;
+    if (bt->B == 0) return EXAGO_OK;
+    const exago_config saved = net->cfg;
+    std::vector<exago_config> cands;
+    {
+        exago_config k{};
+        k.schedule = EXAGO_SCHED_KERNELS;
+        cands.push_back(k);
+        for (int block : {128, 256})
+            for (int occw : {0, 24, 32})
+                for (int lagmul : {1, 2}) {
+                    exago_config c{};
+                    c.schedule = EXAGO_SCHED_PERSISTENT;
+                    c.block = block;
+                    c.occupancy = occw;
+                    c.use_graph = EXAGO_GRAPH_ON;
+                    const int Tbr = (net->plan.nl + block - 1) / block;
+                    int &occ = net->occ[occ_index(block, occw)];
+                    if (occ == 0) occ = persist_blocks_per_sm(block, occw);
+                    const int grid = net->sm_count * occ;
+                    c.lag = lagmul * ((Tbr > 0 ? (grid + Tbr - 1) / Tbr : 1) + 2);
+                    c.ring = 2 * c.lag + 2;
+                    cands.push_back(c);
+                }
+    }
+    cudaStream_t st = (cudaStream_t)bt->stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(EXAGO_ECUDA, "cudaEventCreate");
+    float best_ms = 1e30f;
+    exago_config best_cfg = cands[0];
+    for (auto &c : cands) {
+        c.spin_limit = saved.spin_limit;
+        {
+            std::lock_guard<std::mutex> lk(net->mu);
+            net->cfg = c;
+        }
+        s = eval(net, bt, f, grad, gh, jval, hval);   // warm-up (and graph instantiation)
+        if (s != EXAGO_OK) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && s == EXAGO_OK; r++) s = eval(net, bt, f, grad, gh, jval, hval);
+        cudaEventRecord(e1, st);
+        if (s != EXAGO_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { s = fail(EXAGO_ECUDA, "autotune timing"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best_cfg = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(net->mu);
+    net->cfg = saved;
+    if (s != EXAGO_OK) return s;
+    net->tuned[bt->B] = best_cfg;
+    if (best) *best = best_cfg;
     return EXAGO_OK;
 }
 

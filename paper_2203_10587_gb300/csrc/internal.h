@@ -98,6 +98,20 @@ struct EvalReq {
     double *offscratch;         // [B][NOFF][nshared] off-diagonal values of parallel branches
 };
 
+// One adjoint-product call (adjoint.cu): JVP u -> J u, JTV v -> J^T v, HVP u -> (grad^2 L) u.
+enum AdjMode : int { ADJ_JVP = 0, ADJ_JTV = 1, ADJ_HVP = 2 };
+struct AdjReq {
+    int B;
+    const double *x, *lam;          // lam: HVP multipliers [B][m]
+    const uint8_t *mask;
+    const double *obj_weight;
+    double sigma;
+    const double *v;                // JVP / HVP: [B][n]; JTV: [B][m]
+    double *out;                    // JVP: [B][m]; JTV / HVP: [B][n]
+    double *scratch;                // [B][2][nslot_pad]
+};
+int launch_adjoint(const DevNet &net, const AdjReq &req, int mode, void *stream);
+
 size_t workspace_bytes(const HostPlan &p, int B);
 
 // Builds the plan; returns EXAGO_OK or EXAGO_EINVAL with a message in err.
@@ -121,6 +135,21 @@ int launch_admittance(const double *r, const double *x, const double *b, const d
                       int nl, double *Gff, double *Bff, double *Gtt, double *Btt, double *Gft,
                       double *Bft, void *stream);
 int launch_eval(const DevNet &net, const EvalReq &req, void *stream, ProfileHook *hook = nullptr);
+
+// Persistent schedule (one launch; see kernels.cu).  counters: 1 + 2B ints of the workspace;
+// req.scratch / req.offscratch hold `ring` state slots.
+struct PersistLaunch {
+    int block;              // 64, 128 or 256 threads
+    int occ_warps;          // 0, 24 or 32: resident warps per SM the registers must allow
+    int grid;               // CTAs (SM count x resident CTAs per SM)
+    int lag, ring;          // bus tiles trail branch tiles by `lag` states; ring > lag slots
+    long long spin_limit;   // polls before a bounded wait gives up
+    int force_timeout;      // testing only
+    int *counters;
+};
+int launch_eval_persistent(const DevNet &net, const EvalReq &req, const PersistLaunch &pl,
+                           void *stream, ProfileHook *hook = nullptr);
+int persist_blocks_per_sm(int block, int occ_warps);
 
 // Read-only view of a net's plan and device tables (false for NULL or a plan-only net), and the
 // thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.

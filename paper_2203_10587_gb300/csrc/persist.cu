@@ -1,0 +1,220 @@
+// Persistent fused schedule of the polar AC-OPF model evaluation (ExaGO, arXiv 2203.10587,
+// Sec. III, eqs. (7)-(10)) over a batch of independent states (SCOPFLOW contingencies,
+// Sec. V-A; SOPFLOW scenarios, Sec. VI-A; EMPAR subproblems, Sec. V-A): one launch whose CTAs
+// claim branch and bus tiles of every state from a work list.
+#include <cuda_runtime.h>
+
+#include "eval_items.cuh"
+
+namespace exago {
+
+// ---------------------------------------------------------------------------------------------
+// Persistent schedule: one launch of numSMs x (resident CTAs per SM) blocks that claim work items
+// from a ticket counter until the list is empty.  For each state b there are Tbr branch tiles
+// and Tbu bus tiles of blockDim items.  The list is ordered
+//     Br(0) .. Br(L-1), [Br(L) Bu(0)], [Br(L+1) Bu(1)], ..., Bu(B-L) .. Bu(B-1)
+// so that bus tiles trail branch tiles by L states.  The branch partials of state b live in ring
+// slot b mod Rg of the workspace (Rg > L slots, sized to stay in L2), which keeps the
+// branch -> bus hand-off on chip.  Two waits order the work:
+//   * a bus tile of b waits until all Tbr branch tiles of b have signalled;
+//   * a branch tile of b >= Rg waits until all Tbu bus tiles of b - Rg have signalled (ring reuse).
+// Both wait only on items with smaller tickets, which are held by running CTAs and wait only on
+// smaller tickets still; the smallest unfinished ticket never waits, so the launch cannot
+// deadlock.  Every wait is bounded: after spin_limit polls it records a timeout in the status
+// word, skips its work and still signals, so the launch always ends.  Bus tile 0 of each state
+// also writes its parallel-branch fixups and its objective; every bus tile writes the gradient
+// entries of its buses.
+struct PersistParams {
+    int B, Tbr, Tbu, lag, ring, total;
+    int *ctr;               // [1 + 2B]: ticket, branch tiles done per state, bus tiles done
+    long long spin_limit;
+    int force_timeout;      // testing: bus tiles wait for one branch tile more than exists
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Polls *p until it reaches target; false (and a timeout code in the status word) after
+// spin_limit polls.
+__device__ bool bounded_wait(const int *p, int target, long long limit, int *status, int code) {
+    long long it = 0;
+    while (ld_acquire(p) < target) {
+        if (++it > limit) {
+            if (status) *(volatile int *)status = code;
+            return false;
+        }
+        __nanosleep(100);
+    }
+    return true;
+}
+
+enum : int { ST_TIMEOUT_BUS = 1, ST_TIMEOUT_RING = 2 };
+
+__device__ __forceinline__ void decode_item(const PersistParams &P, int t, bool *is_branch, int *b,
+                                            int *tile) {
+    const int L = P.lag, Tbr = P.Tbr, Tbu = P.Tbu;
+    const int head = L * Tbr;
+    if (t < head) {
+        *is_branch = true; *b = t / Tbr; *tile = t % Tbr;
+        return;
+    }
+    const int u = t - head, grp = Tbr + Tbu, ngroups = P.B - L;
+    if (u < ngroups * grp) {
+        const int g = u / grp, r = u % grp;
+        if (r < Tbr) { *is_branch = true; *b = L + g; *tile = r; }
+        else { *is_branch = false; *b = g; *tile = r - Tbr; }
+        return;
+    }
+    const int v = u - ngroups * grp;
+    *is_branch = false; *b = ngroups + v / Tbu; *tile = v % Tbu;
+}
+
+// MINB: resident CTAs per SM the register allocation must allow (1 = compiler's choice).
+template <int WANT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const EvalReq R,
+                                                      const PersistParams P) {
+    __shared__ int s_item, s_ok;
+    __shared__ double s_part[OBJ_LANES];
+    int *done_br = P.ctr + 1, *done_bu = P.ctr + 1 + P.B;
+    const size_t slot_doubles = (size_t)NCOMP * N.nslot_pad;
+    const size_t off_doubles = (size_t)NOFF * N.nshared;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(P.ctr, 1);
+        __syncthreads();
+        const int t = s_item;
+        if (t >= P.total) return;
+        bool is_branch;
+        int b, tile;
+        decode_item(P, t, &is_branch, &b, &tile);
+        const int slot = b % P.ring;
+        double *scr = R.scratch + (size_t)slot * slot_doubles;
+        double *offs = R.offscratch + (size_t)slot * off_doubles;
+        if (is_branch) {
+            if (threadIdx.x == 0)
+                s_ok = b < P.ring || bounded_wait(done_bu + (b - P.ring), P.Tbu, P.spin_limit,
+                                                  N.status, ST_TIMEOUT_RING);
+            __syncthreads();
+            const int l = tile * NT + threadIdx.x;
+            if (s_ok && l < N.nl) branch_item<WANT>(N, R, b, l, scr, offs);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(done_br + b, 1);
+            }
+        } else {
+            if (threadIdx.x == 0)
+                s_ok = bounded_wait(done_br + b, P.Tbr + P.force_timeout, P.spin_limit, N.status,
+                                    ST_TIMEOUT_BUS);
+            __syncthreads();
+            if (s_ok) {
+                __threadfence();
+                const int i = tile * NT + threadIdx.x;
+                if (i < N.nb) {
+                    if (WANT) bus_item<WANT>(N, R, b, i, scr);
+                    if (R.grad) grad_bus(N, R, b, i);
+                }
+                if (tile == 0) {
+                    if (R.jval || R.hval)
+                        for (int e = threadIdx.x; e < N.nfix; e += NT) fixup_entry(N, R, b, e, offs);
+                    if (R.f) obj_block(N, R, b, s_part);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(done_bu + b, 1);
+            }
+        }
+    }
+}
+
+template <int NT, int MINB>
+static void launch_all(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
+                       cudaStream_t st) {
+    k_persist<W_G | W_J | W_H, NT, MINB><<<grid, NT, 0, st>>>(N, R, P);
+}
+
+// CTAs per SM for a target of occ_warps resident warps (0: the compiler's register choice).
+constexpr int minb(int nt, int occ_warps) {
+    return occ_warps <= 0 ? 1 : (occ_warps / (nt / 32) > 0 ? occ_warps / (nt / 32) : 1);
+}
+
+template <int NT>
+static int launch_persist_nt(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
+                             int occ_warps, cudaStream_t st) {
+    const int want = (R.gh ? W_G : 0) | (R.jval ? W_J : 0) | (R.hval ? W_H : 0);
+    if (want == (W_G | W_J | W_H) && occ_warps == 24) {
+        launch_all<NT, minb(NT, 24)>(N, R, P, grid, st);
+        return (int)cudaGetLastError();
+    }
+    if (want == (W_G | W_J | W_H) && occ_warps == 32) {
+        launch_all<NT, minb(NT, 32)>(N, R, P, grid, st);
+        return (int)cudaGetLastError();
+    }
+    switch (want) {
+        case 0: k_persist<0, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
+        case W_G: k_persist<W_G, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
+        case W_J: k_persist<W_J, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
+        case W_G | W_J: k_persist<W_G | W_J, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
+        case W_H: k_persist<W_H, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
+        case W_G | W_H: k_persist<W_G | W_H, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
+        case W_J | W_H: k_persist<W_J | W_H, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
+        default: k_persist<W_G | W_J | W_H, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
+    }
+    return (int)cudaGetLastError();
+}
+
+template <int NT>
+static int occupancy_nt(int occ_warps) {
+    int per_sm = 0;
+    cudaError_t e;
+    if (occ_warps == 24)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_persist<W_G | W_J | W_H, NT, minb(NT, 24)>, NT, 0);
+    else if (occ_warps == 32)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_persist<W_G | W_J | W_H, NT, minb(NT, 32)>, NT, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<W_G | W_J | W_H, NT, 1>,
+                                                          NT, 0);
+    return e == cudaSuccess && per_sm > 0 ? per_sm : 1;
+}
+
+int persist_blocks_per_sm(int block, int occ_warps) {
+    if (block == 256) return occupancy_nt<256>(occ_warps);
+    if (block == 64) return occupancy_nt<64>(occ_warps);
+    return occupancy_nt<128>(occ_warps);
+}
+
+int launch_eval_persistent(const DevNet &N, const EvalReq &R, const PersistLaunch &L,
+                           void *stream, ProfileHook *hk) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (R.B <= 0) return 0;
+    PersistParams P;
+    P.B = R.B;
+    P.Tbr = (N.nl + L.block - 1) / L.block;
+    P.Tbu = (N.nb + L.block - 1) / L.block;
+    P.lag = L.lag < R.B ? L.lag : R.B;
+    P.ring = L.ring;
+    P.total = R.B * (P.Tbr + P.Tbu);
+    P.ctr = L.counters;
+    P.spin_limit = L.spin_limit;
+    P.force_timeout = L.force_timeout;
+    // every wait must point to a smaller ticket: ring slots must outnumber the lag
+    if (P.lag < 1 || P.ring <= P.lag) return (int)cudaErrorInvalidValue;
+    mark(hk, st, "persistent");
+    cudaError_t e = cudaMemsetAsync(L.counters, 0, (size_t)(1 + 2 * R.B) * sizeof(int), st);
+    if (e != cudaSuccess) return (int)e;
+    int grid = L.grid < P.total ? L.grid : P.total;
+    int rc;
+    if (L.block == 256) rc = launch_persist_nt<256>(N, R, P, grid, L.occ_warps, st);
+    else if (L.block == 64) rc = launch_persist_nt<64>(N, R, P, grid, L.occ_warps, st);
+    else rc = launch_persist_nt<128>(N, R, P, grid, L.occ_warps, st);
+    mark(hk, st, "end");
+    return rc;
+}
+
+}  // namespace exago

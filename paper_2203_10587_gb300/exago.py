@@ -28,9 +28,14 @@ EXPORTS = [
     "exago_net_destroy", "exago_net_dims", "exago_net_jac_pattern", "exago_net_hess_pattern",
     "exago_net_ineq_bounds", "exago_net_plan_array", "exago_eval_workspace_size",
     "exago_net_reserve", "exago_eval_obj", "exago_eval_grad", "exago_eval_cons",
-    "exago_eval_jac", "exago_eval_hess", "exago_eval_all", "exago_eval_all_static",
-    "exago_eval_profile", "exago_net_check",
+    "exago_eval_jac", "exago_eval_hess", "exago_eval_all", "exago_eval_jvp", "exago_eval_jtv",
+    "exago_eval_hvp", "exago_eval_all_static",
+    "exago_eval_profile", "exago_net_set_config", "exago_net_get_config", "exago_net_autotune",
+    "exago_net_check",
 ]
+
+SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT = 0, 1, 2
+GRAPH_DEFAULT, GRAPH_ON, GRAPH_OFF = 0, 1, 2
 
 
 class ExagoError(RuntimeError):
@@ -38,6 +43,16 @@ class ExagoError(RuntimeError):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
         self.name = STATUS.get(status, str(status))
+
+
+class exago_config(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int), ("block", ctypes.c_int),
+                ("occupancy", ctypes.c_int), ("lag", ctypes.c_int),
+                ("ring", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("spin_limit", ctypes.c_longlong), ("test_force_timeout", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class exago_batch(ctypes.Structure):
@@ -81,11 +96,18 @@ def lib():
                 "exago_eval_jac": ([vp, ctypes.POINTER(exago_batch), vp], i32),
                 "exago_eval_hess": ([vp, ctypes.POINTER(exago_batch), vp], i32),
                 "exago_eval_all": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp], i32),
+                "exago_eval_jvp": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
+                "exago_eval_jtv": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
+                "exago_eval_hvp": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
                 "exago_eval_all_static": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp],
                                           i32),
                 "exago_eval_profile": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp, i32,
                                         ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.POINTER(ctypes.c_double)], i32),
+                "exago_net_set_config": ([vp, ctypes.POINTER(exago_config)], i32),
+                "exago_net_get_config": ([vp, i32, ctypes.POINTER(exago_config)], i32),
+                "exago_net_autotune": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp, i32,
+                                        ctypes.POINTER(exago_config)], i32),
                 "exago_net_check": ([vp, vp], i32),
             }
             for name, (args, res) in sig.items():
@@ -248,6 +270,24 @@ def exago_eval_all(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None,
                                 _out(hval)))
 
 
+def exago_eval_jvp(h, batch: exago_batch, u, out):
+    """out [B][m] = J u."""
+    import torch
+    _check(lib().exago_eval_jvp(h, ctypes.byref(batch), _dp(u, torch.float64), _out(out)))
+
+
+def exago_eval_jtv(h, batch: exago_batch, v, out):
+    """out [B][n] = J^T v."""
+    import torch
+    _check(lib().exago_eval_jtv(h, ctypes.byref(batch), _dp(v, torch.float64), _out(out)))
+
+
+def exago_eval_hvp(h, batch: exago_batch, u, out):
+    """out [B][n] = (Lagrangian Hessian at the batch's lambda and obj_factor) u."""
+    import torch
+    _check(lib().exago_eval_hvp(h, ctypes.byref(batch), _dp(u, torch.float64), _out(out)))
+
+
 def exago_eval_all_static(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None,
                           hval=None):
     """exago_eval_all with its scratch in the library's static device array (no allocation)."""
@@ -264,6 +304,27 @@ def exago_eval_profile(h, batch: exago_batch, f=None, grad=None, gh=None, jval=N
     _check(lib().exago_eval_profile(h, ctypes.byref(batch), _out(f), _out(grad), _out(gh),
                                     _out(jval), _out(hval), int(reps), ctypes.byref(nk), names, ms))
     return [(names[k].decode(), ms[k]) for k in range(nk.value)]
+
+
+def exago_net_set_config(h, schedule=0, block=0, occupancy=0, lag=0, ring=0, use_graph=0,
+                         spin_limit=0, test_force_timeout=0):
+    c = exago_config(schedule, block, occupancy, lag, ring, use_graph, spin_limit,
+                     test_force_timeout)
+    _check(lib().exago_net_set_config(h, ctypes.byref(c)))
+
+
+def exago_net_get_config(h, B: int) -> dict:
+    c = exago_config()
+    _check(lib().exago_net_get_config(h, int(B), ctypes.byref(c)))
+    return c.as_dict()
+
+
+def exago_net_autotune(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None, hval=None,
+                       reps: int = 5) -> dict:
+    c = exago_config()
+    _check(lib().exago_net_autotune(h, ctypes.byref(batch), _out(f), _out(grad), _out(gh),
+                                    _out(jval), _out(hval), int(reps), ctypes.byref(c)))
+    return c.as_dict()
 
 
 def exago_net_check(h, stream=None):

@@ -1,0 +1,135 @@
+"""GPU: the persistent fused schedule (one launch, work list, ring scratch, bounded waits, CUDA
+graph) against the multi-kernel schedule and the oracle; fault injection of the bounded waits;
+the autotuner.
+"""
+import numpy as np
+import pytest
+
+from paper_2203_10587_gb300 import synth
+from parity_util import compare_instance, gpu_eval, oracle_eval
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ex():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2203_10587_gb300 import build, exago
+    build.build()
+    exago.lib()
+    return exago
+
+
+CONFIGS = [
+    dict(schedule=1),                                   # multi-kernel
+    dict(schedule=2),                                   # persistent, derived lag/ring, graph
+    dict(schedule=2, use_graph=2),                      # persistent, direct launch
+    dict(schedule=2, block=64, lag=1, ring=2),          # tightest ring: every state reuses a slot
+    dict(schedule=2, block=256, lag=3, ring=5),
+    dict(schedule=2, occupancy=32),                     # register-capped variant
+    dict(schedule=2, block=256, occupancy=24),
+]
+
+
+def grids():
+    from test_capi_host import parallel_grid
+    return {
+        "300bus": (synth.make_grid(71, 300, 389, 77, transformer_frac=0.3, shunts=True), 23),
+        "parallel": (parallel_grid(), 9),
+        "2000bus": (synth.grid_2000(), 40),
+    }
+
+
+@pytest.mark.parametrize("name", ["300bus", "parallel", "2000bus"])
+def test_schedules_bitwise_equal_and_match_oracle(ex, oracle_mod, name):
+    g, B = grids()[name]
+    b = synth.random_batch(5, g, B, masks=True, pd_scale=True, obj_weight=True, sigma=0.9)
+    net = ex.Net(g)
+    outs = []
+    for cfg in CONFIGS:
+        ex.exago_net_set_config(net.h, **cfg)
+        outs.append(gpu_eval(net, b))
+        outs.append(gpu_eval(net, b))          # second call: cached graph / reused ring
+    for o in outs[1:]:
+        for k in outs[0]:
+            np.testing.assert_array_equal(o[k], outs[0][k], err_msg=k)
+    for i in (0, B // 2, B - 1):
+        compare_instance(outs[0], i, oracle_eval(oracle_mod, g, b, i), name)
+
+
+def test_single_state_and_subset_outputs(ex, oracle_mod):
+    g = synth.grid_10k()
+    b = synth.random_batch(8, g, 1)
+    net = ex.Net(g)
+    ex.exago_net_set_config(net.h, schedule=2)
+    out = gpu_eval(net, b)
+    compare_instance(out, 0, oracle_eval(oracle_mod, g, b, 0), "10k persistent")
+    # only some outputs requested: each must equal the full call
+    for which in (("f",), ("grad",), ("gh",), ("jval",), ("hval",), ("f", "hval")):
+        part = gpu_eval(net, b, which=which)
+        for k in which:
+            np.testing.assert_array_equal(part[k], out[k], err_msg=str(which))
+
+
+def test_bounded_wait_timeout_is_reported_and_context_survives(ex):
+    """Every bus tile waits for a branch count that never arrives; the launch still ends."""
+    g = synth.make_grid(73, 60, 80, 15)
+    b = synth.random_batch(73, g, 4)
+    net = ex.Net(g)
+    ex.exago_net_set_config(net.h, schedule=2, use_graph=2, spin_limit=2000, test_force_timeout=1)
+    import torch
+    from parity_util import to_device
+    d = to_device(b)
+    bt = ex.make_batch(d["x"], d["lam"])
+    out = net.outputs(b.B)
+    net.eval_all(bt, out)
+    with pytest.raises(ex.ExagoError) as ei:
+        ex.exago_net_check(net.h)
+    assert ei.value.name == "EXAGO_ETIMEOUT"
+    ex.exago_net_check(net.h)          # the word was cleared
+    ex.exago_net_set_config(net.h, schedule=2)
+    good = gpu_eval(net, b)            # the context is still usable
+    ex.exago_net_set_config(net.h, schedule=1)
+    ref = gpu_eval(net, b)
+    for k in ref:
+        np.testing.assert_array_equal(good[k], ref[k])
+
+
+def test_autotune_picks_a_valid_configuration(ex):
+    g = synth.grid_2000()
+    b = synth.contingency_batch(3, g, 64)
+    net = ex.Net(g)
+    from parity_util import to_device
+    d = to_device(b)
+    bt = ex.make_batch(d["x"], d["lam"], d["mask"])
+    out = net.outputs(b.B)
+    best = ex.exago_net_autotune(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"],
+                                 out["hval"], reps=3)
+    assert best["schedule"] in (1, 2)
+    ex.exago_net_set_config(net.h)     # automatic: uses the tuned choice for B = 64
+    got = ex.exago_net_get_config(net.h, 64)
+    assert got["schedule"] == best["schedule"]
+    a = gpu_eval(net, b)
+    ex.exago_net_set_config(net.h, schedule=1)
+    k = gpu_eval(net, b)
+    for key in a:
+        np.testing.assert_array_equal(a[key], k[key])
+
+
+def test_profile_names_the_persistent_kernel(ex):
+    g = synth.grid_30bus()
+    b = synth.random_batch(1, g, 8)
+    net = ex.Net(g)
+    from parity_util import to_device
+    d = to_device(b)
+    bt = ex.make_batch(d["x"], d["lam"])
+    out = net.outputs(b.B)
+    ex.exago_net_set_config(net.h, schedule=2)
+    prof = ex.exago_eval_profile(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"],
+                                 out["hval"], reps=3)
+    assert [n for n, _ in prof] == ["persistent"] and prof[0][1] > 0
+    ex.exago_net_set_config(net.h, schedule=1)
+    prof = ex.exago_eval_profile(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"],
+                                 out["hval"], reps=3)
+    assert [n for n, _ in prof] == ["branch", "bus", "grad", "obj"]

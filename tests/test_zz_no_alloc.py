@@ -56,16 +56,22 @@ def test_static_scratch_matches_eval_all_twice(ex, which):
 
 
 def test_static_scratch_rejects_oversized_batch(ex):
+    """The largest batch that fits the 16 MiB array runs; one state more is refused."""
     import torch
-    g = synth.grid_2000()
+    g = synth.grid_2000()                      # no parallel branches
     net = ex.Net(g)
     limit = 16 << 20
-    per_state = ex.exago_eval_workspace_size(net.h, 1)
-    B = limit // per_state + 1
-    assert ex.exago_eval_workspace_size(net.h, B) > limit
-    x = torch.zeros(B, net.n, dtype=torch.float64, device="cuda")
-    gh = torch.zeros(B, net.m, dtype=torch.float64, device="cuda")
-    bt = ex.make_batch(x, None, None)
-    with pytest.raises(ex.ExagoError) as ei:
-        ex.exago_eval_all_static(net.h, bt, gh=gh)
-    assert ei.value.name == "EXAGO_EINVAL" and "static scratch" in str(ei.value)
+    per_state = 9 * ((2 * g.nl + 31) // 32 * 32) * 8
+    B_ok = limit // per_state
+    for B in (B_ok, B_ok + 1):
+        x = torch.zeros(B, net.n, dtype=torch.float64, device="cuda")
+        x[:, g.nb:2 * g.nb] = 1.0
+        gh = torch.zeros(B, net.m, dtype=torch.float64, device="cuda")
+        bt = ex.make_batch(x, None, None)
+        if B == B_ok:
+            ex.exago_eval_all_static(net.h, bt, gh=gh)
+            torch.cuda.synchronize()
+        else:
+            with pytest.raises(ex.ExagoError) as ei:
+                ex.exago_eval_all_static(net.h, bt, gh=gh)
+            assert ei.value.name == "EXAGO_EINVAL" and "static scratch" in str(ei.value)
