@@ -112,11 +112,13 @@ exago_status exago_net_hess_pattern(exago_net_t net, int64_t *rowptr, int *col);
 exago_status exago_net_ineq_bounds(exago_net_t net, double *hlo, double *hhi);
 
 /*
- * Copies one of the plan's integer tables (output positions of each kernel's writes) into a
- * caller host buffer, for inspection and tests.  name is one of: br_off ([12][nl]), br_slot
- * ([2][nl]), br_shared, slot_ptr, bus_jP, bus_jQ, bus_k, bus_h ([3][nb]), gen_ptr, gen_ord,
- * gen_jP, gen_jQ, gen_h, fix_ptr, fix_src, fix_dst (int32) and fix_isH (uint8).  *needed receives
- * the size in bytes; dst may be NULL to query it.  EINVAL for an unknown name or small buffer.
+ * Copies one of the plan's int32 tables into a caller host buffer, for inspection and tests:
+ * slot_ptr ([nb+1]), slot_nbr ([2 nl] other bus of each slot; slots are ordered by (bus, other
+ * bus, branch)), slot_ref ([2 nl] record 2 l + end of each slot), bus_jP / bus_jQ (J row starts of
+ * P_i / Q_i), bus_hA / bus_hM (H row starts of Va_i / Vm_i), bus_k (neighbours + 1), bus_nlow
+ * (neighbours below i), bus_perm (the bus phase's thread order: each aligned group of 64 buses
+ * sorted by descending degree), gen_ptr ([nb+1]) and gen_ord ([ng]).  *needed receives the size in bytes;
+ * dst may be NULL to query it.  EINVAL for an unknown name or a small buffer.
  */
 exago_status exago_net_plan_array(exago_net_t net, const char *name, void *dst, size_t bytes,
                                   size_t *needed);
@@ -149,8 +151,8 @@ typedef struct {
     size_t workspace_bytes;
 } exago_batch;
 
-/* Scratch bytes one evaluation of B states needs (per branch end partial sums, and the
- * off-diagonal values of parallel branches). */
+/* Scratch bytes one evaluation of B states needs under the net's configuration (branch-end
+ * values, and the persistent schedule's counters); enough for either schedule. */
 exago_status exago_eval_workspace_size(exago_net_t net, int B, size_t *bytes);
 
 /* Grows the net's internal workspace to hold B states now, so later calls allocate nothing. */
@@ -199,8 +201,7 @@ exago_status exago_eval_hvp(exago_net_t net, const exago_batch *batch, const dou
  *     address (cudaGetSymbolAddress) once for that device; make that first call before any stream
  *     capture.
  *   - EINVAL if the batch's scratch exceeds the array: split the batch.  Each state needs
- *     9 x ceil(2 nl / 32) x 32 doubles of branch-end partials plus 12 doubles per branch that has
- *     a parallel twin (each part rounded up to 256 bytes for the whole batch).
+ *     12 x 2 nl doubles of branch-end records (the batch's total rounded up to 256 bytes).
  *   - All calls share the array: calls that overlap on the GPU race on it, so order them (one
  *     stream, or events).  Nothing in it needs clearing; each call writes all the scratch it reads.
  */
@@ -212,8 +213,8 @@ exago_status exago_eval_all_static(exago_net_t net, const exago_batch *batch, do
  * Per-kernel timing of exago_eval_all (tracing and benchmarks).  Runs the same evaluation `reps`
  * times on batch->stream with a CUDA event recorded on that stream before every kernel launch and
  * after the last one, waits for each repetition, and returns the mean duration in milliseconds of
- * each kernel of one evaluation: names[k] (static strings: "branch", "bus", "fixup", "grad",
- * "obj") and ms[k] for k < *nkernels.  names and ms need room for 16 entries.  Outputs are those
+ * each kernel of one evaluation: names[k] (static strings: "branch", "bus", "grad", "obj" for
+ * the multi-kernel schedule, "persistent" for the fused one) and ms[k] for k < *nkernels.  names and ms need room for 16 entries.  Outputs are those
  * of exago_eval_all.  EINVAL for reps < 1 or null names/ms/nkernels.
  */
 exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, double *f, double *grad,

@@ -3,8 +3,9 @@
 //   JVP  out[B][m] = J(x) u                       (u [B][n])
 //   JTV  out[B][n] = J(x)^T v                     (v [B][m])
 //   HVP  out[B][n] = (sigma grad^2 f + sum_i lam_i grad^2 c_i)(x) u     (u [B][n])
-// Each branch end writes two partials (its bus's Va and Vm component, or its P and Q row for
-// JVP) to a slot-sorted scratch that the bus kernel sums in slot order, as in the evaluation.
+// Each branch end writes a two-value record (its bus's Va and Vm component, or its P and Q row for
+// JVP), ordered by branch; the bus kernel gathers its slots' records and sums them in slot order,
+// as in the evaluation.
 // The branch terms are the evaluation's own (end_terms, end_hess), so HVP applies exactly the
 // Hessian values that exago_eval_hess writes.
 #include <cuda_runtime.h>
@@ -17,13 +18,12 @@ template <int MODE>
 __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A, int b, int l,
                                                 double *scr) {
     const int nb = N.nb, nl = N.nl;
-    const size_t pad = (size_t)N.nslot_pad;
-    const int sf = __ldg(N.br_slot + l), st = __ldg(N.br_slot + nl + l);
+    double *rf = scr + 4 * (size_t)l, *rt = rf + 2;     // records of the from and to end
     const int fb = __ldg(N.f + l), tb = __ldg(N.t + l);
     const bool on = A.mask == nullptr || A.mask[(size_t)b * nl + l] != 0;
     if (!on) {
-        scr[sf] = 0.0; scr[pad + sf] = 0.0;
-        scr[st] = 0.0; scr[pad + st] = 0.0;
+        put2(rf, 0, 0.0, 0.0);
+        put2(rt, 0, 0.0, 0.0);
         if (MODE == ADJ_JVP) {
             A.out[(size_t)b * N.m + 2 * nb + l] = 0.0;
             A.out[(size_t)b * N.m + 2 * nb + nl + l] = 0.0;
@@ -52,8 +52,8 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
         const double dQf = fma(ef.qa, dA, fma(ef.qu, uMf, ef.qv * uMt));
         const double dPt = fma(et.pa, -dA, fma(et.pu, uMt, et.pv * uMf));
         const double dQt = fma(et.qa, -dA, fma(et.qu, uMt, et.qv * uMf));
-        scr[sf] = dPf; scr[pad + sf] = dQf;
-        scr[st] = dPt; scr[pad + st] = dQt;
+        put2(rf, 0, dPf, dQf);
+        put2(rt, 0, dPt, dQt);
         double *ob = A.out + (size_t)b * N.m;
         ob[2 * nb + l] = 2.0 * fma(ef.P, dPf, ef.Q * dQf);
         ob[2 * nb + nl + l] = 2.0 * fma(et.P, dPt, et.Q * dQt);
@@ -70,8 +70,8 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
         const double mf = fma(wPf, ef.pu, fma(wQf, ef.qu, fma(wPt, et.pv, wQt * et.qv)));
         const double mt = fma(wPt, et.pu, fma(wQt, et.qu, fma(wPf, ef.pv, wQf * ef.qv)));
         const double da = af - at;
-        scr[sf] = da; scr[pad + sf] = mf;
-        scr[st] = dneg(da); scr[pad + st] = mt;
+        put2(rf, 0, da, mf);
+        put2(rt, 0, dneg(da), mt);
     } else {
         const double *lb = A.lam + (size_t)b * N.m;
         const double lPf = __ldg(lb + fb), lPt = __ldg(lb + tb);
@@ -90,8 +90,8 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
         const double rAf = fma(haa, dA, fma(xf, uMf, -(xt * uMt)));
         const double rMf = fma(xf, dA, fma(mff, uMf, mft * uMt));
         const double rMt = fma(-xt, dA, fma(mft, uMf, mtt * uMt));
-        scr[sf] = rAf; scr[pad + sf] = rMf;
-        scr[st] = dneg(rAf); scr[pad + st] = rMt;
+        put2(rf, 0, rAf, rMf);
+        put2(rt, 0, dneg(rAf), rMt);
     }
 }
 
@@ -99,13 +99,13 @@ template <int MODE>
 __device__ __forceinline__ void adj_bus_item(const DevNet &N, const AdjReq &A, int b, int i,
                                              const double *scr) {
     const int nb = N.nb, ng = N.ng;
-    const size_t pad = (size_t)N.nslot_pad;
     const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
     double s0v = 0.0, s1v = 0.0;
     for (int s = s0; s < s1; s++) {
-        s0v += __ldcg(scr + s);
-        s1v += __ldcg(scr + pad + s);
+        const double2 r = ld2(scr + 2 * (size_t)__ldg(N.slot_ref + s));
+        s0v += r.x;
+        s1v += r.y;
     }
     const double *xb = A.x + (size_t)b * N.n;
     const double Vm = __ldg(xb + nb + i);
@@ -162,14 +162,14 @@ template <int MODE>
 __global__ void __launch_bounds__(128) k_adj_branch(const DevNet N, const AdjReq A, int b0) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = b0 + blockIdx.y;
-    if (l < N.nl) adj_branch_item<MODE>(N, A, b, l, A.scratch + (size_t)b * 2 * N.nslot_pad);
+    if (l < N.nl) adj_branch_item<MODE>(N, A, b, l, A.scratch + (size_t)b * 2 * N.nslot);
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(128) k_adj_bus(const DevNet N, const AdjReq A, int b0) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = b0 + blockIdx.y;
-    if (i < N.nb) adj_bus_item<MODE>(N, A, b, i, A.scratch + (size_t)b * 2 * N.nslot_pad);
+    if (i < N.nb) adj_bus_item<MODE>(N, A, b, i, A.scratch + (size_t)b * 2 * N.nslot);
 }
 
 template <int MODE>

@@ -111,21 +111,33 @@ exago_status do_upload(exago_net *net) {
     d = DevNet{};
     d.nb = p.nb; d.nl = p.nl; d.ng = p.ng; d.n = p.n; d.m = p.m;
     d.nslot = p.nslot;
-    d.nslot_pad = (p.nslot + 31) / 32 * 32;
-    d.nshared = p.nshared;
-    d.nfix = (int)p.fix_dst.size();
     d.nnzJ = p.nnzJ; d.nnzJg = p.nnzJg; d.nnzH = p.nnzH;
+    d.hpg = p.Hrowptr[2 * p.nb];
+    d.jP_end = (int)p.Jrowptr[p.nb];
+    d.jQ_end = (int)p.Jrowptr[2 * p.nb];
+    d.hA_end = (int)p.Hrowptr[p.nb];
+    d.hM_end = (int)p.Hrowptr[2 * p.nb];
+    for (int t = 0; t < 3; t++) {   // largest bus tile's row segments, tiles of 64/128/256 buses
+        const int T = 64 << t;
+        int64_t worst = 0;
+        for (int i0 = 0; i0 < p.nb; i0 += T) {
+            const int i1 = i0 + T < p.nb ? i0 + T : p.nb;
+            const int64_t need = 2 * (p.Jrowptr[i1] - p.Jrowptr[i0]) +
+                                 (p.Hrowptr[i1] - p.Hrowptr[i0]) +
+                                 (p.Hrowptr[p.nb + i1] - p.Hrowptr[p.nb + i0]);
+            if (need > worst) worst = need;
+        }
+        d.stage_cap[t] = (int)(worst < kStageMaxDoubles ? worst : kStageMaxDoubles);
+    }
     d.baseMVA = p.baseMVA;
 #define UP(field, vec) if ((s = upload(net, p.vec, &d.field)) != EXAGO_OK) return s
     UP(f, f); UP(t, t);
-    UP(br_off, br_off); UP(br_slot, br_slot); UP(br_shared, br_shared);
-    UP(slot_ptr, slot_ptr);
-    UP(bus_jP, bus_jP); UP(bus_jQ, bus_jQ); UP(bus_k, bus_k); UP(bus_h, bus_h);
+    UP(slot_ptr, slot_ptr); UP(slot_nbr, slot_nbr); UP(slot_ref, slot_ref);
+    UP(bus_jP, bus_jP); UP(bus_jQ, bus_jQ); UP(bus_hA, bus_hA); UP(bus_hM, bus_hM);
+    UP(bus_k, bus_k); UP(bus_nlow, bus_nlow); UP(bus_perm, bus_perm);
     UP(Gs, Gs); UP(Bs, Bs); UP(Pd, Pd); UP(Qd, Qd);
-    UP(gen_ptr, gen_ptr); UP(gen_ord, gen_ord); UP(gen_bus, gbus);
-    UP(gen_jP, gen_jP); UP(gen_jQ, gen_jQ); UP(gen_h, gen_h);
+    UP(gen_ptr, gen_ptr); UP(gen_ord, gen_ord);
     UP(c2, c2); UP(c1, c1); UP(c0, c0);
-    UP(fix_ptr, fix_ptr); UP(fix_src, fix_src); UP(fix_dst, fix_dst); UP(fix_isH, fix_isH);
 #undef UP
     // branch parameters, then the pi-model admittances evaluated on the device
     const double *r = nullptr, *x = nullptr, *b = nullptr, *tap = nullptr;
@@ -150,6 +162,17 @@ exago_status do_upload(exago_net *net) {
     *net->status_host = 0;
     e = cudaHostGetDevicePointer((void **)&d.status, net->status_host, 0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaHostGetDevicePointer (status word)");
+    {   // once per device: let the staged bus kernels use more than 48 KB of shared memory
+        static std::mutex mu;
+        static bool done[64] = {false};
+        std::lock_guard<std::mutex> lk(mu);
+        if (net->device >= 0 && net->device < 64 && !done[net->device]) {
+            int le2 = persist_allow_stage();
+            if (le2 == 0) le2 = bus_allow_stage();
+            if (le2 != 0) return cuda_fail((cudaError_t)le2, "cudaFuncSetAttribute");
+            done[net->device] = true;
+        }
+    }
     net->on_device = true;
     return EXAGO_OK;
 }
@@ -209,7 +232,9 @@ Resolved resolve(exago_net *net, int B) {
     r.block = (c.block == 64 || c.block == 256) ? c.block : 128;
     r.occ_warps = (c.occupancy == 24 || c.occupancy == 32) ? c.occupancy : 0;
     int &occ = net->occ[occ_index(r.block, r.occ_warps)];
-    if (occ == 0) occ = persist_blocks_per_sm(r.block, r.occ_warps);
+    if (occ == 0)
+        occ = persist_blocks_per_sm(r.block, r.occ_warps,
+                                    (size_t)net->dev.stage_cap[stage_index(r.block)] * sizeof(double));
     r.grid = net->sm_count * occ;
     const int Tbr = (net->plan.nl + r.block - 1) / r.block;
     // bus tiles trail by the states the resident CTAs can hold in branch work, plus margin
@@ -230,15 +255,12 @@ Resolved resolve(exago_net *net, int B) {
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t slot_bytes(const exago_net *net) {
-    return (size_t)NCOMP * (size_t)net->dev.nslot_pad * sizeof(double);
+    return (size_t)NCOMP * (size_t)net->dev.nslot * sizeof(double);
 }
 
-size_t off_bytes(const exago_net *net) { return (size_t)NOFF * (size_t)net->plan.nshared * sizeof(double); }
-
-// Workspace of the persistent schedule: ring scratch, ring parallel-branch scratch, counters.
+// Workspace of the persistent schedule: ring scratch, then counters.
 size_t persist_bytes(const exago_net *net, const Resolved &r, int B) {
-    return round256(r.ring * slot_bytes(net)) + round256(r.ring * off_bytes(net)) +
-           round256((size_t)(1 + 2 * (size_t)B) * sizeof(int));
+    return round256(r.ring * slot_bytes(net)) + round256((size_t)(1 + 2 * (size_t)B) * sizeof(int));
 }
 
 size_t need_bytes(exago_net *net, int B) {
@@ -300,7 +322,7 @@ exago_status launch_graph_locked(exago_net *net, const EvalReq &R, const Persist
     std::vector<uint64_t> key = {
         (uint64_t)R.x, (uint64_t)R.lam, (uint64_t)R.mask, (uint64_t)R.pd_scale,
         (uint64_t)R.obj_weight, (uint64_t)R.f, (uint64_t)R.grad, (uint64_t)R.gh,
-        (uint64_t)R.jval, (uint64_t)R.hval, (uint64_t)R.scratch, (uint64_t)R.offscratch,
+        (uint64_t)R.jval, (uint64_t)R.hval, (uint64_t)R.scratch,
         (uint64_t)pl.counters, (uint64_t)R.B, bits(R.sigma), (uint64_t)pl.block,
         (uint64_t)pl.grid, (uint64_t)pl.lag, (uint64_t)pl.ring, (uint64_t)pl.spin_limit,
         (uint64_t)pl.occ_warps,
@@ -364,12 +386,7 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
     R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
     cudaStream_t stream = (cudaStream_t)bt->stream;
     if (rs.schedule == EXAGO_SCHED_KERNELS) {
-        if (ws) {
-            char *w = (char *)ws;
-            R.scratch = (double *)w;
-            w += round256((size_t)bt->B * slot_bytes(net));
-            R.offscratch = (double *)w;
-        }
+        R.scratch = (double *)ws;
         int e = launch_eval(net->dev, R, stream, hook);
         if (e != 0) return cuda_fail((cudaError_t)e, "evaluation kernel launch");
         return EXAGO_OK;
@@ -377,8 +394,6 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
     char *w = (char *)ws;
     R.scratch = (double *)w;
     w += round256(rs.ring * slot_bytes(net));
-    R.offscratch = (double *)w;
-    w += round256(rs.ring * off_bytes(net));
     PersistLaunch pl;
     pl.block = rs.block; pl.occ_warps = rs.occ_warps; pl.grid = rs.grid; pl.lag = rs.lag;
     pl.ring = rs.ring;
@@ -508,12 +523,11 @@ exago_status exago_net_plan_array(exago_net_t net, const char *name, void *dst, 
     const void *src = nullptr;
     size_t n = 0;
 #define ARR(key, vec) if (!std::strcmp(name, key)) { src = p.vec.data(); n = p.vec.size() * sizeof(p.vec[0]); }
-    ARR("br_off", br_off) else ARR("br_slot", br_slot) else ARR("br_shared", br_shared)
-    else ARR("slot_ptr", slot_ptr) else ARR("bus_jP", bus_jP) else ARR("bus_jQ", bus_jQ)
-    else ARR("bus_k", bus_k) else ARR("bus_h", bus_h) else ARR("gen_ptr", gen_ptr)
-    else ARR("gen_ord", gen_ord) else ARR("gen_jP", gen_jP) else ARR("gen_jQ", gen_jQ)
-    else ARR("gen_h", gen_h) else ARR("fix_ptr", fix_ptr) else ARR("fix_src", fix_src)
-    else ARR("fix_dst", fix_dst) else ARR("fix_isH", fix_isH)
+    ARR("slot_ptr", slot_ptr) else ARR("slot_nbr", slot_nbr) else ARR("slot_ref", slot_ref)
+    else ARR("bus_jP", bus_jP) else ARR("bus_jQ", bus_jQ) else ARR("bus_hA", bus_hA)
+    else ARR("bus_hM", bus_hM) else ARR("bus_k", bus_k) else ARR("bus_nlow", bus_nlow)
+    else ARR("bus_perm", bus_perm)
+    else ARR("gen_ptr", gen_ptr) else ARR("gen_ord", gen_ord)
     else return fail(EXAGO_EINVAL, std::string("unknown plan array ") + name);
 #undef ARR
     if (needed) *needed = n;
@@ -702,7 +716,10 @@ exago_status exago_net_autotune(exago_net_t net, const exago_batch *bt, double *
                     c.use_graph = EXAGO_GRAPH_ON;
                     const int Tbr = (net->plan.nl + block - 1) / block;
                     int &occ = net->occ[occ_index(block, occw)];
-                    if (occ == 0) occ = persist_blocks_per_sm(block, occw);
+                    if (occ == 0)
+                        occ = persist_blocks_per_sm(block, occw,
+                                                    (size_t)net->dev.stage_cap[stage_index(block)] *
+                                                        sizeof(double));
                     const int grid = net->sm_count * occ;
                     c.lag = lagmul * ((Tbr > 0 ? (grid + Tbr - 1) / Tbr : 1) + 2);
                     c.ring = 2 * c.lag + 2;

@@ -128,43 +128,37 @@ __device__ __forceinline__ void store_hrow(double *Jrow, const End &e, bool self
     }
 }
 
-// One (state b, branch l) item.  scr is state b's slot-partial scratch ([NCOMP][nslot_pad]) and
-// offs its parallel-branch scratch ([NOFF][nshared]).
+// Stores a pair of components of a record (16-byte aligned: records are 96 bytes).
+__device__ __forceinline__ void put2(double *rec, int c, double a, double b) {
+    *reinterpret_cast<double2 *>(rec + c) = make_double2(a, b);
+}
+
+// One (state b, branch l) item.  scr is state b's record scratch ([2 nl][NCOMP]).  The branch
+// writes its two h values, its two Jacobian h rows (four entries each, contiguous) and the
+// records of both ends, all to addresses contiguous across a warp; the bus phase assembles
+// everything else row by row.
 template <int WANT>
 __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, int b, int l,
-                                            double *scr, double *offs_base) {
+                                            double *scr) {
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     constexpr bool DERIV = WJ || WH;
     const int nb = N.nb, nl = N.nl;
-    const size_t pad = (size_t)N.nslot_pad;
-    const int sf = __ldg(N.br_slot + l), st = __ldg(N.br_slot + nl + l);
+    double *rf = scr + (size_t)(2 * l) * NCOMP, *rt = rf + NCOMP;
     const int fb = __ldg(N.f + l), tb = __ldg(N.t + l);
-    const int sh = N.nshared ? __ldg(N.br_shared + l) : -1;
-    double *Jb = WJ ? R.jval + (size_t)b * N.nnzJ : nullptr;
-    double *Hb = WH ? R.hval + (size_t)b * N.nnzH : nullptr;
-    double *offs = sh >= 0 ? offs_base + sh : nullptr;
-    auto put_off = [&](int c, double v, double *base) {
-        if (sh >= 0) offs[(size_t)c * N.nshared] = v;
-        else base[__ldg(N.br_off + (size_t)c * nl + l)] = v;
-    };
-    double *Jf = WJ ? Jb + N.nnzJg + 4 * (size_t)l : nullptr;
-    double *Jt = WJ ? Jb + N.nnzJg + 4 * (size_t)nl + 4 * (size_t)l : nullptr;
+    double *Jf = WJ ? R.jval + (size_t)b * N.nnzJ + N.nnzJg + 4 * (size_t)l : nullptr;
+    double *Jt = WJ ? Jf + 4 * (size_t)nl : nullptr;
     double *ghb = R.gh ? R.gh + (size_t)b * N.m : nullptr;
 
     const bool on = R.mask == nullptr || R.mask[(size_t)b * nl + l] != 0;
     if (!on) {   // out of service: every value of this branch is zero
-        scr[SC_P * pad + sf] = 0.0; scr[SC_Q * pad + sf] = 0.0;
-        scr[SC_P * pad + st] = 0.0; scr[SC_Q * pad + st] = 0.0;
+        for (double *r : {rf, rt}) {
+            put2(r, SC_P, 0.0, 0.0);
+            if (WJ) { put2(r, SC_PA, 0.0, 0.0); put2(r, SC_PV, 0.0, 0.0); put2(r, SC_QU, 0.0, 0.0); }
+            if (WH) { put2(r, SC_HAA, 0.0, 0.0); put2(r, SC_HUU, 0.0, 0.0); }
+        }
         if (WG && ghb) { ghb[2 * nb + l] = 0.0; ghb[2 * nb + nl + l] = 0.0; }
-        if (WJ) {
-            for (int c = SC_PA; c <= SC_QU; c++) { scr[c * pad + sf] = 0.0; scr[c * pad + st] = 0.0; }
-            for (int c = OJ_PF_VAT; c <= OJ_QT_VMF; c++) put_off(c, 0.0, Jb);
+        if (WJ)
             for (int k = 0; k < 4; k++) { Jf[k] = 0.0; Jt[k] = 0.0; }
-        }
-        if (WH) {
-            for (int c = SC_HAA; c <= SC_HUU; c++) { scr[c * pad + sf] = 0.0; scr[c * pad + st] = 0.0; }
-            for (int c = OH_AA; c <= OH_MT_AF; c++) put_off(c, 0.0, Hb);
-        }
         return;
     }
 
@@ -184,21 +178,15 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     const End ef = end_terms<DERIV>(Gff, Bff, Af, Cf, Vf, Vt);
     const End et = end_terms<DERIV>(Gtt, Btt, At, Ct, Vt, Vf);
 
-    scr[SC_P * pad + sf] = ef.P; scr[SC_Q * pad + sf] = ef.Q;
-    scr[SC_P * pad + st] = et.P; scr[SC_Q * pad + st] = et.Q;
+    put2(rf, SC_P, ef.P, ef.Q);
+    put2(rt, SC_P, et.P, et.Q);
     if (WG && ghb) {
         ghb[2 * nb + l] = fma(ef.P, ef.P, ef.Q * ef.Q);
         ghb[2 * nb + nl + l] = fma(et.P, et.P, et.Q * et.Q);
     }
     if (WJ) {
-        scr[SC_PA * pad + sf] = ef.pa; scr[SC_PU * pad + sf] = ef.pu;
-        scr[SC_QA * pad + sf] = ef.qa; scr[SC_QU * pad + sf] = ef.qu;
-        scr[SC_PA * pad + st] = et.pa; scr[SC_PU * pad + st] = et.pu;
-        scr[SC_QA * pad + st] = et.qa; scr[SC_QU * pad + st] = et.qu;
-        put_off(OJ_PF_VAT, dneg(ef.pa), Jb); put_off(OJ_PF_VMT, ef.pv, Jb);
-        put_off(OJ_QF_VAT, dneg(ef.qa), Jb); put_off(OJ_QF_VMT, ef.qv, Jb);
-        put_off(OJ_PT_VAF, dneg(et.pa), Jb); put_off(OJ_PT_VMF, et.pv, Jb);
-        put_off(OJ_QT_VAF, dneg(et.qa), Jb); put_off(OJ_QT_VMF, et.qv, Jb);
+        put2(rf, SC_PA, ef.pa, ef.pu); put2(rf, SC_PV, ef.pv, ef.qa); put2(rf, SC_QU, ef.qu, ef.qv);
+        put2(rt, SC_PA, et.pa, et.pu); put2(rt, SC_PV, et.pv, et.qa); put2(rt, SC_QU, et.qu, et.qv);
         store_hrow(Jf, ef, fb < tb);
         store_hrow(Jt, et, tb < fb);
     }
@@ -212,16 +200,11 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
         const EndHess hf = end_hess(ef, Gff, Bff, Af, Cf, K, Vf, Vt, VV, VV2, lPf, lQf, muf);
         const EndHess ht = end_hess(et, Gtt, Btt, At, Ct, K, Vt, Vf, VV, VV2, lPt, lQt, mut);
         const double haa = hf.haa + ht.haa;
-        const double xf = hf.hau - ht.hav;            // (Vm_f, Va_f)
-        const double xt = ht.hau - hf.hav;            // (Vm_t, Va_t)
-        scr[SC_HAA * pad + sf] = haa; scr[SC_HAA * pad + st] = haa;
-        scr[SC_HUA * pad + sf] = xf;  scr[SC_HUA * pad + st] = xt;
-        scr[SC_HUU * pad + sf] = hf.huu + ht.hvv;
-        scr[SC_HUU * pad + st] = ht.huu + hf.hvv;
-        put_off(OH_AA, dneg(haa), Hb);
-        put_off(OH_MM, hf.huv + ht.huv, Hb);
-        put_off(OH_MF_AT, dneg(xf), Hb);
-        put_off(OH_MT_AF, dneg(xt), Hb);
+        const double mft = hf.huv + ht.huv;
+        put2(rf, SC_HAA, haa, hf.hau - ht.hav);        // (Va_f,Va_f), (Vm_f, Va_f)
+        put2(rt, SC_HAA, haa, ht.hau - hf.hav);        // (Va_t,Va_t), (Vm_t, Va_t)
+        put2(rf, SC_HUU, hf.huu + ht.hvv, mft);
+        put2(rt, SC_HUU, ht.huu + hf.hvv, mft);
     }
 }
 
@@ -233,82 +216,217 @@ __device__ __forceinline__ double grad_pg(const DevNet &N, const EvalReq &R, int
     return w * fma(2.0 * __ldg(N.c2 + k) * base * base, Pg, __ldg(N.c1 + k) * base);
 }
 
-// One (state b, bus i) item: sums the bus's branch-end partials in slot order, adds shunt, load
-// and generator terms, and writes the bus's g rows, its diagonal J and H values and its
-// generators' constant J entries and cost Hessian.  The partials are read through L2 (ld.cg):
-// in the persistent schedule other CTAs wrote them during the same launch.
+// Where one bus writes its Jacobian rows P_i, Q_i and Hessian rows Va_i, Vm_i (global memory, or
+// a shared-memory staging copy of the tile's row segments).
+struct BusRows {
+    double *JP, *JQ, *HA, *HM;
+};
+
+__device__ __forceinline__ double2 ld2(const double *p) {
+    return __ldcg(reinterpret_cast<const double2 *>(p));
+}
+
+// The values of one branch-end record that a request needs.
+struct Rec {
+    double P, Q, pa, pu, pv, qa, qu, qv, haa, hua, huu, huv;
+};
+
+template <int WANT>
+__device__ __forceinline__ Rec load_rec(const double *rec) {
+    Rec r{};
+    if (WANT & W_G) { const double2 v = ld2(rec + SC_P); r.P = v.x; r.Q = v.y; }
+    if (WANT & W_J) {
+        const double2 a = ld2(rec + SC_PA), v = ld2(rec + SC_PV), u = ld2(rec + SC_QU);
+        r.pa = a.x; r.pu = a.y; r.pv = v.x; r.qa = v.y; r.qu = u.x; r.qv = u.y;
+    }
+    if (WANT & W_H) {
+        const double2 h1 = ld2(rec + SC_HAA), h2 = ld2(rec + SC_HUU);
+        r.haa = h1.x; r.hua = h1.y; r.huu = h2.x; r.huv = h2.y;
+    }
+    return r;
+}
+
+// Diagonal sums of a bus: injections, dP/dVa_u, dP/dVm_u, dQ/dVa_u, dQ/dVm_u, H diagonal terms.
+template <int WANT>
+__device__ __forceinline__ void add_diag(Rec &d, const Rec &r) {
+    if (WANT & W_G) { d.P += r.P; d.Q += r.Q; }
+    if (WANT & W_J) { d.pa += r.pa; d.pu += r.pu; d.qa += r.qa; d.qu += r.qu; }
+    if (WANT & W_H) { d.haa += r.haa; d.hua += r.hua; d.huu += r.huu; }
+}
+
+// Off-diagonal entries towards one neighbour, summed over parallel branches.
+template <int WANT>
+__device__ __forceinline__ void add_group(Rec &o, const Rec &r) {
+    if (WANT & W_J) { o.pa += r.pa; o.pv += r.pv; o.qa += r.qa; o.qv += r.qv; }
+    if (WANT & W_H) { o.haa += r.haa; o.hua += r.hua; o.huv += r.huv; }
+}
+
+// One (state b, bus i) item.  Walks the bus's slots, which come in ascending order of the other
+// bus (parallel branches adjacent), gathers each slot's branch-end record, and writes the bus's
+// rows:
+//   g:  P_i and Q_i balances (sums of the end injections, shunt, load and generators);
+//   J:  rows P_i and Q_i entirely -- Va columns, Vm columns (a neighbour's entry is its branch
+//       end's dP/dVa_v = -dP/dVa_u and dP/dVm_v; the diagonal is the sum over all ends plus the
+//       shunt term), then -1 for each generator;
+//   H:  lower-triangle rows Va_i and Vm_i entirely (neighbours below i, the diagonal sums and the
+//       shunt term), and the cost Hessian of the bus's generators.
+// Records are read through L2 (ld.cg): in the persistent schedule other CTAs wrote them during
+// the launch.
 template <int WANT>
 __device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int b, int i,
-                                         const double *scr) {
+                                         const double *scr, const BusRows &W) {
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     const int nb = N.nb;
-    const size_t pad = (size_t)N.nslot_pad;
     const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
     const double *xb = R.x + (size_t)b * N.n;
     const double Vm = __ldg(xb + nb + i);
     const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
+    const int k = __ldg(N.bus_k + i), nlow = __ldg(N.bus_nlow + i);
+    double *JP = W.JP, *JQ = W.JQ, *HA = W.HA, *HM = W.HM;
+
+    // The first record of the bus initialises the diagonal sums and the first neighbour's entries;
+    // every later record adds to the diagonal sums and starts (or, for a parallel branch, adds to)
+    // its neighbour's entries.  Warps hold buses of similar degree (bus_perm), so the loop below
+    // runs nearly converged: the FP64 pipe is charged per warp instruction, not per active lane.
+    Rec D{};
+    int pos = 0;                                                    // column among cols_i
+    auto emit = [&](int j, const Rec &o) {
+        if (pos == nlow) pos++;   // the diagonal column sits between the lower and upper neighbours
+        if (WJ) {
+            JP[pos] = dneg(o.pa); JP[k + pos] = o.pv;
+            JQ[pos] = dneg(o.qa); JQ[k + pos] = o.qv;
+        }
+        if (WH) {
+            HM[pos] = dneg(o.hua);                            // (Vm_i, Va_j)
+            if (j < i) {
+                HA[pos] = dneg(o.haa);                        // (Va_i, Va_j)
+                HM[k + pos] = o.huv;                          // (Vm_i, Vm_j)
+            }
+        }
+        pos++;
+    };
+    auto rec_of = [&](int s) { return scr + (size_t)__ldg(N.slot_ref + s) * NCOMP; };
+    int s = s0;
+    if (s < s1) {
+        int j = __ldg(N.slot_nbr + s);
+        Rec o = load_rec<WANT>(rec_of(s));
+        D = o;
+        for (;;) {
+            s++;
+            int jn = s < s1 ? __ldg(N.slot_nbr + s) : -1;
+            while (jn == j) {                                 // parallel branch to the same bus
+                const Rec p = load_rec<WANT>(rec_of(s));
+                add_group<WANT>(o, p);
+                add_diag<WANT>(D, p);
+                s++;
+                jn = s < s1 ? __ldg(N.slot_nbr + s) : -1;
+            }
+            emit(j, o);
+            if (s >= s1) break;
+            j = jn;
+            o = load_rec<WANT>(rec_of(s));
+            add_diag<WANT>(D, o);
+        }
+    }
+    const double sP = D.P, sQ = D.Q, dPa = D.pa, dPu = D.pu, dQa = D.qa, dQu = D.qu;
+    const double dAA = D.haa, dUA = D.hua, dUU = D.huu;
 
     if (WG && R.gh) {
-        double sP = 0.0, sQ = 0.0;
-        for (int s = s0; s < s1; s++) {
-            sP += __ldcg(scr + SC_P * pad + s);
-            sQ += __ldcg(scr + SC_Q * pad + s);
-        }
         const double sc = R.pd_scale ? __ldg(R.pd_scale + (size_t)b * nb + i) : 1.0;
         const double VV = Vm * Vm;
-        sP += fma(Gs, VV, __ldg(N.Pd + i) * sc);
-        sQ += fma(-Bs, VV, __ldg(N.Qd + i) * sc);
-        for (int s = g0; s < g1; s++) {
-            const int k = __ldg(N.gen_ord + s);
-            sP -= __ldg(xb + 2 * nb + k);
-            sQ -= __ldg(xb + 2 * nb + N.ng + k);
+        double gP = sP + fma(Gs, VV, __ldg(N.Pd + i) * sc);
+        double gQ = sQ + fma(-Bs, VV, __ldg(N.Qd + i) * sc);
+        for (int q = g0; q < g1; q++) {
+            const int g = __ldg(N.gen_ord + q);
+            gP -= __ldg(xb + 2 * nb + g);
+            gQ -= __ldg(xb + 2 * nb + N.ng + g);
         }
         double *ghb = R.gh + (size_t)b * N.m;
-        ghb[i] = sP;
-        ghb[nb + i] = sQ;
+        ghb[i] = gP;
+        ghb[nb + i] = gQ;
     }
     if (WJ) {
-        double pa = 0.0, pu = 0.0, qa = 0.0, qu = 0.0;
-        for (int s = s0; s < s1; s++) {
-            pa += __ldcg(scr + SC_PA * pad + s); pu += __ldcg(scr + SC_PU * pad + s);
-            qa += __ldcg(scr + SC_QA * pad + s); qu += __ldcg(scr + SC_QU * pad + s);
-        }
         const double tV = Vm + Vm;
-        pu = fma(Gs, tV, pu);
-        qu = fma(-Bs, tV, qu);
-        double *Jb = R.jval + (size_t)b * N.nnzJ;
-        const int jP = __ldg(N.bus_jP + i), jQ = __ldg(N.bus_jQ + i), k = __ldg(N.bus_k + i);
-        Jb[jP] = pa; Jb[jP + k] = pu;
-        Jb[jQ] = qa; Jb[jQ + k] = qu;
-        for (int s = g0; s < g1; s++) {
-            const int g = __ldg(N.gen_ord + s);
-            Jb[__ldg(N.gen_jP + g)] = -1.0;
-            Jb[__ldg(N.gen_jQ + g)] = -1.0;
+        JP[nlow] = dPa; JP[k + nlow] = fma(Gs, tV, dPu);
+        JQ[nlow] = dQa; JQ[k + nlow] = fma(-Bs, tV, dQu);
+        for (int q = 0; q < g1 - g0; q++) {
+            JP[2 * k + q] = -1.0;
+            JQ[2 * k + q] = -1.0;
         }
     }
     if (WH) {
-        double aa = 0.0, ua = 0.0, uu = 0.0;
-        for (int s = s0; s < s1; s++) {
-            aa += __ldcg(scr + SC_HAA * pad + s);
-            ua += __ldcg(scr + SC_HUA * pad + s);
-            uu += __ldcg(scr + SC_HUU * pad + s);
-        }
         const double *lb = R.lam + (size_t)b * N.m;
         const double lP = __ldg(lb + i), lQ = __ldg(lb + nb + i);
-        uu += fma(lP, Gs + Gs, -(lQ * (Bs + Bs)));
-        double *Hb = R.hval + (size_t)b * N.nnzH;
-        Hb[__ldg(N.bus_h + i)] = aa;
-        Hb[__ldg(N.bus_h + nb + i)] = ua;
-        Hb[__ldg(N.bus_h + 2 * nb + i)] = uu;
+        HA[nlow] = dAA;                                       // (Va_i, Va_i): last of row Va_i
+        HM[nlow] = dUA;                                       // (Vm_i, Va_i)
+        HM[k + nlow] = dUU + fma(lP, Gs + Gs, -(lQ * (Bs + Bs)));   // (Vm_i, Vm_i): last
         if (g1 > g0) {
             const double sw = R.sigma * (R.obj_weight ? R.obj_weight[b] : 1.0);
             const double base2 = N.baseMVA * N.baseMVA;
-            for (int s = g0; s < g1; s++) {
-                const int g = __ldg(N.gen_ord + s);
-                Hb[__ldg(N.gen_h + g)] = sw * (2.0 * __ldg(N.c2 + g) * base2);
+            double *Hb = R.hval + (size_t)b * N.nnzH + N.hpg;
+            for (int q = g0; q < g1; q++) {
+                const int g = __ldg(N.gen_ord + q);
+                Hb[g] = sw * (2.0 * __ldg(N.c2 + g) * base2);
             }
         }
+    }
+}
+
+// Start of bus i's row in one of the four row blocks, or the block's end for i = nb.
+__device__ __forceinline__ int row_start(const int *starts, int i, int nb, int end) {
+    return i < nb ? __ldg(starts + i) : end;
+}
+
+// The bus items of buses [i0, i0 + blockDim.x) of state b, by the whole block (i0 a multiple
+// of 64).  When the tile's
+// row segments fit `stage` (cap doubles of shared memory), every bus writes its rows there and
+// the block then copies the four contiguous segments out with coalesced stores; otherwise the
+// rows go straight to global memory.  Contains __syncthreads: call from every thread.
+template <int WANT>
+__device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int b, int i0,
+                                         const double *scr, double *stage, int cap) {
+    constexpr bool WJ = WANT & W_J, WH = WANT & W_H;
+    const int nb = N.nb;
+    int i1 = i0 + blockDim.x;
+    if (i1 > nb) i1 = nb;
+    // thread -> bus through the degree-sorted permutation (it maps every aligned 64-bus group,
+    // hence every tile, onto itself)
+    const int i = i0 + (int)threadIdx.x < i1 ? __ldg(N.bus_perm + i0 + threadIdx.x) : nb;
+    const int p0 = row_start(N.bus_jP, i0, nb, N.jP_end), p1 = row_start(N.bus_jP, i1, nb, N.jP_end);
+    const int q0 = row_start(N.bus_jQ, i0, nb, N.jQ_end);
+    const int a0 = row_start(N.bus_hA, i0, nb, N.hA_end), a1 = row_start(N.bus_hA, i1, nb, N.hA_end);
+    const int m0 = row_start(N.bus_hM, i0, nb, N.hM_end), m1 = row_start(N.bus_hM, i1, nb, N.hM_end);
+    const int LP = WJ ? p1 - p0 : 0, LA = WH ? a1 - a0 : 0, LM = WH ? m1 - m0 : 0;
+    const bool staged = 2 * LP + LA + LM <= cap;
+    double *Jb = WJ ? R.jval + (size_t)b * N.nnzJ : nullptr;
+    double *Hb = WH ? R.hval + (size_t)b * N.nnzH : nullptr;
+    if (i < i1) {
+        BusRows W{};
+        if (staged) {
+            if (WJ) {
+                W.JP = stage + (__ldg(N.bus_jP + i) - p0);
+                W.JQ = stage + LP + (__ldg(N.bus_jQ + i) - q0);
+            }
+            if (WH) {
+                W.HA = stage + 2 * LP + (__ldg(N.bus_hA + i) - a0);
+                W.HM = stage + 2 * LP + LA + (__ldg(N.bus_hM + i) - m0);
+            }
+        } else {
+            if (WJ) { W.JP = Jb + __ldg(N.bus_jP + i); W.JQ = Jb + __ldg(N.bus_jQ + i); }
+            if (WH) { W.HA = Hb + __ldg(N.bus_hA + i); W.HM = Hb + __ldg(N.bus_hM + i); }
+        }
+        bus_item<WANT>(N, R, b, i, scr, W);
+    }
+    if (staged && (WJ || WH)) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < LP; e += blockDim.x) {
+            Jb[p0 + e] = stage[e];
+            Jb[q0 + e] = stage[LP + e];
+        }
+        for (int e = threadIdx.x; e < LA; e += blockDim.x) Hb[a0 + e] = stage[2 * LP + e];
+        for (int e = threadIdx.x; e < LM; e += blockDim.x) Hb[m0 + e] = stage[2 * LP + LA + e];
+        __syncthreads();
     }
 }
 
@@ -323,17 +441,6 @@ __device__ __forceinline__ void grad_bus(const DevNet &N, const EvalReq &R, int 
         gb[2 * N.nb + k] = grad_pg(N, R, b, k);
         gb[2 * N.nb + N.ng + k] = 0.0;
     }
-}
-
-// Parallel-branch fixup entry e of state b: sums the group's values in ascending branch order.
-__device__ __forceinline__ void fixup_entry(const DevNet &N, const EvalReq &R, int b, int e,
-                                            const double *offs) {
-    const bool isH = N.fix_isH[e] != 0;
-    if ((isH && !R.hval) || (!isH && !R.jval)) return;
-    double v = 0.0;
-    for (int p = N.fix_ptr[e]; p < N.fix_ptr[e + 1]; p++) v += __ldcg(offs + N.fix_src[p]);
-    if (isH) R.hval[(size_t)b * N.nnzH + N.fix_dst[e]] = v;
-    else R.jval[(size_t)b * N.nnzJ + N.fix_dst[e]] = v;
 }
 
 // Objective of state b, f = w sum_k (c2 MW^2 + c1 MW + c0), MW = base Pg, by the whole block.

@@ -12,31 +12,28 @@
 
 namespace exago {
 
-// Per-(branch, end) partial sums handed from the branch kernel to the bus kernel.  Component k of
-// slot s of state b lives at scratch[(b * NCOMP + k) * nslot_pad + s].
+// Per-(branch, end) record handed from the branch phase to the bus phase: NCOMP doubles at
+// scratch[((b * 2 nl) + 2 l + end) * NCOMP + k] for state b, branch l, end 0 (from) or 1 (to).
+// Records are ordered by branch, so a warp of consecutive branches writes contiguous memory; the
+// bus phase gathers them through the slot lists.  For the end at bus u towards bus v:
 enum SlotComp {
-    SC_P = 0,    // active injection of this end at its own bus
+    SC_P = 0,    // active injection of this end at u
     SC_Q = 1,    // reactive injection
-    SC_PA = 2,   // dP/dVa_u   (u = this end's bus)
+    SC_PA = 2,   // dP/dVa_u            (dP/dVa_v = -dP/dVa_u)
     SC_PU = 3,   // dP/dVm_u
-    SC_QA = 4,   // dQ/dVa_u
-    SC_QU = 5,   // dQ/dVm_u
-    SC_HAA = 6,  // Lagrangian Hessian (Va_u, Va_u)
-    SC_HUA = 7,  // (Vm_u, Va_u)
-    SC_HUU = 8,  // (Vm_u, Vm_u)
-    NCOMP = 9
+    SC_PV = 4,   // dP/dVm_v
+    SC_QA = 5,   // dQ/dVa_u
+    SC_QU = 6,   // dQ/dVm_u
+    SC_QV = 7,   // dQ/dVm_v
+    SC_HAA = 8,  // Lagrangian Hessian of the branch: (Va_u, Va_u) = -(Va_u, Va_v)
+    SC_HUA = 9,  // (Vm_u, Va_u) = -(Vm_u, Va_v)
+    SC_HUU = 10, // (Vm_u, Vm_u)
+    SC_HUV = 11, // (Vm_u, Vm_v)
+    NCOMP = 12
 };
 
-// Off-diagonal outputs of one branch (written directly unless the branch has a parallel twin).
-enum OffComp {
-    OJ_PF_VAT = 0, OJ_PF_VMT, OJ_QF_VAT, OJ_QF_VMT,   // rows of the from bus, columns of the to bus
-    OJ_PT_VAF, OJ_PT_VMF, OJ_QT_VAF, OJ_QT_VMF,       // rows of the to bus, columns of the from bus
-    OH_AA, OH_MM, OH_MF_AT, OH_MT_AF,                 // (Va_f,Va_t), (Vm_f,Vm_t), (Vm_f,Va_t), (Vm_t,Va_f)
-    NOFF
-};
-
-// Host plan of one grid: validated copies of the inputs, both sparsity patterns, and the output
-// position of every value each kernel writes.
+// Host plan of one grid: validated copies of the inputs, both sparsity patterns, and what each
+// kernel needs to write its outputs.
 struct HostPlan {
     int nb = 0, nl = 0, ng = 0, n = 0, m = 0;
     int64_t nnzJ = 0, nnzJg = 0, nnzH = 0;
@@ -47,42 +44,39 @@ struct HostPlan {
     std::vector<int64_t> Jrowptr, Hrowptr;
     std::vector<int> Jcol, Hcol;
 
-    std::vector<int> br_off;      // [NOFF][nl] output positions (J for 0..7, H for 8..11)
-    std::vector<int> br_slot;     // [2][nl] slot of the from end and of the to end
-    std::vector<int> br_shared;   // [nl] -1, or index among branches with a parallel twin
-    int nshared = 0;
-
-    std::vector<int> slot_ptr;    // [nb + 1] slots of bus i are [slot_ptr[i], slot_ptr[i+1])
+    // Slots: one per (branch, end), grouped by the end's bus, ordered by (bus, other bus,
+    // branch).  A bus's slots therefore visit its row columns in ascending order, and parallel
+    // branches are adjacent.
     int nslot = 0;                // 2 nl
+    std::vector<int> slot_ptr;    // [nb + 1] slots of bus i are [slot_ptr[i], slot_ptr[i+1])
+    std::vector<int> slot_nbr;    // [nslot] the other bus of the slot's branch
+    std::vector<int> slot_ref;    // [nslot] record index 2 l + end of the slot
 
-    std::vector<int> bus_jP, bus_jQ, bus_k;   // [nb] J positions of (P_i, Va_i), (Q_i, Va_i);
-                                              // k_i = columns per block, so Vm_i is at +k_i
-    std::vector<int> bus_h;       // [3][nb] H positions (Va_i,Va_i), (Vm_i,Va_i), (Vm_i,Vm_i)
+    // Row starts of bus i: J rows P_i and Q_i, H rows Va_i and Vm_i; k_i = neighbours + 1 (Va
+    // columns of a J row, Vm columns follow); nlow_i = neighbours below i (position of the
+    // diagonal among the Va columns).
+    std::vector<int> bus_jP, bus_jQ, bus_hA, bus_hM, bus_k, bus_nlow;
+    // bus_perm: within every aligned group of 64 buses, the buses by descending degree (then id),
+    // so that a warp of the bus phase walks slot lists of similar length
+    std::vector<int> bus_perm;
     std::vector<int> gen_ptr;     // [nb + 1] generators of bus i: gen_ord[gen_ptr[i] .. )
     std::vector<int> gen_ord;     // [ng] generator ids sorted by (bus, id)
-    std::vector<int> gen_jP, gen_jQ, gen_h;   // [ng] positions of (P_bus, Pg_k), (Q_bus, Qg_k), (Pg_k, Pg_k)
-
-    // Parallel-branch fixups: entry e sums fix_src[fix_ptr[e] .. fix_ptr[e+1]) into position
-    // fix_dst[e] of J (fix_isH[e] == 0) or H.  A source is comp * nshared + shared index.
-    std::vector<int> fix_ptr, fix_src, fix_dst;
-    std::vector<uint8_t> fix_isH;
 };
 
 // Device view handed to the kernels by value.
 struct DevNet {
-    int nb, nl, ng, n, m, nslot, nslot_pad, nshared, nfix;
-    int64_t nnzJ, nnzJg, nnzH;
+    int nb, nl, ng, n, m, nslot;
+    int64_t nnzJ, nnzJg, nnzH, hpg;          // hpg: H position of (Pg_0, Pg_0)
+    int jP_end, jQ_end, hA_end, hM_end;      // ends of the four row blocks of the bus rows
+    int stage_cap[3];                        // staging doubles for bus tiles of 64/128/256 buses
     double baseMVA;
     const int *f, *t;
     const double *Gff, *Bff, *Gtt, *Btt, *Gft, *Bft;   // pi-model admittances (no phase shift: ft == tf)
-    const int *br_off, *br_slot, *br_shared;
-    const int *slot_ptr;
-    const int *bus_jP, *bus_jQ, *bus_k, *bus_h;
+    const int *slot_ptr, *slot_nbr, *slot_ref;
+    const int *bus_jP, *bus_jQ, *bus_hA, *bus_hM, *bus_k, *bus_nlow, *bus_perm;
     const double *Gs, *Bs, *Pd, *Qd;
-    const int *gen_ptr, *gen_ord, *gen_bus, *gen_jP, *gen_jQ, *gen_h;
+    const int *gen_ptr, *gen_ord;
     const double *c2, *c1, *c0;
-    const int *fix_ptr, *fix_src, *fix_dst;
-    const uint8_t *fix_isH;
     int *status;                // device status word (host-mapped)
 };
 
@@ -94,8 +88,7 @@ struct EvalReq {
     const double *pd_scale, *obj_weight;
     double sigma;
     double *f, *grad, *gh, *jval, *hval;
-    double *scratch;            // [B][NCOMP][nslot_pad] slot partial sums
-    double *offscratch;         // [B][NOFF][nshared] off-diagonal values of parallel branches
+    double *scratch;            // [B][2 nl][NCOMP] branch-end records (or ring slots)
 };
 
 // One adjoint-product call (adjoint.cu): JVP u -> J u, JTV v -> J^T v, HVP u -> (grad^2 L) u.
@@ -108,7 +101,7 @@ struct AdjReq {
     double sigma;
     const double *v;                // JVP / HVP: [B][n]; JTV: [B][m]
     double *out;                    // JVP: [B][m]; JTV / HVP: [B][n]
-    double *scratch;                // [B][2][nslot_pad]
+    double *scratch;                // [B][2 nl][2] branch-end records
 };
 int launch_adjoint(const DevNet &net, const AdjReq &req, int mode, void *stream);
 
@@ -136,8 +129,8 @@ int launch_admittance(const double *r, const double *x, const double *b, const d
                       double *Bft, void *stream);
 int launch_eval(const DevNet &net, const EvalReq &req, void *stream, ProfileHook *hook = nullptr);
 
-// Persistent schedule (one launch; see kernels.cu).  counters: 1 + 2B ints of the workspace;
-// req.scratch / req.offscratch hold `ring` state slots.
+// Persistent schedule (one launch; see persist.cu).  counters: 1 + 2B ints of the workspace;
+// req.scratch holds `ring` state slots.
 struct PersistLaunch {
     int block;              // 64, 128 or 256 threads
     int occ_warps;          // 0, 24 or 32: resident warps per SM the registers must allow
@@ -149,7 +142,14 @@ struct PersistLaunch {
 };
 int launch_eval_persistent(const DevNet &net, const EvalReq &req, const PersistLaunch &pl,
                            void *stream, ProfileHook *hook = nullptr);
-int persist_blocks_per_sm(int block, int occ_warps);
+int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes);
+
+// Shared-memory staging of a bus tile's row segments (eval_items.cuh, bus_tile): the largest
+// tile's need in doubles, capped at kStageMaxDoubles (tiles above the cap write directly).
+constexpr int kStageMaxDoubles = 6144;   // 48 KB
+inline int stage_index(int block) { return block == 64 ? 0 : block == 256 ? 2 : 1; }
+int persist_allow_stage();   // persist.cu
+int bus_allow_stage();       // kernels.cu
 
 // Read-only view of a net's plan and device tables (false for NULL or a plan-only net), and the
 // thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.

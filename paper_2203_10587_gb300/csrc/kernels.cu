@@ -53,27 +53,20 @@ int launch_admittance(const double *r, const double *x, const double *b, const d
 }
 
 // ---------------------------------------------------------------------------------------------
-// Multi-kernel schedule: branch, bus, fixup, gradient and objective launches over the batch.
+// Multi-kernel schedule: branch, bus, gradient and objective launches over the batch.
 template <int WANT>
 __global__ void __launch_bounds__(128) k_branch(const DevNet N, const EvalReq R, int b0) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = b0 + blockIdx.y;
-    if (l < N.nl)
-        branch_item<WANT>(N, R, b, l, R.scratch + (size_t)b * NCOMP * N.nslot_pad,
-                          R.offscratch + (size_t)b * NOFF * N.nshared);
+    if (l < N.nl) branch_item<WANT>(N, R, b, l, R.scratch + (size_t)b * N.nslot * NCOMP);
 }
 
 template <int WANT>
 __global__ void __launch_bounds__(128) k_bus(const DevNet N, const EvalReq R, int b0) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ double stage[];
     const int b = b0 + blockIdx.y;
-    if (i < N.nb) bus_item<WANT>(N, R, b, i, R.scratch + (size_t)b * NCOMP * N.nslot_pad);
-}
-
-__global__ void k_fixup(const DevNet N, const EvalReq R, int b0) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = b0 + blockIdx.y;
-    if (e < N.nfix) fixup_entry(N, R, b, e, R.offscratch + (size_t)b * NOFF * N.nshared);
+    bus_tile<WANT>(N, R, b, blockIdx.x * blockDim.x, R.scratch + (size_t)b * N.nslot * NCOMP,
+                   stage, N.stage_cap[1]);
 }
 
 // Gradient of the objective: w (2 c2 base^2 Pg + c1 base) on Pg entries, 0 elsewhere.
@@ -98,7 +91,22 @@ static void launch_branch_bus(const DevNet &N, const EvalReq &R, int b0, int nB,
         k_branch<WANT><<<dim3((N.nl + 127) / 128, nB), 128, 0, st>>>(N, R, b0);
     }
     mark(hk, st, "bus");
-    k_bus<WANT><<<dim3((N.nb + 127) / 128, nB), 128, 0, st>>>(N, R, b0);
+    const size_t smem = (size_t)N.stage_cap[1] * sizeof(double);
+    k_bus<WANT><<<dim3((N.nb + 127) / 128, nB), 128, smem, st>>>(N, R, b0);
+}
+
+// Opts the bus kernels in to kStageMaxDoubles of dynamic shared memory (once per device).
+int bus_allow_stage() {
+    const int bytes = kStageMaxDoubles * (int)sizeof(double);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *k) {
+        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (r != cudaSuccess) e = r;
+    };
+    set((const void *)k_bus<W_G>); set((const void *)k_bus<W_J>); set((const void *)k_bus<W_G | W_J>);
+    set((const void *)k_bus<W_H>); set((const void *)k_bus<W_G | W_H>);
+    set((const void *)k_bus<W_J | W_H>); set((const void *)k_bus<W_G | W_J | W_H>);
+    return (int)e;
 }
 
 int launch_eval(const DevNet &N, const EvalReq &R, void *stream, ProfileHook *hk) {
@@ -116,10 +124,6 @@ int launch_eval(const DevNet &N, const EvalReq &R, void *stream, ProfileHook *hk
             case W_G | W_H: launch_branch_bus<W_G | W_H>(N, R, b0, nB, st, hk); break;
             case W_J | W_H: launch_branch_bus<W_J | W_H>(N, R, b0, nB, st, hk); break;
             default: launch_branch_bus<W_G | W_J | W_H>(N, R, b0, nB, st, hk); break;
-        }
-        if (N.nfix > 0 && (R.jval || R.hval)) {
-            mark(hk, st, "fixup");
-            k_fixup<<<dim3((N.nfix + 127) / 128, nB), 128, 0, st>>>(N, R, b0);
         }
         if (R.grad) {
             mark(hk, st, "grad");

@@ -22,8 +22,7 @@ namespace exago {
 // smaller tickets still; the smallest unfinished ticket never waits, so the launch cannot
 // deadlock.  Every wait is bounded: after spin_limit polls it records a timeout in the status
 // word, skips its work and still signals, so the launch always ends.  Bus tile 0 of each state
-// also writes its parallel-branch fixups and its objective; every bus tile writes the gradient
-// entries of its buses.
+// also writes its objective; every bus tile writes the gradient entries of its buses.
 struct PersistParams {
     int B, Tbr, Tbu, lag, ring, total;
     int *ctr;               // [1 + 2B]: ticket, branch tiles done per state, bus tiles done
@@ -78,9 +77,10 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
                                                       const PersistParams P) {
     __shared__ int s_item, s_ok;
     __shared__ double s_part[OBJ_LANES];
+    extern __shared__ double stage[];
     int *done_br = P.ctr + 1, *done_bu = P.ctr + 1 + P.B;
-    const size_t slot_doubles = (size_t)NCOMP * N.nslot_pad;
-    const size_t off_doubles = (size_t)NOFF * N.nshared;
+    const size_t slot_doubles = (size_t)NCOMP * N.nslot;
+    const int cap = N.stage_cap[NT == 64 ? 0 : NT == 256 ? 2 : 1];
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(P.ctr, 1);
         __syncthreads();
@@ -91,14 +91,13 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
         decode_item(P, t, &is_branch, &b, &tile);
         const int slot = b % P.ring;
         double *scr = R.scratch + (size_t)slot * slot_doubles;
-        double *offs = R.offscratch + (size_t)slot * off_doubles;
         if (is_branch) {
             if (threadIdx.x == 0)
                 s_ok = b < P.ring || bounded_wait(done_bu + (b - P.ring), P.Tbu, P.spin_limit,
                                                   N.status, ST_TIMEOUT_RING);
             __syncthreads();
             const int l = tile * NT + threadIdx.x;
-            if (s_ok && l < N.nl) branch_item<WANT>(N, R, b, l, scr, offs);
+            if (s_ok && l < N.nl) branch_item<WANT>(N, R, b, l, scr);
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
@@ -112,15 +111,9 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
             if (s_ok) {
                 __threadfence();
                 const int i = tile * NT + threadIdx.x;
-                if (i < N.nb) {
-                    if (WANT) bus_item<WANT>(N, R, b, i, scr);
-                    if (R.grad) grad_bus(N, R, b, i);
-                }
-                if (tile == 0) {
-                    if (R.jval || R.hval)
-                        for (int e = threadIdx.x; e < N.nfix; e += NT) fixup_entry(N, R, b, e, offs);
-                    if (R.f) obj_block(N, R, b, s_part);
-                }
+                if (WANT) bus_tile<WANT>(N, R, b, tile * NT, scr, stage, cap);
+                if (i < N.nb && R.grad) grad_bus(N, R, b, i);
+                if (tile == 0 && R.f) obj_block(N, R, b, s_part);
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -131,62 +124,85 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
     }
 }
 
-template <int NT, int MINB>
-static void launch_all(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
-                       cudaStream_t st) {
-    k_persist<W_G | W_J | W_H, NT, MINB><<<grid, NT, 0, st>>>(N, R, P);
-}
-
 // CTAs per SM for a target of occ_warps resident warps (0: the compiler's register choice).
 constexpr int minb(int nt, int occ_warps) {
     return occ_warps <= 0 ? 1 : (occ_warps / (nt / 32) > 0 ? occ_warps / (nt / 32) : 1);
 }
 
+template <int WANT, int NT, int MINB>
+static void launch_one(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
+                       size_t smem, cudaStream_t st) {
+    k_persist<WANT, NT, MINB><<<grid, NT, smem, st>>>(N, R, P);
+}
+
+// Opts every persistent variant in to kStageMaxDoubles of dynamic shared memory (above the
+// default 48 KB once the static part is added).  Called once per device, outside any capture.
+template <int NT>
+static int allow_stage_nt() {
+    const int bytes = kStageMaxDoubles * (int)sizeof(double);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *k) {
+        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (r != cudaSuccess) e = r;
+    };
+    constexpr int ALL = W_G | W_J | W_H;
+    set((const void *)k_persist<0, NT, 1>); set((const void *)k_persist<W_G, NT, 1>);
+    set((const void *)k_persist<W_J, NT, 1>); set((const void *)k_persist<W_G | W_J, NT, 1>);
+    set((const void *)k_persist<W_H, NT, 1>); set((const void *)k_persist<W_G | W_H, NT, 1>);
+    set((const void *)k_persist<W_J | W_H, NT, 1>); set((const void *)k_persist<ALL, NT, 1>);
+    set((const void *)k_persist<ALL, NT, minb(NT, 24)>);
+    set((const void *)k_persist<ALL, NT, minb(NT, 32)>);
+    return (int)e;
+}
+
+int persist_allow_stage() {
+    int e = allow_stage_nt<64>();
+    if (e == 0) e = allow_stage_nt<128>();
+    if (e == 0) e = allow_stage_nt<256>();
+    return e;
+}
+
+
 template <int NT>
 static int launch_persist_nt(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
                              int occ_warps, cudaStream_t st) {
     const int want = (R.gh ? W_G : 0) | (R.jval ? W_J : 0) | (R.hval ? W_H : 0);
-    if (want == (W_G | W_J | W_H) && occ_warps == 24) {
-        launch_all<NT, minb(NT, 24)>(N, R, P, grid, st);
-        return (int)cudaGetLastError();
-    }
-    if (want == (W_G | W_J | W_H) && occ_warps == 32) {
-        launch_all<NT, minb(NT, 32)>(N, R, P, grid, st);
-        return (int)cudaGetLastError();
-    }
-    switch (want) {
-        case 0: k_persist<0, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
-        case W_G: k_persist<W_G, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
-        case W_J: k_persist<W_J, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
-        case W_G | W_J: k_persist<W_G | W_J, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
-        case W_H: k_persist<W_H, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
-        case W_G | W_H: k_persist<W_G | W_H, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
-        case W_J | W_H: k_persist<W_J | W_H, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
-        default: k_persist<W_G | W_J | W_H, NT, 1><<<grid, NT, 0, st>>>(N, R, P); break;
+    const size_t smem = (size_t)N.stage_cap[NT == 64 ? 0 : NT == 256 ? 2 : 1] * sizeof(double);
+    constexpr int ALL = W_G | W_J | W_H;
+    if (want == ALL && occ_warps == 24) launch_one<ALL, NT, minb(NT, 24)>(N, R, P, grid, smem, st);
+    else if (want == ALL && occ_warps == 32) launch_one<ALL, NT, minb(NT, 32)>(N, R, P, grid, smem, st);
+    else switch (want) {
+        case 0: launch_one<0, NT, 1>(N, R, P, grid, smem, st); break;
+        case W_G: launch_one<W_G, NT, 1>(N, R, P, grid, smem, st); break;
+        case W_J: launch_one<W_J, NT, 1>(N, R, P, grid, smem, st); break;
+        case W_G | W_J: launch_one<W_G | W_J, NT, 1>(N, R, P, grid, smem, st); break;
+        case W_H: launch_one<W_H, NT, 1>(N, R, P, grid, smem, st); break;
+        case W_G | W_H: launch_one<W_G | W_H, NT, 1>(N, R, P, grid, smem, st); break;
+        case W_J | W_H: launch_one<W_J | W_H, NT, 1>(N, R, P, grid, smem, st); break;
+        default: launch_one<ALL, NT, 1>(N, R, P, grid, smem, st); break;
     }
     return (int)cudaGetLastError();
 }
 
-template <int NT>
-static int occupancy_nt(int occ_warps) {
+template <int NT, int MINB>
+static int occupancy_of(size_t smem) {
+    auto kern = k_persist<W_G | W_J | W_H, NT, MINB>;
     int per_sm = 0;
-    cudaError_t e;
-    if (occ_warps == 24)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_persist<W_G | W_J | W_H, NT, minb(NT, 24)>, NT, 0);
-    else if (occ_warps == 32)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_persist<W_G | W_J | W_H, NT, minb(NT, 32)>, NT, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<W_G | W_J | W_H, NT, 1>,
-                                                          NT, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     return e == cudaSuccess && per_sm > 0 ? per_sm : 1;
 }
 
-int persist_blocks_per_sm(int block, int occ_warps) {
-    if (block == 256) return occupancy_nt<256>(occ_warps);
-    if (block == 64) return occupancy_nt<64>(occ_warps);
-    return occupancy_nt<128>(occ_warps);
+template <int NT>
+static int occupancy_nt(int occ_warps, size_t smem) {
+    if (occ_warps == 24) return occupancy_of<NT, minb(NT, 24)>(smem);
+    if (occ_warps == 32) return occupancy_of<NT, minb(NT, 32)>(smem);
+    return occupancy_of<NT, 1>(smem);
+}
+
+int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes) {
+    if (block == 256) return occupancy_nt<256>(occ_warps, smem_bytes);
+    if (block == 64) return occupancy_nt<64>(occ_warps, smem_bytes);
+    return occupancy_nt<128>(occ_warps, smem_bytes);
 }
 
 int launch_eval_persistent(const DevNet &N, const EvalReq &R, const PersistLaunch &L,

@@ -4,7 +4,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
-#include <map>
 #include <utility>
 
 #include "internal.h"
@@ -29,12 +28,7 @@ std::vector<double> copy_or(const double *a, int n, double dflt) {
 }  // namespace
 
 size_t workspace_bytes(const HostPlan &p, int B) {
-    const size_t pad = (size_t)((p.nslot + 31) / 32 * 32);
-    size_t bytes = 0;
-    auto add = [&](size_t n) { bytes += (n * sizeof(double) + 255) / 256 * 256; };
-    add((size_t)B * NCOMP * pad);
-    add((size_t)B * NOFF * (size_t)p.nshared);
-    return bytes;
+    return ((size_t)B * (size_t)p.nslot * NCOMP * sizeof(double) + 255) / 256 * 256;
 }
 
 exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs, const double *Pd,
@@ -195,84 +189,51 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
     }
     for (int k = 0; k < ng; k++) p.Hcol[p.Hrowptr[2 * nb + k]] = 2 * nb + k;
 
-    // ---- positions
-    p.br_off.assign((size_t)NOFF * nl, 0);
-    for (int l = 0; l < nl; l++) {
-        int fb = p.f[l], tb = p.t[l];
-        int kf = (int)cols[fb].size(), kt = (int)cols[tb].size();
-        int64_t rPf = p.Jrowptr[fb], rQf = p.Jrowptr[nb + fb], rPt = p.Jrowptr[tb], rQt = p.Jrowptr[nb + tb];
-        int rf = rank(fb, tb), rt = rank(tb, fb);
-        int hi = std::max(fb, tb), lo = std::min(fb, tb);
-        int *o = p.br_off.data();
-        o[OJ_PF_VAT * nl + l] = (int)(rPf + rf);
-        o[OJ_PF_VMT * nl + l] = (int)(rPf + kf + rf);
-        o[OJ_QF_VAT * nl + l] = (int)(rQf + rf);
-        o[OJ_QF_VMT * nl + l] = (int)(rQf + kf + rf);
-        o[OJ_PT_VAF * nl + l] = (int)(rPt + rt);
-        o[OJ_PT_VMF * nl + l] = (int)(rPt + kt + rt);
-        o[OJ_QT_VAF * nl + l] = (int)(rQt + rt);
-        o[OJ_QT_VMF * nl + l] = (int)(rQt + kt + rt);
-        o[OH_AA * nl + l] = (int)(p.Hrowptr[hi] + lowrank(hi, lo));
-        o[OH_MM * nl + l] = (int)(p.Hrowptr[nb + hi] + (int)cols[hi].size() + lowrank(hi, lo));
-        o[OH_MF_AT * nl + l] = (int)(p.Hrowptr[nb + fb] + rf);
-        o[OH_MT_AF * nl + l] = (int)(p.Hrowptr[nb + tb] + rt);
-    }
-    p.bus_jP.assign(nb, 0); p.bus_jQ.assign(nb, 0); p.bus_k.assign(nb, 0);
-    p.bus_h.assign(3 * (size_t)nb, 0);
+    // ---- per-bus row starts
+    p.bus_jP.assign(nb, 0); p.bus_jQ.assign(nb, 0); p.bus_hA.assign(nb, 0); p.bus_hM.assign(nb, 0);
+    p.bus_k.assign(nb, 0); p.bus_nlow.assign(nb, 0);
     for (int i = 0; i < nb; i++) {
-        int ri = rank(i, i);
+        p.bus_jP[i] = (int)p.Jrowptr[i];
+        p.bus_jQ[i] = (int)p.Jrowptr[nb + i];
+        p.bus_hA[i] = (int)p.Hrowptr[i];
+        p.bus_hM[i] = (int)p.Hrowptr[nb + i];
         p.bus_k[i] = (int)cols[i].size();
-        p.bus_jP[i] = (int)(p.Jrowptr[i] + ri);
-        p.bus_jQ[i] = (int)(p.Jrowptr[nb + i] + ri);
-        p.bus_h[0 * nb + i] = (int)(p.Hrowptr[i + 1] - 1);
-        p.bus_h[1 * nb + i] = (int)(p.Hrowptr[nb + i] + ri);
-        p.bus_h[2 * nb + i] = (int)(p.Hrowptr[nb + i + 1] - 1);
-    }
-    p.gen_jP.assign(ng, 0); p.gen_jQ.assign(ng, 0); p.gen_h.assign(ng, 0);
-    for (int i = 0; i < nb; i++) {
-        int k2 = 2 * (int)cols[i].size();
-        for (int s = p.gen_ptr[i]; s < p.gen_ptr[i + 1]; s++) {
-            int k = p.gen_ord[s], q = s - p.gen_ptr[i];
-            p.gen_jP[k] = (int)(p.Jrowptr[i] + k2 + q);
-            p.gen_jQ[k] = (int)(p.Jrowptr[nb + i] + k2 + q);
-            p.gen_h[k] = (int)p.Hrowptr[2 * nb + k];
-        }
+        p.bus_nlow[i] = rank(i, i);
     }
 
-    // ---- slots: (bus, branch, end) sorted by bus, then branch, from end first
+    // ---- degree-sorted bus order inside aligned 64-bus groups
+    // (degree = branch ends at the bus, the trip count of its slot loop)
+    std::vector<int> ends_at(nb, 0);
+    for (int l = 0; l < nl; l++) { ends_at[p.f[l]]++; ends_at[p.t[l]]++; }
+    p.bus_perm.resize(nb);
+    for (int i = 0; i < nb; i++) p.bus_perm[i] = i;
+    for (int g0 = 0; g0 < nb; g0 += 64) {
+        const int g1 = g0 + 64 < nb ? g0 + 64 : nb;
+        std::stable_sort(p.bus_perm.begin() + g0, p.bus_perm.begin() + g1,
+                         [&](int a, int c) { return ends_at[a] > ends_at[c]; });
+    }
+
+    // ---- slots: (bus, other bus, branch); each bus's slots walk its row columns in order
     p.nslot = 2 * nl;
     p.slot_ptr.assign(nb + 1, 0);
     for (int l = 0; l < nl; l++) { p.slot_ptr[p.f[l] + 1]++; p.slot_ptr[p.t[l] + 1]++; }
     for (int i = 0; i < nb; i++) p.slot_ptr[i + 1] += p.slot_ptr[i];
-    p.br_slot.assign(2 * (size_t)nl, 0);
-    {
-        std::vector<int> fill(p.slot_ptr.begin(), p.slot_ptr.end() - 1);
-        for (int l = 0; l < nl; l++) {   // ascending l; a branch meets a bus at one end only
-            p.br_slot[l] = fill[p.f[l]]++;
-            p.br_slot[nl + l] = fill[p.t[l]]++;
-        }
-    }
-
-    // ---- parallel branches: their off-diagonal values meet in one nonzero and are summed
-    std::map<std::pair<int, int>, int> count;
-    for (int l = 0; l < nl; l++) count[{std::min(p.f[l], p.t[l]), std::max(p.f[l], p.t[l])}]++;
-    p.br_shared.assign(nl, -1);
-    p.nshared = 0;
-    for (int l = 0; l < nl; l++)
-        if (count[{std::min(p.f[l], p.t[l]), std::max(p.f[l], p.t[l])}] > 1) p.br_shared[l] = p.nshared++;
-    std::map<std::pair<int, int>, std::vector<int>> targets;  // (isH, pos) -> sources
+    std::vector<std::pair<int, int>> ends;   // (other bus, 2 * branch + end) of one bus
+    std::vector<std::vector<std::pair<int, int>>> at(nb);
     for (int l = 0; l < nl; l++) {
-        int s = p.br_shared[l];
-        if (s < 0) continue;
-        for (int c = 0; c < NOFF; c++)
-            targets[{c >= OH_AA ? 1 : 0, p.br_off[(size_t)c * nl + l]}].push_back(c * p.nshared + s);
+        at[p.f[l]].push_back({p.t[l], 2 * l});
+        at[p.t[l]].push_back({p.f[l], 2 * l + 1});
     }
-    p.fix_ptr.assign(1, 0);
-    for (auto &kv : targets) {
-        for (int src : kv.second) p.fix_src.push_back(src);
-        p.fix_ptr.push_back((int)p.fix_src.size());
-        p.fix_dst.push_back(kv.first.second);
-        p.fix_isH.push_back((uint8_t)kv.first.first);
+    p.slot_nbr.assign(p.nslot, 0);
+    p.slot_ref.assign(p.nslot, 0);
+    for (int i = 0; i < nb; i++) {
+        std::sort(at[i].begin(), at[i].end());
+        int s2 = p.slot_ptr[i];
+        for (auto &e : at[i]) {
+            p.slot_nbr[s2] = e.first;
+            p.slot_ref[s2] = e.second;   // 2 l + end
+            s2++;
+        }
     }
     return EXAGO_OK;
 }

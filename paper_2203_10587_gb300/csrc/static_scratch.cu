@@ -85,10 +85,7 @@ extern "C" exago_status exago_eval_all_static(exago_net_t net, const exago_batch
     R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask;
     R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
     R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
-    char *w = (char *)base;
-    R.scratch = (double *)w;
-    w += ((size_t)bt->B * NCOMP * (size_t)dev->nslot_pad * sizeof(double) + 255) / 256 * 256;
-    R.offscratch = (double *)w;
+    R.scratch = (double *)base;
     int le = launch_eval(*dev, R, bt->stream);
     if (le != 0) return set_last_error(EXAGO_ECUDA, cudaGetErrorString((cudaError_t)le));
     return EXAGO_OK;

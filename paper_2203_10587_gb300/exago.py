@@ -207,7 +207,7 @@ def exago_net_ineq_bounds(h):
 def exago_net_plan_array(h, name: str):
     need = ctypes.c_size_t()
     _check(lib().exago_net_plan_array(h, name.encode(), None, 0, ctypes.byref(need)))
-    dt = np.uint8 if name == "fix_isH" else np.int32
+    dt = np.int32
     out = np.zeros(need.value // np.dtype(dt).itemsize, dt)
     _check(lib().exago_net_plan_array(h, name.encode(), _hp(out) if out.size else None,
                                       need.value, ctypes.byref(need)))

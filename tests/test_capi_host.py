@@ -62,50 +62,91 @@ def test_patterns_match_oracle(L, oracle_mod, name):
     assert net.nnzH == 3 * g.nb + 4 * g.nl + g.ng
 
 
-def write_counts(net, g):
-    """How many times the kernels' write plan touches each J and H position."""
+def write_plan(net, g):
+    """Replays the kernels' writes from the plan: returns, for every J and H position, how often
+    it is written and which column the writing thread believes it holds."""
     A = lambda n: exago.exago_net_plan_array(net.h, n)
     nl, nb = g.nl, g.nb
+    jr, jc = exago.exago_net_jac_pattern(net.h)
+    hr, hc = exago.exago_net_hess_pattern(net.h)
     cj = np.zeros(net.nnzJ, np.int64)
     ch = np.zeros(net.nnzH, np.int64)
-    off = A("br_off").reshape(12, nl)
-    shared = A("br_shared")
-    # every planned write lands inside its output buffer
-    assert np.all(off[:8] >= 0) and np.all(off[:8] < net.nnzJ)
-    assert np.all(off[8:] >= 0) and np.all(off[8:] < net.nnzH)
-    for name, hi in (("bus_jP", net.nnzJ), ("bus_jQ", net.nnzJ), ("gen_jP", net.nnzJ),
-                     ("gen_jQ", net.nnzJ), ("bus_h", net.nnzH), ("gen_h", net.nnzH)):
-        a = A(name)
-        assert np.all(a >= 0) and np.all(a < hi), name
-    assert np.all(A("bus_jP") + A("bus_k") < net.nnzJ)
-    sl = A("br_slot")
-    assert np.all(sl >= 0) and np.all(sl < 2 * nl)
-    assert np.all((shared >= -1) & (shared < max(1, nl)))
-    direct = shared < 0
-    for c in range(8):
-        np.add.at(cj, off[c][direct], 1)
-    for c in range(8, 12):
-        np.add.at(ch, off[c][direct], 1)
-    fix_dst, fix_isH = A("fix_dst"), A("fix_isH")
-    np.add.at(cj, fix_dst[fix_isH == 0], 1)
-    np.add.at(ch, fix_dst[fix_isH == 1], 1)
+    colj = np.full(net.nnzJ, -1, np.int64)
+    colh = np.full(net.nnzH, -1, np.int64)
+
+    def wj(p, col):
+        assert 0 <= p < net.nnzJ
+        cj[p] += 1
+        colj[p] = col
+
+    def wh(p, col):
+        assert 0 <= p < net.nnzH
+        ch[p] += 1
+        colh[p] = col
+
+    slot_ptr, slot_nbr, slot_ref = A("slot_ptr"), A("slot_nbr"), A("slot_ref")
+    # every branch end appears in exactly one slot, at its own bus, naming the other bus
+    assert sorted(slot_ref) == list(range(2 * nl))
+    for i in range(nb):
+        for sl in range(slot_ptr[i], slot_ptr[i + 1]):
+            l, end = divmod(int(slot_ref[sl]), 2)
+            own, other = (g.f[l], g.t[l]) if end == 0 else (g.t[l], g.f[l])
+            assert own == i and slot_nbr[sl] == other
+    # branch: two h rows of four entries, columns (Va_lo, Va_hi, Vm_lo, Vm_hi)
     nnzJg = net.nnzJ - 8 * nl
-    cj[nnzJg:] += 1                                  # h rows: four entries per row, branch-local
-    jP, jQ, k = A("bus_jP"), A("bus_jQ"), A("bus_k")
-    for pos in (jP, jP + k, jQ, jQ + k):
-        np.add.at(cj, pos, 1)
-    np.add.at(cj, A("gen_jP"), 1)
-    np.add.at(cj, A("gen_jQ"), 1)
-    np.add.at(ch, A("bus_h"), 1)
-    np.add.at(ch, A("gen_h"), 1)
-    return cj, ch
+    for l in range(nl):
+        lo, hi = sorted((int(g.f[l]), int(g.t[l])))
+        for row in (nnzJg + 4 * l, nnzJg + 4 * nl + 4 * l):
+            for q, col in enumerate((lo, hi, nb + lo, nb + hi)):
+                wj(row + q, col)
+    jP, jQ, hA, hM = A("bus_jP"), A("bus_jQ"), A("bus_hA"), A("bus_hM")
+    bk, nlow, gptr, gord = A("bus_k"), A("bus_nlow"), A("gen_ptr"), A("gen_ord")
+    hpg = hr[2 * nb]
+    for i in range(nb):
+        nbrs = slot_nbr[slot_ptr[i]:slot_ptr[i + 1]]
+        assert np.all(np.diff(nbrs) >= 0)
+        pos, k = 0, bk[i]
+        for j in np.unique(nbrs):
+            if pos == nlow[i]:
+                pos += 1
+            for base, off, col in ((jP[i], 0, j), (jP[i], k, nb + j), (jQ[i], 0, j), (jQ[i], k, nb + j)):
+                wj(base + off + pos, col)
+            wh(hM[i] + pos, j)
+            if j < i:
+                wh(hA[i] + pos, j)
+                wh(hM[i] + k + pos, nb + j)
+            pos += 1
+        for base, off, col in ((jP[i], 0, i), (jP[i], k, nb + i), (jQ[i], 0, i), (jQ[i], k, nb + i)):
+            wj(base + off + nlow[i], col)
+        wh(hA[i] + nlow[i], i)
+        wh(hM[i] + nlow[i], i)
+        wh(hM[i] + k + nlow[i], nb + i)
+        for q in range(gptr[i + 1] - gptr[i]):
+            kk = gord[gptr[i] + q]
+            wj(jP[i] + 2 * k + q, 2 * nb + kk)
+            wj(jQ[i] + 2 * k + q, 2 * nb + g.ng + kk)
+            wh(hpg + kk, 2 * nb + kk)
+    return cj, ch, colj, colh, jc, hc
+
+
+def check_write_plan(net, g):
+    perm = exago.exago_net_plan_array(net.h, "bus_perm")
+    deg = np.bincount(np.concatenate([g.f, g.t]), minlength=g.nb)
+    for g0 in range(0, g.nb, 64):   # a permutation of each aligned 64-bus group, by degree
+        grp = perm[g0:g0 + 64]
+        assert sorted(grp) == list(range(g0, min(g0 + 64, g.nb)))
+        assert np.all(np.diff(deg[grp]) <= 0)
+    cj, ch, colj, colh, jc, hc = write_plan(net, g)
+    assert np.all(cj == 1) and np.all(ch == 1)
+    np.testing.assert_array_equal(colj, jc)
+    np.testing.assert_array_equal(colh, hc)
 
 
 @pytest.mark.parametrize("name", sorted(GRIDS))
-def test_every_output_written_exactly_once(L, name):
+def test_every_output_written_exactly_once_in_its_column(L, name):
     g = GRIDS[name]()
-    cj, ch = write_counts(plan(g), g)
-    assert np.all(cj == 1) and np.all(ch == 1)
+    net = plan(g)
+    check_write_plan(net, g)
 
 
 def parallel_grid():
@@ -121,26 +162,27 @@ def parallel_grid():
 def test_parallel_branches_plan(L, oracle_mod):
     g = parallel_grid()
     net = plan(g)
-    cj, ch = write_counts(net, g)
-    assert np.all(cj == 1) and np.all(ch == 1)
-    shared = exago.exago_net_plan_array(net.h, "br_shared")
-    assert list(shared) == [0, 1, 2, -1, 3, -1]
+    check_write_plan(net, g)
+    # parallel branches 0/1 (buses 0-1) and 2/4 (buses 1-2) occupy adjacent slots of each bus
+    ref = list(exago.exago_net_plan_array(net.h, "slot_ref"))
+    pos = {r: i for i, r in enumerate(ref)}
+    assert abs(pos[2 * 0 + 0] - pos[2 * 1 + 1]) == 1          # both ends at bus 0
+    assert abs(pos[2 * 2 + 0] - pos[2 * 4 + 0]) == 1          # both from ends at bus 1
     b = synth.random_batch(3, g, 1)
     r = oracle_mod.evaluate(oracle_mod.OracleNet(g), b.x[0], b.lam[0])
     np.testing.assert_array_equal(exago.exago_net_jac_pattern(net.h)[1], r["J"][1])
     np.testing.assert_array_equal(exago.exago_net_hess_pattern(net.h)[1], r["H"][1])
 
 
-def test_slots_sorted_by_bus_then_branch(L):
+def test_slots_sorted_by_bus_other_bus_branch(L):
     g = synth.grid_30bus()
     net = plan(g)
     ptr = exago.exago_net_plan_array(net.h, "slot_ptr")
-    sl = exago.exago_net_plan_array(net.h, "br_slot").reshape(2, g.nl)
-    owner = np.empty(2 * g.nl, np.int64)
-    key = np.empty(2 * g.nl, np.int64)
-    for side, bus in ((0, g.f), (1, g.t)):
-        owner[sl[side]] = bus
-        key[sl[side]] = 2 * np.arange(g.nl) + side
+    ref = exago.exago_net_plan_array(net.h, "slot_ref")
+    l, side = ref // 2, ref % 2
+    owner = np.where(side == 0, g.f[l], g.t[l]).astype(np.int64)
+    other = np.where(side == 0, g.t[l], g.f[l]).astype(np.int64)
+    key = other * (4 * g.nl) + ref
     assert np.all(np.diff(owner) >= 0)
     for i in range(g.nb):
         assert np.all(owner[ptr[i]:ptr[i + 1]] == i)
@@ -192,8 +234,7 @@ def test_degenerate_single_bus(L):
                    c2=np.array([0.01]), c1=np.array([10.0]), c0=np.zeros(1))
     net = plan(g)
     assert (net.n, net.m, net.nnzJ, net.nnzH) == (4, 2, 6, 4)
-    cj, ch = write_counts(net, g)
-    assert np.all(cj == 1) and np.all(ch == 1)
+    check_write_plan(net, g)
 
 
 def test_eval_on_plan_only_net_is_a_state_error(L):

@@ -58,10 +58,10 @@ def test_static_scratch_matches_eval_all_twice(ex, which):
 def test_static_scratch_rejects_oversized_batch(ex):
     """The largest batch that fits the 16 MiB array runs; one state more is refused."""
     import torch
-    g = synth.grid_2000()                      # no parallel branches
+    g = synth.grid_2000()
     net = ex.Net(g)
     limit = 16 << 20
-    per_state = 9 * ((2 * g.nl + 31) // 32 * 32) * 8
+    per_state = 12 * 2 * g.nl * 8
     B_ok = limit // per_state
     for B in (B_ok, B_ok + 1):
         x = torch.zeros(B, net.n, dtype=torch.float64, device="cuda")
