@@ -231,9 +231,16 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *   block     persistent: threads per CTA and items per tile (64, 128, 256; 0 = 128).
  *   occupancy persistent: resident warps per SM the kernel's registers must allow (24 or 32;
  *             0 = the compiler's choice).  Higher occupancy can cost register spills.
+ *   stage_records  EXAGO_STAGE_ON: a bus tile first copies its branch-end records into shared
+ *             memory with coalesced loads; DEFAULT / OFF: each bus reads them through L2.
+ *             EXAGO_SCHED_PIPELINED: the batch in chunks; the branch kernel of a chunk runs on
+ *             the caller's stream while the bus kernel of the previous chunk runs on a
+ *             high-priority net stream, ordered by events only (no device-side waits).
  *   lag       persistent: states by which bus tiles trail branch tiles (0 = derived).
- *   ring      persistent: scratch ring slots, > lag (0 = derived).
- *   use_graph persistent: EXAGO_GRAPH_DEFAULT / ON launch through a cached instantiated CUDA
+ *   ring      persistent: scratch ring slots, > lag (0 = derived); pipelined: chunks of records
+ *             in the ring (0 = 3, at most 7).
+ *   chunk     pipelined: states per chunk (0 = as many as fit 48 MB of records in the ring).
+ *   use_graph persistent and pipelined: EXAGO_GRAPH_DEFAULT / ON launch through a cached instantiated CUDA
  *             graph (one per distinct argument set, 8 kept); OFF launches directly.  A call on a
  *             stream that is being captured always launches directly.
  *   spin_limit  polls (about 0.4 us each) before a device-side wait gives up and records
@@ -241,14 +248,18 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *   test_force_timeout  testing only: bus tiles wait for a count that never arrives, so every
  *             wait times out; the launch still ends and exago_net_check reports it.
  */
-enum { EXAGO_SCHED_AUTO = 0, EXAGO_SCHED_KERNELS = 1, EXAGO_SCHED_PERSISTENT = 2 };
+enum { EXAGO_SCHED_AUTO = 0, EXAGO_SCHED_KERNELS = 1, EXAGO_SCHED_PERSISTENT = 2,
+       EXAGO_SCHED_PIPELINED = 3 };
 enum { EXAGO_GRAPH_DEFAULT = 0, EXAGO_GRAPH_ON = 1, EXAGO_GRAPH_OFF = 2 };
+enum { EXAGO_STAGE_DEFAULT = 0, EXAGO_STAGE_ON = 1, EXAGO_STAGE_OFF = 2 };
 typedef struct {
     int schedule;
     int block;
     int occupancy;
+    int stage_records;
     int lag;
     int ring;
+    int chunk;
     int use_graph;
     long long spin_limit;
     int test_force_timeout;
@@ -261,8 +272,9 @@ exago_status exago_net_set_config(exago_net_t net, const exago_config *cfg);
 exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg);
 
 /*
- * Autotuner: times the multi-kernel schedule and persistent variants (block 128 / 256,
- * occupancy 0 / 24 / 32 warps, two lags)
+ * Autotuner: times the multi-kernel schedule, pipelined variants (three chunk sizes) and
+ * persistent variants (block 128 / 256, occupancy 0 / 24 / 32 warps), each with and without
+ * record staging,
  * on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
  * fastest for batches of this size (used by EXAGO_SCHED_AUTO).  Outputs are written as by
  * exago_eval_all.  *best (may be NULL) receives the choice.
@@ -270,6 +282,46 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg);
 exago_status exago_net_autotune(exago_net_t net, const exago_batch *batch, double *f, double *grad,
                                 double *gh, double *jval, double *hval, int reps,
                                 exago_config *best);
+
+/*
+ * Serving: concurrent solver instances (grids of any sizes, each a registered net) submit
+ * evaluation requests; network data and states stay on the device (ExaGO keeps model evaluation
+ * on the GPU, Sec. II; independent subproblems as in EMPAR, Sec. V-A).  A scheduler thread admits
+ * queued requests in arrival order whenever one of max_slots slots is free and the request's
+ * workspace fits in the server's device arena (device_mem_budget bytes, allocated once here), and
+ * launches each on one of n_streams streams, so requests overlap on the GPU and new ones join as
+ * others finish.  Serving allocates no device memory after exago_serve_create.
+ *   exago_serve_create   EINVAL for max_slots, n_streams < 1 or a zero budget; ENOMEM if the
+ *                        arena cannot be allocated.  The queue holds up to 4 max_slots requests.
+ *   exago_serve_register the server uses (does not own) the net; it must outlive the server.
+ *   exago_serve_submit   request = an exago_batch (device inputs; workspace ignored) and device
+ *                        outputs as for exago_eval_all; all must stay valid until the request
+ *                        completes.  The request runs on a server stream after the work queued on
+ *                        request->stream before the call (an event recorded there), so inputs
+ *                        written on that stream need no synchronisation.  deadline_ms > 0: a request still queued after that
+ *                        long completes with EXAGO_ETIMEOUT without running.  EBUSY when the
+ *                        queue is full, ENOMEM when the request's workspace exceeds the whole
+ *                        budget, EINVAL for bad arguments.  *ticket identifies the request.
+ *   exago_serve_poll     *done = 1 once the request completed (successfully or not).
+ *   exago_serve_wait     waits up to timeout_ms (<= 0: forever) and returns the request's status
+ *                        (EXAGO_OK, or ETIMEOUT for an expired deadline, or the evaluation's
+ *                        error), then forgets the ticket; EBUSY if it is still queued or running.
+ *   exago_serve_stats    submit-to-completion latency quantiles (ms) and count of completed
+ *                        requests so far.
+ *   exago_serve_destroy  fails queued requests (ESTATE), waits for running ones, frees everything.
+ */
+typedef struct exago_server *exago_server_t;
+exago_status exago_serve_create(size_t device_mem_budget, int max_slots, int n_streams,
+                                exago_server_t *out);
+exago_status exago_serve_register(exago_server_t server, exago_net_t net, int *net_id);
+exago_status exago_serve_submit(exago_server_t server, int net_id, const exago_batch *request,
+                                double *f, double *grad, double *gh, double *jval, double *hval,
+                                double deadline_ms, uint64_t *ticket);
+exago_status exago_serve_poll(exago_server_t server, uint64_t ticket, int *done);
+exago_status exago_serve_wait(exago_server_t server, uint64_t ticket, double timeout_ms);
+exago_status exago_serve_stats(exago_server_t server, double *p50_ms, double *p99_ms,
+                               uint64_t *completed);
+exago_status exago_serve_destroy(exago_server_t server);
 
 /*
  * Waits for `stream` and returns the device status word of the net: EXAGO_OK, or EXAGO_ETIMEOUT

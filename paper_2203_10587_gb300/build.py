@@ -49,7 +49,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+    # -fmad=false: no implicit multiply-add contraction, so every instantiation of a kernel
+    # rounds identically (the sources spell out each intended fma)
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
                      "-I", os.path.join(ROOT, "include")]
     if ptxas_info:
         common += ["-Xptxas", "-v"]

@@ -38,9 +38,9 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
     const double Gtt = __ldg(N.Gtt + l), Btt = __ldg(N.Btt + l);
     double s, c;
     branch_sincos(Vaf - Vat, &s, &c);
-    const double Gc = G * c, Gs = G * s, Bc = Bm * c, Bs = Bm * s;
-    const double Af = Gc + Bs, Cf = Gs - Bc;
-    const double At = Gc - Bs, Ct = -(Gs + Bc);
+    const double Bc = Bm * c, Bs = Bm * s;
+    const double Af = fma(G, c, Bs), Cf = fma(G, s, -Bc);
+    const double At = fma(G, c, -Bs), Ct = -fma(G, s, Bc);
     const End ef = end_terms<true>(Gff, Bff, Af, Cf, Vf, Vt);
     const End et = end_terms<true>(Gtt, Btt, At, Ct, Vt, Vf);
 
@@ -81,9 +81,8 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
         const double VV = Vf * Vt, VV2 = VV * VV;
         const EndHess hf = end_hess(ef, Gff, Bff, Af, Cf, K, Vf, Vt, VV, VV2, lPf, lQf, muf);
         const EndHess ht = end_hess(et, Gtt, Btt, At, Ct, K, Vt, Vf, VV, VV2, lPt, lQt, mut);
-        const double haa = hf.haa + ht.haa;
-        const double xf = hf.hau - ht.hav, xt = ht.hau - hf.hav;
-        const double mff = hf.huu + ht.hvv, mtt = ht.huu + hf.hvv, mft = hf.huv + ht.huv;
+        const BranchHess h = branch_hess(hf, ht, Vf, Vt);
+        const double haa = h.haa, xf = h.xf, xt = h.xt, mff = h.mff, mtt = h.mtt, mft = h.mft;
         const double *ub = A.v + (size_t)b * N.n;
         const double dA = __ldg(ub + fb) - __ldg(ub + tb);
         const double uMf = __ldg(ub + nb + fb), uMt = __ldg(ub + nb + tb);

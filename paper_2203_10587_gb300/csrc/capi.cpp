@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -54,7 +55,9 @@ struct exago_net {
     std::vector<GraphEntry> graphs;
     uint64_t graph_clock = 0;
     cudaStream_t cap_stream = nullptr;
-    int occ[9] = {0};             // resident persistent CTAs per SM by (block, occupancy target)
+    cudaStream_t side_stream = nullptr;   // pipelined schedule: bus kernels
+    cudaEvent_t pipe_ev[18] = {};
+    int occ[18] = {0};            // resident persistent CTAs per SM by (block, occupancy, staging)
 };
 
 namespace {
@@ -85,11 +88,18 @@ exago_status alloc_dev(exago_net *net, size_t bytes, double **out) {
 }
 
 void free_device(exago_net *net) {
-    if (!net->graphs.empty() || net->cap_stream) cudaDeviceSynchronize();
+    if (!net->graphs.empty() || net->cap_stream || net->side_stream) cudaDeviceSynchronize();
     for (auto &g : net->graphs) cudaGraphExecDestroy(g.exec);
     net->graphs.clear();
     if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
     net->cap_stream = nullptr;
+    if (net->side_stream) {
+        cudaStreamSynchronize(net->side_stream);
+        cudaStreamDestroy(net->side_stream);
+        for (auto &ev : net->pipe_ev)
+            if (ev) cudaEventDestroy(ev);
+    }
+    net->side_stream = nullptr;
     for (void *p : net->allocs) cudaFree(p);
     net->allocs.clear();
     if (net->ws) cudaFree(net->ws);
@@ -112,27 +122,29 @@ exago_status do_upload(exago_net *net) {
     d.nb = p.nb; d.nl = p.nl; d.ng = p.ng; d.n = p.n; d.m = p.m;
     d.nslot = p.nslot;
     d.nnzJ = p.nnzJ; d.nnzJg = p.nnzJg; d.nnzH = p.nnzH;
+    d.baseMVA = p.baseMVA;
     d.hpg = p.Hrowptr[2 * p.nb];
     d.jP_end = (int)p.Jrowptr[p.nb];
     d.jQ_end = (int)p.Jrowptr[2 * p.nb];
     d.hA_end = (int)p.Hrowptr[p.nb];
     d.hM_end = (int)p.Hrowptr[2 * p.nb];
-    for (int t = 0; t < 3; t++) {   // largest bus tile's row segments, tiles of 64/128/256 buses
+    for (int t = 0; t < 3; t++) {   // largest bus tile's rows (and records), 64/128/256 buses
         const int T = 64 << t;
-        int64_t worst = 0;
+        int64_t rows = 0, all = 0;
         for (int i0 = 0; i0 < p.nb; i0 += T) {
             const int i1 = i0 + T < p.nb ? i0 + T : p.nb;
-            const int64_t need = 2 * (p.Jrowptr[i1] - p.Jrowptr[i0]) +
-                                 (p.Hrowptr[i1] - p.Hrowptr[i0]) +
-                                 (p.Hrowptr[p.nb + i1] - p.Hrowptr[p.nb + i0]);
-            if (need > worst) worst = need;
+            const int64_t r = 2 * (p.Jrowptr[i1] - p.Jrowptr[i0]) + (p.Hrowptr[i1] - p.Hrowptr[i0]) +
+                              (p.Hrowptr[p.nb + i1] - p.Hrowptr[p.nb + i0]);
+            const int64_t a = r + (int64_t)NCOMP * (p.slot_ptr[i1] - p.slot_ptr[i0]);
+            if (r > rows) rows = r;
+            if (a > all) all = a;
         }
-        d.stage_cap[t] = (int)(worst < kStageMaxDoubles ? worst : kStageMaxDoubles);
+        d.stage_cap_rows[t] = (int)(rows < kStageMaxDoubles ? rows : kStageMaxDoubles);
+        d.stage_cap_all[t] = (int)(all < kStageMaxDoubles ? all : kStageMaxDoubles);
     }
-    d.baseMVA = p.baseMVA;
 #define UP(field, vec) if ((s = upload(net, p.vec, &d.field)) != EXAGO_OK) return s
     UP(f, f); UP(t, t);
-    UP(slot_ptr, slot_ptr); UP(slot_nbr, slot_nbr); UP(slot_ref, slot_ref);
+    UP(slot_ptr, slot_ptr); UP(slot_nbr, slot_nbr); UP(slot_ref, slot_ref); UP(br_slot, br_slot);
     UP(bus_jP, bus_jP); UP(bus_jQ, bus_jQ); UP(bus_hA, bus_hA); UP(bus_hM, bus_hM);
     UP(bus_k, bus_k); UP(bus_nlow, bus_nlow); UP(bus_perm, bus_perm);
     UP(Gs, Gs); UP(Bs, Bs); UP(Pd, Pd); UP(Qd, Qd);
@@ -206,14 +218,23 @@ exago_status plan_only(int nb, const double *Gs, const double *Bs, const double 
 // Launch settings of one call, resolved from the net's configuration and the batch size.
 struct Resolved {
     int schedule;          // EXAGO_SCHED_KERNELS or EXAGO_SCHED_PERSISTENT
-    int block, occ_warps, grid, lag, ring, use_graph, force_timeout;
+    int block, occ_warps, stage_recs, grid, lag, ring, use_graph, force_timeout;
+    int chunk, pipe_ring;  // pipelined schedule
     long long spin_limit;
 };
 
 constexpr long long kDefaultSpinLimit = 1ll << 22;   // polls of ~0.4 us: about 1.7 s
 
-int occ_index(int block, int occ_warps) {
-    return (block == 64 ? 0 : block == 256 ? 2 : 1) * 3 + (occ_warps == 24 ? 1 : occ_warps == 32 ? 2 : 0);
+// Resident persistent CTAs per SM for (block, occupancy target, record staging), cached.
+int occupancy(exago_net *net, int block, int occ_warps, int stage_recs) {
+    const int t = stage_index(block);
+    const int idx = (t * 3 + (occ_warps == 24 ? 1 : occ_warps == 32 ? 2 : 0)) * 2 + (stage_recs ? 1 : 0);
+    int &occ = net->occ[idx];
+    if (occ == 0) {
+        const int cap = stage_recs ? net->dev.stage_cap_all[t] : net->dev.stage_cap_rows[t];
+        occ = persist_blocks_per_sm(block, occ_warps, (size_t)cap * sizeof(double));
+    }
+    return occ;
 }
 
 Resolved resolve(exago_net *net, int B) {
@@ -228,14 +249,22 @@ Resolved resolve(exago_net *net, int B) {
         }
     }
     Resolved r{};
-    r.schedule = c.schedule == EXAGO_SCHED_KERNELS ? EXAGO_SCHED_KERNELS : EXAGO_SCHED_PERSISTENT;
+    r.schedule = (c.schedule == EXAGO_SCHED_KERNELS || c.schedule == EXAGO_SCHED_PIPELINED)
+                     ? c.schedule : EXAGO_SCHED_PERSISTENT;
+    {   // pipelined: `ring` chunks of records within about 48 MB of L2
+        const double per_state = (double)NCOMP * net->plan.nslot * sizeof(double);
+        int pr = c.ring > 0 && c.schedule == EXAGO_SCHED_PIPELINED ? c.ring : 3;
+        if (pr > 7) pr = 7;
+        int ch = c.chunk > 0 ? c.chunk : (int)(48e6 / (pr * (per_state > 1 ? per_state : 1)));
+        if (ch < 1) ch = 1;
+        if (ch > B) ch = B;
+        r.chunk = ch;
+        r.pipe_ring = pr;
+    }
     r.block = (c.block == 64 || c.block == 256) ? c.block : 128;
     r.occ_warps = (c.occupancy == 24 || c.occupancy == 32) ? c.occupancy : 0;
-    int &occ = net->occ[occ_index(r.block, r.occ_warps)];
-    if (occ == 0)
-        occ = persist_blocks_per_sm(r.block, r.occ_warps,
-                                    (size_t)net->dev.stage_cap[stage_index(r.block)] * sizeof(double));
-    r.grid = net->sm_count * occ;
+    r.stage_recs = c.stage_records == EXAGO_STAGE_ON;
+    r.grid = net->sm_count * occupancy(net, r.block, r.occ_warps, r.stage_recs);
     const int Tbr = (net->plan.nl + r.block - 1) / r.block;
     // bus tiles trail by the states the resident CTAs can hold in branch work, plus margin
     int lag = c.lag > 0 ? c.lag : (Tbr > 0 ? (r.grid + Tbr - 1) / Tbr : 1) + 2;
@@ -268,7 +297,8 @@ size_t need_bytes(exago_net *net, int B) {
     if (!net->on_device) return k;
     Resolved r = resolve(net, B);
     size_t p = persist_bytes(net, r, B);
-    return k > p ? k : p;
+    size_t q = round256((size_t)r.pipe_ring * r.chunk * slot_bytes(net));
+    return k > p ? (k > q ? k : q) : (p > q ? p : q);
 }
 
 exago_status check_batch(exago_net *net, const exago_batch *bt, bool need_lam) {
@@ -317,16 +347,12 @@ uint64_t bits(double v) {
 
 // Launches the persistent schedule through a cached instantiated CUDA graph (memset of the
 // counters + the persistent kernel).  Caller holds net->mu.
-exago_status launch_graph_locked(exago_net *net, const EvalReq &R, const PersistLaunch &pl,
+// Launches a schedule through a cached instantiated CUDA graph: `launch` queues the schedule's
+// work on a capture stream once per distinct key (every argument the work bakes in).  Caller holds
+// net->mu.
+exago_status launch_graph_locked(exago_net *net, const std::vector<uint64_t> &key,
+                                 const std::function<int(cudaStream_t)> &launch,
                                  cudaStream_t stream) {
-    std::vector<uint64_t> key = {
-        (uint64_t)R.x, (uint64_t)R.lam, (uint64_t)R.mask, (uint64_t)R.pd_scale,
-        (uint64_t)R.obj_weight, (uint64_t)R.f, (uint64_t)R.grad, (uint64_t)R.gh,
-        (uint64_t)R.jval, (uint64_t)R.hval, (uint64_t)R.scratch,
-        (uint64_t)pl.counters, (uint64_t)R.B, bits(R.sigma), (uint64_t)pl.block,
-        (uint64_t)pl.grid, (uint64_t)pl.lag, (uint64_t)pl.ring, (uint64_t)pl.spin_limit,
-        (uint64_t)pl.occ_warps,
-        (uint64_t)pl.force_timeout};
     GraphEntry *hit = nullptr;
     for (auto &g : net->graphs)
         if (g.key == key) { hit = &g; break; }
@@ -338,12 +364,12 @@ exago_status launch_graph_locked(exago_net *net, const EvalReq &R, const Persist
         }
         e = cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-        int le = launch_eval_persistent(net->dev, R, pl, net->cap_stream);
+        int le = launch(net->cap_stream);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(net->cap_stream, &graph);
         if (le != 0) {
             if (graph) cudaGraphDestroy(graph);
-            return cuda_fail((cudaError_t)le, "persistent kernel launch (capture)");
+            return cuda_fail((cudaError_t)le, "kernel launch (capture)");
         }
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
         cudaGraphExec_t exec = nullptr;
@@ -367,8 +393,35 @@ exago_status launch_graph_locked(exago_net *net, const EvalReq &R, const Persist
     return EXAGO_OK;
 }
 
+std::vector<uint64_t> req_key(const EvalReq &R, int schedule) {
+    return {(uint64_t)schedule, (uint64_t)R.x, (uint64_t)R.lam, (uint64_t)R.mask,
+            (uint64_t)R.pd_scale, (uint64_t)R.obj_weight, (uint64_t)R.f, (uint64_t)R.grad,
+            (uint64_t)R.gh, (uint64_t)R.jval, (uint64_t)R.hval, (uint64_t)R.scratch,
+            (uint64_t)R.B, bits(R.sigma), (uint64_t)R.stage_recs};
+}
+
+// The side stream (highest priority, so bus blocks are dispatched as soon as branch blocks retire)
+// and the events of the pipelined schedule, created on first use.  Caller holds net->mu.
+exago_status pipe_resources_locked(exago_net *net, PipeLaunch &pl) {
+    if (!net->side_stream) {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        cudaError_t e = cudaStreamCreateWithPriority(&net->side_stream, cudaStreamNonBlocking, hi);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithPriority");
+        for (int i = 0; i < 18; i++) {
+            e = cudaEventCreateWithFlags(&net->pipe_ev[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate (pipeline)");
+        }
+    }
+    pl.side = net->side_stream;
+    pl.ev_fork = net->pipe_ev[16];
+    pl.ev_join = net->pipe_ev[17];
+    for (int i = 0; i < 8; i++) { pl.ev_br[i] = net->pipe_ev[i]; pl.ev_bu[i] = net->pipe_ev[8 + i]; }
+    return EXAGO_OK;
+}
+
 exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad, double *gh,
-                  double *jval, double *hval, ProfileHook *hook = nullptr) {
+                  double *jval, double *hval, ProfileHook *hook = nullptr, bool allow_graph = true) {
     exago_status s = check_batch(net, bt, hval != nullptr);
     if (s != EXAGO_OK || bt->B == 0) return s;
     std::lock_guard<std::mutex> lk(net->mu);
@@ -384,11 +437,34 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
     R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask;
     R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
     R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
+    R.stage_recs = rs.stage_recs;
     cudaStream_t stream = (cudaStream_t)bt->stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(stream, &cap);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
+    const bool graph = allow_graph && rs.use_graph && !hook && cap == cudaStreamCaptureStatusNone;
     if (rs.schedule == EXAGO_SCHED_KERNELS) {
         R.scratch = (double *)ws;
         int e = launch_eval(net->dev, R, stream, hook);
         if (e != 0) return cuda_fail((cudaError_t)e, "evaluation kernel launch");
+        return EXAGO_OK;
+    }
+    if (rs.schedule == EXAGO_SCHED_PIPELINED) {
+        R.scratch = (double *)ws;
+        PipeLaunch pl{};
+        pl.chunk = rs.chunk;
+        pl.ring = rs.pipe_ring;
+        if ((s = pipe_resources_locked(net, pl)) != EXAGO_OK) return s;
+        const DevNet &dn = net->dev;
+        if (graph) {
+            std::vector<uint64_t> key = req_key(R, EXAGO_SCHED_PIPELINED);
+            key.push_back((uint64_t)pl.chunk);
+            key.push_back((uint64_t)pl.ring);
+            return launch_graph_locked(
+                net, key, [&](cudaStream_t cs) { return launch_eval_pipelined(dn, R, pl, cs); }, stream);
+        }
+        int e = launch_eval_pipelined(dn, R, pl, stream, hook);
+        if (e != 0) return cuda_fail((cudaError_t)e, "pipelined launch");
         return EXAGO_OK;
     }
     char *w = (char *)ws;
@@ -399,11 +475,16 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
     pl.ring = rs.ring;
     pl.spin_limit = rs.spin_limit; pl.force_timeout = rs.force_timeout;
     pl.counters = (int *)w;
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    cudaError_t ce = cudaStreamIsCapturing(stream, &cap);
-    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
-    if (rs.use_graph && !hook && cap == cudaStreamCaptureStatusNone)
-        return launch_graph_locked(net, R, pl, stream);
+    if (graph) {
+        std::vector<uint64_t> key = req_key(R, EXAGO_SCHED_PERSISTENT);
+        for (uint64_t v : {(uint64_t)pl.counters, (uint64_t)pl.block, (uint64_t)pl.grid,
+                           (uint64_t)pl.lag, (uint64_t)pl.ring, (uint64_t)pl.spin_limit,
+                           (uint64_t)pl.occ_warps, (uint64_t)pl.force_timeout})
+            key.push_back(v);
+        const DevNet &dn = net->dev;
+        return launch_graph_locked(
+            net, key, [&](cudaStream_t cs) { return launch_eval_persistent(dn, R, pl, cs); }, stream);
+    }
     int e = launch_eval_persistent(net->dev, R, pl, stream, hook);
     if (e != 0) return cuda_fail((cudaError_t)e, "persistent kernel launch");
     return EXAGO_OK;
@@ -422,6 +503,11 @@ bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **de
 }
 
 exago_status set_last_error(exago_status s, const std::string &msg) { return fail(s, msg); }
+
+exago_status eval_direct(exago_net_t net, const exago_batch *bt, double *f, double *grad,
+                         double *gh, double *jval, double *hval) {
+    return eval(net, bt, f, grad, gh, jval, hval, nullptr, false);
+}
 
 }  // namespace exago
 
@@ -524,6 +610,7 @@ exago_status exago_net_plan_array(exago_net_t net, const char *name, void *dst, 
     size_t n = 0;
 #define ARR(key, vec) if (!std::strcmp(name, key)) { src = p.vec.data(); n = p.vec.size() * sizeof(p.vec[0]); }
     ARR("slot_ptr", slot_ptr) else ARR("slot_nbr", slot_nbr) else ARR("slot_ref", slot_ref)
+    else ARR("br_slot", br_slot)
     else ARR("bus_jP", bus_jP) else ARR("bus_jQ", bus_jQ) else ARR("bus_hA", bus_hA)
     else ARR("bus_hM", bus_hM) else ARR("bus_k", bus_k) else ARR("bus_nlow", bus_nlow)
     else ARR("bus_perm", bus_perm)
@@ -660,15 +747,20 @@ exago_status exago_eval_hvp(exago_net_t net, const exago_batch *bt, const double
 
 exago_status exago_net_set_config(exago_net_t net, const exago_config *cfg) {
     if (!net || !cfg) return fail(EXAGO_EINVAL, "null argument");
-    if (cfg->schedule < EXAGO_SCHED_AUTO || cfg->schedule > EXAGO_SCHED_PERSISTENT)
+    if (cfg->schedule < EXAGO_SCHED_AUTO || cfg->schedule > EXAGO_SCHED_PIPELINED)
         return fail(EXAGO_EINVAL, "unknown schedule");
+    if (cfg->chunk < 0) return fail(EXAGO_EINVAL, "negative chunk");
+    if (cfg->schedule == EXAGO_SCHED_PIPELINED && cfg->ring > 7)
+        return fail(EXAGO_EINVAL, "pipelined ring must be at most 7 chunks");
     if (cfg->block != 0 && cfg->block != 64 && cfg->block != 128 && cfg->block != 256)
         return fail(EXAGO_EINVAL, "block must be 0, 64, 128 or 256");
     if (cfg->occupancy != 0 && cfg->occupancy != 24 && cfg->occupancy != 32)
         return fail(EXAGO_EINVAL, "occupancy must be 0, 24 or 32");
+    if (cfg->stage_records < EXAGO_STAGE_DEFAULT || cfg->stage_records > EXAGO_STAGE_OFF)
+        return fail(EXAGO_EINVAL, "unknown stage_records value");
     if (cfg->lag < 0 || cfg->ring < 0 || cfg->spin_limit < 0)
         return fail(EXAGO_EINVAL, "negative lag, ring or spin limit");
-    if (cfg->ring > 0 && cfg->lag > 0 && cfg->ring <= cfg->lag)
+    if (cfg->schedule != EXAGO_SCHED_PIPELINED && cfg->ring > 0 && cfg->lag > 0 && cfg->ring <= cfg->lag)
         return fail(EXAGO_EINVAL, "ring must exceed lag");
     std::lock_guard<std::mutex> lk(net->mu);
     net->cfg = *cfg;
@@ -682,11 +774,17 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg) {
     const Resolved r = resolve(net, B > 0 ? B : 1);
     *cfg = net->cfg;
     cfg->schedule = r.schedule;
+    cfg->stage_records = r.stage_recs ? EXAGO_STAGE_ON : EXAGO_STAGE_OFF;
     if (r.schedule == EXAGO_SCHED_PERSISTENT) {
         cfg->block = r.block;
         cfg->occupancy = r.occ_warps;
         cfg->lag = r.lag;
         cfg->ring = r.ring;
+        cfg->use_graph = r.use_graph;
+    }
+    if (r.schedule == EXAGO_SCHED_PIPELINED) {
+        cfg->chunk = r.chunk;
+        cfg->ring = r.pipe_ring;
         cfg->use_graph = r.use_graph;
     }
     cfg->spin_limit = r.spin_limit;
@@ -706,25 +804,30 @@ exago_status exago_net_autotune(exago_net_t net, const exago_batch *bt, double *
         exago_config k{};
         k.schedule = EXAGO_SCHED_KERNELS;
         cands.push_back(k);
-        for (int block : {128, 256})
-            for (int occw : {0, 24, 32})
-                for (int lagmul : {1, 2}) {
+        for (int stage : {EXAGO_STAGE_OFF, EXAGO_STAGE_ON}) {
+            exago_config k2 = k;
+            k2.stage_records = stage;
+            if (stage == EXAGO_STAGE_ON) cands.push_back(k2);
+            const Resolved base = resolve(net, bt->B);
+            for (int mul : {1, 2, 4}) {   // pipelined: derived chunk / 2, / 1 and x 2
+                exago_config c{};
+                c.schedule = EXAGO_SCHED_PIPELINED;
+                c.stage_records = stage;
+                c.use_graph = EXAGO_GRAPH_ON;
+                c.chunk = base.chunk * mul / 2 > 0 ? base.chunk * mul / 2 : 1;
+                cands.push_back(c);
+            }
+            for (int block : {128, 256})
+                for (int occw : {0, 24, 32}) {
                     exago_config c{};
                     c.schedule = EXAGO_SCHED_PERSISTENT;
                     c.block = block;
                     c.occupancy = occw;
+                    c.stage_records = stage;
                     c.use_graph = EXAGO_GRAPH_ON;
-                    const int Tbr = (net->plan.nl + block - 1) / block;
-                    int &occ = net->occ[occ_index(block, occw)];
-                    if (occ == 0)
-                        occ = persist_blocks_per_sm(block, occw,
-                                                    (size_t)net->dev.stage_cap[stage_index(block)] *
-                                                        sizeof(double));
-                    const int grid = net->sm_count * occ;
-                    c.lag = lagmul * ((Tbr > 0 ? (grid + Tbr - 1) / Tbr : 1) + 2);
-                    c.ring = 2 * c.lag + 2;
                     cands.push_back(c);
                 }
+        }
     }
     cudaStream_t st = (cudaStream_t)bt->stream;
     cudaEvent_t e0, e1;

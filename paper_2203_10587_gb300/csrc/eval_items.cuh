@@ -76,9 +76,12 @@ __device__ __forceinline__ End end_terms(double Gss, double Bss, double A, doubl
 // Distinct values of one end's Lagrangian Hessian block
 //   lamP grad^2 P + lamQ grad^2 Q + mu grad^2 (P^2 + Q^2)   in (Va_u, Va_v, Vm_u, Vm_v):
 //   (Va_u,Va_u) = -(Va_u,Va_v) = (Va_v,Va_v) = haa;  (Va_u,Vm_u) = -(Va_v,Vm_u) = hau;
-//   (Va_u,Vm_v) = -(Va_v,Vm_v) = hav;  (Vm_u,Vm_u) = huu;  (Vm_u,Vm_v) = huv;  (Vm_v,Vm_v) = hvv.
+//   (Va_u,Vm_v) = -(Va_v,Vm_v) = hav = Vu W2;  (Vm_u,Vm_u) = huu;  (Vm_u,Vm_v) = huv;
+//   (Vm_v,Vm_v) = hvv = tK Vu^2.
+// hav and hvv are left as factors so that the caller folds them into the other end's values
+// with one fma each.
 struct EndHess {
-    double haa, hau, hav, huu, huv, hvv;
+    double haa, hau, huu, huv, W2, tK, Vu2;
 };
 
 __device__ __forceinline__ EndHess end_hess(const End &e, double Gss, double Bss, double A,
@@ -89,19 +92,36 @@ __device__ __forceinline__ EndHess end_hess(const End &e, double Gss, double Bss
     double wP = fma(mu2, e.P, lamP);              // multiplier of grad^2 P
     double wQ = fma(mu2, e.Q, lamQ);
     double W1 = fma(wP, A, wQ * C);
-    double W2 = fma(wQ, A, -(wP * C));
+    h.W2 = fma(wQ, A, -(wP * C));
     double E = fma(A, e.qu, -(C * e.pu));
     double F = fma(e.pu, A, e.qu * C);
-    double tK = mu2 * K;                          // 2 mu (A^2 + C^2)
-    h.haa = fma(tK, VV2, -(VV * W1));
-    h.hau = fma(mu2 * VV, E, Vv * W2);
-    h.hav = Vu * W2;
+    h.tK = mu2 * K;                               // 2 mu (A^2 + C^2)
+    h.haa = fma(h.tK, VV2, -(VV * W1));
+    h.hau = fma(mu2 * VV, E, Vv * h.W2);
     double S = fma(e.pu, e.pu, e.qu * e.qu);
     double in = fma(wP, Gss, -(wQ * Bss));
     h.huu = fma(mu2, S, in + in);
     h.huv = fma(mu2 * Vu, F, W1);
-    h.hvv = tK * (Vu * Vu);
+    h.Vu2 = Vu * Vu;
     return h;
+}
+
+// The branch's Hessian values from its two ends' blocks: (Vm_f, Va_f) = hau_f - hav_t,
+// (Vm_t, Va_t) = hau_t - hav_f, (Vm_f, Vm_f) = huu_f + hvv_t, (Vm_t, Vm_t) = huu_t + hvv_f.
+struct BranchHess {
+    double haa, xf, xt, mff, mtt, mft;
+};
+
+__device__ __forceinline__ BranchHess branch_hess(const EndHess &hf, const EndHess &ht, double Vf,
+                                                  double Vt) {
+    BranchHess b;
+    b.haa = hf.haa + ht.haa;
+    b.xf = fma(-Vt, ht.W2, hf.hau);
+    b.xt = fma(-Vf, hf.W2, ht.hau);
+    b.mff = fma(ht.tK, ht.Vu2, hf.huu);
+    b.mtt = fma(hf.tK, hf.Vu2, ht.huu);
+    b.mft = hf.huv + ht.huv;
+    return b;
 }
 
 // -x for a value that is only stored: the sign bit is flipped on the integer pipe, so that a
@@ -133,9 +153,9 @@ __device__ __forceinline__ void put2(double *rec, int c, double a, double b) {
     *reinterpret_cast<double2 *>(rec + c) = make_double2(a, b);
 }
 
-// One (state b, branch l) item.  scr is state b's record scratch ([2 nl][NCOMP]).  The branch
-// writes its two h values, its two Jacobian h rows (four entries each, contiguous) and the
-// records of both ends, all to addresses contiguous across a warp; the bus phase assembles
+// One (state b, branch l) item.  scr is state b's record scratch ([nslot][NCOMP]).  The branch
+// writes its two h values and its two Jacobian h rows (four entries each, contiguous across a
+// warp), and the 96-byte record of each end at the end's slot; the bus phase assembles
 // everything else row by row.
 template <int WANT>
 __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, int b, int l,
@@ -143,7 +163,8 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     constexpr bool DERIV = WJ || WH;
     const int nb = N.nb, nl = N.nl;
-    double *rf = scr + (size_t)(2 * l) * NCOMP, *rt = rf + NCOMP;
+    double *rf = scr + (size_t)__ldg(N.br_slot + l) * NCOMP;
+    double *rt = scr + (size_t)__ldg(N.br_slot + nl + l) * NCOMP;
     const int fb = __ldg(N.f + l), tb = __ldg(N.t + l);
     double *Jf = WJ ? R.jval + (size_t)b * N.nnzJ + N.nnzJg + 4 * (size_t)l : nullptr;
     double *Jt = WJ ? Jf + 4 * (size_t)nl : nullptr;
@@ -171,9 +192,9 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
 
     double s, c;
     branch_sincos(Vaf - Vat, &s, &c);
-    const double Gc = G * c, Gs = G * s, Bc = Bm * c, Bs = Bm * s;
-    const double Af = Gc + Bs, Cf = Gs - Bc;          // from end, th = Va_f - Va_t
-    const double At = Gc - Bs, Ct = -(Gs + Bc);       // to end,   th = Va_t - Va_f
+    const double Bc = Bm * c, Bs = Bm * s;
+    const double Af = fma(G, c, Bs), Cf = fma(G, s, -Bc);      // from end, th = Va_f - Va_t
+    const double At = fma(G, c, -Bs), Ct = -fma(G, s, Bc);     // to end,   th = Va_t - Va_f
 
     const End ef = end_terms<DERIV>(Gff, Bff, Af, Cf, Vf, Vt);
     const End et = end_terms<DERIV>(Gtt, Btt, At, Ct, Vt, Vf);
@@ -199,12 +220,11 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
         const double VV = Vf * Vt, VV2 = VV * VV;
         const EndHess hf = end_hess(ef, Gff, Bff, Af, Cf, K, Vf, Vt, VV, VV2, lPf, lQf, muf);
         const EndHess ht = end_hess(et, Gtt, Btt, At, Ct, K, Vt, Vf, VV, VV2, lPt, lQt, mut);
-        const double haa = hf.haa + ht.haa;
-        const double mft = hf.huv + ht.huv;
-        put2(rf, SC_HAA, haa, hf.hau - ht.hav);        // (Va_f,Va_f), (Vm_f, Va_f)
-        put2(rt, SC_HAA, haa, ht.hau - hf.hav);        // (Va_t,Va_t), (Vm_t, Va_t)
-        put2(rf, SC_HUU, hf.huu + ht.hvv, mft);
-        put2(rt, SC_HUU, ht.huu + hf.hvv, mft);
+        const BranchHess h = branch_hess(hf, ht, Vf, Vt);
+        put2(rf, SC_HAA, h.haa, h.xf);                 // (Va_f,Va_f), (Vm_f, Va_f)
+        put2(rt, SC_HAA, h.haa, h.xt);                 // (Va_t,Va_t), (Vm_t, Va_t)
+        put2(rf, SC_HUU, h.mff, h.mft);
+        put2(rt, SC_HUU, h.mtt, h.mft);
     }
 }
 
@@ -231,16 +251,24 @@ struct Rec {
     double P, Q, pa, pu, pv, qa, qu, qv, haa, hua, huu, huv;
 };
 
-template <int WANT>
+// A record pair from shared memory (SMEM) or through L2 (records other CTAs wrote this launch).
+template <bool SMEM>
+__device__ __forceinline__ double2 rec2(const double *p) {
+    if (SMEM) return *reinterpret_cast<const double2 *>(p);
+    return ld2(p);
+}
+
+template <int WANT, bool SMEM>
 __device__ __forceinline__ Rec load_rec(const double *rec) {
     Rec r{};
-    if (WANT & W_G) { const double2 v = ld2(rec + SC_P); r.P = v.x; r.Q = v.y; }
+    if (WANT & W_G) { const double2 v = rec2<SMEM>(rec + SC_P); r.P = v.x; r.Q = v.y; }
     if (WANT & W_J) {
-        const double2 a = ld2(rec + SC_PA), v = ld2(rec + SC_PV), u = ld2(rec + SC_QU);
+        const double2 a = rec2<SMEM>(rec + SC_PA), v = rec2<SMEM>(rec + SC_PV);
+        const double2 u = rec2<SMEM>(rec + SC_QU);
         r.pa = a.x; r.pu = a.y; r.pv = v.x; r.qa = v.y; r.qu = u.x; r.qv = u.y;
     }
     if (WANT & W_H) {
-        const double2 h1 = ld2(rec + SC_HAA), h2 = ld2(rec + SC_HUU);
+        const double2 h1 = rec2<SMEM>(rec + SC_HAA), h2 = rec2<SMEM>(rec + SC_HUU);
         r.haa = h1.x; r.hua = h1.y; r.huu = h2.x; r.huv = h2.y;
     }
     return r;
@@ -262,7 +290,7 @@ __device__ __forceinline__ void add_group(Rec &o, const Rec &r) {
 }
 
 // One (state b, bus i) item.  Walks the bus's slots, which come in ascending order of the other
-// bus (parallel branches adjacent), gathers each slot's branch-end record, and writes the bus's
+// bus (parallel branches adjacent), reads each slot's branch-end record, and writes the bus's
 // rows:
 //   g:  P_i and Q_i balances (sums of the end injections, shunt, load and generators);
 //   J:  rows P_i and Q_i entirely -- Va columns, Vm columns (a neighbour's entry is its branch
@@ -270,11 +298,13 @@ __device__ __forceinline__ void add_group(Rec &o, const Rec &r) {
 //       shunt term), then -1 for each generator;
 //   H:  lower-triangle rows Va_i and Vm_i entirely (neighbours below i, the diagonal sums and the
 //       shunt term), and the cost Hessian of the bus's generators.
-// Records are read through L2 (ld.cg): in the persistent schedule other CTAs wrote them during
-// the launch.
-template <int WANT>
+// Records come from the tile's shared-memory copy, or through L2 (ld.cg) when the tile does not
+// fit: in the persistent schedule other CTAs wrote them during the launch.
+// recs + (s - sbase) * NCOMP is slot s's record: the tile's shared-memory copy (SMEM) or state
+// b's scratch in global memory (sbase = 0).
+template <int WANT, bool SMEM>
 __device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int b, int i,
-                                         const double *scr, const BusRows &W) {
+                                         const double *recs, int sbase, const BusRows &W) {
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     const int nb = N.nb;
     const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
@@ -306,17 +336,17 @@ __device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int 
         }
         pos++;
     };
-    auto rec_of = [&](int s) { return scr + (size_t)__ldg(N.slot_ref + s) * NCOMP; };
+    auto rec_of = [&](int s) { return recs + (size_t)(s - sbase) * NCOMP; };
     int s = s0;
     if (s < s1) {
         int j = __ldg(N.slot_nbr + s);
-        Rec o = load_rec<WANT>(rec_of(s));
+        Rec o = load_rec<WANT, SMEM>(rec_of(s));
         D = o;
         for (;;) {
             s++;
             int jn = s < s1 ? __ldg(N.slot_nbr + s) : -1;
             while (jn == j) {                                 // parallel branch to the same bus
-                const Rec p = load_rec<WANT>(rec_of(s));
+                const Rec p = load_rec<WANT, SMEM>(rec_of(s));
                 add_group<WANT>(o, p);
                 add_diag<WANT>(D, p);
                 s++;
@@ -325,7 +355,7 @@ __device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int 
             emit(j, o);
             if (s >= s1) break;
             j = jn;
-            o = load_rec<WANT>(rec_of(s));
+            o = load_rec<WANT, SMEM>(rec_of(s));
             add_diag<WANT>(D, o);
         }
     }
@@ -379,10 +409,13 @@ __device__ __forceinline__ int row_start(const int *starts, int i, int nb, int e
 }
 
 // The bus items of buses [i0, i0 + blockDim.x) of state b, by the whole block (i0 a multiple
-// of 64).  When the tile's
-// row segments fit `stage` (cap doubles of shared memory), every bus writes its rows there and
-// the block then copies the four contiguous segments out with coalesced stores; otherwise the
-// rows go straight to global memory.  Contains __syncthreads: call from every thread.
+// of 64), with `stage` = cap doubles of shared memory.  The tile's slots are one contiguous range.
+// With R.stage_recs, and when the tile's records and row segments fit, the block first copies
+// the records in with coalesced 16-byte loads and every bus reads its slots there; otherwise each
+// bus reads its records through L2.  When the row segments fit (after the records, if staged),
+// every bus writes its rows there and the block copies the four contiguous segments out with
+// coalesced stores; otherwise the rows go straight to global memory.  Contains __syncthreads:
+// call from every thread.
 template <int WANT>
 __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int b, int i0,
                                          const double *scr, double *stage, int cap) {
@@ -393,40 +426,54 @@ __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int 
     // thread -> bus through the degree-sorted permutation (it maps every aligned 64-bus group,
     // hence every tile, onto itself)
     const int i = i0 + (int)threadIdx.x < i1 ? __ldg(N.bus_perm + i0 + threadIdx.x) : nb;
+    const int S0 = __ldg(N.slot_ptr + i0), S1 = __ldg(N.slot_ptr + i1);
     const int p0 = row_start(N.bus_jP, i0, nb, N.jP_end), p1 = row_start(N.bus_jP, i1, nb, N.jP_end);
     const int q0 = row_start(N.bus_jQ, i0, nb, N.jQ_end);
     const int a0 = row_start(N.bus_hA, i0, nb, N.hA_end), a1 = row_start(N.bus_hA, i1, nb, N.hA_end);
     const int m0 = row_start(N.bus_hM, i0, nb, N.hM_end), m1 = row_start(N.bus_hM, i1, nb, N.hM_end);
     const int LP = WJ ? p1 - p0 : 0, LA = WH ? a1 - a0 : 0, LM = WH ? m1 - m0 : 0;
-    const bool staged = 2 * LP + LA + LM <= cap;
+    const int LROWS = 2 * LP + LA + LM;
+    const bool recs_staged = R.stage_recs && NCOMP * (S1 - S0) + LROWS <= cap;
+    const int LR = recs_staged ? NCOMP * (S1 - S0) : 0;
+    const bool staged = (WJ || WH) && LR + LROWS <= cap;
     double *Jb = WJ ? R.jval + (size_t)b * N.nnzJ : nullptr;
     double *Hb = WH ? R.hval + (size_t)b * N.nnzH : nullptr;
+    if (recs_staged) {
+        const double2 *src = reinterpret_cast<const double2 *>(scr + (size_t)S0 * NCOMP);
+        double2 *dst = reinterpret_cast<double2 *>(stage);
+        for (int e = threadIdx.x; e < LR / 2; e += blockDim.x) dst[e] = __ldcg(src + e);
+        __syncthreads();
+    }
+    double *rows = stage + LR;
     if (i < i1) {
         BusRows W{};
         if (staged) {
             if (WJ) {
-                W.JP = stage + (__ldg(N.bus_jP + i) - p0);
-                W.JQ = stage + LP + (__ldg(N.bus_jQ + i) - q0);
+                W.JP = rows + (__ldg(N.bus_jP + i) - p0);
+                W.JQ = rows + LP + (__ldg(N.bus_jQ + i) - q0);
             }
             if (WH) {
-                W.HA = stage + 2 * LP + (__ldg(N.bus_hA + i) - a0);
-                W.HM = stage + 2 * LP + LA + (__ldg(N.bus_hM + i) - m0);
+                W.HA = rows + 2 * LP + (__ldg(N.bus_hA + i) - a0);
+                W.HM = rows + 2 * LP + LA + (__ldg(N.bus_hM + i) - m0);
             }
         } else {
             if (WJ) { W.JP = Jb + __ldg(N.bus_jP + i); W.JQ = Jb + __ldg(N.bus_jQ + i); }
             if (WH) { W.HA = Hb + __ldg(N.bus_hA + i); W.HM = Hb + __ldg(N.bus_hM + i); }
         }
-        bus_item<WANT>(N, R, b, i, scr, W);
+        if (recs_staged) bus_item<WANT, true>(N, R, b, i, stage, S0, W);
+        else bus_item<WANT, false>(N, R, b, i, scr, 0, W);
     }
-    if (staged && (WJ || WH)) {
+    if (staged) {
         __syncthreads();
         for (int e = threadIdx.x; e < LP; e += blockDim.x) {
-            Jb[p0 + e] = stage[e];
-            Jb[q0 + e] = stage[LP + e];
+            Jb[p0 + e] = rows[e];
+            Jb[q0 + e] = rows[LP + e];
         }
-        for (int e = threadIdx.x; e < LA; e += blockDim.x) Hb[a0 + e] = stage[2 * LP + e];
-        for (int e = threadIdx.x; e < LM; e += blockDim.x) Hb[m0 + e] = stage[2 * LP + LA + e];
+        for (int e = threadIdx.x; e < LA; e += blockDim.x) Hb[a0 + e] = rows[2 * LP + e];
+        for (int e = threadIdx.x; e < LM; e += blockDim.x) Hb[m0 + e] = rows[2 * LP + LA + e];
         __syncthreads();
+    } else if (recs_staged) {
+        __syncthreads();   // the next tile may overwrite the records
     }
 }
 

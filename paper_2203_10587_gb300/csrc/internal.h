@@ -13,9 +13,10 @@
 namespace exago {
 
 // Per-(branch, end) record handed from the branch phase to the bus phase: NCOMP doubles at
-// scratch[((b * 2 nl) + 2 l + end) * NCOMP + k] for state b, branch l, end 0 (from) or 1 (to).
-// Records are ordered by branch, so a warp of consecutive branches writes contiguous memory; the
-// bus phase gathers them through the slot lists.  For the end at bus u towards bus v:
+// scratch[(b * nslot + slot) * NCOMP + k] for state b, where slot is the end's position in its
+// bus's slot list.  A bus tile's records are therefore one contiguous range, which the bus phase
+// copies to shared memory in one coalesced pass; the branch phase writes each 96-byte record as
+// three whole sectors.  For the end at bus u towards bus v:
 enum SlotComp {
     SC_P = 0,    // active injection of this end at u
     SC_Q = 1,    // reactive injection
@@ -50,7 +51,8 @@ struct HostPlan {
     int nslot = 0;                // 2 nl
     std::vector<int> slot_ptr;    // [nb + 1] slots of bus i are [slot_ptr[i], slot_ptr[i+1])
     std::vector<int> slot_nbr;    // [nslot] the other bus of the slot's branch
-    std::vector<int> slot_ref;    // [nslot] record index 2 l + end of the slot
+    std::vector<int> slot_ref;    // [nslot] 2 l + end of the slot (adjoint records by branch)
+    std::vector<int> br_slot;     // [2][nl] slot of the from end and of the to end
 
     // Row starts of bus i: J rows P_i and Q_i, H rows Va_i and Vm_i; k_i = neighbours + 1 (Va
     // columns of a J row, Vm columns follow); nlow_i = neighbours below i (position of the
@@ -68,11 +70,12 @@ struct DevNet {
     int nb, nl, ng, n, m, nslot;
     int64_t nnzJ, nnzJg, nnzH, hpg;          // hpg: H position of (Pg_0, Pg_0)
     int jP_end, jQ_end, hA_end, hM_end;      // ends of the four row blocks of the bus rows
-    int stage_cap[3];                        // staging doubles for bus tiles of 64/128/256 buses
+    int stage_cap_rows[3];                   // shared-memory doubles of a bus tile of 64/128/256
+    int stage_cap_all[3];                    // buses: its row segments, or records plus rows
     double baseMVA;
     const int *f, *t;
     const double *Gff, *Bff, *Gtt, *Btt, *Gft, *Bft;   // pi-model admittances (no phase shift: ft == tf)
-    const int *slot_ptr, *slot_nbr, *slot_ref;
+    const int *slot_ptr, *slot_nbr, *slot_ref, *br_slot;
     const int *bus_jP, *bus_jQ, *bus_hA, *bus_hM, *bus_k, *bus_nlow, *bus_perm;
     const double *Gs, *Bs, *Pd, *Qd;
     const int *gen_ptr, *gen_ord;
@@ -88,7 +91,20 @@ struct EvalReq {
     const double *pd_scale, *obj_weight;
     double sigma;
     double *f, *grad, *gh, *jval, *hval;
-    double *scratch;            // [B][2 nl][NCOMP] branch-end records (or ring slots)
+    double *scratch;            // [B][nslot][NCOMP] branch-end records (or ring slots)
+    int scr_b0;                 // state b's records are at scratch + (b - scr_b0) * nslot * NCOMP
+                                // in the multi-kernel and pipelined schedules
+    int stage_recs;             // bus tiles copy their records to shared memory first
+};
+
+// Pipelined schedule (kernels.cu): the batch in chunks; the branch kernel of a chunk runs on the
+// caller's stream while the bus kernel of the previous chunk runs on `side`, ordered by events
+// only.  Records of `ring` chunks rotate through the workspace.
+struct PipeLaunch {
+    int chunk, ring;
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
+    cudaEvent_t ev_br[8], ev_bu[8];   // ring + 1 <= 8
 };
 
 // One adjoint-product call (adjoint.cu): JVP u -> J u, JTV v -> J^T v, HVP u -> (grad^2 L) u.
@@ -128,6 +144,8 @@ int launch_admittance(const double *r, const double *x, const double *b, const d
                       int nl, double *Gff, double *Bff, double *Gtt, double *Btt, double *Gft,
                       double *Bft, void *stream);
 int launch_eval(const DevNet &net, const EvalReq &req, void *stream, ProfileHook *hook = nullptr);
+int launch_eval_pipelined(const DevNet &net, const EvalReq &req, const PipeLaunch &pl,
+                          void *stream, ProfileHook *hook = nullptr);
 
 // Persistent schedule (one launch; see persist.cu).  counters: 1 + 2B ints of the workspace;
 // req.scratch holds `ring` state slots.
@@ -144,9 +162,10 @@ int launch_eval_persistent(const DevNet &net, const EvalReq &req, const PersistL
                            void *stream, ProfileHook *hook = nullptr);
 int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes);
 
-// Shared-memory staging of a bus tile's row segments (eval_items.cuh, bus_tile): the largest
-// tile's need in doubles, capped at kStageMaxDoubles (tiles above the cap write directly).
-constexpr int kStageMaxDoubles = 6144;   // 48 KB
+// Shared memory of a bus tile (eval_items.cuh, bus_tile): its records and its row segments.  The
+// largest tile's need in doubles, capped at kStageMaxDoubles; a tile above the cap reads its
+// records from global memory and writes its rows directly.
+constexpr int kStageMaxDoubles = 9216;   // 72 KB
 inline int stage_index(int block) { return block == 64 ? 0 : block == 256 ? 2 : 1; }
 int persist_allow_stage();   // persist.cu
 int bus_allow_stage();       // kernels.cu
@@ -155,5 +174,8 @@ int bus_allow_stage();       // kernels.cu
 // thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.
 bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **dev, int *device);
 exago_status set_last_error(exago_status s, const std::string &msg);
+// exago_eval_all without the graph cache (serving: every request has its own buffers).
+exago_status eval_direct(exago_net_t net, const exago_batch *bt, double *f, double *grad,
+                         double *gh, double *jval, double *hval);
 
 }  // namespace exago

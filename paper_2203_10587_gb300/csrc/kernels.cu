@@ -5,16 +5,16 @@
 // GB300 executes FP64 at 1/64 of the FP32 rate (about 600 G FP64 instructions/s for the whole
 // GPU), so the branch arithmetic, not HBM, bounds this path.  The kernels are therefore written
 // to issue as few FP64 instructions as possible:
-//   * one sincos per branch, shared by both ends; the trig products G cos, G sin, B cos, B sin
-//     serve both ends' flows (no phase shift: the mutual admittances are equal);
+//   * one sincos per branch, shared by both ends; B cos and B sin serve both ends' flows and
+//     each A, C term is one fma (no phase shift: the mutual admittances are equal);
 //   * P and dP/dVm of an end come from one product Gss Vu + Vv A; the angle derivatives are
 //     products of the magnitude derivatives;
 //   * the Lagrangian Hessian block of an end, lamP grad^2 P + lamQ grad^2 Q + mu grad^2 (P^2+Q^2),
 //     has only six distinct values, because every angle derivative is antisymmetric in
 //     (Va_from, Va_to); A^2 + C^2 = G^2 + B^2 is a per-branch constant;
 //   * out-of-service branches take a predicated path that only stores zeros;
-//   * assembly sums per-bus partials in a fixed order (ascending branch, from end first), with
-//     no atomics, so results do not depend on the launch shape.
+//   * assembly sums each bus's branch-end records in a fixed slot order (by the other bus, then
+//     branch), with no atomics, so results do not depend on the launch shape.
 #include <cuda_runtime.h>
 
 #include "eval_items.cuh"
@@ -58,15 +58,15 @@ template <int WANT>
 __global__ void __launch_bounds__(128) k_branch(const DevNet N, const EvalReq R, int b0) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = b0 + blockIdx.y;
-    if (l < N.nl) branch_item<WANT>(N, R, b, l, R.scratch + (size_t)b * N.nslot * NCOMP);
+    if (l < N.nl) branch_item<WANT>(N, R, b, l, R.scratch + (size_t)(b - R.scr_b0) * N.nslot * NCOMP);
 }
 
 template <int WANT>
 __global__ void __launch_bounds__(128) k_bus(const DevNet N, const EvalReq R, int b0) {
     extern __shared__ double stage[];
     const int b = b0 + blockIdx.y;
-    bus_tile<WANT>(N, R, b, blockIdx.x * blockDim.x, R.scratch + (size_t)b * N.nslot * NCOMP,
-                   stage, N.stage_cap[1]);
+    bus_tile<WANT>(N, R, b, blockIdx.x * blockDim.x, R.scratch + (size_t)(b - R.scr_b0) * N.nslot * NCOMP,
+                   stage, R.stage_recs ? N.stage_cap_all[1] : N.stage_cap_rows[1]);
 }
 
 // Gradient of the objective: w (2 c2 base^2 Pg + c1 base) on Pg entries, 0 elsewhere.
@@ -91,7 +91,7 @@ static void launch_branch_bus(const DevNet &N, const EvalReq &R, int b0, int nB,
         k_branch<WANT><<<dim3((N.nl + 127) / 128, nB), 128, 0, st>>>(N, R, b0);
     }
     mark(hk, st, "bus");
-    const size_t smem = (size_t)N.stage_cap[1] * sizeof(double);
+    const size_t smem = (size_t)(R.stage_recs ? N.stage_cap_all[1] : N.stage_cap_rows[1]) * sizeof(double);
     k_bus<WANT><<<dim3((N.nb + 127) / 128, nB), 128, smem, st>>>(N, R, b0);
 }
 
@@ -135,6 +135,62 @@ int launch_eval(const DevNet &N, const EvalReq &R, void *stream, ProfileHook *hk
         k_obj<<<R.B, OBJ_LANES, 0, st>>>(N, R, 0);
     }
     mark(hk, st, "end");
+    return (int)cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pipelined schedule.  For chunk k of `chunk` states: the branch kernel runs on the caller's
+// stream, then the bus and gradient kernels run on the side stream after an event from it, so
+// the FP64-bound branch work of chunk k + 1 overlaps the latency-bound bus work of chunk k on the
+// same SMs (each kernel keeps its own register allocation).  The branch kernel of chunk k waits
+// for the bus kernel of chunk k - ring before it overwrites that chunk's ring slot.  All ordering
+// is by events between launches; nothing waits inside a kernel.
+template <int WANT>
+static void pipe_chunk(const DevNet &N, const EvalReq &Rk, int b0, int nB, cudaStream_t main,
+                       cudaStream_t side, cudaEvent_t ev_br, cudaEvent_t ev_bu) {
+    if (N.nl > 0) k_branch<WANT><<<dim3((N.nl + 127) / 128, nB), 128, 0, main>>>(N, Rk, b0);
+    cudaEventRecord(ev_br, main);
+    cudaStreamWaitEvent(side, ev_br, 0);
+    const size_t smem = (size_t)(Rk.stage_recs ? N.stage_cap_all[1] : N.stage_cap_rows[1]) * sizeof(double);
+    if constexpr (WANT != 0) k_bus<WANT><<<dim3((N.nb + 127) / 128, nB), 128, smem, side>>>(N, Rk, b0);
+    if (Rk.grad) k_grad<<<dim3((N.n + 255) / 256, nB), 256, 0, side>>>(N, Rk, b0);
+    cudaEventRecord(ev_bu, side);
+}
+
+int launch_eval_pipelined(const DevNet &N, const EvalReq &R, const PipeLaunch &P, void *stream,
+                          ProfileHook *hk) {
+    cudaStream_t main = (cudaStream_t)stream;
+    if (R.B <= 0) return 0;
+    if (P.chunk < 1 || P.ring < 1 || P.ring + 1 > 8) return (int)cudaErrorInvalidValue;
+    const int want = (R.gh ? W_G : 0) | (R.jval ? W_J : 0) | (R.hval ? W_H : 0);
+    const size_t chunk_doubles = (size_t)P.chunk * N.nslot * NCOMP;
+    mark(hk, main, "pipelined");
+    cudaEventRecord(P.ev_fork, main);
+    cudaStreamWaitEvent(P.side, P.ev_fork, 0);
+    if (R.f) k_obj<<<R.B, OBJ_LANES, 0, main>>>(N, R, 0);
+    const int nchunks = (R.B + P.chunk - 1) / P.chunk;
+    for (int k = 0; k < nchunks; k++) {
+        const int b0 = k * P.chunk;
+        const int nB = R.B - b0 < P.chunk ? R.B - b0 : P.chunk;
+        if (k >= P.ring) cudaStreamWaitEvent(main, P.ev_bu[(k - P.ring) % (P.ring + 1)], 0);
+        EvalReq Rk = R;
+        Rk.scratch = R.scratch + (size_t)(k % P.ring) * chunk_doubles;
+        Rk.scr_b0 = b0;
+        cudaEvent_t eb = P.ev_br[k % (P.ring + 1)], eu = P.ev_bu[k % (P.ring + 1)];
+        switch (want) {
+            case 0: pipe_chunk<0>(N, Rk, b0, nB, main, P.side, eb, eu); break;
+            case W_G: pipe_chunk<W_G>(N, Rk, b0, nB, main, P.side, eb, eu); break;
+            case W_J: pipe_chunk<W_J>(N, Rk, b0, nB, main, P.side, eb, eu); break;
+            case W_G | W_J: pipe_chunk<W_G | W_J>(N, Rk, b0, nB, main, P.side, eb, eu); break;
+            case W_H: pipe_chunk<W_H>(N, Rk, b0, nB, main, P.side, eb, eu); break;
+            case W_G | W_H: pipe_chunk<W_G | W_H>(N, Rk, b0, nB, main, P.side, eb, eu); break;
+            case W_J | W_H: pipe_chunk<W_J | W_H>(N, Rk, b0, nB, main, P.side, eb, eu); break;
+            default: pipe_chunk<W_G | W_J | W_H>(N, Rk, b0, nB, main, P.side, eb, eu); break;
+        }
+    }
+    cudaEventRecord(P.ev_join, P.side);
+    cudaStreamWaitEvent(main, P.ev_join, 0);
+    mark(hk, main, "end");
     return (int)cudaGetLastError();
 }
 

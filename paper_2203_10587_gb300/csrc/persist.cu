@@ -36,6 +36,12 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     return v;
 }
 
+// Signals one finished tile: a release add at GPU scope.  Called by thread 0 after a
+// __syncthreads, so it publishes the whole block's writes (release is cumulative).
+__device__ __forceinline__ void red_release_add(int *p) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(p) : "memory");
+}
+
 // Polls *p until it reaches target; false (and a timeout code in the status word) after
 // spin_limit polls.
 __device__ bool bounded_wait(const int *p, int target, long long limit, int *status, int code) {
@@ -80,9 +86,18 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
     extern __shared__ double stage[];
     int *done_br = P.ctr + 1, *done_bu = P.ctr + 1 + P.B;
     const size_t slot_doubles = (size_t)NCOMP * N.nslot;
-    const int cap = N.stage_cap[NT == 64 ? 0 : NT == 256 ? 2 : 1];
+    const int cap = R.stage_recs ? N.stage_cap_all[NT == 64 ? 0 : NT == 256 ? 2 : 1]
+                                 : N.stage_cap_rows[NT == 64 ? 0 : NT == 256 ? 2 : 1];
+    // Thread 0 claims the next ticket while the block works on the current one.  The smallest
+    // unfinished ticket is always some block's current item (a block's prefetched ticket is
+    // larger than its current one), so the argument above still holds.
+    int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(P.ctr, 1);
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(P.ctr, 1);
+        if (threadIdx.x == 0) {
+            s_item = next;
+            if (next < P.total) next = atomicAdd(P.ctr, 1);
+        }
         __syncthreads();
         const int t = s_item;
         if (t >= P.total) return;
@@ -99,27 +114,20 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
             const int l = tile * NT + threadIdx.x;
             if (s_ok && l < N.nl) branch_item<WANT>(N, R, b, l, scr);
             __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(done_br + b, 1);
-            }
+            if (threadIdx.x == 0) red_release_add(done_br + b);
         } else {
             if (threadIdx.x == 0)
                 s_ok = bounded_wait(done_br + b, P.Tbr + P.force_timeout, P.spin_limit, N.status,
                                     ST_TIMEOUT_BUS);
             __syncthreads();
             if (s_ok) {
-                __threadfence();
                 const int i = tile * NT + threadIdx.x;
                 if (WANT) bus_tile<WANT>(N, R, b, tile * NT, scr, stage, cap);
                 if (i < N.nb && R.grad) grad_bus(N, R, b, i);
                 if (tile == 0 && R.f) obj_block(N, R, b, s_part);
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(done_bu + b, 1);
-            }
+            if (threadIdx.x == 0) red_release_add(done_bu + b);
         }
     }
 }
@@ -167,7 +175,8 @@ template <int NT>
 static int launch_persist_nt(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
                              int occ_warps, cudaStream_t st) {
     const int want = (R.gh ? W_G : 0) | (R.jval ? W_J : 0) | (R.hval ? W_H : 0);
-    const size_t smem = (size_t)N.stage_cap[NT == 64 ? 0 : NT == 256 ? 2 : 1] * sizeof(double);
+    const int ti = NT == 64 ? 0 : NT == 256 ? 2 : 1;
+    const size_t smem = (size_t)(R.stage_recs ? N.stage_cap_all[ti] : N.stage_cap_rows[ti]) * sizeof(double);
     constexpr int ALL = W_G | W_J | W_H;
     if (want == ALL && occ_warps == 24) launch_one<ALL, NT, minb(NT, 24)>(N, R, P, grid, smem, st);
     else if (want == ALL && occ_warps == 32) launch_one<ALL, NT, minb(NT, 32)>(N, R, P, grid, smem, st);

@@ -226,12 +226,14 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
     }
     p.slot_nbr.assign(p.nslot, 0);
     p.slot_ref.assign(p.nslot, 0);
+    p.br_slot.assign(2 * (size_t)nl, 0);
     for (int i = 0; i < nb; i++) {
         std::sort(at[i].begin(), at[i].end());
         int s2 = p.slot_ptr[i];
         for (auto &e : at[i]) {
             p.slot_nbr[s2] = e.first;
             p.slot_ref[s2] = e.second;   // 2 l + end
+            p.br_slot[(size_t)(e.second & 1) * nl + (e.second >> 1)] = s2;
             s2++;
         }
     }

@@ -1,0 +1,416 @@
+// Serving loop over the evaluator (the C ABI's exago_serve_*): concurrent solver instances on
+// grids of different sizes submit evaluation requests; network data and states stay on the
+// device (ExaGO's GPU mode keeps model evaluation on the device, Sec. II), and independent
+// subproblems run side by side (EMPAR, Sec. V-A).
+//
+// Continuous batching: a scheduler thread admits queued requests whenever a slot and enough of
+// the device arena are free -- not when a whole batch has drained -- and launches each on one of
+// the server's streams, so requests that arrive while others run overlap with them on the GPU.
+// Each request's scratch is carved from one arena allocated at creation, so serving allocates
+// nothing afterwards.  Completion is signalled by a host function queued behind the request's
+// kernels (it only sets a flag; CUDA calls are not allowed there).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+enum ReqState { RQ_QUEUED, RQ_RUNNING, RQ_DONE };
+
+struct Request {
+    uint64_t ticket = 0;
+    int net_id = 0;
+    exago_batch batch{};
+    double *f = nullptr, *grad = nullptr, *gh = nullptr, *jval = nullptr, *hval = nullptr;
+    size_t ws_bytes = 0, ws_off = 0;
+    bool has_deadline = false;
+    Clock::time_point submitted, deadline, finished;
+    int stream = -1;
+    cudaEvent_t ready = nullptr;    // recorded on the caller's stream at submission
+    ReqState state = RQ_QUEUED;
+    exago_status status = EXAGO_OK;
+    std::string err;
+    struct exago_server *server = nullptr;
+    std::atomic<int> gpu_done{0};   // set by the host function queued behind the kernels
+};
+
+// First-fit allocator over [0, size) with coalescing frees; offsets are 256-byte aligned.
+class Arena {
+  public:
+    void reset(size_t size) {
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        auto it = free_.emplace(off, bytes).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+  private:
+    std::map<size_t, size_t> free_;
+};
+
+}  // namespace
+
+struct exago_server {
+    size_t budget = 0;
+    char *arena_base = nullptr;
+    Arena arena;
+    int max_slots = 1, running = 0;
+    size_t max_queue = 4;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> all_events, free_events;   // one per queued or running request
+    std::vector<exago_net_t> nets;
+    std::deque<Request *> queue;
+    std::map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::vector<double> latencies_ms;
+    uint64_t next_ticket = 1;
+    int next_stream = 0;
+    int device = 0;
+    std::mutex mu;                 // requests, queue, arena, slots (never held by on_done)
+    std::condition_variable cv_done;
+    // Wake-ups of the scheduler: submissions and completions bump `events` under wake_mu, which is
+    // never held across a CUDA call (the completion host function takes it; a CUDA call that
+    // waits for that function must not hold it).
+    std::mutex wake_mu;
+    std::condition_variable cv_wake;
+    uint64_t events = 0;
+    bool stop = false;
+    std::thread worker;
+};
+
+namespace {
+
+exago_status sfail(exago_status s, const std::string &m) {
+    exago::set_last_error(s, m);
+    return s;
+}
+
+void wake(exago_server *S) {
+    {
+        std::lock_guard<std::mutex> lk(S->wake_mu);
+        S->events++;
+    }
+    S->cv_wake.notify_one();
+}
+
+// Host function behind a request's kernels: flags completion and wakes the scheduler.  It takes
+// only wake_mu, so a CUDA call that waits for it can never wait on the server's lock.
+void CUDART_CB on_done(void *p) {
+    Request *r = (Request *)p;
+    r->gpu_done.store(1, std::memory_order_release);
+    wake(r->server);
+}
+
+// Caller holds S->mu.
+void finish_locked(exago_server *S, Request *r, exago_status st, const std::string &err) {
+    r->state = RQ_DONE;
+    r->status = st;
+    r->err = err;
+    r->finished = Clock::now();
+    if (r->ready) {
+        S->free_events.push_back(r->ready);
+        r->ready = nullptr;
+    }
+    if (st == EXAGO_OK)
+        S->latencies_ms.push_back(
+            std::chrono::duration<double, std::milli>(r->finished - r->submitted).count());
+    S->cv_done.notify_all();
+}
+
+void worker_loop(exago_server *S) {
+    cudaSetDevice(S->device);
+    uint64_t seen = 0;
+    for (;;) {
+        bool progress = false;
+        Clock::time_point until = Clock::now() + std::chrono::milliseconds(50);
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->stop) return;
+            // retire finished requests: free their slot and arena range
+            for (auto &kv : S->reqs) {
+                Request *r = kv.second.get();
+                if (r->state == RQ_RUNNING && r->gpu_done.load(std::memory_order_acquire)) {
+                    S->arena.release(r->ws_off, r->ws_bytes);
+                    S->running--;
+                    finish_locked(S, r, EXAGO_OK, "");
+                    progress = true;
+                }
+            }
+            // expire queued requests whose deadline passed
+            const auto now = Clock::now();
+            for (auto it = S->queue.begin(); it != S->queue.end();) {
+                if ((*it)->has_deadline && now > (*it)->deadline) {
+                    finish_locked(S, *it, EXAGO_ETIMEOUT, "deadline passed while queued");
+                    it = S->queue.erase(it);
+                    progress = true;
+                } else {
+                    ++it;
+                }
+            }
+            // admit in arrival order while a slot and arena memory are free
+            while (!S->queue.empty() && S->running < S->max_slots) {
+                Request *r = S->queue.front();
+                size_t off = 0;
+                if (!S->arena.alloc(r->ws_bytes, &off)) break;   // memory-gated: wait for a release
+                S->queue.pop_front();
+                r->ws_off = off;
+                r->stream = S->next_stream;
+                S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
+                r->batch.workspace = S->arena_base + off;
+                r->batch.workspace_bytes = r->ws_bytes;
+                r->batch.stream = S->streams[r->stream];
+                // inputs produced on the caller's stream before submission are ready first
+                cudaError_t ew = cudaStreamWaitEvent(S->streams[r->stream], r->ready, 0);
+                exago_status st = ew != cudaSuccess ? exago::set_last_error(EXAGO_ECUDA, cudaGetErrorString(ew))
+                                                    : exago::eval_direct(S->nets[r->net_id], &r->batch, r->f, r->grad,
+                                                     r->gh, r->jval, r->hval);
+                cudaError_t e = st == EXAGO_OK
+                                    ? cudaLaunchHostFunc(S->streams[r->stream], on_done, r)
+                                    : cudaSuccess;
+                if (st != EXAGO_OK || e != cudaSuccess) {
+                    S->arena.release(off, r->ws_bytes);
+                    finish_locked(S, r, st != EXAGO_OK ? st : EXAGO_ECUDA,
+                                  st != EXAGO_OK ? exago_last_error() : cudaGetErrorString(e));
+                } else {
+                    r->state = RQ_RUNNING;
+                    S->running++;
+                }
+                progress = true;
+            }
+            for (Request *q : S->queue)
+                if (q->has_deadline && q->deadline < until) until = q->deadline;
+        }
+        if (!progress) {
+            // sleep until a submission, a completion, or the nearest deadline
+            std::unique_lock<std::mutex> wl(S->wake_mu);
+            S->cv_wake.wait_until(wl, until, [&] { return S->events != seen || S->stop; });
+            seen = S->events;
+        }
+    }
+}
+
+Request *find_locked(exago_server *S, uint64_t ticket) {
+    auto it = S->reqs.find(ticket);
+    return it == S->reqs.end() ? nullptr : it->second.get();
+}
+
+}  // namespace
+
+extern "C" {
+
+exago_status exago_serve_create(size_t device_mem_budget, int max_slots, int n_streams,
+                                exago_server_t *out) {
+    if (!out) return sfail(EXAGO_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (max_slots < 1 || n_streams < 1 || device_mem_budget == 0)
+        return sfail(EXAGO_EINVAL, "need max_slots >= 1, n_streams >= 1 and a non-zero budget");
+    std::unique_ptr<exago_server> S(new (std::nothrow) exago_server());
+    if (!S) return sfail(EXAGO_ENOMEM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&S->device);
+    if (e != cudaSuccess) return sfail(EXAGO_ECUDA, cudaGetErrorString(e));
+    S->budget = (device_mem_budget + 255) / 256 * 256;
+    e = cudaMalloc((void **)&S->arena_base, S->budget);
+    if (e != cudaSuccess)
+        return sfail(e == cudaErrorMemoryAllocation ? EXAGO_ENOMEM : EXAGO_ECUDA,
+                     std::string("cudaMalloc (serve arena): ") + cudaGetErrorString(e));
+    S->arena.reset(S->budget);
+    S->max_slots = max_slots;
+    S->max_queue = 4 * (size_t)max_slots;
+    for (int i = 0; i < n_streams; i++) {
+        cudaStream_t st;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (auto s2 : S->streams) cudaStreamDestroy(s2);
+            cudaFree(S->arena_base);
+            return sfail(EXAGO_ECUDA, cudaGetErrorString(e));
+        }
+        S->streams.push_back(st);
+    }
+    for (size_t i = 0; i < S->max_queue + (size_t)max_slots; i++) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (auto ev2 : S->all_events) cudaEventDestroy(ev2);
+            for (auto s2 : S->streams) cudaStreamDestroy(s2);
+            cudaFree(S->arena_base);
+            return sfail(EXAGO_ECUDA, cudaGetErrorString(e));
+        }
+        S->all_events.push_back(ev);
+    }
+    S->free_events = S->all_events;
+    exago_server *raw = S.release();
+    raw->worker = std::thread(worker_loop, raw);
+    *out = raw;
+    return EXAGO_OK;
+}
+
+exago_status exago_serve_register(exago_server_t S, exago_net_t net, int *net_id) {
+    if (!S || !net || !net_id) return sfail(EXAGO_EINVAL, "null argument");
+    int n = 0;
+    if (exago_net_dims(net, &n, nullptr, nullptr, nullptr, nullptr) != EXAGO_OK)
+        return sfail(EXAGO_EINVAL, "invalid net");
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->nets.push_back(net);
+    *net_id = (int)S->nets.size() - 1;
+    return EXAGO_OK;
+}
+
+exago_status exago_serve_submit(exago_server_t S, int net_id, const exago_batch *req, double *f,
+                                double *grad, double *gh, double *jval, double *hval,
+                                double deadline_ms, uint64_t *ticket) {
+    if (!S || !req || !ticket) return sfail(EXAGO_EINVAL, "null argument");
+    std::unique_ptr<Request> r(new (std::nothrow) Request());
+    if (!r) return sfail(EXAGO_ENOMEM, "host allocation failed");
+    exago_net_t net;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (net_id < 0 || net_id >= (int)S->nets.size()) return sfail(EXAGO_EINVAL, "unknown net id");
+        net = S->nets[net_id];
+    }
+    if (req->B < 1 || !req->x) return sfail(EXAGO_EINVAL, "request needs B >= 1 and x");
+    if (hval && !req->lambda) return sfail(EXAGO_EINVAL, "the Hessian needs lambda");
+    size_t ws = 0;
+    exago_status st = exago_eval_workspace_size(net, req->B, &ws);
+    if (st != EXAGO_OK) return st;
+    if ((ws + 255) / 256 * 256 > S->budget)
+        return sfail(EXAGO_ENOMEM, "request needs more workspace than the server's whole budget");
+    r->net_id = net_id;
+    r->batch = *req;
+    r->f = f; r->grad = grad; r->gh = gh; r->jval = jval; r->hval = hval;
+    r->ws_bytes = ws > 0 ? ws : 256;
+    r->submitted = Clock::now();
+    if (deadline_ms > 0) {
+        r->has_deadline = true;
+        r->deadline = r->submitted + std::chrono::microseconds((long long)(deadline_ms * 1000.0));
+    }
+    r->server = S;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->queue.size() >= S->max_queue || S->free_events.empty())
+            return sfail(EXAGO_EBUSY, "serve queue full");
+        cudaError_t e = cudaEventRecord(S->free_events.back(), (cudaStream_t)req->stream);
+        if (e != cudaSuccess)
+            return sfail(EXAGO_ECUDA, std::string("cudaEventRecord (request stream): ") + cudaGetErrorString(e));
+        r->ready = S->free_events.back();
+        S->free_events.pop_back();
+        r->ticket = S->next_ticket++;
+        *ticket = r->ticket;
+        S->queue.push_back(r.get());
+        S->reqs[r->ticket] = std::move(r);
+    }
+    wake(S);
+    return EXAGO_OK;
+}
+
+exago_status exago_serve_poll(exago_server_t S, uint64_t ticket, int *done) {
+    if (!S || !done) return sfail(EXAGO_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    Request *r = find_locked(S, ticket);
+    if (!r) return sfail(EXAGO_EINVAL, "unknown ticket");
+    *done = r->state == RQ_DONE;
+    return EXAGO_OK;
+}
+
+exago_status exago_serve_wait(exago_server_t S, uint64_t ticket, double timeout_ms) {
+    if (!S) return sfail(EXAGO_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    Request *r = find_locked(S, ticket);
+    if (!r) return sfail(EXAGO_EINVAL, "unknown ticket");
+    auto pred = [&] { return r->state == RQ_DONE; };
+    if (timeout_ms > 0) {
+        if (!S->cv_done.wait_for(lk, std::chrono::microseconds((long long)(timeout_ms * 1000.0)), pred))
+            return sfail(EXAGO_EBUSY, "request still queued or running");
+    } else {
+        S->cv_done.wait(lk, pred);
+    }
+    const exago_status st = r->status;
+    const std::string err = r->err;
+    S->reqs.erase(ticket);
+    if (st != EXAGO_OK) return sfail(st, err);
+    return EXAGO_OK;
+}
+
+exago_status exago_serve_stats(exago_server_t S, double *p50_ms, double *p99_ms, uint64_t *completed) {
+    if (!S) return sfail(EXAGO_EINVAL, "null server");
+    std::vector<double> v;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        v = S->latencies_ms;
+    }
+    if (completed) *completed = v.size();
+    std::sort(v.begin(), v.end());
+    auto q = [&](double p) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(p * (v.size() - 1) + 0.5))]; };
+    if (p50_ms) *p50_ms = q(0.50);
+    if (p99_ms) *p99_ms = q(0.99);
+    return EXAGO_OK;
+}
+
+exago_status exago_serve_destroy(exago_server_t S) {
+    if (!S) return EXAGO_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (Request *r : S->queue) finish_locked(S, r, EXAGO_ESTATE, "server destroyed");
+        S->queue.clear();
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->wake_mu);
+        S->stop = true;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_wake.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (auto st : S->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (auto ev : S->all_events) cudaEventDestroy(ev);
+    cudaFree(S->arena_base);
+    delete S;
+    return EXAGO_OK;
+}
+
+}  // extern "C"

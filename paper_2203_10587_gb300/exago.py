@@ -31,11 +31,13 @@ EXPORTS = [
     "exago_eval_jac", "exago_eval_hess", "exago_eval_all", "exago_eval_jvp", "exago_eval_jtv",
     "exago_eval_hvp", "exago_eval_all_static",
     "exago_eval_profile", "exago_net_set_config", "exago_net_get_config", "exago_net_autotune",
-    "exago_net_check",
+    "exago_net_check", "exago_serve_create", "exago_serve_register", "exago_serve_submit",
+    "exago_serve_poll", "exago_serve_wait", "exago_serve_stats", "exago_serve_destroy",
 ]
 
-SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT = 0, 1, 2
+SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
 GRAPH_DEFAULT, GRAPH_ON, GRAPH_OFF = 0, 1, 2
+STAGE_DEFAULT, STAGE_ON, STAGE_OFF = 0, 1, 2
 
 
 class ExagoError(RuntimeError):
@@ -47,8 +49,8 @@ class ExagoError(RuntimeError):
 
 class exago_config(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("block", ctypes.c_int),
-                ("occupancy", ctypes.c_int), ("lag", ctypes.c_int),
-                ("ring", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("occupancy", ctypes.c_int), ("stage_records", ctypes.c_int), ("lag", ctypes.c_int),
+                ("ring", ctypes.c_int), ("chunk", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("spin_limit", ctypes.c_longlong), ("test_force_timeout", ctypes.c_int)]
 
     def as_dict(self):
@@ -109,6 +111,16 @@ def lib():
                 "exago_net_autotune": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp, i32,
                                         ctypes.POINTER(exago_config)], i32),
                 "exago_net_check": ([vp, vp], i32),
+                "exago_serve_create": ([ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)], i32),
+                "exago_serve_register": ([vp, vp, ctypes.POINTER(i32)], i32),
+                "exago_serve_submit": ([vp, i32, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], i32),
+                "exago_serve_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(i32)], i32),
+                "exago_serve_wait": ([vp, ctypes.c_uint64, ctypes.c_double], i32),
+                "exago_serve_stats": ([vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_uint64)], i32),
+                "exago_serve_destroy": ([vp], i32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -306,10 +318,10 @@ def exago_eval_profile(h, batch: exago_batch, f=None, grad=None, gh=None, jval=N
     return [(names[k].decode(), ms[k]) for k in range(nk.value)]
 
 
-def exago_net_set_config(h, schedule=0, block=0, occupancy=0, lag=0, ring=0, use_graph=0,
-                         spin_limit=0, test_force_timeout=0):
-    c = exago_config(schedule, block, occupancy, lag, ring, use_graph, spin_limit,
-                     test_force_timeout)
+def exago_net_set_config(h, schedule=0, block=0, occupancy=0, stage_records=0, lag=0, ring=0,
+                         chunk=0, use_graph=0, spin_limit=0, test_force_timeout=0):
+    c = exago_config(schedule, block, occupancy, stage_records, lag, ring, chunk, use_graph,
+                     spin_limit, test_force_timeout)
     _check(lib().exago_net_set_config(h, ctypes.byref(c)))
 
 
@@ -332,6 +344,48 @@ def exago_net_check(h, stream=None):
     if stream is None:
         stream = torch.cuda.current_stream()
     _check(lib().exago_net_check(h, ctypes.c_void_p(stream.cuda_stream)))
+
+
+def exago_serve_create(device_mem_budget: int, max_slots: int, n_streams: int):
+    h = ctypes.c_void_p()
+    _check(lib().exago_serve_create(int(device_mem_budget), int(max_slots), int(n_streams),
+                                    ctypes.byref(h)))
+    return h
+
+
+def exago_serve_register(s, net_h) -> int:
+    i = ctypes.c_int()
+    _check(lib().exago_serve_register(s, net_h, ctypes.byref(i)))
+    return i.value
+
+
+def exago_serve_submit(s, net_id: int, batch: exago_batch, f=None, grad=None, gh=None, jval=None,
+                       hval=None, deadline_ms: float = 0.0) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().exago_serve_submit(s, int(net_id), ctypes.byref(batch), _out(f), _out(grad),
+                                    _out(gh), _out(jval), _out(hval), float(deadline_ms),
+                                    ctypes.byref(t)))
+    return t.value
+
+
+def exago_serve_poll(s, ticket: int) -> bool:
+    d = ctypes.c_int()
+    _check(lib().exago_serve_poll(s, ctypes.c_uint64(ticket), ctypes.byref(d)))
+    return bool(d.value)
+
+
+def exago_serve_wait(s, ticket: int, timeout_ms: float = 0.0):
+    _check(lib().exago_serve_wait(s, ctypes.c_uint64(ticket), float(timeout_ms)))
+
+
+def exago_serve_stats(s):
+    p50, p99, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+    _check(lib().exago_serve_stats(s, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n)))
+    return p50.value, p99.value, n.value
+
+
+def exago_serve_destroy(s):
+    _check(lib().exago_serve_destroy(s))
 
 
 # ---- convenience ------------------------------------------------------------------------------

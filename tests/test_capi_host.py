@@ -85,8 +85,11 @@ def write_plan(net, g):
         colh[p] = col
 
     slot_ptr, slot_nbr, slot_ref = A("slot_ptr"), A("slot_nbr"), A("slot_ref")
-    # every branch end appears in exactly one slot, at its own bus, naming the other bus
+    # every branch end appears in exactly one slot, at its own bus, naming the other bus; its
+    # record lives at that slot (br_slot)
     assert sorted(slot_ref) == list(range(2 * nl))
+    br_slot = A("br_slot")
+    assert np.all(slot_ref[br_slot] == np.concatenate([2 * np.arange(nl), 2 * np.arange(nl) + 1]))
     for i in range(nb):
         for sl in range(slot_ptr[i], slot_ptr[i + 1]):
             l, end = divmod(int(slot_ref[sl]), 2)

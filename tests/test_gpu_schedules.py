@@ -1,6 +1,6 @@
 """GPU: the persistent fused schedule (one launch, work list, ring scratch, bounded waits, CUDA
-graph) against the multi-kernel schedule and the oracle; fault injection of the bounded waits;
-the autotuner.
+graph) and the pipelined two-stream schedule against the multi-kernel schedule and the oracle;
+fault injection of the bounded waits; the autotuner.
 """
 import numpy as np
 import pytest
@@ -29,6 +29,10 @@ CONFIGS = [
     dict(schedule=2, block=256, lag=3, ring=5),
     dict(schedule=2, occupancy=32),                     # register-capped variant
     dict(schedule=2, block=256, occupancy=24),
+    dict(schedule=3),                                   # pipelined, derived chunk, graph
+    dict(schedule=3, chunk=7, ring=2, stage_records=1), # ring reuse from the third chunk on
+    dict(schedule=3, chunk=5, use_graph=2),             # direct launches
+    dict(schedule=1, stage_records=1),
 ]
 
 
@@ -133,3 +137,7 @@ def test_profile_names_the_persistent_kernel(ex):
     prof = ex.exago_eval_profile(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"],
                                  out["hval"], reps=3)
     assert [n for n, _ in prof] == ["branch", "bus", "grad", "obj"]
+    ex.exago_net_set_config(net.h, schedule=3)
+    prof = ex.exago_eval_profile(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"],
+                                 out["hval"], reps=3)
+    assert [n for n, _ in prof] == ["pipelined"]
