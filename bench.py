@@ -33,12 +33,15 @@ UNIT = "evals/s"
 WORKLOAD = "2000-bus x 512 N-1 contingencies: f, grad f, g|h, J values, Lagrangian Hessian values"
 B_DEFAULT = 512
 N_INPUT_SETS = 4
-# FP64 work per unit with every output requested, counted from the kernel source (an FMA counts
-# 2 flops): (flops, instructions).
-FP64_PER_BRANCH = (188, 136)   # branch terms, fast sincos path
-FP64_PER_SLOT = (9, 9)         # one branch end's 9 partial sums at its bus
+# FP64 work per unit with every output requested, counted from the kernel source on the fast
+# sincos path (an FMA counts 2 flops): (flops, instructions).  Per 2000-bus state they sum to
+# 593,400 flops / 419,900 instructions; ncu's executed FP64 thread-instruction counters of the
+# persistent kernel give 596,300 / 422,900.
+FP64_PER_BRANCH = (190, 130)   # sincos, flows, 16 derivatives, h and its J row, Hessian fold
+FP64_PER_SLOT = (9, 9)         # a branch end's record summed into its bus (all but the first)
 FP64_PER_BUS = (20, 15)        # shunt, load and diagonal terms of one bus
-FP64_PER_GEN = (18, 15)        # balance, cost Hessian, gradient and objective terms of one generator
+FP64_PER_GEN = (19, 16)        # balance, cost Hessian, gradient and objective terms of a generator
+FP64_PER_STATE = (255, 255)    # the objective's fixed 256-lane reduction tree
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 2 FP64 FMA per SM per clock x
 # 2 flops x 2.07 GHz (the probe measured 1.20 TFLOP/s at 1.97 GHz under load).
 SMS, FP64_FMA_PER_SM_CLK, SM_MAX_GHZ = 152, 2, 2.07
@@ -46,7 +49,8 @@ FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ / 1e3
 FP64_PEAK_GINSTR = SMS * FP64_FMA_PER_SM_CLK * SM_MAX_GHZ
 # dram bytes per launch of the dominant kernel from its ncu capture, by kernel name; a kernel
 # changed since its capture has no entry
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {"persistent": 384_762_624}   # 61.5 MB read + 323.2 MB written (ncu, 2000-bus x 512)
+HBM_PEAK_FALLBACK_GBS = 6800.0
 
 
 def parse():
@@ -58,7 +62,32 @@ def parse():
     p.add_argument("--B", type=int, default=B_DEFAULT)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving-mix measurement")
+    p.add_argument("--serve-seconds", type=float, default=1.5, help="length of each serving phase")
     return p.parse_args()
+
+
+# ---- multi-rank helpers (one process per GPU; states are independent, so ranks share nothing
+# but the timing reduction)
+
+def rank_seed(rank: int, s: int) -> int:
+    """Seed of input set s on `rank`: every rank evaluates its own contingency states."""
+    return 3 + 1000 * rank + 17 * s
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's elapsed time (all ranks receive it)."""
+    if world == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, B: int, elapsed_ms: float) -> float:
+    """Whole-job evaluations per second: all ranks' states over the slowest rank's time."""
+    return world * steps * B / (elapsed_ms / 1e3)
 
 
 # ---- clocks during the timed region ------------------------------------------------------------
@@ -167,6 +196,166 @@ def run_reference(args, rank: int):
     }), flush=True)
 
 
+# ---- serving mix ---------------------------------------------------------------------------------
+
+SERVE_MIX = ((118, 0.4), (2_000, 0.3), (10_000, 0.2), (70_000, 0.1))
+SERVE_CLIENTS = 64
+SERVE_SLOTS, SERVE_STREAMS, SERVE_BUDGET = 16, 8, 2 << 30
+
+
+def quantiles(v):
+    v = sorted(v)
+    q = lambda p: v[min(len(v) - 1, int(p * (len(v) - 1) + 0.5))] if v else None
+    return q(0.50), q(0.99)
+
+
+class ServeClients:
+    """64 simulated IPM clients on grids of 118 / 2,000 / 10,000 / 70,000 buses (40/30/20/10%);
+    each owns one device state (B = 1) and its output buffers, and has at most one request out."""
+
+    def __init__(self, exago, synth, torch, np, dev, seed=5):
+        import ctypes
+        self.exago, self.torch, self.ct = exago, torch, ctypes
+        self.grids = [synth.grid_sized(50 + k, nb) for k, (nb, _) in enumerate(SERVE_MIX)]
+        self.nets = [exago.Net(g) for g in self.grids]
+        share = [p for _, p in SERVE_MIX]
+        counts = [int(round(SERVE_CLIENTS * p)) for p in share]
+        counts[0] += SERVE_CLIENTS - sum(counts)
+        self.by_grid = []
+        self.clients = []
+        td = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        for gi, cnt in enumerate(counts):
+            ids = []
+            for _ in range(cnt):
+                b = synth.random_batch(seed * 1000 + len(self.clients), self.grids[gi], 1)
+                x, lam = td(b.x, torch.float64), td(b.lam, torch.float64)
+                bt = exago.make_batch(x, lam, obj_factor=1.0)
+                out = self.nets[gi].outputs(1, dev)
+                ptrs = [ctypes.c_void_p(out[k].data_ptr()) for k in ("f", "grad", "gh", "jval", "hval")]
+                ids.append(len(self.clients))
+                self.clients.append((gi, x, lam, bt, out, ptrs))
+            self.by_grid.append(ids)
+        self.share = share
+        torch.cuda.synchronize()
+
+    def one_at_a_time(self, rng, n):
+        """The same kind of requests, each launched alone and waited for (no overlap)."""
+        seq = [self.pick(rng) for _ in range(n)]
+        for c in seq[:8]:
+            self.eval_alone(c)
+        lat = []
+        t0 = time.perf_counter()
+        for c in seq:
+            t = time.perf_counter()
+            self.eval_alone(c)
+            lat.append(1e3 * (time.perf_counter() - t))
+        dt = time.perf_counter() - t0
+        p50, p99 = quantiles(lat)
+        return {"evals_per_s": n / dt, "p50_ms": p50, "p99_ms": p99, "requests": n}
+
+    def pick(self, rng):
+        gi = int(rng.choice(len(self.share), p=self.share))
+        ids = self.by_grid[gi]
+        return ids[int(rng.integers(len(ids)))]
+
+    def eval_alone(self, c):
+        gi, _, _, bt, out, _ = self.clients[c]
+        self.nets[gi].eval_all(bt, out)
+        self.torch.cuda.synchronize()
+
+    def run(self, rng, seconds, rate=None):
+        """Closed loop (rate None: every client resubmits as soon as its request completes) or
+        Poisson arrivals at `rate` requests/s, each taking a free client of a grid drawn from the
+        mix.  Returns throughput and the server's submit-to-completion latency quantiles."""
+        ex, L, ct = self.exago, self.exago.lib(), self.ct
+        srv = ex.exago_serve_create(SERVE_BUDGET, SERVE_SLOTS, SERVE_STREAMS)
+        nids = [ex.exago_serve_register(srv, n.h) for n in self.nets]
+        tk = ct.c_uint64()
+        done = ct.c_int()
+        out_t = {}                      # client -> ticket
+        free = [list(ids) for ids in self.by_grid]
+        deferred = 0
+
+        def submit(c):
+            gi, _, _, bt, _, p = self.clients[c]
+            st = L.exago_serve_submit(srv, nids[gi], ct.byref(bt), p[0], p[1], p[2], p[3], p[4],
+                                      ct.c_double(0.0), ct.byref(tk))
+            if st != 0:
+                ex._check(st)
+            out_t[c] = tk.value
+
+        def finish(c):
+            ex._check(L.exago_serve_wait(srv, ct.c_uint64(out_t.pop(c)), ct.c_double(0.0)))
+            free[self.clients[c][0]].append(c)
+
+        def harvest(gi):
+            for c in [c for c in self.by_grid[gi] if c in out_t]:
+                ex._check(L.exago_serve_poll(srv, ct.c_uint64(out_t[c]), ct.byref(done)))
+                if done.value:
+                    finish(c)
+
+        t0 = time.perf_counter()
+        n_sub = 0
+        try:
+            if rate is None:
+                order = list(range(len(self.clients)))
+                for c in order:
+                    submit(c)
+                    n_sub += 1
+                k = 0
+                while time.perf_counter() - t0 < seconds:
+                    c = order[k % len(order)]
+                    k += 1
+                    gi = self.clients[c][0]
+                    finish(c)
+                    free[gi].remove(c)
+                    submit(c)
+                    n_sub += 1
+            else:
+                t_next = t0
+                while True:
+                    t_next += float(rng.exponential(1.0 / rate))
+                    if t_next - t0 >= seconds:
+                        break
+                    while time.perf_counter() < t_next:
+                        pass
+                    gi = int(rng.choice(len(self.share), p=self.share))
+                    if not free[gi]:
+                        harvest(gi)
+                    if not free[gi]:
+                        deferred += 1
+                        oldest = min((c for c in self.by_grid[gi] if c in out_t), key=out_t.get)
+                        finish(oldest)
+                    submit(free[gi].pop())
+                    n_sub += 1
+            for c in list(out_t):
+                finish(c)
+            dt = time.perf_counter() - t0
+            p50, p99, n = ex.exago_serve_stats(srv)
+        finally:
+            ex.exago_serve_destroy(srv)
+        res = {"evals_per_s": n / dt, "p50_ms": p50, "p99_ms": p99, "requests": int(n)}
+        if rate is not None:
+            res.update(offered_per_s=rate, deferred=deferred)
+        return res
+
+
+def run_serve(exago, synth, torch, np, dev, seconds):
+    rng = np.random.default_rng(5)
+    sc = ServeClients(exago, synth, torch, np, dev)
+    alone = sc.one_at_a_time(rng, 2000)
+    sc.run(rng, 0.3)                                   # warm-up
+    peak = sc.run(rng, seconds)
+    res = {"workload": "Poisson arrivals of B=1 requests from 64 clients on 118 / 2,000 / 10,000 / "
+                       "70,000-bus grids (40/30/20/10%), one registered net per grid",
+           "server": {"max_slots": SERVE_SLOTS, "streams": SERVE_STREAMS,
+                      "arena_mb": SERVE_BUDGET >> 20},
+           "one_at_a_time": alone, "closed_loop_peak": peak}
+    for frac in (0.5, 0.9):
+        res[f"load_{frac}"] = sc.run(rng, seconds, rate=frac * peak["evals_per_s"])
+    return res
+
+
 # ---- GPU arm -------------------------------------------------------------------------------------
 
 def run_gpu(args, rank: int, world: int, local_rank: int):
@@ -184,7 +373,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     grid = synth.grid_2000()
     net = exago.Net(grid)
     B = args.B
-    sets = [synth.contingency_batch(3 + 1000 * rank + 17 * s, grid, B) for s in range(N_INPUT_SETS)]
+    sets = [synth.contingency_batch(rank_seed(rank, s), grid, B) for s in range(N_INPUT_SETS)]
     td = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     ins = [(td(b.x, torch.float64), td(b.lam, torch.float64), td(b.mask, torch.uint8)) for b in sets]
     stream = torch.cuda.current_stream(dev)
@@ -229,11 +418,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     exago.exago_net_check(net.h)
     elapsed_ms = ev[0].elapsed_time(ev[-1])
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
-    value = world * args.steps * B / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, world, dev)
+    value = job_value(world, args.steps, B, elapsed_ms)
 
     # ---- per-kernel timing of the same evaluation (CUDA events on the launching stream)
     prof = exago.exago_eval_profile(net.h, batches[0], out["f"], out["grad"], out["gh"],
@@ -244,11 +430,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     # FP64 work of the dominant kernel per launch: the fused persistent kernel does every stage,
     # the multi-kernel schedule's top kernel is the branch kernel
     if top_name == "persistent":
-        work = [(FP64_PER_BRANCH, grid.nl), (FP64_PER_SLOT, 2 * grid.nl), (FP64_PER_BUS, grid.nb),
-                (FP64_PER_GEN, grid.ng)]
-        per_unit = ("per state: %d branches x %d + %d branch ends x %d + %d buses x %d + "
-                    "%d generators x %d FP64 flops" % (grid.nl, FP64_PER_BRANCH[0], 2 * grid.nl,
-                    FP64_PER_SLOT[0], grid.nb, FP64_PER_BUS[0], grid.ng, FP64_PER_GEN[0]))
+        work = [(FP64_PER_BRANCH, grid.nl), (FP64_PER_SLOT, 2 * grid.nl - grid.nb),
+                (FP64_PER_BUS, grid.nb), (FP64_PER_GEN, grid.ng), (FP64_PER_STATE, 1)]
+        per_unit = ("per state: %d branches x %d + %d extra branch ends x %d + %d buses x %d + "
+                    "%d generators x %d + %d FP64 flops" % (
+                        grid.nl, FP64_PER_BRANCH[0], 2 * grid.nl - grid.nb, FP64_PER_SLOT[0],
+                        grid.nb, FP64_PER_BUS[0], grid.ng, FP64_PER_GEN[0], FP64_PER_STATE[0]))
     else:
         work = [(FP64_PER_BRANCH, grid.nl)]
         per_unit = "per state: %d branches x %d FP64 flops" % (grid.nl, FP64_PER_BRANCH[0])
@@ -265,6 +452,12 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     net_bytes = 112 * grid.nl + 64 * grid.nb + 40 * grid.ng   # network tables, once per launch
     bytes_per_eval = in_bytes + out_bytes
     hbm_gbs = (bytes_per_eval * B + net_bytes) * args.steps / (elapsed_ms / 1e3) / 1e9
+    hbm_peak, hbm_src = HBM_PEAK_FALLBACK_GBS, "fallback"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            hbm_peak, hbm_src = float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        pass
 
     # ---- the same kernels one instance at a time (unbatched)
     n_single = min(B, 128)
@@ -315,13 +508,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = world * k_e2e * B / (float(t.item()) / 1e3)
+    e2e_value = job_value(world, k_e2e, B, max_over_ranks(e2e_ms, world, dev))
 
     if rank != 0:
         return
+    serve = None if args.no_serve else run_serve(exago, synth, torch, np, dev, args.serve_seconds)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -345,16 +536,22 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                      "units_per_launch": units, "launch_ms": top_ms,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
                      "fp64_instr": {"achieved_g_per_s": achieved_gi, "peak_g_per_s": FP64_PEAK_GINSTR,
-                                    "frac": achieved_gi / FP64_PEAK_GINSTR}},
+                                    "frac": achieved_gi / FP64_PEAK_GINSTR},
+                     "hbm": {"achieved_gbs": (bytes_per_eval * B + net_bytes) / (top_ms * 1e-3) / 1e9,
+                             "peak_gbs": hbm_peak, "peak_source": hbm_src,
+                             "frac": (bytes_per_eval * B + net_bytes) / (top_ms * 1e-3) / 1e9 / hbm_peak,
+                             "algorithmic_bytes_per_launch": bytes_per_eval * B + net_bytes}},
         "gpu_launches": kernels_per_step * args.steps,
         "launch_config": {"autotuned": tuned, "used": launch_cfg},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": k_e2e},
     }
+    if serve is not None:
+        res["serve"] = serve
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        n_evals = 64 * cores
+        n_evals = 256 * cores
         rate, dt = oracle_rate(grid, sets[0], n_evals, cores)
         res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{n_evals} evaluations of the first contingency states "
