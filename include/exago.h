@@ -116,8 +116,9 @@ exago_status exago_net_ineq_bounds(exago_net_t net, double *hlo, double *hhi);
  * slot_ptr ([nb+1]), slot_nbr ([2 nl] other bus of each slot; slots are ordered by (bus, other
  * bus, branch)), slot_ref ([2 nl] record 2 l + end of each slot), bus_jP / bus_jQ (J row starts of
  * P_i / Q_i), bus_hA / bus_hM (H row starts of Va_i / Vm_i), bus_k (neighbours + 1), bus_nlow
- * (neighbours below i), bus_perm (the bus phase's thread order: each aligned group of 64 buses
- * sorted by descending degree), gen_ptr ([nb+1]) and gen_ord ([ng]).  *needed receives the size in bytes;
+ * (neighbours below i), bus_perm ([3][nb], the bus phase's thread order for tiles of 64, 128 and
+ * 256 buses: each aligned tile sorted by descending degree), gen_ptr ([nb+1]) and gen_ord ([ng]).
+ * *needed receives the size in bytes;
  * dst may be NULL to query it.  EINVAL for an unknown name or a small buffer.
  */
 exago_status exago_net_plan_array(exago_net_t net, const char *name, void *dst, size_t bytes,
@@ -229,10 +230,12 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *             one fused launch whose CTAs claim branch and bus tiles of all states from a work
  *             list (the batched evaluation of SCOPFLOW / SOPFLOW subproblems, Sec. V-A, VI-A).
  *   block     persistent: threads per CTA and items per tile (64, 128, 256; 0 = 128).
- *   occupancy persistent: resident warps per SM the kernel's registers must allow (24 or 32;
+ *   occupancy persistent: resident warps per SM the kernel's registers must allow (16 or 24;
  *             0 = the compiler's choice).  Higher occupancy can cost register spills.
- *   stage_records  EXAGO_STAGE_ON: a bus tile first copies its branch-end records into shared
- *             memory with coalesced loads; DEFAULT / OFF: each bus reads them through L2.
+ *   stage_records  EXAGO_STAGE_ON: a bus tile runs slot-parallel -- one thread per branch end
+ *             reads its record (coalesced) and writes the neighbour's row entries, then one
+ *             thread per bus sums its ends' diagonal terms from shared memory; DEFAULT / OFF:
+ *             one thread per bus walks its ends, reading the records through L2.
  *             EXAGO_SCHED_PIPELINED: the batch in chunks; the branch kernel of a chunk runs on
  *             the caller's stream while the bus kernel of the previous chunk runs on a
  *             high-priority net stream, ordered by events only (no device-side waits).
@@ -273,9 +276,8 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg);
 
 /*
  * Autotuner: times the multi-kernel schedule, pipelined variants (three chunk sizes) and
- * persistent variants (block 128 / 256, occupancy 0 / 24 / 32 warps), each with and without
- * record staging,
- * on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
+ * persistent variants (block 64 / 128 / 256, occupancy 0 / 16 / 24 warps), each with and
+ * without slot-parallel bus tiles, on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
  * fastest for batches of this size (used by EXAGO_SCHED_AUTO).  Outputs are written as by
  * exago_eval_all.  *best (may be NULL) receives the choice.
  */

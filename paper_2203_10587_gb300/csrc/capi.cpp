@@ -44,6 +44,7 @@ struct exago_net {
     bool on_device = false;
     int device = -1;
     int sm_count = 0;
+    int smem_per_sm = 0;          // shared memory per SM (bytes)
     DevNet dev{};
     std::vector<void *> allocs;
     int *status_host = nullptr;   // host-mapped device status word
@@ -57,7 +58,7 @@ struct exago_net {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side_stream = nullptr;   // pipelined schedule: bus kernels
     cudaEvent_t pipe_ev[18] = {};
-    int occ[18] = {0};            // resident persistent CTAs per SM by (block, occupancy, staging)
+    std::map<uint64_t, int> occ;  // resident CTAs per SM by (schedule, block, occupancy, shared memory)
 };
 
 namespace {
@@ -118,6 +119,9 @@ exago_status do_upload(exago_net *net) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     e = cudaDeviceGetAttribute(&net->sm_count, cudaDevAttrMultiProcessorCount, net->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    e = cudaDeviceGetAttribute(&net->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                               net->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     d = DevNet{};
     d.nb = p.nb; d.nl = p.nl; d.ng = p.ng; d.n = p.n; d.m = p.m;
     d.nslot = p.nslot;
@@ -135,7 +139,7 @@ exago_status do_upload(exago_net *net) {
             const int i1 = i0 + T < p.nb ? i0 + T : p.nb;
             const int64_t r = 2 * (p.Jrowptr[i1] - p.Jrowptr[i0]) + (p.Hrowptr[i1] - p.Hrowptr[i0]) +
                               (p.Hrowptr[p.nb + i1] - p.Hrowptr[p.nb + i0]);
-            const int64_t a = r + (int64_t)NCOMP * (p.slot_ptr[i1] - p.slot_ptr[i0]);
+            const int64_t a = r + (int64_t)kDiagComps * (p.slot_ptr[i1] - p.slot_ptr[i0]);
             if (r > rows) rows = r;
             if (a > all) all = a;
         }
@@ -145,6 +149,7 @@ exago_status do_upload(exago_net *net) {
 #define UP(field, vec) if ((s = upload(net, p.vec, &d.field)) != EXAGO_OK) return s
     UP(f, f); UP(t, t);
     UP(slot_ptr, slot_ptr); UP(slot_nbr, slot_nbr); UP(slot_ref, slot_ref); UP(br_slot, br_slot);
+    UP(slot_bus, slot_bus); UP(slot_pos, slot_pos);
     UP(bus_jP, bus_jP); UP(bus_jQ, bus_jQ); UP(bus_hA, bus_hA); UP(bus_hM, bus_hM);
     UP(bus_k, bus_k); UP(bus_nlow, bus_nlow); UP(bus_perm, bus_perm);
     UP(Gs, Gs); UP(Bs, Bs); UP(Pd, Pd); UP(Qd, Qd);
@@ -218,23 +223,37 @@ exago_status plan_only(int nb, const double *Gs, const double *Bs, const double 
 // Launch settings of one call, resolved from the net's configuration and the batch size.
 struct Resolved {
     int schedule;          // EXAGO_SCHED_KERNELS or EXAGO_SCHED_PERSISTENT
-    int block, occ_warps, stage_recs, grid, lag, ring, use_graph, force_timeout;
+    int block, occ_warps, stage_recs, stage_cap, grid, lag, ring, use_graph, force_timeout;
     int chunk, pipe_ring;  // pipelined schedule
     long long spin_limit;
 };
 
 constexpr long long kDefaultSpinLimit = 1ll << 22;   // polls of ~0.4 us: about 1.7 s
 
-// Resident persistent CTAs per SM for (block, occupancy target, record staging), cached.
-int occupancy(exago_net *net, int block, int occ_warps, int stage_recs) {
-    const int t = stage_index(block);
-    const int idx = (t * 3 + (occ_warps == 24 ? 1 : occ_warps == 32 ? 2 : 0)) * 2 + (stage_recs ? 1 : 0);
-    int &occ = net->occ[idx];
-    if (occ == 0) {
-        const int cap = stage_recs ? net->dev.stage_cap_all[t] : net->dev.stage_cap_rows[t];
-        occ = persist_blocks_per_sm(block, occ_warps, (size_t)cap * sizeof(double));
-    }
-    return occ;
+// Resident CTAs per SM of the persistent kernel (persistent) or of the bus kernel (otherwise)
+// with `smem` bytes of dynamic shared memory, cached.
+int occupancy(exago_net *net, bool persistent, int block, int occ_warps, size_t smem) {
+    const uint64_t key = ((uint64_t)persistent << 62) | ((uint64_t)block << 48) |
+                         ((uint64_t)occ_warps << 40) | (uint64_t)smem;
+    auto it = net->occ.find(key);
+    if (it != net->occ.end()) return it->second;
+    const int o = persistent ? persist_blocks_per_sm(block, occ_warps, smem) : bus_blocks_per_sm(smem);
+    net->occ[key] = o;
+    return o;
+}
+
+// Shared-memory doubles of one bus tile.  Row segments always; with record staging also the
+// records, but only up to what keeps the register-limited number of resident CTAs per SM (a tile
+// whose records do not fit reads them through L2).
+int stage_cap(exago_net *net, bool persistent, int block, int occ_warps, bool stage_recs) {
+    const int t = stage_index(persistent ? block : 128);
+    const int rows = net->dev.stage_cap_rows[t];
+    if (!stage_recs) return rows;
+    const int by_regs = occupancy(net, persistent, block, occ_warps, 0);
+    const long budget = ((long)net->smem_per_sm / (by_regs > 0 ? by_regs : 1) - 4096) / 8;
+    int cap = net->dev.stage_cap_all[t];
+    if (cap > budget) cap = (int)(budget & ~1l);
+    return cap > rows ? cap : rows;
 }
 
 Resolved resolve(exago_net *net, int B) {
@@ -262,9 +281,12 @@ Resolved resolve(exago_net *net, int B) {
         r.pipe_ring = pr;
     }
     r.block = (c.block == 64 || c.block == 256) ? c.block : 128;
-    r.occ_warps = (c.occupancy == 24 || c.occupancy == 32) ? c.occupancy : 0;
+    r.occ_warps = (c.occupancy == 16 || c.occupancy == 24) ? c.occupancy : 0;
     r.stage_recs = c.stage_records == EXAGO_STAGE_ON;
-    r.grid = net->sm_count * occupancy(net, r.block, r.occ_warps, r.stage_recs);
+    const bool pers = r.schedule == EXAGO_SCHED_PERSISTENT;
+    r.stage_cap = stage_cap(net, pers, r.block, r.occ_warps, r.stage_recs);
+    r.grid = net->sm_count * occupancy(net, true, r.block, r.occ_warps,
+                                       pers ? (size_t)r.stage_cap * sizeof(double) : 0);
     const int Tbr = (net->plan.nl + r.block - 1) / r.block;
     // bus tiles trail by the states the resident CTAs can hold in branch work, plus margin
     int lag = c.lag > 0 ? c.lag : (Tbr > 0 ? (r.grid + Tbr - 1) / Tbr : 1) + 2;
@@ -397,7 +419,7 @@ std::vector<uint64_t> req_key(const EvalReq &R, int schedule) {
     return {(uint64_t)schedule, (uint64_t)R.x, (uint64_t)R.lam, (uint64_t)R.mask,
             (uint64_t)R.pd_scale, (uint64_t)R.obj_weight, (uint64_t)R.f, (uint64_t)R.grad,
             (uint64_t)R.gh, (uint64_t)R.jval, (uint64_t)R.hval, (uint64_t)R.scratch,
-            (uint64_t)R.B, bits(R.sigma), (uint64_t)R.stage_recs};
+            (uint64_t)R.B, bits(R.sigma), (uint64_t)R.stage_recs, (uint64_t)R.stage_cap};
 }
 
 // The side stream (highest priority, so bus blocks are dispatched as soon as branch blocks retire)
@@ -438,6 +460,7 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
     R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
     R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
     R.stage_recs = rs.stage_recs;
+    R.stage_cap = rs.stage_cap;
     cudaStream_t stream = (cudaStream_t)bt->stream;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t ce = cudaStreamIsCapturing(stream, &cap);
@@ -610,7 +633,7 @@ exago_status exago_net_plan_array(exago_net_t net, const char *name, void *dst, 
     size_t n = 0;
 #define ARR(key, vec) if (!std::strcmp(name, key)) { src = p.vec.data(); n = p.vec.size() * sizeof(p.vec[0]); }
     ARR("slot_ptr", slot_ptr) else ARR("slot_nbr", slot_nbr) else ARR("slot_ref", slot_ref)
-    else ARR("br_slot", br_slot)
+    else ARR("br_slot", br_slot) else ARR("slot_bus", slot_bus) else ARR("slot_pos", slot_pos)
     else ARR("bus_jP", bus_jP) else ARR("bus_jQ", bus_jQ) else ARR("bus_hA", bus_hA)
     else ARR("bus_hM", bus_hM) else ARR("bus_k", bus_k) else ARR("bus_nlow", bus_nlow)
     else ARR("bus_perm", bus_perm)
@@ -754,8 +777,8 @@ exago_status exago_net_set_config(exago_net_t net, const exago_config *cfg) {
         return fail(EXAGO_EINVAL, "pipelined ring must be at most 7 chunks");
     if (cfg->block != 0 && cfg->block != 64 && cfg->block != 128 && cfg->block != 256)
         return fail(EXAGO_EINVAL, "block must be 0, 64, 128 or 256");
-    if (cfg->occupancy != 0 && cfg->occupancy != 24 && cfg->occupancy != 32)
-        return fail(EXAGO_EINVAL, "occupancy must be 0, 24 or 32");
+    if (cfg->occupancy != 0 && cfg->occupancy != 16 && cfg->occupancy != 24)
+        return fail(EXAGO_EINVAL, "occupancy must be 0, 16 or 24");
     if (cfg->stage_records < EXAGO_STAGE_DEFAULT || cfg->stage_records > EXAGO_STAGE_OFF)
         return fail(EXAGO_EINVAL, "unknown stage_records value");
     if (cfg->lag < 0 || cfg->ring < 0 || cfg->spin_limit < 0)
@@ -817,8 +840,8 @@ exago_status exago_net_autotune(exago_net_t net, const exago_batch *bt, double *
                 c.chunk = base.chunk * mul / 2 > 0 ? base.chunk * mul / 2 : 1;
                 cands.push_back(c);
             }
-            for (int block : {128, 256})
-                for (int occw : {0, 24, 32}) {
+            for (int block : {64, 128, 256})
+                for (int occw : {0, 16, 24}) {
                     exago_config c{};
                     c.schedule = EXAGO_SCHED_PERSISTENT;
                     c.block = block;

@@ -172,7 +172,9 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
 
     const bool on = R.mask == nullptr || R.mask[(size_t)b * nl + l] != 0;
     if (!on) {   // out of service: every value of this branch is zero
-        for (double *r : {rf, rt}) {
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            double *r = e ? rt : rf;
             put2(r, SC_P, 0.0, 0.0);
             if (WJ) { put2(r, SC_PA, 0.0, 0.0); put2(r, SC_PV, 0.0, 0.0); put2(r, SC_QU, 0.0, 0.0); }
             if (WH) { put2(r, SC_HAA, 0.0, 0.0); put2(r, SC_HUU, 0.0, 0.0); }
@@ -289,29 +291,80 @@ __device__ __forceinline__ void add_group(Rec &o, const Rec &r) {
     if (WANT & W_H) { o.haa += r.haa; o.hua += r.hua; o.huv += r.huv; }
 }
 
-// One (state b, bus i) item.  Walks the bus's slots, which come in ascending order of the other
-// bus (parallel branches adjacent), reads each slot's branch-end record, and writes the bus's
-// rows:
-//   g:  P_i and Q_i balances (sums of the end injections, shunt, load and generators);
-//   J:  rows P_i and Q_i entirely -- Va columns, Vm columns (a neighbour's entry is its branch
-//       end's dP/dVa_v = -dP/dVa_u and dP/dVm_v; the diagonal is the sum over all ends plus the
-//       shunt term), then -1 for each generator;
-//   H:  lower-triangle rows Va_i and Vm_i entirely (neighbours below i, the diagonal sums and the
-//       shunt term), and the cost Hessian of the bus's generators.
-// Records come from the tile's shared-memory copy, or through L2 (ld.cg) when the tile does not
-// fit: in the persistent schedule other CTAs wrote them during the launch.
-// recs + (s - sbase) * NCOMP is slot s's record: the tile's shared-memory copy (SMEM) or state
-// b's scratch in global memory (sbase = 0).
-template <int WANT, bool SMEM>
-__device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int b, int i,
-                                         const double *recs, int sbase, const BusRows &W) {
+// The rest of one (state b, bus i) item once D holds the sums of the bus's branch-end records
+// (injections and the diagonal derivative and Hessian terms):
+//   g:  P_i and Q_i balances (end injections, shunt, load and generators);
+//   J:  the diagonal entries of rows P_i and Q_i (plus the shunt term) and -1 for each generator;
+//   H:  the diagonals of rows Va_i and Vm_i (plus the shunt term) and the cost Hessian of the
+//       bus's generators.
+template <int WANT>
+__device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int b, int i,
+                                         const Rec &D, const BusRows &W) {
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     const int nb = N.nb;
-    const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
     const double *xb = R.x + (size_t)b * N.n;
     const double Vm = __ldg(xb + nb + i);
     const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
+    const int k = __ldg(N.bus_k + i), nlow = __ldg(N.bus_nlow + i);
+    double *JP = W.JP, *JQ = W.JQ, *HA = W.HA, *HM = W.HM;
+    const double sP = D.P, sQ = D.Q, dPa = D.pa, dPu = D.pu, dQa = D.qa, dQu = D.qu;
+    const double dAA = D.haa, dUA = D.hua, dUU = D.huu;
+
+    if (WG && R.gh) {
+        const double sc = R.pd_scale ? __ldg(R.pd_scale + (size_t)b * nb + i) : 1.0;
+        const double VV = Vm * Vm;
+        double gP = sP + fma(Gs, VV, __ldg(N.Pd + i) * sc);
+        double gQ = sQ + fma(-Bs, VV, __ldg(N.Qd + i) * sc);
+        for (int q = g0; q < g1; q++) {
+            const int g = __ldg(N.gen_ord + q);
+            gP -= __ldg(xb + 2 * nb + g);
+            gQ -= __ldg(xb + 2 * nb + N.ng + g);
+        }
+        double *ghb = R.gh + (size_t)b * N.m;
+        ghb[i] = gP;
+        ghb[nb + i] = gQ;
+    }
+    if (WJ) {
+        const double tV = Vm + Vm;
+        JP[nlow] = dPa; JP[k + nlow] = fma(Gs, tV, dPu);
+        JQ[nlow] = dQa; JQ[k + nlow] = fma(-Bs, tV, dQu);
+        for (int q = 0; q < g1 - g0; q++) {
+            JP[2 * k + q] = -1.0;
+            JQ[2 * k + q] = -1.0;
+        }
+    }
+    if (WH) {
+        const double *lb = R.lam + (size_t)b * N.m;
+        const double lP = __ldg(lb + i), lQ = __ldg(lb + nb + i);
+        HA[nlow] = dAA;                                       // (Va_i, Va_i): last of row Va_i
+        HM[nlow] = dUA;                                       // (Vm_i, Va_i)
+        HM[k + nlow] = dUU + fma(lP, Gs + Gs, -(lQ * (Bs + Bs)));   // (Vm_i, Vm_i): last
+        if (g1 > g0) {
+            const double sw = R.sigma * (R.obj_weight ? R.obj_weight[b] : 1.0);
+            const double base2 = N.baseMVA * N.baseMVA;
+            double *Hb = R.hval + (size_t)b * N.nnzH + N.hpg;
+            for (int q = g0; q < g1; q++) {
+                const int g = __ldg(N.gen_ord + q);
+                Hb[g] = sw * (2.0 * __ldg(N.c2 + g) * base2);
+            }
+        }
+    }
+}
+
+// One (state b, bus i) item.  Walks the bus's slots, which come in ascending order of the other
+// bus (parallel branches adjacent), reads each slot's branch-end record, writes the bus's
+// off-diagonal row entries (a neighbour's J entry is its branch end's dP/dVa_v = -dP/dVa_u and
+// dP/dVm_v; its H entries the end's Hessian values), sums the diagonal terms and finishes with
+// bus_tail.  Records come from the tile's shared-memory copy, or through L2 (ld.cg): in the
+// persistent schedule other CTAs wrote them during the launch.  recs + (s - sbase) * NCOMP is slot
+// s's record: the tile's shared-memory copy (SMEM) or state b's scratch in global memory
+// (sbase = 0).
+template <int WANT, bool SMEM>
+__device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int b, int i,
+                                         const double *recs, int sbase, const BusRows &W) {
+    constexpr bool WJ = WANT & W_J, WH = WANT & W_H;
+    const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
     const int k = __ldg(N.bus_k + i), nlow = __ldg(N.bus_nlow + i);
     double *JP = W.JP, *JQ = W.JQ, *HA = W.HA, *HM = W.HM;
 
@@ -359,48 +412,7 @@ __device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int 
             add_diag<WANT>(D, o);
         }
     }
-    const double sP = D.P, sQ = D.Q, dPa = D.pa, dPu = D.pu, dQa = D.qa, dQu = D.qu;
-    const double dAA = D.haa, dUA = D.hua, dUU = D.huu;
-
-    if (WG && R.gh) {
-        const double sc = R.pd_scale ? __ldg(R.pd_scale + (size_t)b * nb + i) : 1.0;
-        const double VV = Vm * Vm;
-        double gP = sP + fma(Gs, VV, __ldg(N.Pd + i) * sc);
-        double gQ = sQ + fma(-Bs, VV, __ldg(N.Qd + i) * sc);
-        for (int q = g0; q < g1; q++) {
-            const int g = __ldg(N.gen_ord + q);
-            gP -= __ldg(xb + 2 * nb + g);
-            gQ -= __ldg(xb + 2 * nb + N.ng + g);
-        }
-        double *ghb = R.gh + (size_t)b * N.m;
-        ghb[i] = gP;
-        ghb[nb + i] = gQ;
-    }
-    if (WJ) {
-        const double tV = Vm + Vm;
-        JP[nlow] = dPa; JP[k + nlow] = fma(Gs, tV, dPu);
-        JQ[nlow] = dQa; JQ[k + nlow] = fma(-Bs, tV, dQu);
-        for (int q = 0; q < g1 - g0; q++) {
-            JP[2 * k + q] = -1.0;
-            JQ[2 * k + q] = -1.0;
-        }
-    }
-    if (WH) {
-        const double *lb = R.lam + (size_t)b * N.m;
-        const double lP = __ldg(lb + i), lQ = __ldg(lb + nb + i);
-        HA[nlow] = dAA;                                       // (Va_i, Va_i): last of row Va_i
-        HM[nlow] = dUA;                                       // (Vm_i, Va_i)
-        HM[k + nlow] = dUU + fma(lP, Gs + Gs, -(lQ * (Bs + Bs)));   // (Vm_i, Vm_i): last
-        if (g1 > g0) {
-            const double sw = R.sigma * (R.obj_weight ? R.obj_weight[b] : 1.0);
-            const double base2 = N.baseMVA * N.baseMVA;
-            double *Hb = R.hval + (size_t)b * N.nnzH + N.hpg;
-            for (int q = g0; q < g1; q++) {
-                const int g = __ldg(N.gen_ord + q);
-                Hb[g] = sw * (2.0 * __ldg(N.c2 + g) * base2);
-            }
-        }
-    }
+    bus_tail<WANT>(N, R, b, i, D, W);
 }
 
 // Start of bus i's row in one of the four row blocks, or the block's end for i = nb.
@@ -408,24 +420,109 @@ __device__ __forceinline__ int row_start(const int *starts, int i, int nb, int e
     return i < nb ? __ldg(starts + i) : end;
 }
 
-// The bus items of buses [i0, i0 + blockDim.x) of state b, by the whole block (i0 a multiple
-// of 64), with `stage` = cap doubles of shared memory.  The tile's slots are one contiguous range.
-// With R.stage_recs, and when the tile's records and row segments fit, the block first copies
-// the records in with coalesced 16-byte loads and every bus reads its slots there; otherwise each
-// bus reads its records through L2.  When the row segments fit (after the records, if staged),
-// every bus writes its rows there and the block copies the four contiguous segments out with
-// coalesced stores; otherwise the rows go straight to global memory.  Contains __syncthreads:
-// call from every thread.
+// The threads that share one bus tile: a whole block of 64, 128 or 256 threads.
+struct BlockGroup {
+    static __device__ __forceinline__ int rank() { return threadIdx.x; }
+    static __device__ __forceinline__ int size() { return blockDim.x; }
+    static __device__ __forceinline__ void sync() { __syncthreads(); }
+};
+
+// Where a bus tile's rows go: the start of the tile's segment in each of the four row blocks
+// (shared-memory staging or global memory) and the blocks' first positions p0, q0, a0, m0.
+struct TileRows {
+    double *P, *Q, *A, *M;
+    int p0, q0, a0, m0;
+    template <int WANT>
+    __device__ __forceinline__ BusRows of(const DevNet &N, int i) const {
+        BusRows W{};
+        if (WANT & W_J) {
+            W.JP = P + (__ldg(N.bus_jP + i) - p0);
+            W.JQ = Q + (__ldg(N.bus_jQ + i) - q0);
+        }
+        if (WANT & W_H) {
+            W.HA = A + (__ldg(N.bus_hA + i) - a0);
+            W.HM = M + (__ldg(N.bus_hM + i) - m0);
+        }
+        return W;
+    }
+};
+
+// Slot-parallel first phase of a bus tile, for slot s of bus i = slot_bus[s]: reads the slot's
+// record (consecutive slots are consecutive records, so a warp's loads are coalesced), keeps its
+// diagonal components in dg[0 .. kDiagComps) of shared memory, and -- if the slot leads its
+// neighbour group -- sums the group's later parallel branches in slot order and writes the
+// neighbour's row entries, exactly as bus_item does.
 template <int WANT>
+__device__ __forceinline__ void slot_item(const DevNet &N, int s, const double *scr, double *dg,
+                                          const TileRows &T) {
+    constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
+    Rec o = load_rec<WANT, false>(scr + (size_t)s * NCOMP);
+    if (WG) { dg[0] = o.P; dg[1] = o.Q; }
+    if (WJ) { dg[2] = o.pa; dg[3] = o.pu; dg[4] = o.qa; dg[5] = o.qu; }
+    if (WH) { dg[6] = o.haa; dg[7] = o.hua; dg[8] = o.huu; }
+    const int pos = __ldg(N.slot_pos + s);
+    if (!(WJ || WH) || pos < 0) return;
+    const int i = __ldg(N.slot_bus + s), j = __ldg(N.slot_nbr + s);
+    const int e = __ldg(N.slot_ptr + i + 1);
+    for (int q = s + 1; q < e && __ldg(N.slot_nbr + q) == j; q++)
+        add_group<WANT>(o, load_rec<WANT, false>(scr + (size_t)q * NCOMP));
+    const int k = __ldg(N.bus_k + i);
+    const BusRows W = T.template of<WANT>(N, i);
+    if (WJ) {
+        W.JP[pos] = dneg(o.pa); W.JP[k + pos] = o.pv;
+        W.JQ[pos] = dneg(o.qa); W.JQ[k + pos] = o.qv;
+    }
+    if (WH) {
+        W.HM[pos] = dneg(o.hua);                              // (Vm_i, Va_j)
+        if (j < i) {
+            W.HA[pos] = dneg(o.haa);                          // (Va_i, Va_j)
+            W.HM[k + pos] = o.huv;                            // (Vm_i, Vm_j)
+        }
+    }
+}
+
+// Second phase for bus i: the diagonal sums over its slots' components in slot order (the same
+// additions as bus_item), then bus_tail.
+template <int WANT>
+__device__ __forceinline__ void bus_sums(const DevNet &N, const EvalReq &R, int b, int i, int S0,
+                                         const double *dgs, const BusRows &W) {
+    constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
+    const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
+    Rec D{};
+    for (int s = s0; s < s1; s++) {
+        const double *d = dgs + (size_t)(s - S0) * kDiagComps;
+        Rec r{};
+        if (WG) { r.P = d[0]; r.Q = d[1]; }
+        if (WJ) { r.pa = d[2]; r.pu = d[3]; r.qa = d[4]; r.qu = d[5]; }
+        if (WH) { r.haa = d[6]; r.hua = d[7]; r.huu = d[8]; }
+        if (s == s0) D = r;
+        else add_diag<WANT>(D, r);
+    }
+    bus_tail<WANT>(N, R, b, i, D, W);
+}
+
+// The bus items of buses [i0, i0 + G::size()) of state b, by the whole group (i0 a multiple of
+// the group size), with `stage` = cap doubles of shared memory.  The tile's slots are one
+// contiguous range [S0, S1), and its rows are four contiguous segments.
+//   * With R.stage_recs, and when the slots' diagonal components and the row segments fit, the
+//     tile runs slot-parallel: every thread takes slots (slot_item), then every thread sums its
+//     bus's components from shared memory (bus_sums).
+//   * Otherwise every thread walks its own bus's slots, reading the records through L2
+//     (bus_item).
+// When the row segments fit (after the components, if used), every row entry is written to
+// shared memory and the group copies the four segments out with coalesced stores; otherwise
+// the rows go straight to global memory.  Contains G::sync(): call from every thread.
+template <int WANT, class G>
 __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int b, int i0,
                                          const double *scr, double *stage, int cap) {
     constexpr bool WJ = WANT & W_J, WH = WANT & W_H;
-    const int nb = N.nb;
-    int i1 = i0 + blockDim.x;
+    const int nb = N.nb, r = G::rank(), sz = G::size();
+    int i1 = i0 + sz;
     if (i1 > nb) i1 = nb;
-    // thread -> bus through the degree-sorted permutation (it maps every aligned 64-bus group,
-    // hence every tile, onto itself)
-    const int i = i0 + (int)threadIdx.x < i1 ? __ldg(N.bus_perm + i0 + threadIdx.x) : nb;
+    // thread -> bus through the tile size's degree-sorted permutation (it maps every tile onto
+    // itself)
+    const int *perm = N.bus_perm + (size_t)stage_index(sz) * nb;
+    const int i = i0 + r < i1 ? __ldg(perm + i0 + r) : nb;
     const int S0 = __ldg(N.slot_ptr + i0), S1 = __ldg(N.slot_ptr + i1);
     const int p0 = row_start(N.bus_jP, i0, nb, N.jP_end), p1 = row_start(N.bus_jP, i1, nb, N.jP_end);
     const int q0 = row_start(N.bus_jQ, i0, nb, N.jQ_end);
@@ -433,47 +530,39 @@ __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int 
     const int m0 = row_start(N.bus_hM, i0, nb, N.hM_end), m1 = row_start(N.bus_hM, i1, nb, N.hM_end);
     const int LP = WJ ? p1 - p0 : 0, LA = WH ? a1 - a0 : 0, LM = WH ? m1 - m0 : 0;
     const int LROWS = 2 * LP + LA + LM;
-    const bool recs_staged = R.stage_recs && NCOMP * (S1 - S0) + LROWS <= cap;
-    const int LR = recs_staged ? NCOMP * (S1 - S0) : 0;
-    const bool staged = (WJ || WH) && LR + LROWS <= cap;
+    const bool slotpar = R.stage_recs && kDiagComps * (S1 - S0) + LROWS <= cap;
+    const int LD = slotpar ? kDiagComps * (S1 - S0) : 0;
+    const bool staged = (WJ || WH) && LD + LROWS <= cap;
     double *Jb = WJ ? R.jval + (size_t)b * N.nnzJ : nullptr;
     double *Hb = WH ? R.hval + (size_t)b * N.nnzH : nullptr;
-    if (recs_staged) {
-        const double2 *src = reinterpret_cast<const double2 *>(scr + (size_t)S0 * NCOMP);
-        double2 *dst = reinterpret_cast<double2 *>(stage);
-        for (int e = threadIdx.x; e < LR / 2; e += blockDim.x) dst[e] = __ldcg(src + e);
-        __syncthreads();
+    double *rows = stage + LD;
+    TileRows T{};
+    T.p0 = p0; T.q0 = q0; T.a0 = a0; T.m0 = m0;
+    if (staged) {
+        T.P = rows; T.Q = rows + LP; T.A = rows + 2 * LP; T.M = rows + 2 * LP + LA;
+    } else {
+        if (WJ) { T.P = Jb + p0; T.Q = Jb + q0; }
+        if (WH) { T.A = Hb + a0; T.M = Hb + m0; }
     }
-    double *rows = stage + LR;
-    if (i < i1) {
-        BusRows W{};
-        if (staged) {
-            if (WJ) {
-                W.JP = rows + (__ldg(N.bus_jP + i) - p0);
-                W.JQ = rows + LP + (__ldg(N.bus_jQ + i) - q0);
-            }
-            if (WH) {
-                W.HA = rows + 2 * LP + (__ldg(N.bus_hA + i) - a0);
-                W.HM = rows + 2 * LP + LA + (__ldg(N.bus_hM + i) - m0);
-            }
-        } else {
-            if (WJ) { W.JP = Jb + __ldg(N.bus_jP + i); W.JQ = Jb + __ldg(N.bus_jQ + i); }
-            if (WH) { W.HA = Hb + __ldg(N.bus_hA + i); W.HM = Hb + __ldg(N.bus_hM + i); }
-        }
-        if (recs_staged) bus_item<WANT, true>(N, R, b, i, stage, S0, W);
-        else bus_item<WANT, false>(N, R, b, i, scr, 0, W);
+    if (slotpar) {
+        for (int s = S0 + r; s < S1; s += sz)
+            slot_item<WANT>(N, s, scr, stage + (size_t)(s - S0) * kDiagComps, T);
+        G::sync();
+        if (i < i1) bus_sums<WANT>(N, R, b, i, S0, stage, T.template of<WANT>(N, i));
+    } else if (i < i1) {
+        bus_item<WANT, false>(N, R, b, i, scr, 0, T.template of<WANT>(N, i));
     }
     if (staged) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < LP; e += blockDim.x) {
+        G::sync();
+        for (int e = r; e < LP; e += sz) {
             Jb[p0 + e] = rows[e];
             Jb[q0 + e] = rows[LP + e];
         }
-        for (int e = threadIdx.x; e < LA; e += blockDim.x) Hb[a0 + e] = rows[2 * LP + e];
-        for (int e = threadIdx.x; e < LM; e += blockDim.x) Hb[m0 + e] = rows[2 * LP + LA + e];
-        __syncthreads();
-    } else if (recs_staged) {
-        __syncthreads();   // the next tile may overwrite the records
+        for (int e = r; e < LA; e += sz) Hb[a0 + e] = rows[2 * LP + e];
+        for (int e = r; e < LM; e += sz) Hb[m0 + e] = rows[2 * LP + LA + e];
+        G::sync();
+    } else if (slotpar) {
+        G::sync();   // the next tile may overwrite the components
     }
 }
 

@@ -53,13 +53,17 @@ struct HostPlan {
     std::vector<int> slot_nbr;    // [nslot] the other bus of the slot's branch
     std::vector<int> slot_ref;    // [nslot] 2 l + end of the slot (adjoint records by branch)
     std::vector<int> br_slot;     // [2][nl] slot of the from end and of the to end
+    std::vector<int> slot_bus;    // [nslot] the bus of the slot
+    std::vector<int> slot_pos;    // [nslot] column of the neighbour among the bus's row columns,
+                                  // or -1 for a later branch of a parallel group
 
     // Row starts of bus i: J rows P_i and Q_i, H rows Va_i and Vm_i; k_i = neighbours + 1 (Va
     // columns of a J row, Vm columns follow); nlow_i = neighbours below i (position of the
     // diagonal among the Va columns).
     std::vector<int> bus_jP, bus_jQ, bus_hA, bus_hM, bus_k, bus_nlow;
-    // bus_perm: within every aligned group of 64 buses, the buses by descending degree (then id),
-    // so that a warp of the bus phase walks slot lists of similar length
+    // bus_perm: [3][nb]; row t holds, within every aligned tile of 64 << t buses, the tile's buses
+    // by descending degree (then id), so that a warp of the bus phase walks slot lists of similar
+    // length
     std::vector<int> bus_perm;
     std::vector<int> gen_ptr;     // [nb + 1] generators of bus i: gen_ord[gen_ptr[i] .. )
     std::vector<int> gen_ord;     // [ng] generator ids sorted by (bus, id)
@@ -75,7 +79,7 @@ struct DevNet {
     double baseMVA;
     const int *f, *t;
     const double *Gff, *Bff, *Gtt, *Btt, *Gft, *Bft;   // pi-model admittances (no phase shift: ft == tf)
-    const int *slot_ptr, *slot_nbr, *slot_ref, *br_slot;
+    const int *slot_ptr, *slot_nbr, *slot_ref, *br_slot, *slot_bus, *slot_pos;
     const int *bus_jP, *bus_jQ, *bus_hA, *bus_hM, *bus_k, *bus_nlow, *bus_perm;
     const double *Gs, *Bs, *Pd, *Qd;
     const int *gen_ptr, *gen_ord;
@@ -94,7 +98,8 @@ struct EvalReq {
     double *scratch;            // [B][nslot][NCOMP] branch-end records (or ring slots)
     int scr_b0;                 // state b's records are at scratch + (b - scr_b0) * nslot * NCOMP
                                 // in the multi-kernel and pipelined schedules
-    int stage_recs;             // bus tiles copy their records to shared memory first
+    int stage_recs;             // bus tiles read their records slot-parallel into shared memory
+    int stage_cap;              // shared-memory doubles of one bus tile (records and rows)
 };
 
 // Pipelined schedule (kernels.cu): the batch in chunks; the branch kernel of a chunk runs on the
@@ -151,7 +156,7 @@ int launch_eval_pipelined(const DevNet &net, const EvalReq &req, const PipeLaunc
 // req.scratch holds `ring` state slots.
 struct PersistLaunch {
     int block;              // 64, 128 or 256 threads
-    int occ_warps;          // 0, 24 or 32: resident warps per SM the registers must allow
+    int occ_warps;          // 0, 16 or 24: resident warps per SM the registers must allow
     int grid;               // CTAs (SM count x resident CTAs per SM)
     int lag, ring;          // bus tiles trail branch tiles by `lag` states; ring > lag slots
     long long spin_limit;   // polls before a bounded wait gives up
@@ -166,9 +171,11 @@ int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes);
 // largest tile's need in doubles, capped at kStageMaxDoubles; a tile above the cap reads its
 // records from global memory and writes its rows directly.
 constexpr int kStageMaxDoubles = 9216;   // 72 KB
-inline int stage_index(int block) { return block == 64 ? 0 : block == 256 ? 2 : 1; }
+constexpr int kDiagComps = 9;            // record components summed into a bus's diagonal
+__host__ __device__ inline int stage_index(int block) { return block == 64 ? 0 : block == 256 ? 2 : 1; }
 int persist_allow_stage();   // persist.cu
 int bus_allow_stage();       // kernels.cu
+int bus_blocks_per_sm(size_t smem_bytes);   // k_bus blocks of 128 threads per SM (kernels.cu)
 
 // Read-only view of a net's plan and device tables (false for NULL or a plan-only net), and the
 // thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.

@@ -65,8 +65,8 @@ template <int WANT>
 __global__ void __launch_bounds__(128) k_bus(const DevNet N, const EvalReq R, int b0) {
     extern __shared__ double stage[];
     const int b = b0 + blockIdx.y;
-    bus_tile<WANT>(N, R, b, blockIdx.x * blockDim.x, R.scratch + (size_t)(b - R.scr_b0) * N.nslot * NCOMP,
-                   stage, R.stage_recs ? N.stage_cap_all[1] : N.stage_cap_rows[1]);
+    bus_tile<WANT, BlockGroup>(N, R, b, blockIdx.x * blockDim.x,
+                               R.scratch + (size_t)(b - R.scr_b0) * N.nslot * NCOMP, stage, R.stage_cap);
 }
 
 // Gradient of the objective: w (2 c2 base^2 Pg + c1 base) on Pg entries, 0 elsewhere.
@@ -91,7 +91,7 @@ static void launch_branch_bus(const DevNet &N, const EvalReq &R, int b0, int nB,
         k_branch<WANT><<<dim3((N.nl + 127) / 128, nB), 128, 0, st>>>(N, R, b0);
     }
     mark(hk, st, "bus");
-    const size_t smem = (size_t)(R.stage_recs ? N.stage_cap_all[1] : N.stage_cap_rows[1]) * sizeof(double);
+    const size_t smem = (size_t)R.stage_cap * sizeof(double);
     k_bus<WANT><<<dim3((N.nb + 127) / 128, nB), 128, smem, st>>>(N, R, b0);
 }
 
@@ -107,6 +107,13 @@ int bus_allow_stage() {
     set((const void *)k_bus<W_H>); set((const void *)k_bus<W_G | W_H>);
     set((const void *)k_bus<W_J | W_H>); set((const void *)k_bus<W_G | W_J | W_H>);
     return (int)e;
+}
+
+int bus_blocks_per_sm(size_t smem_bytes) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bus<W_G | W_J | W_H>,
+                                                                  128, smem_bytes);
+    return e == cudaSuccess && per_sm > 0 ? per_sm : 1;
 }
 
 int launch_eval(const DevNet &N, const EvalReq &R, void *stream, ProfileHook *hk) {
@@ -151,7 +158,7 @@ static void pipe_chunk(const DevNet &N, const EvalReq &Rk, int b0, int nB, cudaS
     if (N.nl > 0) k_branch<WANT><<<dim3((N.nl + 127) / 128, nB), 128, 0, main>>>(N, Rk, b0);
     cudaEventRecord(ev_br, main);
     cudaStreamWaitEvent(side, ev_br, 0);
-    const size_t smem = (size_t)(Rk.stage_recs ? N.stage_cap_all[1] : N.stage_cap_rows[1]) * sizeof(double);
+    const size_t smem = (size_t)Rk.stage_cap * sizeof(double);
     if constexpr (WANT != 0) k_bus<WANT><<<dim3((N.nb + 127) / 128, nB), 128, smem, side>>>(N, Rk, b0);
     if (Rk.grad) k_grad<<<dim3((N.n + 255) / 256, nB), 256, 0, side>>>(N, Rk, b0);
     cudaEventRecord(ev_bu, side);

@@ -86,8 +86,7 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
     extern __shared__ double stage[];
     int *done_br = P.ctr + 1, *done_bu = P.ctr + 1 + P.B;
     const size_t slot_doubles = (size_t)NCOMP * N.nslot;
-    const int cap = R.stage_recs ? N.stage_cap_all[NT == 64 ? 0 : NT == 256 ? 2 : 1]
-                                 : N.stage_cap_rows[NT == 64 ? 0 : NT == 256 ? 2 : 1];
+    const int cap = R.stage_cap;
     // Thread 0 claims the next ticket while the block works on the current one.  The smallest
     // unfinished ticket is always some block's current item (a block's prefetched ticket is
     // larger than its current one), so the argument above still holds.
@@ -122,7 +121,7 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
             __syncthreads();
             if (s_ok) {
                 const int i = tile * NT + threadIdx.x;
-                if (WANT) bus_tile<WANT>(N, R, b, tile * NT, scr, stage, cap);
+                if (WANT) bus_tile<WANT, BlockGroup>(N, R, b, tile * NT, scr, stage, cap);
                 if (i < N.nb && R.grad) grad_bus(N, R, b, i);
                 if (tile == 0 && R.f) obj_block(N, R, b, s_part);
             }
@@ -159,7 +158,7 @@ static int allow_stage_nt() {
     set((const void *)k_persist<W_H, NT, 1>); set((const void *)k_persist<W_G | W_H, NT, 1>);
     set((const void *)k_persist<W_J | W_H, NT, 1>); set((const void *)k_persist<ALL, NT, 1>);
     set((const void *)k_persist<ALL, NT, minb(NT, 24)>);
-    set((const void *)k_persist<ALL, NT, minb(NT, 32)>);
+    set((const void *)k_persist<ALL, NT, minb(NT, 16)>);
     return (int)e;
 }
 
@@ -175,11 +174,10 @@ template <int NT>
 static int launch_persist_nt(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
                              int occ_warps, cudaStream_t st) {
     const int want = (R.gh ? W_G : 0) | (R.jval ? W_J : 0) | (R.hval ? W_H : 0);
-    const int ti = NT == 64 ? 0 : NT == 256 ? 2 : 1;
-    const size_t smem = (size_t)(R.stage_recs ? N.stage_cap_all[ti] : N.stage_cap_rows[ti]) * sizeof(double);
+    const size_t smem = (size_t)R.stage_cap * sizeof(double);
     constexpr int ALL = W_G | W_J | W_H;
     if (want == ALL && occ_warps == 24) launch_one<ALL, NT, minb(NT, 24)>(N, R, P, grid, smem, st);
-    else if (want == ALL && occ_warps == 32) launch_one<ALL, NT, minb(NT, 32)>(N, R, P, grid, smem, st);
+    else if (want == ALL && occ_warps == 16) launch_one<ALL, NT, minb(NT, 16)>(N, R, P, grid, smem, st);
     else switch (want) {
         case 0: launch_one<0, NT, 1>(N, R, P, grid, smem, st); break;
         case W_G: launch_one<W_G, NT, 1>(N, R, P, grid, smem, st); break;
@@ -204,7 +202,7 @@ static int occupancy_of(size_t smem) {
 template <int NT>
 static int occupancy_nt(int occ_warps, size_t smem) {
     if (occ_warps == 24) return occupancy_of<NT, minb(NT, 24)>(smem);
-    if (occ_warps == 32) return occupancy_of<NT, minb(NT, 32)>(smem);
+    if (occ_warps == 16) return occupancy_of<NT, minb(NT, 16)>(smem);
     return occupancy_of<NT, 1>(smem);
 }
 

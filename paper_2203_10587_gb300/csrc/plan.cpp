@@ -201,16 +201,21 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
         p.bus_nlow[i] = rank(i, i);
     }
 
-    // ---- degree-sorted bus order inside aligned 64-bus groups
-    // (degree = branch ends at the bus, the trip count of its slot loop)
+    // ---- degree-sorted bus order inside every aligned bus tile of 64, 128 and 256 buses
+    // (degree = branch ends at the bus, the trip count of its slot loop), so that each warp of a
+    // tile holds buses of similar degree
     std::vector<int> ends_at(nb, 0);
     for (int l = 0; l < nl; l++) { ends_at[p.f[l]]++; ends_at[p.t[l]]++; }
-    p.bus_perm.resize(nb);
-    for (int i = 0; i < nb; i++) p.bus_perm[i] = i;
-    for (int g0 = 0; g0 < nb; g0 += 64) {
-        const int g1 = g0 + 64 < nb ? g0 + 64 : nb;
-        std::stable_sort(p.bus_perm.begin() + g0, p.bus_perm.begin() + g1,
-                         [&](int a, int c) { return ends_at[a] > ends_at[c]; });
+    p.bus_perm.resize(3 * (size_t)nb);
+    for (int t = 0; t < 3; t++) {
+        const int T = 64 << t;
+        auto perm = p.bus_perm.begin() + (size_t)t * nb;
+        for (int i = 0; i < nb; i++) perm[i] = i;
+        for (int g0 = 0; g0 < nb; g0 += T) {
+            const int g1 = g0 + T < nb ? g0 + T : nb;
+            std::stable_sort(perm + g0, perm + g1,
+                             [&](int a, int c) { return ends_at[a] > ends_at[c]; });
+        }
     }
 
     // ---- slots: (bus, other bus, branch); each bus's slots walk its row columns in order
@@ -235,6 +240,20 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
             p.slot_ref[s2] = e.second;   // 2 l + end
             p.br_slot[(size_t)(e.second & 1) * nl + (e.second >> 1)] = s2;
             s2++;
+        }
+    }
+    // slot -> bus, and the column of the slot's neighbour among the bus's row columns (the
+    // diagonal sits after the nlow lower neighbours); -1 for a later branch of a parallel group,
+    // whose values the group's first slot sums
+    p.slot_bus.assign(p.nslot, 0);
+    p.slot_pos.assign(p.nslot, -1);
+    for (int i = 0; i < nb; i++) {
+        int pos = 0;
+        for (int s = p.slot_ptr[i]; s < p.slot_ptr[i + 1]; s++) {
+            p.slot_bus[s] = i;
+            if (s > p.slot_ptr[i] && p.slot_nbr[s] == p.slot_nbr[s - 1]) continue;
+            if (pos == p.bus_nlow[i]) pos++;
+            p.slot_pos[s] = pos++;
         }
     }
     return EXAGO_OK;

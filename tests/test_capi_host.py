@@ -62,9 +62,11 @@ def test_patterns_match_oracle(L, oracle_mod, name):
     assert net.nnzH == 3 * g.nb + 4 * g.nl + g.ng
 
 
-def write_plan(net, g):
+def write_plan(net, g, slot_parallel=False):
     """Replays the kernels' writes from the plan: returns, for every J and H position, how often
-    it is written and which column the writing thread believes it holds."""
+    it is written and which column the writing thread believes it holds.  slot_parallel replays
+    the slot-parallel bus tiles, where a group's leading slot writes its neighbour's entries at
+    slot_pos."""
     A = lambda n: exago.exago_net_plan_array(net.h, n)
     nl, nb = g.nl, g.nb
     jr, jc = exago.exago_net_jac_pattern(net.h)
@@ -105,20 +107,31 @@ def write_plan(net, g):
     jP, jQ, hA, hM = A("bus_jP"), A("bus_jQ"), A("bus_hA"), A("bus_hM")
     bk, nlow, gptr, gord = A("bus_k"), A("bus_nlow"), A("gen_ptr"), A("gen_ord")
     hpg = hr[2 * nb]
+    slot_bus, slot_pos = A("slot_bus"), A("slot_pos")
     for i in range(nb):
         nbrs = slot_nbr[slot_ptr[i]:slot_ptr[i + 1]]
         assert np.all(np.diff(nbrs) >= 0)
+        assert np.all(slot_bus[slot_ptr[i]:slot_ptr[i + 1]] == i)
         pos, k = 0, bk[i]
-        for j in np.unique(nbrs):
-            if pos == nlow[i]:
+        if slot_parallel:
+            lead = [(int(slot_pos[sl]), int(slot_nbr[sl])) for sl in range(slot_ptr[i], slot_ptr[i + 1])
+                    if slot_pos[sl] >= 0]
+            for sl in range(slot_ptr[i], slot_ptr[i + 1]):   # -1 only for later parallel branches
+                assert (slot_pos[sl] < 0) == (sl > slot_ptr[i] and slot_nbr[sl] == slot_nbr[sl - 1])
+        else:
+            lead = []
+            for j in np.unique(nbrs):
+                if pos == nlow[i]:
+                    pos += 1
+                lead.append((pos, int(j)))
                 pos += 1
+        for pos, j in lead:
             for base, off, col in ((jP[i], 0, j), (jP[i], k, nb + j), (jQ[i], 0, j), (jQ[i], k, nb + j)):
                 wj(base + off + pos, col)
             wh(hM[i] + pos, j)
             if j < i:
                 wh(hA[i] + pos, j)
                 wh(hM[i] + k + pos, nb + j)
-            pos += 1
         for base, off, col in ((jP[i], 0, i), (jP[i], k, nb + i), (jQ[i], 0, i), (jQ[i], k, nb + i)):
             wj(base + off + nlow[i], col)
         wh(hA[i] + nlow[i], i)
@@ -133,16 +146,19 @@ def write_plan(net, g):
 
 
 def check_write_plan(net, g):
-    perm = exago.exago_net_plan_array(net.h, "bus_perm")
+    perms = exago.exago_net_plan_array(net.h, "bus_perm").reshape(3, g.nb)
     deg = np.bincount(np.concatenate([g.f, g.t]), minlength=g.nb)
-    for g0 in range(0, g.nb, 64):   # a permutation of each aligned 64-bus group, by degree
-        grp = perm[g0:g0 + 64]
-        assert sorted(grp) == list(range(g0, min(g0 + 64, g.nb)))
-        assert np.all(np.diff(deg[grp]) <= 0)
-    cj, ch, colj, colh, jc, hc = write_plan(net, g)
-    assert np.all(cj == 1) and np.all(ch == 1)
-    np.testing.assert_array_equal(colj, jc)
-    np.testing.assert_array_equal(colh, hc)
+    for t, perm in enumerate(perms):   # per tile size: each aligned tile permuted, by degree
+        T = 64 << t
+        for g0 in range(0, g.nb, T):
+            grp = perm[g0:g0 + T]
+            assert sorted(grp) == list(range(g0, min(g0 + T, g.nb)))
+            assert np.all(np.diff(deg[grp]) <= 0)
+    for sp in (False, True):
+        cj, ch, colj, colh, jc, hc = write_plan(net, g, slot_parallel=sp)
+        assert np.all(cj == 1) and np.all(ch == 1)
+        np.testing.assert_array_equal(colj, jc)
+        np.testing.assert_array_equal(colh, hc)
 
 
 @pytest.mark.parametrize("name", sorted(GRIDS))

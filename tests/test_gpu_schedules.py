@@ -27,8 +27,9 @@ CONFIGS = [
     dict(schedule=2, use_graph=2),                      # persistent, direct launch
     dict(schedule=2, block=64, lag=1, ring=2),          # tightest ring: every state reuses a slot
     dict(schedule=2, block=256, lag=3, ring=5),
-    dict(schedule=2, occupancy=32),                     # register-capped variant
-    dict(schedule=2, block=256, occupancy=24),
+    dict(schedule=2, occupancy=24),                     # register-capped variant
+    dict(schedule=2, block=64, occupancy=16),
+    dict(schedule=2, block=256, occupancy=16, stage_records=1),
     dict(schedule=3),                                   # pipelined, derived chunk, graph
     dict(schedule=3, chunk=7, ring=2, stage_records=1), # ring reuse from the third chunk on
     dict(schedule=3, chunk=5, use_graph=2),             # direct launches
