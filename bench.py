@@ -35,9 +35,8 @@ B_DEFAULT = 512
 N_INPUT_SETS = 4
 # FP64 work per unit with every output requested, counted from the kernel source on the fast
 # sincos path (an FMA counts 2 flops): (flops, instructions).  Per 2000-bus state they sum to
-# 593,400 flops / 419,900 instructions; ncu's executed FP64 thread-instruction counters of the
-# persistent kernel give 596,300 / 422,900.
-FP64_PER_BRANCH = (190, 130)   # sincos, flows, 16 derivatives, h and its J row, Hessian fold
+# 563,700 flops / 390,200 instructions.
+FP64_PER_BRANCH = (179, 119)   # sincos, flows, 16 derivatives, h and its J row, Hessian fold
 FP64_PER_SLOT = (9, 9)         # a branch end's record summed into its bus (all but the first)
 FP64_PER_BUS = (20, 15)        # shunt, load and diagonal terms of one bus
 FP64_PER_GEN = (19, 16)        # balance, cost Hessian, gradient and objective terms of a generator

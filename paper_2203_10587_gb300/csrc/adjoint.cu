@@ -36,13 +36,16 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
     const double G = __ldg(N.Gft + l), Bm = __ldg(N.Bft + l);
     const double Gff = __ldg(N.Gff + l), Bff = __ldg(N.Bff + l);
     const double Gtt = __ldg(N.Gtt + l), Btt = __ldg(N.Btt + l);
+    const double Gff2 = __ldg(N.Gff2 + l), Bff2 = __ldg(N.Bff2 + l);
+    const double Gtt2 = __ldg(N.Gtt2 + l), Btt2 = __ldg(N.Btt2 + l);
     double s, c;
     branch_sincos(Vaf - Vat, &s, &c);
     const double Bc = Bm * c, Bs = Bm * s;
     const double Af = fma(G, c, Bs), Cf = fma(G, s, -Bc);
     const double At = fma(G, c, -Bs), Ct = -fma(G, s, Bc);
-    const End ef = end_terms<true>(Gff, Bff, Af, Cf, Vf, Vt);
-    const End et = end_terms<true>(Gtt, Btt, At, Ct, Vt, Vf);
+    const double VV = Vf * Vt, Vf2 = Vf * Vf, Vt2 = Vt * Vt;
+    const End ef = end_terms<true>(Gff, Bff, Gff2, Bff2, Af, Cf, Vf, Vt, Vf2, VV);
+    const End et = end_terms<true>(Gtt, Btt, Gtt2, Btt2, At, Ct, Vt, Vf, Vt2, VV);
 
     if (MODE == ADJ_JVP) {
         const double *ub = A.v + (size_t)b * N.n;
@@ -78,10 +81,9 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
         const double lQf = __ldg(lb + nb + fb), lQt = __ldg(lb + nb + tb);
         const double muf = __ldg(lb + 2 * nb + l), mut = __ldg(lb + 2 * nb + nl + l);
         const double K = fma(G, G, Bm * Bm);
-        const double VV = Vf * Vt, VV2 = VV * VV;
-        const EndHess hf = end_hess(ef, Gff, Bff, Af, Cf, K, Vf, Vt, VV, VV2, lPf, lQf, muf);
-        const EndHess ht = end_hess(et, Gtt, Btt, At, Ct, K, Vt, Vf, VV, VV2, lPt, lQt, mut);
-        const BranchHess h = branch_hess(hf, ht, Vf, Vt);
+        const EndHess hf = end_hess(ef, Gff2, Bff2, Af, Cf, K, Vf, Vt, VV, lPf, lQf, muf);
+        const EndHess ht = end_hess(et, Gtt2, Btt2, At, Ct, K, Vt, Vf, VV, lPt, lQt, mut);
+        const BranchHess h = branch_hess(hf, ht, Vf, Vt, Vf2, Vt2, VV);
         const double haa = h.haa, xf = h.xf, xt = h.xt, mff = h.mff, mtt = h.mtt, mft = h.mft;
         const double *ub = A.v + (size_t)b * N.n;
         const double dA = __ldg(ub + fb) - __ldg(ub + tb);

@@ -162,14 +162,15 @@ exago_status do_upload(exago_net *net) {
     if ((s = upload(net, p.x, &x)) != EXAGO_OK) return s;
     if ((s = upload(net, p.b, &b)) != EXAGO_OK) return s;
     if ((s = upload(net, p.tap, &tap)) != EXAGO_OK) return s;
-    double *Y[6];
-    for (int k = 0; k < 6; k++)
+    double *Y[10];
+    for (int k = 0; k < 10; k++)
         if ((s = alloc_dev(net, (size_t)p.nl * sizeof(double), &Y[k])) != EXAGO_OK) return s;
     d.Gff = Y[0]; d.Bff = Y[1]; d.Gtt = Y[2]; d.Btt = Y[3]; d.Gft = Y[4]; d.Bft = Y[5];
+    d.Gff2 = Y[6]; d.Bff2 = Y[7]; d.Gtt2 = Y[8]; d.Btt2 = Y[9];
     cudaStream_t st;
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamCreate");
-    int le = launch_admittance(r, x, b, tap, p.nl, Y[0], Y[1], Y[2], Y[3], Y[4], Y[5], st);
+    int le = launch_admittance(r, x, b, tap, p.nl, Y, st);
     e = cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     if (le != 0) return cuda_fail((cudaError_t)le, "admittance kernel launch");
@@ -242,18 +243,16 @@ int occupancy(exago_net *net, bool persistent, int block, int occ_warps, size_t 
     return o;
 }
 
-// Shared-memory doubles of one bus tile.  Row segments always; with record staging also the
-// records, but only up to what keeps the register-limited number of resident CTAs per SM (a tile
-// whose records do not fit reads them through L2).
+// Shared-memory doubles of one bus tile: its row segments (and, slot-parallel, its slots'
+// diagonal components), but no more than keeps the register-limited number of resident CTAs per
+// SM.  A tile that does not fit writes its rows straight to global memory (and walks its slots
+// per bus).
 int stage_cap(exago_net *net, bool persistent, int block, int occ_warps, bool stage_recs) {
     const int t = stage_index(persistent ? block : 128);
-    const int rows = net->dev.stage_cap_rows[t];
-    if (!stage_recs) return rows;
     const int by_regs = occupancy(net, persistent, block, occ_warps, 0);
     const long budget = ((long)net->smem_per_sm / (by_regs > 0 ? by_regs : 1) - 4096) / 8;
-    int cap = net->dev.stage_cap_all[t];
-    if (cap > budget) cap = (int)(budget & ~1l);
-    return cap > rows ? cap : rows;
+    const int want = stage_recs ? net->dev.stage_cap_all[t] : net->dev.stage_cap_rows[t];
+    return want > budget ? (int)(budget & ~1l) : want;
 }
 
 Resolved resolve(exago_net *net, int B) {

@@ -13,32 +13,30 @@ enum : int { W_G = 1, W_J = 2, W_H = 4 };
 
 // ---------------------------------------------------------------------------------------------
 // sin and cos of the branch angle.  For |th| <= pi/4 -- every branch of a grid in normal
-// operation -- their Taylor series are summed by Horner's rule in z = th^2, truncated after th^15
-// (sin) and th^16 (cos): on that interval the first omitted terms are below 5e-17 and 2e-18, under
-// half an ulp of the results.  That is 17 FP64 instructions, against about 28 for the library
-// sincos (measured throughput), which is kept for larger angles.  The interval test compares the
-// bit pattern of |th| with that of pi/4 on the integer pipe.
+// operation -- minimax polynomials in z = th^2 (Remez exchange; the coefficients are written by
+// paper_2203_10587_gb300/sincos_minimax.py, which states their derivation):
+//   sin th = th + th^3 p(z),  cos th = 1 + z q(z),  p and q of degree 5,
+// evaluated by Horner's rule with fused multiply-adds: 14 FP64 instructions for the pair, against
+// about 28 for the library sincos, which is kept for larger angles.  Evaluated in this order the
+// results are within 0.61 ulp (sin) and 1.17 ulp (cos) of the exact values (checked on the CPU
+// with single-rounding fma).  The interval test compares the bit pattern of |th| with that of
+// pi/4 on the integer pipe.
 __device__ __forceinline__ void branch_sincos(double th, double *s, double *c) {
     const unsigned long long PI4_BITS = 0x3FE921FB54442D18ull;   // pi/4 rounded to double
     if ((__double_as_longlong(th) & 0x7FFFFFFFFFFFFFFFull) <= PI4_BITS) {
+        // SINCOS_COEFFS_BEGIN
+        constexpr double p0 = -0x1.5555555555549p-3, p1 = 0x1.111111110f881p-7,
+                         p2 = -0x1.a01a019c126c0p-13, p3 = 0x1.71de357875383p-19,
+                         p4 = -0x1.ae5e66d592248p-26, p5 = 0x1.5d932f7c7cd31p-33;
+        constexpr double q0 = -0x1.fffffffffff96p-2, q1 = 0x1.555555554f0abp-5,
+                         q2 = -0x1.6c16c1640aabdp-10, q3 = 0x1.a019f81cb610fp-16,
+                         q4 = -0x1.27df46099bb75p-22, q5 = 0x1.1b8b993bdb8c1p-29;
+        // SINCOS_COEFFS_END
         const double z = th * th;
-        double p = -1.0 / 1307674368000.0;                  // -1/15!
-        p = fma(p, z, 1.0 / 6227020800.0);                  //  1/13!
-        p = fma(p, z, -1.0 / 39916800.0);                   // -1/11!
-        p = fma(p, z, 1.0 / 362880.0);                      //  1/9!
-        p = fma(p, z, -1.0 / 5040.0);                       // -1/7!
-        p = fma(p, z, 1.0 / 120.0);                         //  1/5!
-        p = fma(p, z, -1.0 / 6.0);                          // -1/3!
-        *s = fma(th * z, p, th);
-        double q = 1.0 / 20922789888000.0;                  //  1/16!
-        q = fma(q, z, -1.0 / 87178291200.0);                // -1/14!
-        q = fma(q, z, 1.0 / 479001600.0);                   //  1/12!
-        q = fma(q, z, -1.0 / 3628800.0);                    // -1/10!
-        q = fma(q, z, 1.0 / 40320.0);                       //  1/8!
-        q = fma(q, z, -1.0 / 720.0);                        // -1/6!
-        q = fma(q, z, 1.0 / 24.0);                          //  1/4!
-        q = fma(q, z, -0.5);                                // -1/2!
-        *c = fma(q, z, 1.0);
+        const double u = fma(fma(fma(fma(fma(p5, z, p4), z, p3), z, p2), z, p1), z, p0);
+        *s = fma(th * z, u, th);
+        const double v = fma(fma(fma(fma(fma(q5, z, q4), z, q3), z, q2), z, q1), z, q0);
+        *c = fma(v, z, 1.0);
     } else {
         sincos(th, s, c);
     }
@@ -46,80 +44,83 @@ __device__ __forceinline__ void branch_sincos(double th, double *s, double *c) {
 
 // One end of a branch seen from its own bus u towards bus v:
 //   P = Gss Vu^2 + Vu Vv A,  Q = -Bss Vu^2 + Vu Vv C,  A = G cos th_u + B sin th_u,
-//   C = G sin th_u - B cos th_u,  th_u = Va_u - Va_v.
+//   C = G sin th_u - B cos th_u,  th_u = Va_u - Va_v,
+// and, since dA/dth = -C and dC/dth = A, its derivatives
+//   dP/dth = -Vu Vv C,  dQ/dth = Vu Vv A,  dP/dVu = 2 Gss Vu + Vv A,  dQ/dVu = -2 Bss Vu + Vv C,
+//   dP/dVv = Vu A,  dQ/dVv = Vu C.
 struct End {
     double P, Q;
     double pa, pu, pv;   // dP / d(Va_u, Vm_u, Vm_v); dP/dVa_v = -pa
     double qa, qu, qv;   // dQ / d(Va_u, Vm_u, Vm_v)
 };
 
+// Gss2 = 2 Gss and Bss2 = 2 Bss (network tables); Vu2 = Vu^2 and VV = Vu Vv from the caller.
 template <bool DERIV>
-__device__ __forceinline__ End end_terms(double Gss, double Bss, double A, double C, double Vu,
-                                         double Vv) {
+__device__ __forceinline__ End end_terms(double Gss, double Bss, double Gss2, double Bss2,
+                                         double A, double C, double Vu, double Vv, double Vu2,
+                                         double VV) {
     End e;
-    double GV = Gss * Vu, BV = Bss * Vu;
-    double Ta = fma(Vv, A, GV);    // Gss Vu + Vv A
-    double Tc = fma(Vv, C, -BV);   // -Bss Vu + Vv C
-    e.P = Vu * Ta;
-    e.Q = Vu * Tc;
+    e.qa = VV * A;                 //  Vu Vv A
+    e.pa = -(VV * C);              // -Vu Vv C
+    e.P = fma(Gss, Vu2, e.qa);
+    e.Q = fma(-Bss, Vu2, -e.pa);
     if (DERIV) {
-        e.pu = Ta + GV;            // 2 Gss Vu + Vv A
-        e.qu = Tc - BV;            // -2 Bss Vu + Vv C
         e.pv = Vu * A;
         e.qv = Vu * C;
-        e.pa = -(Vv * e.qv);       // -Vu Vv C
-        e.qa = Vv * e.pv;          //  Vu Vv A
+        e.pu = fma(Gss2, Vu, Vv * A);
+        e.qu = fma(-Bss2, Vu, Vv * C);
     }
     return e;
 }
 
-// Distinct values of one end's Lagrangian Hessian block
-//   lamP grad^2 P + lamQ grad^2 Q + mu grad^2 (P^2 + Q^2)   in (Va_u, Va_v, Vm_u, Vm_v):
-//   (Va_u,Va_u) = -(Va_u,Va_v) = (Va_v,Va_v) = haa;  (Va_u,Vm_u) = -(Va_v,Vm_u) = hau;
-//   (Va_u,Vm_v) = -(Va_v,Vm_v) = hav = Vu W2;  (Vm_u,Vm_u) = huu;  (Vm_u,Vm_v) = huv;
-//   (Vm_v,Vm_v) = hvv = tK Vu^2.
-// hav and hvv are left as factors so that the caller folds them into the other end's values
-// with one fma each.
+// One end's Lagrangian Hessian block  lamP grad^2 P + lamQ grad^2 Q + mu grad^2 (P^2 + Q^2)  in
+// (Va_u, Va_v, Vm_u, Vm_v), with wP = lamP + 2 mu P, wQ = lamQ + 2 mu Q, W1 = wP A + wQ C,
+// W2 = wQ A - wP C and K = A^2 + C^2 = G^2 + B^2:
+//   (Va_u,Va_u) = -(Va_u,Va_v) = (Va_v,Va_v) = 2 mu K (Vu Vv)^2 - Vu Vv W1;
+//   (Va_u,Vm_u) = -(Va_v,Vm_u) = hau = 2 mu Vu Vv (A qu - C pu) + Vv W2;
+//   (Va_u,Vm_v) = -(Va_v,Vm_v) = Vu W2;
+//   (Vm_u,Vm_u) = huu = 2 mu (pu^2 + qu^2) + 2 Gss wP - 2 Bss wQ;
+//   (Vm_u,Vm_v) = huv = 2 mu Vu (pu A + qu C) + W1;   (Vm_v,Vm_v) = 2 mu K Vu^2.
+// The caller folds the two ends' blocks into the branch's values (branch_hess).
 struct EndHess {
-    double haa, hau, huu, huv, W2, tK, Vu2;
+    double W1, W2, tK, hau, huu, huv;   // tK = 2 mu K
 };
 
-__device__ __forceinline__ EndHess end_hess(const End &e, double Gss, double Bss, double A,
+__device__ __forceinline__ EndHess end_hess(const End &e, double Gss2, double Bss2, double A,
                                             double C, double K, double Vu, double Vv, double VV,
-                                            double VV2, double lamP, double lamQ, double mu) {
+                                            double lamP, double lamQ, double mu) {
     EndHess h;
-    double mu2 = mu + mu;
-    double wP = fma(mu2, e.P, lamP);              // multiplier of grad^2 P
-    double wQ = fma(mu2, e.Q, lamQ);
-    double W1 = fma(wP, A, wQ * C);
+    const double mu2 = mu + mu;
+    const double wP = fma(mu2, e.P, lamP);
+    const double wQ = fma(mu2, e.Q, lamQ);
+    h.W1 = fma(wP, A, wQ * C);
     h.W2 = fma(wQ, A, -(wP * C));
-    double E = fma(A, e.qu, -(C * e.pu));
-    double F = fma(e.pu, A, e.qu * C);
-    h.tK = mu2 * K;                               // 2 mu (A^2 + C^2)
-    h.haa = fma(h.tK, VV2, -(VV * W1));
+    const double E = fma(A, e.qu, -(C * e.pu));
+    const double F = fma(e.pu, A, e.qu * C);
+    h.tK = mu2 * K;
     h.hau = fma(mu2 * VV, E, Vv * h.W2);
-    double S = fma(e.pu, e.pu, e.qu * e.qu);
-    double in = fma(wP, Gss, -(wQ * Bss));
-    h.huu = fma(mu2, S, in + in);
-    h.huv = fma(mu2 * Vu, F, W1);
-    h.Vu2 = Vu * Vu;
+    const double S = fma(e.pu, e.pu, e.qu * e.qu);
+    h.huu = fma(mu2, S, fma(wP, Gss2, -(wQ * Bss2)));
+    h.huv = fma(mu2 * Vu, F, h.W1);
     return h;
 }
 
-// The branch's Hessian values from its two ends' blocks: (Vm_f, Va_f) = hau_f - hav_t,
-// (Vm_t, Va_t) = hau_t - hav_f, (Vm_f, Vm_f) = huu_f + hvv_t, (Vm_t, Vm_t) = huu_t + hvv_f.
+// The branch's Hessian values from its two ends' blocks:
+//   (Va_f,Va_f) = haa = Vf Vt (Vf Vt (tK_f + tK_t) - (W1_f + W1_t));
+//   (Vm_f, Va_f) = hau_f - Vt W2_t,  (Vm_t, Va_t) = hau_t - Vf W2_f;
+//   (Vm_f, Vm_f) = huu_f + tK_t Vt^2,  (Vm_t, Vm_t) = huu_t + tK_f Vf^2,  (Vm_f, Vm_t) = huv_f + huv_t.
 struct BranchHess {
     double haa, xf, xt, mff, mtt, mft;
 };
 
 __device__ __forceinline__ BranchHess branch_hess(const EndHess &hf, const EndHess &ht, double Vf,
-                                                  double Vt) {
+                                                  double Vt, double Vf2, double Vt2, double VV) {
     BranchHess b;
-    b.haa = hf.haa + ht.haa;
+    b.haa = VV * fma(VV, hf.tK + ht.tK, -(hf.W1 + ht.W1));
     b.xf = fma(-Vt, ht.W2, hf.hau);
     b.xt = fma(-Vf, hf.W2, ht.hau);
-    b.mff = fma(ht.tK, ht.Vu2, hf.huu);
-    b.mtt = fma(hf.tK, hf.Vu2, ht.huu);
+    b.mff = fma(ht.tK, Vt2, hf.huu);
+    b.mtt = fma(hf.tK, Vf2, ht.huu);
     b.mft = hf.huv + ht.huv;
     return b;
 }
@@ -191,15 +192,18 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     const double G = __ldg(N.Gft + l), Bm = __ldg(N.Bft + l);
     const double Gff = __ldg(N.Gff + l), Bff = __ldg(N.Bff + l);
     const double Gtt = __ldg(N.Gtt + l), Btt = __ldg(N.Btt + l);
+    const double Gff2 = __ldg(N.Gff2 + l), Bff2 = __ldg(N.Bff2 + l);
+    const double Gtt2 = __ldg(N.Gtt2 + l), Btt2 = __ldg(N.Btt2 + l);
 
     double s, c;
     branch_sincos(Vaf - Vat, &s, &c);
     const double Bc = Bm * c, Bs = Bm * s;
     const double Af = fma(G, c, Bs), Cf = fma(G, s, -Bc);      // from end, th = Va_f - Va_t
     const double At = fma(G, c, -Bs), Ct = -fma(G, s, Bc);     // to end,   th = Va_t - Va_f
+    const double VV = Vf * Vt, Vf2 = Vf * Vf, Vt2 = Vt * Vt;
 
-    const End ef = end_terms<DERIV>(Gff, Bff, Af, Cf, Vf, Vt);
-    const End et = end_terms<DERIV>(Gtt, Btt, At, Ct, Vt, Vf);
+    const End ef = end_terms<DERIV>(Gff, Bff, Gff2, Bff2, Af, Cf, Vf, Vt, Vf2, VV);
+    const End et = end_terms<DERIV>(Gtt, Btt, Gtt2, Btt2, At, Ct, Vt, Vf, Vt2, VV);
 
     put2(rf, SC_P, ef.P, ef.Q);
     put2(rt, SC_P, et.P, et.Q);
@@ -219,10 +223,9 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
         const double lQf = __ldg(lb + nb + fb), lQt = __ldg(lb + nb + tb);
         const double muf = __ldg(lb + 2 * nb + l), mut = __ldg(lb + 2 * nb + nl + l);
         const double K = fma(G, G, Bm * Bm);          // A^2 + C^2 at both ends
-        const double VV = Vf * Vt, VV2 = VV * VV;
-        const EndHess hf = end_hess(ef, Gff, Bff, Af, Cf, K, Vf, Vt, VV, VV2, lPf, lQf, muf);
-        const EndHess ht = end_hess(et, Gtt, Btt, At, Ct, K, Vt, Vf, VV, VV2, lPt, lQt, mut);
-        const BranchHess h = branch_hess(hf, ht, Vf, Vt);
+        const EndHess hf = end_hess(ef, Gff2, Bff2, Af, Cf, K, Vf, Vt, VV, lPf, lQf, muf);
+        const EndHess ht = end_hess(et, Gtt2, Btt2, At, Ct, K, Vt, Vf, VV, lPt, lQt, mut);
+        const BranchHess h = branch_hess(hf, ht, Vf, Vt, Vf2, Vt2, VV);
         put2(rf, SC_HAA, h.haa, h.xf);                 // (Va_f,Va_f), (Vm_f, Va_f)
         put2(rt, SC_HAA, h.haa, h.xt);                 // (Va_t,Va_t), (Vm_t, Va_t)
         put2(rf, SC_HUU, h.mff, h.mft);

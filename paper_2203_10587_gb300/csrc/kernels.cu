@@ -24,10 +24,13 @@ namespace exago {
 // ---------------------------------------------------------------------------------------------
 // pi-model admittances (once per network).  ys = 1/(r + jx); Yff = (ys + jb/2)/tau^2,
 // Yft = Ytf = -ys/tau, Ytt = ys + jb/2; tap 0 means tau = 1.
+struct AdmittanceOut {
+    double *Y[10];   // Gff, Bff, Gtt, Btt, Gft, Bft, 2 Gff, 2 Bff, 2 Gtt, 2 Btt
+};
+
 __global__ void k_admittance(const double *__restrict__ r, const double *__restrict__ x,
                              const double *__restrict__ b, const double *__restrict__ tap, int nl,
-                             double *Gff, double *Bff, double *Gtt, double *Btt, double *Gft,
-                             double *Bft) {
+                             AdmittanceOut out) {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nl) return;
     double rl = r[l], xl = x[l];
@@ -35,20 +38,25 @@ __global__ void k_admittance(const double *__restrict__ r, const double *__restr
     double gs = rl / z2, bs = -xl / z2;
     double tau = tap[l] == 0.0 ? 1.0 : tap[l];
     double bc = bs + 0.5 * b[l];
-    Gff[l] = gs / (tau * tau);
-    Bff[l] = bc / (tau * tau);
-    Gtt[l] = gs;
-    Btt[l] = bc;
-    Gft[l] = -gs / tau;
-    Bft[l] = -bs / tau;
+    const double Gff = gs / (tau * tau), Bff = bc / (tau * tau);
+    out.Y[0][l] = Gff;
+    out.Y[1][l] = Bff;
+    out.Y[2][l] = gs;
+    out.Y[3][l] = bc;
+    out.Y[4][l] = -gs / tau;
+    out.Y[5][l] = -bs / tau;
+    out.Y[6][l] = 2.0 * Gff;     // doubling is exact
+    out.Y[7][l] = 2.0 * Bff;
+    out.Y[8][l] = 2.0 * gs;
+    out.Y[9][l] = 2.0 * bc;
 }
 
 int launch_admittance(const double *r, const double *x, const double *b, const double *tap,
-                      int nl, double *Gff, double *Bff, double *Gtt, double *Btt, double *Gft,
-                      double *Bft, void *stream) {
+                      int nl, double *const Y[10], void *stream) {
     if (nl <= 0) return 0;
-    k_admittance<<<(nl + 127) / 128, 128, 0, (cudaStream_t)stream>>>(r, x, b, tap, nl, Gff, Bff,
-                                                                      Gtt, Btt, Gft, Bft);
+    AdmittanceOut out;
+    for (int k = 0; k < 10; k++) out.Y[k] = Y[k];
+    k_admittance<<<(nl + 127) / 128, 128, 0, (cudaStream_t)stream>>>(r, x, b, tap, nl, out);
     return (int)cudaGetLastError();
 }
 
