@@ -34,12 +34,12 @@ WORKLOAD = "2000-bus x 512 N-1 contingencies: f, grad f, g|h, J values, Lagrangi
 B_DEFAULT = 512
 N_INPUT_SETS = 4
 # FP64 work per unit with every output requested, counted from the kernel source on the fast
-# sincos path (an FMA counts 2 flops): (flops, instructions).  Per 2000-bus state they sum to
-# 563,700 flops / 390,200 instructions.
-FP64_PER_BRANCH = (179, 119)   # sincos, flows, 16 derivatives, h and its J row, Hessian fold
+# sincos path (an FMA counts 2 flops; doublings run on the integer pipe and count nothing):
+# (flops, instructions).  Per 2000-bus state they sum to 536,000 flops / 364,500 instructions.
+FP64_PER_BRANCH = (173, 113)   # sincos, flows, 16 derivatives, h and its J row, Hessian fold
 FP64_PER_SLOT = (9, 9)         # a branch end's record summed into its bus (all but the first)
-FP64_PER_BUS = (20, 15)        # shunt, load and diagonal terms of one bus
-FP64_PER_GEN = (19, 16)        # balance, cost Hessian, gradient and objective terms of a generator
+FP64_PER_BUS = (16, 12)        # shunt, load and diagonal terms of one bus
+FP64_PER_GEN = (12, 9)         # balance, cost Hessian, gradient and objective terms of a generator
 FP64_PER_STATE = (255, 255)    # the objective's fixed 256-lane reduction tree
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 2 FP64 FMA per SM per clock x
 # 2 flops x 2.07 GHz (the probe measured 1.20 TFLOP/s at 1.97 GHz under load).

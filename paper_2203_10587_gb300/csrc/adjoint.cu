@@ -58,16 +58,17 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
         put2(rf, 0, dPf, dQf);
         put2(rt, 0, dPt, dQt);
         double *ob = A.out + (size_t)b * N.m;
-        ob[2 * nb + l] = 2.0 * fma(ef.P, dPf, ef.Q * dQf);
-        ob[2 * nb + nl + l] = 2.0 * fma(et.P, dPt, et.Q * dQt);
+        ob[2 * nb + l] = twice(fma(ef.P, dPf, ef.Q * dQf));
+        ob[2 * nb + nl + l] = twice(fma(et.P, dPt, et.Q * dQt));
     } else if (MODE == ADJ_JTV) {
         const double *vb = A.v + (size_t)b * N.m;
         const double vhf = __ldg(vb + 2 * nb + l), vht = __ldg(vb + 2 * nb + nl + l);
         // weights of grad P and grad Q at each end: row multiplier + 2 v_h (P or Q)
-        const double wPf = fma(vhf + vhf, ef.P, __ldg(vb + fb));
-        const double wQf = fma(vhf + vhf, ef.Q, __ldg(vb + nb + fb));
-        const double wPt = fma(vht + vht, et.P, __ldg(vb + tb));
-        const double wQt = fma(vht + vht, et.Q, __ldg(vb + nb + tb));
+        const double vhf2 = twice(vhf), vht2 = twice(vht);
+        const double wPf = fma(vhf2, ef.P, __ldg(vb + fb));
+        const double wQf = fma(vhf2, ef.Q, __ldg(vb + nb + fb));
+        const double wPt = fma(vht2, et.P, __ldg(vb + tb));
+        const double wQt = fma(vht2, et.Q, __ldg(vb + nb + tb));
         const double af = fma(wPf, ef.pa, wQf * ef.qa);     // d/dVa_f through the from end
         const double at = fma(wPt, et.pa, wQt * et.qa);     // d/dVa_t through the to end
         const double mf = fma(wPf, ef.pu, fma(wQf, ef.qu, fma(wPt, et.pv, wQt * et.qv)));
@@ -113,7 +114,7 @@ __device__ __forceinline__ void adj_bus_item(const DevNet &N, const AdjReq &A, i
     const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
     if (MODE == ADJ_JVP) {
         const double *ub = A.v + (size_t)b * N.n;
-        const double tu = (Vm + Vm) * __ldg(ub + nb + i);
+        const double tu = twice(Vm) * __ldg(ub + nb + i);
         s0v = fma(Gs, tu, s0v);
         s1v = fma(-Bs, tu, s1v);
         for (int s = g0; s < g1; s++) {
@@ -127,7 +128,7 @@ __device__ __forceinline__ void adj_bus_item(const DevNet &N, const AdjReq &A, i
     } else if (MODE == ADJ_JTV) {
         const double *vb = A.v + (size_t)b * N.m;
         const double vP = __ldg(vb + i), vQ = __ldg(vb + nb + i);
-        const double tV = Vm + Vm;
+        const double tV = twice(Vm);
         s1v = fma(vP * Gs, tV, fma(-(vQ * Bs), tV, s1v));
         double *ob = A.out + (size_t)b * N.n;
         ob[i] = s0v;
@@ -141,17 +142,16 @@ __device__ __forceinline__ void adj_bus_item(const DevNet &N, const AdjReq &A, i
         const double *lb = A.lam + (size_t)b * N.m;
         const double *ub = A.v + (size_t)b * N.n;
         const double lP = __ldg(lb + i), lQ = __ldg(lb + nb + i);
-        const double dshunt = fma(lP, Gs + Gs, -(lQ * (Bs + Bs)));
+        const double dshunt = fma(lP, twice(Gs), -(lQ * twice(Bs)));
         s1v = fma(dshunt, __ldg(ub + nb + i), s1v);
         double *ob = A.out + (size_t)b * N.n;
         ob[i] = s0v;
         ob[nb + i] = s1v;
         if (g1 > g0) {
             const double sw = A.sigma * (A.obj_weight ? A.obj_weight[b] : 1.0);
-            const double base2 = N.baseMVA * N.baseMVA;
             for (int s = g0; s < g1; s++) {
                 const int k = __ldg(N.gen_ord + s);
-                const double h = sw * (2.0 * __ldg(N.c2 + k) * base2);
+                const double h = sw * __ldg(N.c2g + k);
                 ob[2 * nb + k] = h * __ldg(ub + 2 * nb + k);
                 ob[2 * nb + ng + k] = 0.0;
             }

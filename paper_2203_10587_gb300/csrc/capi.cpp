@@ -154,7 +154,7 @@ exago_status do_upload(exago_net *net) {
     UP(bus_k, bus_k); UP(bus_nlow, bus_nlow); UP(bus_perm, bus_perm);
     UP(Gs, Gs); UP(Bs, Bs); UP(Pd, Pd); UP(Qd, Qd);
     UP(gen_ptr, gen_ptr); UP(gen_ord, gen_ord);
-    UP(c2, c2); UP(c1, c1); UP(c0, c0);
+    UP(c2, c2); UP(c1, c1); UP(c0, c0); UP(c2g, c2g); UP(c1g, c1g);
 #undef UP
     // branch parameters, then the pi-model admittances evaluated on the device
     const double *r = nullptr, *x = nullptr, *b = nullptr, *tap = nullptr;

@@ -42,6 +42,22 @@ __device__ __forceinline__ void branch_sincos(double th, double *s, double *c) {
     }
 }
 
+// 2 x, exactly, on the integer pipe (the FP64 pipe is the path's bottleneck): for a normal x
+// whose double stays finite the exponent field goes up by one; zero and subnormals shift their
+// magnitude bits left by one (the largest subnormals then become normal, as 2 x does); the
+// largest binade goes to infinity; infinities and NaNs are returned unchanged.
+__device__ __forceinline__ double twice(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long sgn = b & 0x8000000000000000ull, mag = b ^ sgn;
+    const unsigned long long e = mag >> 52;
+    unsigned long long r;
+    if (e == 0) r = sgn | (mag << 1);
+    else if (e < 0x7FEull) r = b + (1ull << 52);
+    else if (e == 0x7FEull) r = sgn | 0x7FF0000000000000ull;
+    else r = b;
+    return __longlong_as_double((long long)r);
+}
+
 // One end of a branch seen from its own bus u towards bus v:
 //   P = Gss Vu^2 + Vu Vv A,  Q = -Bss Vu^2 + Vu Vv C,  A = G cos th_u + B sin th_u,
 //   C = G sin th_u - B cos th_u,  th_u = Va_u - Va_v,
@@ -90,7 +106,7 @@ __device__ __forceinline__ EndHess end_hess(const End &e, double Gss2, double Bs
                                             double C, double K, double Vu, double Vv, double VV,
                                             double lamP, double lamQ, double mu) {
     EndHess h;
-    const double mu2 = mu + mu;
+    const double mu2 = twice(mu);
     const double wP = fma(mu2, e.P, lamP);
     const double wQ = fma(mu2, e.Q, lamQ);
     h.W1 = fma(wP, A, wQ * C);
@@ -137,7 +153,7 @@ __device__ __forceinline__ double dneg(double v) {
 // h row of one end, |S|^2, and its four Jacobian entries in the row's ascending column order
 // (Va_lo, Va_hi, Vm_lo, Vm_hi).
 __device__ __forceinline__ void store_hrow(double *Jrow, const End &e, bool self_is_lo) {
-    double P2 = e.P + e.P, Q2 = e.Q + e.Q;
+    const double P2 = twice(e.P), Q2 = twice(e.Q);
     double da = fma(P2, e.pa, Q2 * e.qa);
     double du = fma(P2, e.pu, Q2 * e.qu);
     double dv = fma(P2, e.pv, Q2 * e.qv);
@@ -233,12 +249,12 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     }
 }
 
-// Gradient entry of generator k's active power: w (2 c2 base^2 Pg + c1 base).
+// Gradient entry of generator k's active power: w (2 c2 base^2 Pg + c1 base), with the network
+// constants c2g = 2 c2 base^2 and c1g = c1 base.
 __device__ __forceinline__ double grad_pg(const DevNet &N, const EvalReq &R, int b, int k) {
     const double w = R.obj_weight ? R.obj_weight[b] : 1.0;
-    const double base = N.baseMVA;
     const double Pg = __ldg(R.x + (size_t)b * N.n + 2 * N.nb + k);
-    return w * fma(2.0 * __ldg(N.c2 + k) * base * base, Pg, __ldg(N.c1 + k) * base);
+    return w * fma(__ldg(N.c2g + k), Pg, __ldg(N.c1g + k));
 }
 
 // Where one bus writes its Jacobian rows P_i, Q_i and Hessian rows Va_i, Vm_i (global memory, or
@@ -329,7 +345,7 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
         ghb[nb + i] = gQ;
     }
     if (WJ) {
-        const double tV = Vm + Vm;
+        const double tV = twice(Vm);
         JP[nlow] = dPa; JP[k + nlow] = fma(Gs, tV, dPu);
         JQ[nlow] = dQa; JQ[k + nlow] = fma(-Bs, tV, dQu);
         for (int q = 0; q < g1 - g0; q++) {
@@ -342,14 +358,13 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
         const double lP = __ldg(lb + i), lQ = __ldg(lb + nb + i);
         HA[nlow] = dAA;                                       // (Va_i, Va_i): last of row Va_i
         HM[nlow] = dUA;                                       // (Vm_i, Va_i)
-        HM[k + nlow] = dUU + fma(lP, Gs + Gs, -(lQ * (Bs + Bs)));   // (Vm_i, Vm_i): last
+        HM[k + nlow] = dUU + fma(lP, twice(Gs), -(lQ * twice(Bs)));   // (Vm_i, Vm_i): last
         if (g1 > g0) {
             const double sw = R.sigma * (R.obj_weight ? R.obj_weight[b] : 1.0);
-            const double base2 = N.baseMVA * N.baseMVA;
             double *Hb = R.hval + (size_t)b * N.nnzH + N.hpg;
             for (int q = g0; q < g1; q++) {
                 const int g = __ldg(N.gen_ord + q);
-                Hb[g] = sw * (2.0 * __ldg(N.c2 + g) * base2);
+                Hb[g] = sw * __ldg(N.c2g + g);
             }
         }
     }

@@ -40,6 +40,7 @@ struct HostPlan {
     int64_t nnzJ = 0, nnzJg = 0, nnzH = 0;
     double baseMVA = 100.0;
     std::vector<double> Gs, Bs, Pd, Qd, r, x, b, tap, rateA, c2, c1, c0;
+    std::vector<double> c2g, c1g;   // 2 c2 baseMVA^2 and c1 baseMVA
     std::vector<int> f, t, gbus;
 
     std::vector<int64_t> Jrowptr, Hrowptr;
@@ -85,6 +86,7 @@ struct DevNet {
     const double *Gs, *Bs, *Pd, *Qd;
     const int *gen_ptr, *gen_ord;
     const double *c2, *c1, *c0;
+    const double *c2g, *c1g;    // 2 c2 baseMVA^2 and c1 baseMVA (cost derivatives in p.u.)
     int *status;                // device status word (host-mapped)
 };
 

@@ -63,6 +63,13 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
     p.r = copy_or(r, nl, 0.0); p.x = copy_or(x, nl, 0.0); p.b = copy_or(b, nl, 0.0);
     p.tap = copy_or(tap, nl, 0.0); p.rateA = copy_or(rateA, nl, 0.0);
     p.c2 = copy_or(c2, ng, 0.0); p.c1 = copy_or(c1, ng, 0.0); p.c0 = copy_or(c0, ng, 0.0);
+    // cost derivatives per p.u. of Pg: d/dPg of c2 (base Pg)^2 + c1 base Pg
+    p.c2g.resize(ng);
+    p.c1g.resize(ng);
+    for (int k = 0; k < ng; k++) {
+        p.c2g[k] = 2.0 * p.c2[k] * baseMVA * baseMVA;
+        p.c1g[k] = p.c1[k] * baseMVA;
+    }
     p.f.assign(f ? f : nullptr, f ? f + nl : nullptr);
     p.t.assign(t ? t : nullptr, t ? t + nl : nullptr);
     p.gbus.assign(gbus ? gbus : nullptr, gbus ? gbus + ng : nullptr);

@@ -51,6 +51,25 @@ def test_ragged_batch_with_masks_scales_weights(ex, oracle_mod, sigma):
         compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"300-bus sigma={sigma}")
 
 
+def test_signed_zero_and_subnormal_inputs(ex, oracle_mod):
+    """Doubling on the integer pipe must equal 2 x for +-0 and subnormal multipliers, voltages and
+    loads; flat angles give sin = 0 and cos = 1 exactly."""
+    g = synth.make_grid(17, 200, 260, 50, shunts=True)
+    b = synth.random_batch(17, g, 4, masks=True, sigma=0.5)
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2e-308, 1e-310, -1e-310])
+    rng = np.random.default_rng(17)
+    for i in range(b.B):
+        idx = rng.choice(g.m, size=64, replace=False)
+        b.lam[i, idx] = rng.choice(special, size=64)
+    b.x[1, :g.nb] = 0.0                      # flat angles
+    b.x[2, g.nb:2 * g.nb][::7] = -0.0 * 1.0  # signed-zero voltages at some buses
+    b.x[3, 2 * g.nb:] = rng.choice(special, size=2 * g.ng)
+    net = ex.Net(g)
+    out = gpu_eval(net, b)
+    for i in range(b.B):
+        compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"special inputs [{i}]")
+
+
 def test_parallel_branches_and_shared_generator_bus(ex, oracle_mod):
     from test_capi_host import parallel_grid
     g = parallel_grid()
