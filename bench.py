@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch configuration")
     p.add_argument("--no-serve", action="store_true", help="skip the serving-mix measurement")
+    p.add_argument("--config", default="", help="launch configuration instead of autotuning, "
+                   "e.g. schedule=2,block=64,occupancy=16")
     p.add_argument("--serve-seconds", type=float, default=1.5, help="length of each serving phase")
     return p.parse_args()
 
@@ -384,7 +386,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         net.eval_all(batches[k % N_INPUT_SETS], out)
 
     tuned = None
-    if not args.no_autotune:
+    if args.config:
+        cfg = {k: int(v) for k, v in (kv.split("=") for kv in args.config.split(","))}
+        exago.exago_net_set_config(net.h, **cfg)
+    elif not args.no_autotune:
         tuned = exago.exago_net_autotune(net.h, batches[0], out["f"], out["grad"], out["gh"],
                                          out["jval"], out["hval"], reps=10)
     launch_cfg = exago.exago_net_get_config(net.h, B)

@@ -21,6 +21,10 @@ enum : int { W_G = 1, W_J = 2, W_H = 4 };
 // results are within 0.61 ulp (sin) and 1.17 ulp (cos) of the exact values (checked on the CPU
 // with single-rounding fma).  The interval test compares the bit pattern of |th| with that of
 // pi/4 on the integer pipe.
+// The library sincos for wide angles, kept out of line so that none of its instructions is
+// scheduled ahead of the interval test and executed for every branch.
+static __device__ __noinline__ void sincos_wide(double th, double *s, double *c) { sincos(th, s, c); }
+
 __device__ __forceinline__ void branch_sincos(double th, double *s, double *c) {
     const unsigned long long PI4_BITS = 0x3FE921FB54442D18ull;   // pi/4 rounded to double
     if ((__double_as_longlong(th) & 0x7FFFFFFFFFFFFFFFull) <= PI4_BITS) {
@@ -38,7 +42,7 @@ __device__ __forceinline__ void branch_sincos(double th, double *s, double *c) {
         const double v = fma(fma(fma(fma(fma(q5, z, q4), z, q3), z, q2), z, q1), z, q0);
         *c = fma(v, z, 1.0);
     } else {
-        sincos(th, s, c);
+        sincos_wide(th, s, c);
     }
 }
 
@@ -47,15 +51,30 @@ __device__ __forceinline__ void branch_sincos(double th, double *s, double *c) {
 // magnitude bits left by one (the largest subnormals then become normal, as 2 x does); the
 // largest binade goes to infinity; infinities and NaNs are returned unchanged.
 __device__ __forceinline__ double twice(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long sgn = b & 0x8000000000000000ull, mag = b ^ sgn;
-    const unsigned long long e = mag >> 52;
-    unsigned long long r;
-    if (e == 0) r = sgn | (mag << 1);
-    else if (e < 0x7FEull) r = b + (1ull << 52);
-    else if (e == 0x7FEull) r = sgn | 0x7FF0000000000000ull;
-    else r = b;
-    return __longlong_as_double((long long)r);
+    // written in PTX so that the compiler keeps it on the integer pipe
+    double r;
+    asm("{\n\t"
+        ".reg .b64 b, s, m, e, t1, t2;\n\t"
+        ".reg .pred p0, p1, p2;\n\t"
+        "mov.b64 b, %1;\n\t"
+        "and.b64 s, b, 0x8000000000000000;\n\t"
+        "xor.b64 m, b, s;\n\t"
+        "shr.u64 e, m, 52;\n\t"
+        "shl.b64 t1, m, 1;\n\t"
+        "or.b64 t1, t1, s;\n\t"                      // zero or subnormal: magnitude bits << 1
+        "add.u64 t2, b, 0x0010000000000000;\n\t"     // normal: exponent + 1
+        "setp.eq.u64 p0, e, 0;\n\t"
+        "selp.b64 t2, t1, t2, p0;\n\t"
+        "setp.eq.u64 p1, e, 0x7FE;\n\t"
+        "or.b64 t1, s, 0x7FF0000000000000;\n\t"      // top binade: infinity
+        "selp.b64 t2, t1, t2, p1;\n\t"
+        "setp.eq.u64 p2, e, 0x7FF;\n\t"
+        "selp.b64 t2, b, t2, p2;\n\t"                // infinity or NaN: unchanged
+        "mov.b64 %0, t2;\n\t"
+        "}"
+        : "=d"(r)
+        : "d"(x));
+    return r;
 }
 
 // One end of a branch seen from its own bus u towards bus v:
@@ -331,10 +350,15 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
     const double dAA = D.haa, dUA = D.hua, dUU = D.huu;
 
     if (WG && R.gh) {
-        const double sc = R.pd_scale ? __ldg(R.pd_scale + (size_t)b * nb + i) : 1.0;
         const double VV = Vm * Vm;
-        double gP = sP + fma(Gs, VV, __ldg(N.Pd + i) * sc);
-        double gQ = sQ + fma(-Bs, VV, __ldg(N.Qd + i) * sc);
+        double Pd = __ldg(N.Pd + i), Qd = __ldg(N.Qd + i);
+        if (R.pd_scale) {                                     // load scenarios
+            const double sc = __ldg(R.pd_scale + (size_t)b * nb + i);
+            Pd *= sc;
+            Qd *= sc;
+        }
+        double gP = sP + fma(Gs, VV, Pd);
+        double gQ = sQ + fma(-Bs, VV, Qd);
         for (int q = g0; q < g1; q++) {
             const int g = __ldg(N.gen_ord + q);
             gP -= __ldg(xb + 2 * nb + g);
