@@ -250,6 +250,8 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *             EXAGO_ETIMEOUT in the status word (0 = 2^22).
  *   test_force_timeout  testing only: bus tiles wait for a count that never arrives, so every
  *             wait times out; the launch still ends and exago_net_check reports it.
+ *   tile_group  persistent: tiles of one kind and state per work item (1 to 4; 0 = 1), which
+ *             divides the items' claims, waits and signals by that number.
  */
 enum { EXAGO_SCHED_AUTO = 0, EXAGO_SCHED_KERNELS = 1, EXAGO_SCHED_PERSISTENT = 2,
        EXAGO_SCHED_PIPELINED = 3 };
@@ -266,6 +268,7 @@ typedef struct {
     int use_graph;
     long long spin_limit;
     int test_force_timeout;
+    int tile_group;
 } exago_config;
 
 /* Sets the net's configuration (validated: EINVAL for unknown values or ring <= lag). */
@@ -276,8 +279,8 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg);
 
 /*
  * Autotuner: times the multi-kernel schedule, pipelined variants (three chunk sizes) and
- * persistent variants (block 64 / 128 / 256, occupancy 0 / 16 / 24 warps), each with and
- * without slot-parallel bus tiles, on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
+ * persistent variants (block 64 / 128 / 256, occupancy 0 / 16 / 24 warps, 1 or 2 tiles per
+ * work item), each with and without slot-parallel bus tiles, on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
  * fastest for batches of this size (used by EXAGO_SCHED_AUTO).  Outputs are written as by
  * exago_eval_all.  *best (may be NULL) receives the choice.
  */

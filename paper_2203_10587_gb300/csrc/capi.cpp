@@ -225,6 +225,7 @@ exago_status plan_only(int nb, const double *Gs, const double *Bs, const double 
 struct Resolved {
     int schedule;          // EXAGO_SCHED_KERNELS or EXAGO_SCHED_PERSISTENT
     int block, occ_warps, stage_recs, stage_cap, grid, lag, ring, use_graph, force_timeout;
+    int group;             // persistent: tiles per work item
     int chunk, pipe_ring;  // pipelined schedule
     long long spin_limit;
 };
@@ -286,7 +287,8 @@ Resolved resolve(exago_net *net, int B) {
     r.stage_cap = stage_cap(net, pers, r.block, r.occ_warps, r.stage_recs);
     r.grid = net->sm_count * occupancy(net, true, r.block, r.occ_warps,
                                        pers ? (size_t)r.stage_cap * sizeof(double) : 0);
-    const int Tbr = (net->plan.nl + r.block - 1) / r.block;
+    r.group = c.tile_group >= 1 && c.tile_group <= 4 ? c.tile_group : 1;
+    const int Tbr = (net->plan.nl + r.block * r.group - 1) / (r.block * r.group);
     // bus tiles trail by the states the resident CTAs can hold in branch work, plus margin
     int lag = c.lag > 0 ? c.lag : (Tbr > 0 ? (r.grid + Tbr - 1) / Tbr : 1) + 2;
     if (lag > B) lag = B;
@@ -495,13 +497,14 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
     PersistLaunch pl;
     pl.block = rs.block; pl.occ_warps = rs.occ_warps; pl.grid = rs.grid; pl.lag = rs.lag;
     pl.ring = rs.ring;
+    pl.group = rs.group;
     pl.spin_limit = rs.spin_limit; pl.force_timeout = rs.force_timeout;
     pl.counters = (int *)w;
     if (graph) {
         std::vector<uint64_t> key = req_key(R, EXAGO_SCHED_PERSISTENT);
         for (uint64_t v : {(uint64_t)pl.counters, (uint64_t)pl.block, (uint64_t)pl.grid,
                            (uint64_t)pl.lag, (uint64_t)pl.ring, (uint64_t)pl.spin_limit,
-                           (uint64_t)pl.occ_warps, (uint64_t)pl.force_timeout})
+                           (uint64_t)pl.occ_warps, (uint64_t)pl.force_timeout, (uint64_t)pl.group})
             key.push_back(v);
         const DevNet &dn = net->dev;
         return launch_graph_locked(
@@ -782,6 +785,8 @@ exago_status exago_net_set_config(exago_net_t net, const exago_config *cfg) {
         return fail(EXAGO_EINVAL, "unknown stage_records value");
     if (cfg->lag < 0 || cfg->ring < 0 || cfg->spin_limit < 0)
         return fail(EXAGO_EINVAL, "negative lag, ring or spin limit");
+    if (cfg->tile_group < 0 || cfg->tile_group > 4)
+        return fail(EXAGO_EINVAL, "tile_group must be 0 to 4");
     if (cfg->schedule != EXAGO_SCHED_PIPELINED && cfg->ring > 0 && cfg->lag > 0 && cfg->ring <= cfg->lag)
         return fail(EXAGO_EINVAL, "ring must exceed lag");
     std::lock_guard<std::mutex> lk(net->mu);
@@ -803,6 +808,7 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg) {
         cfg->lag = r.lag;
         cfg->ring = r.ring;
         cfg->use_graph = r.use_graph;
+        cfg->tile_group = r.group;
     }
     if (r.schedule == EXAGO_SCHED_PIPELINED) {
         cfg->chunk = r.chunk;
@@ -840,15 +846,17 @@ exago_status exago_net_autotune(exago_net_t net, const exago_batch *bt, double *
                 cands.push_back(c);
             }
             for (int block : {64, 128, 256})
-                for (int occw : {0, 16, 24}) {
-                    exago_config c{};
-                    c.schedule = EXAGO_SCHED_PERSISTENT;
-                    c.block = block;
-                    c.occupancy = occw;
-                    c.stage_records = stage;
-                    c.use_graph = EXAGO_GRAPH_ON;
-                    cands.push_back(c);
-                }
+                for (int occw : {0, 16, 24})
+                    for (int group : {1, 2}) {
+                        exago_config c{};
+                        c.schedule = EXAGO_SCHED_PERSISTENT;
+                        c.block = block;
+                        c.occupancy = occw;
+                        c.stage_records = stage;
+                        c.tile_group = group;
+                        c.use_graph = EXAGO_GRAPH_ON;
+                        cands.push_back(c);
+                    }
         }
     }
     cudaStream_t st = (cudaStream_t)bt->stream;

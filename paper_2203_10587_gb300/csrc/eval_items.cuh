@@ -19,15 +19,20 @@ enum : int { W_G = 1, W_J = 2, W_H = 4 };
 // evaluated by Horner's rule with fused multiply-adds: 14 FP64 instructions for the pair, against
 // about 28 for the library sincos, which is kept for larger angles.  Evaluated in this order the
 // results are within 0.61 ulp (sin) and 1.17 ulp (cos) of the exact values (checked on the CPU
-// with single-rounding fma).  The interval test compares the bit pattern of |th| with that of
-// pi/4 on the integer pipe.
+// with single-rounding fma).
 // The library sincos for wide angles, kept out of line so that none of its instructions is
 // scheduled ahead of the interval test and executed for every branch.
 static __device__ __noinline__ void sincos_wide(double th, double *s, double *c) { sincos(th, s, c); }
 
 __device__ __forceinline__ void branch_sincos(double th, double *s, double *c) {
-    const unsigned long long PI4_BITS = 0x3FE921FB54442D18ull;   // pi/4 rounded to double
-    if ((__double_as_longlong(th) & 0x7FFFFFFFFFFFFFFFull) <= PI4_BITS) {
+    // |th| <= pi/4 by comparing bit patterns, in PTX so that it stays on the integer pipe
+    int small;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.le.u64 p, %1, 0x3FE921FB54442D18;\n\t"   // pi/4 rounded to double
+        "selp.s32 %0, 1, 0, p;\n\t}"
+        : "=r"(small)
+        : "l"((unsigned long long)__double_as_longlong(th) & 0x7FFFFFFFFFFFFFFFull));
+    if (small) {
         // SINCOS_COEFFS_BEGIN
         constexpr double p0 = -0x1.5555555555549p-3, p1 = 0x1.111111110f881p-7,
                          p2 = -0x1.a01a019c126c0p-13, p3 = 0x1.71de357875383p-19,
@@ -237,29 +242,36 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     const double At = fma(G, c, -Bs), Ct = -fma(G, s, Bc);     // to end,   th = Va_t - Va_f
     const double VV = Vf * Vt, Vf2 = Vf * Vf, Vt2 = Vt * Vt;
 
-    const End ef = end_terms<DERIV>(Gff, Bff, Gff2, Bff2, Af, Cf, Vf, Vt, Vf2, VV);
-    const End et = end_terms<DERIV>(Gtt, Btt, Gtt2, Btt2, At, Ct, Vt, Vf, Vt2, VV);
-
-    put2(rf, SC_P, ef.P, ef.Q);
-    put2(rt, SC_P, et.P, et.Q);
-    if (WG && ghb) {
-        ghb[2 * nb + l] = fma(ef.P, ef.P, ef.Q * ef.Q);
-        ghb[2 * nb + nl + l] = fma(et.P, et.P, et.Q * et.Q);
+    // One end at a time, stored as soon as it is computed, so that fewer values are live at once
+    // (the compiler would otherwise recompute products to save registers).
+    const double *lb = WH ? R.lam + (size_t)b * N.m : nullptr;
+    const double K = WH ? fma(G, G, Bm * Bm) : 0.0;   // A^2 + C^2 at both ends
+    EndHess hf{}, ht{};
+    {
+        const End ef = end_terms<DERIV>(Gff, Bff, Gff2, Bff2, Af, Cf, Vf, Vt, Vf2, VV);
+        put2(rf, SC_P, ef.P, ef.Q);
+        if (WG && ghb) ghb[2 * nb + l] = fma(ef.P, ef.P, ef.Q * ef.Q);
+        if (WJ) {
+            put2(rf, SC_PA, ef.pa, ef.pu); put2(rf, SC_PV, ef.pv, ef.qa); put2(rf, SC_QU, ef.qu, ef.qv);
+            store_hrow(Jf, ef, fb < tb);
+        }
+        if (WH)
+            hf = end_hess(ef, Gff2, Bff2, Af, Cf, K, Vf, Vt, VV, __ldg(lb + fb), __ldg(lb + nb + fb),
+                          __ldg(lb + 2 * nb + l));
     }
-    if (WJ) {
-        put2(rf, SC_PA, ef.pa, ef.pu); put2(rf, SC_PV, ef.pv, ef.qa); put2(rf, SC_QU, ef.qu, ef.qv);
-        put2(rt, SC_PA, et.pa, et.pu); put2(rt, SC_PV, et.pv, et.qa); put2(rt, SC_QU, et.qu, et.qv);
-        store_hrow(Jf, ef, fb < tb);
-        store_hrow(Jt, et, tb < fb);
+    {
+        const End et = end_terms<DERIV>(Gtt, Btt, Gtt2, Btt2, At, Ct, Vt, Vf, Vt2, VV);
+        put2(rt, SC_P, et.P, et.Q);
+        if (WG && ghb) ghb[2 * nb + nl + l] = fma(et.P, et.P, et.Q * et.Q);
+        if (WJ) {
+            put2(rt, SC_PA, et.pa, et.pu); put2(rt, SC_PV, et.pv, et.qa); put2(rt, SC_QU, et.qu, et.qv);
+            store_hrow(Jt, et, tb < fb);
+        }
+        if (WH)
+            ht = end_hess(et, Gtt2, Btt2, At, Ct, K, Vt, Vf, VV, __ldg(lb + tb), __ldg(lb + nb + tb),
+                          __ldg(lb + 2 * nb + nl + l));
     }
     if (WH) {
-        const double *lb = R.lam + (size_t)b * N.m;
-        const double lPf = __ldg(lb + fb), lPt = __ldg(lb + tb);
-        const double lQf = __ldg(lb + nb + fb), lQt = __ldg(lb + nb + tb);
-        const double muf = __ldg(lb + 2 * nb + l), mut = __ldg(lb + 2 * nb + nl + l);
-        const double K = fma(G, G, Bm * Bm);          // A^2 + C^2 at both ends
-        const EndHess hf = end_hess(ef, Gff2, Bff2, Af, Cf, K, Vf, Vt, VV, lPf, lQf, muf);
-        const EndHess ht = end_hess(et, Gtt2, Btt2, At, Ct, K, Vt, Vf, VV, lPt, lQt, mut);
         const BranchHess h = branch_hess(hf, ht, Vf, Vt, Vf2, Vt2, VV);
         put2(rf, SC_HAA, h.haa, h.xf);                 // (Va_f,Va_f), (Vm_f, Va_f)
         put2(rt, SC_HAA, h.haa, h.xt);                 // (Va_t,Va_t), (Vm_t, Va_t)

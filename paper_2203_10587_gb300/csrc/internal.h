@@ -162,6 +162,7 @@ struct PersistLaunch {
     int occ_warps;          // 0, 16 or 24: resident warps per SM the registers must allow
     int grid;               // CTAs (SM count x resident CTAs per SM)
     int lag, ring;          // bus tiles trail branch tiles by `lag` states; ring > lag slots
+    int group;              // tiles of one kind and state per work item
     long long spin_limit;   // polls before a bounded wait gives up
     int force_timeout;      // testing only
     int *counters;

@@ -10,8 +10,10 @@ namespace exago {
 
 // ---------------------------------------------------------------------------------------------
 // Persistent schedule: one launch of numSMs x (resident CTAs per SM) blocks that claim work items
-// from a ticket counter until the list is empty.  For each state b there are Tbr branch tiles
-// and Tbu bus tiles of blockDim items.  The list is ordered
+// from a ticket counter until the list is empty.  A work item is `group` consecutive tiles of
+// one kind and one state (blockDim branches or buses each), so that the items' claims, waits and
+// signals are shared by several tiles.  For each state b there are Tbr branch items and Tbu bus
+// items.  The list is ordered
 //     Br(0) .. Br(L-1), [Br(L) Bu(0)], [Br(L+1) Bu(1)], ..., Bu(B-L) .. Bu(B-1)
 // so that bus tiles trail branch tiles by L states.  The branch partials of state b live in ring
 // slot b mod Rg of the workspace (Rg > L slots, sized to stay in L2), which keeps the
@@ -24,7 +26,7 @@ namespace exago {
 // word, skips its work and still signals, so the launch always ends.  Bus tile 0 of each state
 // also writes its objective; every bus tile writes the gradient entries of its buses.
 struct PersistParams {
-    int B, Tbr, Tbu, lag, ring, total;
+    int B, Tbr, Tbu, lag, ring, total, group;
     int *ctr;               // [1 + 2B]: ticket, branch tiles done per state, bus tiles done
     long long spin_limit;
     int force_timeout;      // testing: bus tiles wait for one branch tile more than exists
@@ -110,8 +112,10 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
                 s_ok = b < P.ring || bounded_wait(done_bu + (b - P.ring), P.Tbu, P.spin_limit,
                                                   N.status, ST_TIMEOUT_RING);
             __syncthreads();
-            const int l = tile * NT + threadIdx.x;
-            if (s_ok && l < N.nl) branch_item<WANT>(N, R, b, l, scr);
+            if (s_ok)
+                for (int l = tile * P.group * NT + threadIdx.x; l < N.nl && l < (tile + 1) * P.group * NT;
+                     l += NT)
+                    branch_item<WANT>(N, R, b, l, scr);
             __syncthreads();
             if (threadIdx.x == 0) red_release_add(done_br + b);
         } else {
@@ -120,9 +124,12 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
                                     ST_TIMEOUT_BUS);
             __syncthreads();
             if (s_ok) {
-                const int i = tile * NT + threadIdx.x;
-                if (WANT) bus_tile<WANT, BlockGroup>(N, R, b, tile * NT, scr, stage, cap);
-                if (i < N.nb && R.grad) grad_bus(N, R, b, i);
+                for (int k = 0; k < P.group; k++) {
+                    const int i0 = (tile * P.group + k) * NT;
+                    if (i0 >= N.nb) break;
+                    if (WANT) bus_tile<WANT, BlockGroup>(N, R, b, i0, scr, stage, cap);
+                    if (i0 + (int)threadIdx.x < N.nb && R.grad) grad_bus(N, R, b, i0 + threadIdx.x);
+                }
                 if (tile == 0 && R.f) obj_block(N, R, b, s_part);
             }
             __syncthreads();
@@ -218,8 +225,9 @@ int launch_eval_persistent(const DevNet &N, const EvalReq &R, const PersistLaunc
     if (R.B <= 0) return 0;
     PersistParams P;
     P.B = R.B;
-    P.Tbr = (N.nl + L.block - 1) / L.block;
-    P.Tbu = (N.nb + L.block - 1) / L.block;
+    P.group = L.group >= 1 ? L.group : 1;
+    P.Tbr = (N.nl + L.block * P.group - 1) / (L.block * P.group);
+    P.Tbu = (N.nb + L.block * P.group - 1) / (L.block * P.group);
     P.lag = L.lag < R.B ? L.lag : R.B;
     P.ring = L.ring;
     P.total = R.B * (P.Tbr + P.Tbu);

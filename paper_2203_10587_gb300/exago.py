@@ -51,7 +51,8 @@ class exago_config(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int), ("block", ctypes.c_int),
                 ("occupancy", ctypes.c_int), ("stage_records", ctypes.c_int), ("lag", ctypes.c_int),
                 ("ring", ctypes.c_int), ("chunk", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("spin_limit", ctypes.c_longlong), ("test_force_timeout", ctypes.c_int)]
+                ("spin_limit", ctypes.c_longlong), ("test_force_timeout", ctypes.c_int),
+                ("tile_group", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -319,9 +320,9 @@ def exago_eval_profile(h, batch: exago_batch, f=None, grad=None, gh=None, jval=N
 
 
 def exago_net_set_config(h, schedule=0, block=0, occupancy=0, stage_records=0, lag=0, ring=0,
-                         chunk=0, use_graph=0, spin_limit=0, test_force_timeout=0):
+                         chunk=0, use_graph=0, spin_limit=0, test_force_timeout=0, tile_group=0):
     c = exago_config(schedule, block, occupancy, stage_records, lag, ring, chunk, use_graph,
-                     spin_limit, test_force_timeout)
+                     spin_limit, test_force_timeout, tile_group)
     _check(lib().exago_net_set_config(h, ctypes.byref(c)))
 
 
