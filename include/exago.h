@@ -116,8 +116,9 @@ exago_status exago_net_ineq_bounds(exago_net_t net, double *hlo, double *hhi);
  * slot_ptr ([nb+1]), slot_nbr ([2 nl] other bus of each slot; slots are ordered by (bus, other
  * bus, branch)), slot_ref ([2 nl] record 2 l + end of each slot), bus_jP / bus_jQ (J row starts of
  * P_i / Q_i), bus_hA / bus_hM (H row starts of Va_i / Vm_i), bus_k (neighbours + 1), bus_nlow
- * (neighbours below i), bus_perm ([3][nb], the bus phase's thread order for tiles of 64, 128 and
- * 256 buses: each aligned tile sorted by descending degree), gen_ptr ([nb+1]) and gen_ord ([ng]).
+ * (neighbours below i), bus_perm ([4][nb], the bus phase's thread order for tiles of 32, 64, 128
+ * and 256 buses: each aligned tile sorted by descending degree), gen_ptr ([nb+1]) and gen_ord
+ * ([ng]).
  * *needed receives the size in bytes;
  * dst may be NULL to query it.  EINVAL for an unknown name or a small buffer.
  */
@@ -229,9 +230,11 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *             (branch, bus, fixup, gradient, objective) over the batch.  EXAGO_SCHED_PERSISTENT:
  *             one fused launch whose CTAs claim branch and bus tiles of all states from a work
  *             list (the batched evaluation of SCOPFLOW / SOPFLOW subproblems, Sec. V-A, VI-A).
- *   block     persistent: threads per CTA and items per tile (64, 128, 256; 0 = 128).
+ *   block     persistent: threads per CTA and items per tile (32, 64, 128, 256; 0 = 64, or 32
+ *             when the batch has fewer 64-branch tiles than twice the SM count).
  *   occupancy persistent: resident warps per SM the kernel's registers must allow (16 or 24;
- *             0 = the compiler's choice).  Higher occupancy can cost register spills.
+ *             8 = the compiler's choice of registers; 0 = 16).  Higher occupancy can cost
+ *             register spills.
  *   stage_records  EXAGO_STAGE_ON: a bus tile runs slot-parallel -- one thread per branch end
  *             reads its record (coalesced) and writes the neighbour's row entries, then one
  *             thread per bus sums its ends' diagonal terms from shared memory; DEFAULT / OFF:
@@ -279,7 +282,7 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg);
 
 /*
  * Autotuner: times the multi-kernel schedule, pipelined variants (three chunk sizes) and
- * persistent variants (block 64 / 128 / 256, occupancy 0 / 16 / 24 warps, 1 or 2 tiles per
+ * persistent variants (block 32 / 64 / 128 / 256, occupancy 8 / 16 / 24 warps, 1 or 2 tiles per
  * work item), each with and without slot-parallel bus tiles, on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
  * fastest for batches of this size (used by EXAGO_SCHED_AUTO).  Outputs are written as by
  * exago_eval_all.  *best (may be NULL) receives the choice.

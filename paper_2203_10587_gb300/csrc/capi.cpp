@@ -132,8 +132,8 @@ exago_status do_upload(exago_net *net) {
     d.jQ_end = (int)p.Jrowptr[2 * p.nb];
     d.hA_end = (int)p.Hrowptr[p.nb];
     d.hM_end = (int)p.Hrowptr[2 * p.nb];
-    for (int t = 0; t < 3; t++) {   // largest bus tile's rows (and records), 64/128/256 buses
-        const int T = 64 << t;
+    for (int t = 0; t < 4; t++) {   // largest bus tile's rows (and components), 32 to 256 buses
+        const int T = 32 << t;
         int64_t rows = 0, all = 0;
         for (int i0 = 0; i0 < p.nb; i0 += T) {
             const int i1 = i0 + T < p.nb ? i0 + T : p.nb;
@@ -280,8 +280,13 @@ Resolved resolve(exago_net *net, int B) {
         r.chunk = ch;
         r.pipe_ring = pr;
     }
-    r.block = (c.block == 64 || c.block == 256) ? c.block : 128;
-    r.occ_warps = (c.occupancy == 16 || c.occupancy == 24) ? c.occupancy : 0;
+    if (c.block == 32 || c.block == 64 || c.block == 128 || c.block == 256) {
+        r.block = c.block;
+    } else {   // automatic: 64-thread tiles, or 32 when a batch has too few of them to fill the GPU
+        const long tiles64 = (long)B * ((net->plan.nl + 63) / 64);
+        r.block = tiles64 < 2l * net->sm_count ? 32 : 64;
+    }
+    r.occ_warps = (c.occupancy == 8 || c.occupancy == 24) ? c.occupancy : 16;
     r.stage_recs = c.stage_records == EXAGO_STAGE_ON;
     const bool pers = r.schedule == EXAGO_SCHED_PERSISTENT;
     r.stage_cap = stage_cap(net, pers, r.block, r.occ_warps, r.stage_recs);
@@ -777,10 +782,11 @@ exago_status exago_net_set_config(exago_net_t net, const exago_config *cfg) {
     if (cfg->chunk < 0) return fail(EXAGO_EINVAL, "negative chunk");
     if (cfg->schedule == EXAGO_SCHED_PIPELINED && cfg->ring > 7)
         return fail(EXAGO_EINVAL, "pipelined ring must be at most 7 chunks");
-    if (cfg->block != 0 && cfg->block != 64 && cfg->block != 128 && cfg->block != 256)
-        return fail(EXAGO_EINVAL, "block must be 0, 64, 128 or 256");
-    if (cfg->occupancy != 0 && cfg->occupancy != 16 && cfg->occupancy != 24)
-        return fail(EXAGO_EINVAL, "occupancy must be 0, 16 or 24");
+    if (cfg->block != 0 && cfg->block != 32 && cfg->block != 64 && cfg->block != 128 &&
+        cfg->block != 256)
+        return fail(EXAGO_EINVAL, "block must be 0, 32, 64, 128 or 256");
+    if (cfg->occupancy != 0 && cfg->occupancy != 8 && cfg->occupancy != 16 && cfg->occupancy != 24)
+        return fail(EXAGO_EINVAL, "occupancy must be 0, 8, 16 or 24");
     if (cfg->stage_records < EXAGO_STAGE_DEFAULT || cfg->stage_records > EXAGO_STAGE_OFF)
         return fail(EXAGO_EINVAL, "unknown stage_records value");
     if (cfg->lag < 0 || cfg->ring < 0 || cfg->spin_limit < 0)
@@ -845,8 +851,8 @@ exago_status exago_net_autotune(exago_net_t net, const exago_batch *bt, double *
                 c.chunk = base.chunk * mul / 2 > 0 ? base.chunk * mul / 2 : 1;
                 cands.push_back(c);
             }
-            for (int block : {64, 128, 256})
-                for (int occw : {0, 16, 24})
+            for (int block : {32, 64, 128, 256})
+                for (int occw : {8, 16, 24})
                     for (int group : {1, 2}) {
                         exago_config c{};
                         c.schedule = EXAGO_SCHED_PERSISTENT;

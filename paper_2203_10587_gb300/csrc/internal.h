@@ -62,7 +62,7 @@ struct HostPlan {
     // columns of a J row, Vm columns follow); nlow_i = neighbours below i (position of the
     // diagonal among the Va columns).
     std::vector<int> bus_jP, bus_jQ, bus_hA, bus_hM, bus_k, bus_nlow;
-    // bus_perm: [3][nb]; row t holds, within every aligned tile of 64 << t buses, the tile's buses
+    // bus_perm: [4][nb]; row t holds, within every aligned tile of 32 << t buses, the tile's buses
     // by descending degree (then id), so that a warp of the bus phase walks slot lists of similar
     // length
     std::vector<int> bus_perm;
@@ -75,8 +75,8 @@ struct DevNet {
     int nb, nl, ng, n, m, nslot;
     int64_t nnzJ, nnzJg, nnzH, hpg;          // hpg: H position of (Pg_0, Pg_0)
     int jP_end, jQ_end, hA_end, hM_end;      // ends of the four row blocks of the bus rows
-    int stage_cap_rows[3];                   // shared-memory doubles of a bus tile of 64/128/256
-    int stage_cap_all[3];                    // buses: its row segments, or records plus rows
+    int stage_cap_rows[4];                   // shared-memory doubles of a bus tile of 32/64/128/256
+    int stage_cap_all[4];                    // buses: its row segments, or components plus rows
     double baseMVA;
     const int *f, *t;
     const double *Gff, *Bff, *Gtt, *Btt, *Gft, *Bft;   // pi-model admittances (no phase shift: ft == tf)
@@ -159,7 +159,8 @@ int launch_eval_pipelined(const DevNet &net, const EvalReq &req, const PipeLaunc
 // req.scratch holds `ring` state slots.
 struct PersistLaunch {
     int block;              // 64, 128 or 256 threads
-    int occ_warps;          // 0, 16 or 24: resident warps per SM the registers must allow
+    int occ_warps;          // 16 or 24: resident warps per SM the registers must allow; 8: the
+                            // compiler's choice
     int grid;               // CTAs (SM count x resident CTAs per SM)
     int lag, ring;          // bus tiles trail branch tiles by `lag` states; ring > lag slots
     int group;              // tiles of one kind and state per work item
@@ -176,7 +177,9 @@ int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes);
 // records from global memory and writes its rows directly.
 constexpr int kStageMaxDoubles = 9216;   // 72 KB
 constexpr int kDiagComps = 9;            // record components summed into a bus's diagonal
-__host__ __device__ inline int stage_index(int block) { return block == 64 ? 0 : block == 256 ? 2 : 1; }
+__host__ __device__ inline int stage_index(int block) {
+    return block == 32 ? 0 : block == 64 ? 1 : block == 256 ? 3 : 2;
+}
 int persist_allow_stage();   // persist.cu
 int bus_allow_stage();       // kernels.cu
 int bus_blocks_per_sm(size_t smem_bytes);   // k_bus blocks of 128 threads per SM (kernels.cu)

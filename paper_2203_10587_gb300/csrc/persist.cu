@@ -170,7 +170,8 @@ static int allow_stage_nt() {
 }
 
 int persist_allow_stage() {
-    int e = allow_stage_nt<64>();
+    int e = allow_stage_nt<32>();
+    if (e == 0) e = allow_stage_nt<64>();
     if (e == 0) e = allow_stage_nt<128>();
     if (e == 0) e = allow_stage_nt<256>();
     return e;
@@ -214,6 +215,7 @@ static int occupancy_nt(int occ_warps, size_t smem) {
 }
 
 int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes) {
+    if (block == 32) return occupancy_nt<32>(occ_warps, smem_bytes);
     if (block == 256) return occupancy_nt<256>(occ_warps, smem_bytes);
     if (block == 64) return occupancy_nt<64>(occ_warps, smem_bytes);
     return occupancy_nt<128>(occ_warps, smem_bytes);
@@ -241,7 +243,8 @@ int launch_eval_persistent(const DevNet &N, const EvalReq &R, const PersistLaunc
     if (e != cudaSuccess) return (int)e;
     int grid = L.grid < P.total ? L.grid : P.total;
     int rc;
-    if (L.block == 256) rc = launch_persist_nt<256>(N, R, P, grid, L.occ_warps, st);
+    if (L.block == 32) rc = launch_persist_nt<32>(N, R, P, grid, L.occ_warps, st);
+    else if (L.block == 256) rc = launch_persist_nt<256>(N, R, P, grid, L.occ_warps, st);
     else if (L.block == 64) rc = launch_persist_nt<64>(N, R, P, grid, L.occ_warps, st);
     else rc = launch_persist_nt<128>(N, R, P, grid, L.occ_warps, st);
     mark(hk, st, "end");

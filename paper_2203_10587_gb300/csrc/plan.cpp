@@ -208,14 +208,14 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
         p.bus_nlow[i] = rank(i, i);
     }
 
-    // ---- degree-sorted bus order inside every aligned bus tile of 64, 128 and 256 buses
+    // ---- degree-sorted bus order inside every aligned bus tile of 32, 64, 128 and 256 buses
     // (degree = branch ends at the bus, the trip count of its slot loop), so that each warp of a
     // tile holds buses of similar degree
     std::vector<int> ends_at(nb, 0);
     for (int l = 0; l < nl; l++) { ends_at[p.f[l]]++; ends_at[p.t[l]]++; }
-    p.bus_perm.resize(3 * (size_t)nb);
-    for (int t = 0; t < 3; t++) {
-        const int T = 64 << t;
+    p.bus_perm.resize(4 * (size_t)nb);
+    for (int t = 0; t < 4; t++) {
+        const int T = 32 << t;
         auto perm = p.bus_perm.begin() + (size_t)t * nb;
         for (int i = 0; i < nb; i++) perm[i] = i;
         for (int g0 = 0; g0 < nb; g0 += T) {

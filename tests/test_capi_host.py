@@ -146,10 +146,10 @@ def write_plan(net, g, slot_parallel=False):
 
 
 def check_write_plan(net, g):
-    perms = exago.exago_net_plan_array(net.h, "bus_perm").reshape(3, g.nb)
+    perms = exago.exago_net_plan_array(net.h, "bus_perm").reshape(4, g.nb)
     deg = np.bincount(np.concatenate([g.f, g.t]), minlength=g.nb)
     for t, perm in enumerate(perms):   # per tile size: each aligned tile permuted, by degree
-        T = 64 << t
+        T = 32 << t
         for g0 in range(0, g.nb, T):
             grp = perm[g0:g0 + T]
             assert sorted(grp) == list(range(g0, min(g0 + T, g.nb)))

@@ -30,6 +30,9 @@ CONFIGS = [
     dict(schedule=2, occupancy=24),                     # register-capped variant
     dict(schedule=2, block=64, occupancy=16),
     dict(schedule=2, block=64, occupancy=16, tile_group=1),
+    dict(schedule=2, block=32),
+    dict(schedule=2, block=32, occupancy=8, stage_records=1),
+    dict(schedule=2, block=256, occupancy=8),
     dict(schedule=2, block=128, tile_group=3, stage_records=1),
     dict(schedule=2, block=64, tile_group=4, lag=1, ring=2),       # smallest ring, grouped items
     dict(schedule=2, block=256, occupancy=16, stage_records=1),
