@@ -347,13 +347,19 @@ def run_serve(exago, synth, torch, np, dev, seconds):
     alone = sc.one_at_a_time(rng, 2000)
     sc.run(rng, 0.3)                                   # warm-up
     peak = sc.run(rng, seconds)
+    # the fastest arrival rate this Python client sustains (arrivals due at once, every one
+    # submitted as soon as a client of its grid is free): offered loads stay below it
+    client = sc.run(rng, min(seconds, 0.5), rate=1e9)
+    ref = min(peak["evals_per_s"], client["evals_per_s"])
     res = {"workload": "Poisson arrivals of B=1 requests from 64 clients on 118 / 2,000 / 10,000 / "
                        "70,000-bus grids (40/30/20/10%), one registered net per grid",
            "server": {"max_slots": SERVE_SLOTS, "streams": SERVE_STREAMS,
-                      "arena_mb": SERVE_BUDGET >> 20},
-           "one_at_a_time": alone, "closed_loop_peak": peak}
+                      "arena_mb": SERVE_BUDGET >> 20, "max_merge_states": 32},
+           "one_at_a_time": alone, "closed_loop_peak": peak,
+           "client_limit_per_s": client["evals_per_s"],
+           "loads_relative_to": "min(closed-loop peak, client limit)"}
     for frac in (0.5, 0.9):
-        res[f"load_{frac}"] = sc.run(rng, seconds, rate=frac * peak["evals_per_s"])
+        res[f"load_{frac}"] = sc.run(rng, seconds, rate=frac * ref)
     return res
 
 

@@ -230,8 +230,7 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *             (branch, bus, fixup, gradient, objective) over the batch.  EXAGO_SCHED_PERSISTENT:
  *             one fused launch whose CTAs claim branch and bus tiles of all states from a work
  *             list (the batched evaluation of SCOPFLOW / SOPFLOW subproblems, Sec. V-A, VI-A).
- *   block     persistent: threads per CTA and items per tile (32, 64, 128, 256; 0 = 64, or 32
- *             when the batch has fewer 64-branch tiles than twice the SM count).
+ *   block     persistent: threads per CTA and items per tile (32, 64, 128, 256; 0 = 64).
  *   occupancy persistent: resident warps per SM the kernel's registers must allow (16 or 24;
  *             8 = the compiler's choice of registers; 0 = 16).  Higher occupancy can cost
  *             register spills.
@@ -298,7 +297,11 @@ exago_status exago_net_autotune(exago_net_t net, const exago_batch *batch, doubl
  * queued requests in arrival order whenever one of max_slots slots is free and the request's
  * workspace fits in the server's device arena (device_mem_budget bytes, allocated once here), and
  * launches each on one of n_streams streams, so requests overlap on the GPU and new ones join as
- * others finish.  Serving allocates no device memory after exago_serve_create.
+ * others finish.  An admission takes the oldest queued request together with later queued
+ * requests for the same net and the same set of outputs, up to a number of states (32 by
+ * default; exago_serve_set_merge), and evaluates all their states in one launch through a
+ * device table of per-state pointers: each result is the one the request would get alone.
+ * Serving allocates no device memory after exago_serve_create.
  *   exago_serve_create   EINVAL for max_slots, n_streams < 1 or a zero budget; ENOMEM if the
  *                        arena cannot be allocated.  The queue holds up to 4 max_slots requests.
  *   exago_serve_register the server uses (does not own) the net; it must outlive the server.
@@ -325,6 +328,8 @@ exago_status exago_serve_register(exago_server_t server, exago_net_t net, int *n
 exago_status exago_serve_submit(exago_server_t server, int net_id, const exago_batch *request,
                                 double *f, double *grad, double *gh, double *jval, double *hval,
                                 double deadline_ms, uint64_t *ticket);
+/* States per merged admission (>= 1; 1 evaluates every request on its own).  EINVAL otherwise. */
+exago_status exago_serve_set_merge(exago_server_t server, int max_states);
 exago_status exago_serve_poll(exago_server_t server, uint64_t ticket, int *done);
 exago_status exago_serve_wait(exago_server_t server, uint64_t ticket, double timeout_ms);
 exago_status exago_serve_stats(exago_server_t server, double *p50_ms, double *p99_ms,

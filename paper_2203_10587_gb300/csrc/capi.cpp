@@ -280,12 +280,7 @@ Resolved resolve(exago_net *net, int B) {
         r.chunk = ch;
         r.pipe_ring = pr;
     }
-    if (c.block == 32 || c.block == 64 || c.block == 128 || c.block == 256) {
-        r.block = c.block;
-    } else {   // automatic: 64-thread tiles, or 32 when a batch has too few of them to fill the GPU
-        const long tiles64 = (long)B * ((net->plan.nl + 63) / 64);
-        r.block = tiles64 < 2l * net->sm_count ? 32 : 64;
-    }
+    r.block = (c.block == 32 || c.block == 128 || c.block == 256) ? c.block : 64;
     r.occ_warps = (c.occupancy == 8 || c.occupancy == 24) ? c.occupancy : 16;
     r.stage_recs = c.stage_records == EXAGO_STAGE_ON;
     const bool pers = r.schedule == EXAGO_SCHED_PERSISTENT;
@@ -449,7 +444,8 @@ exago_status pipe_resources_locked(exago_net *net, PipeLaunch &pl) {
 }
 
 exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad, double *gh,
-                  double *jval, double *hval, ProfileHook *hook = nullptr, bool allow_graph = true) {
+                  double *jval, double *hval, ProfileHook *hook = nullptr, bool allow_graph = true,
+                  const StateTab *tab = nullptr) {
     exago_status s = check_batch(net, bt, hval != nullptr);
     if (s != EXAGO_OK || bt->B == 0) return s;
     std::lock_guard<std::mutex> lk(net->mu);
@@ -467,11 +463,12 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
     R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
     R.stage_recs = rs.stage_recs;
     R.stage_cap = rs.stage_cap;
+    R.tab = tab;
     cudaStream_t stream = (cudaStream_t)bt->stream;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaError_t ce = cudaStreamIsCapturing(stream, &cap);
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamIsCapturing");
-    const bool graph = allow_graph && rs.use_graph && !hook && cap == cudaStreamCaptureStatusNone;
+    const bool graph = allow_graph && !tab && rs.use_graph && !hook && cap == cudaStreamCaptureStatusNone;
     if (rs.schedule == EXAGO_SCHED_KERNELS) {
         R.scratch = (double *)ws;
         int e = launch_eval(net->dev, R, stream, hook);
@@ -535,8 +532,8 @@ bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **de
 exago_status set_last_error(exago_status s, const std::string &msg) { return fail(s, msg); }
 
 exago_status eval_direct(exago_net_t net, const exago_batch *bt, double *f, double *grad,
-                         double *gh, double *jval, double *hval) {
-    return eval(net, bt, f, grad, gh, jval, hval, nullptr, false);
+                         double *gh, double *jval, double *hval, const StateTab *tab) {
+    return eval(net, bt, f, grad, gh, jval, hval, nullptr, false, tab);
 }
 
 }  // namespace exago

@@ -11,6 +11,41 @@ namespace exago {
 
 enum : int { W_G = 1, W_J = 2, W_H = 4 };
 
+// Where state b's inputs and outputs live: row b of the batch arrays, or entry b of a gathered
+// batch's state table.
+__device__ __forceinline__ const double *st_x(const DevNet &N, const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].x : R.x + (size_t)b * N.n;
+}
+__device__ __forceinline__ const double *st_lam(const DevNet &N, const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].lam : R.lam + (size_t)b * N.m;
+}
+__device__ __forceinline__ const uint8_t *st_mask(const DevNet &N, const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].mask : R.mask ? R.mask + (size_t)b * N.nl : nullptr;
+}
+__device__ __forceinline__ const double *st_pd(const DevNet &N, const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].pd_scale : R.pd_scale ? R.pd_scale + (size_t)b * N.nb : nullptr;
+}
+__device__ __forceinline__ double st_w(const EvalReq &R, int b) {
+    const double *w = R.tab ? R.tab[b].obj_weight : R.obj_weight ? R.obj_weight + b : nullptr;
+    return w ? *w : 1.0;
+}
+__device__ __forceinline__ double st_sigma(const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].sigma : R.sigma;
+}
+__device__ __forceinline__ double *st_f(const EvalReq &R, int b) { return R.tab ? R.tab[b].f : R.f + b; }
+__device__ __forceinline__ double *st_grad(const DevNet &N, const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].grad : R.grad + (size_t)b * N.n;
+}
+__device__ __forceinline__ double *st_gh(const DevNet &N, const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].gh : R.gh + (size_t)b * N.m;
+}
+__device__ __forceinline__ double *st_jval(const DevNet &N, const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].jval : R.jval + (size_t)b * N.nnzJ;
+}
+__device__ __forceinline__ double *st_hval(const DevNet &N, const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].hval : R.hval + (size_t)b * N.nnzH;
+}
+
 // ---------------------------------------------------------------------------------------------
 // sin and cos of the branch angle.  For |th| <= pi/4 -- every branch of a grid in normal
 // operation -- minimax polynomials in z = th^2 (Remez exchange; the coefficients are written by
@@ -207,11 +242,12 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     double *rf = scr + (size_t)__ldg(N.br_slot + l) * NCOMP;
     double *rt = scr + (size_t)__ldg(N.br_slot + nl + l) * NCOMP;
     const int fb = __ldg(N.f + l), tb = __ldg(N.t + l);
-    double *Jf = WJ ? R.jval + (size_t)b * N.nnzJ + N.nnzJg + 4 * (size_t)l : nullptr;
+    double *Jf = WJ ? st_jval(N, R, b) + N.nnzJg + 4 * (size_t)l : nullptr;
     double *Jt = WJ ? Jf + 4 * (size_t)nl : nullptr;
-    double *ghb = R.gh ? R.gh + (size_t)b * N.m : nullptr;
+    double *ghb = R.gh ? st_gh(N, R, b) : nullptr;
 
-    const bool on = R.mask == nullptr || R.mask[(size_t)b * nl + l] != 0;
+    const uint8_t *mk = st_mask(N, R, b);
+    const bool on = mk == nullptr || mk[l] != 0;
     if (!on) {   // out of service: every value of this branch is zero
 #pragma unroll
         for (int e = 0; e < 2; e++) {
@@ -226,7 +262,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
         return;
     }
 
-    const double *xb = R.x + (size_t)b * N.n;
+    const double *xb = st_x(N, R, b);
     const double Vaf = __ldg(xb + fb), Vat = __ldg(xb + tb);
     const double Vf = __ldg(xb + nb + fb), Vt = __ldg(xb + nb + tb);
     const double G = __ldg(N.Gft + l), Bm = __ldg(N.Bft + l);
@@ -244,7 +280,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
 
     // One end at a time, stored as soon as it is computed, so that fewer values are live at once
     // (the compiler would otherwise recompute products to save registers).
-    const double *lb = WH ? R.lam + (size_t)b * N.m : nullptr;
+    const double *lb = WH ? st_lam(N, R, b) : nullptr;
     const double K = WH ? fma(G, G, Bm * Bm) : 0.0;   // A^2 + C^2 at both ends
     EndHess hf{}, ht{};
     {
@@ -283,8 +319,8 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
 // Gradient entry of generator k's active power: w (2 c2 base^2 Pg + c1 base), with the network
 // constants c2g = 2 c2 base^2 and c1g = c1 base.
 __device__ __forceinline__ double grad_pg(const DevNet &N, const EvalReq &R, int b, int k) {
-    const double w = R.obj_weight ? R.obj_weight[b] : 1.0;
-    const double Pg = __ldg(R.x + (size_t)b * N.n + 2 * N.nb + k);
+    const double w = st_w(R, b);
+    const double Pg = __ldg(st_x(N, R, b) + 2 * N.nb + k);
     return w * fma(__ldg(N.c2g + k), Pg, __ldg(N.c1g + k));
 }
 
@@ -353,7 +389,7 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     const int nb = N.nb;
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
-    const double *xb = R.x + (size_t)b * N.n;
+    const double *xb = st_x(N, R, b);
     const double Vm = __ldg(xb + nb + i);
     const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
     const int k = __ldg(N.bus_k + i), nlow = __ldg(N.bus_nlow + i);
@@ -364,8 +400,9 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
     if (WG && R.gh) {
         const double VV = Vm * Vm;
         double Pd = __ldg(N.Pd + i), Qd = __ldg(N.Qd + i);
-        if (R.pd_scale) {                                     // load scenarios
-            const double sc = __ldg(R.pd_scale + (size_t)b * nb + i);
+        const double *pds = st_pd(N, R, b);
+        if (pds) {                                            // load scenarios
+            const double sc = __ldg(pds + i);
             Pd *= sc;
             Qd *= sc;
         }
@@ -376,7 +413,7 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
             gP -= __ldg(xb + 2 * nb + g);
             gQ -= __ldg(xb + 2 * nb + N.ng + g);
         }
-        double *ghb = R.gh + (size_t)b * N.m;
+        double *ghb = st_gh(N, R, b);
         ghb[i] = gP;
         ghb[nb + i] = gQ;
     }
@@ -390,14 +427,14 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
         }
     }
     if (WH) {
-        const double *lb = R.lam + (size_t)b * N.m;
+        const double *lb = st_lam(N, R, b);
         const double lP = __ldg(lb + i), lQ = __ldg(lb + nb + i);
         HA[nlow] = dAA;                                       // (Va_i, Va_i): last of row Va_i
         HM[nlow] = dUA;                                       // (Vm_i, Va_i)
         HM[k + nlow] = dUU + fma(lP, twice(Gs), -(lQ * twice(Bs)));   // (Vm_i, Vm_i): last
         if (g1 > g0) {
-            const double sw = R.sigma * (R.obj_weight ? R.obj_weight[b] : 1.0);
-            double *Hb = R.hval + (size_t)b * N.nnzH + N.hpg;
+            const double sw = st_sigma(R, b) * st_w(R, b);
+            double *Hb = st_hval(N, R, b) + N.hpg;
             for (int q = g0; q < g1; q++) {
                 const int g = __ldg(N.gen_ord + q);
                 Hb[g] = sw * __ldg(N.c2g + g);
@@ -587,8 +624,8 @@ __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int 
     const bool slotpar = R.stage_recs && kDiagComps * (S1 - S0) + LROWS <= cap;
     const int LD = slotpar ? kDiagComps * (S1 - S0) : 0;
     const bool staged = (WJ || WH) && LD + LROWS <= cap;
-    double *Jb = WJ ? R.jval + (size_t)b * N.nnzJ : nullptr;
-    double *Hb = WH ? R.hval + (size_t)b * N.nnzH : nullptr;
+    double *Jb = WJ ? st_jval(N, R, b) : nullptr;
+    double *Hb = WH ? st_hval(N, R, b) : nullptr;
     double *rows = stage + LD;
     TileRows T{};
     T.p0 = p0; T.q0 = q0; T.a0 = a0; T.m0 = m0;
@@ -622,7 +659,7 @@ __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int 
 
 // Gradient entries owned by bus i: Va_i and Vm_i (zero) and, for each generator at i, Pg and Qg.
 __device__ __forceinline__ void grad_bus(const DevNet &N, const EvalReq &R, int b, int i) {
-    double *gb = R.grad + (size_t)b * N.n;
+    double *gb = st_grad(N, R, b);
     gb[i] = 0.0;
     gb[N.nb + i] = 0.0;
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
@@ -639,7 +676,7 @@ __device__ __forceinline__ void grad_bus(const DevNet &N, const EvalReq &R, int 
 // shared memory.
 constexpr int OBJ_LANES = 256;
 __device__ __forceinline__ void obj_block(const DevNet &N, const EvalReq &R, int b, double *part) {
-    const double *Pg = R.x + (size_t)b * N.n + 2 * N.nb;
+    const double *Pg = st_x(N, R, b) + 2 * N.nb;
     for (int v = threadIdx.x; v < OBJ_LANES; v += blockDim.x) {
         double acc = 0.0;
         for (int k = v; k < N.ng; k += OBJ_LANES) {
@@ -653,7 +690,7 @@ __device__ __forceinline__ void obj_block(const DevNet &N, const EvalReq &R, int
         for (int v = threadIdx.x; v < w; v += blockDim.x) part[v] += part[v + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) R.f[b] = (R.obj_weight ? R.obj_weight[b] : 1.0) * part[0];
+    if (threadIdx.x == 0) *st_f(R, b) = st_w(R, b) * part[0];
     __syncthreads();
 }
 

@@ -90,7 +90,18 @@ struct DevNet {
     int *status;                // device status word (host-mapped)
 };
 
-// What one evaluation call asks for.
+// One state of a gathered batch (serving: states of several requests in one launch): where its
+// inputs and outputs live.  Absent inputs are nullptr (no mask, unit load scale, weight 1).
+struct StateTab {
+    const double *x, *lam;
+    const uint8_t *mask;
+    const double *pd_scale, *obj_weight;   // obj_weight: this state's weight
+    double sigma;
+    double *f, *grad, *gh, *jval, *hval;   // this state's outputs (f: one value)
+};
+
+// What one evaluation call asks for.  With tab, state b's inputs and outputs are tab[b]'s, and the
+// batch pointers below only say which outputs are wanted (non-null) and which inputs exist.
 struct EvalReq {
     int B;
     const double *x, *lam;
@@ -103,6 +114,7 @@ struct EvalReq {
                                 // in the multi-kernel and pipelined schedules
     int stage_recs;             // bus tiles read their records slot-parallel into shared memory
     int stage_cap;              // shared-memory doubles of one bus tile (records and rows)
+    const StateTab *tab;        // device table of B states, or nullptr
 };
 
 // Pipelined schedule (kernels.cu): the batch in chunks; the branch kernel of a chunk runs on the
@@ -188,8 +200,10 @@ int bus_blocks_per_sm(size_t smem_bytes);   // k_bus blocks of 128 threads per S
 // thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.
 bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **dev, int *device);
 exago_status set_last_error(exago_status s, const std::string &msg);
-// exago_eval_all without the graph cache (serving: every request has its own buffers).
+// exago_eval_all without the graph cache (serving: every request has its own buffers).  With
+// tab (a device table of bt->B states), state b's inputs and outputs are tab[b]'s; bt and the
+// output pointers then only say which inputs exist and which outputs are wanted.
 exago_status eval_direct(exago_net_t net, const exago_batch *bt, double *f, double *grad,
-                         double *gh, double *jval, double *hval);
+                         double *gh, double *jval, double *hval, const StateTab *tab = nullptr);
 
 }  // namespace exago

@@ -83,7 +83,7 @@ __global__ void k_grad(const DevNet N, const EvalReq R, int b0) {
     if (j >= N.n) return;
     const int b = b0 + blockIdx.y;
     const int k = j - 2 * N.nb;
-    R.grad[(size_t)b * N.n + j] = (k >= 0 && k < N.ng) ? grad_pg(N, R, b, k) : 0.0;
+    st_grad(N, R, b)[j] = (k >= 0 && k < N.ng) ? grad_pg(N, R, b, k) : 0.0;
 }
 
 __global__ void __launch_bounds__(OBJ_LANES) k_obj(const DevNet N, const EvalReq R, int b0) {

@@ -4,11 +4,14 @@
 // subproblems run side by side (EMPAR, Sec. V-A).
 //
 // Continuous batching: a scheduler thread admits queued requests whenever a slot and enough of
-// the device arena are free -- not when a whole batch has drained -- and launches each on one of
-// the server's streams, so requests that arrive while others run overlap with them on the GPU.
-// Each request's scratch is carved from one arena allocated at creation, so serving allocates
-// nothing afterwards.  Completion is signalled by a host function queued behind the request's
-// kernels (it only sets a flag; CUDA calls are not allowed there).
+// the device arena are free -- not when a whole batch has drained -- and launches each admission
+// on one of the server's streams, so requests that arrive while others run overlap with them on
+// the GPU.  An admission takes the oldest queued request together with later queued requests for
+// the same grid and the same outputs, up to a state budget, and evaluates all their states in one
+// launch through a device table of per-state pointers (inputs and outputs stay where each client
+// put them).  Each admission's scratch and table are carved from one arena allocated at creation,
+// so serving allocates no device memory afterwards.  Completion is signalled by a host function
+// queued behind the kernels (it only sets a flag; CUDA calls are not allowed there).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,19 +35,27 @@ using Clock = std::chrono::steady_clock;
 
 enum ReqState { RQ_QUEUED, RQ_RUNNING, RQ_DONE };
 
+struct Group;
+
 struct Request {
     uint64_t ticket = 0;
     int net_id = 0;
     exago_batch batch{};
     double *f = nullptr, *grad = nullptr, *gh = nullptr, *jval = nullptr, *hval = nullptr;
-    size_t ws_bytes = 0, ws_off = 0;
+    size_t ws_bytes = 0;            // workspace of this request alone
     bool has_deadline = false;
     Clock::time_point submitted, deadline, finished;
-    int stream = -1;
     cudaEvent_t ready = nullptr;    // recorded on the caller's stream at submission
     ReqState state = RQ_QUEUED;
     exago_status status = EXAGO_OK;
     std::string err;
+};
+
+// One admission: the requests evaluated by one launch, its arena range and its stream.
+struct Group {
+    std::vector<Request *> members;
+    size_t ws_off = 0, ws_bytes = 0;
+    int stream = -1;
     struct exago_server *server = nullptr;
     std::atomic<int> gpu_done{0};   // set by the host function queued behind the kernels
 };
@@ -103,6 +114,8 @@ struct exago_server {
     std::vector<exago_net_t> nets;
     std::deque<Request *> queue;
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::vector<std::unique_ptr<Group>> running_groups;
+    int max_merge = 32;            // states per launch when requests are merged (1: no merging)
     std::vector<double> latencies_ms;
     uint64_t next_ticket = 1;
     int next_stream = 0;
@@ -134,12 +147,49 @@ void wake(exago_server *S) {
     S->cv_wake.notify_one();
 }
 
-// Host function behind a request's kernels: flags completion and wakes the scheduler.  It takes
-// only wake_mu, so a CUDA call that waits for it can never wait on the server's lock.
+// Host function behind an admission's kernels: flags completion and wakes the scheduler.  It
+// takes only wake_mu, so a CUDA call that waits for it can never wait on the server's lock.
 void CUDART_CB on_done(void *p) {
-    Request *r = (Request *)p;
-    r->gpu_done.store(1, std::memory_order_release);
-    wake(r->server);
+    Group *g = (Group *)p;
+    g->gpu_done.store(1, std::memory_order_release);
+    wake(g->server);
+}
+
+// Whether two requests can share a launch: same grid and the same outputs (the launch computes
+// one set of outputs for all its states).
+bool same_shape(const Request &a, const Request &b) {
+    return a.net_id == b.net_id && !a.f == !b.f && !a.grad == !b.grad && !a.gh == !b.gh &&
+           !a.jval == !b.jval && !a.hval == !b.hval;
+}
+
+size_t round256(size_t v) { return (v + 255) / 256 * 256; }
+
+// The per-state table of a merged admission (host copy).
+std::vector<exago::StateTab> state_table(exago_net_t net, const std::vector<Request *> &members) {
+    const exago::HostPlan *p = nullptr;
+    const exago::DevNet *d = nullptr;
+    int dev = 0;
+    exago::net_internal_view(net, &p, &d, &dev);
+    std::vector<exago::StateTab> tab;
+    for (const Request *r : members) {
+        const exago_batch &bt = r->batch;
+        for (int j = 0; j < bt.B; j++) {
+            exago::StateTab e{};
+            e.x = bt.x + (size_t)j * p->n;
+            e.lam = bt.lambda ? bt.lambda + (size_t)j * p->m : nullptr;
+            e.mask = bt.mask ? bt.mask + (size_t)j * p->nl : nullptr;
+            e.pd_scale = bt.pd_scale ? bt.pd_scale + (size_t)j * p->nb : nullptr;
+            e.obj_weight = bt.obj_weight ? bt.obj_weight + j : nullptr;
+            e.sigma = bt.obj_factor;
+            e.f = r->f ? r->f + j : nullptr;
+            e.grad = r->grad ? r->grad + (size_t)j * p->n : nullptr;
+            e.gh = r->gh ? r->gh + (size_t)j * p->m : nullptr;
+            e.jval = r->jval ? r->jval + (size_t)j * p->nnzJ : nullptr;
+            e.hval = r->hval ? r->hval + (size_t)j * p->nnzH : nullptr;
+            tab.push_back(e);
+        }
+    }
+    return tab;
 }
 
 // Caller holds S->mu.
@@ -158,6 +208,88 @@ void finish_locked(exago_server *S, Request *r, exago_status st, const std::stri
     S->cv_done.notify_all();
 }
 
+// Admits the oldest queued request, merged with later compatible ones when their states fit the
+// merge budget and the arena.  Caller holds S->mu.  False when nothing could be admitted.
+bool admit_locked(exago_server *S) {
+    Request *head = S->queue.front();
+    exago_net_t net = S->nets[head->net_id];
+    std::vector<Request *> members{head};
+    int Btot = head->batch.B;
+    if (S->max_merge > 1)
+        for (auto it = std::next(S->queue.begin()); it != S->queue.end(); ++it) {
+            Request *q = *it;
+            if (same_shape(*q, *head) && Btot + q->batch.B <= S->max_merge) {
+                members.push_back(q);
+                Btot += q->batch.B;
+            }
+        }
+    // the merged admission if the arena holds it, else the oldest request alone
+    size_t off = 0, bytes = 0, tab_bytes = 0;
+    for (;;) {
+        if (members.size() == 1) {
+            bytes = head->ws_bytes;
+            tab_bytes = 0;
+        } else {
+            size_t ws = 0;
+            if (exago_eval_workspace_size(net, Btot, &ws) != EXAGO_OK) ws = (size_t)-1 / 2;
+            tab_bytes = round256((size_t)Btot * sizeof(exago::StateTab));
+            bytes = tab_bytes + round256(ws > 0 ? ws : 256);
+        }
+        if (S->arena.alloc(bytes, &off)) break;
+        if (members.size() == 1) return false;     // memory-gated: wait for a release
+        members.resize(1);
+        Btot = head->batch.B;
+    }
+    for (Request *m : members) S->queue.erase(std::find(S->queue.begin(), S->queue.end(), m));
+    std::unique_ptr<Group> g(new Group());
+    g->members = members;
+    g->ws_off = off;
+    g->ws_bytes = bytes;
+    g->server = S;
+    g->stream = S->next_stream;
+    S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
+    cudaStream_t st = S->streams[g->stream];
+    // inputs produced on the callers' streams before submission are ready first
+    exago_status rc = EXAGO_OK;
+    for (Request *m : members) {
+        cudaError_t ew = cudaStreamWaitEvent(st, m->ready, 0);
+        if (ew != cudaSuccess) rc = exago::set_last_error(EXAGO_ECUDA, cudaGetErrorString(ew));
+    }
+    if (rc == EXAGO_OK) {
+        exago_batch bt = head->batch;
+        bt.stream = st;
+        bt.workspace = S->arena_base + off + tab_bytes;
+        bt.workspace_bytes = bytes - tab_bytes;
+        if (members.size() == 1) {
+            rc = exago::eval_direct(net, &bt, head->f, head->grad, head->gh, head->jval, head->hval);
+        } else {
+            // per-state table: copied from pageable memory, so the host vector may go afterwards
+            const std::vector<exago::StateTab> tab = state_table(net, members);
+            exago::StateTab *dtab = (exago::StateTab *)(S->arena_base + off);
+            cudaError_t ec = cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(tab[0]),
+                                             cudaMemcpyHostToDevice, st);
+            bt.B = Btot;
+            rc = ec != cudaSuccess ? exago::set_last_error(EXAGO_ECUDA, cudaGetErrorString(ec))
+                                   : exago::eval_direct(net, &bt, head->f, head->grad, head->gh,
+                                                        head->jval, head->hval, dtab);
+        }
+    }
+    cudaError_t e = rc == EXAGO_OK ? cudaLaunchHostFunc(st, on_done, g.get()) : cudaSuccess;
+    if (rc != EXAGO_OK || e != cudaSuccess) {
+        // nothing of this admission is queued behind the host function: release at once (the
+        // stream may still read the arena range if a launch went out, so wait for it first)
+        cudaStreamSynchronize(st);
+        S->arena.release(off, bytes);
+        const std::string msg = rc != EXAGO_OK ? exago_last_error() : cudaGetErrorString(e);
+        for (Request *m : members) finish_locked(S, m, rc != EXAGO_OK ? rc : EXAGO_ECUDA, msg);
+        return true;
+    }
+    for (Request *m : members) m->state = RQ_RUNNING;
+    S->running++;
+    S->running_groups.push_back(std::move(g));
+    return true;
+}
+
 void worker_loop(exago_server *S) {
     cudaSetDevice(S->device);
     uint64_t seen = 0;
@@ -167,14 +299,17 @@ void worker_loop(exago_server *S) {
         {
             std::unique_lock<std::mutex> lk(S->mu);
             if (S->stop) return;
-            // retire finished requests: free their slot and arena range
-            for (auto &kv : S->reqs) {
-                Request *r = kv.second.get();
-                if (r->state == RQ_RUNNING && r->gpu_done.load(std::memory_order_acquire)) {
-                    S->arena.release(r->ws_off, r->ws_bytes);
+            // retire finished admissions: free their slot and arena range
+            for (auto it = S->running_groups.begin(); it != S->running_groups.end();) {
+                Group *g = it->get();
+                if (g->gpu_done.load(std::memory_order_acquire)) {
+                    S->arena.release(g->ws_off, g->ws_bytes);
                     S->running--;
-                    finish_locked(S, r, EXAGO_OK, "");
+                    for (Request *m : g->members) finish_locked(S, m, EXAGO_OK, "");
+                    it = S->running_groups.erase(it);
                     progress = true;
+                } else {
+                    ++it;
                 }
             }
             // expire queued requests whose deadline passed
@@ -189,35 +324,7 @@ void worker_loop(exago_server *S) {
                 }
             }
             // admit in arrival order while a slot and arena memory are free
-            while (!S->queue.empty() && S->running < S->max_slots) {
-                Request *r = S->queue.front();
-                size_t off = 0;
-                if (!S->arena.alloc(r->ws_bytes, &off)) break;   // memory-gated: wait for a release
-                S->queue.pop_front();
-                r->ws_off = off;
-                r->stream = S->next_stream;
-                S->next_stream = (S->next_stream + 1) % (int)S->streams.size();
-                r->batch.workspace = S->arena_base + off;
-                r->batch.workspace_bytes = r->ws_bytes;
-                r->batch.stream = S->streams[r->stream];
-                // inputs produced on the caller's stream before submission are ready first
-                cudaError_t ew = cudaStreamWaitEvent(S->streams[r->stream], r->ready, 0);
-                exago_status st = ew != cudaSuccess ? exago::set_last_error(EXAGO_ECUDA, cudaGetErrorString(ew))
-                                                    : exago::eval_direct(S->nets[r->net_id], &r->batch, r->f, r->grad,
-                                                     r->gh, r->jval, r->hval);
-                cudaError_t e = st == EXAGO_OK
-                                    ? cudaLaunchHostFunc(S->streams[r->stream], on_done, r)
-                                    : cudaSuccess;
-                if (st != EXAGO_OK || e != cudaSuccess) {
-                    S->arena.release(off, r->ws_bytes);
-                    finish_locked(S, r, st != EXAGO_OK ? st : EXAGO_ECUDA,
-                                  st != EXAGO_OK ? exago_last_error() : cudaGetErrorString(e));
-                } else {
-                    r->state = RQ_RUNNING;
-                    S->running++;
-                }
-                progress = true;
-            }
+            while (!S->queue.empty() && S->running < S->max_slots && admit_locked(S)) progress = true;
             for (Request *q : S->queue)
                 if (q->has_deadline && q->deadline < until) until = q->deadline;
         }
@@ -318,13 +425,12 @@ exago_status exago_serve_submit(exago_server_t S, int net_id, const exago_batch 
     r->net_id = net_id;
     r->batch = *req;
     r->f = f; r->grad = grad; r->gh = gh; r->jval = jval; r->hval = hval;
-    r->ws_bytes = ws > 0 ? ws : 256;
+    r->ws_bytes = round256(ws > 0 ? ws : 256);
     r->submitted = Clock::now();
     if (deadline_ms > 0) {
         r->has_deadline = true;
         r->deadline = r->submitted + std::chrono::microseconds((long long)(deadline_ms * 1000.0));
     }
-    r->server = S;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->queue.size() >= S->max_queue || S->free_events.empty())
@@ -340,6 +446,13 @@ exago_status exago_serve_submit(exago_server_t S, int net_id, const exago_batch 
         S->reqs[r->ticket] = std::move(r);
     }
     wake(S);
+    return EXAGO_OK;
+}
+
+exago_status exago_serve_set_merge(exago_server_t S, int max_states) {
+    if (!S || max_states < 1) return sfail(EXAGO_EINVAL, "need a server and max_states >= 1");
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->max_merge = max_states;
     return EXAGO_OK;
 }
 

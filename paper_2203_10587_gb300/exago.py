@@ -32,7 +32,8 @@ EXPORTS = [
     "exago_eval_hvp", "exago_eval_all_static",
     "exago_eval_profile", "exago_net_set_config", "exago_net_get_config", "exago_net_autotune",
     "exago_net_check", "exago_serve_create", "exago_serve_register", "exago_serve_submit",
-    "exago_serve_poll", "exago_serve_wait", "exago_serve_stats", "exago_serve_destroy",
+    "exago_serve_set_merge", "exago_serve_poll", "exago_serve_wait", "exago_serve_stats",
+    "exago_serve_destroy",
 ]
 
 SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
@@ -116,6 +117,7 @@ def lib():
                 "exago_serve_register": ([vp, vp, ctypes.POINTER(i32)], i32),
                 "exago_serve_submit": ([vp, i32, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], i32),
+                "exago_serve_set_merge": ([vp, i32], i32),
                 "exago_serve_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(i32)], i32),
                 "exago_serve_wait": ([vp, ctypes.c_uint64, ctypes.c_double], i32),
                 "exago_serve_stats": ([vp, ctypes.POINTER(ctypes.c_double),
@@ -367,6 +369,10 @@ def exago_serve_submit(s, net_id: int, batch: exago_batch, f=None, grad=None, gh
                                     _out(gh), _out(jval), _out(hval), float(deadline_ms),
                                     ctypes.byref(t)))
     return t.value
+
+
+def exago_serve_set_merge(s, max_states: int):
+    _check(lib().exago_serve_set_merge(s, int(max_states)))
 
 
 def exago_serve_poll(s, ticket: int) -> bool:

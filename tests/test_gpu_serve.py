@@ -32,32 +32,38 @@ class Req:
         self.out = net.outputs(batch.B)
 
     def host(self):
-        return {k: v.cpu().numpy() for k, v in self.out.items()}
+        return {k: v.cpu().numpy() for k, v in self.out.items() if v is not None}
 
 
 def alone(ex, net, r):
     import torch
-    out = net.outputs(r.batch.B)
+    out = net.outputs(r.batch.B, hess=r.out.get("hval") is not None)
     net.eval_all(r.bt, out)
     torch.cuda.synchronize()
-    return {k: v.cpu().numpy() for k, v in out.items()}
+    return {k: v.cpu().numpy() for k, v in out.items() if v is not None}
 
 
-def test_mixed_grids_same_alone_and_in_the_mix(ex, oracle_mod):
+@pytest.mark.parametrize("merge", [1, 32])
+def test_mixed_grids_same_alone_and_in_the_mix(ex, oracle_mod, merge):
+    """Requests on three grids, with their own masks, load scales, weights and objective factors,
+    some without the Hessian: merged or not, every result equals the request evaluated alone."""
     import torch
     grids = [synth.grid_sized(5, 118), synth.grid_2000(), synth.grid_sized(6, 10_000)]
     nets = [ex.Net(g) for g in grids]
     srv = ex.exago_serve_create(1 << 30, max_slots=6, n_streams=3)
     try:
+        ex.exago_serve_set_merge(srv, merge)
         ids = [ex.exago_serve_register(srv, n.h) for n in nets]
         rng = np.random.default_rng(11)
         reqs, tickets = [], []
-        for k in range(18):
+        for k in range(24):
             gi = int(rng.integers(3))
             B = int(rng.integers(1, 9))
-            b = synth.random_batch(100 + k, grids[gi], B, masks=True, pd_scale=True,
-                                   obj_weight=True, sigma=0.8)
+            b = synth.random_batch(100 + k, grids[gi], B, masks=bool(k % 2), pd_scale=bool(k % 3),
+                                   obj_weight=bool(k % 4), sigma=float(rng.choice([0.0, 0.8, 1.0])))
             r = Req(ex, nets[gi], b)
+            if k % 5 == 0:
+                r.out["hval"] = None           # a different set of outputs: never merged with the rest
             t = ex.exago_serve_submit(srv, ids[gi], r.bt, **r.out)
             reqs.append((gi, r))
             tickets.append(t)
@@ -68,7 +74,7 @@ def test_mixed_grids_same_alone_and_in_the_mix(ex, oracle_mod):
             got, ref = r.host(), alone(ex, nets[gi], r)
             for key in ref:
                 np.testing.assert_array_equal(got[key], ref[key], err_msg=key)
-        gi, r = reqs[0]
+        gi, r = next((gi, r) for gi, r in reqs if r.out["hval"] is not None)
         compare_instance(r.host(), 0, oracle_eval(oracle_mod, grids[gi], r.batch, 0), "served")
         p50, p99, n = ex.exago_serve_stats(srv)
         assert n == len(tickets) and 0 < p50 <= p99
@@ -153,6 +159,8 @@ def test_serve_argument_errors(ex):
         ex.exago_serve_create(1 << 20, 0, 1)
     srv = ex.exago_serve_create(1 << 20, 1, 1)
     try:
+        with pytest.raises(ex.ExagoError):
+            ex.exago_serve_set_merge(srv, 0)
         g = synth.grid_30bus()
         net = ex.Net(g)
         r = Req(ex, net, synth.random_batch(1, g, 1))
