@@ -316,7 +316,7 @@ class ServeClients:
                 t_next = t0
                 while True:
                     t_next += float(rng.exponential(1.0 / rate))
-                    if t_next - t0 >= seconds:
+                    if t_next - t0 >= seconds or time.perf_counter() - t0 >= seconds:
                         break
                     while time.perf_counter() < t_next:
                         pass
