@@ -147,23 +147,45 @@ class ClockSampler:
 
 # ---- CPU oracle ----------------------------------------------------------------------------------
 
+class OracleRunner:
+    """The CPU oracle over the batch's states on a pool of host threads (ctypes releases the GIL
+    during each evaluation)."""
+
+    def __init__(self, grid, batch, threads: int):
+        import concurrent.futures as cf
+        from oracle import acopf
+        acopf.build()
+        self.acopf, self.batch = acopf, batch
+        self.onet = acopf.OracleNet(grid)
+        self.pool = cf.ThreadPoolExecutor(max_workers=threads)
+        self.next = 0
+        self.one(0)
+
+    def one(self, i):
+        b = i % self.batch.B
+        self.acopf.evaluate(self.onet, self.batch.x[b], self.batch.lam[b], self.batch.mask[b], None,
+                            1.0, self.batch.sigma)
+
+    def rate(self, n_evals: int):
+        """Evaluations per second over the next n_evals states (cycling the batch)."""
+        idx = range(self.next, self.next + n_evals)
+        self.next += n_evals
+        t0 = time.perf_counter()
+        list(self.pool.map(self.one, idx))
+        dt = time.perf_counter() - t0
+        return n_evals / dt, dt
+
+    def close(self):
+        self.pool.shutdown()
+
+
 def oracle_rate(grid, batch, n_evals: int, threads: int):
-    """Oracle evaluations per second over n_evals instances (cycling the batch) on `threads`."""
-    import concurrent.futures as cf
-    from oracle import acopf
-    acopf.build()
-    onet = acopf.OracleNet(grid)
-
-    def one(i):
-        b = i % batch.B
-        acopf.evaluate(onet, batch.x[b], batch.lam[b], batch.mask[b], None, 1.0, batch.sigma)
-
-    one(0)
-    t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
-        list(ex.map(one, range(n_evals)))
-    dt = time.perf_counter() - t0
-    return n_evals / dt, dt
+    """Oracle evaluations per second over n_evals states on `threads` host threads."""
+    runner = OracleRunner(grid, batch, threads)
+    try:
+        return runner.rate(n_evals)
+    finally:
+        runner.close()
 
 
 def run_reference(args, rank: int):
@@ -175,14 +197,14 @@ def run_reference(args, rank: int):
     batch = synth.contingency_batch(3, grid, args.B)
     cores = os.cpu_count() or 1
     per_step = cores
+    runner = OracleRunner(grid, batch, cores)
     for _ in range(args.warmup):
-        oracle_rate(grid, batch, per_step, cores)
-    times = []
+        runner.rate(per_step)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _, dt = oracle_rate(grid, batch, per_step, cores)
-        times.append(dt)
+        runner.rate(per_step)
     total = time.perf_counter() - t0
+    runner.close()
     value = args.steps * per_step / total
     sample = f"{per_step} of the {args.B} contingency states per step (one per host thread)"
     print(json.dumps({
