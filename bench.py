@@ -35,8 +35,8 @@ B_DEFAULT = 512
 N_INPUT_SETS = 4
 # FP64 work per unit with every output requested, counted from the kernel source on the fast
 # sincos path (an FMA counts 2 flops; doublings run on the integer pipe and count nothing):
-# (flops, instructions).  Per 2000-bus state they sum to 536,000 flops / 364,500 instructions.
-FP64_PER_BRANCH = (173, 113)   # sincos, flows, 16 derivatives, h and its J row, Hessian fold
+# (flops, instructions).  Per 2000-bus state they sum to 522,500 flops / 353,700 instructions.
+FP64_PER_BRANCH = (168, 109)   # sincos, flows, 16 derivatives, h and its J row, Hessian fold
 FP64_PER_SLOT = (9, 9)         # a branch end's record summed into its bus (all but the first)
 FP64_PER_BUS = (16, 12)        # shunt, load and diagonal terms of one bus
 FP64_PER_GEN = (12, 9)         # balance, cost Hessian, gradient and objective terms of a generator

@@ -81,9 +81,9 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
         const double lPf = __ldg(lb + fb), lPt = __ldg(lb + tb);
         const double lQf = __ldg(lb + nb + fb), lQt = __ldg(lb + nb + tb);
         const double muf = __ldg(lb + 2 * nb + l), mut = __ldg(lb + 2 * nb + nl + l);
-        const double K = fma(G, G, Bm * Bm);
-        const EndHess hf = end_hess(ef, Gff2, Bff2, Af, Cf, K, Vf, Vt, VV, lPf, lQf, muf);
-        const EndHess ht = end_hess(et, Gtt2, Btt2, At, Ct, K, Vt, Vf, VV, lPt, lQt, mut);
+        const double K = __ldg(N.Kft + l);
+        const EndHess hf = end_hess(ef, Gff2, Bff2, Af, Cf, K, Vf, Vt, lPf, lQf, muf);
+        const EndHess ht = end_hess(et, Gtt2, Btt2, At, Ct, K, Vt, Vf, lPt, lQt, mut);
         const BranchHess h = branch_hess(hf, ht, Vf, Vt, Vf2, Vt2, VV);
         const double haa = h.haa, xf = h.xf, xt = h.xt, mff = h.mff, mtt = h.mtt, mft = h.mft;
         const double *ub = A.v + (size_t)b * N.n;

@@ -162,11 +162,11 @@ exago_status do_upload(exago_net *net) {
     if ((s = upload(net, p.x, &x)) != EXAGO_OK) return s;
     if ((s = upload(net, p.b, &b)) != EXAGO_OK) return s;
     if ((s = upload(net, p.tap, &tap)) != EXAGO_OK) return s;
-    double *Y[10];
-    for (int k = 0; k < 10; k++)
+    double *Y[11];
+    for (int k = 0; k < 11; k++)
         if ((s = alloc_dev(net, (size_t)p.nl * sizeof(double), &Y[k])) != EXAGO_OK) return s;
     d.Gff = Y[0]; d.Bff = Y[1]; d.Gtt = Y[2]; d.Btt = Y[3]; d.Gft = Y[4]; d.Bft = Y[5];
-    d.Gff2 = Y[6]; d.Bff2 = Y[7]; d.Gtt2 = Y[8]; d.Btt2 = Y[9];
+    d.Gff2 = Y[6]; d.Bff2 = Y[7]; d.Gtt2 = Y[8]; d.Btt2 = Y[9]; d.Kft = Y[10];
     cudaStream_t st;
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamCreate");

@@ -162,7 +162,7 @@ struct EndHess {
 };
 
 __device__ __forceinline__ EndHess end_hess(const End &e, double Gss2, double Bss2, double A,
-                                            double C, double K, double Vu, double Vv, double VV,
+                                            double C, double K, double Vu, double Vv,
                                             double lamP, double lamQ, double mu) {
     EndHess h;
     const double mu2 = twice(mu);
@@ -173,10 +173,11 @@ __device__ __forceinline__ EndHess end_hess(const End &e, double Gss2, double Bs
     const double E = fma(A, e.qu, -(C * e.pu));
     const double F = fma(e.pu, A, e.qu * C);
     h.tK = mu2 * K;
-    h.hau = fma(mu2 * VV, E, Vv * h.W2);
+    const double mu2Vu = mu2 * Vu;
+    h.hau = Vv * fma(mu2Vu, E, h.W2);             // 2 mu Vu Vv E + Vv W2
     const double S = fma(e.pu, e.pu, e.qu * e.qu);
     h.huu = fma(mu2, S, fma(wP, Gss2, -(wQ * Bss2)));
-    h.huv = fma(mu2 * Vu, F, h.W1);
+    h.huv = fma(mu2Vu, F, h.W1);
     return h;
 }
 
@@ -281,7 +282,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     // One end at a time, stored as soon as it is computed, so that fewer values are live at once
     // (the compiler would otherwise recompute products to save registers).
     const double *lb = WH ? st_lam(N, R, b) : nullptr;
-    const double K = WH ? fma(G, G, Bm * Bm) : 0.0;   // A^2 + C^2 at both ends
+    const double K = WH ? __ldg(N.Kft + l) : 0.0;    // A^2 + C^2 = G^2 + B^2 at both ends
     EndHess hf{}, ht{};
     {
         const End ef = end_terms<DERIV>(Gff, Bff, Gff2, Bff2, Af, Cf, Vf, Vt, Vf2, VV);
@@ -292,7 +293,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
             store_hrow(Jf, ef, fb < tb);
         }
         if (WH)
-            hf = end_hess(ef, Gff2, Bff2, Af, Cf, K, Vf, Vt, VV, __ldg(lb + fb), __ldg(lb + nb + fb),
+            hf = end_hess(ef, Gff2, Bff2, Af, Cf, K, Vf, Vt, __ldg(lb + fb), __ldg(lb + nb + fb),
                           __ldg(lb + 2 * nb + l));
     }
     {
@@ -304,7 +305,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
             store_hrow(Jt, et, tb < fb);
         }
         if (WH)
-            ht = end_hess(et, Gtt2, Btt2, At, Ct, K, Vt, Vf, VV, __ldg(lb + tb), __ldg(lb + nb + tb),
+            ht = end_hess(et, Gtt2, Btt2, At, Ct, K, Vt, Vf, __ldg(lb + tb), __ldg(lb + nb + tb),
                           __ldg(lb + 2 * nb + nl + l));
     }
     if (WH) {

@@ -81,6 +81,7 @@ struct DevNet {
     const int *f, *t;
     const double *Gff, *Bff, *Gtt, *Btt, *Gft, *Bft;   // pi-model admittances (no phase shift: ft == tf)
     const double *Gff2, *Bff2, *Gtt2, *Btt2;            // 2 Gff, 2 Bff, 2 Gtt, 2 Btt (exact)
+    const double *Kft;                                  // Gft^2 + Bft^2
     const int *slot_ptr, *slot_nbr, *slot_ref, *br_slot, *slot_bus, *slot_pos;
     const int *bus_jP, *bus_jQ, *bus_hA, *bus_hM, *bus_k, *bus_nlow, *bus_perm;
     const double *Gs, *Bs, *Pd, *Qd;
@@ -160,9 +161,9 @@ struct ProfileHook {
 };
 
 // Kernel launchers (kernels.cu).  Each returns the launch's cudaError_t as int.
-// Y[0..9] = Gff, Bff, Gtt, Btt, Gft, Bft, 2 Gff, 2 Bff, 2 Gtt, 2 Btt.
+// Y[0..10] = Gff, Bff, Gtt, Btt, Gft, Bft, 2 Gff, 2 Bff, 2 Gtt, 2 Btt, Gft^2 + Bft^2.
 int launch_admittance(const double *r, const double *x, const double *b, const double *tap,
-                      int nl, double *const Y[10], void *stream);
+                      int nl, double *const Y[11], void *stream);
 int launch_eval(const DevNet &net, const EvalReq &req, void *stream, ProfileHook *hook = nullptr);
 int launch_eval_pipelined(const DevNet &net, const EvalReq &req, const PipeLaunch &pl,
                           void *stream, ProfileHook *hook = nullptr);

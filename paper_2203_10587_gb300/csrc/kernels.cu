@@ -25,7 +25,7 @@ namespace exago {
 // pi-model admittances (once per network).  ys = 1/(r + jx); Yff = (ys + jb/2)/tau^2,
 // Yft = Ytf = -ys/tau, Ytt = ys + jb/2; tap 0 means tau = 1.
 struct AdmittanceOut {
-    double *Y[10];   // Gff, Bff, Gtt, Btt, Gft, Bft, 2 Gff, 2 Bff, 2 Gtt, 2 Btt
+    double *Y[11];   // Gff, Bff, Gtt, Btt, Gft, Bft, 2 Gff, 2 Bff, 2 Gtt, 2 Btt, Gft^2 + Bft^2
 };
 
 __global__ void k_admittance(const double *__restrict__ r, const double *__restrict__ x,
@@ -43,8 +43,10 @@ __global__ void k_admittance(const double *__restrict__ r, const double *__restr
     out.Y[1][l] = Bff;
     out.Y[2][l] = gs;
     out.Y[3][l] = bc;
-    out.Y[4][l] = -gs / tau;
-    out.Y[5][l] = -bs / tau;
+    const double Gft = -gs / tau, Bft = -bs / tau;
+    out.Y[4][l] = Gft;
+    out.Y[5][l] = Bft;
+    out.Y[10][l] = fma(Gft, Gft, Bft * Bft);
     out.Y[6][l] = 2.0 * Gff;     // doubling is exact
     out.Y[7][l] = 2.0 * Bff;
     out.Y[8][l] = 2.0 * gs;
@@ -52,10 +54,10 @@ __global__ void k_admittance(const double *__restrict__ r, const double *__restr
 }
 
 int launch_admittance(const double *r, const double *x, const double *b, const double *tap,
-                      int nl, double *const Y[10], void *stream) {
+                      int nl, double *const Y[11], void *stream) {
     if (nl <= 0) return 0;
     AdmittanceOut out;
-    for (int k = 0; k < 10; k++) out.Y[k] = Y[k];
+    for (int k = 0; k < 11; k++) out.Y[k] = Y[k];
     k_admittance<<<(nl + 127) / 128, 128, 0, (cudaStream_t)stream>>>(r, x, b, tap, nl, out);
     return (int)cudaGetLastError();
 }
