@@ -363,6 +363,53 @@ class ServeClients:
         return res
 
 
+def time_calls(torch, fn, reps, warm=3):
+    """ms per call of fn (CUDA events on the current stream, after warm-up)."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_other_configs(exago, synth, torch, np, dev):
+    """The other workloads: a 10,000-bus grid evaluated 1,000 times in sequence (one IPM run),
+    and 10,000 buses x 64 load scenarios with the adjoint products."""
+    td = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    g = synth.grid_10k()
+    net = exago.Net(g)
+    res = {}
+    # C2: one state, 1,000 evaluations in sequence
+    b1 = synth.random_batch(2, g, 1)
+    x1, l1 = td(b1.x, torch.float64), td(b1.lam, torch.float64)
+    bt1 = exago.make_batch(x1, l1)
+    out1 = net.outputs(1, dev)
+    ms = time_calls(torch, lambda: net.eval_all(bt1, out1), 1000)
+    res["10k_bus_single_x1000"] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms}
+    # C4: 64 load scenarios, all outputs, then J^T v and (grad^2 L) u
+    b = synth.scenario_batch(4, g, 64)
+    x, lam, ps, w = (td(b.x, torch.float64), td(b.lam, torch.float64),
+                     td(b.pd_scale, torch.float64), td(b.obj_weight, torch.float64))
+    bt = exago.make_batch(x, lam, None, ps, w, b.sigma)
+    out = net.outputs(64, dev)
+    exago.exago_net_reserve(net.h, 64)
+    ms = time_calls(torch, lambda: net.eval_all(bt, out), 200)
+    v = torch.randn(64, net.m, dtype=torch.float64, device=dev)
+    u = torch.randn(64, net.n, dtype=torch.float64, device=dev)
+    o = torch.empty(64, net.n, dtype=torch.float64, device=dev)
+    ms_jtv = time_calls(torch, lambda: exago.exago_eval_jtv(net.h, bt, v, o), 200)
+    ms_hvp = time_calls(torch, lambda: exago.exago_eval_hvp(net.h, bt, u, o), 200)
+    res["10k_bus_x64_scenarios"] = {"evals_per_s": 64e3 / ms, "ms_per_batch": ms,
+                                    "jtv_per_s": 64e3 / ms_jtv, "hvp_per_s": 64e3 / ms_hvp}
+    net.close()
+    return res
+
+
 def run_serve(exago, synth, torch, np, dev, seconds):
     rng = np.random.default_rng(5)
     sc = ServeClients(exago, synth, torch, np, dev)
@@ -545,6 +592,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     if rank != 0:
         return
     serve = None if args.no_serve else run_serve(exago, synth, torch, np, dev, args.serve_seconds)
+    others = None if args.no_serve else run_other_configs(exago, synth, torch, np, dev)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -581,6 +629,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     }
     if serve is not None:
         res["serve"] = serve
+    if others is not None:
+        res["other_workloads"] = others
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_evals = 256 * cores
