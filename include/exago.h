@@ -337,6 +337,13 @@ exago_status exago_serve_stats(exago_server_t server, double *p50_ms, double *p9
 exago_status exago_serve_destroy(exago_server_t server);
 
 /*
+ * Testing only: the next n device allocations made by the library (network tables, workspaces,
+ * serving arenas) fail as if the device were out of memory, so that callers' ENOMEM paths can be
+ * exercised without exhausting a GPU.  n <= 0 clears the hook.  The paper has no counterpart.
+ */
+void exago_test_fail_allocations(int n);
+
+/*
  * Waits for `stream` and returns the device status word of the net: EXAGO_OK, or EXAGO_ETIMEOUT
  * if a bounded device-side wait gave up since the last check (the word is then cleared).
  */

@@ -1,7 +1,9 @@
 // C ABI of the evaluator (declared in include/exago.h): network lifetime, pattern queries and the
 // evaluation entry points of the polar AC-OPF model (ExaGO, Sec. III, eqs. (7)-(10)).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,9 +18,37 @@
 
 using namespace exago;
 
+namespace exago {
+
+// Testing hook: the next g_fail_allocs device allocations fail as if the device were out of
+// memory (exago_test_fail_allocations).
+std::atomic<int> g_fail_allocs{0};
+
+// Every device allocation of a net goes through here.
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    int left = g_fail_allocs.load();
+    while (left > 0 && !g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+    }
+    if (left > 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) cudaGetLastError();   // reported here; must not resurface at a launch
+    return e;
+}
+
+}  // namespace exago
+
 namespace {
 
 thread_local std::string g_err;
+
+// An NVTX range over one C-ABI call (visible to Nsight tools; free without them).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 exago_status fail(exago_status s, const std::string &msg) {
     g_err = msg;
@@ -68,7 +98,7 @@ exago_status upload(exago_net *net, const std::vector<T> &v, const T **out) {
     *out = nullptr;
     if (v.empty()) return EXAGO_OK;
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, v.size() * sizeof(T));
+    cudaError_t e = dev_malloc(&p, v.size() * sizeof(T));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (network arrays)");
     net->allocs.push_back(p);
     e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
@@ -81,7 +111,7 @@ exago_status alloc_dev(exago_net *net, size_t bytes, double **out) {
     *out = nullptr;
     if (bytes == 0) return EXAGO_OK;
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes);
+    cudaError_t e = dev_malloc(&p, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (admittances)");
     net->allocs.push_back(p);
     *out = (double *)p;
@@ -351,8 +381,11 @@ exago_status ensure_workspace_locked(exago_net *net, size_t need) {
         net->ws = nullptr;
         net->ws_bytes = 0;
     }
-    cudaError_t e = cudaMalloc(&net->ws, need);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (workspace)");
+    cudaError_t e = dev_malloc(&net->ws, need);
+    if (e != cudaSuccess) {
+        net->ws = nullptr;
+        return cuda_fail(e, "cudaMalloc (workspace)");
+    }
     net->ws_bytes = need;
     return EXAGO_OK;
 }
@@ -542,6 +575,8 @@ extern "C" {
 
 const char *exago_last_error(void) { return g_err.c_str(); }
 
+void exago_test_fail_allocations(int n) { g_fail_allocs.store(n > 0 ? n : 0); }
+
 const char *exago_status_name(exago_status s) {
     switch (s) {
         case EXAGO_OK: return "EXAGO_OK";
@@ -571,6 +606,7 @@ exago_status exago_net_create(int nb, const double *Gs, const double *Bs, const 
                               const double *tap, const double *rateA, int ng, const int *gbus,
                               const double *c2, const double *c1, const double *c0,
                               double baseMVA, exago_net_t *out) {
+    Range range("exago_net_create");
     exago_status s = plan_only(nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng, gbus, c2,
                                c1, c0, baseMVA, out);
     if (s != EXAGO_OK) return s;
@@ -666,32 +702,38 @@ exago_status exago_net_reserve(exago_net_t net, int B) {
 }
 
 exago_status exago_eval_obj(exago_net_t net, const exago_batch *bt, double *f) {
+    Range range("exago_eval_obj");
     if (!f) return fail(EXAGO_EINVAL, "f is NULL");
     return eval(net, bt, f, nullptr, nullptr, nullptr, nullptr);
 }
 
 exago_status exago_eval_grad(exago_net_t net, const exago_batch *bt, double *grad) {
+    Range range("exago_eval_grad");
     if (!grad) return fail(EXAGO_EINVAL, "grad is NULL");
     return eval(net, bt, nullptr, grad, nullptr, nullptr, nullptr);
 }
 
 exago_status exago_eval_cons(exago_net_t net, const exago_batch *bt, double *gh) {
+    Range range("exago_eval_cons");
     if (!gh) return fail(EXAGO_EINVAL, "gh is NULL");
     return eval(net, bt, nullptr, nullptr, gh, nullptr, nullptr);
 }
 
 exago_status exago_eval_jac(exago_net_t net, const exago_batch *bt, double *jval) {
+    Range range("exago_eval_jac");
     if (!jval) return fail(EXAGO_EINVAL, "jval is NULL");
     return eval(net, bt, nullptr, nullptr, nullptr, jval, nullptr);
 }
 
 exago_status exago_eval_hess(exago_net_t net, const exago_batch *bt, double *hval) {
+    Range range("exago_eval_hess");
     if (!hval) return fail(EXAGO_EINVAL, "hval is NULL");
     return eval(net, bt, nullptr, nullptr, nullptr, nullptr, hval);
 }
 
 exago_status exago_eval_all(exago_net_t net, const exago_batch *bt, double *f, double *grad,
                             double *gh, double *jval, double *hval) {
+    Range range("exago_eval_all");
     return eval(net, bt, f, grad, gh, jval, hval);
 }
 
@@ -761,14 +803,17 @@ exago_status adjoint(exago_net *net, const exago_batch *bt, const double *v, dou
 }  // namespace
 
 exago_status exago_eval_jvp(exago_net_t net, const exago_batch *bt, const double *u, double *out) {
+    Range range("exago_eval_jvp");
     return adjoint(net, bt, u, out, ADJ_JVP);
 }
 
 exago_status exago_eval_jtv(exago_net_t net, const exago_batch *bt, const double *v, double *out) {
+    Range range("exago_eval_jtv");
     return adjoint(net, bt, v, out, ADJ_JTV);
 }
 
 exago_status exago_eval_hvp(exago_net_t net, const exago_batch *bt, const double *u, double *out) {
+    Range range("exago_eval_hvp");
     return adjoint(net, bt, u, out, ADJ_HVP);
 }
 
@@ -825,6 +870,7 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg) {
 exago_status exago_net_autotune(exago_net_t net, const exago_batch *bt, double *f, double *grad,
                                 double *gh, double *jval, double *hval, int reps,
                                 exago_config *best) {
+    Range range("exago_net_autotune");
     if (reps < 1) return fail(EXAGO_EINVAL, "reps < 1");
     exago_status s = check_batch(net, bt, hval != nullptr);
     if (s != EXAGO_OK) return s;

@@ -13,6 +13,7 @@
 // so serving allocates no device memory afterwards.  Completion is signalled by a host function
 // queued behind the kernels (it only sets a flag; CUDA calls are not allowed there).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -211,6 +212,10 @@ void finish_locked(exago_server *S, Request *r, exago_status st, const std::stri
 // Admits the oldest queued request, merged with later compatible ones when their states fit the
 // merge budget and the arena.  Caller holds S->mu.  False when nothing could be admitted.
 bool admit_locked(exago_server *S) {
+    nvtxRangePushA("exago_serve_admit");
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop;
     Request *head = S->queue.front();
     exago_net_t net = S->nets[head->net_id];
     std::vector<Request *> members{head};
@@ -357,7 +362,7 @@ exago_status exago_serve_create(size_t device_mem_budget, int max_slots, int n_s
     cudaError_t e = cudaGetDevice(&S->device);
     if (e != cudaSuccess) return sfail(EXAGO_ECUDA, cudaGetErrorString(e));
     S->budget = (device_mem_budget + 255) / 256 * 256;
-    e = cudaMalloc((void **)&S->arena_base, S->budget);
+    e = exago::dev_malloc((void **)&S->arena_base, S->budget);
     if (e != cudaSuccess)
         return sfail(e == cudaErrorMemoryAllocation ? EXAGO_ENOMEM : EXAGO_ECUDA,
                      std::string("cudaMalloc (serve arena): ") + cudaGetErrorString(e));

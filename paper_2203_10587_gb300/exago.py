@@ -33,7 +33,7 @@ EXPORTS = [
     "exago_eval_profile", "exago_net_set_config", "exago_net_get_config", "exago_net_autotune",
     "exago_net_check", "exago_serve_create", "exago_serve_register", "exago_serve_submit",
     "exago_serve_set_merge", "exago_serve_poll", "exago_serve_wait", "exago_serve_stats",
-    "exago_serve_destroy",
+    "exago_serve_destroy", "exago_test_fail_allocations",
 ]
 
 SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
@@ -118,6 +118,7 @@ def lib():
                 "exago_serve_submit": ([vp, i32, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], i32),
                 "exago_serve_set_merge": ([vp, i32], i32),
+                "exago_test_fail_allocations": ([i32], None),
                 "exago_serve_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(i32)], i32),
                 "exago_serve_wait": ([vp, ctypes.c_uint64, ctypes.c_double], i32),
                 "exago_serve_stats": ([vp, ctypes.POINTER(ctypes.c_double),
@@ -369,6 +370,10 @@ def exago_serve_submit(s, net_id: int, batch: exago_batch, f=None, grad=None, gh
                                     _out(gh), _out(jval), _out(hval), float(deadline_ms),
                                     ctypes.byref(t)))
     return t.value
+
+
+def exago_test_fail_allocations(n: int):
+    lib().exago_test_fail_allocations(int(n))
 
 
 def exago_serve_set_merge(s, max_states: int):

@@ -117,6 +117,7 @@ def test_queue_full_and_deadline(ex):
     net = ex.Net(g)
     srv = ex.exago_serve_create(1 << 28, max_slots=1, n_streams=1)
     try:
+        ex.exago_serve_set_merge(srv, 1)       # the late request must queue, not join the first
         i = ex.exago_serve_register(srv, net.h)
         # every input is uploaded before the sleep (a pageable upload would wait for it)
         first = Req(ex, net, synth.random_batch(400, g, 2))
@@ -168,5 +169,32 @@ def test_serve_argument_errors(ex):
             ex.exago_serve_submit(srv, 5, r.bt, **r.out)        # unknown net id
         with pytest.raises(ex.ExagoError):
             ex.exago_serve_wait(srv, 12345)                     # unknown ticket
+    finally:
+        ex.exago_serve_destroy(srv)
+
+
+def test_queued_requests_merge_into_one_launch(ex):
+    """With the only slot held behind a GPU sleep, requests queue; when it frees, one admission
+    takes them all (up to the merge budget), and every result equals its request alone."""
+    import torch
+    g = synth.grid_sized(9, 118)
+    net = ex.Net(g)
+    srv = ex.exago_serve_create(1 << 28, max_slots=1, n_streams=1)
+    try:
+        ex.exago_serve_set_merge(srv, 8)
+        i = ex.exago_serve_register(srv, net.h)
+        first = Req(ex, net, synth.random_batch(500, g, 1))
+        rest = [Req(ex, net, synth.random_batch(510 + k, g, 1 + k % 3, masks=True, sigma=0.5 * k))
+                for k in range(3)]
+        torch.cuda.synchronize()
+        torch.cuda._sleep(200_000_000)
+        tickets = [ex.exago_serve_submit(srv, i, first.bt, **first.out)]
+        tickets += [ex.exago_serve_submit(srv, i, r.bt, **r.out) for r in rest]
+        for t in tickets:
+            ex.exago_serve_wait(srv, t)
+        for r in [first] + rest:
+            got, ref = r.host(), alone(ex, net, r)
+            for key in ref:
+                np.testing.assert_array_equal(got[key], ref[key])
     finally:
         ex.exago_serve_destroy(srv)
