@@ -206,6 +206,18 @@ def test_10k_bus_single_instance(ex, oracle_mod):
     compare_instance(out, 0, oracle_eval(oracle_mod, g, b, 0), "10k")
 
 
+def test_70k_bus_largest_serving_grid(ex, oracle_mod):
+    """The largest grid of the serving mix (70,000 buses, 91,000 branches): two states, the
+    second with masks and load scales, each against the oracle."""
+    g = synth.grid_sized(53, 70_000)
+    b = synth.random_batch(53, g, 2, masks=True, pd_scale=True, sigma=0.9)
+    b.mask[0, :] = 1
+    net = ex.Net(g)
+    out = gpu_eval(net, b)
+    for i in range(2):
+        compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"70k [{i}]")
+
+
 def test_2000_bus_512_contingencies_sampled(ex, oracle_mod):
     g = synth.grid_2000()
     b = synth.contingency_batch(3, g, 512)
