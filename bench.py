@@ -37,8 +37,8 @@ N_INPUT_SETS = 4
 # sincos path (an FMA counts 2 flops; doublings run on the integer pipe and count nothing):
 # (flops, instructions).  Per 2000-bus state they sum to 522,500 flops / 353,700 instructions.
 FP64_PER_BRANCH = (168, 109)   # sincos, flows, 16 derivatives, h and its J row, Hessian fold
-FP64_PER_SLOT = (9, 9)         # a branch end's record summed into its bus (all but the first)
-FP64_PER_BUS = (16, 12)        # shunt, load and diagonal terms of one bus
+FP64_PER_SLOT = (7, 7)         # a branch end's record summed into its bus (all but the first)
+FP64_PER_BUS = (16, 9)         # shunt, balances (Euler, from the derivative sums), diagonal terms
 FP64_PER_GEN = (12, 9)         # balance, cost Hessian, gradient and objective terms of a generator
 FP64_PER_STATE = (255, 255)    # the objective's fixed 256-lane reduction tree
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 2 FP64 FMA per SM per clock x

@@ -225,7 +225,7 @@ __device__ __forceinline__ void store_hrow(double *Jrow, const End &e, bool self
     }
 }
 
-// Stores a pair of components of a record (16-byte aligned: records are 96 bytes).
+// Stores a pair of components of a record (16-byte aligned: records are 80 bytes).
 __device__ __forceinline__ void put2(double *rec, int c, double a, double b) {
     *reinterpret_cast<double2 *>(rec + c) = make_double2(a, b);
 }
@@ -238,7 +238,7 @@ template <int WANT>
 __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, int b, int l,
                                             double *scr) {
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
-    constexpr bool DERIV = WJ || WH;
+    constexpr bool DERIV = WG || WJ || WH;   // the bus balances come from derivative sums
     const int nb = N.nb, nl = N.nl;
     double *rf = scr + (size_t)__ldg(N.br_slot + l) * NCOMP;
     double *rt = scr + (size_t)__ldg(N.br_slot + nl + l) * NCOMP;
@@ -253,8 +253,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
 #pragma unroll
         for (int e = 0; e < 2; e++) {
             double *r = e ? rt : rf;
-            put2(r, SC_P, 0.0, 0.0);
-            if (WJ) { put2(r, SC_PA, 0.0, 0.0); put2(r, SC_PV, 0.0, 0.0); put2(r, SC_QU, 0.0, 0.0); }
+            if (WG || WJ) { put2(r, SC_PA, 0.0, 0.0); put2(r, SC_PV, 0.0, 0.0); put2(r, SC_QU, 0.0, 0.0); }
             if (WH) { put2(r, SC_HAA, 0.0, 0.0); put2(r, SC_HUU, 0.0, 0.0); }
         }
         if (WG && ghb) { ghb[2 * nb + l] = 0.0; ghb[2 * nb + nl + l] = 0.0; }
@@ -286,24 +285,22 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     EndHess hf{}, ht{};
     {
         const End ef = end_terms<DERIV>(Gff, Bff, Gff2, Bff2, Af, Cf, Vf, Vt, Vf2, VV);
-        put2(rf, SC_P, ef.P, ef.Q);
         if (WG && ghb) ghb[2 * nb + l] = fma(ef.P, ef.P, ef.Q * ef.Q);
-        if (WJ) {
+        if (WG || WJ) {
             put2(rf, SC_PA, ef.pa, ef.pu); put2(rf, SC_PV, ef.pv, ef.qa); put2(rf, SC_QU, ef.qu, ef.qv);
-            store_hrow(Jf, ef, fb < tb);
         }
+        if (WJ) store_hrow(Jf, ef, fb < tb);
         if (WH)
             hf = end_hess(ef, Gff2, Bff2, Af, Cf, K, Vf, Vt, __ldg(lb + fb), __ldg(lb + nb + fb),
                           __ldg(lb + 2 * nb + l));
     }
     {
         const End et = end_terms<DERIV>(Gtt, Btt, Gtt2, Btt2, At, Ct, Vt, Vf, Vt2, VV);
-        put2(rt, SC_P, et.P, et.Q);
         if (WG && ghb) ghb[2 * nb + nl + l] = fma(et.P, et.P, et.Q * et.Q);
-        if (WJ) {
+        if (WG || WJ) {
             put2(rt, SC_PA, et.pa, et.pu); put2(rt, SC_PV, et.pv, et.qa); put2(rt, SC_QU, et.qu, et.qv);
-            store_hrow(Jt, et, tb < fb);
         }
+        if (WJ) store_hrow(Jt, et, tb < fb);
         if (WH)
             ht = end_hess(et, Gtt2, Btt2, At, Ct, K, Vt, Vf, __ldg(lb + tb), __ldg(lb + nb + tb),
                           __ldg(lb + 2 * nb + nl + l));
@@ -337,7 +334,7 @@ __device__ __forceinline__ double2 ld2(const double *p) {
 
 // The values of one branch-end record that a request needs.
 struct Rec {
-    double P, Q, pa, pu, pv, qa, qu, qv, haa, hua, huu, huv;
+    double pa, pu, pv, qa, qu, qv, haa, hua, huu, huv;
 };
 
 // A record pair from shared memory (SMEM) or through L2 (records other CTAs wrote this launch).
@@ -350,8 +347,7 @@ __device__ __forceinline__ double2 rec2(const double *p) {
 template <int WANT, bool SMEM>
 __device__ __forceinline__ Rec load_rec(const double *rec) {
     Rec r{};
-    if (WANT & W_G) { const double2 v = rec2<SMEM>(rec + SC_P); r.P = v.x; r.Q = v.y; }
-    if (WANT & W_J) {
+    if (WANT & (W_G | W_J)) {
         const double2 a = rec2<SMEM>(rec + SC_PA), v = rec2<SMEM>(rec + SC_PV);
         const double2 u = rec2<SMEM>(rec + SC_QU);
         r.pa = a.x; r.pu = a.y; r.pv = v.x; r.qa = v.y; r.qu = u.x; r.qv = u.y;
@@ -363,11 +359,10 @@ __device__ __forceinline__ Rec load_rec(const double *rec) {
     return r;
 }
 
-// Diagonal sums of a bus: injections, dP/dVa_u, dP/dVm_u, dQ/dVa_u, dQ/dVm_u, H diagonal terms.
+// Diagonal sums of a bus: dP/dVa_u, dP/dVm_u, dQ/dVa_u, dQ/dVm_u, H diagonal terms.
 template <int WANT>
 __device__ __forceinline__ void add_diag(Rec &d, const Rec &r) {
-    if (WANT & W_G) { d.P += r.P; d.Q += r.Q; }
-    if (WANT & W_J) { d.pa += r.pa; d.pu += r.pu; d.qa += r.qa; d.qu += r.qu; }
+    if (WANT & (W_G | W_J)) { d.pa += r.pa; d.pu += r.pu; d.qa += r.qa; d.qu += r.qu; }
     if (WANT & W_H) { d.haa += r.haa; d.hua += r.hua; d.huu += r.huu; }
 }
 
@@ -379,8 +374,12 @@ __device__ __forceinline__ void add_group(Rec &o, const Rec &r) {
 }
 
 // The rest of one (state b, bus i) item once D holds the sums of the bus's branch-end records
-// (injections and the diagonal derivative and Hessian terms):
-//   g:  P_i and Q_i balances (end injections, shunt, load and generators);
+// (the diagonal derivative and Hessian terms):
+//   g:  P_i and Q_i balances (injections, load and generators).  The injections are
+//       homogeneous of degree 2 in the voltage magnitudes, so (Euler) 2 P_i = Vm_i dP_i/dVm_i +
+//       sum over the ends of Vm_v dP/dVm_v, and Vm_v dP/dVm_v = Vu Vv A is the end's dQ/dVa_u;
+//       likewise 2 Q_i = Vm_i dQ_i/dVm_i - sum of dP/dVa_u.  An out-of-service end's record is
+//       zero, so no end's injection needs summing on its own;
 //   J:  the diagonal entries of rows P_i and Q_i (plus the shunt term) and -1 for each generator;
 //   H:  the diagonals of rows Va_i and Vm_i (plus the shunt term) and the cost Hessian of the
 //       bus's generators.
@@ -395,11 +394,13 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
     const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
     const int k = __ldg(N.bus_k + i), nlow = __ldg(N.bus_nlow + i);
     double *JP = W.JP, *JQ = W.JQ, *HA = W.HA, *HM = W.HM;
-    const double sP = D.P, sQ = D.Q, dPa = D.pa, dPu = D.pu, dQa = D.qa, dQu = D.qu;
+    const double dPa = D.pa, dPu = D.pu, dQa = D.qa, dQu = D.qu;
     const double dAA = D.haa, dUA = D.hua, dUU = D.huu;
+    // dP_i/dVm_i and dQ_i/dVm_i, with the shunt terms
+    const double tV = twice(Vm);
+    const double JPu = fma(Gs, tV, dPu), JQu = fma(-Bs, tV, dQu);
 
     if (WG && R.gh) {
-        const double VV = Vm * Vm;
         double Pd = __ldg(N.Pd + i), Qd = __ldg(N.Qd + i);
         const double *pds = st_pd(N, R, b);
         if (pds) {                                            // load scenarios
@@ -407,8 +408,8 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
             Pd *= sc;
             Qd *= sc;
         }
-        double gP = sP + fma(Gs, VV, Pd);
-        double gQ = sQ + fma(-Bs, VV, Qd);
+        double gP = fma(0.5, fma(Vm, JPu, dQa), Pd);
+        double gQ = fma(0.5, fma(Vm, JQu, -dPa), Qd);
         for (int q = g0; q < g1; q++) {
             const int g = __ldg(N.gen_ord + q);
             gP -= __ldg(xb + 2 * nb + g);
@@ -419,9 +420,8 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
         ghb[nb + i] = gQ;
     }
     if (WJ) {
-        const double tV = twice(Vm);
-        JP[nlow] = dPa; JP[k + nlow] = fma(Gs, tV, dPu);
-        JQ[nlow] = dQa; JQ[k + nlow] = fma(-Bs, tV, dQu);
+        JP[nlow] = dPa; JP[k + nlow] = JPu;
+        JQ[nlow] = dQa; JQ[k + nlow] = JQu;
         for (int q = 0; q < g1 - g0; q++) {
             JP[2 * k + q] = -1.0;
             JQ[2 * k + q] = -1.0;
@@ -549,9 +549,8 @@ __device__ __forceinline__ void slot_item(const DevNet &N, int s, const double *
                                           const TileRows &T) {
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     Rec o = load_rec<WANT, false>(scr + (size_t)s * NCOMP);
-    if (WG) { dg[0] = o.P; dg[1] = o.Q; }
-    if (WJ) { dg[2] = o.pa; dg[3] = o.pu; dg[4] = o.qa; dg[5] = o.qu; }
-    if (WH) { dg[6] = o.haa; dg[7] = o.hua; dg[8] = o.huu; }
+    if (WG || WJ) { dg[0] = o.pa; dg[1] = o.pu; dg[2] = o.qa; dg[3] = o.qu; }
+    if (WH) { dg[4] = o.haa; dg[5] = o.hua; dg[6] = o.huu; }
     const int pos = __ldg(N.slot_pos + s);
     if (!(WJ || WH) || pos < 0) return;
     const int i = __ldg(N.slot_bus + s), j = __ldg(N.slot_nbr + s);
@@ -584,9 +583,8 @@ __device__ __forceinline__ void bus_sums(const DevNet &N, const EvalReq &R, int 
     for (int s = s0; s < s1; s++) {
         const double *d = dgs + (size_t)(s - S0) * kDiagComps;
         Rec r{};
-        if (WG) { r.P = d[0]; r.Q = d[1]; }
-        if (WJ) { r.pa = d[2]; r.pu = d[3]; r.qa = d[4]; r.qu = d[5]; }
-        if (WH) { r.haa = d[6]; r.hua = d[7]; r.huu = d[8]; }
+        if (WG || WJ) { r.pa = d[0]; r.pu = d[1]; r.qa = d[2]; r.qu = d[3]; }
+        if (WH) { r.haa = d[4]; r.hua = d[5]; r.huu = d[6]; }
         if (s == s0) D = r;
         else add_diag<WANT>(D, r);
     }

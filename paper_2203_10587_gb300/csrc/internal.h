@@ -15,22 +15,22 @@ namespace exago {
 // Per-(branch, end) record handed from the branch phase to the bus phase: NCOMP doubles at
 // scratch[(b * nslot + slot) * NCOMP + k] for state b, where slot is the end's position in its
 // bus's slot list.  A bus tile's records are therefore one contiguous range, which the bus phase
-// copies to shared memory in one coalesced pass; the branch phase writes each 96-byte record as
-// three whole sectors.  For the end at bus u towards bus v:
+// can copy to shared memory in one coalesced pass; the branch phase writes each 80-byte record
+// as five 16-byte pairs.  The end's injections P and Q are not carried: a bus's balances follow
+// from its sums of dP/dVm_u, dQ/dVm_u, dP/dVa_u and dQ/dVa_u (bus_tail).  For the end at bus u
+// towards bus v:
 enum SlotComp {
-    SC_P = 0,    // active injection of this end at u
-    SC_Q = 1,    // reactive injection
-    SC_PA = 2,   // dP/dVa_u            (dP/dVa_v = -dP/dVa_u)
-    SC_PU = 3,   // dP/dVm_u
-    SC_PV = 4,   // dP/dVm_v
-    SC_QA = 5,   // dQ/dVa_u
-    SC_QU = 6,   // dQ/dVm_u
-    SC_QV = 7,   // dQ/dVm_v
-    SC_HAA = 8,  // Lagrangian Hessian of the branch: (Va_u, Va_u) = -(Va_u, Va_v)
-    SC_HUA = 9,  // (Vm_u, Va_u) = -(Vm_u, Va_v)
-    SC_HUU = 10, // (Vm_u, Vm_u)
-    SC_HUV = 11, // (Vm_u, Vm_v)
-    NCOMP = 12
+    SC_PA = 0,   // dP/dVa_u            (dP/dVa_v = -dP/dVa_u)
+    SC_PU = 1,   // dP/dVm_u
+    SC_PV = 2,   // dP/dVm_v
+    SC_QA = 3,   // dQ/dVa_u
+    SC_QU = 4,   // dQ/dVm_u
+    SC_QV = 5,   // dQ/dVm_v
+    SC_HAA = 6,  // Lagrangian Hessian of the branch: (Va_u, Va_u) = -(Va_u, Va_v)
+    SC_HUA = 7,  // (Vm_u, Va_u) = -(Vm_u, Va_v)
+    SC_HUU = 8,  // (Vm_u, Vm_u)
+    SC_HUV = 9,  // (Vm_u, Vm_v)
+    NCOMP = 10
 };
 
 // Host plan of one grid: validated copies of the inputs, both sparsity patterns, and what each
@@ -189,7 +189,7 @@ int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes);
 // largest tile's need in doubles, capped at kStageMaxDoubles; a tile above the cap reads its
 // records from global memory and writes its rows directly.
 constexpr int kStageMaxDoubles = 9216;   // 72 KB
-constexpr int kDiagComps = 9;            // record components summed into a bus's diagonal
+constexpr int kDiagComps = 7;            // record components summed into a bus's diagonal
 __host__ __device__ inline int stage_index(int block) {
     return block == 32 ? 0 : block == 64 ? 1 : block == 256 ? 3 : 2;
 }

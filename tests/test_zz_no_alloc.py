@@ -61,7 +61,7 @@ def test_static_scratch_rejects_oversized_batch(ex):
     g = synth.grid_2000()
     net = ex.Net(g)
     limit = 16 << 20
-    per_state = 12 * 2 * g.nl * 8
+    per_state = 10 * 2 * g.nl * 8          # 10-double records, one per branch end
     B_ok = limit // per_state
     for B in (B_ok, B_ok + 1):
         x = torch.zeros(B, net.n, dtype=torch.float64, device="cuda")
