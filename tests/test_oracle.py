@@ -10,6 +10,8 @@ the oracle is pinned by:
   * the loss invariant: sum of net injections = sum over branches of gs |V_f e^{j Va_f}/tau - V_t e^{j Va_t}|^2;
   * central finite differences of g, h (Jacobian), f (gradient) and sigma grad f + J' lam (Hessian);
   * mask semantics: an out-of-service branch equals the branch removed from the grid;
+  * symmetries: angle-shift invariance and the degree-2 (injections) and degree-4 (|S|^2)
+    homogeneity in the voltage magnitudes, which tie J to g and H to J;
   * the nonzero counts 4nb + 16nl + 2ng (J) and 3nb + 4nl + ng (lower Hessian).
 Each pin is chosen so that a dropped term, a sign error, a swapped from/to index or a transposed
 operand in the oracle fails at least one of them; test_oracle_mutants.py plants 22 such
@@ -228,6 +230,45 @@ def test_finite_differences_sigma_zero_and_transformers(oracle_mod):
     g = synth.make_grid(43, 10, 14, 3, transformer_frac=0.5, shunts=True)
     b = synth.random_batch(43, g, 1)
     _fd_check(oracle_mod, g, b, sigma=0.0)
+
+
+# ---- symmetries of the model ----------------------------------------------------------------
+
+def test_homogeneity_and_angle_invariance(oracle_mod):
+    """Two symmetries of the polar model (Sec. III, eqs. (8)-(9)) tie J and H together:
+      * shifting every angle by one amount changes nothing, so every row of J and of H sums to
+        zero over the angle columns;
+      * the injections are homogeneous of degree 2 in the voltage magnitudes and |S|^2 of degree
+        4, so (Euler) sum_k Vm_k dg_i/dVm_k = 2 (g_i less load and generation) and
+        sum_k Vm_k dh_l/dVm_k = 4 h_l; differentiated once more, the Lagrangian Hessian's
+        Vm-weighted rows are (1 lam_g + 3 lam_h) J on Vm rows and (2 lam_g + 4 lam_h) J on Va rows.
+    The bus balances in the CUDA path rest on the degree-2 identity."""
+    g = synth.make_grid(61, 40, 56, 9, transformer_frac=0.3, shunts=True)
+    b = synth.random_batch(61, g, 1, masks=True, pd_scale=True, obj_weight=True, sigma=0.6)
+    x, lam, mask, ps = b.x[0], b.lam[0], b.mask[0], b.pd_scale[0]
+    r = oracle_mod.evaluate(oracle_mod.OracleNet(g), x, lam, mask, ps, float(b.obj_weight[0]), 0.6)
+    nb, nl, n, m = g.nb, g.nl, g.n, g.m
+    J = oracle_mod.csr_to_dense(r["J"], (m, n))
+    Hl = oracle_mod.csr_to_dense(r["H"], (n, n))
+    H = Hl + np.tril(Hl, -1).T
+    Vm = x[nb:2 * nb]
+    va, vm = slice(0, nb), slice(nb, 2 * nb)
+    scale = np.abs(J[:, :2 * nb]).max(axis=1) * np.maximum(1.0, Vm.max())
+    np.testing.assert_allclose(J[:, va].sum(axis=1), 0.0, atol=1e-12 * scale.max())
+    Hs = np.abs(H[:2 * nb, :2 * nb]).max()
+    np.testing.assert_allclose(H[:2 * nb, va].sum(axis=1), 0.0, atol=1e-12 * Hs)
+    # injections: balances less load and generation
+    Pg, Qg = x[2 * nb:2 * nb + g.ng], x[2 * nb + g.ng:]
+    SgP = np.bincount(g.gbus, weights=Pg, minlength=nb)
+    SgQ = np.bincount(g.gbus, weights=Qg, minlength=nb)
+    inj = np.concatenate([r["gh"][:nb] - g.Pd * ps + SgP, r["gh"][nb:2 * nb] - g.Qd * ps + SgQ])
+    deg = np.concatenate([2.0 * inj, 4.0 * r["gh"][2 * nb:]])
+    np.testing.assert_allclose(J[:, vm] @ Vm, deg, rtol=1e-11, atol=1e-11 * scale.max())
+    lg = lam.copy(); lg[2 * nb:] = 0.0
+    lh = lam.copy(); lh[:2 * nb] = 0.0
+    np.testing.assert_allclose(H[vm, vm] @ Vm, (J.T @ (lg + 3.0 * lh))[vm], rtol=1e-10, atol=1e-11 * Hs)
+    np.testing.assert_allclose(H[va, vm] @ Vm, (J.T @ (2.0 * lg + 4.0 * lh))[va], rtol=1e-10,
+                               atol=1e-11 * Hs)
 
 
 # ---- masks, structure, batch --------------------------------------------------------------------

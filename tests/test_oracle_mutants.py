@@ -67,6 +67,7 @@ PINS = [
     ("fd", lambda om: T.test_finite_differences(om, 41)),
     ("fd_sigma0", lambda om: T.test_finite_differences_sigma_zero_and_transformers(om)),
     ("mask", lambda om: T.test_mask_equals_branch_removed(om)),
+    ("symmetries", lambda om: T.test_homogeneity_and_angle_invariance(om)),
 ]
 
 
