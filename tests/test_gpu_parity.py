@@ -194,6 +194,10 @@ def test_argument_errors(ex):
     bt4.B = -1
     with pytest.raises(ex.ExagoError):
         ex.exago_eval_cons(net.h, bt4, hv)
+    for bad in (dict(tile_group=5), dict(block=48), dict(occupancy=12), dict(lag=4, ring=4)):
+        with pytest.raises(ex.ExagoError) as ei:
+            ex.exago_net_set_config(net.h, **bad)
+        assert ei.value.name == "EXAGO_EINVAL"
 
 
 # ---- paper-sized workloads, sampled ---------------------------------------------------------
