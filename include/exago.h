@@ -246,8 +246,10 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *             in the ring (0 = 3, at most 7).
  *   chunk     pipelined: states per chunk (0 = as many as fit 48 MB of records in the ring).
  *   use_graph persistent and pipelined: EXAGO_GRAPH_DEFAULT / ON launch through a cached instantiated CUDA
- *             graph (one per distinct argument set, 8 kept); OFF launches directly.  A call on a
- *             stream that is being captured always launches directly.
+ *             graph (one per distinct argument set, 8 kept).  An argument set is captured on its
+ *             second use among the last 32 uncached calls, so a one-off set launches directly.
+ *             OFF always launches directly.  A call on a stream that is being captured always
+ *             launches directly.
  *   spin_limit  polls (about 0.4 us each) before a device-side wait gives up and records
  *             EXAGO_ETIMEOUT in the status word (0 = 2^22).
  *   test_force_timeout  testing only: bus tiles wait for a count that never arrives, so every

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -85,6 +86,7 @@ struct exago_net {
     std::map<int, exago_config> tuned;   // autotuned configuration per batch size
     std::vector<GraphEntry> graphs;
     uint64_t graph_clock = 0;
+    std::vector<std::vector<uint64_t>> graph_seen;   // argument sets launched once, oldest first
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side_stream = nullptr;   // pipelined schedule: bus kernels
     cudaEvent_t pipe_ev[18] = {};
@@ -417,6 +419,18 @@ exago_status launch_graph_locked(exago_net *net, const std::vector<uint64_t> &ke
         if (g.key == key) { hit = &g; break; }
     cudaError_t e;
     if (!hit) {
+        // An argument set is captured on its second use among the last 32 uncached calls; a
+        // one-off set (a caller cycling through many buffers) launches directly instead of paying
+        // a capture and an instantiation on the host.
+        auto seen = std::find(net->graph_seen.begin(), net->graph_seen.end(), key);
+        if (seen == net->graph_seen.end()) {
+            if (net->graph_seen.size() >= 32) net->graph_seen.erase(net->graph_seen.begin());
+            net->graph_seen.push_back(key);
+            const int le = launch(stream);
+            if (le != 0) return cuda_fail((cudaError_t)le, "kernel launch");
+            return EXAGO_OK;
+        }
+        net->graph_seen.erase(seen);
         if (!net->cap_stream) {
             e = cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking);
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate (graph capture)");
@@ -439,7 +453,8 @@ exago_status launch_graph_locked(exago_net *net, const std::vector<uint64_t> &ke
             size_t lru = 0;
             for (size_t i = 1; i < net->graphs.size(); i++)
                 if (net->graphs[i].last_use < net->graphs[lru].last_use) lru = i;
-            cudaDeviceSynchronize();
+            // no device synchronisation: an executable graph destroyed while a launch of it is
+            // still in flight is freed by the runtime once that launch completes
             cudaGraphExecDestroy(net->graphs[lru].exec);
             net->graphs.erase(net->graphs.begin() + lru);
         }

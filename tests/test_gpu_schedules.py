@@ -69,6 +69,34 @@ def test_schedules_bitwise_equal_and_match_oracle(ex, oracle_mod, name):
         compare_instance(outs[0], i, oracle_eval(oracle_mod, g, b, i), name)
 
 
+def test_graph_cache_under_many_argument_sets(ex):
+    """More distinct argument sets than the graph cache holds, cycled three times with no
+    synchronisation between calls: first uses launch directly, second uses are captured, the
+    least recently used graphs are evicted while earlier launches may still be in flight.  Every
+    result equals the direct launch of the same state."""
+    import torch
+    g = synth.make_grid(75, 120, 160, 30, shunts=True)
+    b = synth.random_batch(75, g, 12, masks=True, sigma=0.7)
+    net = ex.Net(g)
+    from parity_util import to_device
+    d = to_device(b)
+    batches = [ex.make_batch(d["x"][i:i + 1], d["lam"][i:i + 1], d["mask"][i:i + 1], obj_factor=b.sigma)
+               for i in range(b.B)]
+    ex.exago_net_set_config(net.h, schedule=2, use_graph=2)
+    ref = [net.eval_all(bt, net.outputs(1)) for bt in batches]
+    ex.exago_net_set_config(net.h, schedule=2, use_graph=1)
+    outs = [[net.outputs(1) for _ in range(3)] for _ in batches]
+    for r in range(3):
+        for i, bt in enumerate(batches):
+            net.eval_all(bt, outs[i][r])
+    torch.cuda.synchronize()
+    ex.exago_net_check(net.h)
+    for i in range(b.B):
+        for r in range(3):
+            for k, v in ref[i].items():
+                assert torch.equal(outs[i][r][k], v), (i, r, k)
+
+
 def test_single_state_and_subset_outputs(ex, oracle_mod):
     g = synth.grid_10k()
     b = synth.random_batch(8, g, 1)
