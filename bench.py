@@ -389,8 +389,12 @@ def run_other_configs(exago, synth, torch, np, dev):
     x1, l1 = td(b1.x, torch.float64), td(b1.lam, torch.float64)
     bt1 = exago.make_batch(x1, l1)
     out1 = net.outputs(1, dev)
+    tuned1 = exago.exago_net_autotune(net.h, bt1, out1["f"], out1["grad"], out1["gh"],
+                                      out1["jval"], out1["hval"])
     ms = time_calls(torch, lambda: net.eval_all(bt1, out1), 1000)
-    res["10k_bus_single_x1000"] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms}
+    res["10k_bus_single_x1000"] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms,
+                                   "launch_config": {k: tuned1[k] for k in
+                                                     ("schedule", "block", "occupancy", "tile_group")}}
     # C4: 64 load scenarios, all outputs, then J^T v and (grad^2 L) u
     b = synth.scenario_batch(4, g, 64)
     x, lam, ps, w = (td(b.x, torch.float64), td(b.lam, torch.float64),
@@ -398,6 +402,8 @@ def run_other_configs(exago, synth, torch, np, dev):
     bt = exago.make_batch(x, lam, None, ps, w, b.sigma)
     out = net.outputs(64, dev)
     exago.exago_net_reserve(net.h, 64)
+    tuned = exago.exago_net_autotune(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"],
+                                     out["hval"])
     ms = time_calls(torch, lambda: net.eval_all(bt, out), 200)
     v = torch.randn(64, net.m, dtype=torch.float64, device=dev)
     u = torch.randn(64, net.n, dtype=torch.float64, device=dev)
@@ -405,7 +411,9 @@ def run_other_configs(exago, synth, torch, np, dev):
     ms_jtv = time_calls(torch, lambda: exago.exago_eval_jtv(net.h, bt, v, o), 200)
     ms_hvp = time_calls(torch, lambda: exago.exago_eval_hvp(net.h, bt, u, o), 200)
     res["10k_bus_x64_scenarios"] = {"evals_per_s": 64e3 / ms, "ms_per_batch": ms,
-                                    "jtv_per_s": 64e3 / ms_jtv, "hvp_per_s": 64e3 / ms_hvp}
+                                    "jtv_per_s": 64e3 / ms_jtv, "hvp_per_s": 64e3 / ms_hvp,
+                                    "launch_config": {k: tuned[k] for k in
+                                                      ("schedule", "block", "occupancy", "tile_group")}}
     net.close()
     return res
 
