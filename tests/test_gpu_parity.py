@@ -81,6 +81,37 @@ def test_parallel_branches_and_shared_generator_bus(ex, oracle_mod):
         compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), "parallel")
 
 
+def test_isolated_and_zero_voltage_buses(ex, oracle_mod):
+    """The bus balances come from the sums of the ends' derivatives (degree-2 homogeneity in the
+    voltage magnitudes).  Cases where those sums are empty or degenerate: a bus whose every branch
+    is out of service (its balance is shunt, load and generation only), a bus at zero or negative
+    zero voltage, a bus with no branch at all, and very large shunts next to small flows."""
+    g = synth.make_grid(81, 40, 52, 9, shunts=True)
+    # one more bus, with a shunt, a load and a generator but no branch
+    g = synth.Grid(**{**g.__dict__, "nb": g.nb + 1,
+                      "Gs": np.append(g.Gs, 0.03), "Bs": np.append(g.Bs, -0.02),
+                      "Pd": np.append(g.Pd, 0.4), "Qd": np.append(g.Qd, 0.1),
+                      "gbus": np.append(g.gbus, g.nb).astype(np.int32), "c2": np.append(g.c2, 0.02),
+                      "c1": np.append(g.c1, 15.0), "c0": np.append(g.c0, 1.0)})
+    nb = g.nb
+    g.Gs[3] = 250.0                          # large shunt: the balance must not lose its flow terms
+    b = synth.random_batch(81, g, 6, masks=True, pd_scale=True, sigma=0.5)
+    deg = np.bincount(np.concatenate([g.f, g.t]), minlength=nb)
+    at = lambda i: np.flatnonzero((g.f == i) | (g.t == i))
+    b.mask[0, :] = 1
+    b.mask[0, at(7)] = 0                     # every branch of bus 7 out of service
+    b.mask[1, :] = 0                         # every branch out: balances are shunts, loads, gens
+    b.x[2, nb + 9] = 0.0                     # zero voltage
+    b.x[3, nb + 11] = -0.0                   # negative zero
+    b.x[4, nb:2 * nb] = 1.0
+    b.x[4, :nb] = 0.0                        # flat start
+    b.mask[5, at(int(np.argmax(deg)))] = 0   # the busiest bus loses all its branches
+    net = ex.Net(g)
+    out = gpu_eval(net, b)
+    for i in range(b.B):
+        compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"isolated/zero-V [{i}]")
+
+
 def test_single_bus_no_branches(ex, oracle_mod):
     g = synth.Grid(nb=1, Gs=np.array([0.1]), Bs=np.array([0.2]), Pd=np.array([0.3]),
                    Qd=np.array([0.1]), f=np.zeros(0, np.int32), t=np.zeros(0, np.int32),
