@@ -145,7 +145,7 @@ def test_autotune_picks_a_valid_configuration(ex):
     out = net.outputs(b.B)
     best = ex.exago_net_autotune(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"],
                                  out["hval"], reps=3)
-    assert best["schedule"] in (1, 2)
+    assert best["schedule"] in (1, 2, 3)
     ex.exago_net_set_config(net.h)     # automatic: uses the tuned choice for B = 64
     got = ex.exago_net_get_config(net.h, 64)
     assert got["schedule"] == best["schedule"]
