@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the benchma
 are the only callers.  Nothing here touches the CUDA library.
 
 The oracle evaluates the polar pi-model AC-OPF of ExaGO (arXiv 2203.10587, Sec. III, eqs. (7)-(10))
-for one state at a time; ``evaluate_batch`` loops over instances.  J and the lower-triangle
+for one state at a time; ``evaluate_batch`` loops over instances.  ``coupling`` and
+``coupling_jtv`` evaluate the linear coupling (ramp) rows between the states of a batch (eqs. (5)-(6),
+(15), (20), (31)) and their transpose product.  J and the lower-triangle
 Lagrangian Hessian come back as CSR (int64 row pointers, int32 ascending columns, float64 values).
 """
 from __future__ import annotations
@@ -60,6 +62,9 @@ def bind_library(path: str):
     lib.oracle_coo_capacity.argtypes = [ctypes.POINTER(_Net), vp, vp]
     lib.oracle_pi_model.argtypes = [ctypes.c_double] * 4 + [vp]
     lib.oracle_pi_model.restype = ctypes.c_int
+    for fn in (lib.oracle_coupling, lib.oracle_coupling_jtv):
+        fn.argtypes = [ctypes.c_int] * 4 + [vp, vp, vp]
+        fn.restype = ctypes.c_int
     return lib
 
 
@@ -175,6 +180,36 @@ def evaluate_batch(net: OracleNet, batch, **kw) -> list[dict]:
                             1.0 if batch.obj_weight is None else float(batch.obj_weight[b]),
                             batch.sigma, **kw))
     return res
+
+
+def coupling(parent, x, nb: int, ng: int, lib=None) -> np.ndarray:
+    """Coupling (ramp) rows r[B][ng] = Pg(x_b) - Pg(x_parent(b)) of the stacked states x [B][n]
+    (zero rows for parent -1); see oracle_coupling."""
+    lib = lib or _load()
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    B, n = x.shape
+    if parent.shape != (B,):
+        raise ValueError("parent shape")
+    r = np.zeros((B, ng))
+    if lib.oracle_coupling(B, n, nb, ng, _p(parent), _p(x), _p(r)) != 0:
+        raise ValueError("invalid parent index")
+    return r
+
+
+def coupling_jtv(parent, nu, n: int, nb: int, lib=None) -> np.ndarray:
+    """C^T nu in the stacked variable layout [B][n] for multipliers nu [B][ng] of the coupling
+    rows; see oracle_coupling_jtv."""
+    lib = lib or _load()
+    parent = np.ascontiguousarray(parent, dtype=np.int32)
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    B, ng = nu.shape
+    if parent.shape != (B,):
+        raise ValueError("parent shape")
+    out = np.zeros((B, n))
+    if lib.oracle_coupling_jtv(B, n, nb, ng, _p(parent), _p(nu), _p(out)) != 0:
+        raise ValueError("invalid parent index")
+    return out
 
 
 def csr_to_dense(csr, shape) -> np.ndarray:

@@ -22,6 +22,9 @@
  * (Sec. VI-A, eqs. (27)-(31)) enter as a per-bus load scale, and the scenario weight pi_s as a
  * factor on the objective.
  *
+ * The coupling (ramp) rows that tie the states of the multi-period, security-constrained and
+ * stochastic problems together (Sec. I, eqs. (5)-(6); eqs. (15), (20), (31)) are at the end of
+ * this file: oracle_coupling and its transpose product oracle_coupling_jtv.
  * Everything is evaluated directly, in plain loops, in the order: branches by ascending index
  * (from side, then to side), then bus shunts and loads, then generators.  Derivatives are the
  * chain rule through the branch angle theta = Va_u - Va_v, written out per side.  J and the
@@ -310,4 +313,47 @@ int64_t oracle_coo_to_csr(const oracle_coo *c, int nrows, int64_t *rowptr, int *
     for (r = 0; r < nrows; r++) rowptr[r + 1] += rowptr[r];
     free(keys);
     return nnz;
+}
+
+/* ---- Coupling (ramp) rows between the subproblems of the multi-stage problems ----
+ * The general problem (Sec. I, eqs. (5)-(6)), the multi-period problem (Sec. IV, eq. (15)), the
+ * security-constrained one (Sec. V-A, eq. (20)) and the stochastic one (Sec. VI-A, eq. (31)) tie
+ * each subproblem state x_b to one other state x_p(b) -- the previous time step, the base case,
+ * or the base scenario -- by a bounded difference  -delta <= x_b - x_p(b) <= delta.  The text
+ * names the generators' real power output as the quantity that is ramp-limited, so there is one
+ * row per (state b, generator k):
+ *     r[b][k] = Pg_k(x_b) - Pg_k(x_p(b)),
+ * with Pg_k(x_b) = x_b[2 nb + k].  A state with p(b) = -1 (the first period, the base case) has
+ * no rows; its entries of r are 0.  The states are stacked: x is [B][n], r is [B][ng].
+ * Returns 0, or -1 for a parent index outside [-1, B) or equal to b. */
+int oracle_coupling(int B, int n, int nb, int ng, const int *parent, const double *x, double *r)
+{
+    for (int b = 0; b < B; b++) {
+        int p = parent[b];
+        if (p < -1 || p >= B || p == b) return -1;
+        for (int k = 0; k < ng; k++)
+            r[(int64_t)b * ng + k] =
+                p < 0 ? 0.0 : x[(int64_t)b * n + 2 * nb + k] - x[(int64_t)p * n + 2 * nb + k];
+    }
+    return 0;
+}
+
+/* The transpose product  out = C^T nu  in the stacked variable layout [B][n], straight from the
+ * rows: row (b, k) holds +1 at column (b, Pg_k) and -1 at column (p(b), Pg_k), so its multiplier
+ * nu[b][k] is added to the first and subtracted from the second, rows taken in ascending (b, k).
+ * Every other entry of out is zero.  Returns 0, or -1 as oracle_coupling. */
+int oracle_coupling_jtv(int B, int n, int nb, int ng, const int *parent, const double *nu,
+                        double *out)
+{
+    for (int64_t i = 0; i < (int64_t)B * n; i++) out[i] = 0.0;
+    for (int b = 0; b < B; b++) {
+        int p = parent[b];
+        if (p < -1 || p >= B || p == b) return -1;
+        if (p < 0) continue;
+        for (int k = 0; k < ng; k++) {
+            out[(int64_t)b * n + 2 * nb + k] += nu[(int64_t)b * ng + k];
+            out[(int64_t)p * n + 2 * nb + k] -= nu[(int64_t)b * ng + k];
+        }
+    }
+    return 0;
 }

@@ -11,6 +11,7 @@ import pytest
 
 from oracle import acopf
 import test_oracle as T
+import test_oracle_coupling as TC
 
 SRC = os.path.join(os.path.dirname(acopf.__file__), "acopf_oracle.c")
 
@@ -41,6 +42,12 @@ MUTANTS = {
     "load_scale_dropped": ("net->Pd[i] * sc;", "net->Pd[i];"),
     "mask_ignored": ("P[s] *= m;", "P[s] *= 1.0;"),
     "gen_q_on_p_row": ("gQ[gb] -= Qg[k];", "gP[gb] -= Qg[k];"),
+    "coupling_sign": ("x[(int64_t)b * n + 2 * nb + k] - x[(int64_t)p * n + 2 * nb + k]",
+                      "x[(int64_t)b * n + 2 * nb + k] + x[(int64_t)p * n + 2 * nb + k]"),
+    "coupling_parent_stride": ("- x[(int64_t)p * n + 2 * nb + k]", "- x[(int64_t)p * ng + 2 * nb + k]"),
+    "coupling_root_row": ("p < 0 ? 0.0 :", "p < 0 ? x[(int64_t)b * n + 2 * nb + k] :"),
+    "coupling_jtv_parent_sign": ("out[(int64_t)p * n + 2 * nb + k] -=", "out[(int64_t)p * n + 2 * nb + k] +="),
+    "coupling_jtv_offset": ("out[(int64_t)b * n + 2 * nb + k] +=", "out[(int64_t)b * n + nb + k] +="),
 }
 
 
@@ -55,6 +62,12 @@ class Bound:
     def evaluate(self, *a, **k):
         return acopf.evaluate(*a, lib=self.lib, **k)
 
+    def coupling(self, *a, **k):
+        return acopf.coupling(*a, lib=self.lib, **k)
+
+    def coupling_jtv(self, *a, **k):
+        return acopf.coupling_jtv(*a, lib=self.lib, **k)
+
 
 PINS = [
     ("power_angle", lambda om: T.test_power_angle_equations_lossless_line(om)),
@@ -68,6 +81,10 @@ PINS = [
     ("fd_sigma0", lambda om: T.test_finite_differences_sigma_zero_and_transformers(om)),
     ("mask", lambda om: T.test_mask_equals_branch_removed(om)),
     ("symmetries", lambda om: T.test_homogeneity_and_angle_invariance(om)),
+    ("coupling_hand", lambda om: TC.test_hand_rows(om)),
+    ("coupling_hand_transpose", lambda om: TC.test_hand_transpose(om)),
+    ("coupling_telescopes", lambda om: TC.test_chain_telescopes(om)),
+    ("coupling_transpose", lambda om: TC.test_transpose_identity(om, 9, 40, 5)),
 ]
 
 
