@@ -418,6 +418,58 @@ def run_other_configs(exago, synth, torch, np, dev):
     return res
 
 
+def run_coupling(exago, synth, torch, np, dev, hbm_peak):
+    """The coupling (ramp) rows between the states of a batch and their transpose product, on
+    three workloads: the 2,000-bus x 512 N-1 batch (511 contingencies tied to the base case), a
+    10,000-bus grid over 64 periods and a 70,000-bus grid over 512 periods (chains).  Each launch
+    is timed alone with CUDA events after a 256 MB write has flushed L2 ("cold"), and back to back
+    ("warm", inputs in L2 as right after the solver wrote them).  Algorithmic bytes: forward -- Pg
+    of every state read once, r written, parent indices; transpose -- nu read, out written, the
+    parent and child tables."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    for name, grid, kind, B in (("2000bus_x512_contingencies", synth.grid_2000, "star", 512),
+                                ("10k_bus_x64_periods", synth.grid_10k, "chain", 64),
+                                ("70k_bus_x512_periods", lambda: synth.grid_sized(9, 70_000),
+                                 "chain", 512)):
+        g = grid()
+        net = exago.Net(g)
+        parent = synth.coupling_parents(kind, B)
+        h = exago.exago_coupling_create(net.h, parent)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(11)
+        x = torch.randn(B, net.n, dtype=torch.float64, device=dev, generator=gen)
+        nu = torch.randn(B, g.ng, dtype=torch.float64, device=dev, generator=gen)
+        r = torch.empty(B, g.ng, dtype=torch.float64, device=dev)
+        o = torch.empty(B, g.ng, dtype=torch.float64, device=dev)
+        fwd = lambda: exago.exago_eval_coupling(h, x, r)
+        jtv = lambda: exago.exago_eval_coupling_jtv(h, nu, o, g.ng)
+        nchild = int((parent >= 0).sum())
+        bytes_fwd = 2 * B * g.ng * 8 + 4 * B
+        bytes_jtv = 2 * B * g.ng * 8 + 4 * (3 * B + 1 + nchild)
+        out = {"states": B, "ng": g.ng, "structure": kind}
+        for what, fn, nbytes in (("rows", fwd, bytes_fwd), ("transpose", jtv, bytes_jtv)):
+            warm = time_calls(torch, fn, 500)
+            cold = []
+            for _ in range(50):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                cold.append(e0.elapsed_time(e1))
+            cold_ms = float(np.median(cold))
+            out[what] = {"warm_us": warm * 1e3, "cold_us": cold_ms * 1e3,
+                         "algorithmic_bytes": nbytes,
+                         "cold_gbs": nbytes / (cold_ms * 1e-3) / 1e9,
+                         "cold_frac_hbm": nbytes / (cold_ms * 1e-3) / 1e9 / hbm_peak}
+        exago.exago_coupling_destroy(h)
+        net.close()
+        res[name] = out
+    return res
+
+
 def run_serve(exago, synth, torch, np, dev, seconds):
     rng = np.random.default_rng(5)
     sc = ServeClients(exago, synth, torch, np, dev)
@@ -628,6 +680,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         return
     serve = None if args.no_serve else run_serve(exago, synth, torch, np, dev, args.serve_seconds)
     others = None if args.no_serve else run_other_configs(exago, synth, torch, np, dev)
+    coupling = None if args.no_serve else run_coupling(exago, synth, torch, np, dev, hbm_peak)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -668,6 +721,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         res["serve"] = serve
     if others is not None:
         res["other_workloads"] = others
+    if coupling is not None:
+        res["coupling_rows"] = coupling
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_evals = 256 * cores

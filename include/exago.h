@@ -192,6 +192,55 @@ exago_status exago_eval_jtv(exago_net_t net, const exago_batch *batch, const dou
 exago_status exago_eval_hvp(exago_net_t net, const exago_batch *batch, const double *u, double *out);
 
 /*
+ * Coupling (ramp) rows between the states of a batch.  ExaGO's multi-stage problems tie each
+ * subproblem's state to one other state by a bounded difference: consecutive periods of the
+ * multi-period problem (Sec. IV, eq. (15)), each contingency to the base case (Sec. V-A,
+ * eq. (20)), each scenario to the base scenario (Sec. VI-A, eq. (31)), and trees of these (the
+ * general form, Sec. I, eqs. (5)-(6)).  The ramp-limited quantity is the generators' real power, so
+ * with parent p(b) of state b (-1: none) there is one row per (state b, generator k):
+ *     r[b][k] = Pg_k(x_b) - Pg_k(x_p(b)),   bounds -delta_k <= r <= delta_k (solver data).
+ * A state without a parent keeps its ng rows, which are zero and have no Jacobian entries.  The
+ * rows are linear: exago_eval_coupling applied to a direction u is the Jacobian-vector product, the
+ * Jacobian values are constants, and the rows add nothing to the Lagrangian Hessian.
+ *
+ *   exago_coupling_create   parent: HOST [B], each -1 or another state's index (not b itself);
+ *                           copied, so the caller keeps its array.  Any parent structure is
+ *                           accepted (chains, stars, trees, forests).  A net made by
+ *                           exago_net_plan gives a host-only coupling (dims and pattern only;
+ *                           evaluations return ESTATE).  The net's device must be current.
+ *                           EINVAL for a NULL net or out, B < 0, a NULL parent with B > 0 or a
+ *                           parent index outside [-1, B) or equal to its state; ENOMEM if the
+ *                           device tables cannot be allocated.  The coupling does not refer to the
+ *                           net after creation.
+ *   exago_coupling_dims     B, rows = B ng, nnz = 2 ng x (states with a parent).
+ *   exago_coupling_jac_pattern  HOST outputs: rowptr [rows + 1], col [nnz] and, if not NULL,
+ *                           val [nnz] of the Jacobian with respect to the stacked variables of all
+ *                           states: the column of (state b, Pg_k) is b n + 2 nb + k; +1 on the
+ *                           row's own state, -1 on its parent's; columns ascending within a row.
+ *   exago_eval_coupling     r [B][ng] from x [B][n] (DEVICE buffers, row-major per state), queued on
+ *                           stream.  Bitwise the definition above (one subtraction per value).
+ *   exago_eval_coupling_jtv out = C^T nu restricted to the Pg columns: for every state b and k,
+ *                           out[b ldo + k] = [p(b) >= 0] nu[b][k] - sum over the children c of b
+ *                           (states with p(c) = b) of nu[c][k];  (C^T nu) is zero in every other
+ *                           column.  nu [B][ng]; out holds (B - 1) ldo + ng doubles and must not
+ *                           overlap nu; ldo >= ng.  accumulate = 0 stores, 1 adds to out.  To add
+ *                           C^T nu to a [B][n] gradient g, pass out = g + 2 nb and ldo = n.  The
+ *                           children are summed in a fixed order (deterministic, no atomics).
+ * Errors of the evaluations: EINVAL for NULL pointers (B > 0) or a different current device;
+ * ECUDA if a launch fails.  B = 0 or ng = 0 does nothing.
+ */
+typedef struct exago_coupling *exago_coupling_t;
+exago_status exago_coupling_create(exago_net_t net, int B, const int *parent,
+                                   exago_coupling_t *out);
+exago_status exago_coupling_destroy(exago_coupling_t cpl);
+exago_status exago_coupling_dims(exago_coupling_t cpl, int *B, int64_t *rows, int64_t *nnz);
+exago_status exago_coupling_jac_pattern(exago_coupling_t cpl, int64_t *rowptr, int64_t *col,
+                                        double *val);
+exago_status exago_eval_coupling(exago_coupling_t cpl, const double *x, double *r, void *stream);
+exago_status exago_eval_coupling_jtv(exago_coupling_t cpl, const double *nu, double *out,
+                                     int64_t ldo, int accumulate, void *stream);
+
+/*
  * exago_eval_all without any allocation.  The paper has no counterpart: this serves callers that
  * may not allocate device memory once running -- for example a solver whose device memory belongs
  * to a pooling allocator (a raw cudaMalloc would bypass it, and cudaFree synchronises the device),

@@ -33,7 +33,9 @@ EXPORTS = [
     "exago_eval_profile", "exago_net_set_config", "exago_net_get_config", "exago_net_autotune",
     "exago_net_check", "exago_serve_create", "exago_serve_register", "exago_serve_submit",
     "exago_serve_set_merge", "exago_serve_poll", "exago_serve_wait", "exago_serve_stats",
-    "exago_serve_destroy", "exago_test_fail_allocations",
+    "exago_serve_destroy", "exago_test_fail_allocations", "exago_coupling_create",
+    "exago_coupling_destroy", "exago_coupling_dims", "exago_coupling_jac_pattern",
+    "exago_eval_coupling", "exago_eval_coupling_jtv",
 ]
 
 SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
@@ -125,6 +127,12 @@ def lib():
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_uint64)], i32),
                 "exago_serve_destroy": ([vp], i32),
+                "exago_coupling_create": ([vp, i32, vp, ctypes.POINTER(vp)], i32),
+                "exago_coupling_destroy": ([vp], i32),
+                "exago_coupling_dims": ([vp, ctypes.POINTER(i32), i64p, i64p], i32),
+                "exago_coupling_jac_pattern": ([vp, vp, vp, vp], i32),
+                "exago_eval_coupling": ([vp, vp, vp, vp], i32),
+                "exago_eval_coupling_jtv": ([vp, vp, vp, ctypes.c_int64, i32, vp], i32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -398,6 +406,56 @@ def exago_serve_stats(s):
 
 def exago_serve_destroy(s):
     _check(lib().exago_serve_destroy(s))
+
+
+def exago_coupling_create(net_h, parent):
+    """Coupling rows of a batch whose state b is tied to state parent[b] (-1: none); host array."""
+    parent = _np(parent, np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().exago_coupling_create(net_h, int(parent.shape[0]), _hp(parent), ctypes.byref(h)))
+    return h
+
+
+def exago_coupling_destroy(h):
+    _check(lib().exago_coupling_destroy(h))
+
+
+def exago_coupling_dims(h):
+    B, rows, nnz = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().exago_coupling_dims(h, ctypes.byref(B), ctypes.byref(rows), ctypes.byref(nnz)))
+    return B.value, rows.value, nnz.value
+
+
+def exago_coupling_jac_pattern(h):
+    """(rowptr, col, val) of the coupling rows' Jacobian over the stacked variables of all states."""
+    _, rows, nnz = exago_coupling_dims(h)
+    rowptr = np.zeros(rows + 1, np.int64)
+    col = np.zeros(max(nnz, 1), np.int64)
+    val = np.zeros(max(nnz, 1), np.float64)
+    _check(lib().exago_coupling_jac_pattern(h, _hp(rowptr), _hp(col), _hp(val)))
+    return rowptr, col[:nnz], val[:nnz]
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def exago_eval_coupling(h, x, r, stream=None):
+    """r [B][ng] = Pg(x_b) - Pg(x_parent(b)) for x [B][n] (CUDA float64 tensors)."""
+    import torch
+    _check(lib().exago_eval_coupling(h, _dp(x, torch.float64), _out(r), _stream_ptr(stream)))
+
+
+def exago_eval_coupling_jtv(h, nu, out, ldo: int, accumulate: bool = False, stream=None):
+    """out[b * ldo + k] (+)= (C^T nu) at (state b, Pg_k); out is a CUDA float64 tensor or a raw
+    device address (an int), e.g. grad.data_ptr() + 16 * nb to add into a [B][n] gradient."""
+    import torch
+    optr = out if isinstance(out, int) else _out(out)
+    _check(lib().exago_eval_coupling_jtv(h, _dp(nu, torch.float64), optr, int(ldo),
+                                         1 if accumulate else 0, _stream_ptr(stream)))
 
 
 # ---- convenience ------------------------------------------------------------------------------

@@ -283,3 +283,25 @@ def grid_2000() -> Grid:
 def grid_sized(seed: int, nb: int) -> Grid:
     """Serving-mix grid: nl = round(1.3 nb), ng = round(nb / 4)."""
     return make_grid(seed, nb, int(round(1.3 * nb)), int(round(nb / 4)))
+
+
+def coupling_parents(kind: str, B: int, seed: int = 0, roots: int = 1):
+    """Parent index of each state of a coupled batch (-1: none), as the multi-stage problems tie
+    their subproblems together: "chain" -- consecutive periods (state t tied to t - 1); "star" --
+    contingencies or scenarios tied to state 0, the base case; "forest" -- a random forest with
+    `roots` roots (e.g. contingencies of several multi-period cases)."""
+    if kind == "chain":
+        return np.arange(-1, B - 1, dtype=np.int32)
+    if kind == "star":
+        p = np.zeros(B, np.int32)
+        if B:
+            p[0] = -1
+        return p
+    if kind == "forest":
+        rng = _rng(seed)
+        order = rng.permutation(B)
+        p = np.full(B, -1, np.int32)
+        for j in range(min(roots, B), B):
+            p[order[j]] = order[rng.integers(0, j)]
+        return p
+    raise ValueError(kind)

@@ -270,3 +270,70 @@ def test_create_without_gpu_fails_cleanly(L):
     with pytest.raises(exago.ExagoError) as ei:
         exago.Net(synth.grid_30bus())
     assert ei.value.name in ("EXAGO_ECUDA", "EXAGO_ENOMEM")
+
+
+# ---- coupling (ramp) rows: host side ---------------------------------------------------------
+
+def coupling_parents():
+    rng = np.random.default_rng(31)
+    B = 40
+    forest = np.full(B, -1, np.int32)
+    order = rng.permutation(B)
+    for j in range(3, B):
+        forest[order[j]] = order[rng.integers(0, j)]
+    return {"chain": np.arange(-1, 9, dtype=np.int32),
+            "star": np.array([-1] + [0] * 20, np.int32),
+            "star_last": np.array([5] * 5 + [-1], np.int32),
+            "forest": forest,
+            "roots": np.full(4, -1, np.int32)}
+
+
+@pytest.mark.parametrize("kind", sorted(coupling_parents()))
+def test_coupling_pattern_matches_oracle(L, oracle_mod, kind):
+    """The exported Jacobian of the coupling rows equals the oracle's rows applied to unit vectors
+    (the rows are linear, so this recovers the exact Jacobian)."""
+    g = synth.make_grid(8, 12, 16, 3)
+    net = plan(g)
+    parent = coupling_parents()[kind]
+    B = parent.shape[0]
+    h = exago.exago_coupling_create(net.h, parent)
+    try:
+        Bc, rows, nnz = exago.exago_coupling_dims(h)
+        assert (Bc, rows, nnz) == (B, B * g.ng, 2 * g.ng * int((parent >= 0).sum()))
+        rowptr, col, val = exago.exago_coupling_jac_pattern(h)
+        dense = np.zeros((rows, B * net.n))
+        for r in range(rows):
+            cols = col[rowptr[r]:rowptr[r + 1]]
+            assert np.all(np.diff(cols) > 0)
+            dense[r, cols] = val[rowptr[r]:rowptr[r + 1]]
+        ref = np.zeros_like(dense)
+        for j in range(B * net.n):
+            e = np.zeros(B * net.n)
+            e[j] = 1.0
+            ref[:, j] = oracle_mod.coupling(parent, e.reshape(B, net.n), g.nb, g.ng).reshape(-1)
+        np.testing.assert_array_equal(dense, ref)
+    finally:
+        exago.exago_coupling_destroy(h)
+
+
+@pytest.mark.parametrize("bad", [[-2, 0], [0, 0], [-1, 2], [1, 0, 3]])
+def test_coupling_rejects_invalid_parents(L, bad):
+    net = plan(synth.grid_30bus())
+    with pytest.raises(exago.ExagoError) as ei:
+        exago.exago_coupling_create(net.h, np.array(bad, np.int32))
+    assert ei.value.name == "EXAGO_EINVAL"
+
+
+def test_coupling_host_only_refuses_evaluation(L):
+    net = plan(synth.grid_30bus())
+    h = exago.exago_coupling_create(net.h, np.array([-1, 0], np.int32))
+    try:
+        rc = L.exago_eval_coupling(h, ctypes.c_void_p(8), ctypes.c_void_p(8), None)
+        assert exago.STATUS[rc] == "EXAGO_ESTATE"
+        rc = L.exago_eval_coupling_jtv(h, ctypes.c_void_p(8), ctypes.c_void_p(8), 6, 0, None)
+        assert exago.STATUS[rc] == "EXAGO_ESTATE"
+    finally:
+        exago.exago_coupling_destroy(h)
+    h = exago.exago_coupling_create(net.h, np.zeros(0, np.int32))
+    assert exago.exago_coupling_dims(h) == (0, 0, 0)
+    exago.exago_coupling_destroy(h)
