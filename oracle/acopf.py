@@ -6,7 +6,8 @@ are the only callers.  Nothing here touches the CUDA library.
 The oracle evaluates the polar pi-model AC-OPF of ExaGO (arXiv 2203.10587, Sec. III, eqs. (7)-(10))
 for one state at a time; ``evaluate_batch`` loops over instances.  ``coupling`` and
 ``coupling_jtv`` evaluate the linear coupling (ramp) rows between the states of a batch (eqs. (5)-(6),
-(15), (20), (31)) and their transpose product.  J and the lower-triangle
+(15), (20), (31)) and their transpose product.  ``evaluate(..., cartesian=True)`` evaluates the
+power-balance-cartesian formulation that Sec. III names beside the polar one.  J and the lower-triangle
 Lagrangian Hessian come back as CSR (int64 row pointers, int32 ascending columns, float64 values).
 """
 from __future__ import annotations
@@ -60,6 +61,9 @@ def bind_library(path: str):
     lib.oracle_coo_to_csr.argtypes = [ctypes.POINTER(_Coo), ctypes.c_int, vp, vp, vp]
     lib.oracle_coo_to_csr.restype = ctypes.c_int64
     lib.oracle_coo_capacity.argtypes = [ctypes.POINTER(_Net), vp, vp]
+    lib.oracle_eval_cart.argtypes = lib.oracle_eval.argtypes
+    lib.oracle_eval_cart.restype = ctypes.c_int
+    lib.oracle_coo_capacity_cart.argtypes = [ctypes.POINTER(_Net), vp, vp]
     lib.oracle_pi_model.argtypes = [ctypes.c_double] * 4 + [vp]
     lib.oracle_pi_model.restype = ctypes.c_int
     for fn in (lib.oracle_coupling, lib.oracle_coupling_jtv):
@@ -130,18 +134,22 @@ def _csr(lib, coo: _Coo, nrows: int):
 
 def evaluate(net: OracleNet, x, lam, mask=None, pd_scale=None, obj_weight: float = 1.0,
              sigma: float = 1.0, want_jac: bool = True, want_hess: bool = True,
-             lib=None) -> dict:
-    """One evaluation.  Returns f, grad[n], gh[m], and J / H as (rowptr, col, val) CSR."""
+             lib=None, cartesian: bool = False) -> dict:
+    """One evaluation.  Returns f, grad[n], gh[m], and J / H as (rowptr, col, val) CSR.
+    cartesian=True evaluates the power-balance-cartesian formulation (oracle_eval_cart): x holds
+    [e | f | Pg | Qg] and lam, gh have m + nb entries (the voltage rows last)."""
     lib = lib or _load()
     x = np.ascontiguousarray(x, dtype=np.float64)
     lam = np.ascontiguousarray(lam, dtype=np.float64)
-    if x.shape != (net.n,) or lam.shape != (net.m,):
+    m = net.m + net.nb if cartesian else net.m
+    if x.shape != (net.n,) or lam.shape != (m,):
         raise ValueError("x / lam shape")
     mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     pd_scale = None if pd_scale is None else np.ascontiguousarray(pd_scale, dtype=np.float64)
     capJ = ctypes.c_int64()
     capH = ctypes.c_int64()
-    lib.oracle_coo_capacity(ctypes.byref(net.c), ctypes.addressof(capJ), ctypes.addressof(capH))
+    (lib.oracle_coo_capacity_cart if cartesian else lib.oracle_coo_capacity)(
+        ctypes.byref(net.c), ctypes.addressof(capJ), ctypes.addressof(capH))
     keep = []
 
     def coo(cap):
@@ -155,8 +163,8 @@ def evaluate(net: OracleNet, x, lam, mask=None, pd_scale=None, obj_weight: float
     H = coo(capH.value) if want_hess else None
     fval = np.zeros(1)
     grad = np.zeros(net.n)
-    gh = np.zeros(net.m)
-    rc = lib.oracle_eval(ctypes.byref(net.c), _p(x), _p(lam), _p(mask), _p(pd_scale),
+    gh = np.zeros(m)
+    rc = (lib.oracle_eval_cart if cartesian else lib.oracle_eval)(ctypes.byref(net.c), _p(x), _p(lam), _p(mask), _p(pd_scale),
                          float(obj_weight), float(sigma), _p(fval), _p(grad), _p(gh),
                          ctypes.byref(J) if J is not None else None,
                          ctypes.byref(H) if H is not None else None)
@@ -164,7 +172,7 @@ def evaluate(net: OracleNet, x, lam, mask=None, pd_scale=None, obj_weight: float
         raise ValueError(f"oracle_eval failed ({rc})")
     out = {"f": float(fval[0]), "grad": grad, "gh": gh}
     if J is not None:
-        out["J"] = _csr(lib, J, net.m)
+        out["J"] = _csr(lib, J, m)
     if H is not None:
         out["H"] = _csr(lib, H, net.n)
     return out

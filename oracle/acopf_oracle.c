@@ -22,6 +22,9 @@
  * (Sec. VI-A, eqs. (27)-(31)) enter as a per-bus load scale, and the scenario weight pi_s as a
  * factor on the objective.
  *
+ * The power-balance-cartesian formulation, which Sec. III names beside the polar one, is
+ * oracle_eval_cart (voltages e + j f, voltage-magnitude rows e^2 + f^2); it shares the branch-end
+ * rows (end_rows) and generator terms (gen_terms) with the polar evaluation.
  * The coupling (ramp) rows that tie the states of the multi-period, security-constrained and
  * stochastic problems together (Sec. I, eqs. (5)-(6); eqs. (15), (20), (31)) are at the end of
  * this file: oracle_coupling and its transpose product oracle_coupling_jtv.
@@ -144,6 +147,82 @@ static int push_sym(oracle_coo *c, int gi, int gj, double v)
     return gi >= gj ? push(c, gi, gj, v) : push(c, gj, gi, v);
 }
 
+/* One branch end's rows, shared by both formulations: the end's injection into its bus's balances,
+ * its h value |S|^2, its Jacobian entries (P, Q and h rows over the end's four variables gidx)
+ * and its Lagrangian-Hessian block  lamP_u grad^2 P + lamQ_u grad^2 Q + mu grad^2 (P^2 + Q^2),
+ * with grad^2 (P^2 + Q^2) = 2 (dP dP' + P HP + dQ dQ' + Q HQ).  m (0 or 1) is the branch's
+ * in-service flag and multiplies every term.  Returns 0 or -2 when a triplet array is full. */
+static int end_rows(int nb, int u, int hrow, double m, double lamPu, double lamQu, double mu,
+                    double P0, double Q0, const double *dP0, const double *dQ0,
+                    const double *HP0, const double *HQ0, const int *gidx,
+                    double *gP, double *gQ, double *hval, oracle_coo *J, oracle_coo *H)
+{
+    double P = P0, Q = Q0, dP[4], dQ[4], HP[16], HQ[16], Hs[16];
+    int a, bb;
+    for (a = 0; a < 4; a++) { dP[a] = dP0[a]; dQ[a] = dQ0[a]; }
+    for (a = 0; a < 16; a++) { HP[a] = HP0[a]; HQ[a] = HQ0[a]; }
+    P *= m;
+    Q *= m;
+    for (a = 0; a < 4; a++) { dP[a] *= m; dQ[a] *= m; }
+    for (a = 0; a < 16; a++) { HP[a] *= m; HQ[a] *= m; }
+
+    /* g: this end's injection enters the balance of its own bus u */
+    gP[u] += P;
+    gQ[u] += Q;
+    /* h: squared apparent power at this end */
+    *hval = P * P + Q * Q;
+
+    if (J) {
+        for (a = 0; a < 4; a++) {
+            if (push(J, u, gidx[a], dP[a])) return -2;
+            if (push(J, nb + u, gidx[a], dQ[a])) return -2;
+        }
+        for (a = 0; a < 4; a++) /* grad |S|^2 = 2 P grad P + 2 Q grad Q */
+            if (push(J, hrow, gidx[a], 2.0 * P * dP[a] + 2.0 * Q * dQ[a])) return -2;
+    }
+    if (H) {
+        for (a = 0; a < 4; a++)
+            for (bb = 0; bb < 4; bb++)
+                Hs[a * 4 + bb] = lamPu * HP[a * 4 + bb] + lamQu * HQ[a * 4 + bb]
+                    + mu * 2.0 * (dP[a] * dP[bb] + P * HP[a * 4 + bb]
+                                  + dQ[a] * dQ[bb] + Q * HQ[a * 4 + bb]);
+        for (a = 0; a < 4; a++)
+            for (bb = a; bb < 4; bb++)
+                if (push_sym(H, gidx[a], gidx[bb], Hs[a * 4 + bb])) return -2;
+    }
+    return 0;
+}
+
+/* Generators, shared by both formulations: injection -Pg, -Qg at their bus, cost in MW
+ * (f = w sum c2 MW^2 + c1 MW + c0, MW = baseMVA Pg), its gradient and Hessian (sigma-weighted),
+ * and the -1 Jacobian entries.  Returns 0, -1 on a bad bus index, -2 when a triplet array is full. */
+static int gen_terms(const oracle_net *net, const double *Pg, const double *Qg, double w,
+                     double sigma, double *gP, double *gQ, double *fval, double *grad,
+                     oracle_coo *J, oracle_coo *H)
+{
+    const int nb = net->nb, ng = net->ng;
+    const double base = net->baseMVA;
+    int k;
+    *fval = 0.0;
+    for (k = 0; k < ng; k++) {
+        int gb = net->gbus[k];
+        double MW = base * Pg[k];
+        if (gb < 0 || gb >= nb) return -1;
+        gP[gb] -= Pg[k];
+        gQ[gb] -= Qg[k];
+        *fval += w * (net->c2[k] * MW * MW + net->c1[k] * MW + net->c0[k]);
+        grad[2 * nb + k] = w * (2.0 * net->c2[k] * base * base * Pg[k] + net->c1[k] * base);
+        if (J) {
+            if (push(J, gb, 2 * nb + k, -1.0)) return -2;
+            if (push(J, nb + gb, 2 * nb + ng + k, -1.0)) return -2;
+        }
+        if (H) {
+            if (push(H, 2 * nb + k, 2 * nb + k, sigma * w * 2.0 * net->c2[k] * base * base)) return -2;
+        }
+    }
+    return 0;
+}
+
 /* Capacity the triplet arrays need for one evaluation. */
 void oracle_coo_capacity(const oracle_net *net, int64_t *capJ, int64_t *capH)
 {
@@ -167,8 +246,7 @@ int oracle_eval(const oracle_net *net, const double *x, const double *lam, const
     const double *Va = x, *Vm = x + nb, *Pg = x + 2 * nb, *Qg = x + 2 * nb + ng;
     const double *lamP = lam, *lamQ = lam + nb, *muF = lam + 2 * nb, *muT = lam + 2 * nb + nl;
     double *gP = gh, *gQ = gh + nb, *hF = gh + 2 * nb, *hT = gh + 2 * nb + nl;
-    const double base = net->baseMVA;
-    int i, l, k, a, bb;
+    int i, l;
 
     for (i = 0; i < 2 * nb + 2 * nl; i++) gh[i] = 0.0;
     for (i = 0; i < n; i++) grad[i] = 0.0;
@@ -192,42 +270,11 @@ int oracle_eval(const oracle_net *net, const double *x, const double *lam, const
         gidx[1][0] = tb; gidx[1][1] = fb; gidx[1][2] = nb + tb; gidx[1][3] = nb + fb;
 
         for (s = 0; s < 2; s++) {
-            int u = s == 0 ? fb : tb;
-            double mu = s == 0 ? muF[l] : muT[l];
-            double Hs[16];
-            P[s] *= m;
-            Q[s] *= m;
-            for (a = 0; a < 4; a++) { dP[s][a] *= m; dQ[s][a] *= m; }
-            for (a = 0; a < 16; a++) { HP[s][a] *= m; HQ[s][a] *= m; }
-
-            /* g: this end's injection enters the balance of its own bus u */
-            gP[u] += P[s];
-            gQ[u] += Q[s];
-            /* h: squared apparent power at this end */
-            (s == 0 ? hF : hT)[l] = P[s] * P[s] + Q[s] * Q[s];
-
-            if (J) {
-                int hrow = 2 * nb + (s == 0 ? l : nl + l);
-                for (a = 0; a < 4; a++) {
-                    if (push(J, u, gidx[s][a], dP[s][a])) return -2;
-                    if (push(J, nb + u, gidx[s][a], dQ[s][a])) return -2;
-                }
-                for (a = 0; a < 4; a++) /* grad |S|^2 = 2 P grad P + 2 Q grad Q */
-                    if (push(J, hrow, gidx[s][a], 2.0 * P[s] * dP[s][a] + 2.0 * Q[s] * dQ[s][a]))
-                        return -2;
-            }
-            if (H) {
-                /* lamP_u grad^2 P + lamQ_u grad^2 Q
-                   + mu * grad^2 (P^2 + Q^2),  grad^2 (P^2+Q^2) = 2 (dP dP' + P HP + dQ dQ' + Q HQ) */
-                for (a = 0; a < 4; a++)
-                    for (bb = 0; bb < 4; bb++)
-                        Hs[a * 4 + bb] = lamP[u] * HP[s][a * 4 + bb] + lamQ[u] * HQ[s][a * 4 + bb]
-                            + mu * 2.0 * (dP[s][a] * dP[s][bb] + P[s] * HP[s][a * 4 + bb]
-                                          + dQ[s][a] * dQ[s][bb] + Q[s] * HQ[s][a * 4 + bb]);
-                for (a = 0; a < 4; a++)
-                    for (bb = a; bb < 4; bb++)
-                        if (push_sym(H, gidx[s][a], gidx[s][bb], Hs[a * 4 + bb])) return -2;
-            }
+            int rc = end_rows(nb, s == 0 ? fb : tb, 2 * nb + (s == 0 ? l : nl + l), m,
+                              lamP[s == 0 ? fb : tb], lamQ[s == 0 ? fb : tb],
+                              s == 0 ? muF[l] : muT[l], P[s], Q[s], dP[s], dQ[s], HP[s], HQ[s],
+                              gidx[s], gP, gQ, (s == 0 ? hF : hT) + l, J, H);
+            if (rc) return rc;
         }
     }
 
@@ -251,24 +298,7 @@ int oracle_eval(const oracle_net *net, const double *x, const double *lam, const
     }
 
     /* generators: injection -Pg, -Qg at their bus; cost in MW */
-    *fval = 0.0;
-    for (k = 0; k < ng; k++) {
-        int gb = net->gbus[k];
-        double MW = base * Pg[k];
-        if (gb < 0 || gb >= nb) return -1;
-        gP[gb] -= Pg[k];
-        gQ[gb] -= Qg[k];
-        *fval += w * (net->c2[k] * MW * MW + net->c1[k] * MW + net->c0[k]);
-        grad[2 * nb + k] = w * (2.0 * net->c2[k] * base * base * Pg[k] + net->c1[k] * base);
-        if (J) {
-            if (push(J, gb, 2 * nb + k, -1.0)) return -2;
-            if (push(J, nb + gb, 2 * nb + ng + k, -1.0)) return -2;
-        }
-        if (H) {
-            if (push(H, 2 * nb + k, 2 * nb + k, sigma * w * 2.0 * net->c2[k] * base * base)) return -2;
-        }
-    }
-    return 0;
+    return gen_terms(net, Pg, Qg, w, sigma, gP, gQ, fval, grad, J, H);
 }
 
 /* ---- sum duplicate triplets into CSR with ascending columns ---- */
@@ -356,4 +386,130 @@ int oracle_coupling_jtv(int B, int n, int nb, int ng, const int *parent, const d
         }
     }
     return 0;
+}
+
+/* ---- Power-balance-cartesian formulation (Sec. III names it beside the polar one) ----
+ * The same network, balances, flow limits and cost, with the bus voltage in rectangular form
+ * V_i = e_i + j f_i:
+ *   variables     x   = [e (nb) | f (nb) | Pg (ng) | Qg (ng)]
+ *   equalities    g   = [P balance (nb) | Q balance (nb)]
+ *   inequalities  h   = [|S_from|^2 (nl) | |S_to|^2 (nl) | e_i^2 + f_i^2 (nb)]
+ *   multipliers   lam = [lamP (nb) | lamQ (nb) | muF (nl) | muT (nl) | muV (nb)]
+ * The voltage-magnitude limits, simple bounds on Vm in the polar model, become the last nb rows:
+ * Vmin^2 <= e^2 + f^2 <= Vmax^2.
+ * One end of a branch, from its bus u towards v, with a = e_u e_v + f_u f_v (= Vu Vv cos th),
+ * b = f_u e_v - e_u f_v (= Vu Vv sin th) and s = e_u^2 + f_u^2 (= Vu^2):
+ *   P =  Gss s + Gm a + Bm b
+ *   Q = -Bss s + Gm b - Bm a
+ * Both are linear in (s, a, b), so their gradients and (constant) Hessians follow from those of
+ * s, a and b in the local order (e_u, f_u, e_v, f_v). */
+static void side_terms_cart(double Gss, double Bss, double Gm, double Bm,
+                            double eu, double fu, double ev, double fv,
+                            double *P, double *Q, double *dP, double *dQ, double *HP, double *HQ)
+{
+    const double da[4] = {ev, fv, eu, fu};
+    const double db[4] = {-fv, ev, fu, -eu};
+    const double ds[4] = {2.0 * eu, 2.0 * fu, 0.0, 0.0};
+    static const double Ha[16] = {0, 0, 1, 0,  0, 0, 0, 1,  1, 0, 0, 0,  0, 1, 0, 0};
+    static const double Hb[16] = {0, 0, 0, -1,  0, 0, 1, 0,  0, 1, 0, 0,  -1, 0, 0, 0};
+    static const double Hs[16] = {2, 0, 0, 0,  0, 2, 0, 0,  0, 0, 0, 0,  0, 0, 0, 0};
+    double a = eu * ev + fu * fv;
+    double b = fu * ev - eu * fv;
+    double s = eu * eu + fu * fu;
+    int i;
+    *P = Gss * s + Gm * a + Bm * b;
+    *Q = -Bss * s + Gm * b - Bm * a;
+    for (i = 0; i < 4; i++) {
+        dP[i] = Gss * ds[i] + Gm * da[i] + Bm * db[i];
+        dQ[i] = -Bss * ds[i] + Gm * db[i] - Bm * da[i];
+    }
+    for (i = 0; i < 16; i++) {
+        HP[i] = Gss * Hs[i] + Gm * Ha[i] + Bm * Hb[i];
+        HQ[i] = -Bss * Hs[i] + Gm * Hb[i] - Bm * Ha[i];
+    }
+}
+
+/* Capacity the triplet arrays need for one cartesian evaluation. */
+void oracle_coo_capacity_cart(const oracle_net *net, int64_t *capJ, int64_t *capH)
+{
+    *capJ = 24 * (int64_t)net->nl + 6 * (int64_t)net->nb + 2 * (int64_t)net->ng;
+    *capH = 20 * (int64_t)net->nl + 5 * (int64_t)net->nb + (int64_t)net->ng;
+}
+
+/*
+ * One cartesian evaluation: arguments and returns as oracle_eval, with x[n] = [e | f | Pg | Qg],
+ * lam[m] and gh[m] of m = 3 nb + 2 nl (the voltage rows last).  Triplets are emitted for every
+ * structural dependency: per branch end its P, Q and h rows over (e_u, f_u, e_v, f_v); per bus the
+ * shunt entries of its P and Q rows, its voltage row over (e_i, f_i), and the Hessian diagonal
+ * block (e_i, e_i), (f_i, e_i), (f_i, f_i); per generator as in the polar model.
+ */
+int oracle_eval_cart(const oracle_net *net, const double *x, const double *lam,
+                     const uint8_t *mask, const double *pd_scale, double w, double sigma,
+                     double *fval, double *grad, double *gh, oracle_coo *J, oracle_coo *H)
+{
+    const int nb = net->nb, nl = net->nl, ng = net->ng;
+    const int n = 2 * nb + 2 * ng;
+    const double *E = x, *F = x + nb, *Pg = x + 2 * nb, *Qg = x + 2 * nb + ng;
+    const double *lamP = lam, *lamQ = lam + nb, *muF = lam + 2 * nb, *muT = lam + 2 * nb + nl;
+    const double *muV = lam + 2 * nb + 2 * nl;
+    double *gP = gh, *gQ = gh + nb, *hF = gh + 2 * nb, *hT = gh + 2 * nb + nl;
+    double *hV = gh + 2 * nb + 2 * nl;
+    int i, l;
+
+    for (i = 0; i < 3 * nb + 2 * nl; i++) gh[i] = 0.0;
+    for (i = 0; i < n; i++) grad[i] = 0.0;
+
+    /* branches */
+    for (l = 0; l < nl; l++) {
+        double Y[8];
+        int fb = net->f[l], tb = net->t[l];
+        double m = (mask == NULL || mask[l]) ? 1.0 : 0.0;
+        double P[2], Q[2], dP[2][4], dQ[2][4], HP[2][16], HQ[2][16];
+        int gidx[2][4];
+        int s;
+        if (fb < 0 || fb >= nb || tb < 0 || tb >= nb || fb == tb) return -1;
+        if (oracle_pi_model(net->r[l], net->x[l], net->b[l], net->tap[l], Y) != 0) return -1;
+        side_terms_cart(Y[0], Y[1], Y[2], Y[3], E[fb], F[fb], E[tb], F[tb],
+                        &P[0], &Q[0], dP[0], dQ[0], HP[0], HQ[0]);
+        side_terms_cart(Y[6], Y[7], Y[4], Y[5], E[tb], F[tb], E[fb], F[fb],
+                        &P[1], &Q[1], dP[1], dQ[1], HP[1], HQ[1]);
+        gidx[0][0] = fb; gidx[0][1] = nb + fb; gidx[0][2] = tb; gidx[0][3] = nb + tb;
+        gidx[1][0] = tb; gidx[1][1] = nb + tb; gidx[1][2] = fb; gidx[1][3] = nb + fb;
+
+        for (s = 0; s < 2; s++) {
+            int rc = end_rows(nb, s == 0 ? fb : tb, 2 * nb + (s == 0 ? l : nl + l), m,
+                              lamP[s == 0 ? fb : tb], lamQ[s == 0 ? fb : tb],
+                              s == 0 ? muF[l] : muT[l], P[s], Q[s], dP[s], dQ[s], HP[s], HQ[s],
+                              gidx[s], gP, gQ, (s == 0 ? hF : hT) + l, J, H);
+            if (rc) return rc;
+        }
+    }
+
+    /* bus shunts, loads and voltage rows: Gs |V|^2 + Pd, -Bs |V|^2 + Qd, |V|^2 = e^2 + f^2 */
+    for (i = 0; i < nb; i++) {
+        double sc = pd_scale ? pd_scale[i] : 1.0;
+        double V2 = E[i] * E[i] + F[i] * F[i];
+        gP[i] += net->Gs[i] * V2 + net->Pd[i] * sc;
+        gQ[i] += -net->Bs[i] * V2 + net->Qd[i] * sc;
+        hV[i] = V2;
+        if (J) {
+            int vrow = 2 * nb + 2 * nl + i;
+            if (push(J, i, i, 2.0 * net->Gs[i] * E[i])) return -2;
+            if (push(J, i, nb + i, 2.0 * net->Gs[i] * F[i])) return -2;
+            if (push(J, nb + i, i, -2.0 * net->Bs[i] * E[i])) return -2;
+            if (push(J, nb + i, nb + i, -2.0 * net->Bs[i] * F[i])) return -2;
+            if (push(J, vrow, i, 2.0 * E[i])) return -2;
+            if (push(J, vrow, nb + i, 2.0 * F[i])) return -2;
+        }
+        if (H) {
+            /* lamP 2 Gs - lamQ 2 Bs + muV 2 on both diagonals; the (f_i, e_i) entry is 0 */
+            double d = lamP[i] * 2.0 * net->Gs[i] - lamQ[i] * 2.0 * net->Bs[i] + muV[i] * 2.0;
+            if (push(H, i, i, d)) return -2;
+            if (push(H, nb + i, i, 0.0)) return -2;
+            if (push(H, nb + i, nb + i, d)) return -2;
+        }
+    }
+
+    /* generators, exactly as in the polar model */
+    return gen_terms(net, Pg, Qg, w, sigma, gP, gQ, fval, grad, J, H);
 }

@@ -14,7 +14,7 @@ the oracle is pinned by:
     homogeneity in the voltage magnitudes, which tie J to g and H to J;
   * the nonzero counts 4nb + 16nl + 2ng (J) and 3nb + 4nl + ng (lower Hessian).
 Each pin is chosen so that a dropped term, a sign error, a swapped from/to index or a transposed
-operand in the oracle fails at least one of them; test_oracle_mutants.py plants 22 such
+operand in the oracle fails at least one of them; test_oracle_mutants.py plants such
 mistakes in copies of the C oracle and checks that each one is caught.
 """
 import numpy as np

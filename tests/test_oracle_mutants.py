@@ -11,6 +11,7 @@ import pytest
 
 from oracle import acopf
 import test_oracle as T
+import test_oracle_cartesian as TK
 import test_oracle_coupling as TC
 
 SRC = os.path.join(os.path.dirname(acopf.__file__), "acopf_oracle.c")
@@ -25,23 +26,34 @@ MUTANTS = {
     "HQ_angle_term": ("HQ[i * 4 + j] = VV * (-c) * e[i] * e[j];",
                       "HQ[i * 4 + j] = VV * (-a) * e[i] * e[j];"),
     "HQ_self_sign": ("HQ[2 * 4 + 2] = -2.0 * Bss;", "HQ[2 * 4 + 2] = 2.0 * Bss;"),
-    "hess_dropped_outer": ("+ dQ[s][a] * dQ[s][bb] + Q[s] * HQ[s][a * 4 + bb]);",
-                           "+ Q[s] * HQ[s][a * 4 + bb]);"),
-    "hess_mu_factor": ("+ mu * 2.0 * (dP[s][a]", "+ mu * (dP[s][a]"),
+    "hess_dropped_outer": ("+ dQ[a] * dQ[bb] + Q * HQ[a * 4 + bb]);", "+ Q * HQ[a * 4 + bb]);"),
+    "hess_mu_factor": ("+ mu * 2.0 * (dP[a]", "+ mu * (dP[a]"),
     "to_side_swapped": ("gidx[1][0] = tb; gidx[1][1] = fb;", "gidx[1][0] = fb; gidx[1][1] = tb;"),
     "charging_not_halved": ("Y[1] = (bs + 0.5 * b) / (tau * tau);", "Y[1] = (bs + b) / (tau * tau);"),
     "tap_square_mutual": ("Y[2] = -gs / tau;", "Y[2] = -gs / (tau * tau);"),
     "tap_on_wrong_end": ("Y[6] = gs;", "Y[6] = gs / (tau * tau);"),
-    "h_jac_factor": ("2.0 * P[s] * dP[s][a] + 2.0 * Q[s] * dQ[s][a]", "P[s] * dP[s][a] + Q[s] * dQ[s][a]"),
+    "h_jac_factor": ("2.0 * P * dP[a] + 2.0 * Q * dQ[a]", "P * dP[a] + Q * dQ[a]"),
     "cost_units": ("net->c1[k] * MW + net->c0[k]", "net->c1[k] * Pg[k] + net->c0[k]"),
     "grad_units": ("+ net->c1[k] * base);", "+ net->c1[k]);"),
     "hess_sigma": ("sigma * w * 2.0 * net->c2[k]", "w * 2.0 * net->c2[k]"),
-    "shunt_hess_sign": ("- lamQ[i] * 2.0 * net->Bs[i]", "+ lamQ[i] * 2.0 * net->Bs[i]"),
+    "shunt_hess_sign": ("- lamQ[i] * 2.0 * net->Bs[i])) return -2;", "+ lamQ[i] * 2.0 * net->Bs[i])) return -2;"),
     "shunt_jac_dropped": ("if (push(J, i, nb + i, 2.0 * net->Gs[i] * Vm[i])) return -2;",
                           "if (push(J, i, nb + i, 0.0)) return -2;"),
-    "load_scale_dropped": ("net->Pd[i] * sc;", "net->Pd[i];"),
-    "mask_ignored": ("P[s] *= m;", "P[s] *= 1.0;"),
+    "load_scale_dropped": ("Vm[i] * Vm[i] + net->Pd[i] * sc;", "Vm[i] * Vm[i] + net->Pd[i];"),
+    "mask_ignored": ("P *= m;", "P *= 1.0;"),
     "gen_q_on_p_row": ("gQ[gb] -= Qg[k];", "gP[gb] -= Qg[k];"),
+    "cart_db_sign": ("const double db[4] = {-fv, ev, fu, -eu};", "const double db[4] = {fv, ev, fu, -eu};"),
+    "cart_Hb_sign": ("Hb[16] = {0, 0, 0, -1,", "Hb[16] = {0, 0, 0, 1,"),
+    "cart_Ha_index": ("Ha[16] = {0, 0, 1, 0,  0, 0, 0, 1,", "Ha[16] = {0, 1, 0, 0,  1, 0, 0, 1,"),
+    "cart_Q_sign": ("*Q = -Bss * s + Gm * b - Bm * a;", "*Q = -Bss * s + Gm * b + Bm * a;"),
+    "cart_ds_factor": ("const double ds[4] = {2.0 * eu, 2.0 * fu, 0.0, 0.0};",
+                       "const double ds[4] = {eu, fu, 0.0, 0.0};"),
+    "cart_voltage_row": ("if (push(J, vrow, nb + i, 2.0 * F[i])) return -2;",
+                         "if (push(J, vrow, nb + i, F[i])) return -2;"),
+    "cart_muV_hess": ("+ muV[i] * 2.0;", "+ muV[i];"),
+    "cart_shunt_f": ("if (push(J, nb + i, nb + i, -2.0 * net->Bs[i] * F[i])) return -2;",
+                     "if (push(J, nb + i, nb + i, -2.0 * net->Bs[i] * E[i])) return -2;"),
+    "cart_to_side": ("gidx[1][2] = fb; gidx[1][3] = nb + fb;", "gidx[1][2] = nb + fb; gidx[1][3] = fb;"),
     "coupling_sign": ("x[(int64_t)b * n + 2 * nb + k] - x[(int64_t)p * n + 2 * nb + k]",
                       "x[(int64_t)b * n + 2 * nb + k] + x[(int64_t)p * n + 2 * nb + k]"),
     "coupling_parent_stride": ("- x[(int64_t)p * n + 2 * nb + k]", "- x[(int64_t)p * ng + 2 * nb + k]"),
@@ -81,6 +93,10 @@ PINS = [
     ("fd_sigma0", lambda om: T.test_finite_differences_sigma_zero_and_transformers(om)),
     ("mask", lambda om: T.test_mask_equals_branch_removed(om)),
     ("symmetries", lambda om: T.test_homogeneity_and_angle_invariance(om)),
+    ("cart_nodal", lambda om: TK.test_matches_complex_nodal_form(om)),
+    ("cart_polar", lambda om: TK.test_change_of_variables_to_polar(om, 53)),
+    ("cart_fd", lambda om: TK.test_finite_differences(om)),
+    ("cart_homogeneity", lambda om: TK.test_homogeneity_and_rotation(om)),
     ("coupling_hand", lambda om: TC.test_hand_rows(om)),
     ("coupling_hand_transpose", lambda om: TC.test_hand_transpose(om)),
     ("coupling_telescopes", lambda om: TC.test_chain_telescopes(om)),
