@@ -470,6 +470,39 @@ def run_coupling(exago, synth, torch, np, dev, hbm_peak):
     return res
 
 
+def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):
+    """The power-balance-cartesian formulation (exago_eval_cart) on the headline workload, the
+    2,000-bus x 512 N-1 batch at the same operating points (e = Vm cos Va, f = Vm sin Va), all
+    outputs, CUDA events over back-to-back calls (each call writes 350 MB, more than L2).
+    Algorithmic bytes per state: x, lambda (m + nb) and mask read; f, grad, g | h (m + nb),
+    J (nnzJ + 2 nb) and H written; the network tables once per call."""
+    g = synth.grid_2000()
+    b = synth.contingency_batch(3, g, 512)
+    nb = g.nb
+    x = b.x.copy()
+    x[:, :nb] = b.x[:, nb:2 * nb] * np.cos(b.x[:, :nb])
+    x[:, nb:2 * nb] = b.x[:, nb:2 * nb] * np.sin(b.x[:, :nb])
+    lam = np.concatenate([b.lam, np.random.default_rng(3).normal(size=(b.B, nb))], axis=1)
+    td = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    X, LAM, M = td(x, torch.float64), td(lam, torch.float64), td(b.mask, torch.uint8)
+    net = exago.Net(g)
+    n, me, mi, nj, nh = exago.exago_net_dims_cart(net.h)
+    bt = exago.make_batch(X, LAM, M, obj_factor=b.sigma)
+    z = lambda *sh: torch.empty(*sh, dtype=torch.float64, device=dev)
+    out = [z(b.B), z(b.B, n), z(b.B, me + mi), z(b.B, nj), z(b.B, nh)]
+    ms = time_calls(torch, lambda: exago.exago_eval_cart(net.h, bt, *out), 200, warm=5)
+    per_state = 8 * (n + (me + mi) + 1 + n + (me + mi) + nj + nh) + g.nl
+    net_bytes = 8 * (11 * g.nl + 4 * nb + 4 * g.ng) + 4 * (2 * g.nl + 8 * nb + g.ng + 4 * g.nl)
+    nbytes = per_state * b.B + net_bytes
+    net.close()
+    return {"workload": "2000-bus x 512 N-1 states in rectangular voltages, all outputs",
+            "evals_per_s": b.B / (ms * 1e-3), "ms_per_batch": ms,
+            "vs_polar_same_states": polar_ms / ms,
+            "algorithmic_bytes": nbytes, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
+            "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak,
+            "schedule": "branch records + bus assembly per chunk of states (records stay in L2)"}
+
+
 def run_serve(exago, synth, torch, np, dev, seconds):
     rng = np.random.default_rng(5)
     sc = ServeClients(exago, synth, torch, np, dev)
@@ -681,6 +714,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     serve = None if args.no_serve else run_serve(exago, synth, torch, np, dev, args.serve_seconds)
     others = None if args.no_serve else run_other_configs(exago, synth, torch, np, dev)
     coupling = None if args.no_serve else run_coupling(exago, synth, torch, np, dev, hbm_peak)
+    cartesian = None if args.no_serve else run_cartesian(exago, synth, torch, np, dev, hbm_peak,
+                                                         top_ms)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -723,6 +758,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         res["other_workloads"] = others
     if coupling is not None:
         res["coupling_rows"] = coupling
+    if cartesian is not None:
+        res["cartesian"] = cartesian
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_evals = 256 * cores

@@ -192,6 +192,40 @@ exago_status exago_eval_jtv(exago_net_t net, const exago_batch *batch, const dou
 exago_status exago_eval_hvp(exago_net_t net, const exago_batch *batch, const double *u, double *out);
 
 /*
+ * The power-balance-cartesian formulation (Sec. III names it beside the power-balance-polar one)
+ * on the same net: bus voltages V_i = e_i + j f_i instead of (Va, Vm).
+ *   variables     x      = [e (nb) | f (nb) | Pg (ng) | Qg (ng)]                 (n as polar)
+ *   constraints   g | h  = [P balance | Q balance | |S_from|^2 | |S_to|^2 | e_i^2 + f_i^2 (nb)]
+ *                 (m_c = 3 nb + 2 nl: the voltage-magnitude limits, bounds on Vm in the polar
+ *                 model, become the last nb rows, Vmin^2 <= e^2 + f^2 <= Vmax^2)
+ *   multipliers   lambda = [lamP | lamQ | muF | muT | muV]                        (m_c values)
+ *   one branch end at bus u towards v, a = e_u e_v + f_u f_v, b = f_u e_v - e_u f_v:
+ *                 P = Gss (e_u^2 + f_u^2) + G a + B b,   Q = -Bss (e_u^2 + f_u^2) + G b - B a
+ * The balances, flow rows, masks, load scales, objective and generator terms are the polar model's.
+ *   exago_net_dims_cart         n, m_eq = 2 nb, m_ineq = 2 nl + nb, nnzJ_c = nnzJ + 2 nb, nnzH.
+ *   exago_net_jac_pattern_cart  HOST rowptr [m_c + 1], col [nnzJ_c]: the polar pattern with e in
+ *                               place of Va and f in place of Vm, then voltage row i with columns
+ *                               e_i, f_i.  The Hessian pattern is exago_net_hess_pattern's (same
+ *                               substitution).  Works on a net made by exago_net_plan.
+ *   exago_eval_cart_workspace_size  scratch bytes of exago_eval_cart for B states (branch-end
+ *                               records of one chunk of states, at most about 48 MB).
+ *   exago_eval_cart             f [B], grad [B][n], gh [B][m_c], jval [B][nnzJ_c], hval [B][nnzH]
+ *                               (DEVICE buffers; any may be NULL) for the batch's states x [B][n]
+ *                               and multipliers lambda [B][m_c].  batch->workspace as for
+ *                               exago_eval_all (else the net's internal workspace, grown on
+ *                               demand).  Errors as exago_eval_all.  Runs the multi-kernel
+ *                               schedule (branch records, then bus assembly, per chunk of states);
+ *                               the persistent schedule, the graph cache and the adjoint products
+ *                               are the polar model's only.
+ */
+exago_status exago_net_dims_cart(exago_net_t net, int *n, int *m_eq, int *m_ineq, int64_t *nnzJ,
+                                 int64_t *nnzH);
+exago_status exago_net_jac_pattern_cart(exago_net_t net, int64_t *rowptr, int *col);
+exago_status exago_eval_cart_workspace_size(exago_net_t net, int B, size_t *bytes);
+exago_status exago_eval_cart(exago_net_t net, const exago_batch *batch, double *f, double *grad,
+                             double *gh, double *jval, double *hval);
+
+/*
  * Coupling (ramp) rows between the states of a batch.  ExaGO's multi-stage problems tie each
  * subproblem's state to one other state by a bounded difference: consecutive periods of the
  * multi-period problem (Sec. IV, eq. (15)), each contingency to the base case (Sec. V-A,

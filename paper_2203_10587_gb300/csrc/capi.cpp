@@ -582,6 +582,13 @@ bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **de
 
 exago_status set_last_error(exago_status s, const std::string &msg) { return fail(s, msg); }
 
+exago_status net_workspace(exago_net_t net, size_t bytes, void **ws) {
+    std::lock_guard<std::mutex> lk(net->mu);
+    exago_status s = ensure_workspace_locked(net, bytes);
+    *ws = s == EXAGO_OK ? net->ws : nullptr;
+    return s;
+}
+
 exago_status eval_direct(exago_net_t net, const exago_batch *bt, double *f, double *grad,
                          double *gh, double *jval, double *hval, const StateTab *tab) {
     return eval(net, bt, f, grad, gh, jval, hval, nullptr, false, tab);

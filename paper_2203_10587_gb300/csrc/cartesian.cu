@@ -1,0 +1,443 @@
+// The power-balance-cartesian formulation of the AC-OPF model, which ExaGO offers beside the polar
+// one (arXiv 2203.10587, Sec. III): the bus voltage is V_i = e_i + j f_i, the variables are
+// x = [e | f | Pg | Qg], and the voltage-magnitude limits become rows e_i^2 + f_i^2 after the
+// flow rows, so that g | h = [P balance | Q balance | |S_from|^2 | |S_to|^2 | e^2 + f^2] and the
+// multipliers are [lamP | lamQ | muF | muT | muV].
+//
+// For one end of a branch, from its bus u towards v, with a = e_u e_v + f_u f_v,
+// b = f_u e_v - e_u f_v and s = e_u^2 + f_u^2:
+//     P = Gss s + G a + B b,     Q = -Bss s + G b - B a.
+// Both are quadratic forms, so every derivative is a product of admittances and voltages (no sine
+// or cosine), the second derivatives of P and Q are constants, and dQ/de_v = dP/df_v,
+// dQ/df_v = -dP/de_v.
+//
+// The J rows of g and h and the Hessian have the polar model's sparsity pattern with e in place of
+// Va and f in place of Vm, so the kernels reuse the net's plan (row starts, slot order, positions);
+// the nb voltage rows follow the polar rows in the Jacobian (entries 2 e_i, 2 f_i).  Schedule: per
+// chunk of states, a branch kernel writes each branch end's 14-value record at its slot and the
+// branch's h values and h rows; a bus kernel walks each bus's slots in the plan's fixed order,
+// writes the neighbour entries of its J and H rows and finishes the diagonal, balance, voltage
+// and generator terms.  Chunks are sized so that the records stay in L2 between the two kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "eval_items.cuh"
+
+namespace exago {
+namespace {
+
+// One branch-end record (end at bus u towards bus v).
+enum CartComp {
+    CR_P = 0, CR_Q = 1,                        // injections
+    CR_PE = 2, CR_PF = 3, CR_QE = 4, CR_QF = 5,   // dP/de_u, dP/df_u, dQ/de_u, dQ/df_u
+    CR_PEV = 6, CR_PFV = 7,                    // dP/de_v, dP/df_v (dQ/de_v = dP/df_v, dQ/df_v = -dP/de_v)
+    CR_HEE = 8, CR_HFE = 9, CR_HFF = 10,       // branch Hessian (e_u,e_u), (f_u,e_u), (f_u,f_u)
+    CR_HEEV = 11, CR_HFEV = 12, CR_HFFV = 13,  // (e_u,e_v), (f_u,e_v), (f_u,f_v)
+    CNC = 14
+};
+
+constexpr size_t kChunkRecordBytes = (size_t)48 << 20;   // records of one chunk stay in L2
+
+struct CartReq {
+    int B, b0;                  // states of this launch: b0 .. b0 + gridDim.y
+    int mc;                     // rows of g | h: m + nb
+    int64_t nnzJc;              // Jacobian entries per state: nnzJ + 2 nb
+    const double *x, *lam;
+    const uint8_t *mask;
+    const double *pd_scale, *obj_weight;
+    double sigma;
+    double *f, *grad, *gh, *jval, *hval;
+    double *scratch;            // [chunk][nslot][CNC]
+};
+
+__device__ __forceinline__ void put2c(double *rec, int c, double a, double b) {
+    *reinterpret_cast<double2 *>(rec + c) = make_double2(a, b);
+}
+
+// Outer-product weights of one end: with m2 = 2 mu, p = dP/d(e_u, f_u, e_v, f_v), q = dQ/d(...)
+// (q3 = p4, q4 = -p3), O_ij = m2 (p_i p_j + q_i q_j); O_33 = O_44 = m2 (p3^2 + p4^2), O_43 = 0.
+struct EndOuter {
+    double o11, o21, o22, ovv, o13, o14, o23, o24;
+};
+
+__device__ __forceinline__ EndOuter end_outer(double m2, double p1, double p2, double q1,
+                                              double q2, double p3, double p4) {
+    EndOuter o;
+    o.o11 = m2 * fma(p1, p1, q1 * q1);
+    o.o21 = m2 * fma(p2, p1, q2 * q1);
+    o.o22 = m2 * fma(p2, p2, q2 * q2);
+    o.ovv = m2 * fma(p3, p3, p4 * p4);
+    o.o13 = m2 * fma(p1, p3, q1 * p4);
+    o.o14 = m2 * fma(p1, p4, -(q1 * p3));
+    o.o23 = m2 * fma(p2, p3, q2 * p4);
+    o.o24 = m2 * fma(p2, p4, -(q2 * p3));
+    return o;
+}
+
+__global__ void __launch_bounds__(128) k_cart_branch(const DevNet N, const CartReq R) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= N.nl) return;
+    const int bl = blockIdx.y, b = R.b0 + bl;
+    const int nb = N.nb, nl = N.nl;
+    double *scr = R.scratch + (size_t)bl * N.nslot * CNC;
+    double *rf = scr + (size_t)__ldg(N.br_slot + l) * CNC;
+    double *rt = scr + (size_t)__ldg(N.br_slot + nl + l) * CNC;
+    const int fb = __ldg(N.f + l), tb = __ldg(N.t + l);
+    double *ghb = R.gh ? R.gh + (size_t)b * R.mc : nullptr;
+    double *Jf = R.jval ? R.jval + (size_t)b * R.nnzJc + N.nnzJg + 4 * (size_t)l : nullptr;
+    double *Jt = Jf ? Jf + 4 * (size_t)nl : nullptr;
+    const bool on = R.mask == nullptr || R.mask[(size_t)b * nl + l] != 0;
+    if (!on) {
+#pragma unroll
+        for (int c = 0; c < CNC; c += 2) { put2c(rf, c, 0.0, 0.0); put2c(rt, c, 0.0, 0.0); }
+        if (ghb) { ghb[2 * nb + l] = 0.0; ghb[2 * nb + nl + l] = 0.0; }
+        if (Jf)
+            for (int k = 0; k < 4; k++) { Jf[k] = 0.0; Jt[k] = 0.0; }
+        return;
+    }
+    const double *xb = R.x + (size_t)b * N.n;
+    const double ef = __ldg(xb + fb), et = __ldg(xb + tb);
+    const double ff = __ldg(xb + nb + fb), ft = __ldg(xb + nb + tb);
+    const double G = __ldg(N.Gft + l), Bm = __ldg(N.Bft + l);
+    const double Gff = __ldg(N.Gff + l), Bff = __ldg(N.Bff + l);
+    const double Gtt = __ldg(N.Gtt + l), Btt = __ldg(N.Btt + l);
+    const double Gff2 = __ldg(N.Gff2 + l), Bff2 = __ldg(N.Bff2 + l);
+    const double Gtt2 = __ldg(N.Gtt2 + l), Btt2 = __ldg(N.Btt2 + l);
+
+    // a = Vf Vt cos th, bf = Vf Vt sin th (th = Va_f - Va_t); the to end sees -bf
+    const double a = fma(ef, et, ff * ft);
+    const double bf = fma(ff, et, -(ef * ft));
+    const double sf = fma(ef, ef, ff * ff), st = fma(et, et, ft * ft);
+    const double Ga = G * a, Ba = Bm * a, Gb = G * bf, Bb = Bm * bf;
+    const double Pf = fma(Gff, sf, Ga + Bb), Qf = fma(-Bff, sf, Gb - Ba);
+    const double Pt = fma(Gtt, st, Ga - Bb), Qt = fma(-Btt, st, -(Gb + Ba));
+
+    // admittance-voltage products shared by both ends' derivatives
+    const double Gef = G * ef, Gff_ = G * ff, Get = G * et, Gft_ = G * ft;
+    const double Bef = Bm * ef, Bff_ = Bm * ff, Bet = Bm * et, Bft_ = Bm * ft;
+    // from end (u = f, v = t)
+    const double u1 = Get - Bft_, u2 = Gft_ + Bet;
+    const double p1f = fma(Gff2, ef, u1), p2f = fma(Gff2, ff, u2);
+    const double q1f = fma(-Bff2, ef, -u2), q2f = fma(-Bff2, ff, u1);
+    const double p3f = Gef + Bff_, p4f = Gff_ - Bef;
+    // to end (u = t, v = f)
+    const double w1 = Gef - Bff_, w2 = Gff_ + Bef;
+    const double p1t = fma(Gtt2, et, w1), p2t = fma(Gtt2, ft, w2);
+    const double q1t = fma(-Btt2, et, -w2), q2t = fma(-Btt2, ft, w1);
+    const double p3t = Get + Bft_, p4t = Gft_ - Bet;
+
+    if (ghb) {
+        ghb[2 * nb + l] = fma(Pf, Pf, Qf * Qf);
+        ghb[2 * nb + nl + l] = fma(Pt, Pt, Qt * Qt);
+    }
+    if (Jf) {
+        // grad |S|^2 = 2 P grad P + 2 Q grad Q, columns (e_lo, e_hi, f_lo, f_hi)
+        const double Pf2 = twice(Pf), Qf2 = twice(Qf), Pt2 = twice(Pt), Qt2 = twice(Qt);
+        const double hff_e = fma(Pf2, p1f, Qf2 * q1f), hff_f = fma(Pf2, p2f, Qf2 * q2f);
+        const double hft_e = fma(Pf2, p3f, Qf2 * p4f), hft_f = fma(Pf2, p4f, -(Qf2 * p3f));
+        const double htt_e = fma(Pt2, p1t, Qt2 * q1t), htt_f = fma(Pt2, p2t, Qt2 * q2t);
+        const double htf_e = fma(Pt2, p3t, Qt2 * p4t), htf_f = fma(Pt2, p4t, -(Qt2 * p3t));
+        if (fb < tb) {
+            Jf[0] = hff_e; Jf[1] = hft_e; Jf[2] = hff_f; Jf[3] = hft_f;
+            Jt[0] = htf_e; Jt[1] = htt_e; Jt[2] = htf_f; Jt[3] = htt_f;
+        } else {
+            Jf[0] = hft_e; Jf[1] = hff_e; Jf[2] = hft_f; Jf[3] = hff_f;
+            Jt[0] = htt_e; Jt[1] = htf_e; Jt[2] = htt_f; Jt[3] = htf_f;
+        }
+    }
+    put2c(rf, CR_P, Pf, Qf);
+    put2c(rf, CR_PE, p1f, p2f);
+    put2c(rf, CR_QE, q1f, q2f);
+    put2c(rf, CR_PEV, p3f, p4f);
+    put2c(rt, CR_P, Pt, Qt);
+    put2c(rt, CR_PE, p1t, p2t);
+    put2c(rt, CR_QE, q1t, q2t);
+    put2c(rt, CR_PEV, p3t, p4t);
+    if (R.hval) {
+        // end weights: wP = lamP + 2 mu P, wQ = lamQ + 2 mu Q; the linear part of each end's block
+        // is wP grad^2 P + wQ grad^2 Q: diagonal d = 2 (wP Gss - wQ Bss) on (e_u,e_u) and
+        // (f_u,f_u), c1 = wP G - wQ B on (e_u,e_v) and (f_u,f_v), c2 = wP B + wQ G on (f_u,e_v)
+        // and -c2 on (e_u,f_v)
+        const double *lb = R.lam + (size_t)b * R.mc;
+        const double muf2 = twice(__ldg(lb + 2 * nb + l)), mut2 = twice(__ldg(lb + 2 * nb + nl + l));
+        const double wPf = fma(muf2, Pf, __ldg(lb + fb)), wQf = fma(muf2, Qf, __ldg(lb + nb + fb));
+        const double wPt = fma(mut2, Pt, __ldg(lb + tb)), wQt = fma(mut2, Qt, __ldg(lb + nb + tb));
+        const double df = fma(wPf, Gff2, -(wQf * Bff2)), dt = fma(wPt, Gtt2, -(wQt * Btt2));
+        const double c1 = fma(wPf, G, -(wQf * Bm)) + fma(wPt, G, -(wQt * Bm));
+        const double c2f = fma(wPf, Bm, wQf * G), c2t = fma(wPt, Bm, wQt * G);
+        const EndOuter of = end_outer(muf2, p1f, p2f, q1f, q2f, p3f, p4f);
+        const EndOuter ot = end_outer(mut2, p1t, p2t, q1t, q2t, p3t, p4t);
+        const double eeft = c1 + (of.o13 + ot.o13);            // (e_f, e_t)
+        const double ffft = c1 + (of.o24 + ot.o24);            // (f_f, f_t)
+        const double ef_ft = (c2t - c2f) + (of.o14 + ot.o23);  // (e_f, f_t) = (f_t, e_f)
+        const double ff_et = (c2f - c2t) + (of.o23 + ot.o14);  // (f_f, e_t)
+        put2c(rf, CR_HEE, df + (of.o11 + ot.ovv), of.o21);
+        put2c(rf, CR_HFF, df + (of.o22 + ot.ovv), eeft);
+        put2c(rf, CR_HFEV, ff_et, ffft);
+        put2c(rt, CR_HEE, dt + (ot.o11 + of.ovv), ot.o21);
+        put2c(rt, CR_HFF, dt + (ot.o22 + of.ovv), eeft);
+        put2c(rt, CR_HFEV, ef_ft, ffft);
+    }
+}
+
+// The values a bus reads from one record.
+struct CRec {
+    double P, Q, pe, pf, qe, qf, pev, pfv, hee, hfe, hff, heev, hfev, hffv;
+};
+
+__device__ __forceinline__ CRec load_crec(const double *r, bool wantH) {
+    CRec o;
+    double2 v = ld2(r + CR_P);
+    o.P = v.x; o.Q = v.y;
+    v = ld2(r + CR_PE); o.pe = v.x; o.pf = v.y;
+    v = ld2(r + CR_QE); o.qe = v.x; o.qf = v.y;
+    v = ld2(r + CR_PEV); o.pev = v.x; o.pfv = v.y;
+    if (wantH) {
+        v = ld2(r + CR_HEE); o.hee = v.x; o.hfe = v.y;
+        v = ld2(r + CR_HFF); o.hff = v.x; o.heev = v.y;
+        v = ld2(r + CR_HFEV); o.hfev = v.x; o.hffv = v.y;
+    } else {
+        o.hee = o.hfe = o.hff = o.heev = o.hfev = o.hffv = 0.0;
+    }
+    return o;
+}
+
+__global__ void __launch_bounds__(128) k_cart_bus(const DevNet N, const CartReq R) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N.nb) return;
+    const int bl = blockIdx.y, b = R.b0 + bl;
+    const int nb = N.nb, ng = N.ng;
+    const bool wantH = R.hval != nullptr;
+    const double *scr = R.scratch + (size_t)bl * N.nslot * CNC;
+    const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
+    const int k = __ldg(N.bus_k + i), nlow = __ldg(N.bus_nlow + i);
+    double *Jb = R.jval ? R.jval + (size_t)b * R.nnzJc : nullptr;
+    double *Hb = wantH ? R.hval + (size_t)b * N.nnzH : nullptr;
+    double *JP = Jb ? Jb + __ldg(N.bus_jP + i) : nullptr;
+    double *JQ = Jb ? Jb + __ldg(N.bus_jQ + i) : nullptr;
+    double *HA = Hb ? Hb + __ldg(N.bus_hA + i) : nullptr;
+    double *HM = Hb ? Hb + __ldg(N.bus_hM + i) : nullptr;
+
+    // diagonal sums over the bus's ends, and one neighbour group (parallel branches) at a time
+    double P = 0.0, Q = 0.0, pe = 0.0, pf = 0.0, qe = 0.0, qf = 0.0, hee = 0.0, hfe = 0.0, hff = 0.0;
+    int pos = 0;
+    int s = s0;
+    while (s < s1) {
+        const int j = __ldg(N.slot_nbr + s);
+        CRec o = load_crec(scr + (size_t)s * CNC, wantH);
+        P += o.P; Q += o.Q; pe += o.pe; pf += o.pf; qe += o.qe; qf += o.qf;
+        hee += o.hee; hfe += o.hfe; hff += o.hff;
+        for (s++; s < s1 && __ldg(N.slot_nbr + s) == j; s++) {
+            const CRec p = load_crec(scr + (size_t)s * CNC, wantH);
+            P += p.P; Q += p.Q; pe += p.pe; pf += p.pf; qe += p.qe; qf += p.qf;
+            hee += p.hee; hfe += p.hfe; hff += p.hff;
+            o.pev += p.pev; o.pfv += p.pfv; o.heev += p.heev; o.hfev += p.hfev; o.hffv += p.hffv;
+        }
+        if (pos == nlow) pos++;   // the diagonal column sits between lower and upper neighbours
+        if (JP) {
+            JP[pos] = o.pev; JP[k + pos] = o.pfv;              // dP/de_j, dP/df_j
+            JQ[pos] = o.pfv; JQ[k + pos] = dneg(o.pev);        // dQ/de_j, dQ/df_j
+        }
+        if (HM) {
+            HM[pos] = o.hfev;                                  // (f_i, e_j)
+            if (j < i) {
+                HA[pos] = o.heev;                              // (e_i, e_j)
+                HM[k + pos] = o.hffv;                          // (f_i, f_j)
+            }
+        }
+        pos++;
+    }
+
+    const double *xb = R.x + (size_t)b * N.n;
+    const double ei = __ldg(xb + i), fi = __ldg(xb + nb + i);
+    const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
+    const double V2 = fma(ei, ei, fi * fi);
+    const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
+    if (R.gh) {
+        double Pd = __ldg(N.Pd + i), Qd = __ldg(N.Qd + i);
+        if (R.pd_scale) {
+            const double sc = __ldg(R.pd_scale + (size_t)b * nb + i);
+            Pd *= sc;
+            Qd *= sc;
+        }
+        double gP = fma(Gs, V2, P) + Pd;
+        double gQ = fma(-Bs, V2, Q) + Qd;
+        for (int q = g0; q < g1; q++) {
+            const int g = __ldg(N.gen_ord + q);
+            gP -= __ldg(xb + 2 * nb + g);
+            gQ -= __ldg(xb + 2 * nb + ng + g);
+        }
+        double *ghb = R.gh + (size_t)b * R.mc;
+        ghb[i] = gP;
+        ghb[nb + i] = gQ;
+        ghb[2 * nb + 2 * N.nl + i] = V2;
+    }
+    if (JP) {
+        const double tG = twice(Gs), tB = twice(Bs);
+        JP[nlow] = fma(tG, ei, pe);
+        JP[k + nlow] = fma(tG, fi, pf);
+        JQ[nlow] = fma(-tB, ei, qe);
+        JQ[k + nlow] = fma(-tB, fi, qf);
+        for (int q = 0; q < g1 - g0; q++) {
+            JP[2 * k + q] = -1.0;
+            JQ[2 * k + q] = -1.0;
+        }
+        double *Jv = Jb + N.nnzJ + 2 * (size_t)i;              // voltage row: 2 e_i, 2 f_i
+        Jv[0] = twice(ei);
+        Jv[1] = twice(fi);
+    }
+    if (HM) {
+        const double *lb = R.lam + (size_t)b * R.mc;
+        const double lP = __ldg(lb + i), lQ = __ldg(lb + nb + i);
+        const double muV = __ldg(lb + 2 * nb + 2 * N.nl + i);
+        const double dsh = fma(lP, twice(Gs), fma(-lQ, twice(Bs), twice(muV)));
+        HA[nlow] = hee + dsh;                                  // (e_i, e_i)
+        HM[nlow] = hfe;                                        // (f_i, e_i)
+        HM[k + nlow] = hff + dsh;                              // (f_i, f_i)
+        if (g1 > g0) {
+            const double sw = R.sigma * (R.obj_weight ? __ldg(R.obj_weight + b) : 1.0);
+            for (int q = g0; q < g1; q++) {
+                const int g = __ldg(N.gen_ord + q);
+                Hb[N.hpg + g] = sw * __ldg(N.c2g + g);
+            }
+        }
+    }
+    if (R.grad) {
+        double *gb = R.grad + (size_t)b * N.n;
+        gb[i] = 0.0;
+        gb[nb + i] = 0.0;
+        const double w = R.obj_weight ? __ldg(R.obj_weight + b) : 1.0;
+        for (int q = g0; q < g1; q++) {
+            const int g = __ldg(N.gen_ord + q);
+            gb[2 * nb + g] = w * fma(__ldg(N.c2g + g), __ldg(xb + 2 * nb + g), __ldg(N.c1g + g));
+            gb[2 * nb + ng + g] = 0.0;
+        }
+    }
+}
+
+// Objective of each state (the polar model's: it depends on Pg only).
+__global__ void __launch_bounds__(OBJ_LANES) k_cart_obj(const DevNet N, const EvalReq R, int b0) {
+    __shared__ double part[OBJ_LANES];
+    obj_block(N, R, b0 + blockIdx.x, part);
+}
+
+size_t record_bytes(const DevNet &N) { return (size_t)N.nslot * CNC * sizeof(double); }
+
+int chunk_states(const DevNet &N, int B) {
+    const size_t per = std::max<size_t>(record_bytes(N), 1);
+    return (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(B, 65535), kChunkRecordBytes / per));
+}
+
+}  // namespace
+}  // namespace exago
+
+using namespace exago;
+
+extern "C" {
+
+exago_status exago_net_dims_cart(exago_net_t net, int *n, int *m_eq, int *m_ineq, int64_t *nnzJ,
+                                 int64_t *nnzH) {
+    int nn = 0, me = 0, mi = 0;
+    int64_t nj = 0, nh = 0;
+    exago_status s = exago_net_dims(net, &nn, &me, &mi, &nj, &nh);
+    if (s != EXAGO_OK) return s;
+    const int nb = me / 2;
+    if (n) *n = nn;
+    if (m_eq) *m_eq = me;
+    if (m_ineq) *m_ineq = mi + nb;
+    if (nnzJ) *nnzJ = nj + 2 * (int64_t)nb;
+    if (nnzH) *nnzH = nh;
+    return EXAGO_OK;
+}
+
+exago_status exago_net_jac_pattern_cart(exago_net_t net, int64_t *rowptr, int *col) {
+    int nn = 0, me = 0, mi = 0;
+    int64_t nj = 0, nh = 0;
+    exago_status s = exago_net_dims(net, &nn, &me, &mi, &nj, &nh);
+    if (s != EXAGO_OK) return s;
+    if (!rowptr || !col) return set_last_error(EXAGO_EINVAL, "null argument");
+    if ((s = exago_net_jac_pattern(net, rowptr, col)) != EXAGO_OK) return s;
+    const int nb = me / 2, m = me + mi;
+    for (int i = 0; i < nb; i++) {   // voltage row i: columns e_i, f_i
+        col[nj + 2 * i] = i;
+        col[nj + 2 * i + 1] = nb + i;
+        rowptr[m + i + 1] = nj + 2 * (int64_t)(i + 1);
+    }
+    return EXAGO_OK;
+}
+
+exago_status exago_eval_cart_workspace_size(exago_net_t net, int B, size_t *bytes) {
+    const HostPlan *plan = nullptr;
+    const DevNet *dev = nullptr;
+    int device = -1;
+    if (!bytes) return set_last_error(EXAGO_EINVAL, "bytes is NULL");
+    if (!net_internal_view(net, &plan, &dev, &device))
+        return set_last_error(net ? EXAGO_ESTATE : EXAGO_EINVAL,
+                              net ? "net was planned without a device" : "net is NULL");
+    if (B < 0) return set_last_error(EXAGO_EINVAL, "B < 0");
+    *bytes = B == 0 ? 0 : (size_t)chunk_states(*dev, B) * record_bytes(*dev);
+    return EXAGO_OK;
+}
+
+exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, double *grad,
+                             double *gh, double *jval, double *hval) {
+    const HostPlan *plan = nullptr;
+    const DevNet *dev = nullptr;
+    int device = -1;
+    if (!net_internal_view(net, &plan, &dev, &device))
+        return set_last_error(net ? EXAGO_ESTATE : EXAGO_EINVAL,
+                              net ? "net was planned without a device" : "net is NULL");
+    if (!bt) return set_last_error(EXAGO_EINVAL, "batch is NULL");
+    if (bt->B < 0) return set_last_error(EXAGO_EINVAL, "batch B < 0");
+    if (bt->B == 0) return EXAGO_OK;
+    if (!bt->x) return set_last_error(EXAGO_EINVAL, "batch x is NULL");
+    if (hval && !bt->lambda)
+        return set_last_error(EXAGO_EINVAL, "batch lambda is NULL (needed by the Hessian)");
+    const DevNet &N = *dev;
+    cudaStream_t st = (cudaStream_t)bt->stream;
+    const bool rows = gh || jval || hval || grad;
+    if (rows && N.nb > 0) {
+        const int chunk = chunk_states(N, bt->B);
+        const size_t need = (size_t)chunk * record_bytes(N);
+        void *ws = bt->workspace;
+        if (ws) {
+            if (((uintptr_t)ws & 255) != 0)
+                return set_last_error(EXAGO_EINVAL, "workspace not 256-byte aligned");
+            if (bt->workspace_bytes < need)
+                return set_last_error(EXAGO_EINVAL, "workspace smaller than exago_eval_cart_workspace_size");
+        } else if (need > 0) {
+            exago_status s = net_workspace(net, need, &ws);
+            if (s != EXAGO_OK) return s;
+        }
+        CartReq R{};
+        R.B = bt->B;
+        R.mc = N.m + N.nb;
+        R.nnzJc = N.nnzJ + 2 * (int64_t)N.nb;
+        R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask;
+        R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
+        R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
+        R.scratch = (double *)ws;
+        for (int b0 = 0; b0 < bt->B; b0 += chunk) {
+            const int nB = std::min(chunk, bt->B - b0);
+            R.b0 = b0;
+            if (N.nl > 0) k_cart_branch<<<dim3((N.nl + 127) / 128, nB), 128, 0, st>>>(N, R);
+            k_cart_bus<<<dim3((N.nb + 127) / 128, nB), 128, 0, st>>>(N, R);
+        }
+    }
+    if (f) {
+        EvalReq E{};
+        E.B = bt->B;
+        E.x = bt->x; E.obj_weight = bt->obj_weight; E.f = f;
+        for (int b0 = 0; b0 < bt->B; b0 += 65535)
+            k_cart_obj<<<std::min(65535, bt->B - b0), OBJ_LANES, 0, st>>>(N, E, b0);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_last_error(EXAGO_ECUDA, std::string("cartesian evaluation launch: ") +
+                                               cudaGetErrorString(e));
+    return EXAGO_OK;
+}
+
+}  // extern "C"

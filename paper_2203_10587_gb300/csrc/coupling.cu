@@ -42,8 +42,12 @@ constexpr int kMaxGridY = 65535;
 // Children of a heavy state staged in shared memory per pass.
 constexpr int kStageChildren = 2048;
 
-// Block (256 threads) per (state b0 + blockIdx.y, 256 generators): one subtraction per value.  The
-// state and its parent are uniform over the block.
+// Values per thread along a row: every load of a thread is issued before its first store.
+constexpr int kUnroll = 4;
+constexpr int kRowSpan = 256 * kUnroll;   // values of one row per block
+
+// Block (256 threads) per (state b0 + blockIdx.y, kRowSpan generators): one subtraction per value.
+// The state and its parent are uniform over the block.
 __global__ void __launch_bounds__(256) k_coupling(const int *__restrict__ parent, int b0, int n,
                                                   int nb, int ng, const double *__restrict__ x,
                                                   double *__restrict__ r) {
@@ -52,15 +56,26 @@ __global__ void __launch_bounds__(256) k_coupling(const int *__restrict__ parent
     const double *xb = x + (int64_t)b * n + 2 * nb;
     const double *xp = x + (int64_t)(p < 0 ? b : p) * n + 2 * nb;
     double *rb = r + (int64_t)b * ng;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x)
-        rb[k] = p < 0 ? 0.0 : __ldg(xb + k) - __ldg(xp + k);
+    const int k0 = blockIdx.x * kRowSpan + threadIdx.x;
+    double own[kUnroll], par[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+        const int k = k0 + u * 256;
+        own[u] = k < ng && p >= 0 ? __ldg(xb + k) : 0.0;
+        par[u] = k < ng && p >= 0 ? __ldg(xp + k) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+        const int k = k0 + u * 256;
+        if (k < ng) rb[k] = p < 0 ? 0.0 : own[u] - par[u];
+    }
 }
 
 __device__ __forceinline__ void put(double *o, double v, int accumulate) {
     *o = accumulate ? *o + v : v;
 }
 
-// Block (256 threads) per (listed state, 256 generators): its own row's multiplier minus its
+// Block (256 threads) per (listed state, kRowSpan generators): its own row's multiplier minus its
 // children's, the children in ascending order.  The state's child range is uniform over the block.
 __global__ void __launch_bounds__(256) k_coupling_jtv_light(
     const int *__restrict__ light, int j0, const int *__restrict__ parent,
@@ -71,10 +86,25 @@ __global__ void __launch_bounds__(256) k_coupling_jtv_light(
     const int c0 = __ldg(cptr + s), c1 = __ldg(cptr + s + 1);
     const double *ns = nu + (int64_t)s * ng;
     double *os = out + (int64_t)s * ldo;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ng; k += gridDim.x * blockDim.x) {
-        double v = own ? __ldg(ns + k) : 0.0;
-        for (int c = c0; c < c1; c++) v -= __ldg(nu + (int64_t)__ldg(cidx + c) * ng + k);
-        put(os + k, v, accumulate);
+    const int k0 = blockIdx.x * kRowSpan + threadIdx.x;
+    double v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+        const int k = k0 + u * 256;
+        v[u] = own && k < ng ? __ldg(ns + k) : 0.0;
+    }
+    for (int c = c0; c < c1; c++) {
+        const double *nc = nu + (int64_t)__ldg(cidx + c) * ng;
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const int k = k0 + u * 256;
+            if (k < ng) v[u] -= __ldg(nc + k);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+        const int k = k0 + u * 256;
+        if (k < ng) put(os + k, v[u], accumulate);
     }
 }
 
@@ -126,8 +156,8 @@ exago_status check_call(exago_coupling_t c) {
     return EXAGO_OK;
 }
 
-// Blocks along a row of ng values: one 256-thread block per 256 values.
-unsigned row_blocks(int ng) { return (unsigned)((ng + 255) / 256); }
+// Blocks along a row of ng values: one 256-thread block per kRowSpan values.
+unsigned row_blocks(int ng) { return (unsigned)((ng + kRowSpan - 1) / kRowSpan); }
 
 }  // namespace
 

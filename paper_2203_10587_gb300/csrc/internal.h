@@ -201,6 +201,9 @@ int bus_blocks_per_sm(size_t smem_bytes);   // k_bus blocks of 128 threads per S
 // thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.
 bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **dev, int *device);
 exago_status set_last_error(exago_status s, const std::string &msg);
+// The net's internal workspace, grown to at least `bytes` (a growth synchronises the device first,
+// as in the evaluations); calls that use it must be ordered like the evaluations.
+exago_status net_workspace(exago_net_t net, size_t bytes, void **ws);
 // cudaMalloc for every device allocation of the library (honours exago_test_fail_allocations).
 cudaError_t dev_malloc(void **p, size_t bytes);
 // exago_eval_all without the graph cache (serving: every request has its own buffers).  With

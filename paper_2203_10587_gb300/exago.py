@@ -35,7 +35,8 @@ EXPORTS = [
     "exago_serve_set_merge", "exago_serve_poll", "exago_serve_wait", "exago_serve_stats",
     "exago_serve_destroy", "exago_test_fail_allocations", "exago_coupling_create",
     "exago_coupling_destroy", "exago_coupling_dims", "exago_coupling_jac_pattern",
-    "exago_eval_coupling", "exago_eval_coupling_jtv",
+    "exago_eval_coupling", "exago_eval_coupling_jtv", "exago_net_dims_cart",
+    "exago_net_jac_pattern_cart", "exago_eval_cart_workspace_size", "exago_eval_cart",
 ]
 
 SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
@@ -127,6 +128,11 @@ def lib():
                                        ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_uint64)], i32),
                 "exago_serve_destroy": ([vp], i32),
+                "exago_net_dims_cart": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32), i64p, i64p], i32),
+                "exago_net_jac_pattern_cart": ([vp, vp, vp], i32),
+                "exago_eval_cart_workspace_size": ([vp, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
+                "exago_eval_cart": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp], i32),
                 "exago_coupling_create": ([vp, i32, vp, ctypes.POINTER(vp)], i32),
                 "exago_coupling_destroy": ([vp], i32),
                 "exago_coupling_dims": ([vp, ctypes.POINTER(i32), i64p, i64p], i32),
@@ -406,6 +412,35 @@ def exago_serve_stats(s):
 
 def exago_serve_destroy(s):
     _check(lib().exago_serve_destroy(s))
+
+
+def exago_net_dims_cart(h):
+    """(n, m_eq, m_ineq, nnzJ, nnzH) of the power-balance-cartesian formulation."""
+    n, me, mi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nj, nh = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().exago_net_dims_cart(h, ctypes.byref(n), ctypes.byref(me), ctypes.byref(mi),
+                                     ctypes.byref(nj), ctypes.byref(nh)))
+    return n.value, me.value, mi.value, nj.value, nh.value
+
+
+def exago_net_jac_pattern_cart(h):
+    n, me, mi, nj, _ = exago_net_dims_cart(h)
+    rowptr = np.zeros(me + mi + 1, np.int64)
+    col = np.zeros(max(nj, 1), np.int32)
+    _check(lib().exago_net_jac_pattern_cart(h, _hp(rowptr), _hp(col)))
+    return rowptr, col[:nj]
+
+
+def exago_eval_cart_workspace_size(h, B: int) -> int:
+    v = ctypes.c_size_t()
+    _check(lib().exago_eval_cart_workspace_size(h, int(B), ctypes.byref(v)))
+    return v.value
+
+
+def exago_eval_cart(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None, hval=None):
+    """The power-balance-cartesian evaluation: x = [e | f | Pg | Qg], lambda and gh of m + nb."""
+    _check(lib().exago_eval_cart(h, ctypes.byref(batch), _out(f), _out(grad), _out(gh),
+                                 _out(jval), _out(hval)))
 
 
 def exago_coupling_create(net_h, parent):

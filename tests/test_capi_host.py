@@ -337,3 +337,31 @@ def test_coupling_host_only_refuses_evaluation(L):
     h = exago.exago_coupling_create(net.h, np.zeros(0, np.int32))
     assert exago.exago_coupling_dims(h) == (0, 0, 0)
     exago.exago_coupling_destroy(h)
+
+
+# ---- power-balance-cartesian formulation: host side ----------------------------------------------
+
+@pytest.mark.parametrize("name", sorted(GRIDS))
+def test_cartesian_patterns_match_oracle(L, oracle_mod, name):
+    g = GRIDS[name]()
+    net = plan(g)
+    b = synth.random_batch(4, g, 1)
+    lam = np.concatenate([b.lam[0], np.ones(g.nb)])
+    r = oracle_mod.evaluate(oracle_mod.OracleNet(g), b.x[0], lam, cartesian=True)
+    n, me, mi, nj, nh = exago.exago_net_dims_cart(net.h)
+    assert (n, me, mi) == (g.n, 2 * g.nb, 2 * g.nl + g.nb)
+    assert nj == 6 * g.nb + 16 * g.nl + 2 * g.ng and nh == net.nnzH
+    jr, jc = exago.exago_net_jac_pattern_cart(net.h)
+    hr, hc = exago.exago_net_hess_pattern(net.h)
+    np.testing.assert_array_equal(jr, r["J"][0])
+    np.testing.assert_array_equal(jc, r["J"][1])
+    np.testing.assert_array_equal(hr, r["H"][0])
+    np.testing.assert_array_equal(hc, r["H"][1])
+
+
+def test_cartesian_evaluation_needs_a_device_net(L):
+    net = plan(synth.grid_30bus())
+    rc = L.exago_eval_cart(net.h, None, None, None, None, None, None)
+    assert exago.STATUS[rc] == "EXAGO_ESTATE"
+    v = ctypes.c_size_t()
+    assert exago.STATUS[L.exago_eval_cart_workspace_size(net.h, 4, ctypes.byref(v))] == "EXAGO_ESTATE"

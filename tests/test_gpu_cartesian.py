@@ -1,0 +1,160 @@
+"""GPU: the power-balance-cartesian evaluation (exago_eval_cart) through the C ABI against the
+oracle's cartesian evaluator on the same seeded inputs, element by element, within
+|gpu - oracle| <= 1e-11 max(1, |oracle|).
+
+States are the seeded polar states of the synthetic generator mapped to e = Vm cos Va,
+f = Vm sin Va, with multipliers for the voltage rows appended.  Cases: the 30-bus grid with
+outages, a 300-bus grid with shunts, transformers, load scales and objective weights, a grid with
+parallel branches and several generators on one bus, chunked batches (more states than one chunk
+of branch-end records), subsets of outputs, a caller workspace, and the 2,000-bus x 512 N-1 batch
+at full size (sampled states against the oracle, and every state against the polar GPU path at
+the same point).
+"""
+import numpy as np
+import pytest
+
+from paper_2203_10587_gb300 import synth
+from parity_util import assert_close, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ex():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2203_10587_gb300 import build, exago
+    build.build()
+    exago.lib()
+    return exago
+
+
+def to_cartesian(g, b, seed):
+    """Cartesian copies of a polar synth.Batch: x -> [e | f | Pg | Qg], lambda + muV."""
+    nb = g.nb
+    Va, Vm = b.x[:, :nb], b.x[:, nb:2 * nb]
+    x = b.x.copy()
+    x[:, :nb] = Vm * np.cos(Va)
+    x[:, nb:2 * nb] = Vm * np.sin(Va)
+    muV = np.random.default_rng(seed).normal(size=(b.B, nb))
+    lam = np.concatenate([b.lam, muV], axis=1)
+    return x, lam
+
+
+def run_cart(ex, net, b, x, lam, which=("f", "grad", "gh", "jval", "hval"), workspace=None):
+    import torch
+    d = to_device(b)
+    X = torch.as_tensor(x, device="cuda")
+    LAM = torch.as_tensor(lam, device="cuda")
+    bt = ex.make_batch(X, LAM, d["mask"], d["pd_scale"], d["obj_weight"], b.sigma,
+                       workspace=workspace)
+    n, me, mi, nj, nh = ex.exago_net_dims_cart(net.h)
+    z = lambda *s: torch.full(s, np.nan, dtype=torch.float64, device="cuda")
+    out = {"f": z(b.B), "grad": z(b.B, n), "gh": z(b.B, me + mi), "jval": z(b.B, nj),
+           "hval": z(b.B, nh)}
+    out = {k: (v if k in which else None) for k, v in out.items()}
+    ex.exago_eval_cart(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"], out["hval"])
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+
+
+def oracle_cart(om, g, b, x, lam, i):
+    return om.evaluate(om.OracleNet(g), x[i], lam[i],
+                       None if b.mask is None else b.mask[i],
+                       None if b.pd_scale is None else b.pd_scale[i],
+                       1.0 if b.obj_weight is None else float(b.obj_weight[i]), b.sigma,
+                       cartesian=True)
+
+
+def compare(out, ref, i, what):
+    if "f" in out:
+        assert_close(out["f"][i], ref["f"], f"{what} f[{i}]")
+    if "grad" in out:
+        assert_close(out["grad"][i], ref["grad"], f"{what} grad[{i}]")
+    if "gh" in out:
+        assert_close(out["gh"][i], ref["gh"], f"{what} gh[{i}]")
+    if "jval" in out:
+        assert_close(out["jval"][i], ref["J"][2], f"{what} J[{i}]")
+    if "hval" in out:
+        assert_close(out["hval"][i], ref["H"][2], f"{what} H[{i}]")
+
+
+def parallel_grid():
+    from test_capi_host import parallel_grid as pg
+    return pg()
+
+
+CASES = {
+    "30bus_outages": (lambda: synth.grid_30bus(),
+                      dict(B=4, masks=True, sigma=0.8)),
+    "300bus_shunts_scenarios": (lambda: synth.make_grid(61, 300, 389, 77, transformer_frac=0.3,
+                                                        shunts=True),
+                                dict(B=5, masks=True, pd_scale=True, obj_weight=True, sigma=0.7)),
+    "parallel_branches": (parallel_grid, dict(B=3, masks=True, sigma=1.0)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_cartesian_matches_oracle(ex, oracle_mod, name):
+    mk, kw = CASES[name]
+    g = mk()
+    B = kw.pop("B")
+    b = synth.random_batch(62, g, B, **kw)
+    x, lam = to_cartesian(g, b, 62)
+    net = ex.Net(g)
+    out = run_cart(ex, net, b, x, lam)
+    for i in range(B):
+        compare(out, oracle_cart(oracle_mod, g, b, x, lam, i), i, name)
+    net.close()
+
+
+def test_cartesian_output_subsets_and_workspace(ex, oracle_mod):
+    """Every subset of outputs gives the full call's values bit for bit; a caller workspace
+    gives the same values as the internal one."""
+    import torch
+    g = synth.make_grid(63, 120, 160, 30, shunts=True)
+    b = synth.random_batch(63, g, 3, masks=True, sigma=0.9)
+    x, lam = to_cartesian(g, b, 63)
+    net = ex.Net(g)
+    full = run_cart(ex, net, b, x, lam)
+    for which in (("f",), ("grad",), ("gh",), ("jval",), ("hval",), ("gh", "hval")):
+        part = run_cart(ex, net, b, x, lam, which)
+        for k in which:
+            np.testing.assert_array_equal(part[k], full[k], err_msg=str(which))
+    ws_bytes = ex.exago_eval_cart_workspace_size(net.h, b.B)
+    ws = torch.empty(ws_bytes // 8 + 32, dtype=torch.float64, device="cuda")
+    off = (-ws.data_ptr()) % 256 // 8
+    wsa = ws[off:off + ws_bytes // 8]
+    own = run_cart(ex, net, b, x, lam, workspace=wsa)
+    for k in full:
+        np.testing.assert_array_equal(own[k], full[k])
+    compare(full, oracle_cart(oracle_mod, g, b, x, lam, 1), 1, "subset grid")
+    net.close()
+
+
+def test_cartesian_full_size_n1(ex, oracle_mod):
+    """2,000-bus grid x 512 N-1 states (several chunks of records): sampled states against the
+    oracle, and every state's g | h against the polar GPU path at the same point."""
+    from parity_util import gpu_eval
+    g = synth.grid_2000()
+    b = synth.contingency_batch(3, g, 512)
+    x, lam = to_cartesian(g, b, 64)
+    net = ex.Net(g)
+    assert ex.exago_eval_cart_workspace_size(net.h, 512) < 512 * 2 * g.nl * 14 * 8
+    out = run_cart(ex, net, b, x, lam)
+    for i in (0, 1, 255, 511):
+        compare(out, oracle_cart(oracle_mod, g, b, x, lam, i), i, "2000-bus")
+    polar = gpu_eval(net, b, which=("gh",))
+    assert_close(out["gh"][:, :g.m], polar["gh"], "cartesian vs polar g|h")
+    np.testing.assert_allclose(out["gh"][:, g.m:], b.x[:, g.nb:2 * g.nb] ** 2, rtol=1e-14)
+    net.close()
+
+
+def test_cartesian_empty_batch(ex):
+    import torch
+    g = synth.grid_30bus()
+    net = ex.Net(g)
+    x = torch.zeros(0, g.n, dtype=torch.float64, device="cuda")
+    ex.exago_eval_cart(net.h, ex.make_batch(x))
+    assert ex.exago_eval_cart_workspace_size(net.h, 0) == 0
+    net.close()
