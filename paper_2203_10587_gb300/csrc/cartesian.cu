@@ -17,7 +17,8 @@
 // chunk of states, a branch kernel writes each branch end's 14-value record at its slot and the
 // branch's h values and h rows; a bus kernel walks each bus's slots in the plan's fixed order,
 // writes the neighbour entries of its J and H rows and finishes the diagonal, balance, voltage
-// and generator terms.  Chunks are sized so that the records stay in L2 between the two kernels.
+// and generator terms.  Chunks are sized so that the records stay in L2 between the two kernels;
+// each kernel's grid is its resident CTA count, looping over (state, block) work items.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,7 +42,7 @@ enum CartComp {
 constexpr size_t kChunkRecordBytes = (size_t)48 << 20;   // records of one chunk stay in L2
 
 struct CartReq {
-    int B, b0;                  // states of this launch: b0 .. b0 + gridDim.y
+    int B, b0;                  // states of this launch: b0 .. b0 + nB (the kernels' argument)
     int mc;                     // rows of g | h: m + nb
     int64_t nnzJc;              // Jacobian entries per state: nnzJ + 2 nb
     const double *x, *lam;
@@ -76,10 +77,9 @@ __device__ __forceinline__ EndOuter end_outer(double m2, double p1, double p2, d
     return o;
 }
 
-__global__ void __launch_bounds__(128) k_cart_branch(const DevNet N, const CartReq R) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= N.nl) return;
-    const int bl = blockIdx.y, b = R.b0 + bl;
+// One (state, branch) item of the branch kernel.
+__device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq &R, int bl, int l) {
+    const int b = R.b0 + bl;
     const int nb = N.nb, nl = N.nl;
     double *scr = R.scratch + (size_t)bl * N.nslot * CNC;
     double *rf = scr + (size_t)__ldg(N.br_slot + l) * CNC;
@@ -182,6 +182,17 @@ __global__ void __launch_bounds__(128) k_cart_branch(const DevNet N, const CartR
     }
 }
 
+// Work items (state of the chunk, block of 128 branches or buses), state-major, taken by a grid
+// of the resident CTA count so that no launch ends in a nearly empty wave.
+__global__ void __launch_bounds__(128) k_cart_branch(const DevNet N, const CartReq R, int nB) {
+    const int per = (N.nl + 127) / 128;
+    for (int it = blockIdx.x; it < nB * per; it += gridDim.x) {
+        const int bl = it / per;
+        const int l = (it - bl * per) * 128 + threadIdx.x;
+        if (l < N.nl) cart_branch_item(N, R, bl, l);
+    }
+}
+
 // The values a bus reads from one record.
 struct CRec {
     double P, Q, pe, pf, qe, qf, pev, pfv, hee, hfe, hff, heev, hfev, hffv;
@@ -204,10 +215,8 @@ __device__ __forceinline__ CRec load_crec(const double *r, bool wantH) {
     return o;
 }
 
-__global__ void __launch_bounds__(128) k_cart_bus(const DevNet N, const CartReq R) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N.nb) return;
-    const int bl = blockIdx.y, b = R.b0 + bl;
+__device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R, int bl, int i) {
+    const int b = R.b0 + bl;
     const int nb = N.nb, ng = N.ng;
     const bool wantH = R.hval != nullptr;
     const double *scr = R.scratch + (size_t)bl * N.nslot * CNC;
@@ -317,6 +326,15 @@ __global__ void __launch_bounds__(128) k_cart_bus(const DevNet N, const CartReq 
     }
 }
 
+__global__ void __launch_bounds__(128) k_cart_bus(const DevNet N, const CartReq R, int nB) {
+    const int per = (N.nb + 127) / 128;
+    for (int it = blockIdx.x; it < nB * per; it += gridDim.x) {
+        const int bl = it / per;
+        const int i = (it - bl * per) * 128 + threadIdx.x;
+        if (i < N.nb) cart_bus_item(N, R, bl, i);
+    }
+}
+
 // Objective of each state (the polar model's: it depends on Pg only).
 __global__ void __launch_bounds__(OBJ_LANES) k_cart_obj(const DevNet N, const EvalReq R, int b0) {
     __shared__ double part[OBJ_LANES];
@@ -324,6 +342,24 @@ __global__ void __launch_bounds__(OBJ_LANES) k_cart_obj(const DevNet N, const Ev
 }
 
 size_t record_bytes(const DevNet &N) { return (size_t)N.nslot * CNC * sizeof(double); }
+
+// Resident CTAs of a kernel on the current device (looked up once per device and kernel).
+int resident_ctas(const void *kernel, int slot) {
+    static int cache[64][2];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev][slot] == 0) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            per_sm < 1 || sms < 1) {
+            cudaGetLastError();
+            return 152;
+        }
+        cache[dev][slot] = per_sm * sms;
+    }
+    return cache[dev][slot];
+}
 
 int chunk_states(const DevNet &N, int B) {
     const size_t per = std::max<size_t>(record_bytes(N), 1);
@@ -422,8 +458,12 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
         for (int b0 = 0; b0 < bt->B; b0 += chunk) {
             const int nB = std::min(chunk, bt->B - b0);
             R.b0 = b0;
-            if (N.nl > 0) k_cart_branch<<<dim3((N.nl + 127) / 128, nB), 128, 0, st>>>(N, R);
-            k_cart_bus<<<dim3((N.nb + 127) / 128, nB), 128, 0, st>>>(N, R);
+            const int br_items = nB * ((N.nl + 127) / 128), bus_items = nB * ((N.nb + 127) / 128);
+            if (N.nl > 0)
+                k_cart_branch<<<std::min(br_items, resident_ctas((const void *)k_cart_branch, 0)),
+                                128, 0, st>>>(N, R, nB);
+            k_cart_bus<<<std::min(bus_items, resident_ctas((const void *)k_cart_bus, 1)), 128, 0,
+                         st>>>(N, R, nB);
         }
     }
     if (f) {

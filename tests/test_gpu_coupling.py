@@ -132,3 +132,49 @@ def test_coupling_full_size_70k_periods(ex, oracle_mod):
     L2; every element against the oracle."""
     run_case(ex, oracle_mod, synth.grid_sized(9, 70_000), synth.coupling_parents("chain", 512),
              seed=70)
+
+
+def test_multi_period_stacked_quantities(ex, oracle_mod):
+    """The multi-period problem (Sec. IV, eqs. (11)-(15)) over 6 periods of a 300-bus grid with
+    per-period load scales: stacked constraints [g | h of every period ; ramp rows] and the
+    stacked transpose product J' [lambda ; nu] = per-period exago_eval_jtv plus the coupling
+    transpose added into the Pg block, against the oracle's per-period Jacobians (CSR) and its
+    coupling rows."""
+    import scipy.sparse as sp
+    import torch
+    from parity_util import to_device
+    g = synth.make_grid(71, 300, 389, 77, transformer_frac=0.2, shunts=True)
+    T = 6
+    b = synth.random_batch(71, g, T, pd_scale=True, sigma=0.5)
+    parent = synth.coupling_parents("chain", T)
+    nu = np.random.default_rng(72).normal(size=(T, g.ng))
+    net = ex.Net(g)
+    d = to_device(b)
+    bt = ex.make_batch(d["x"], d["lam"], None, d["pd_scale"], None, b.sigma)
+    gh = torch.empty(T, g.m, dtype=torch.float64, device="cuda")
+    ex.exago_eval_cons(net.h, bt, gh)
+    r = torch.empty(T, g.ng, dtype=torch.float64, device="cuda")
+    cpl = ex.exago_coupling_create(net.h, parent)
+    try:
+        ex.exago_eval_coupling(cpl, d["x"], r)
+        jt = torch.empty(T, g.n, dtype=torch.float64, device="cuda")
+        ex.exago_eval_jtv(net.h, bt, d["lam"], jt)
+        ex.exago_eval_coupling_jtv(cpl, torch.as_tensor(nu, device="cuda"),
+                                   jt.data_ptr() + 8 * 2 * g.nb, ldo=g.n, accumulate=True)
+        torch.cuda.synchronize()
+    finally:
+        ex.exago_coupling_destroy(cpl)
+    c_gpu = np.concatenate([gh.cpu().numpy().reshape(-1), r.cpu().numpy().reshape(-1)])
+    jt_gpu = jt.cpu().numpy()
+    onet = oracle_mod.OracleNet(g)
+    c_ref, jt_ref = [], np.zeros((T, g.n))
+    for t in range(T):
+        o = oracle_mod.evaluate(onet, b.x[t], b.lam[t], None, b.pd_scale[t], 1.0, b.sigma)
+        c_ref.append(o["gh"])
+        J = sp.csr_matrix((o["J"][2], o["J"][1], o["J"][0]), shape=(g.m, g.n))
+        jt_ref[t] = J.T @ b.lam[t]
+    c_ref = np.concatenate(c_ref + [oracle_mod.coupling(parent, b.x, g.nb, g.ng).reshape(-1)])
+    jt_ref += oracle_mod.coupling_jtv(parent, nu, g.n, g.nb)
+    assert_close(c_gpu, c_ref, "stacked constraints")
+    assert_close(jt_gpu, jt_ref, "stacked J' [lambda; nu]")
+    net.close()
