@@ -491,6 +491,11 @@ def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):
     z = lambda *sh: torch.empty(*sh, dtype=torch.float64, device=dev)
     out = [z(b.B), z(b.B, n), z(b.B, me + mi), z(b.B, nj), z(b.B, nh)]
     ms = time_calls(torch, lambda: exago.exago_eval_cart(net.h, bt, *out), 200, warm=5)
+    v = torch.randn(b.B, me + mi, dtype=torch.float64, device=dev)
+    u = torch.randn(b.B, n, dtype=torch.float64, device=dev)
+    o = torch.empty(b.B, n, dtype=torch.float64, device=dev)
+    ms_jtv = time_calls(torch, lambda: exago.exago_eval_cart_jtv(net.h, bt, v, o), 200)
+    ms_hvp = time_calls(torch, lambda: exago.exago_eval_cart_hvp(net.h, bt, u, o), 200)
     per_state = 8 * (n + (me + mi) + 1 + n + (me + mi) + nj + nh) + g.nl
     net_bytes = 8 * (11 * g.nl + 4 * nb + 4 * g.ng) + 4 * (2 * g.nl + 8 * nb + g.ng + 4 * g.nl)
     nbytes = per_state * b.B + net_bytes
@@ -498,6 +503,7 @@ def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):
     return {"workload": "2000-bus x 512 N-1 states in rectangular voltages, all outputs",
             "evals_per_s": b.B / (ms * 1e-3), "ms_per_batch": ms,
             "vs_polar_same_states": polar_ms / ms,
+            "jtv_per_s": b.B / (ms_jtv * 1e-3), "hvp_per_s": b.B / (ms_hvp * 1e-3),
             "algorithmic_bytes": nbytes, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
             "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak,
             "schedule": "branch records + bus assembly per chunk of states (records stay in L2)"}

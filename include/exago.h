@@ -215,8 +215,8 @@ exago_status exago_eval_hvp(exago_net_t net, const exago_batch *batch, const dou
  *                               exago_eval_all (else the net's internal workspace, grown on
  *                               demand).  Errors as exago_eval_all.  Runs the multi-kernel
  *                               schedule (branch records, then bus assembly, per chunk of states);
- *                               the persistent schedule, the graph cache and the adjoint products
- *                               are the polar model's only.
+ *                               the persistent schedule and the graph cache are the polar
+ *                               model's only.
  */
 exago_status exago_net_dims_cart(exago_net_t net, int *n, int *m_eq, int *m_ineq, int64_t *nnzJ,
                                  int64_t *nnzH);
@@ -224,6 +224,17 @@ exago_status exago_net_jac_pattern_cart(exago_net_t net, int64_t *rowptr, int *c
 exago_status exago_eval_cart_workspace_size(exago_net_t net, int B, size_t *bytes);
 exago_status exago_eval_cart(exago_net_t net, const exago_batch *batch, double *f, double *grad,
                              double *gh, double *jval, double *hval);
+/* Adjoint products of the cartesian constraint map c = [g; h] (m_c rows), as exago_eval_jvp / jtv
+ * / hvp for the polar one: out [B][m_c] = J u (u [B][n]); out [B][n] = J^T v (v [B][m_c]);
+ * out [B][n] = H u with H = obj_factor w grad^2 f + sum_i lambda_i grad^2 c_i, the Hessian of
+ * exago_eval_cart (needs lambda [B][m_c]).  A batch->workspace of exago_eval_cart_workspace_size
+ * bytes is enough.  Errors as exago_eval_jvp. */
+exago_status exago_eval_cart_jvp(exago_net_t net, const exago_batch *batch, const double *u,
+                                 double *out);
+exago_status exago_eval_cart_jtv(exago_net_t net, const exago_batch *batch, const double *v,
+                                 double *out);
+exago_status exago_eval_cart_hvp(exago_net_t net, const exago_batch *batch, const double *u,
+                                 double *out);
 
 /*
  * Coupling (ramp) rows between the states of a batch.  ExaGO's multi-stage problems tie each

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "eval_items.cuh"
@@ -77,6 +78,94 @@ __device__ __forceinline__ EndOuter end_outer(double m2, double p1, double p2, d
     return o;
 }
 
+// Flows and first derivatives of one branch at voltages (ef + j ff, et + j ft).  For the end at u
+// towards v, p = dP/d(e_u, f_u, e_v, f_v) and q1, q2 = dQ/d(e_u, f_u); dQ/de_v = p4, dQ/df_v = -p3.
+struct CartBranch {
+    double Pf, Qf, Pt, Qt;
+    double p1f, p2f, q1f, q2f, p3f, p4f;   // from end (u = f, v = t)
+    double p1t, p2t, q1t, q2t, p3t, p4t;   // to end (u = t, v = f)
+};
+
+// The admittances of one branch (network tables).
+struct CartY {
+    double G, Bm, Gff, Bff, Gtt, Btt, Gff2, Bff2, Gtt2, Btt2;
+};
+
+__device__ __forceinline__ CartY cart_y(const DevNet &N, int l) {
+    CartY y;
+    y.G = __ldg(N.Gft + l); y.Bm = __ldg(N.Bft + l);
+    y.Gff = __ldg(N.Gff + l); y.Bff = __ldg(N.Bff + l);
+    y.Gtt = __ldg(N.Gtt + l); y.Btt = __ldg(N.Btt + l);
+    y.Gff2 = __ldg(N.Gff2 + l); y.Bff2 = __ldg(N.Bff2 + l);
+    y.Gtt2 = __ldg(N.Gtt2 + l); y.Btt2 = __ldg(N.Btt2 + l);
+    return y;
+}
+
+__device__ __forceinline__ CartBranch cart_terms(const CartY &y, double ef, double ff, double et,
+                                                 double ft) {
+    const double G = y.G, Bm = y.Bm, Gff = y.Gff, Bff = y.Bff, Gtt = y.Gtt, Btt = y.Btt;
+    const double Gff2 = y.Gff2, Bff2 = y.Bff2, Gtt2 = y.Gtt2, Btt2 = y.Btt2;
+    CartBranch c;
+    // a = Vf Vt cos th, bf = Vf Vt sin th (th = Va_f - Va_t); the to end sees -bf
+    const double a = fma(ef, et, ff * ft);
+    const double bf = fma(ff, et, -(ef * ft));
+    const double sf = fma(ef, ef, ff * ff), st = fma(et, et, ft * ft);
+    const double Ga = G * a, Ba = Bm * a, Gb = G * bf, Bb = Bm * bf;
+    c.Pf = fma(Gff, sf, Ga + Bb);
+    c.Qf = fma(-Bff, sf, Gb - Ba);
+    c.Pt = fma(Gtt, st, Ga - Bb);
+    c.Qt = fma(-Btt, st, -(Gb + Ba));
+    // admittance-voltage products shared by both ends' derivatives
+    const double Gef = G * ef, Gff_ = G * ff, Get = G * et, Gft_ = G * ft;
+    const double Bef = Bm * ef, Bff_ = Bm * ff, Bet = Bm * et, Bft_ = Bm * ft;
+    const double u1 = Get - Bft_, u2 = Gft_ + Bet;
+    c.p1f = fma(Gff2, ef, u1); c.p2f = fma(Gff2, ff, u2);
+    c.q1f = fma(-Bff2, ef, -u2); c.q2f = fma(-Bff2, ff, u1);
+    c.p3f = Gef + Bff_; c.p4f = Gff_ - Bef;
+    const double w1 = Gef - Bff_, w2 = Gff_ + Bef;
+    c.p1t = fma(Gtt2, et, w1); c.p2t = fma(Gtt2, ft, w2);
+    c.q1t = fma(-Btt2, et, -w2); c.q2t = fma(-Btt2, ft, w1);
+    c.p3t = Get + Bft_; c.p4t = Gft_ - Bet;
+    return c;
+}
+
+// The branch's Lagrangian-Hessian block over (e_f, f_f, e_t, f_t), 10 distinct values.  End
+// weights wP = lamP + 2 mu P, wQ = lamQ + 2 mu Q; the linear part of each end's block is
+// wP grad^2 P + wQ grad^2 Q: d = 2 (wP Gss - wQ Bss) on (e_u,e_u) and (f_u,f_u),
+// c1 = wP G - wQ B on (e_u,e_v) and (f_u,f_v), c2 = wP B + wQ G on (f_u,e_v) and -c2 on (e_u,f_v);
+// the rest is 2 mu (grad P grad P' + grad Q grad Q') (end_outer).
+struct CartHess {
+    double eef, fef, fff;            // (e_f,e_f), (f_f,e_f), (f_f,f_f)
+    double eet, fet, fft;            // (e_t,e_t), (f_t,e_t), (f_t,f_t)
+    double eeft, ffft, ef_ft, ff_et; // (e_f,e_t), (f_f,f_t), (e_f,f_t), (f_f,e_t)
+};
+
+__device__ __forceinline__ CartHess cart_hess(const CartY &y, const CartBranch &c, double lPf,
+                                              double lQf, double lPt, double lQt, double muf,
+                                              double mut) {
+    const double G = y.G, Bm = y.Bm, Gff2 = y.Gff2, Bff2 = y.Bff2, Gtt2 = y.Gtt2, Btt2 = y.Btt2;
+    const double muf2 = twice(muf), mut2 = twice(mut);
+    const double wPf = fma(muf2, c.Pf, lPf), wQf = fma(muf2, c.Qf, lQf);
+    const double wPt = fma(mut2, c.Pt, lPt), wQt = fma(mut2, c.Qt, lQt);
+    const double df = fma(wPf, Gff2, -(wQf * Bff2)), dt = fma(wPt, Gtt2, -(wQt * Btt2));
+    const double c1 = fma(wPf, G, -(wQf * Bm)) + fma(wPt, G, -(wQt * Bm));
+    const double c2f = fma(wPf, Bm, wQf * G), c2t = fma(wPt, Bm, wQt * G);
+    const EndOuter of = end_outer(muf2, c.p1f, c.p2f, c.q1f, c.q2f, c.p3f, c.p4f);
+    const EndOuter ot = end_outer(mut2, c.p1t, c.p2t, c.q1t, c.q2t, c.p3t, c.p4t);
+    CartHess h;
+    h.eeft = c1 + (of.o13 + ot.o13);
+    h.ffft = c1 + (of.o24 + ot.o24);
+    h.ef_ft = (c2t - c2f) + (of.o14 + ot.o23);
+    h.ff_et = (c2f - c2t) + (of.o23 + ot.o14);
+    h.eef = df + (of.o11 + ot.ovv);
+    h.fef = of.o21;
+    h.fff = df + (of.o22 + ot.ovv);
+    h.eet = dt + (ot.o11 + of.ovv);
+    h.fet = ot.o21;
+    h.fft = dt + (ot.o22 + of.ovv);
+    return h;
+}
+
 // One (state, branch) item of the branch kernel.
 __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq &R, int bl, int l) {
     const int b = R.b0 + bl;
@@ -98,47 +187,20 @@ __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq 
         return;
     }
     const double *xb = R.x + (size_t)b * N.n;
-    const double ef = __ldg(xb + fb), et = __ldg(xb + tb);
-    const double ff = __ldg(xb + nb + fb), ft = __ldg(xb + nb + tb);
-    const double G = __ldg(N.Gft + l), Bm = __ldg(N.Bft + l);
-    const double Gff = __ldg(N.Gff + l), Bff = __ldg(N.Bff + l);
-    const double Gtt = __ldg(N.Gtt + l), Btt = __ldg(N.Btt + l);
-    const double Gff2 = __ldg(N.Gff2 + l), Bff2 = __ldg(N.Bff2 + l);
-    const double Gtt2 = __ldg(N.Gtt2 + l), Btt2 = __ldg(N.Btt2 + l);
-
-    // a = Vf Vt cos th, bf = Vf Vt sin th (th = Va_f - Va_t); the to end sees -bf
-    const double a = fma(ef, et, ff * ft);
-    const double bf = fma(ff, et, -(ef * ft));
-    const double sf = fma(ef, ef, ff * ff), st = fma(et, et, ft * ft);
-    const double Ga = G * a, Ba = Bm * a, Gb = G * bf, Bb = Bm * bf;
-    const double Pf = fma(Gff, sf, Ga + Bb), Qf = fma(-Bff, sf, Gb - Ba);
-    const double Pt = fma(Gtt, st, Ga - Bb), Qt = fma(-Btt, st, -(Gb + Ba));
-
-    // admittance-voltage products shared by both ends' derivatives
-    const double Gef = G * ef, Gff_ = G * ff, Get = G * et, Gft_ = G * ft;
-    const double Bef = Bm * ef, Bff_ = Bm * ff, Bet = Bm * et, Bft_ = Bm * ft;
-    // from end (u = f, v = t)
-    const double u1 = Get - Bft_, u2 = Gft_ + Bet;
-    const double p1f = fma(Gff2, ef, u1), p2f = fma(Gff2, ff, u2);
-    const double q1f = fma(-Bff2, ef, -u2), q2f = fma(-Bff2, ff, u1);
-    const double p3f = Gef + Bff_, p4f = Gff_ - Bef;
-    // to end (u = t, v = f)
-    const double w1 = Gef - Bff_, w2 = Gff_ + Bef;
-    const double p1t = fma(Gtt2, et, w1), p2t = fma(Gtt2, ft, w2);
-    const double q1t = fma(-Btt2, et, -w2), q2t = fma(-Btt2, ft, w1);
-    const double p3t = Get + Bft_, p4t = Gft_ - Bet;
-
+    const CartY y = cart_y(N, l);
+    const CartBranch c = cart_terms(y, __ldg(xb + fb), __ldg(xb + nb + fb), __ldg(xb + tb),
+                                    __ldg(xb + nb + tb));
     if (ghb) {
-        ghb[2 * nb + l] = fma(Pf, Pf, Qf * Qf);
-        ghb[2 * nb + nl + l] = fma(Pt, Pt, Qt * Qt);
+        ghb[2 * nb + l] = fma(c.Pf, c.Pf, c.Qf * c.Qf);
+        ghb[2 * nb + nl + l] = fma(c.Pt, c.Pt, c.Qt * c.Qt);
     }
     if (Jf) {
         // grad |S|^2 = 2 P grad P + 2 Q grad Q, columns (e_lo, e_hi, f_lo, f_hi)
-        const double Pf2 = twice(Pf), Qf2 = twice(Qf), Pt2 = twice(Pt), Qt2 = twice(Qt);
-        const double hff_e = fma(Pf2, p1f, Qf2 * q1f), hff_f = fma(Pf2, p2f, Qf2 * q2f);
-        const double hft_e = fma(Pf2, p3f, Qf2 * p4f), hft_f = fma(Pf2, p4f, -(Qf2 * p3f));
-        const double htt_e = fma(Pt2, p1t, Qt2 * q1t), htt_f = fma(Pt2, p2t, Qt2 * q2t);
-        const double htf_e = fma(Pt2, p3t, Qt2 * p4t), htf_f = fma(Pt2, p4t, -(Qt2 * p3t));
+        const double Pf2 = twice(c.Pf), Qf2 = twice(c.Qf), Pt2 = twice(c.Pt), Qt2 = twice(c.Qt);
+        const double hff_e = fma(Pf2, c.p1f, Qf2 * c.q1f), hff_f = fma(Pf2, c.p2f, Qf2 * c.q2f);
+        const double hft_e = fma(Pf2, c.p3f, Qf2 * c.p4f), hft_f = fma(Pf2, c.p4f, -(Qf2 * c.p3f));
+        const double htt_e = fma(Pt2, c.p1t, Qt2 * c.q1t), htt_f = fma(Pt2, c.p2t, Qt2 * c.q2t);
+        const double htf_e = fma(Pt2, c.p3t, Qt2 * c.p4t), htf_f = fma(Pt2, c.p4t, -(Qt2 * c.p3t));
         if (fb < tb) {
             Jf[0] = hff_e; Jf[1] = hft_e; Jf[2] = hff_f; Jf[3] = hft_f;
             Jt[0] = htf_e; Jt[1] = htt_e; Jt[2] = htf_f; Jt[3] = htt_f;
@@ -147,38 +209,25 @@ __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq 
             Jt[0] = htt_e; Jt[1] = htf_e; Jt[2] = htt_f; Jt[3] = htf_f;
         }
     }
-    put2c(rf, CR_P, Pf, Qf);
-    put2c(rf, CR_PE, p1f, p2f);
-    put2c(rf, CR_QE, q1f, q2f);
-    put2c(rf, CR_PEV, p3f, p4f);
-    put2c(rt, CR_P, Pt, Qt);
-    put2c(rt, CR_PE, p1t, p2t);
-    put2c(rt, CR_QE, q1t, q2t);
-    put2c(rt, CR_PEV, p3t, p4t);
+    put2c(rf, CR_P, c.Pf, c.Qf);
+    put2c(rf, CR_PE, c.p1f, c.p2f);
+    put2c(rf, CR_QE, c.q1f, c.q2f);
+    put2c(rf, CR_PEV, c.p3f, c.p4f);
+    put2c(rt, CR_P, c.Pt, c.Qt);
+    put2c(rt, CR_PE, c.p1t, c.p2t);
+    put2c(rt, CR_QE, c.q1t, c.q2t);
+    put2c(rt, CR_PEV, c.p3t, c.p4t);
     if (R.hval) {
-        // end weights: wP = lamP + 2 mu P, wQ = lamQ + 2 mu Q; the linear part of each end's block
-        // is wP grad^2 P + wQ grad^2 Q: diagonal d = 2 (wP Gss - wQ Bss) on (e_u,e_u) and
-        // (f_u,f_u), c1 = wP G - wQ B on (e_u,e_v) and (f_u,f_v), c2 = wP B + wQ G on (f_u,e_v)
-        // and -c2 on (e_u,f_v)
         const double *lb = R.lam + (size_t)b * R.mc;
-        const double muf2 = twice(__ldg(lb + 2 * nb + l)), mut2 = twice(__ldg(lb + 2 * nb + nl + l));
-        const double wPf = fma(muf2, Pf, __ldg(lb + fb)), wQf = fma(muf2, Qf, __ldg(lb + nb + fb));
-        const double wPt = fma(mut2, Pt, __ldg(lb + tb)), wQt = fma(mut2, Qt, __ldg(lb + nb + tb));
-        const double df = fma(wPf, Gff2, -(wQf * Bff2)), dt = fma(wPt, Gtt2, -(wQt * Btt2));
-        const double c1 = fma(wPf, G, -(wQf * Bm)) + fma(wPt, G, -(wQt * Bm));
-        const double c2f = fma(wPf, Bm, wQf * G), c2t = fma(wPt, Bm, wQt * G);
-        const EndOuter of = end_outer(muf2, p1f, p2f, q1f, q2f, p3f, p4f);
-        const EndOuter ot = end_outer(mut2, p1t, p2t, q1t, q2t, p3t, p4t);
-        const double eeft = c1 + (of.o13 + ot.o13);            // (e_f, e_t)
-        const double ffft = c1 + (of.o24 + ot.o24);            // (f_f, f_t)
-        const double ef_ft = (c2t - c2f) + (of.o14 + ot.o23);  // (e_f, f_t) = (f_t, e_f)
-        const double ff_et = (c2f - c2t) + (of.o23 + ot.o14);  // (f_f, e_t)
-        put2c(rf, CR_HEE, df + (of.o11 + ot.ovv), of.o21);
-        put2c(rf, CR_HFF, df + (of.o22 + ot.ovv), eeft);
-        put2c(rf, CR_HFEV, ff_et, ffft);
-        put2c(rt, CR_HEE, dt + (ot.o11 + of.ovv), ot.o21);
-        put2c(rt, CR_HFF, dt + (ot.o22 + of.ovv), eeft);
-        put2c(rt, CR_HFEV, ef_ft, ffft);
+        const CartHess h = cart_hess(y, c, __ldg(lb + fb), __ldg(lb + nb + fb), __ldg(lb + tb),
+                                     __ldg(lb + nb + tb), __ldg(lb + 2 * nb + l),
+                                     __ldg(lb + 2 * nb + nl + l));
+        put2c(rf, CR_HEE, h.eef, h.fef);
+        put2c(rf, CR_HFF, h.fff, h.eeft);
+        put2c(rf, CR_HFEV, h.ff_et, h.ffft);
+        put2c(rt, CR_HEE, h.eet, h.fet);
+        put2c(rt, CR_HFF, h.fft, h.eeft);
+        put2c(rt, CR_HFEV, h.ef_ft, h.ffft);
     }
 }
 
@@ -341,14 +390,153 @@ __global__ void __launch_bounds__(OBJ_LANES) k_cart_obj(const DevNet N, const Ev
     obj_block(N, R, b0 + blockIdx.x, part);
 }
 
+// ---- adjoint products of the cartesian constraint map c = [g; h] ----
+//   JVP  out [B][m_c] = J u,  JTV  out [B][n] = J^T v,  HVP  out [B][n] = (grad^2 L) u.
+// Each branch writes two values per end -- its P and Q row entries (JVP), or its contributions
+// to the end bus's e and f components (JTV, HVP) -- ordered by branch; the bus kernel sums its
+// slots' values in slot order and adds the shunt, voltage-row and generator terms.
+enum CartAdjMode : int { CADJ_JVP = 0, CADJ_JTV = 1, CADJ_HVP = 2 };
+
+struct CartAdjReq {
+    int b0, mc;
+    const double *x, *lam;
+    const uint8_t *mask;
+    const double *obj_weight;
+    double sigma;
+    const double *v;            // JVP / HVP: [B][n]; JTV: [B][m_c]
+    double *out;                // JVP: [B][m_c]; JTV / HVP: [B][n]
+    double *scratch;            // [chunk][nl][4]
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_cart_adj_branch(const DevNet N, const CartAdjReq A) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= N.nl) return;
+    const int bl = blockIdx.y, b = A.b0 + bl;
+    const int nb = N.nb, nl = N.nl;
+    double *rf = A.scratch + ((size_t)bl * nl + l) * 4, *rt = rf + 2;
+    const int fb = __ldg(N.f + l), tb = __ldg(N.t + l);
+    const bool on = A.mask == nullptr || A.mask[(size_t)b * nl + l] != 0;
+    if (!on) {
+        put2c(rf, 0, 0.0, 0.0);
+        put2c(rt, 0, 0.0, 0.0);
+        if (MODE == CADJ_JVP) {
+            A.out[(size_t)b * A.mc + 2 * nb + l] = 0.0;
+            A.out[(size_t)b * A.mc + 2 * nb + nl + l] = 0.0;
+        }
+        return;
+    }
+    const double *xb = A.x + (size_t)b * N.n;
+    const CartY y = cart_y(N, l);
+    const CartBranch c = cart_terms(y, __ldg(xb + fb), __ldg(xb + nb + fb), __ldg(xb + tb),
+                                    __ldg(xb + nb + tb));
+    if (MODE == CADJ_JTV) {
+        const double *vb = A.v + (size_t)b * A.mc;
+        const double vhf2 = twice(__ldg(vb + 2 * nb + l)), vht2 = twice(__ldg(vb + 2 * nb + nl + l));
+        // weights of grad P and grad Q at each end: row multiplier + 2 v_h (P or Q)
+        const double wPf = fma(vhf2, c.Pf, __ldg(vb + fb)), wQf = fma(vhf2, c.Qf, __ldg(vb + nb + fb));
+        const double wPt = fma(vht2, c.Pt, __ldg(vb + tb)), wQt = fma(vht2, c.Qt, __ldg(vb + nb + tb));
+        put2c(rf, 0, fma(wPf, c.p1f, fma(wQf, c.q1f, fma(wPt, c.p3t, wQt * c.p4t))),
+              fma(wPf, c.p2f, fma(wQf, c.q2f, fma(wPt, c.p4t, -(wQt * c.p3t)))));
+        put2c(rt, 0, fma(wPt, c.p1t, fma(wQt, c.q1t, fma(wPf, c.p3f, wQf * c.p4f))),
+              fma(wPt, c.p2t, fma(wQt, c.q2t, fma(wPf, c.p4f, -(wQf * c.p3f)))));
+        return;
+    }
+    const double *ub = A.v + (size_t)b * N.n;
+    const double uef = __ldg(ub + fb), uff = __ldg(ub + nb + fb);
+    const double uet = __ldg(ub + tb), uft = __ldg(ub + nb + tb);
+    if (MODE == CADJ_JVP) {
+        const double dPf = fma(c.p1f, uef, fma(c.p2f, uff, fma(c.p3f, uet, c.p4f * uft)));
+        const double dQf = fma(c.q1f, uef, fma(c.q2f, uff, fma(c.p4f, uet, -(c.p3f * uft))));
+        const double dPt = fma(c.p1t, uet, fma(c.p2t, uft, fma(c.p3t, uef, c.p4t * uff)));
+        const double dQt = fma(c.q1t, uet, fma(c.q2t, uft, fma(c.p4t, uef, -(c.p3t * uff))));
+        put2c(rf, 0, dPf, dQf);
+        put2c(rt, 0, dPt, dQt);
+        double *ob = A.out + (size_t)b * A.mc;
+        ob[2 * nb + l] = twice(fma(c.Pf, dPf, c.Qf * dQf));
+        ob[2 * nb + nl + l] = twice(fma(c.Pt, dPt, c.Qt * dQt));
+    } else {
+        const double *lb = A.lam + (size_t)b * A.mc;
+        const CartHess h = cart_hess(y, c, __ldg(lb + fb), __ldg(lb + nb + fb), __ldg(lb + tb),
+                                     __ldg(lb + nb + tb), __ldg(lb + 2 * nb + l),
+                                     __ldg(lb + 2 * nb + nl + l));
+        // rows of the block over (e_f, f_f, e_t, f_t) times u
+        put2c(rf, 0, fma(h.eef, uef, fma(h.fef, uff, fma(h.eeft, uet, h.ef_ft * uft))),
+              fma(h.fef, uef, fma(h.fff, uff, fma(h.ff_et, uet, h.ffft * uft))));
+        put2c(rt, 0, fma(h.eeft, uef, fma(h.ff_et, uff, fma(h.eet, uet, h.fet * uft))),
+              fma(h.ef_ft, uef, fma(h.ffft, uff, fma(h.fet, uet, h.fft * uft))));
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) k_cart_adj_bus(const DevNet N, const CartAdjReq A) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N.nb) return;
+    const int bl = blockIdx.y, b = A.b0 + bl;
+    const int nb = N.nb, ng = N.ng, nl = N.nl;
+    const double *scr = A.scratch + (size_t)bl * nl * 4;
+    const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
+    const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
+    double s0v = 0.0, s1v = 0.0;
+    for (int s = s0; s < s1; s++) {
+        const double2 r = ld2(scr + 2 * (size_t)__ldg(N.slot_ref + s));
+        s0v += r.x;
+        s1v += r.y;
+    }
+    const double *xb = A.x + (size_t)b * N.n;
+    const double ei = __ldg(xb + i), fi = __ldg(xb + nb + i);
+    const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
+    if (MODE == CADJ_JVP) {
+        const double *ub = A.v + (size_t)b * N.n;
+        const double dV = twice(fma(ei, __ldg(ub + i), fi * __ldg(ub + nb + i)));   // d(e^2 + f^2)
+        double oP = fma(Gs, dV, s0v), oQ = fma(-Bs, dV, s1v);
+        for (int q = g0; q < g1; q++) {
+            const int g = __ldg(N.gen_ord + q);
+            oP -= __ldg(ub + 2 * nb + g);
+            oQ -= __ldg(ub + 2 * nb + ng + g);
+        }
+        double *ob = A.out + (size_t)b * A.mc;
+        ob[i] = oP;
+        ob[nb + i] = oQ;
+        ob[2 * nb + 2 * nl + i] = dV;
+    } else if (MODE == CADJ_JTV) {
+        const double *vb = A.v + (size_t)b * A.mc;
+        const double vP = __ldg(vb + i), vQ = __ldg(vb + nb + i);
+        const double coef = twice(fma(Gs, vP, fma(-Bs, vQ, __ldg(vb + 2 * nb + 2 * nl + i))));
+        double *ob = A.out + (size_t)b * N.n;
+        ob[i] = fma(coef, ei, s0v);
+        ob[nb + i] = fma(coef, fi, s1v);
+        for (int q = g0; q < g1; q++) {
+            const int g = __ldg(N.gen_ord + q);
+            ob[2 * nb + g] = dneg(vP);
+            ob[2 * nb + ng + g] = dneg(vQ);
+        }
+    } else {
+        const double *lb = A.lam + (size_t)b * A.mc;
+        const double *ub = A.v + (size_t)b * N.n;
+        const double dsh = twice(fma(__ldg(lb + i), Gs,
+                                     fma(-__ldg(lb + nb + i), Bs, __ldg(lb + 2 * nb + 2 * nl + i))));
+        double *ob = A.out + (size_t)b * N.n;
+        ob[i] = fma(dsh, __ldg(ub + i), s0v);
+        ob[nb + i] = fma(dsh, __ldg(ub + nb + i), s1v);
+        const double sw = A.sigma * (A.obj_weight ? __ldg(A.obj_weight + b) : 1.0);
+        for (int q = g0; q < g1; q++) {
+            const int g = __ldg(N.gen_ord + q);
+            ob[2 * nb + g] = sw * __ldg(N.c2g + g) * __ldg(ub + 2 * nb + g);
+            ob[2 * nb + ng + g] = 0.0;
+        }
+    }
+}
+
 size_t record_bytes(const DevNet &N) { return (size_t)N.nslot * CNC * sizeof(double); }
 
 // Resident CTAs of a kernel on the current device (looked up once per device and kernel).
 int resident_ctas(const void *kernel, int slot) {
-    static int cache[64][2];
+    static std::atomic<int> cache[64][2];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (cache[dev][slot] == 0) {
+    int v = cache[dev][slot].load(std::memory_order_relaxed);
+    if (v == 0) {
         int per_sm = 0, sms = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 128, 0) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -356,14 +544,75 @@ int resident_ctas(const void *kernel, int slot) {
             cudaGetLastError();
             return 152;
         }
-        cache[dev][slot] = per_sm * sms;
+        v = per_sm * sms;
+        cache[dev][slot].store(v, std::memory_order_relaxed);
     }
-    return cache[dev][slot];
+    return v;
 }
 
 int chunk_states(const DevNet &N, int B) {
     const size_t per = std::max<size_t>(record_bytes(N), 1);
     return (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(B, 65535), kChunkRecordBytes / per));
+}
+
+// One adjoint product over the batch, in chunks of states whose branch values fit the workspace.
+exago_status cart_adjoint(exago_net_t net, const exago_batch *bt, const double *in, double *out,
+                          int mode) {
+    const HostPlan *plan = nullptr;
+    const DevNet *dev = nullptr;
+    int device = -1;
+    if (!net_internal_view(net, &plan, &dev, &device))
+        return set_last_error(net ? EXAGO_ESTATE : EXAGO_EINVAL,
+                              net ? "net was planned without a device" : "net is NULL");
+    if (!bt) return set_last_error(EXAGO_EINVAL, "batch is NULL");
+    if (bt->B < 0) return set_last_error(EXAGO_EINVAL, "batch B < 0");
+    if (bt->B == 0) return EXAGO_OK;
+    if (!bt->x) return set_last_error(EXAGO_EINVAL, "batch x is NULL");
+    if (!in || !out) return set_last_error(EXAGO_EINVAL, "input or output vector is NULL");
+    if (mode == CADJ_HVP && !bt->lambda)
+        return set_last_error(EXAGO_EINVAL, "batch lambda is NULL (needed by the Hessian)");
+    const DevNet &N = *dev;
+    const size_t per = (size_t)std::max(N.nl, 1) * 4 * sizeof(double);
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(bt->B, 65535),
+                                                          kChunkRecordBytes / per));
+    void *ws = bt->workspace;
+    if (ws) {
+        if (((uintptr_t)ws & 255) != 0)
+            return set_last_error(EXAGO_EINVAL, "workspace not 256-byte aligned");
+        if (bt->workspace_bytes < per)
+            return set_last_error(EXAGO_EINVAL, "workspace smaller than one state's branch values");
+        chunk = (int)std::min<size_t>((size_t)chunk, bt->workspace_bytes / per);
+    } else {
+        exago_status s = net_workspace(net, (size_t)chunk * per, &ws);
+        if (s != EXAGO_OK) return s;
+    }
+    CartAdjReq A{};
+    A.mc = N.m + N.nb;
+    A.x = bt->x; A.lam = bt->lambda; A.mask = bt->mask;
+    A.obj_weight = bt->obj_weight; A.sigma = bt->obj_factor;
+    A.v = in; A.out = out;
+    A.scratch = (double *)ws;
+    cudaStream_t st = (cudaStream_t)bt->stream;
+    for (int b0 = 0; b0 < bt->B; b0 += chunk) {
+        const int nB = std::min(chunk, bt->B - b0);
+        A.b0 = b0;
+        const dim3 gbr((N.nl + 127) / 128, nB), gbu((N.nb + 127) / 128, nB);
+        if (mode == CADJ_JVP) {
+            if (N.nl > 0) k_cart_adj_branch<CADJ_JVP><<<gbr, 128, 0, st>>>(N, A);
+            k_cart_adj_bus<CADJ_JVP><<<gbu, 128, 0, st>>>(N, A);
+        } else if (mode == CADJ_JTV) {
+            if (N.nl > 0) k_cart_adj_branch<CADJ_JTV><<<gbr, 128, 0, st>>>(N, A);
+            k_cart_adj_bus<CADJ_JTV><<<gbu, 128, 0, st>>>(N, A);
+        } else {
+            if (N.nl > 0) k_cart_adj_branch<CADJ_HVP><<<gbr, 128, 0, st>>>(N, A);
+            k_cart_adj_bus<CADJ_HVP><<<gbu, 128, 0, st>>>(N, A);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_last_error(EXAGO_ECUDA, std::string("cartesian adjoint launch: ") +
+                                               cudaGetErrorString(e));
+    return EXAGO_OK;
 }
 
 }  // namespace
@@ -478,6 +727,21 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
         return set_last_error(EXAGO_ECUDA, std::string("cartesian evaluation launch: ") +
                                                cudaGetErrorString(e));
     return EXAGO_OK;
+}
+
+exago_status exago_eval_cart_jvp(exago_net_t net, const exago_batch *batch, const double *u,
+                                 double *out) {
+    return cart_adjoint(net, batch, u, out, CADJ_JVP);
+}
+
+exago_status exago_eval_cart_jtv(exago_net_t net, const exago_batch *batch, const double *v,
+                                 double *out) {
+    return cart_adjoint(net, batch, v, out, CADJ_JTV);
+}
+
+exago_status exago_eval_cart_hvp(exago_net_t net, const exago_batch *batch, const double *u,
+                                 double *out) {
+    return cart_adjoint(net, batch, u, out, CADJ_HVP);
 }
 
 }  // extern "C"

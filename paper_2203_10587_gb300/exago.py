@@ -37,6 +37,7 @@ EXPORTS = [
     "exago_coupling_destroy", "exago_coupling_dims", "exago_coupling_jac_pattern",
     "exago_eval_coupling", "exago_eval_coupling_jtv", "exago_net_dims_cart",
     "exago_net_jac_pattern_cart", "exago_eval_cart_workspace_size", "exago_eval_cart",
+    "exago_eval_cart_jvp", "exago_eval_cart_jtv", "exago_eval_cart_hvp",
 ]
 
 SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
@@ -133,6 +134,9 @@ def lib():
                 "exago_net_jac_pattern_cart": ([vp, vp, vp], i32),
                 "exago_eval_cart_workspace_size": ([vp, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
                 "exago_eval_cart": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp], i32),
+                "exago_eval_cart_jvp": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
+                "exago_eval_cart_jtv": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
+                "exago_eval_cart_hvp": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
                 "exago_coupling_create": ([vp, i32, vp, ctypes.POINTER(vp)], i32),
                 "exago_coupling_destroy": ([vp], i32),
                 "exago_coupling_dims": ([vp, ctypes.POINTER(i32), i64p, i64p], i32),
@@ -443,6 +447,24 @@ def exago_eval_cart(h, batch: exago_batch, f=None, grad=None, gh=None, jval=None
                                  _out(jval), _out(hval)))
 
 
+def exago_eval_cart_jvp(h, batch: exago_batch, u, out):
+    """out [B][m + nb] = J u of the cartesian constraint map."""
+    import torch
+    _check(lib().exago_eval_cart_jvp(h, ctypes.byref(batch), _dp(u, torch.float64), _out(out)))
+
+
+def exago_eval_cart_jtv(h, batch: exago_batch, v, out):
+    """out [B][n] = J^T v of the cartesian constraint map (v [B][m + nb])."""
+    import torch
+    _check(lib().exago_eval_cart_jtv(h, ctypes.byref(batch), _dp(v, torch.float64), _out(out)))
+
+
+def exago_eval_cart_hvp(h, batch: exago_batch, u, out):
+    """out [B][n] = (cartesian Lagrangian Hessian at the batch's lambda and obj_factor) u."""
+    import torch
+    _check(lib().exago_eval_cart_hvp(h, ctypes.byref(batch), _dp(u, torch.float64), _out(out)))
+
+
 def exago_coupling_create(net_h, parent):
     """Coupling rows of a batch whose state b is tied to state parent[b] (-1: none); host array."""
     parent = _np(parent, np.int32)
@@ -532,3 +554,24 @@ class Net:
         exago_eval_all(self.h, batch, out.get("f"), out.get("grad"), out.get("gh"),
                        out.get("jval"), out.get("hval"))
         return out
+
+
+class Coupling:
+    """Owns the coupling rows of a batch of B states of a net, state b tied to parent[b] (-1:
+    none): r = Pg(x_b) - Pg(x_parent(b)) and its transpose product (exago_coupling_*)."""
+
+    def __init__(self, net: Net, parent):
+        self.h = exago_coupling_create(net.h, parent)
+        self.B, self.rows, self.nnz = exago_coupling_dims(self.h)
+        self.nb, self.ng, self.n = net.nb, net.ng, net.n
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            exago_coupling_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -158,3 +158,70 @@ def test_cartesian_empty_batch(ex):
     ex.exago_eval_cart(net.h, ex.make_batch(x))
     assert ex.exago_eval_cart_workspace_size(net.h, 0) == 0
     net.close()
+
+
+def test_cartesian_adjoints_match_oracle(ex, oracle_mod):
+    """J u, J' v and (grad^2 L) u of the cartesian map against the oracle's J and H (sparse
+    matrix-vector products), with outages, shunts, transformers and objective weights."""
+    import scipy.sparse as sp
+    import torch
+    g = synth.make_grid(65, 300, 389, 77, transformer_frac=0.3, shunts=True)
+    b = synth.random_batch(65, g, 4, masks=True, obj_weight=True, sigma=0.6)
+    x, lam = to_cartesian(g, b, 65)
+    mc = g.m + g.nb
+    rng = np.random.default_rng(65)
+    u = rng.normal(size=(b.B, g.n))
+    v = rng.normal(size=(b.B, mc))
+    net = ex.Net(g)
+    d = to_device(b)
+    X, LAM = torch.as_tensor(x, device="cuda"), torch.as_tensor(lam, device="cuda")
+    bt = ex.make_batch(X, LAM, d["mask"], None, d["obj_weight"], b.sigma)
+    U, V = torch.as_tensor(u, device="cuda"), torch.as_tensor(v, device="cuda")
+    jvp = torch.empty(b.B, mc, dtype=torch.float64, device="cuda")
+    jtv = torch.empty(b.B, g.n, dtype=torch.float64, device="cuda")
+    hvp = torch.empty(b.B, g.n, dtype=torch.float64, device="cuda")
+    ex.exago_eval_cart_jvp(net.h, bt, U, jvp)
+    ex.exago_eval_cart_jtv(net.h, bt, V, jtv)
+    ex.exago_eval_cart_hvp(net.h, bt, U, hvp)
+    torch.cuda.synchronize()
+    jvp, jtv, hvp = jvp.cpu().numpy(), jtv.cpu().numpy(), hvp.cpu().numpy()
+    for i in range(b.B):
+        r = oracle_cart(oracle_mod, g, b, x, lam, i)
+        J = sp.csr_matrix((r["J"][2], r["J"][1], r["J"][0]), shape=(mc, g.n))
+        L = sp.csr_matrix((r["H"][2], r["H"][1], r["H"][0]), shape=(g.n, g.n))
+        H = L + L.T - sp.diags(L.diagonal())
+        assert_close(jvp[i], J @ u[i], f"cart J u [{i}]")
+        assert_close(jtv[i], J.T @ v[i], f"cart J' v [{i}]")
+        assert_close(hvp[i], H @ u[i], f"cart H u [{i}]")
+    net.close()
+
+
+def test_cartesian_autograd_double_backward(ex, oracle_mod):
+    """torch.autograd over the cartesian map: grad of <v, c(x)> is J' v, and differentiating that
+    again along w gives (sum_i v_i grad^2 c_i) w, both against the oracle."""
+    import scipy.sparse as sp
+    import torch
+    from paper_2203_10587_gb300 import autograd
+    g = synth.make_grid(66, 120, 160, 30, shunts=True)
+    b = synth.random_batch(66, g, 3)
+    x, _ = to_cartesian(g, b, 66)
+    mc = g.m + g.nb
+    rng = np.random.default_rng(66)
+    v = rng.normal(size=(b.B, mc))
+    w = rng.normal(size=(b.B, g.n))
+    net = ex.Net(g)
+    X = torch.as_tensor(x, device="cuda").requires_grad_(True)
+    c = autograd.cons(X, net, cartesian=True)
+    (gx,) = torch.autograd.grad(c, X, torch.as_tensor(v, device="cuda"), create_graph=True)
+    (hw,) = torch.autograd.grad(gx, X, torch.as_tensor(w, device="cuda"))
+    gx, hw = gx.detach().cpu().numpy(), hw.cpu().numpy()
+    for i in range(b.B):
+        r = oracle_mod.evaluate(oracle_mod.OracleNet(g), x[i], v[i], None, None, 1.0, 0.0,
+                                cartesian=True)
+        J = sp.csr_matrix((r["J"][2], r["J"][1], r["J"][0]), shape=(mc, g.n))
+        L = sp.csr_matrix((r["H"][2], r["H"][1], r["H"][0]), shape=(g.n, g.n))
+        H = L + L.T - sp.diags(L.diagonal())
+        assert_close(c.detach().cpu().numpy()[i], r["gh"], f"cart c [{i}]")
+        assert_close(gx[i], J.T @ v[i], f"autograd J' v [{i}]")
+        assert_close(hw[i], H @ w[i], f"autograd H w [{i}]")
+    net.close()

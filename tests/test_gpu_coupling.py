@@ -178,3 +178,30 @@ def test_multi_period_stacked_quantities(ex, oracle_mod):
     assert_close(c_gpu, c_ref, "stacked constraints")
     assert_close(jt_gpu, jt_ref, "stacked J' [lambda; nu]")
     net.close()
+
+
+def test_coupling_autograd(ex, oracle_mod):
+    """torch.autograd over the coupling rows: backward is C^T (oracle), and differentiating the
+    backward again gives C w (the rows are linear)."""
+    import torch
+    from paper_2203_10587_gb300 import autograd
+    g = synth.make_grid(73, 120, 160, 30)
+    parent = synth.coupling_parents("forest", 40, seed=6, roots=4)
+    rng = np.random.default_rng(73)
+    x = torch.as_tensor(rng.normal(size=(40, g.n)), device="cuda").requires_grad_(True)
+    v = torch.as_tensor(rng.normal(size=(40, g.ng)), device="cuda")
+    net = ex.Net(g)
+    cpl = ex.Coupling(net, parent)
+    r = autograd.coupling(x, cpl)
+    (gx,) = torch.autograd.grad(r, x, v, create_graph=True)
+    np.testing.assert_array_equal(r.detach().cpu().numpy(),
+                                  oracle_mod.coupling(parent, x.detach().cpu().numpy(), g.nb, g.ng))
+    assert_close(gx.detach().cpu().numpy(), oracle_mod.coupling_jtv(parent, v.cpu().numpy(), g.n, g.nb),
+                 "autograd C^T v")
+    w = torch.as_tensor(rng.normal(size=(40, g.n)), device="cuda")
+    vv = v.clone().requires_grad_(True)
+    (gx2,) = torch.autograd.grad(autograd.coupling(x, cpl), x, vv, create_graph=True)
+    (gv,) = torch.autograd.grad(gx2, vv, w)
+    np.testing.assert_array_equal(gv.cpu().numpy(), oracle_mod.coupling(parent, w.cpu().numpy(), g.nb, g.ng))
+    cpl.close()
+    net.close()
