@@ -54,7 +54,7 @@ def bind_library(path: str):
     """Load one compiled oracle library (the default one, or a test's mutated copy)."""
     lib = ctypes.CDLL(path)
     vp = ctypes.c_void_p
-    lib.oracle_eval.argtypes = [ctypes.POINTER(_Net), vp, vp, vp, vp, ctypes.c_double,
+    lib.oracle_eval.argtypes = [ctypes.POINTER(_Net), vp, vp, vp, vp, vp, ctypes.c_double,
                                 ctypes.c_double, vp, vp, vp, ctypes.POINTER(_Coo),
                                 ctypes.POINTER(_Coo)]
     lib.oracle_eval.restype = ctypes.c_int
@@ -134,10 +134,11 @@ def _csr(lib, coo: _Coo, nrows: int):
 
 def evaluate(net: OracleNet, x, lam, mask=None, pd_scale=None, obj_weight: float = 1.0,
              sigma: float = 1.0, want_jac: bool = True, want_hess: bool = True,
-             lib=None, cartesian: bool = False) -> dict:
+             lib=None, cartesian: bool = False, gen_mask=None) -> dict:
     """One evaluation.  Returns f, grad[n], gh[m], and J / H as (rowptr, col, val) CSR.
     cartesian=True evaluates the power-balance-cartesian formulation (oracle_eval_cart): x holds
-    [e | f | Pg | Qg] and lam, gh have m + nb entries (the voltage rows last)."""
+    [e | f | Pg | Qg] and lam, gh have m + nb entries (the voltage rows last).  gen_mask [ng]
+    (1 in service, 0 out) takes generators out of service; None = all in service."""
     lib = lib or _load()
     x = np.ascontiguousarray(x, dtype=np.float64)
     lam = np.ascontiguousarray(lam, dtype=np.float64)
@@ -145,6 +146,7 @@ def evaluate(net: OracleNet, x, lam, mask=None, pd_scale=None, obj_weight: float
     if x.shape != (net.n,) or lam.shape != (m,):
         raise ValueError("x / lam shape")
     mask = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    gen_mask = None if gen_mask is None else np.ascontiguousarray(gen_mask, dtype=np.uint8)
     pd_scale = None if pd_scale is None else np.ascontiguousarray(pd_scale, dtype=np.float64)
     capJ = ctypes.c_int64()
     capH = ctypes.c_int64()
@@ -164,10 +166,10 @@ def evaluate(net: OracleNet, x, lam, mask=None, pd_scale=None, obj_weight: float
     fval = np.zeros(1)
     grad = np.zeros(net.n)
     gh = np.zeros(m)
-    rc = (lib.oracle_eval_cart if cartesian else lib.oracle_eval)(ctypes.byref(net.c), _p(x), _p(lam), _p(mask), _p(pd_scale),
-                         float(obj_weight), float(sigma), _p(fval), _p(grad), _p(gh),
-                         ctypes.byref(J) if J is not None else None,
-                         ctypes.byref(H) if H is not None else None)
+    rc = (lib.oracle_eval_cart if cartesian else lib.oracle_eval)(
+        ctypes.byref(net.c), _p(x), _p(lam), _p(mask), _p(gen_mask), _p(pd_scale),
+        float(obj_weight), float(sigma), _p(fval), _p(grad), _p(gh),
+        ctypes.byref(J) if J is not None else None, ctypes.byref(H) if H is not None else None)
     if rc != 0:
         raise ValueError(f"oracle_eval failed ({rc})")
     out = {"f": float(fval[0]), "grad": grad, "gh": gh}
@@ -186,7 +188,8 @@ def evaluate_batch(net: OracleNet, batch, **kw) -> list[dict]:
                             None if batch.mask is None else batch.mask[b],
                             None if batch.pd_scale is None else batch.pd_scale[b],
                             1.0 if batch.obj_weight is None else float(batch.obj_weight[b]),
-                            batch.sigma, **kw))
+                            batch.sigma,
+                            gen_mask=None if batch.gen_mask is None else batch.gen_mask[b], **kw))
     return res
 
 

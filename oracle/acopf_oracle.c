@@ -195,10 +195,13 @@ static int end_rows(int nb, int u, int hrow, double m, double lamPu, double lamQ
 
 /* Generators, shared by both formulations: injection -Pg, -Qg at their bus, cost in MW
  * (f = w sum c2 MW^2 + c1 MW + c0, MW = baseMVA Pg), its gradient and Hessian (sigma-weighted),
- * and the -1 Jacobian entries.  Returns 0, -1 on a bad bus index, -2 when a triplet array is full. */
-static int gen_terms(const oracle_net *net, const double *Pg, const double *Qg, double w,
-                     double sigma, double *gP, double *gQ, double *fval, double *grad,
-                     oracle_coo *J, oracle_coo *H)
+ * and the -1 Jacobian entries.  A generator out of service (gmask[k] = 0; a contingency may be a
+ * generator outage, Sec. V-A) contributes nothing: no injection, no cost, and zero gradient,
+ * Jacobian and Hessian entries (the pattern keeps them).  gmask NULL = all in service.
+ * Returns 0, -1 on a bad bus index, -2 when a triplet array is full. */
+static int gen_terms(const oracle_net *net, const double *Pg, const double *Qg,
+                     const uint8_t *gmask, double w, double sigma, double *gP, double *gQ,
+                     double *fval, double *grad, oracle_coo *J, oracle_coo *H)
 {
     const int nb = net->nb, ng = net->ng;
     const double base = net->baseMVA;
@@ -206,18 +209,22 @@ static int gen_terms(const oracle_net *net, const double *Pg, const double *Qg, 
     *fval = 0.0;
     for (k = 0; k < ng; k++) {
         int gb = net->gbus[k];
+        int on = gmask == NULL || gmask[k] != 0;
         double MW = base * Pg[k];
         if (gb < 0 || gb >= nb) return -1;
-        gP[gb] -= Pg[k];
-        gQ[gb] -= Qg[k];
-        *fval += w * (net->c2[k] * MW * MW + net->c1[k] * MW + net->c0[k]);
-        grad[2 * nb + k] = w * (2.0 * net->c2[k] * base * base * Pg[k] + net->c1[k] * base);
+        if (on) {
+            gP[gb] -= Pg[k];
+            gQ[gb] -= Qg[k];
+            *fval += w * (net->c2[k] * MW * MW + net->c1[k] * MW + net->c0[k]);
+            grad[2 * nb + k] = w * (2.0 * net->c2[k] * base * base * Pg[k] + net->c1[k] * base);
+        }
         if (J) {
-            if (push(J, gb, 2 * nb + k, -1.0)) return -2;
-            if (push(J, nb + gb, 2 * nb + ng + k, -1.0)) return -2;
+            if (push(J, gb, 2 * nb + k, on ? -1.0 : 0.0)) return -2;
+            if (push(J, nb + gb, 2 * nb + ng + k, on ? -1.0 : 0.0)) return -2;
         }
         if (H) {
-            if (push(H, 2 * nb + k, 2 * nb + k, sigma * w * 2.0 * net->c2[k] * base * base)) return -2;
+            double hk = on ? sigma * w * 2.0 * net->c2[k] * base * base : 0.0;
+            if (push(H, 2 * nb + k, 2 * nb + k, hk)) return -2;
         }
     }
     return 0;
@@ -232,13 +239,14 @@ void oracle_coo_capacity(const oracle_net *net, int64_t *capJ, int64_t *capH)
 
 /*
  * One evaluation (Sec. III, eqs. (7)-(10); objective weight pi_s of eq. (27)).
- *   x[n], lam[m]; mask[nl] (1 in service, 0 out; NULL = all in service);
+ *   x[n], lam[m]; mask[nl] (1 in service, 0 out; NULL = all in service); gmask[ng] the same for
+ *   generators;
  *   pd_scale[nb] (NULL = 1); w = objective weight; sigma = objective factor in the Hessian.
  * Outputs: *fval, grad[n], gh[m]; J and H triplets appended to *J, *H (either may be NULL).
  * Returns 0, -1 on a bad branch (r = x = 0) or bus index, -2 when a triplet array is full.
  */
 int oracle_eval(const oracle_net *net, const double *x, const double *lam, const uint8_t *mask,
-                const double *pd_scale, double w, double sigma,
+                const uint8_t *gmask, const double *pd_scale, double w, double sigma,
                 double *fval, double *grad, double *gh, oracle_coo *J, oracle_coo *H)
 {
     const int nb = net->nb, nl = net->nl, ng = net->ng;
@@ -298,7 +306,7 @@ int oracle_eval(const oracle_net *net, const double *x, const double *lam, const
     }
 
     /* generators: injection -Pg, -Qg at their bus; cost in MW */
-    return gen_terms(net, Pg, Qg, w, sigma, gP, gQ, fval, grad, J, H);
+    return gen_terms(net, Pg, Qg, gmask, w, sigma, gP, gQ, fval, grad, J, H);
 }
 
 /* ---- sum duplicate triplets into CSR with ascending columns ---- */
@@ -444,7 +452,8 @@ void oracle_coo_capacity_cart(const oracle_net *net, int64_t *capJ, int64_t *cap
  * block (e_i, e_i), (f_i, e_i), (f_i, f_i); per generator as in the polar model.
  */
 int oracle_eval_cart(const oracle_net *net, const double *x, const double *lam,
-                     const uint8_t *mask, const double *pd_scale, double w, double sigma,
+                     const uint8_t *mask, const uint8_t *gmask, const double *pd_scale, double w,
+                     double sigma,
                      double *fval, double *grad, double *gh, oracle_coo *J, oracle_coo *H)
 {
     const int nb = net->nb, nl = net->nl, ng = net->ng;
@@ -511,5 +520,5 @@ int oracle_eval_cart(const oracle_net *net, const double *x, const double *lam,
     }
 
     /* generators, exactly as in the polar model */
-    return gen_terms(net, Pg, Qg, w, sigma, gP, gQ, fval, grad, J, H);
+    return gen_terms(net, Pg, Qg, gmask, w, sigma, gP, gQ, fval, grad, J, H);
 }

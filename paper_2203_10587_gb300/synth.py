@@ -217,6 +217,7 @@ class Batch:
     pd_scale: np.ndarray | None = None  # [B][nb] float64
     obj_weight: np.ndarray | None = None  # [B] float64
     sigma: float = 1.0
+    gen_mask: np.ndarray | None = None  # [B][ng] uint8, 1 = in service
     meta: dict = field(default_factory=dict)
 
     @property
@@ -225,8 +226,9 @@ class Batch:
 
 
 def random_batch(seed: int, g: Grid, B: int, *, masks: bool = False, pd_scale: bool = False,
-                 obj_weight: bool = False, sigma: float = 1.0) -> Batch:
-    """B independent states; optional random 0/1 masks, load scales and objective weights."""
+                 obj_weight: bool = False, sigma: float = 1.0, gen_masks: bool = False) -> Batch:
+    """B independent states; optional random 0/1 branch masks, load scales, objective weights and
+    0/1 generator masks (about 20% of generators out of service)."""
     rng = _rng(seed)
     xs, ls = zip(*(base_state(rng, g) for _ in range(B))) if B else ((), ())
     x = np.array(xs, dtype=np.float64).reshape(B, g.n)
@@ -234,7 +236,8 @@ def random_batch(seed: int, g: Grid, B: int, *, masks: bool = False, pd_scale: b
     mask = (rng.random((B, g.nl)) > 0.2).astype(np.uint8) if masks else None
     ps = np.exp(0.1 * rng.normal(size=(B, g.nb))) if pd_scale else None
     w = rng.uniform(0.1, 1.0, B) if obj_weight else None
-    return Batch(x=x, lam=lam, mask=mask, pd_scale=ps, obj_weight=w, sigma=sigma)
+    gm = (rng.random((B, g.ng)) > 0.2).astype(np.uint8) if gen_masks else None
+    return Batch(x=x, lam=lam, mask=mask, pd_scale=ps, obj_weight=w, sigma=sigma, gen_mask=gm)
 
 
 def contingency_batch(seed: int, g: Grid, B: int, sigma_state: float = 0.02) -> Batch:
@@ -305,3 +308,20 @@ def coupling_parents(kind: str, B: int, seed: int = 0, roots: int = 1):
             p[order[j]] = order[rng.integers(0, j)]
         return p
     raise ValueError(kind)
+
+
+def generator_contingency_batch(seed: int, g: Grid, B: int, sigma_state: float = 0.02) -> Batch:
+    """Security batch of generator outages (Sec. V-A: a contingency may be a generator outage, or
+    a generator and a line together): state c takes generator c mod ng out of service, and every
+    third state also one non-bridge branch; states around one base state as contingency_batch."""
+    rng = _rng(seed)
+    x0, l0 = base_state(rng, g)
+    cand = np.flatnonzero(~bridges(g.nb, g.f, g.t))
+    gm = np.ones((B, g.ng), dtype=np.uint8)
+    gm[np.arange(B), np.arange(B) % g.ng] = 0
+    mask = np.ones((B, g.nl), dtype=np.uint8)
+    both = np.arange(0, B, 3)
+    mask[both, rng.choice(cand, size=both.shape[0])] = 0
+    x = x0[None, :] + rng.normal(0.0, sigma_state, (B, g.n))
+    lam = l0[None, :] + rng.normal(0.0, sigma_state, (B, g.m))
+    return Batch(x=x, lam=lam, mask=mask, gen_mask=gm)

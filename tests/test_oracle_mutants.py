@@ -12,6 +12,7 @@ import pytest
 from oracle import acopf
 import test_oracle as T
 import test_oracle_cartesian as TK
+import test_oracle_genmask as TG
 import test_oracle_coupling as TC
 
 SRC = os.path.join(os.path.dirname(acopf.__file__), "acopf_oracle.c")
@@ -54,6 +55,10 @@ MUTANTS = {
     "cart_shunt_f": ("if (push(J, nb + i, nb + i, -2.0 * net->Bs[i] * F[i])) return -2;",
                      "if (push(J, nb + i, nb + i, -2.0 * net->Bs[i] * E[i])) return -2;"),
     "cart_to_side": ("gidx[1][2] = fb; gidx[1][3] = nb + fb;", "gidx[1][2] = nb + fb; gidx[1][3] = fb;"),
+    "gen_mask_ignored": ("int on = gmask == NULL || gmask[k] != 0;", "int on = 1;"),
+    "gen_mask_jac_kept": ("if (push(J, gb, 2 * nb + k, on ? -1.0 : 0.0)) return -2;",
+                          "if (push(J, gb, 2 * nb + k, -1.0)) return -2;"),
+    "gen_mask_hess_kept": ("double hk = on ? sigma", "double hk = 1 ? sigma"),
     "coupling_sign": ("x[(int64_t)b * n + 2 * nb + k] - x[(int64_t)p * n + 2 * nb + k]",
                       "x[(int64_t)b * n + 2 * nb + k] + x[(int64_t)p * n + 2 * nb + k]"),
     "coupling_parent_stride": ("- x[(int64_t)p * n + 2 * nb + k]", "- x[(int64_t)p * ng + 2 * nb + k]"),
@@ -97,6 +102,8 @@ PINS = [
     ("cart_polar", lambda om: TK.test_change_of_variables_to_polar(om, 53)),
     ("cart_fd", lambda om: TK.test_finite_differences(om)),
     ("cart_homogeneity", lambda om: TK.test_homogeneity_and_rotation(om)),
+    ("gen_out_polar", lambda om: TG.test_generator_out_equals_generator_removed(om, False)),
+    ("gen_out_hand", lambda om: TG.test_two_bus_generator_outage_by_hand(om)),
     ("coupling_hand", lambda om: TC.test_hand_rows(om)),
     ("coupling_hand_transpose", lambda om: TC.test_hand_transpose(om)),
     ("coupling_telescopes", lambda om: TC.test_chain_telescopes(om)),
