@@ -139,6 +139,12 @@ exago_status exago_net_plan_array(exago_net_t net, const char *name, void *dst, 
  *                        256-byte aligned; NULL = use the net's internal workspace, grown on
  *                        demand (a growth calls cudaMalloc; use exago_net_reserve before any
  *                        stream capture)
+ *   gen_mask   [B][ng]   1 in service, 0 out of service (a generator outage, alone or with line
+ *                        outages: SCOPFLOW contingencies, Sec. V-A); NULL = all 1.  An
+ *                        out-of-service generator contributes nothing: no injection in its bus's
+ *                        balances, no cost, and zero gradient, Jacobian (-1 entries) and cost
+ *                        Hessian values; the sparsity pattern is unchanged.  Last in the struct,
+ *                        so a caller that zero-initialises the batch gets NULL.
  */
 typedef struct {
     int B;
@@ -151,6 +157,7 @@ typedef struct {
     void *stream;
     void *workspace;
     size_t workspace_bytes;
+    const uint8_t *gen_mask;
 } exago_batch;
 
 /* Scratch bytes one evaluation of B states needs under the net's configuration (branch-end

@@ -112,6 +112,8 @@ __device__ __forceinline__ void adj_bus_item(const DevNet &N, const AdjReq &A, i
     const double *xb = A.x + (size_t)b * N.n;
     const double Vm = __ldg(xb + nb + i);
     const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
+    // generators out of service contribute nothing
+    const uint8_t *gm = A.gen_mask && g1 > g0 ? A.gen_mask + (size_t)b * ng : nullptr;
     if (MODE == ADJ_JVP) {
         const double *ub = A.v + (size_t)b * N.n;
         const double tu = twice(Vm) * __ldg(ub + nb + i);
@@ -119,6 +121,7 @@ __device__ __forceinline__ void adj_bus_item(const DevNet &N, const AdjReq &A, i
         s1v = fma(-Bs, tu, s1v);
         for (int s = g0; s < g1; s++) {
             const int k = __ldg(N.gen_ord + s);
+            if (gm && !gm[k]) continue;
             s0v -= __ldg(ub + 2 * nb + k);
             s1v -= __ldg(ub + 2 * nb + ng + k);
         }
@@ -135,8 +138,9 @@ __device__ __forceinline__ void adj_bus_item(const DevNet &N, const AdjReq &A, i
         ob[nb + i] = s1v;
         for (int s = g0; s < g1; s++) {
             const int k = __ldg(N.gen_ord + s);
-            ob[2 * nb + k] = dneg(vP);
-            ob[2 * nb + ng + k] = dneg(vQ);
+            const bool on = !gm || gm[k];
+            ob[2 * nb + k] = on ? dneg(vP) : 0.0;
+            ob[2 * nb + ng + k] = on ? dneg(vQ) : 0.0;
         }
     } else {
         const double *lb = A.lam + (size_t)b * N.m;
@@ -151,7 +155,7 @@ __device__ __forceinline__ void adj_bus_item(const DevNet &N, const AdjReq &A, i
             const double sw = A.sigma * (A.obj_weight ? A.obj_weight[b] : 1.0);
             for (int s = g0; s < g1; s++) {
                 const int k = __ldg(N.gen_ord + s);
-                const double h = sw * __ldg(N.c2g + k);
+                const double h = !gm || gm[k] ? sw * __ldg(N.c2g + k) : 0.0;
                 ob[2 * nb + k] = h * __ldg(ub + 2 * nb + k);
                 ob[2 * nb + ng + k] = 0.0;
             }

@@ -468,7 +468,7 @@ exago_status launch_graph_locked(exago_net *net, const std::vector<uint64_t> &ke
 }
 
 std::vector<uint64_t> req_key(const EvalReq &R, int schedule) {
-    return {(uint64_t)schedule, (uint64_t)R.x, (uint64_t)R.lam, (uint64_t)R.mask,
+    return {(uint64_t)schedule, (uint64_t)R.x, (uint64_t)R.lam, (uint64_t)R.mask, (uint64_t)R.gen_mask,
             (uint64_t)R.pd_scale, (uint64_t)R.obj_weight, (uint64_t)R.f, (uint64_t)R.grad,
             (uint64_t)R.gh, (uint64_t)R.jval, (uint64_t)R.hval, (uint64_t)R.scratch,
             (uint64_t)R.B, bits(R.sigma), (uint64_t)R.stage_recs, (uint64_t)R.stage_cap};
@@ -509,7 +509,7 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
     }
     EvalReq R{};
     R.B = bt->B;
-    R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask;
+    R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask; R.gen_mask = bt->gen_mask;
     R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
     R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
     R.stage_recs = rs.stage_recs;
@@ -816,7 +816,8 @@ exago_status adjoint(exago_net *net, const exago_batch *bt, const double *v, dou
     }
     AdjReq A{};
     A.B = bt->B;
-    A.x = bt->x; A.lam = bt->lambda; A.mask = bt->mask; A.obj_weight = bt->obj_weight;
+    A.x = bt->x; A.lam = bt->lambda; A.mask = bt->mask; A.gen_mask = bt->gen_mask;
+    A.obj_weight = bt->obj_weight;
     A.sigma = bt->obj_factor;
     A.v = v; A.out = out;
     A.scratch = (double *)ws;

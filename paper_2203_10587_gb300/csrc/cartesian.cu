@@ -47,7 +47,7 @@ struct CartReq {
     int mc;                     // rows of g | h: m + nb
     int64_t nnzJc;              // Jacobian entries per state: nnzJ + 2 nb
     const double *x, *lam;
-    const uint8_t *mask;
+    const uint8_t *mask, *gen_mask;
     const double *pd_scale, *obj_weight;
     double sigma;
     double *f, *grad, *gh, *jval, *hval;
@@ -313,6 +313,8 @@ __device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R,
     const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
     const double V2 = fma(ei, ei, fi * fi);
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
+    // generators out of service inject nothing and have zero entries
+    const uint8_t *gm = R.gen_mask && g1 > g0 ? R.gen_mask + (size_t)b * ng : nullptr;
     if (R.gh) {
         double Pd = __ldg(N.Pd + i), Qd = __ldg(N.Qd + i);
         if (R.pd_scale) {
@@ -324,6 +326,7 @@ __device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R,
         double gQ = fma(-Bs, V2, Q) + Qd;
         for (int q = g0; q < g1; q++) {
             const int g = __ldg(N.gen_ord + q);
+            if (!gen_on(gm, g)) continue;
             gP -= __ldg(xb + 2 * nb + g);
             gQ -= __ldg(xb + 2 * nb + ng + g);
         }
@@ -339,8 +342,9 @@ __device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R,
         JQ[nlow] = fma(-tB, ei, qe);
         JQ[k + nlow] = fma(-tB, fi, qf);
         for (int q = 0; q < g1 - g0; q++) {
-            JP[2 * k + q] = -1.0;
-            JQ[2 * k + q] = -1.0;
+            const double v = gen_on(gm, gm ? __ldg(N.gen_ord + g0 + q) : 0) ? -1.0 : 0.0;
+            JP[2 * k + q] = v;
+            JQ[2 * k + q] = v;
         }
         double *Jv = Jb + N.nnzJ + 2 * (size_t)i;              // voltage row: 2 e_i, 2 f_i
         Jv[0] = twice(ei);
@@ -358,7 +362,7 @@ __device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R,
             const double sw = R.sigma * (R.obj_weight ? __ldg(R.obj_weight + b) : 1.0);
             for (int q = g0; q < g1; q++) {
                 const int g = __ldg(N.gen_ord + q);
-                Hb[N.hpg + g] = sw * __ldg(N.c2g + g);
+                Hb[N.hpg + g] = gen_on(gm, g) ? sw * __ldg(N.c2g + g) : 0.0;
             }
         }
     }
@@ -369,7 +373,9 @@ __device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R,
         const double w = R.obj_weight ? __ldg(R.obj_weight + b) : 1.0;
         for (int q = g0; q < g1; q++) {
             const int g = __ldg(N.gen_ord + q);
-            gb[2 * nb + g] = w * fma(__ldg(N.c2g + g), __ldg(xb + 2 * nb + g), __ldg(N.c1g + g));
+            gb[2 * nb + g] = gen_on(gm, g) ? w * fma(__ldg(N.c2g + g), __ldg(xb + 2 * nb + g),
+                                                     __ldg(N.c1g + g))
+                                           : 0.0;
             gb[2 * nb + ng + g] = 0.0;
         }
     }
@@ -387,7 +393,7 @@ __global__ void __launch_bounds__(128) k_cart_bus(const DevNet N, const CartReq 
 // Objective of each state (the polar model's: it depends on Pg only).
 __global__ void __launch_bounds__(OBJ_LANES) k_cart_obj(const DevNet N, const EvalReq R, int b0) {
     __shared__ double part[OBJ_LANES];
-    obj_block(N, R, b0 + blockIdx.x, part);
+    obj_block<true>(N, R, b0 + blockIdx.x, part);
 }
 
 // ---- adjoint products of the cartesian constraint map c = [g; h] ----
@@ -400,7 +406,7 @@ enum CartAdjMode : int { CADJ_JVP = 0, CADJ_JTV = 1, CADJ_HVP = 2 };
 struct CartAdjReq {
     int b0, mc;
     const double *x, *lam;
-    const uint8_t *mask;
+    const uint8_t *mask, *gen_mask;
     const double *obj_weight;
     double sigma;
     const double *v;            // JVP / HVP: [B][n]; JTV: [B][m_c]
@@ -486,12 +492,14 @@ __global__ void __launch_bounds__(128) k_cart_adj_bus(const DevNet N, const Cart
     const double *xb = A.x + (size_t)b * N.n;
     const double ei = __ldg(xb + i), fi = __ldg(xb + nb + i);
     const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
+    const uint8_t *gm = A.gen_mask && g1 > g0 ? A.gen_mask + (size_t)b * ng : nullptr;
     if (MODE == CADJ_JVP) {
         const double *ub = A.v + (size_t)b * N.n;
         const double dV = twice(fma(ei, __ldg(ub + i), fi * __ldg(ub + nb + i)));   // d(e^2 + f^2)
         double oP = fma(Gs, dV, s0v), oQ = fma(-Bs, dV, s1v);
         for (int q = g0; q < g1; q++) {
             const int g = __ldg(N.gen_ord + q);
+            if (!gen_on(gm, g)) continue;
             oP -= __ldg(ub + 2 * nb + g);
             oQ -= __ldg(ub + 2 * nb + ng + g);
         }
@@ -508,8 +516,8 @@ __global__ void __launch_bounds__(128) k_cart_adj_bus(const DevNet N, const Cart
         ob[nb + i] = fma(coef, fi, s1v);
         for (int q = g0; q < g1; q++) {
             const int g = __ldg(N.gen_ord + q);
-            ob[2 * nb + g] = dneg(vP);
-            ob[2 * nb + ng + g] = dneg(vQ);
+            ob[2 * nb + g] = gen_on(gm, g) ? dneg(vP) : 0.0;
+            ob[2 * nb + ng + g] = gen_on(gm, g) ? dneg(vQ) : 0.0;
         }
     } else {
         const double *lb = A.lam + (size_t)b * A.mc;
@@ -522,7 +530,7 @@ __global__ void __launch_bounds__(128) k_cart_adj_bus(const DevNet N, const Cart
         const double sw = A.sigma * (A.obj_weight ? __ldg(A.obj_weight + b) : 1.0);
         for (int q = g0; q < g1; q++) {
             const int g = __ldg(N.gen_ord + q);
-            ob[2 * nb + g] = sw * __ldg(N.c2g + g) * __ldg(ub + 2 * nb + g);
+            ob[2 * nb + g] = gen_on(gm, g) ? sw * __ldg(N.c2g + g) * __ldg(ub + 2 * nb + g) : 0.0;
             ob[2 * nb + ng + g] = 0.0;
         }
     }
@@ -588,7 +596,7 @@ exago_status cart_adjoint(exago_net_t net, const exago_batch *bt, const double *
     }
     CartAdjReq A{};
     A.mc = N.m + N.nb;
-    A.x = bt->x; A.lam = bt->lambda; A.mask = bt->mask;
+    A.x = bt->x; A.lam = bt->lambda; A.mask = bt->mask; A.gen_mask = bt->gen_mask;
     A.obj_weight = bt->obj_weight; A.sigma = bt->obj_factor;
     A.v = in; A.out = out;
     A.scratch = (double *)ws;
@@ -700,7 +708,7 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
         R.B = bt->B;
         R.mc = N.m + N.nb;
         R.nnzJc = N.nnzJ + 2 * (int64_t)N.nb;
-        R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask;
+        R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask; R.gen_mask = bt->gen_mask;
         R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
         R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
         R.scratch = (double *)ws;
@@ -718,7 +726,7 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
     if (f) {
         EvalReq E{};
         E.B = bt->B;
-        E.x = bt->x; E.obj_weight = bt->obj_weight; E.f = f;
+        E.x = bt->x; E.obj_weight = bt->obj_weight; E.f = f; E.gen_mask = bt->gen_mask;
         for (int b0 = 0; b0 < bt->B; b0 += 65535)
             k_cart_obj<<<std::min(65535, bt->B - b0), OBJ_LANES, 0, st>>>(N, E, b0);
     }

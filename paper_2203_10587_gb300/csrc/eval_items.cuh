@@ -9,7 +9,9 @@
 
 namespace exago {
 
-enum : int { W_G = 1, W_J = 2, W_H = 4 };
+// What an item computes: g | h values, Jacobian values, Hessian values; W_GM compiles in the
+// per-state generator mask (st_gmask), which a launch without one leaves out.
+enum : int { W_G = 1, W_J = 2, W_H = 4, W_GM = 8 };
 
 // Where state b's inputs and outputs live: row b of the batch arrays, or entry b of a gathered
 // batch's state table.
@@ -22,6 +24,11 @@ __device__ __forceinline__ const double *st_lam(const DevNet &N, const EvalReq &
 __device__ __forceinline__ const uint8_t *st_mask(const DevNet &N, const EvalReq &R, int b) {
     return R.tab ? R.tab[b].mask : R.mask ? R.mask + (size_t)b * N.nl : nullptr;
 }
+__device__ __forceinline__ const uint8_t *st_gmask(const DevNet &N, const EvalReq &R, int b) {
+    return R.tab ? R.tab[b].gen_mask : R.gen_mask ? R.gen_mask + (size_t)b * N.ng : nullptr;
+}
+// Whether generator k of state b is in service (gm: st_gmask of the state).
+__device__ __forceinline__ bool gen_on(const uint8_t *gm, int k) { return gm == nullptr || gm[k] != 0; }
 __device__ __forceinline__ const double *st_pd(const DevNet &N, const EvalReq &R, int b) {
     return R.tab ? R.tab[b].pd_scale : R.pd_scale ? R.pd_scale + (size_t)b * N.nb : nullptr;
 }
@@ -316,7 +323,11 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
 
 // Gradient entry of generator k's active power: w (2 c2 base^2 Pg + c1 base), with the network
 // constants c2g = 2 c2 base^2 and c1g = c1 base.
+template <bool GM>
 __device__ __forceinline__ double grad_pg(const DevNet &N, const EvalReq &R, int b, int k) {
+    if constexpr (GM) {
+        if (!gen_on(st_gmask(N, R, b), k)) return 0.0;    // generator out of service
+    }
     const double w = st_w(R, b);
     const double Pg = __ldg(st_x(N, R, b) + 2 * N.nb + k);
     return w * fma(__ldg(N.c2g + k), Pg, __ldg(N.c1g + k));
@@ -383,10 +394,11 @@ __device__ __forceinline__ void add_group(Rec &o, const Rec &r) {
 //   J:  the diagonal entries of rows P_i and Q_i (plus the shunt term) and -1 for each generator;
 //   H:  the diagonals of rows Va_i and Vm_i (plus the shunt term) and the cost Hessian of the
 //       bus's generators.
+// A generator out of service (st_gmask) injects nothing and its -1 and cost Hessian entries are 0.
 template <int WANT>
 __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int b, int i,
                                          const Rec &D, const BusRows &W) {
-    constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
+    constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H, GM = WANT & W_GM;
     const int nb = N.nb;
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
     const double *xb = st_x(N, R, b);
@@ -399,6 +411,8 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
     // dP_i/dVm_i and dQ_i/dVm_i, with the shunt terms
     const double tV = twice(Vm);
     const double JPu = fma(Gs, tV, dPu), JQu = fma(-Bs, tV, dQu);
+    [[maybe_unused]] const uint8_t *gm = nullptr;
+    if constexpr (GM) gm = g1 > g0 ? st_gmask(N, R, b) : nullptr;
 
     if (WG && R.gh) {
         double Pd = __ldg(N.Pd + i), Qd = __ldg(N.Qd + i);
@@ -412,6 +426,9 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
         double gQ = fma(0.5, fma(Vm, JQu, -dPa), Qd);
         for (int q = g0; q < g1; q++) {
             const int g = __ldg(N.gen_ord + q);
+            if constexpr (GM) {
+                if (!gen_on(gm, g)) continue;
+            }
             gP -= __ldg(xb + 2 * nb + g);
             gQ -= __ldg(xb + 2 * nb + N.ng + g);
         }
@@ -423,8 +440,14 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
         JP[nlow] = dPa; JP[k + nlow] = JPu;
         JQ[nlow] = dQa; JQ[k + nlow] = JQu;
         for (int q = 0; q < g1 - g0; q++) {
-            JP[2 * k + q] = -1.0;
-            JQ[2 * k + q] = -1.0;
+            if constexpr (GM) {
+                const double v = gen_on(gm, gm ? __ldg(N.gen_ord + g0 + q) : 0) ? -1.0 : 0.0;
+                JP[2 * k + q] = v;
+                JQ[2 * k + q] = v;
+            } else {
+                JP[2 * k + q] = -1.0;
+                JQ[2 * k + q] = -1.0;
+            }
         }
     }
     if (WH) {
@@ -438,7 +461,8 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
             double *Hb = st_hval(N, R, b) + N.hpg;
             for (int q = g0; q < g1; q++) {
                 const int g = __ldg(N.gen_ord + q);
-                Hb[g] = sw * __ldg(N.c2g + g);
+                if constexpr (GM) Hb[g] = gen_on(gm, g) ? sw * __ldg(N.c2g + g) : 0.0;
+                else Hb[g] = sw * __ldg(N.c2g + g);
             }
         }
     }
@@ -657,6 +681,7 @@ __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int 
 }
 
 // Gradient entries owned by bus i: Va_i and Vm_i (zero) and, for each generator at i, Pg and Qg.
+template <bool GM>
 __device__ __forceinline__ void grad_bus(const DevNet &N, const EvalReq &R, int b, int i) {
     double *gb = st_grad(N, R, b);
     gb[i] = 0.0;
@@ -664,7 +689,7 @@ __device__ __forceinline__ void grad_bus(const DevNet &N, const EvalReq &R, int 
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
     for (int s = g0; s < g1; s++) {
         const int k = __ldg(N.gen_ord + s);
-        gb[2 * N.nb + k] = grad_pg(N, R, b, k);
+        gb[2 * N.nb + k] = grad_pg<GM>(N, R, b, k);
         gb[2 * N.nb + N.ng + k] = 0.0;
     }
 }
@@ -674,11 +699,17 @@ __device__ __forceinline__ void grad_bus(const DevNet &N, const EvalReq &R, int 
 // a fixed pairwise tree.  The result is the same for every block size.  part: 256 doubles of
 // shared memory.
 constexpr int OBJ_LANES = 256;
+template <bool GM>
 __device__ __forceinline__ void obj_block(const DevNet &N, const EvalReq &R, int b, double *part) {
     const double *Pg = st_x(N, R, b) + 2 * N.nb;
+    [[maybe_unused]] const uint8_t *gm = nullptr;
+    if constexpr (GM) gm = st_gmask(N, R, b);
     for (int v = threadIdx.x; v < OBJ_LANES; v += blockDim.x) {
         double acc = 0.0;
         for (int k = v; k < N.ng; k += OBJ_LANES) {
+            if constexpr (GM) {
+                if (!gen_on(gm, k)) continue;                 // generator out of service
+            }
             const double MW = N.baseMVA * __ldg(Pg + k);
             acc += fma(fma(__ldg(N.c2 + k), MW, __ldg(N.c1 + k)), MW, __ldg(N.c0 + k));
         }

@@ -99,14 +99,14 @@ struct StateTab {
     const double *pd_scale, *obj_weight;   // obj_weight: this state's weight
     double sigma;
     double *f, *grad, *gh, *jval, *hval;   // this state's outputs (f: one value)
+    const uint8_t *gen_mask;               // [ng], or nullptr (all in service)
 };
 
 // What one evaluation call asks for.  With tab, state b's inputs and outputs are tab[b]'s, and the
 // batch pointers below only say which outputs are wanted (non-null) and which inputs exist.
 struct EvalReq {
-    int B;
     const double *x, *lam;
-    const uint8_t *mask;
+    const uint8_t *mask;        // [B][nl]; NULL = all in service
     const double *pd_scale, *obj_weight;
     double sigma;
     double *f, *grad, *gh, *jval, *hval;
@@ -115,8 +115,14 @@ struct EvalReq {
                                 // in the multi-kernel and pipelined schedules
     int stage_recs;             // bus tiles read their records slot-parallel into shared memory
     int stage_cap;              // shared-memory doubles of one bus tile (records and rows)
+    int B;
     const StateTab *tab;        // device table of B states, or nullptr
+    const uint8_t *gen_mask;    // [B][ng] generator status; NULL = all in service
 };
+// The persistent kernel takes this struct by value beside DevNet and its own parameters; its
+// size (128 bytes, no padding) is kept so that adding a field does not shift the kernel's other
+// parameters (which measurably changed the generated code of the persistent kernel).
+static_assert(sizeof(EvalReq) == 128, "EvalReq layout");
 
 // Pipelined schedule (kernels.cu): the batch in chunks; the branch kernel of a chunk runs on the
 // caller's stream while the bus kernel of the previous chunk runs on `side`, ordered by events
@@ -133,7 +139,7 @@ enum AdjMode : int { ADJ_JVP = 0, ADJ_JTV = 1, ADJ_HVP = 2 };
 struct AdjReq {
     int B;
     const double *x, *lam;          // lam: HVP multipliers [B][m]
-    const uint8_t *mask;
+    const uint8_t *mask, *gen_mask;
     const double *obj_weight;
     double sigma;
     const double *v;                // JVP / HVP: [B][n]; JTV: [B][m]

@@ -75,7 +75,8 @@ template <int WANT>
 __global__ void __launch_bounds__(128) k_bus(const DevNet N, const EvalReq R, int b0) {
     extern __shared__ double stage[];
     const int b = b0 + blockIdx.y;
-    bus_tile<WANT, BlockGroup>(N, R, b, blockIdx.x * blockDim.x,
+    // this schedule always honours generator masks (W_GM)
+    bus_tile<WANT | W_GM, BlockGroup>(N, R, b, blockIdx.x * blockDim.x,
                                R.scratch + (size_t)(b - R.scr_b0) * N.nslot * NCOMP, stage, R.stage_cap);
 }
 
@@ -85,12 +86,12 @@ __global__ void k_grad(const DevNet N, const EvalReq R, int b0) {
     if (j >= N.n) return;
     const int b = b0 + blockIdx.y;
     const int k = j - 2 * N.nb;
-    st_grad(N, R, b)[j] = (k >= 0 && k < N.ng) ? grad_pg(N, R, b, k) : 0.0;
+    st_grad(N, R, b)[j] = (k >= 0 && k < N.ng) ? grad_pg<true>(N, R, b, k) : 0.0;
 }
 
 __global__ void __launch_bounds__(OBJ_LANES) k_obj(const DevNet N, const EvalReq R, int b0) {
     __shared__ double part[OBJ_LANES];
-    obj_block(N, R, b0 + blockIdx.x, part);
+    obj_block<true>(N, R, b0 + blockIdx.x, part);
 }
 
 template <int WANT>

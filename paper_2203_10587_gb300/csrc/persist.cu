@@ -4,199 +4,17 @@
 // claim branch and bus tiles of every state from a work list.
 #include <cuda_runtime.h>
 
-#include "eval_items.cuh"
+#include "persist_kernel.cuh"
 
 namespace exago {
 
-// ---------------------------------------------------------------------------------------------
-// Persistent schedule: one launch of numSMs x (resident CTAs per SM) blocks that claim work items
-// from a ticket counter until the list is empty.  A work item is `group` consecutive tiles of
-// one kind and one state (blockDim branches or buses each), so that the items' claims, waits and
-// signals are shared by several tiles.  For each state b there are Tbr branch items and Tbu bus
-// items.  The list is ordered
-//     Br(0) .. Br(L-1), [Br(L) Bu(0)], [Br(L+1) Bu(1)], ..., Bu(B-L) .. Bu(B-1)
-// so that bus tiles trail branch tiles by L states.  The branch partials of state b live in ring
-// slot b mod Rg of the workspace (Rg > L slots, sized to stay in L2), which keeps the
-// branch -> bus hand-off on chip.  Two waits order the work:
-//   * a bus tile of b waits until all Tbr branch tiles of b have signalled;
-//   * a branch tile of b >= Rg waits until all Tbu bus tiles of b - Rg have signalled (ring reuse).
-// Both wait only on items with smaller tickets, which are held by running CTAs and wait only on
-// smaller tickets still; the smallest unfinished ticket never waits, so the launch cannot
-// deadlock.  Every wait is bounded: after spin_limit polls it records a timeout in the status
-// word, skips its work and still signals, so the launch always ends.  Bus tile 0 of each state
-// also writes its objective; every bus tile writes the gradient entries of its buses.
-struct PersistParams {
-    int B, Tbr, Tbu, lag, ring, total, group;
-    int *ctr;               // [1 + 2B]: ticket, branch tiles done per state, bus tiles done
-    long long spin_limit;
-    int force_timeout;      // testing: bus tiles wait for one branch tile more than exists
-};
-
-__device__ __forceinline__ int ld_acquire(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Signals one finished tile: a release add at GPU scope.  Called by thread 0 after a
-// __syncthreads, so it publishes the whole block's writes (release is cumulative).
-__device__ __forceinline__ void red_release_add(int *p) {
-    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(p) : "memory");
-}
-
-// Polls *p until it reaches target; false (and a timeout code in the status word) after
-// spin_limit polls.
-__device__ bool bounded_wait(const int *p, int target, long long limit, int *status, int code) {
-    long long it = 0;
-    while (ld_acquire(p) < target) {
-        if (++it > limit) {
-            if (status) *(volatile int *)status = code;
-            return false;
-        }
-        __nanosleep(100);
-    }
-    return true;
-}
-
-enum : int { ST_TIMEOUT_BUS = 1, ST_TIMEOUT_RING = 2 };
-
-__device__ __forceinline__ void decode_item(const PersistParams &P, int t, bool *is_branch, int *b,
-                                            int *tile) {
-    const int L = P.lag, Tbr = P.Tbr, Tbu = P.Tbu;
-    const int head = L * Tbr;
-    if (t < head) {
-        *is_branch = true; *b = t / Tbr; *tile = t % Tbr;
-        return;
-    }
-    const int u = t - head, grp = Tbr + Tbu, ngroups = P.B - L;
-    if (u < ngroups * grp) {
-        const int g = u / grp, r = u % grp;
-        if (r < Tbr) { *is_branch = true; *b = L + g; *tile = r; }
-        else { *is_branch = false; *b = g; *tile = r - Tbr; }
-        return;
-    }
-    const int v = u - ngroups * grp;
-    *is_branch = false; *b = ngroups + v / Tbu; *tile = v % Tbu;
-}
-
-// MINB: resident CTAs per SM the register allocation must allow (1 = compiler's choice).
-template <int WANT, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const EvalReq R,
-                                                      const PersistParams P) {
-    __shared__ int s_item, s_ok;
-    __shared__ double s_part[OBJ_LANES];
-    extern __shared__ double stage[];
-    int *done_br = P.ctr + 1, *done_bu = P.ctr + 1 + P.B;
-    const size_t slot_doubles = (size_t)NCOMP * N.nslot;
-    const int cap = R.stage_cap;
-    // Thread 0 claims the next ticket while the block works on the current one.  The smallest
-    // unfinished ticket is always some block's current item (a block's prefetched ticket is
-    // larger than its current one), so the argument above still holds.
-    int next = 0;
-    if (threadIdx.x == 0) next = atomicAdd(P.ctr, 1);
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_item = next;
-            if (next < P.total) next = atomicAdd(P.ctr, 1);
-        }
-        __syncthreads();
-        const int t = s_item;
-        if (t >= P.total) return;
-        bool is_branch;
-        int b, tile;
-        decode_item(P, t, &is_branch, &b, &tile);
-        const int slot = b % P.ring;
-        double *scr = R.scratch + (size_t)slot * slot_doubles;
-        if (is_branch) {
-            if (threadIdx.x == 0)
-                s_ok = b < P.ring || bounded_wait(done_bu + (b - P.ring), P.Tbu, P.spin_limit,
-                                                  N.status, ST_TIMEOUT_RING);
-            __syncthreads();
-            if (s_ok)
-                for (int l = tile * P.group * NT + threadIdx.x; l < N.nl && l < (tile + 1) * P.group * NT;
-                     l += NT)
-                    branch_item<WANT>(N, R, b, l, scr);
-            __syncthreads();
-            if (threadIdx.x == 0) red_release_add(done_br + b);
-        } else {
-            if (threadIdx.x == 0)
-                s_ok = bounded_wait(done_br + b, P.Tbr + P.force_timeout, P.spin_limit, N.status,
-                                    ST_TIMEOUT_BUS);
-            __syncthreads();
-            if (s_ok) {
-                for (int k = 0; k < P.group; k++) {
-                    const int i0 = (tile * P.group + k) * NT;
-                    if (i0 >= N.nb) break;
-                    if (WANT) bus_tile<WANT, BlockGroup>(N, R, b, i0, scr, stage, cap);
-                    if (i0 + (int)threadIdx.x < N.nb && R.grad) grad_bus(N, R, b, i0 + threadIdx.x);
-                }
-                if (tile == 0 && R.f) obj_block(N, R, b, s_part);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) red_release_add(done_bu + b);
-        }
-    }
-}
-
-// CTAs per SM for a target of occ_warps resident warps (0: the compiler's register choice).
-constexpr int minb(int nt, int occ_warps) {
-    return occ_warps <= 0 ? 1 : (occ_warps / (nt / 32) > 0 ? occ_warps / (nt / 32) : 1);
-}
-
-template <int WANT, int NT, int MINB>
-static void launch_one(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
-                       size_t smem, cudaStream_t st) {
-    k_persist<WANT, NT, MINB><<<grid, NT, smem, st>>>(N, R, P);
-}
-
-// Opts every persistent variant in to kStageMaxDoubles of dynamic shared memory (above the
-// default 48 KB once the static part is added).  Called once per device, outside any capture.
-template <int NT>
-static int allow_stage_nt() {
-    const int bytes = kStageMaxDoubles * (int)sizeof(double);
-    cudaError_t e = cudaSuccess;
-    auto set = [&](const void *k) {
-        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (r != cudaSuccess) e = r;
-    };
-    constexpr int ALL = W_G | W_J | W_H;
-    set((const void *)k_persist<0, NT, 1>); set((const void *)k_persist<W_G, NT, 1>);
-    set((const void *)k_persist<W_J, NT, 1>); set((const void *)k_persist<W_G | W_J, NT, 1>);
-    set((const void *)k_persist<W_H, NT, 1>); set((const void *)k_persist<W_G | W_H, NT, 1>);
-    set((const void *)k_persist<W_J | W_H, NT, 1>); set((const void *)k_persist<ALL, NT, 1>);
-    set((const void *)k_persist<ALL, NT, minb(NT, 24)>);
-    set((const void *)k_persist<ALL, NT, minb(NT, 16)>);
-    return (int)e;
-}
-
 int persist_allow_stage() {
-    int e = allow_stage_nt<32>();
-    if (e == 0) e = allow_stage_nt<64>();
-    if (e == 0) e = allow_stage_nt<128>();
-    if (e == 0) e = allow_stage_nt<256>();
+    int e = allow_stage_nt<32, 0>();
+    if (e == 0) e = allow_stage_nt<64, 0>();
+    if (e == 0) e = allow_stage_nt<128, 0>();
+    if (e == 0) e = allow_stage_nt<256, 0>();
+    if (e == 0) e = persist_allow_stage_gm();
     return e;
-}
-
-
-template <int NT>
-static int launch_persist_nt(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
-                             int occ_warps, cudaStream_t st) {
-    const int want = (R.gh ? W_G : 0) | (R.jval ? W_J : 0) | (R.hval ? W_H : 0);
-    const size_t smem = (size_t)R.stage_cap * sizeof(double);
-    constexpr int ALL = W_G | W_J | W_H;
-    if (want == ALL && occ_warps == 24) launch_one<ALL, NT, minb(NT, 24)>(N, R, P, grid, smem, st);
-    else if (want == ALL && occ_warps == 16) launch_one<ALL, NT, minb(NT, 16)>(N, R, P, grid, smem, st);
-    else switch (want) {
-        case 0: launch_one<0, NT, 1>(N, R, P, grid, smem, st); break;
-        case W_G: launch_one<W_G, NT, 1>(N, R, P, grid, smem, st); break;
-        case W_J: launch_one<W_J, NT, 1>(N, R, P, grid, smem, st); break;
-        case W_G | W_J: launch_one<W_G | W_J, NT, 1>(N, R, P, grid, smem, st); break;
-        case W_H: launch_one<W_H, NT, 1>(N, R, P, grid, smem, st); break;
-        case W_G | W_H: launch_one<W_G | W_H, NT, 1>(N, R, P, grid, smem, st); break;
-        case W_J | W_H: launch_one<W_J | W_H, NT, 1>(N, R, P, grid, smem, st); break;
-        default: launch_one<ALL, NT, 1>(N, R, P, grid, smem, st); break;
-    }
-    return (int)cudaGetLastError();
 }
 
 template <int NT, int MINB>
@@ -243,10 +61,13 @@ int launch_eval_persistent(const DevNet &N, const EvalReq &R, const PersistLaunc
     if (e != cudaSuccess) return (int)e;
     int grid = L.grid < P.total ? L.grid : P.total;
     int rc;
-    if (L.block == 32) rc = launch_persist_nt<32>(N, R, P, grid, L.occ_warps, st);
-    else if (L.block == 256) rc = launch_persist_nt<256>(N, R, P, grid, L.occ_warps, st);
-    else if (L.block == 64) rc = launch_persist_nt<64>(N, R, P, grid, L.occ_warps, st);
-    else rc = launch_persist_nt<128>(N, R, P, grid, L.occ_warps, st);
+    if (R.gen_mask || R.tab) {
+        // generator masks (a gathered batch's states may carry their own)
+        rc = launch_persist_gm(L.block, N, R, P, grid, L.occ_warps, st);
+    } else if (L.block == 32) rc = launch_persist_nt<32, 0>(N, R, P, grid, L.occ_warps, st);
+    else if (L.block == 256) rc = launch_persist_nt<256, 0>(N, R, P, grid, L.occ_warps, st);
+    else if (L.block == 64) rc = launch_persist_nt<64, 0>(N, R, P, grid, L.occ_warps, st);
+    else rc = launch_persist_nt<128, 0>(N, R, P, grid, L.occ_warps, st);
     mark(hk, st, "end");
     return rc;
 }

@@ -179,6 +179,7 @@ std::vector<exago::StateTab> state_table(exago_net_t net, const std::vector<Requ
             e.x = bt.x + (size_t)j * p->n;
             e.lam = bt.lambda ? bt.lambda + (size_t)j * p->m : nullptr;
             e.mask = bt.mask ? bt.mask + (size_t)j * p->nl : nullptr;
+            e.gen_mask = bt.gen_mask ? bt.gen_mask + (size_t)j * p->ng : nullptr;
             e.pd_scale = bt.pd_scale ? bt.pd_scale + (size_t)j * p->nb : nullptr;
             e.obj_weight = bt.obj_weight ? bt.obj_weight + j : nullptr;
             e.sigma = bt.obj_factor;

@@ -82,7 +82,7 @@ extern "C" exago_status exago_eval_all_static(exago_net_t net, const exago_batch
                                                cudaGetErrorString(e));
     EvalReq R{};
     R.B = bt->B;
-    R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask;
+    R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask; R.gen_mask = bt->gen_mask;
     R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
     R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
     R.scratch = (double *)base;

@@ -68,7 +68,7 @@ class exago_batch(ctypes.Structure):
                 ("mask", ctypes.c_void_p), ("pd_scale", ctypes.c_void_p),
                 ("obj_weight", ctypes.c_void_p), ("obj_factor", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("gen_mask", ctypes.c_void_p)]
 
 
 def lib():
@@ -259,19 +259,24 @@ def exago_net_reserve(h, B: int):
 
 
 def make_batch(x, lam=None, mask=None, pd_scale=None, obj_weight=None, obj_factor=1.0,
-               stream=None, workspace=None) -> exago_batch:
+               stream=None, workspace=None, gen_mask=None) -> exago_batch:
     """exago_batch over torch CUDA tensors x [B][n] (float64), lam [B][m], mask [B][nl] (uint8),
-    pd_scale [B][nb], obj_weight [B]; stream is a torch.cuda.Stream or None (current stream)."""
+    pd_scale [B][nb], obj_weight [B], gen_mask [B][ng] (uint8); stream is a torch.cuda.Stream or
+    None (current stream)."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream(x.device)
     ws_ptr, ws_bytes = (None, 0)
     if workspace is not None:
         ws_ptr, ws_bytes = _dp(workspace), workspace.numel() * workspace.element_size()
-    return exago_batch(int(x.shape[0]), _dp(x, torch.float64), _dp(lam, torch.float64),
-                       _dp(mask, torch.uint8), _dp(pd_scale, torch.float64),
-                       _dp(obj_weight, torch.float64), float(obj_factor),
-                       ctypes.c_void_p(stream.cuda_stream), ws_ptr, ws_bytes)
+    bt = exago_batch(int(x.shape[0]), _dp(x, torch.float64), _dp(lam, torch.float64),
+                     _dp(mask, torch.uint8), _dp(pd_scale, torch.float64),
+                     _dp(obj_weight, torch.float64), float(obj_factor),
+                     ctypes.c_void_p(stream.cuda_stream), ws_ptr, ws_bytes,
+                     _dp(gen_mask, torch.uint8))
+    # the struct holds raw device pointers: keep the tensors alive as long as the batch
+    bt._tensors = (x, lam, mask, pd_scale, obj_weight, workspace, gen_mask)
+    return bt
 
 
 def _out(t):

@@ -27,7 +27,8 @@ def to_device(batch, device="cuda"):
     t = lambda a, dt: None if a is None else torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
     return dict(x=t(batch.x, torch.float64), lam=t(batch.lam, torch.float64),
                 mask=t(batch.mask, torch.uint8), pd_scale=t(batch.pd_scale, torch.float64),
-                obj_weight=t(batch.obj_weight, torch.float64))
+                obj_weight=t(batch.obj_weight, torch.float64),
+                gen_mask=t(batch.gen_mask, torch.uint8))
 
 
 def gpu_eval(net, batch, device="cuda", workspace=None, which=("f", "grad", "gh", "jval", "hval")):
@@ -36,7 +37,7 @@ def gpu_eval(net, batch, device="cuda", workspace=None, which=("f", "grad", "gh"
     from paper_2203_10587_gb300 import exago
     d = to_device(batch, device)
     bt = exago.make_batch(d["x"], d["lam"], d["mask"], d["pd_scale"], d["obj_weight"],
-                          batch.sigma, workspace=workspace)
+                          batch.sigma, workspace=workspace, gen_mask=d["gen_mask"])
     out = net.outputs(batch.B, device, f="f" in which, grad="grad" in which, gh="gh" in which,
                       jac="jval" in which, hess="hval" in which)
     net.eval_all(bt, out)
@@ -51,7 +52,8 @@ def oracle_eval(om, grid, batch, idx):
                        None if batch.mask is None else batch.mask[idx],
                        None if batch.pd_scale is None else batch.pd_scale[idx],
                        1.0 if batch.obj_weight is None else float(batch.obj_weight[idx]),
-                       batch.sigma)
+                       batch.sigma,
+                       gen_mask=None if batch.gen_mask is None else batch.gen_mask[idx])
 
 
 def compare_instance(out, b, ref, what=""):

@@ -47,7 +47,7 @@ def run_cart(ex, net, b, x, lam, which=("f", "grad", "gh", "jval", "hval"), work
     X = torch.as_tensor(x, device="cuda")
     LAM = torch.as_tensor(lam, device="cuda")
     bt = ex.make_batch(X, LAM, d["mask"], d["pd_scale"], d["obj_weight"], b.sigma,
-                       workspace=workspace)
+                       workspace=workspace, gen_mask=d["gen_mask"])
     n, me, mi, nj, nh = ex.exago_net_dims_cart(net.h)
     z = lambda *s: torch.full(s, np.nan, dtype=torch.float64, device="cuda")
     out = {"f": z(b.B), "grad": z(b.B, n), "gh": z(b.B, me + mi), "jval": z(b.B, nj),
@@ -63,7 +63,8 @@ def oracle_cart(om, g, b, x, lam, i):
                        None if b.mask is None else b.mask[i],
                        None if b.pd_scale is None else b.pd_scale[i],
                        1.0 if b.obj_weight is None else float(b.obj_weight[i]), b.sigma,
-                       cartesian=True)
+                       cartesian=True,
+                       gen_mask=None if b.gen_mask is None else b.gen_mask[i])
 
 
 def compare(out, ref, i, what):

@@ -28,7 +28,7 @@ class Req:
         self.batch = batch
         self.d = to_device(batch)
         self.bt = ex.make_batch(self.d["x"], self.d["lam"], self.d["mask"], self.d["pd_scale"],
-                                self.d["obj_weight"], batch.sigma)
+                                self.d["obj_weight"], batch.sigma, gen_mask=self.d["gen_mask"])
         self.out = net.outputs(batch.B)
 
     def host(self):
@@ -45,8 +45,9 @@ def alone(ex, net, r):
 
 @pytest.mark.parametrize("merge", [1, 32])
 def test_mixed_grids_same_alone_and_in_the_mix(ex, oracle_mod, merge):
-    """Requests on three grids, with their own masks, load scales, weights and objective factors,
-    some without the Hessian: merged or not, every result equals the request evaluated alone."""
+    """Requests on three grids, with their own branch and generator masks, load scales, weights
+    and objective factors, some without the Hessian: merged or not, every result equals the
+    request evaluated alone."""
     import torch
     grids = [synth.grid_sized(5, 118), synth.grid_2000(), synth.grid_sized(6, 10_000)]
     nets = [ex.Net(g) for g in grids]
@@ -60,7 +61,8 @@ def test_mixed_grids_same_alone_and_in_the_mix(ex, oracle_mod, merge):
             gi = int(rng.integers(3))
             B = int(rng.integers(1, 9))
             b = synth.random_batch(100 + k, grids[gi], B, masks=bool(k % 2), pd_scale=bool(k % 3),
-                                   obj_weight=bool(k % 4), sigma=float(rng.choice([0.0, 0.8, 1.0])))
+                                   obj_weight=bool(k % 4), sigma=float(rng.choice([0.0, 0.8, 1.0])),
+                                   gen_masks=k % 3 == 1)
             r = Req(ex, nets[gi], b)
             if k % 5 == 0:
                 r.out["hval"] = None           # a different set of outputs: never merged with the rest
