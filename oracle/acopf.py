@@ -66,6 +66,9 @@ def bind_library(path: str):
     lib.oracle_coo_capacity_cart.argtypes = [ctypes.POINTER(_Net), vp, vp]
     lib.oracle_pi_model.argtypes = [ctypes.c_double] * 4 + [vp]
     lib.oracle_pi_model.restype = ctypes.c_int
+    lib.oracle_slack.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp,
+                                 ctypes.c_double, vp, vp, vp]
+    lib.oracle_slack.restype = ctypes.c_int
     for fn in (lib.oracle_coupling, lib.oracle_coupling_jtv):
         fn.argtypes = [ctypes.c_int] * 4 + [vp, vp, vp]
         fn.restype = ctypes.c_int
@@ -221,6 +224,25 @@ def coupling_jtv(parent, nu, n: int, nb: int, lib=None) -> np.ndarray:
     if lib.oracle_coupling_jtv(B, n, nb, ng, _p(parent), _p(nu), _p(out)) != 0:
         raise ValueError("invalid parent index")
     return out
+
+
+def slack(nb: int, bus, row, sign, cost, z, w: float = 1.0, gh=None, f: float | None = None,
+          lib=None):
+    """Feasibility slacks (load loss, power imbalance) of one state: returns (gh + the slacks'
+    balance terms, f + their cost, grad_z); see oracle_slack.  gh, f default to zero."""
+    lib = lib or _load()
+    i32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    bus, row, sign = i32(bus), i32(row), i32(sign)
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    nz = bus.shape[0]
+    gh = np.zeros(2 * nb) if gh is None else np.array(gh, dtype=np.float64)
+    fv = np.array([0.0 if f is None else float(f)])
+    grad = np.zeros(nz)
+    if lib.oracle_slack(nb, nz, _p(bus), _p(row), _p(sign), _p(cost), _p(z), float(w), _p(gh),
+                        _p(fv), _p(grad)) != 0:
+        raise ValueError("invalid slack bus, row or sign")
+    return gh, float(fv[0]), grad
 
 
 def csr_to_dense(csr, shape) -> np.ndarray:

@@ -522,3 +522,29 @@ int oracle_eval_cart(const oracle_net *net, const double *x, const double *lam,
     /* generators, exactly as in the polar model */
     return gen_terms(net, Pg, Qg, gmask, w, sigma, gP, gQ, fval, grad, J, H);
 }
+
+/* ---- Feasibility slacks: load loss and power imbalance ----
+ * The model's feasibility options (Sec. III, Fig. 2: load loss, power imbalance) add nonnegative
+ * variables that enter the bus balances linearly and are penalised linearly in the objective.
+ * Slack k sits at bus bus[k] in the P balance (row[k] = 0) or the Q balance (row[k] = 1), with
+ * sign[k] = +1 or -1 and cost coefficient cost[k] (per p.u.):
+ *     g_{row,bus}  +=  sign z_k,      f  +=  w cost z_k,      df/dz_k = w cost,
+ * and the Jacobian column of z_k has the single entry sign[k] in that row; the Hessian gets
+ * nothing.  Load loss at bus i is a slack with sign -1 (it lowers the load Pd_i); an imbalance is
+ * a pair with signs -1 and +1.  For one state: z[nz], gh[m] and *f are added to, grad_z[nz]
+ * written (either pointer may be NULL).  Returns 0, or -1 for a bus, row or sign out of range. */
+int oracle_slack(int nb, int nz, const int *bus, const int *row, const int *sign,
+                 const double *cost, const double *z, double w, double *gh, double *f,
+                 double *grad_z)
+{
+    int k;
+    for (k = 0; k < nz; k++) {
+        if (bus[k] < 0 || bus[k] >= nb || (row[k] != 0 && row[k] != 1) ||
+            (sign[k] != 1 && sign[k] != -1))
+            return -1;
+        if (gh) gh[row[k] * nb + bus[k]] += sign[k] * z[k];
+        if (f) *f += w * cost[k] * z[k];
+        if (grad_z) grad_z[k] = w * cost[k];
+    }
+    return 0;
+}

@@ -13,6 +13,7 @@ from oracle import acopf
 import test_oracle as T
 import test_oracle_cartesian as TK
 import test_oracle_genmask as TG
+import test_oracle_slack as TS
 import test_oracle_coupling as TC
 
 SRC = os.path.join(os.path.dirname(acopf.__file__), "acopf_oracle.c")
@@ -59,6 +60,9 @@ MUTANTS = {
     "gen_mask_jac_kept": ("if (push(J, gb, 2 * nb + k, on ? -1.0 : 0.0)) return -2;",
                           "if (push(J, gb, 2 * nb + k, -1.0)) return -2;"),
     "gen_mask_hess_kept": ("double hk = on ? sigma", "double hk = 1 ? sigma"),
+    "slack_sign_dropped": ("gh[row[k] * nb + bus[k]] += sign[k] * z[k];", "gh[row[k] * nb + bus[k]] += z[k];"),
+    "slack_row_dropped": ("gh[row[k] * nb + bus[k]] += sign[k]", "gh[bus[k]] += sign[k]"),
+    "slack_weight_dropped": ("if (f) *f += w * cost[k] * z[k];", "if (f) *f += cost[k] * z[k];"),
     "coupling_sign": ("x[(int64_t)b * n + 2 * nb + k] - x[(int64_t)p * n + 2 * nb + k]",
                       "x[(int64_t)b * n + 2 * nb + k] + x[(int64_t)p * n + 2 * nb + k]"),
     "coupling_parent_stride": ("- x[(int64_t)p * n + 2 * nb + k]", "- x[(int64_t)p * ng + 2 * nb + k]"),
@@ -78,6 +82,9 @@ class Bound:
 
     def evaluate(self, *a, **k):
         return acopf.evaluate(*a, lib=self.lib, **k)
+
+    def slack(self, *a, **k):
+        return acopf.slack(*a, lib=self.lib, **k)
 
     def coupling(self, *a, **k):
         return acopf.coupling(*a, lib=self.lib, **k)
@@ -104,6 +111,8 @@ PINS = [
     ("cart_homogeneity", lambda om: TK.test_homogeneity_and_rotation(om)),
     ("gen_out_polar", lambda om: TG.test_generator_out_equals_generator_removed(om, False)),
     ("gen_out_hand", lambda om: TG.test_two_bus_generator_outage_by_hand(om)),
+    ("slack_hand", lambda om: TS.test_hand_values(om)),
+    ("slack_load_loss", lambda om: TS.test_load_loss_equals_lower_load(om)),
     ("coupling_hand", lambda om: TC.test_hand_rows(om)),
     ("coupling_hand_transpose", lambda om: TC.test_hand_transpose(om)),
     ("coupling_telescopes", lambda om: TC.test_chain_telescopes(om)),
