@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ / 1e3
 FP64_PEAK_GINSTR = SMS * FP64_FMA_PER_SM_CLK * SM_MAX_GHZ
 # dram bytes per launch of the dominant kernel from its ncu capture, by kernel name; a kernel
 # changed since its capture has no entry
-TRAFFIC_BYTES = {"persistent": 578_803_968}   # 65.7 MB read + 513.1 MB written (ncu, 2000-bus x 512)
+TRAFFIC_BYTES = {"persistent": 579_142_400}   # 65.9 MB read + 513.3 MB written (ncu, 2000-bus x 512)
 HBM_PEAK_FALLBACK_GBS = 6800.0
 
 
@@ -470,6 +470,39 @@ def run_coupling(exago, synth, torch, np, dev, hbm_peak):
     return res
 
 
+def run_slacks(exago, synth, torch, np, dev, hbm_peak):
+    """Feasibility slacks (load loss, power imbalance) added to a finished evaluation of the
+    2,000-bus x 512 batch: an imbalance pair on every P and Q balance and load loss at the loaded
+    buses (about 4.5 slacks per bus), balance terms, objective and gradient in one call; warm
+    (inputs in L2, as right after the evaluation).  Algorithmic bytes per state: z read, grad_z
+    written, 2 nb balance values read and written, f read and written."""
+    g = synth.grid_2000()
+    B, nb = 512, g.nb
+    load = np.flatnonzero(g.Pd > 0.3)
+    bus = np.concatenate([np.tile(np.arange(nb), 4), load, load]).astype(np.int32)
+    row = np.concatenate([np.zeros(2 * nb), np.ones(2 * nb), np.zeros(len(load)),
+                          np.ones(len(load))]).astype(np.int32)
+    sign = np.concatenate([-np.ones(nb), np.ones(nb), -np.ones(nb), np.ones(nb),
+                           -np.ones(2 * len(load))]).astype(np.int32)
+    cost = np.full(bus.shape[0], 500.0)
+    net = exago.Net(g)
+    sl = exago.Slack(net, bus, row, sign, cost)
+    nz = bus.shape[0]
+    z = torch.rand(B, nz, dtype=torch.float64, device=dev) * 0.1
+    gh = torch.zeros(B, net.m, dtype=torch.float64, device=dev)
+    f = torch.zeros(B, dtype=torch.float64, device=dev)
+    gz = torch.empty(B, nz, dtype=torch.float64, device=dev)
+    x = torch.zeros(B, net.n, dtype=torch.float64, device=dev)
+    bt = exago.make_batch(x)
+    ms = time_calls(torch, lambda: exago.exago_eval_slack(sl, bt, z, gh, net.m, f, gz), 500)
+    nbytes = B * (16 * nz + 32 * nb + 16)
+    sl.close()
+    net.close()
+    return {"workload": "2000-bus x 512 states, imbalance pairs on every balance plus load loss",
+            "slacks_per_state": nz, "us_per_call": ms * 1e3, "algorithmic_bytes": nbytes,
+            "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}
+
+
 def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):
     """The power-balance-cartesian formulation (exago_eval_cart) on the headline workload, the
     2,000-bus x 512 N-1 batch at the same operating points (e = Vm cos Va, f = Vm sin Va), all
@@ -722,6 +755,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     coupling = None if args.no_serve else run_coupling(exago, synth, torch, np, dev, hbm_peak)
     cartesian = None if args.no_serve else run_cartesian(exago, synth, torch, np, dev, hbm_peak,
                                                          top_ms)
+    slacks = None if args.no_serve else run_slacks(exago, synth, torch, np, dev, hbm_peak)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -766,6 +800,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         res["coupling_rows"] = coupling
     if cartesian is not None:
         res["cartesian"] = cartesian
+    if slacks is not None:
+        res["feasibility_slacks"] = slacks
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_evals = 256 * cores
