@@ -244,6 +244,42 @@ exago_status exago_eval_cart_hvp(exago_net_t net, const exago_batch *batch, cons
                                  double *out);
 
 /*
+ * Feasibility slacks: load loss and power imbalance (Sec. III, Fig. 2).  Each slack z_k >= 0 sits
+ * at bus bus[k] in the P balance (row[k] = 0) or the Q balance (row[k] = 1) with sign[k] = +1 or
+ * -1 and a linear cost cost[k] per p.u.:  g_{row,bus} += sign z_k  and  f += w cost_k z_k, with
+ * w the batch's obj_weight.  Load loss at a bus is a slack of sign -1 (it lowers the load); an
+ * imbalance is a pair of signs -1 and +1.  The slack variables follow x in the solver's vector;
+ * their Jacobian column is the single constant entry sign_k in balance row row_k nb + bus_k,
+ * and they add nothing to the Lagrangian Hessian.
+ *   exago_slack_create    HOST arrays [nz], copied.  EINVAL for a NULL net or out, nz < 0, NULL
+ *                         arrays with nz > 0, a bus outside [0, nb), a row not 0 or 1, a sign not
+ *                         +1 or -1, or a cost that is not finite.  A net made by exago_net_plan
+ *                         gives a host-only set (pattern only; evaluations return ESTATE).
+ *   exago_slack_pattern   HOST rows [nz] (the balance row of each slack's Jacobian entry) and
+ *                         vals [nz] (its value, the sign).
+ *   exago_eval_slack      adds the slacks to a finished evaluation of the same states, on
+ *                         batch->stream (batch: B, obj_weight and stream are used): z [B][nz];
+ *                         gh [B][ldgh] += the balance terms (rows 0 .. 2 nb of each state, in the
+ *                         slacks' ascending order; ldgh = m for the polar model, m + nb for the
+ *                         cartesian one); f [B] += w sum_k cost_k z_k; grad_z [B][nz] = w cost_k.
+ *                         Any of gh, f, grad_z may be NULL.  All DEVICE buffers.
+ *   exago_eval_slack_jtv  out [B][nz] = the slack columns' part of J^T v: sign_k v[row_k nb +
+ *                         bus_k] for v [B][ldv] (ldv >= 2 nb); J u for the slack columns is
+ *                         exago_eval_slack with z = u, gh the accumulator, f = grad_z = NULL.
+ * Errors: EINVAL for NULL vectors (B > 0), ldgh or ldv below 2 nb or a different current device;
+ * ECUDA if a launch fails.  B = 0 or nz = 0 does nothing.
+ */
+typedef struct exago_slack *exago_slack_t;
+exago_status exago_slack_create(exago_net_t net, int nz, const int *bus, const int *row,
+                                const int *sign, const double *cost, exago_slack_t *out);
+exago_status exago_slack_destroy(exago_slack_t slack);
+exago_status exago_slack_pattern(exago_slack_t slack, int64_t *rows, double *vals);
+exago_status exago_eval_slack(exago_slack_t slack, const exago_batch *batch, const double *z,
+                              double *gh, int64_t ldgh, double *f, double *grad_z);
+exago_status exago_eval_slack_jtv(exago_slack_t slack, const exago_batch *batch, const double *v,
+                                  int64_t ldv, double *out);
+
+/*
  * Coupling (ramp) rows between the states of a batch.  ExaGO's multi-stage problems tie each
  * subproblem's state to one other state by a bounded difference: consecutive periods of the
  * multi-period problem (Sec. IV, eq. (15)), each contingency to the base case (Sec. V-A,

@@ -37,7 +37,8 @@ EXPORTS = [
     "exago_coupling_destroy", "exago_coupling_dims", "exago_coupling_jac_pattern",
     "exago_eval_coupling", "exago_eval_coupling_jtv", "exago_net_dims_cart",
     "exago_net_jac_pattern_cart", "exago_eval_cart_workspace_size", "exago_eval_cart",
-    "exago_eval_cart_jvp", "exago_eval_cart_jtv", "exago_eval_cart_hvp",
+    "exago_eval_cart_jvp", "exago_eval_cart_jtv", "exago_eval_cart_hvp", "exago_slack_create",
+    "exago_slack_destroy", "exago_slack_pattern", "exago_eval_slack", "exago_eval_slack_jtv",
 ]
 
 SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
@@ -137,6 +138,13 @@ def lib():
                 "exago_eval_cart_jvp": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
                 "exago_eval_cart_jtv": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
                 "exago_eval_cart_hvp": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
+                "exago_slack_create": ([vp, i32, vp, vp, vp, vp, ctypes.POINTER(vp)], i32),
+                "exago_slack_destroy": ([vp], i32),
+                "exago_slack_pattern": ([vp, vp, vp], i32),
+                "exago_eval_slack": ([vp, ctypes.POINTER(exago_batch), vp, vp, ctypes.c_int64, vp,
+                                      vp], i32),
+                "exago_eval_slack_jtv": ([vp, ctypes.POINTER(exago_batch), vp, ctypes.c_int64, vp],
+                                         i32),
                 "exago_coupling_create": ([vp, i32, vp, ctypes.POINTER(vp)], i32),
                 "exago_coupling_destroy": ([vp], i32),
                 "exago_coupling_dims": ([vp, ctypes.POINTER(i32), i64p, i64p], i32),
@@ -468,6 +476,52 @@ def exago_eval_cart_hvp(h, batch: exago_batch, u, out):
     """out [B][n] = (cartesian Lagrangian Hessian at the batch's lambda and obj_factor) u."""
     import torch
     _check(lib().exago_eval_cart_hvp(h, ctypes.byref(batch), _dp(u, torch.float64), _out(out)))
+
+
+class Slack:
+    """Owns a set of feasibility slacks (load loss, power imbalance) of a net: host arrays bus,
+    row (0 = P balance, 1 = Q balance), sign (+1 / -1) and cost, all [nz]."""
+
+    def __init__(self, net: Net, bus, row, sign, cost):
+        i = lambda a: _np(a, np.int32)
+        keep = [i(bus), i(row), i(sign), _np(cost, np.float64)]
+        self.nz = int(keep[0].shape[0])
+        h = ctypes.c_void_p()
+        _check(lib().exago_slack_create(net.h, self.nz, *map(_hp, keep), ctypes.byref(h)))
+        self.h = h
+        self.nb = net.nb
+
+    def pattern(self):
+        rows = np.zeros(max(self.nz, 1), np.int64)
+        vals = np.zeros(max(self.nz, 1), np.float64)
+        _check(lib().exago_slack_pattern(self.h, _hp(rows), _hp(vals)))
+        return rows[:self.nz], vals[:self.nz]
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            lib().exago_slack_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def exago_eval_slack(slack: Slack, batch: exago_batch, z, gh=None, ldgh: int = 0, f=None,
+                     grad_z=None):
+    """Adds the slacks' balance terms to gh [B][ldgh] and their cost to f [B]; writes grad_z."""
+    import torch
+    _check(lib().exago_eval_slack(slack.h, ctypes.byref(batch), _dp(z, torch.float64), _out(gh),
+                                  int(ldgh), _out(f), _out(grad_z)))
+
+
+def exago_eval_slack_jtv(slack: Slack, batch: exago_batch, v, ldv: int, out):
+    """out [B][nz] = sign_k v[b][row_k] (the slack columns of J^T v)."""
+    import torch
+    _check(lib().exago_eval_slack_jtv(slack.h, ctypes.byref(batch), _dp(v, torch.float64),
+                                      int(ldv), _out(out)))
 
 
 def exago_coupling_create(net_h, parent):

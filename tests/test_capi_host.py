@@ -365,3 +365,28 @@ def test_cartesian_evaluation_needs_a_device_net(L):
     assert exago.STATUS[rc] == "EXAGO_ESTATE"
     v = ctypes.c_size_t()
     assert exago.STATUS[L.exago_eval_cart_workspace_size(net.h, 4, ctypes.byref(v))] == "EXAGO_ESTATE"
+
+
+# ---- feasibility slacks: host side ----------------------------------------------------------------
+
+def test_slack_pattern_and_validation(L):
+    g = synth.grid_30bus()
+    net = plan(g)
+    bus = np.array([0, 4, 4, 29], np.int32)
+    row = np.array([0, 0, 1, 1], np.int32)
+    sign = np.array([-1, 1, -1, 1], np.int32)
+    s = exago.Slack(net, bus, row, sign, np.array([1.0, 2.0, 3.0, 4.0]))
+    rows, vals = s.pattern()
+    np.testing.assert_array_equal(rows, row * g.nb + bus)
+    np.testing.assert_array_equal(vals, sign)
+    x = np.zeros(1)
+    rc = L.exago_eval_slack(s.h, ctypes.byref(exago.exago_batch(1)), x.ctypes.data, None, 0, None,
+                            None)
+    assert exago.STATUS[rc] == "EXAGO_ESTATE"
+    s.close()
+    for bad in (dict(bus=[30]), dict(bus=[-1]), dict(row=[2]), dict(sign=[0]), dict(cost=[np.inf])):
+        kw = dict(bus=[1], row=[0], sign=[1], cost=[1.0])
+        kw.update(bad)
+        with pytest.raises(exago.ExagoError) as ei:
+            exago.Slack(net, kw["bus"], kw["row"], kw["sign"], kw["cost"])
+        assert ei.value.name == "EXAGO_EINVAL"
