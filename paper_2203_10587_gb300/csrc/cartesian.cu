@@ -58,26 +58,6 @@ __device__ __forceinline__ void put2c(double *rec, int c, double a, double b) {
     *reinterpret_cast<double2 *>(rec + c) = make_double2(a, b);
 }
 
-// Outer-product weights of one end: with m2 = 2 mu, p = dP/d(e_u, f_u, e_v, f_v), q = dQ/d(...)
-// (q3 = p4, q4 = -p3), O_ij = m2 (p_i p_j + q_i q_j); O_33 = O_44 = m2 (p3^2 + p4^2), O_43 = 0.
-struct EndOuter {
-    double o11, o21, o22, ovv, o13, o14, o23, o24;
-};
-
-__device__ __forceinline__ EndOuter end_outer(double m2, double p1, double p2, double q1,
-                                              double q2, double p3, double p4) {
-    EndOuter o;
-    o.o11 = m2 * fma(p1, p1, q1 * q1);
-    o.o21 = m2 * fma(p2, p1, q2 * q1);
-    o.o22 = m2 * fma(p2, p2, q2 * q2);
-    o.ovv = m2 * fma(p3, p3, p4 * p4);
-    o.o13 = m2 * fma(p1, p3, q1 * p4);
-    o.o14 = m2 * fma(p1, p4, -(q1 * p3));
-    o.o23 = m2 * fma(p2, p3, q2 * p4);
-    o.o24 = m2 * fma(p2, p4, -(q2 * p3));
-    return o;
-}
-
 // Flows and first derivatives of one branch at voltages (ef + j ff, et + j ft).  For the end at u
 // towards v, p = dP/d(e_u, f_u, e_v, f_v) and q1, q2 = dQ/d(e_u, f_u); dQ/de_v = p4, dQ/df_v = -p3.
 struct CartBranch {
@@ -132,8 +112,10 @@ __device__ __forceinline__ CartBranch cart_terms(const CartY &y, double ef, doub
 // The branch's Lagrangian-Hessian block over (e_f, f_f, e_t, f_t), 10 distinct values.  End
 // weights wP = lamP + 2 mu P, wQ = lamQ + 2 mu Q; the linear part of each end's block is
 // wP grad^2 P + wQ grad^2 Q: d = 2 (wP Gss - wQ Bss) on (e_u,e_u) and (f_u,f_u),
-// c1 = wP G - wQ B on (e_u,e_v) and (f_u,f_v), c2 = wP B + wQ G on (f_u,e_v) and -c2 on (e_u,f_v);
-// the rest is 2 mu (grad P grad P' + grad Q grad Q') (end_outer).
+// c1 = wP G - wQ B on (e_u,e_v) and (f_u,f_v), c2 = wP B + wQ G on (f_u,e_v) and -c2 on (e_u,f_v).
+// The rest is O = 2 mu (grad P grad P' + grad Q grad Q') of each end; with q3 = p4, q4 = -p3 its
+// (e_v,e_v) and (f_v,f_v) entries are both 2 mu (p3^2 + p4^2) and its (f_v,e_v) entry vanishes.
+// The gradients are scaled by 2 mu once, and each entry is one chain of fused multiply-adds.
 struct CartHess {
     double eef, fef, fff;            // (e_f,e_f), (f_f,e_f), (f_f,f_f)
     double eet, fet, fft;            // (e_t,e_t), (f_t,e_t), (f_t,f_t)
@@ -148,21 +130,26 @@ __device__ __forceinline__ CartHess cart_hess(const CartY &y, const CartBranch &
     const double wPf = fma(muf2, c.Pf, lPf), wQf = fma(muf2, c.Qf, lQf);
     const double wPt = fma(mut2, c.Pt, lPt), wQt = fma(mut2, c.Qt, lQt);
     const double df = fma(wPf, Gff2, -(wQf * Bff2)), dt = fma(wPt, Gtt2, -(wQt * Btt2));
-    const double c1 = fma(wPf, G, -(wQf * Bm)) + fma(wPt, G, -(wQt * Bm));
-    const double c2f = fma(wPf, Bm, wQf * G), c2t = fma(wPt, Bm, wQt * G);
-    const EndOuter of = end_outer(muf2, c.p1f, c.p2f, c.q1f, c.q2f, c.p3f, c.p4f);
-    const EndOuter ot = end_outer(mut2, c.p1t, c.p2t, c.q1t, c.q2t, c.p3t, c.p4t);
+    const double c1 = fma(wPf + wPt, G, -((wQf + wQt) * Bm));            // c1_f + c1_t
+    const double dc = fma(wPt - wPf, Bm, (wQt - wQf) * G);               // c2_t - c2_f
+    // 2 mu times each end's gradient
+    const double a1 = muf2 * c.p1f, a2 = muf2 * c.p2f, a3 = muf2 * c.p3f, a4 = muf2 * c.p4f;
+    const double b1 = muf2 * c.q1f, b2 = muf2 * c.q2f;
+    const double s1 = mut2 * c.p1t, s2 = mut2 * c.p2t, s3 = mut2 * c.p3t, s4 = mut2 * c.p4t;
+    const double r1 = mut2 * c.q1t, r2 = mut2 * c.q2t;
     CartHess h;
-    h.eeft = c1 + (of.o13 + ot.o13);
-    h.ffft = c1 + (of.o24 + ot.o24);
-    h.ef_ft = (c2t - c2f) + (of.o14 + ot.o23);
-    h.ff_et = (c2f - c2t) + (of.o23 + ot.o14);
-    h.eef = df + (of.o11 + ot.ovv);
-    h.fef = of.o21;
-    h.fff = df + (of.o22 + ot.ovv);
-    h.eet = dt + (ot.o11 + of.ovv);
-    h.fet = ot.o21;
-    h.fft = dt + (ot.o22 + of.ovv);
+    const double dfo = df + fma(s3, c.p3t, s4 * c.p4t);   // d_f + (e_t,e_t) block of O_t
+    const double dto = dt + fma(a3, c.p3f, a4 * c.p4f);
+    h.eef = fma(a1, c.p1f, fma(b1, c.q1f, dfo));
+    h.fef = fma(a2, c.p1f, b2 * c.q1f);
+    h.fff = fma(a2, c.p2f, fma(b2, c.q2f, dfo));
+    h.eet = fma(s1, c.p1t, fma(r1, c.q1t, dto));
+    h.fet = fma(s2, c.p1t, r2 * c.q1t);
+    h.fft = fma(s2, c.p2t, fma(r2, c.q2t, dto));
+    h.eeft = fma(a1, c.p3f, fma(b1, c.p4f, fma(s1, c.p3t, fma(r1, c.p4t, c1))));
+    h.ffft = fma(a2, c.p4f, fma(-b2, c.p3f, fma(s2, c.p4t, fma(-r2, c.p3t, c1))));
+    h.ef_ft = fma(a1, c.p4f, fma(-b1, c.p3f, fma(s2, c.p3t, fma(r2, c.p4t, dc))));
+    h.ff_et = fma(a2, c.p3f, fma(b2, c.p4f, fma(s1, c.p4t, fma(-r1, c.p3t, -dc))));
     return h;
 }
 

@@ -3,10 +3,11 @@
 // +1 or -1 and a linear cost: it adds sign z_k to that balance and w cost_k z_k to the objective;
 // its Jacobian column is the constant sign in that row and the Hessian gets nothing.  The terms
 // are applied to a finished evaluation (exago_eval_* outputs) by three small kernels:
-//   * rows: one thread per (state, balance row with slacks) adds its slacks in ascending slack
-//     order to the row's value (the same additions, in the same order, as the definition);
-//   * objective: one block per state sums cost_k z_k over a fixed 256-lane tree and adds w times
-//     the sum to f; the gradient w cost_k is written beside it;
+//   * rows: one thread per (balance row with slacks, group of 8 states) adds the row's slacks in
+//     ascending slack order to each state's value (the same additions, in the same order, as the
+//     definition);
+//   * objective: one block per state sums cost_k z_k (four partial sums per thread, then a fixed
+//     256-lane tree) and adds w times the sum to f; the gradient w cost_k by its own kernel;
 //   * transpose: one thread per (state, slack) gathers sign_k v[row_k].
 #include <cuda_runtime.h>
 
@@ -38,48 +39,78 @@ using exago::set_last_error;
 constexpr int kLanes = 256;
 constexpr int kMaxGridY = 65535;
 
+// Balance rows: one thread per (balance row with slacks, group of kGroup states).  The row's slack
+// list is read once for the group; each state's value gets the row's slacks in ascending order
+// (the definition's additions in the definition's order), the group's loads issued together.
+constexpr int kGroup = 8;
 __global__ void __launch_bounds__(128) k_slack_rows(const int *__restrict__ used, int nused,
                                                     const int *__restrict__ rptr,
                                                     const int *__restrict__ rlist,
                                                     const int *__restrict__ sign, int nz, int b0,
-                                                    const double *__restrict__ z, double *gh,
-                                                    int64_t ldgh) {
+                                                    int nB, const double *__restrict__ z,
+                                                    double *gh, int64_t ldgh) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nused) return;
-    const int b = b0 + blockIdx.y;
+    const int g0 = b0 + blockIdx.y * kGroup;
+    const int ns = min(kGroup, b0 + nB - g0);
     const int r = __ldg(used + j);
-    const double *zb = z + (int64_t)b * nz;
-    double *g = gh + (int64_t)b * ldgh + r;
-    double v = *g;
+    double v[kGroup];
+#pragma unroll
+    for (int t = 0; t < kGroup; t++)
+        if (t < ns) v[t] = gh[(int64_t)(g0 + t) * ldgh + r];
     for (int q = __ldg(rptr + r), q1 = __ldg(rptr + r + 1); q < q1; q++) {
         const int k = __ldg(rlist + q);
-        v += __ldg(sign + k) * __ldg(zb + k);
+        const double sk = __ldg(sign + k);
+#pragma unroll
+        for (int t = 0; t < kGroup; t++)
+            if (t < ns) v[t] += sk * __ldg(z + (int64_t)(g0 + t) * nz + k);
     }
-    *g = v;
+#pragma unroll
+    for (int t = 0; t < kGroup; t++)
+        if (t < ns) gh[(int64_t)(g0 + t) * ldgh + r] = v[t];
 }
 
+// Objective: one block per state; each thread keeps four partial sums over slacks t, t + 256,
+// t + 512, t + 768, then t + 1024, ... (independent loads in flight), combined in a fixed order
+// and then over a fixed 256-lane tree.
 __global__ void __launch_bounds__(kLanes) k_slack_obj(const double *__restrict__ cost, int nz,
                                                       int b0, const double *__restrict__ z,
                                                       const double *__restrict__ obj_weight,
-                                                      double *f, double *grad_z) {
+                                                      double *f) {
     __shared__ double part[kLanes];
     const int b = b0 + blockIdx.x;
-    const double w = obj_weight ? __ldg(obj_weight + b) : 1.0;
     const double *zb = z + (int64_t)b * nz;
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < nz; k += kLanes) {
-        const double c = __ldg(cost + k);
-        if (f) acc = fma(c, __ldg(zb + k), acc);
-        if (grad_z) grad_z[(int64_t)b * nz + k] = w * c;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int k = threadIdx.x;
+    for (; k + 3 * kLanes < nz; k += 4 * kLanes) {
+        a0 = fma(__ldg(cost + k), __ldg(zb + k), a0);
+        a1 = fma(__ldg(cost + k + kLanes), __ldg(zb + k + kLanes), a1);
+        a2 = fma(__ldg(cost + k + 2 * kLanes), __ldg(zb + k + 2 * kLanes), a2);
+        a3 = fma(__ldg(cost + k + 3 * kLanes), __ldg(zb + k + 3 * kLanes), a3);
     }
-    if (!f) return;
-    part[threadIdx.x] = acc;
+    for (; k < nz; k += kLanes) a0 = fma(__ldg(cost + k), __ldg(zb + k), a0);
+    part[threadIdx.x] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     for (int h = kLanes / 2; h > 0; h >>= 1) {
         if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) f[b] = fma(w, part[0], f[b]);
+    if (threadIdx.x == 0) f[b] = fma(obj_weight ? __ldg(obj_weight + b) : 1.0, part[0], f[b]);
+}
+
+// Gradient w cost_k: blocks of 256 threads along each state's slacks, four values per thread.
+__global__ void __launch_bounds__(256) k_slack_grad(const double *__restrict__ cost, int nz,
+                                                    int b0, const double *__restrict__ obj_weight,
+                                                    double *__restrict__ grad_z) {
+    const int b = b0 + blockIdx.y;
+    const double w = obj_weight ? __ldg(obj_weight + b) : 1.0;
+    double *gb = grad_z + (int64_t)b * nz;
+    const int k0 = blockIdx.x * 1024 + threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int k = k0 + u * 256;
+        if (k < nz) gb[k] = w * __ldg(cost + k);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_slack_jtv(const int *__restrict__ grow,
@@ -224,11 +255,12 @@ exago_status exago_eval_slack(exago_slack_t s, const exago_batch *bt, const doub
     for (int b0 = 0; b0 < bt->B; b0 += kMaxGridY) {
         const int nB = std::min(kMaxGridY, bt->B - b0);
         if (gh && nused > 0)
-            k_slack_rows<<<dim3((nused + 127) / 128, nB), 128, 0, stream>>>(
-                used, nused, rptr, rlist, sign, s->nz, b0, z, gh, ldgh);
-        if (f || grad_z)
-            k_slack_obj<<<nB, kLanes, 0, stream>>>(s->d_cost, s->nz, b0, z, bt->obj_weight, f,
-                                                   grad_z);
+            k_slack_rows<<<dim3((nused + 127) / 128, (nB + kGroup - 1) / kGroup), 128, 0, stream>>>(
+                used, nused, rptr, rlist, sign, s->nz, b0, nB, z, gh, ldgh);
+        if (f) k_slack_obj<<<nB, kLanes, 0, stream>>>(s->d_cost, s->nz, b0, z, bt->obj_weight, f);
+        if (grad_z)
+            k_slack_grad<<<dim3((s->nz + 1023) / 1024, nB), 256, 0, stream>>>(
+                s->d_cost, s->nz, b0, bt->obj_weight, grad_z);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
