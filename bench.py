@@ -539,7 +539,9 @@ def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):
             "jtv_per_s": b.B / (ms_jtv * 1e-3), "hvp_per_s": b.B / (ms_hvp * 1e-3),
             "algorithmic_bytes": nbytes, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
             "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak,
-            "schedule": "branch records + bus assembly per chunk of states (records stay in L2)"}
+            "schedule": "per chunk of 41 states, branch records on the caller's stream while the "
+                        "previous chunk's bus assembly runs on a side stream; a ring of 3 chunks "
+                        "of records stays in L2"}
 
 
 def run_serve(exago, synth, torch, np, dev, seconds):

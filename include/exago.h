@@ -215,13 +215,16 @@ exago_status exago_eval_hvp(exago_net_t net, const exago_batch *batch, const dou
  *                               e_i, f_i.  The Hessian pattern is exago_net_hess_pattern's (same
  *                               substitution).  Works on a net made by exago_net_plan.
  *   exago_eval_cart_workspace_size  scratch bytes of exago_eval_cart for B states (branch-end
- *                               records of one chunk of states, at most about 48 MB).
+ *                               records of up to three chunks of states, at most about 75 MB).
  *   exago_eval_cart             f [B], grad [B][n], gh [B][m_c], jval [B][nnzJ_c], hval [B][nnzH]
  *                               (DEVICE buffers; any may be NULL) for the batch's states x [B][n]
  *                               and multipliers lambda [B][m_c].  batch->workspace as for
  *                               exago_eval_all (else the net's internal workspace, grown on
- *                               demand).  Errors as exago_eval_all.  Runs the multi-kernel
- *                               schedule (branch records, then bus assembly, per chunk of states);
+ *                               demand).  Errors as exago_eval_all.  Per chunk of states, a
+ *                               branch kernel writes records and a bus kernel assembles the rows;
+ *                               the bus kernel of a chunk runs on the net's side stream while the
+ *                               next chunk's branch kernel runs on batch->stream (ordered by
+ *                               events; the call returns with all work ordered on batch->stream);
  *                               the persistent schedule and the graph cache are the polar
  *                               model's only.
  */

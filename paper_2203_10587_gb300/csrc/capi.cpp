@@ -582,6 +582,15 @@ bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **de
 
 exago_status set_last_error(exago_status s, const std::string &msg) { return fail(s, msg); }
 
+exago_status with_net_pipeline(exago_net_t net,
+                                const std::function<exago_status(const PipeLaunch &)> &fn) {
+    std::lock_guard<std::mutex> lk(net->mu);
+    PipeLaunch pl{};
+    exago_status s = pipe_resources_locked(net, pl);
+    if (s != EXAGO_OK) return s;
+    return fn(pl);
+}
+
 exago_status net_workspace(exago_net_t net, size_t bytes, void **ws) {
     std::lock_guard<std::mutex> lk(net->mu);
     exago_status s = ensure_workspace_locked(net, bytes);

@@ -17,8 +17,10 @@
 // chunk of states, a branch kernel writes each branch end's 14-value record at its slot and the
 // branch's h values and h rows; a bus kernel walks each bus's slots in the plan's fixed order,
 // writes the neighbour entries of its J and H rows and finishes the diagonal, balance, voltage
-// and generator terms.  Chunks are sized so that the records stay in L2 between the two kernels;
-// each kernel's grid is its resident CTA count, looping over (state, block) work items.
+// and generator terms.  The branch kernel of the next chunk runs on the caller's stream while the
+// bus kernel of the previous one runs on the net's side stream (ordered by events only), with a
+// ring of three chunks of records sized to stay in L2; each kernel's grid is its resident CTA
+// count, looping over (state, block) work items.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,7 +42,12 @@ enum CartComp {
     CNC = 14
 };
 
-constexpr size_t kChunkRecordBytes = (size_t)48 << 20;   // records of one chunk stay in L2
+// Records of one chunk of states; a ring of kRing chunks (72 MiB) stays in L2 between the branch
+// kernel that writes a chunk and the bus kernel that reads it.
+constexpr size_t kChunkRecordBytes = (size_t)24 << 20;
+constexpr int kRing = 3;
+// Branch values of one chunk of states in the adjoint products (one stream, no ring).
+constexpr size_t kAdjChunkBytes = (size_t)48 << 20;
 
 struct CartReq {
     int B, b0;                  // states of this launch: b0 .. b0 + nB (the kernels' argument)
@@ -569,7 +576,7 @@ exago_status cart_adjoint(exago_net_t net, const exago_batch *bt, const double *
     const DevNet &N = *dev;
     const size_t per = (size_t)std::max(N.nl, 1) * 4 * sizeof(double);
     int chunk = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(bt->B, 65535),
-                                                          kChunkRecordBytes / per));
+                                                          kAdjChunkBytes / per));
     void *ws = bt->workspace;
     if (ws) {
         if (((uintptr_t)ws & 255) != 0)
@@ -657,7 +664,9 @@ exago_status exago_eval_cart_workspace_size(exago_net_t net, int B, size_t *byte
         return set_last_error(net ? EXAGO_ESTATE : EXAGO_EINVAL,
                               net ? "net was planned without a device" : "net is NULL");
     if (B < 0) return set_last_error(EXAGO_EINVAL, "B < 0");
-    *bytes = B == 0 ? 0 : (size_t)chunk_states(*dev, B) * record_bytes(*dev);
+    const int chunk = B == 0 ? 0 : chunk_states(*dev, B);
+    const int ring = chunk == 0 ? 0 : std::min(kRing, (B + chunk - 1) / chunk);
+    *bytes = (size_t)ring * chunk * record_bytes(*dev);
     return EXAGO_OK;
 }
 
@@ -680,15 +689,18 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
     const bool rows = gh || jval || hval || grad;
     if (rows && N.nb > 0) {
         const int chunk = chunk_states(N, bt->B);
-        const size_t need = (size_t)chunk * record_bytes(N);
+        const size_t chunk_bytes = (size_t)chunk * record_bytes(N);
+        const int nchunks = (bt->B + chunk - 1) / chunk;
+        int ring = std::min(kRing, nchunks);
         void *ws = bt->workspace;
         if (ws) {
             if (((uintptr_t)ws & 255) != 0)
                 return set_last_error(EXAGO_EINVAL, "workspace not 256-byte aligned");
-            if (bt->workspace_bytes < need)
+            if (bt->workspace_bytes < chunk_bytes)
                 return set_last_error(EXAGO_EINVAL, "workspace smaller than exago_eval_cart_workspace_size");
-        } else if (need > 0) {
-            exago_status s = net_workspace(net, need, &ws);
+            ring = (int)std::min<size_t>((size_t)ring, bt->workspace_bytes / std::max<size_t>(chunk_bytes, 1));
+        } else if (chunk_bytes > 0) {
+            exago_status s = net_workspace(net, (size_t)ring * chunk_bytes, &ws);
             if (s != EXAGO_OK) return s;
         }
         CartReq R{};
@@ -698,17 +710,47 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
         R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask; R.gen_mask = bt->gen_mask;
         R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
         R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
-        R.scratch = (double *)ws;
-        for (int b0 = 0; b0 < bt->B; b0 += chunk) {
-            const int nB = std::min(chunk, bt->B - b0);
-            R.b0 = b0;
-            const int br_items = nB * ((N.nl + 127) / 128), bus_items = nB * ((N.nb + 127) / 128);
-            if (N.nl > 0)
-                k_cart_branch<<<std::min(br_items, resident_ctas((const void *)k_cart_branch, 0)),
-                                128, 0, st>>>(N, R, nB);
-            k_cart_bus<<<std::min(bus_items, resident_ctas((const void *)k_cart_bus, 1)), 128, 0,
-                         st>>>(N, R, nB);
-        }
+        const int br_ctas = resident_ctas((const void *)k_cart_branch, 0);
+        const int bu_ctas = resident_ctas((const void *)k_cart_bus, 1);
+        // chunk k: branch kernel on `main`, then its bus kernel on `side` (after an event), so the
+        // FP64-bound branch work of chunk k + 1 overlaps the latency-bound bus work of chunk k;
+        // the branch kernel of chunk k waits for the bus kernel of chunk k - ring, whose ring
+        // slot it overwrites.  With one chunk or one ring slot everything runs on `main`.
+        auto run = [&](cudaStream_t main, cudaStream_t side, const PipeLaunch *pl) {
+            if (pl) {
+                cudaEventRecord(pl->ev_fork, main);
+                cudaStreamWaitEvent(side, pl->ev_fork, 0);
+            }
+            for (int k = 0; k < nchunks; k++) {
+                const int b0 = k * chunk, nB = std::min(chunk, bt->B - b0);
+                CartReq Rk = R;
+                Rk.b0 = b0;
+                Rk.scratch = (double *)ws + (size_t)(k % ring) * chunk * N.nslot * CNC;
+                const int br_items = nB * ((N.nl + 127) / 128), bus_items = nB * ((N.nb + 127) / 128);
+                if (pl && k >= ring) cudaStreamWaitEvent(main, pl->ev_bu[(k - ring) % (ring + 1)], 0);
+                if (N.nl > 0)
+                    k_cart_branch<<<std::min(br_items, br_ctas), 128, 0, main>>>(N, Rk, nB);
+                cudaStream_t bs = main;
+                if (pl) {
+                    cudaEventRecord(pl->ev_br[k % (ring + 1)], main);
+                    cudaStreamWaitEvent(side, pl->ev_br[k % (ring + 1)], 0);
+                    bs = side;
+                }
+                k_cart_bus<<<std::min(bus_items, bu_ctas), 128, 0, bs>>>(N, Rk, nB);
+                if (pl) cudaEventRecord(pl->ev_bu[k % (ring + 1)], side);
+            }
+            if (pl) {
+                cudaEventRecord(pl->ev_join, side);
+                cudaStreamWaitEvent(main, pl->ev_join, 0);
+            }
+            return EXAGO_OK;
+        };
+        exago_status s = EXAGO_OK;
+        if (nchunks > 1 && ring > 1)
+            s = with_net_pipeline(net, [&](const PipeLaunch &pl) { return run(st, pl.side, &pl); });
+        else
+            s = run(st, st, nullptr);
+        if (s != EXAGO_OK) return s;
     }
     if (f) {
         EvalReq E{};

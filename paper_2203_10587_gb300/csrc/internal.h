@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -207,6 +208,11 @@ int bus_blocks_per_sm(size_t smem_bytes);   // k_bus blocks of 128 threads per S
 // thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.
 bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **dev, int *device);
 exago_status set_last_error(exago_status s, const std::string &msg);
+// Runs fn with the net's lock held and its two-stream pipeline resources (a high-priority side
+// stream and events; PipeLaunch's chunk and ring are left 0) created on first use: for schedules
+// in other translation units that overlap two kernels on two streams.
+exago_status with_net_pipeline(exago_net_t net,
+                               const std::function<exago_status(const PipeLaunch &)> &fn);
 // The net's internal workspace, grown to at least `bytes` (a growth synchronises the device first,
 // as in the evaluations); calls that use it must be ordered like the evaluations.
 exago_status net_workspace(exago_net_t net, size_t bytes, void **ws);
