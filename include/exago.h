@@ -224,7 +224,9 @@ exago_status exago_eval_hvp(exago_net_t net, const exago_batch *batch, const dou
  *                               branch kernel writes records and a bus kernel assembles the rows;
  *                               the bus kernel of a chunk runs on the net's side stream while the
  *                               next chunk's branch kernel runs on batch->stream (ordered by
- *                               events; the call returns with all work ordered on batch->stream);
+ *                               events; the call returns with all work ordered on batch->stream;
+ *                               the call may be captured in a CUDA graph once a first call outside
+ *                               the capture has grown the workspace, or with a batch->workspace);
  *                               the persistent schedule and the graph cache are the polar
  *                               model's only.
  */
