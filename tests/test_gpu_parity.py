@@ -273,3 +273,23 @@ def test_10k_bus_64_scenarios_sampled(ex, oracle_mod):
     out = gpu_eval(net, b)
     for i in [0, 31, 63]:
         compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), "scenarios")
+
+
+@pytest.mark.parametrize("grid,batch,cfg,sample", [
+    # the launch configuration bench.py times on the 2,000-bus x 512 N-1 workload
+    ("2000", "n1", dict(schedule=2, block=64, occupancy=16, stage_records=2, tile_group=1),
+     [0, 255, 511]),
+    # the configuration the autotuner picks for the 10,000-bus x 64 scenario workload
+    ("10k", "scen", dict(schedule=2, block=128, occupancy=16, tile_group=1), [0, 63]),
+])
+def test_full_size_in_the_benchmarked_configuration(ex, oracle_mod, grid, batch, cfg, sample):
+    g = synth.grid_2000() if grid == "2000" else synth.grid_10k()
+    b = synth.contingency_batch(3, g, 512) if batch == "n1" else synth.scenario_batch(4, g, 64)
+    net = ex.Net(g)
+    default = gpu_eval(net, b)
+    ex.exago_net_set_config(net.h, **cfg)
+    out = gpu_eval(net, b)
+    for k in default:
+        np.testing.assert_array_equal(out[k], default[k], err_msg=k)
+    for i in sample:
+        compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"benchmarked config [{i}]")
