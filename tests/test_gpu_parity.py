@@ -293,3 +293,27 @@ def test_full_size_in_the_benchmarked_configuration(ex, oracle_mod, grid, batch,
         np.testing.assert_array_equal(out[k], default[k], err_msg=k)
     for i in sample:
         compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"benchmarked config [{i}]")
+
+
+def test_batch_keeps_its_tensors_alive(ex, oracle_mod):
+    """make_batch holds references to the tensors whose device pointers it stores: a batch built
+    from temporaries stays valid after the caller's references are gone and new allocations
+    have been made."""
+    import gc
+    import torch
+    g = synth.make_grid(131, 120, 160, 30, shunts=True)
+    b = synth.random_batch(131, g, 3, masks=True, sigma=0.7)
+    net = ex.Net(g)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    bt = ex.make_batch(t(b.x, torch.float64), t(b.lam, torch.float64), t(b.mask, torch.uint8),
+                       obj_factor=b.sigma)
+    gc.collect()
+    junk = [torch.full((b.B, g.n), np.nan, dtype=torch.float64, device="cuda") for _ in range(8)]
+    out = net.outputs(b.B)
+    net.eval_all(bt, out)
+    torch.cuda.synchronize()
+    host = {k: v.cpu().numpy() for k, v in out.items()}
+    for i in range(b.B):
+        compare_instance(host, i, oracle_eval(oracle_mod, g, b, i), f"temporaries [{i}]")
+    del junk
+    net.close()
