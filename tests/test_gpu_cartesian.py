@@ -226,3 +226,24 @@ def test_cartesian_autograd_double_backward(ex, oracle_mod):
         assert_close(gx[i], J.T @ v[i], f"autograd J' v [{i}]")
         assert_close(hw[i], H @ w[i], f"autograd H w [{i}]")
     net.close()
+
+
+def test_cartesian_ring_and_caller_workspace(ex):
+    """The two-stream schedule over 5 chunks (ring slots reused) with a caller workspace of the
+    full size, and with one chunk's worth (a single ring slot: everything on the caller's
+    stream), equals the internal workspace bit for bit."""
+    import torch
+    g = synth.grid_2000()
+    b = synth.contingency_batch(7, g, 190)        # 41-state chunks: 5 chunks, ring of 3
+    x, lam = to_cartesian(g, b, 7)
+    net = ex.Net(g)
+    ref = run_cart(ex, net, b, x, lam)
+    full = ex.exago_eval_cart_workspace_size(net.h, b.B)
+    one = ex.exago_eval_cart_workspace_size(net.h, 41)
+    assert full == 3 * one
+    for nbytes in (full, one):
+        ws = torch.empty(nbytes // 8, dtype=torch.float64, device="cuda")
+        got = run_cart(ex, net, b, x, lam, workspace=ws)
+        for k in ref:
+            np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{k} ({nbytes} bytes)")
+    net.close()
