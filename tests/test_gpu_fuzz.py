@@ -88,3 +88,27 @@ def test_random_irregular_grid_and_configuration(ex, oracle_mod, case):
     out = gpu_eval(net, b)
     for i in sorted({0, B - 1, int(rng.integers(B))}):
         compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"case {case} {cfg} [{i}]")
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_random_grids_with_generator_outages_both_formulations(ex, oracle_mod, case):
+    """The same kind of irregular grids with random generator outages (about 20% of the
+    generators out, a separate mask per state): the polar model under a random launch
+    configuration, and the cartesian model at the same operating points, against the oracle."""
+    from test_gpu_cartesian import oracle_cart, run_cart, to_cartesian
+    rng = np.random.default_rng(3000 + case)
+    g = irregular_grid(rng, 3000 + case)
+    B = int(rng.integers(1, 12))
+    b = synth.random_batch(4000 + case, g, B, masks=True, pd_scale=bool(rng.integers(2)),
+                           obj_weight=bool(rng.integers(2)), sigma=float(rng.choice([0.0, 0.6, 1.0])),
+                           gen_masks=True)
+    net = ex.Net(g)
+    cfg = random_config(rng)
+    ex.exago_net_set_config(net.h, **cfg)
+    out = gpu_eval(net, b)
+    x, lam = to_cartesian(g, b, 5000 + case)
+    cart = run_cart(ex, net, b, x, lam)
+    for i in sorted({0, B - 1, int(rng.integers(B))}):
+        compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"case {case} {cfg} [{i}]")
+        ref = oracle_cart(oracle_mod, g, b, x, lam, i)
+        compare_instance(cart, i, ref, f"cartesian case {case} [{i}]")
