@@ -84,3 +84,37 @@ def test_serve_arena_allocation_failure(ex):
         ex.exago_test_fail_allocations(0)
     srv = ex.exago_serve_create(1 << 20, 1, 1)
     ex.exago_serve_destroy(srv)
+
+
+def test_coupling_slack_and_cartesian_allocation_failures(ex):
+    """The coupling rows' and the slacks' device tables, and the cartesian schedule's workspace
+    growth: each failed allocation returns EXAGO_ENOMEM, and the same call then succeeds."""
+    import torch
+    g = synth.make_grid(141, 120, 160, 30)
+    net = ex.Net(g)
+    parent = synth.coupling_parents("chain", 6)
+    for make in (lambda: ex.Coupling(net, parent),
+                 lambda: ex.Slack(net, [0, 1], [0, 1], [-1, 1], [1.0, 2.0])):
+        ex.exago_test_fail_allocations(1)
+        try:
+            with pytest.raises(ex.ExagoError) as ei:
+                make()
+            assert ei.value.name == "EXAGO_ENOMEM"
+        finally:
+            ex.exago_test_fail_allocations(0)
+        make().close()
+    b = synth.random_batch(141, g, 4)
+    x = torch.as_tensor(b.x, device="cuda")
+    gh = torch.empty(4, g.m + g.nb, dtype=torch.float64, device="cuda")
+    bt = ex.make_batch(x)
+    ex.exago_test_fail_allocations(1)        # the net has no workspace yet: growth fails
+    try:
+        with pytest.raises(ex.ExagoError) as ei:
+            ex.exago_eval_cart(net.h, bt, gh=gh)
+        assert ei.value.name == "EXAGO_ENOMEM"
+    finally:
+        ex.exago_test_fail_allocations(0)
+    ex.exago_eval_cart(net.h, bt, gh=gh)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(gh.cpu().numpy()))
+    net.close()
