@@ -247,3 +247,22 @@ def test_cartesian_ring_and_caller_workspace(ex):
         for k in ref:
             np.testing.assert_array_equal(got[k], ref[k], err_msg=f"{k} ({nbytes} bytes)")
     net.close()
+
+
+def test_cartesian_30bus_against_golden(ex):
+    """The 30-bus cartesian snapshot written by the oracle-only golden script."""
+    import json
+    import os
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    sys.path.insert(0, os.path.join(here, "golden"))
+    import make_golden
+    g, b, x, lam = make_golden.cartesian_cases()
+    stored = json.load(open(os.path.join(here, "golden", "c1_30bus_cartesian.json")))["instances"]
+    net = ex.Net(g)
+    out = run_cart(ex, net, b, x, lam)
+    for i, s in enumerate(stored):
+        ref = {"f": s["f"], "grad": np.array(s["grad"]), "gh": np.array(s["gh"]),
+               "J": (None, None, np.array(s["J_val"])), "H": (None, None, np.array(s["H_val"]))}
+        compare(out, ref, i, "cartesian golden")
+    net.close()
