@@ -266,3 +266,32 @@ def test_cartesian_30bus_against_golden(ex):
                "J": (None, None, np.array(s["J_val"])), "H": (None, None, np.array(s["H_val"]))}
         compare(out, ref, i, "cartesian golden")
     net.close()
+
+
+def test_cartesian_adjoints_in_chunks(ex):
+    """A caller workspace that holds the branch values of 41 states splits the adjoint products of
+    190 states into 5 chunks; the results equal one chunk bit for bit."""
+    import torch
+    g = synth.grid_2000()
+    b = synth.contingency_batch(9, g, 190)
+    x, lam = to_cartesian(g, b, 9)
+    mc = g.m + g.nb
+    rng = np.random.default_rng(9)
+    U = torch.as_tensor(rng.normal(size=(b.B, g.n)), device="cuda")
+    V = torch.as_tensor(rng.normal(size=(b.B, mc)), device="cuda")
+    X, LAM = torch.as_tensor(x, device="cuda"), torch.as_tensor(lam, device="cuda")
+    M = torch.as_tensor(b.mask, device="cuda")
+    net = ex.Net(g)
+    ws = torch.empty(41 * g.nl * 4, dtype=torch.float64, device="cuda")
+    res = []
+    for workspace in (None, ws):
+        bt = ex.make_batch(X, LAM, M, obj_factor=0.7, workspace=workspace)
+        o = [torch.empty(b.B, k, dtype=torch.float64, device="cuda") for k in (mc, g.n, g.n)]
+        ex.exago_eval_cart_jvp(net.h, bt, U, o[0])
+        ex.exago_eval_cart_jtv(net.h, bt, V, o[1])
+        ex.exago_eval_cart_hvp(net.h, bt, U, o[2])
+        torch.cuda.synchronize()
+        res.append([t.cpu().numpy() for t in o])
+    for a, c in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, c)
+    net.close()

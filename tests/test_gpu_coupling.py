@@ -205,3 +205,12 @@ def test_coupling_autograd(ex, oracle_mod):
     np.testing.assert_array_equal(gv.cpu().numpy(), oracle_mod.coupling(parent, w.cpu().numpy(), g.nb, g.ng))
     cpl.close()
     net.close()
+
+
+def test_coupling_more_states_than_one_grid_row(ex, oracle_mod):
+    """70,000 states (more than one launch's 65,535 grid rows): a chain of 40,000 periods and a
+    star of 30,000 contingencies around state 40,000, on the 30-bus grid."""
+    parent = np.concatenate([synth.coupling_parents("chain", 40_000),
+                             np.full(30_000, 40_000, np.int32)])
+    parent[40_000] = -1
+    run_case(ex, oracle_mod, synth.grid_30bus(), parent, seed=71)

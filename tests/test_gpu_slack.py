@@ -118,3 +118,37 @@ def test_slacks_on_cartesian_rows_and_empty(ex, oracle_mod):
         ex.exago_eval_slack(s2, bt, torch.as_tensor(z, device="cuda"), GH, 2 * g.nb - 1)
     empty.close()
     net.close()
+
+
+def test_slacks_more_states_than_one_grid_row(ex, oracle_mod):
+    """70,000 states on the 30-bus grid (several launches per call): balance terms, gradient and
+    transpose bit for bit, the objective within the tolerance."""
+    import torch
+    g = synth.grid_30bus()
+    B = 70_000
+    bus, row, sign, cost = slack_set(g, 131)
+    nz = bus.shape[0]
+    rng = np.random.default_rng(132)
+    z = rng.uniform(0.0, 0.2, (B, nz))
+    gh0 = rng.normal(size=(B, g.m))
+    f0 = rng.normal(size=B)
+    net = ex.Net(g)
+    sl = ex.Slack(net, bus, row, sign, cost)
+    x = torch.zeros(B, g.n, dtype=torch.float64, device="cuda")
+    bt = ex.make_batch(x)
+    GH, F = torch.as_tensor(gh0.copy(), device="cuda"), torch.as_tensor(f0.copy(), device="cuda")
+    GZ = torch.empty(B, nz, dtype=torch.float64, device="cuda")
+    ex.exago_eval_slack(sl, bt, torch.as_tensor(z, device="cuda"), GH, g.m, F, GZ)
+    JT = torch.empty(B, nz, dtype=torch.float64, device="cuda")
+    ex.exago_eval_slack_jtv(sl, bt, torch.as_tensor(gh0, device="cuda"), g.m, JT)
+    torch.cuda.synchronize()
+    gh, f, gz, jt = GH.cpu().numpy(), F.cpu().numpy(), GZ.cpu().numpy(), JT.cpu().numpy()
+    for i in (0, 65_534, 65_535, 65_536, B - 1):
+        ref_gh, ref_f, ref_g = oracle_mod.slack(g.nb, bus, row, sign, cost, z[i],
+                                                gh=gh0[i, :2 * g.nb], f=f0[i])
+        np.testing.assert_array_equal(gh[i, :2 * g.nb], ref_gh)
+        assert_close(f[i], ref_f, f"f [{i}]")
+        np.testing.assert_array_equal(gz[i], ref_g)
+        np.testing.assert_array_equal(jt[i], sign * gh0[i, row * g.nb + bus])
+    sl.close()
+    net.close()
