@@ -28,8 +28,9 @@
  *
  * Threading and streams: every function may be called from any host thread.  Evaluation calls
  * are asynchronous on the stream given in the batch; host-side argument errors return at once.
- * Calls that share one net and no caller workspace must be ordered (one stream, or events):
- * they share the net's internal workspace.  Errors raised inside kernels (a bounded wait that
+ * Calls that share one net and no caller workspace share the net's internal workspace; the
+ * library orders them across streams and threads (exago_batch, `workspace`), except calls
+ * captured into a caller's CUDA graph, which the caller orders.  Errors raised inside kernels (a bounded wait that
  * timed out) are recorded in a device status word and returned by exago_net_check.
  * Every function returns EXAGO_OK or an error code; exago_last_error() then describes it.
  */
@@ -138,7 +139,14 @@ exago_status exago_net_plan_array(exago_net_t net, const char *name, void *dst, 
  *   workspace            optional device scratch of at least exago_eval_workspace_size bytes,
  *                        256-byte aligned; NULL = use the net's internal workspace, grown on
  *                        demand (a growth calls cudaMalloc; use exago_net_reserve before any
- *                        stream capture)
+ *                        stream capture).  Calls that use the internal workspace are ordered by
+ *                        the library: a call on another stream than the workspace's last user
+ *                        first waits (on the device) for that use, and a growth waits for every
+ *                        earlier use before it frees the old buffer, so such calls may come from
+ *                        any stream and any host thread.  Calls captured into a caller's CUDA
+ *                        graph are outside this ordering: the caller orders their replays against
+ *                        other calls on the same net (and a growth after such a capture drains
+ *                        the device).  Calls with their own `workspace` share nothing.
  *   gen_mask   [B][ng]   1 in service, 0 out of service (a generator outage, alone or with line
  *                        outages: SCOPFLOW contingencies, Sec. V-A); NULL = all 1.  An
  *                        out-of-service generator contributes nothing: no injection in its bus's
@@ -345,7 +353,8 @@ exago_status exago_eval_coupling_jtv(exago_coupling_t cpl, const double *nu, dou
  *     address (cudaGetSymbolAddress) once for that device; make that first call before any stream
  *     capture.
  *   - EINVAL if the batch's scratch exceeds the array: split the batch.  Each state needs
- *     12 x 2 nl doubles of branch-end records (the batch's total rounded up to 256 bytes).
+ *     10 x 2 nl doubles of branch-end records (80 bytes per branch end; the batch's total is
+ *     rounded up to 256 bytes).
  *   - All calls share the array: calls that overlap on the GPU race on it, so order them (one
  *     stream, or events).  Nothing in it needs clearing; each call writes all the scratch it reads.
  */

@@ -81,6 +81,12 @@ struct exago_net {
     int *status_host = nullptr;   // host-mapped device status word
     void *ws = nullptr;           // internal workspace
     size_t ws_bytes = 0;
+    // Stream order of the internal workspace's users: every uncaptured call that uses it records
+    // ws_ev on its stream, and a call on another stream first waits for that event.  ws_captured:
+    // some use was captured into a caller's graph, whose replays the event cannot see.
+    cudaEvent_t ws_ev = nullptr;
+    cudaStream_t ws_stream = nullptr;
+    bool ws_captured = false;
     std::mutex mu;                // guards the workspace, the graph cache and the configuration
     exago_config cfg{};           // user configuration (zeros = automatic)
     std::map<int, exago_config> tuned;   // autotuned configuration per batch size
@@ -138,6 +144,8 @@ void free_device(exago_net *net) {
     if (net->ws) cudaFree(net->ws);
     net->ws = nullptr;
     net->ws_bytes = 0;
+    if (net->ws_ev) cudaEventDestroy(net->ws_ev);
+    net->ws_ev = nullptr;
     if (net->status_host) cudaFreeHost(net->status_host);
     net->status_host = nullptr;
     net->on_device = false;
@@ -380,8 +388,12 @@ exago_status check_batch(exago_net *net, const exago_batch *bt, bool need_lam) {
 exago_status ensure_workspace_locked(exago_net *net, size_t need) {
     if (net->ws_bytes >= need) return EXAGO_OK;
     if (net->ws) {
-        cudaError_t e = cudaDeviceSynchronize();   // earlier work may still use the old buffer
-        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize (workspace growth)");
+        // Earlier work may still use the old buffer.  Uncaptured uses are chained through ws_ev
+        // (ws_acquire_locked), so its last record covers them all; a use captured into a
+        // caller's graph is not, and then the whole device is drained.
+        cudaError_t e = net->ws_captured || !net->ws_ev ? cudaDeviceSynchronize()
+                                                        : cudaEventSynchronize(net->ws_ev);
+        if (e != cudaSuccess) return cuda_fail(e, "synchronisation before workspace growth");
         cudaFree(net->ws);
         net->ws = nullptr;
         net->ws_bytes = 0;
@@ -392,6 +404,43 @@ exago_status ensure_workspace_locked(exago_net *net, size_t need) {
         return cuda_fail(e, "cudaMalloc (workspace)");
     }
     net->ws_bytes = need;
+    return EXAGO_OK;
+}
+
+// Before a call queues work that uses the internal workspace on `st`: waits (on the device) for
+// the last uncaptured use on another stream.  Caller holds net->mu.
+exago_status ws_acquire_locked(exago_net *net, cudaStream_t st, bool capturing) {
+    if (capturing) {
+        net->ws_captured = true;
+        return EXAGO_OK;
+    }
+    if (!net->ws_ev) {
+        cudaError_t e = cudaEventCreateWithFlags(&net->ws_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate (workspace order)");
+        return EXAGO_OK;
+    }
+    if (net->ws_stream != st) {
+        cudaError_t e = cudaStreamWaitEvent(st, net->ws_ev, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent (workspace order)");
+    }
+    return EXAGO_OK;
+}
+
+// After a call has queued its work that uses the internal workspace on `st`.  Caller holds
+// net->mu.
+exago_status ws_release_locked(exago_net *net, cudaStream_t st, bool capturing) {
+    if (capturing) return EXAGO_OK;
+    cudaError_t e = cudaEventRecord(net->ws_ev, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord (workspace order)");
+    net->ws_stream = st;
+    return EXAGO_OK;
+}
+
+exago_status is_capturing(cudaStream_t st, bool *capturing) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    *capturing = cap != cudaStreamCaptureStatusNone;
     return EXAGO_OK;
 }
 
@@ -494,6 +543,12 @@ exago_status pipe_resources_locked(exago_net *net, PipeLaunch &pl) {
     return EXAGO_OK;
 }
 
+exago_status eval_locked(exago_net *net, const exago_batch *bt, double *f, double *grad,
+                         double *gh, double *jval, double *hval, ProfileHook *hook,
+                         bool allow_graph, const StateTab *tab, const Resolved &rs, void *ws);
+
+// One evaluation call.  With the internal workspace, the call is ordered after the last use of
+// that workspace on any other stream (ws_acquire_locked).
 exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad, double *gh,
                   double *jval, double *hval, ProfileHook *hook = nullptr, bool allow_graph = true,
                   const StateTab *tab = nullptr) {
@@ -503,10 +558,21 @@ exago_status eval(exago_net *net, const exago_batch *bt, double *f, double *grad
     const Resolved rs = resolve(net, bt->B);
     void *ws = bt->workspace;
     const bool needs_ws = gh || jval || hval || rs.schedule == EXAGO_SCHED_PERSISTENT;
-    if (!ws && needs_ws) {
-        if ((s = ensure_workspace_locked(net, need_bytes(net, bt->B))) != EXAGO_OK) return s;
-        ws = net->ws;
-    }
+    if (ws || !needs_ws) return eval_locked(net, bt, f, grad, gh, jval, hval, hook, allow_graph, tab, rs, ws);
+    if ((s = ensure_workspace_locked(net, need_bytes(net, bt->B))) != EXAGO_OK) return s;
+    const cudaStream_t st = (cudaStream_t)bt->stream;
+    bool capturing = false;
+    if ((s = is_capturing(st, &capturing)) != EXAGO_OK) return s;
+    if ((s = ws_acquire_locked(net, st, capturing)) != EXAGO_OK) return s;
+    s = eval_locked(net, bt, f, grad, gh, jval, hval, hook, allow_graph, tab, rs, net->ws);
+    const exago_status r = ws_release_locked(net, st, capturing);
+    return s != EXAGO_OK ? s : r;
+}
+
+exago_status eval_locked(exago_net *net, const exago_batch *bt, double *f, double *grad,
+                         double *gh, double *jval, double *hval, ProfileHook *hook,
+                         bool allow_graph, const StateTab *tab, const Resolved &rs, void *ws) {
+    exago_status s = EXAGO_OK;
     EvalReq R{};
     R.B = bt->B;
     R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask; R.gen_mask = bt->gen_mask;
@@ -582,20 +648,27 @@ bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **de
 
 exago_status set_last_error(exago_status s, const std::string &msg) { return fail(s, msg); }
 
-exago_status with_net_pipeline(exago_net_t net,
-                                const std::function<exago_status(const PipeLaunch &)> &fn) {
+int multi_kernel_stage_cap(exago_net_t net) {
     std::lock_guard<std::mutex> lk(net->mu);
-    PipeLaunch pl{};
-    exago_status s = pipe_resources_locked(net, pl);
-    if (s != EXAGO_OK) return s;
-    return fn(pl);
+    return stage_cap(net, false, 128, 16, false);
 }
 
-exago_status net_workspace(exago_net_t net, size_t bytes, void **ws) {
+exago_status with_net_workspace(exago_net_t net, void *caller_ws, size_t bytes, cudaStream_t st,
+                                bool pipeline,
+                                const std::function<exago_status(void *, const PipeLaunch *)> &fn) {
     std::lock_guard<std::mutex> lk(net->mu);
-    exago_status s = ensure_workspace_locked(net, bytes);
-    *ws = s == EXAGO_OK ? net->ws : nullptr;
-    return s;
+    PipeLaunch pl{};
+    exago_status s = EXAGO_OK;
+    if (pipeline && (s = pipe_resources_locked(net, pl)) != EXAGO_OK) return s;
+    const PipeLaunch *plp = pipeline ? &pl : nullptr;
+    if (caller_ws || bytes == 0) return fn(caller_ws, plp);
+    if ((s = ensure_workspace_locked(net, bytes)) != EXAGO_OK) return s;
+    bool capturing = false;
+    if ((s = is_capturing(st, &capturing)) != EXAGO_OK) return s;
+    if ((s = ws_acquire_locked(net, st, capturing)) != EXAGO_OK) return s;
+    s = fn(net->ws, plp);
+    const exago_status r = ws_release_locked(net, st, capturing);
+    return s != EXAGO_OK ? s : r;
 }
 
 exago_status eval_direct(exago_net_t net, const exago_batch *bt, double *f, double *grad,
@@ -819,9 +892,14 @@ exago_status adjoint(exago_net *net, const exago_batch *bt, const double *v, dou
     if (!v || !out) return fail(EXAGO_EINVAL, "input or output vector is NULL");
     void *ws = bt->workspace;
     std::lock_guard<std::mutex> lk(net->mu);
-    if (!ws) {
+    const cudaStream_t st = (cudaStream_t)bt->stream;
+    bool capturing = false;
+    const bool internal = ws == nullptr;
+    if (internal) {
         if ((s = ensure_workspace_locked(net, need_bytes(net, bt->B))) != EXAGO_OK) return s;
         ws = net->ws;
+        if ((s = is_capturing(st, &capturing)) != EXAGO_OK) return s;
+        if ((s = ws_acquire_locked(net, st, capturing)) != EXAGO_OK) return s;
     }
     AdjReq A{};
     A.B = bt->B;
@@ -831,8 +909,9 @@ exago_status adjoint(exago_net *net, const exago_batch *bt, const double *v, dou
     A.v = v; A.out = out;
     A.scratch = (double *)ws;
     int e = launch_adjoint(net->dev, A, mode, bt->stream);
+    const exago_status r = internal ? ws_release_locked(net, st, capturing) : EXAGO_OK;
     if (e != 0) return cuda_fail((cudaError_t)e, "adjoint kernel launch");
-    return EXAGO_OK;
+    return r;
 }
 
 }  // namespace

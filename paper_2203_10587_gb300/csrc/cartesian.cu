@@ -584,37 +584,38 @@ exago_status cart_adjoint(exago_net_t net, const exago_batch *bt, const double *
         if (bt->workspace_bytes < per)
             return set_last_error(EXAGO_EINVAL, "workspace smaller than one state's branch values");
         chunk = (int)std::min<size_t>((size_t)chunk, bt->workspace_bytes / per);
-    } else {
-        exago_status s = net_workspace(net, (size_t)chunk * per, &ws);
-        if (s != EXAGO_OK) return s;
     }
-    CartAdjReq A{};
-    A.mc = N.m + N.nb;
-    A.x = bt->x; A.lam = bt->lambda; A.mask = bt->mask; A.gen_mask = bt->gen_mask;
-    A.obj_weight = bt->obj_weight; A.sigma = bt->obj_factor;
-    A.v = in; A.out = out;
-    A.scratch = (double *)ws;
     cudaStream_t st = (cudaStream_t)bt->stream;
-    for (int b0 = 0; b0 < bt->B; b0 += chunk) {
-        const int nB = std::min(chunk, bt->B - b0);
-        A.b0 = b0;
-        const dim3 gbr((N.nl + 127) / 128, nB), gbu((N.nb + 127) / 128, nB);
-        if (mode == CADJ_JVP) {
-            if (N.nl > 0) k_cart_adj_branch<CADJ_JVP><<<gbr, 128, 0, st>>>(N, A);
-            k_cart_adj_bus<CADJ_JVP><<<gbu, 128, 0, st>>>(N, A);
-        } else if (mode == CADJ_JTV) {
-            if (N.nl > 0) k_cart_adj_branch<CADJ_JTV><<<gbr, 128, 0, st>>>(N, A);
-            k_cart_adj_bus<CADJ_JTV><<<gbu, 128, 0, st>>>(N, A);
-        } else {
-            if (N.nl > 0) k_cart_adj_branch<CADJ_HVP><<<gbr, 128, 0, st>>>(N, A);
-            k_cart_adj_bus<CADJ_HVP><<<gbu, 128, 0, st>>>(N, A);
+    // the net's lock stays held until every kernel that uses its workspace is queued
+    return with_net_workspace(net, ws, (size_t)chunk * per, st, false,
+                              [&](void *w, const PipeLaunch *) -> exago_status {
+        CartAdjReq A{};
+        A.mc = N.m + N.nb;
+        A.x = bt->x; A.lam = bt->lambda; A.mask = bt->mask; A.gen_mask = bt->gen_mask;
+        A.obj_weight = bt->obj_weight; A.sigma = bt->obj_factor;
+        A.v = in; A.out = out;
+        A.scratch = (double *)w;
+        for (int b0 = 0; b0 < bt->B; b0 += chunk) {
+            const int nB = std::min(chunk, bt->B - b0);
+            A.b0 = b0;
+            const dim3 gbr((N.nl + 127) / 128, nB), gbu((N.nb + 127) / 128, nB);
+            if (mode == CADJ_JVP) {
+                if (N.nl > 0) k_cart_adj_branch<CADJ_JVP><<<gbr, 128, 0, st>>>(N, A);
+                k_cart_adj_bus<CADJ_JVP><<<gbu, 128, 0, st>>>(N, A);
+            } else if (mode == CADJ_JTV) {
+                if (N.nl > 0) k_cart_adj_branch<CADJ_JTV><<<gbr, 128, 0, st>>>(N, A);
+                k_cart_adj_bus<CADJ_JTV><<<gbu, 128, 0, st>>>(N, A);
+            } else {
+                if (N.nl > 0) k_cart_adj_branch<CADJ_HVP><<<gbr, 128, 0, st>>>(N, A);
+                k_cart_adj_bus<CADJ_HVP><<<gbu, 128, 0, st>>>(N, A);
+            }
         }
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return set_last_error(EXAGO_ECUDA, std::string("cartesian adjoint launch: ") +
-                                               cudaGetErrorString(e));
-    return EXAGO_OK;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return set_last_error(EXAGO_ECUDA, std::string("cartesian adjoint launch: ") +
+                                                   cudaGetErrorString(e));
+        return EXAGO_OK;
+    });
 }
 
 }  // namespace
@@ -699,9 +700,6 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
             if (bt->workspace_bytes < chunk_bytes)
                 return set_last_error(EXAGO_EINVAL, "workspace smaller than exago_eval_cart_workspace_size");
             ring = (int)std::min<size_t>((size_t)ring, bt->workspace_bytes / std::max<size_t>(chunk_bytes, 1));
-        } else if (chunk_bytes > 0) {
-            exago_status s = net_workspace(net, (size_t)ring * chunk_bytes, &ws);
-            if (s != EXAGO_OK) return s;
         }
         CartReq R{};
         R.B = bt->B;
@@ -716,7 +714,7 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
         // FP64-bound branch work of chunk k + 1 overlaps the latency-bound bus work of chunk k;
         // the branch kernel of chunk k waits for the bus kernel of chunk k - ring, whose ring
         // slot it overwrites.  With one chunk or one ring slot everything runs on `main`.
-        auto run = [&](cudaStream_t main, cudaStream_t side, const PipeLaunch *pl) {
+        auto run = [&](void *ws, cudaStream_t main, cudaStream_t side, const PipeLaunch *pl) {
             if (pl) {
                 cudaEventRecord(pl->ev_fork, main);
                 cudaStreamWaitEvent(side, pl->ev_fork, 0);
@@ -745,11 +743,13 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
             }
             return EXAGO_OK;
         };
-        exago_status s = EXAGO_OK;
-        if (nchunks > 1 && ring > 1)
-            s = with_net_pipeline(net, [&](const PipeLaunch &pl) { return run(st, pl.side, &pl); });
-        else
-            s = run(st, st, nullptr);
+        // the net's lock stays held until every kernel that uses its workspace is queued
+        const bool pipe = nchunks > 1 && ring > 1;
+        exago_status s = with_net_workspace(
+            net, ws, (size_t)ring * chunk_bytes, st, pipe,
+            [&](void *w, const PipeLaunch *pl) {
+                return pl ? run(w, st, pl->side, pl) : run(w, st, st, nullptr);
+            });
         if (s != EXAGO_OK) return s;
     }
     if (f) {

@@ -208,14 +208,17 @@ int bus_blocks_per_sm(size_t smem_bytes);   // k_bus blocks of 128 threads per S
 // thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.
 bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **dev, int *device);
 exago_status set_last_error(exago_status s, const std::string &msg);
-// Runs fn with the net's lock held and its two-stream pipeline resources (a high-priority side
-// stream and events; PipeLaunch's chunk and ring are left 0) created on first use: for schedules
-// in other translation units that overlap two kernels on two streams.
-exago_status with_net_pipeline(exago_net_t net,
-                               const std::function<exago_status(const PipeLaunch &)> &fn);
-// The net's internal workspace, grown to at least `bytes` (a growth synchronises the device first,
-// as in the evaluations); calls that use it must be ordered like the evaluations.
-exago_status net_workspace(exago_net_t net, size_t bytes, void **ws);
+// Shared-memory doubles of a bus tile of the multi-kernel schedule's bus kernel (128 threads),
+// within the budget that keeps its register-limited residency, as exago_eval_all launches it.
+int multi_kernel_stage_cap(exago_net_t net);
+// Runs fn(ws, pl) with the net's lock held from the workspace lookup until fn returns, so that no
+// other host thread can grow (and free) the workspace before fn's kernels are queued.  ws is
+// caller_ws when given (or when bytes is 0), else the net's internal workspace grown to at least
+// `bytes`, and then fn's work on `st` is ordered after the workspace's last use on another stream
+// (as in the evaluations).  pl: the net's two-stream pipeline resources when `pipeline`, else null.
+exago_status with_net_workspace(exago_net_t net, void *caller_ws, size_t bytes, cudaStream_t st,
+                                bool pipeline,
+                                const std::function<exago_status(void *, const PipeLaunch *)> &fn);
 // cudaMalloc for every device allocation of the library (honours exago_test_fail_allocations).
 cudaError_t dev_malloc(void **p, size_t bytes);
 // exago_eval_all without the graph cache (serving: every request has its own buffers).  With

@@ -86,7 +86,7 @@ extern "C" exago_status exago_eval_all_static(exago_net_t net, const exago_batch
     R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
     R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
     R.scratch = (double *)base;
-    R.stage_cap = dev->stage_cap_rows[stage_index(128)];   // rows of the multi-kernel bus tiles
+    R.stage_cap = multi_kernel_stage_cap(net);   // as the multi-kernel schedule stages its rows
     int le = launch_eval(*dev, R, bt->stream);
     if (le != 0) return set_last_error(EXAGO_ECUDA, cudaGetErrorString((cudaError_t)le));
     return EXAGO_OK;

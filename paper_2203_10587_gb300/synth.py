@@ -52,6 +52,7 @@ class Grid:
     c0: np.ndarray
     baseMVA: float = BASE_MVA
     meta: dict = field(default_factory=dict)
+    shift: np.ndarray | None = None  # per-branch phase shift (rad) of phase-shifting transformers
 
     @property
     def nl(self) -> int:
@@ -164,8 +165,12 @@ def bridges(nb: int, f: np.ndarray, t: np.ndarray) -> np.ndarray:
 
 
 def make_grid(seed: int, nb: int, nl: int, ng: int, *, max_degree: int = 8,
-              transformer_frac: float = 0.1, shunts: bool = False) -> Grid:
-    """Synthetic grid with the distributions listed in the module docstring."""
+              transformer_frac: float = 0.1, shunts: bool = False,
+              shifter_frac: float = 0.0) -> Grid:
+    """Synthetic grid with the distributions listed in the module docstring.  With
+    shifter_frac > 0, that fraction of branches (drawn after everything else, so the rest of the
+    grid is the same as without) become phase-shifting transformers: tap ~ U(0.95, 1.05) and
+    phase shift ~ U(-0.5, 0.5) rad (about +-29 degrees)."""
     if ng > nb:
         raise ValueError("generators sit at distinct buses, so ng <= nb")
     rng = _rng(seed)
@@ -191,9 +196,16 @@ def make_grid(seed: int, nb: int, nl: int, ng: int, *, max_degree: int = 8,
     else:
         Gs = np.zeros(nb)
         Bs = np.zeros(nb)
+    shift = None
+    nps = int(round(shifter_frac * nl))
+    if nps:
+        shift = np.zeros(nl)
+        idx = rng.choice(nl, size=nps, replace=False)
+        tap[idx] = rng.uniform(0.95, 1.05, nps)
+        shift[idx] = rng.uniform(-0.5, 0.5, nps)
     return Grid(nb=nb, Gs=Gs, Bs=Bs, Pd=Pd, Qd=Qd, f=f, t=t, r=r, x=x, b=b, tap=tap,
                 rateA=rateA, gbus=gbus, c2=c2, c1=c1, c0=c0,
-                meta={"seed": seed, "max_degree": max_degree})
+                meta={"seed": seed, "max_degree": max_degree}, shift=shift)
 
 
 def base_state(rng: np.random.Generator, g: Grid):
@@ -325,3 +337,48 @@ def generator_contingency_batch(seed: int, g: Grid, B: int, sigma_state: float =
     x = x0[None, :] + rng.normal(0.0, sigma_state, (B, g.n))
     lam = l0[None, :] + rng.normal(0.0, sigma_state, (B, g.m))
     return Batch(x=x, lam=lam, mask=mask, gen_mask=gm)
+
+
+# Angle differences of the wide-angle batches: both sides of the switch between the kernels'
+# polynomial and the library sine and cosine (the double nearest pi/4 and its neighbours), the
+# quarter and half turns, and angles beyond a half turn.
+_PI4 = float.fromhex("0x1.921fb54442d18p-1")      # the double nearest pi/4
+WIDE_ANGLES = np.array([
+    np.nextafter(_PI4, 0.0), _PI4, np.nextafter(_PI4, 4.0),
+    -np.nextafter(_PI4, 0.0), -_PI4, -np.nextafter(_PI4, 4.0),
+    np.pi / 2, -np.pi / 2, np.pi, -np.pi, 3.5, -3.5, 2 * np.pi + 0.3, -7.0, 20.0, -45.25,
+    0.78, 0.79, -0.78, -0.79])
+
+
+def branch_matching(g: Grid) -> np.ndarray:
+    """Branches with pairwise distinct end buses (a greedy matching in branch order), so that each
+    one's angle difference can be set exactly by the angles of its own two buses."""
+    used = np.zeros(g.nb, dtype=bool)
+    pick = []
+    for l in range(g.nl):
+        a, c = int(g.f[l]), int(g.t[l])
+        if a != c and not used[a] and not used[c]:
+            used[a] = used[c] = True
+            pick.append(l)
+    return np.array(pick, dtype=np.int64)
+
+
+def wide_angle_batch(seed: int, g: Grid, B: int, *, masks: bool = False,
+                     sigma: float = 1.0) -> Batch:
+    """States whose branch angle differences Va_f - Va_t reach far beyond the normal operating
+    range.  State 0 and every other even state put each matched branch (branch_matching) on one of
+    WIDE_ANGLES exactly, cycling through the list with a per-state offset: Va_t = 0 and
+    Va_f = angle, so the subtraction is exact.  Odd states draw every angle from U(-pi, pi)."""
+    rng = _rng(seed)
+    b = random_batch(seed, g, B, masks=masks, sigma=sigma)
+    match = branch_matching(g)
+    for s in range(B):
+        if s % 2 == 1:
+            b.x[s, :g.nb] = rng.uniform(-np.pi, np.pi, g.nb)
+            continue
+        for j, l in enumerate(match):
+            a = WIDE_ANGLES[(j + s // 2) % WIDE_ANGLES.shape[0]]
+            b.x[s, g.t[l]] = 0.0
+            b.x[s, g.f[l]] = a
+    b.meta["matched"] = match
+    return b

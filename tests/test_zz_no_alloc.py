@@ -27,15 +27,20 @@ def ex():
     return exago
 
 
-def _run(ex, net, b, static):
+OUTS = ("f", "grad", "gh", "jval", "hval")
+
+
+def _run(ex, net, b, static, which=OUTS):
     import torch
     d = to_device(b)
-    bt = ex.make_batch(d["x"], d["lam"], d["mask"], d["pd_scale"], d["obj_weight"], b.sigma)
-    out = net.outputs(b.B)
+    bt = ex.make_batch(d["x"], d["lam"], d["mask"], d["pd_scale"], d["obj_weight"], b.sigma,
+                       gen_mask=d["gen_mask"])
+    out = net.outputs(b.B, f="f" in which, grad="grad" in which, gh="gh" in which,
+                      jac="jval" in which, hess="hval" in which)
     fn = ex.exago_eval_all_static if static else ex.exago_eval_all
     fn(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"], out["hval"])
     torch.cuda.synchronize()
-    return {k: v.cpu().numpy() for k, v in out.items()}
+    return {k: v.cpu().numpy() for k, v in out.items() if v is not None}
 
 
 @pytest.mark.parametrize("which", ["300bus", "parallel"])
@@ -51,6 +56,22 @@ def test_static_scratch_matches_eval_all_twice(ex, which):
                                sigma=0.6 + 0.2 * call)
         want = _run(ex, net, b, static=False)
         got = _run(ex, net, b, static=True)
+        for k in want:
+            assert_close(got[k], want[k], f"call {call} {k}", TOL)
+
+
+@pytest.mark.parametrize("which", [("gh", "jval"), ("f", "gh"), ("hval",), ("grad", "jval", "hval")])
+def test_static_scratch_generator_outages_and_output_subsets(ex, which):
+    """Per-state generator outages (Sec. V-A) and partial output sets go through the same
+    static scratch and give exago_eval_all's results."""
+    g = synth.make_grid(43, 300, 389, 77, transformer_frac=0.3, shunts=True)
+    net = ex.Net(g)
+    for call, seed in enumerate((44, 45)):
+        b = synth.random_batch(seed, g, 5, masks=True, pd_scale=True, obj_weight=True,
+                               sigma=0.9, gen_masks=True)
+        want = _run(ex, net, b, static=False, which=which)
+        got = _run(ex, net, b, static=True, which=which)
+        assert set(got) == set(which)
         for k in want:
             assert_close(got[k], want[k], f"call {call} {k}", TOL)
 
