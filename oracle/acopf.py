@@ -42,7 +42,8 @@ class _Net(ctypes.Structure):
                 ("Qd", ctypes.c_void_p), ("f", ctypes.c_void_p), ("t", ctypes.c_void_p),
                 ("r", ctypes.c_void_p), ("x", ctypes.c_void_p), ("b", ctypes.c_void_p),
                 ("tap", ctypes.c_void_p), ("gbus", ctypes.c_void_p), ("c2", ctypes.c_void_p),
-                ("c1", ctypes.c_void_p), ("c0", ctypes.c_void_p), ("baseMVA", ctypes.c_double)]
+                ("c1", ctypes.c_void_p), ("c0", ctypes.c_void_p), ("baseMVA", ctypes.c_double),
+                ("shift", ctypes.c_void_p)]
 
 
 class _Coo(ctypes.Structure):
@@ -66,6 +67,8 @@ def bind_library(path: str):
     lib.oracle_coo_capacity_cart.argtypes = [ctypes.POINTER(_Net), vp, vp]
     lib.oracle_pi_model.argtypes = [ctypes.c_double] * 4 + [vp]
     lib.oracle_pi_model.restype = ctypes.c_int
+    lib.oracle_pi_model_shift.argtypes = [ctypes.c_double] * 5 + [vp]
+    lib.oracle_pi_model_shift.restype = ctypes.c_int
     lib.oracle_slack.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp,
                                  ctypes.c_double, vp, vp, vp]
     lib.oracle_slack.restype = ctypes.c_int
@@ -107,19 +110,24 @@ class OracleNet:
                           f=i(grid.f), t=i(grid.t), r=d(grid.r), x=d(grid.x), b=d(grid.b),
                           tap=d(grid.tap), gbus=i(grid.gbus), c2=d(grid.c2), c1=d(grid.c1),
                           c0=d(grid.c0))
+        shift = getattr(grid, "shift", None)
+        self._keep["shift"] = None if shift is None else d(shift)
         k = self._keep
         self.c = _Net(self.nb, self.nl, self.ng, _p(k["Gs"]), _p(k["Bs"]), _p(k["Pd"]),
                       _p(k["Qd"]), _p(k["f"]), _p(k["t"]), _p(k["r"]), _p(k["x"]), _p(k["b"]),
                       _p(k["tap"]), _p(k["gbus"]), _p(k["c2"]), _p(k["c1"]), _p(k["c0"]),
-                      float(grid.baseMVA))
+                      float(grid.baseMVA), _p(k["shift"]))
         self.n = 2 * self.nb + 2 * self.ng
         self.m = 2 * self.nb + 2 * self.nl
 
 
-def pi_model(r: float, x: float, b: float, tap: float, lib=None) -> np.ndarray:
-    """[Gff, Bff, Gft, Bft, Gtf, Btf, Gtt, Btt] of one branch."""
+def pi_model(r: float, x: float, b: float, tap: float, lib=None, shift: float | None = None) -> np.ndarray:
+    """[Gff, Bff, Gft, Bft, Gtf, Btf, Gtt, Btt] of one branch (phase shift in rad, or None)."""
     Y = np.zeros(8)
-    if (lib or _load()).oracle_pi_model(r, x, b, tap, _p(Y)) != 0:
+    L = lib or _load()
+    rc = (L.oracle_pi_model(r, x, b, tap, _p(Y)) if shift is None
+          else L.oracle_pi_model_shift(r, x, b, tap, shift, _p(Y)))
+    if rc != 0:
         raise ValueError("zero series impedance")
     return Y
 

@@ -48,6 +48,8 @@ typedef struct {
     const int *gbus;                     /* per generator */
     const double *c2, *c1, *c0;          /* cost in MW terms: c2*MW^2 + c1*MW + c0 */
     double baseMVA;
+    const double *shift;                 /* per branch, rad: phase shift of the from-side tap
+                                            (phase-shifting transformer); NULL = all 0 */
 } oracle_net;
 
 typedef struct {
@@ -57,27 +59,47 @@ typedef struct {
     double *val;
 } oracle_coo;
 
-/* ---- pi-model two-port of one branch (textbook; MATPOWER's branch model without phase shift) ----
- * series admittance ys = 1/(r + j x) = gs + j bs, line charging b split half per end, off-nominal
- * tap tau on the from side.  Y = [[(ys + j b/2)/tau^2, -ys/tau], [-ys/tau, ys + j b/2]].
+/* ---- pi-model two-port of one branch (textbook; MATPOWER's branch model) ----
+ * series admittance ys = 1/(r + j x) = gs + j bs, line charging b split half per end, and on the
+ * from side an ideal transformer of complex ratio T = tau e^{j phi}: off-nominal tap tau and phase
+ * shift phi (rad; a phase-shifting transformer).  The from-side series terminal sees V_f / T and
+ * the from current is the series current divided by conj(T), so
+ *   Y = [[(ys + j b/2)/tau^2, -ys/conj(T)], [-ys/T, ys + j b/2]],
+ * -ys/conj(T) = -ys e^{j phi}/tau and -ys/T = -ys e^{-j phi}/tau.  The two mutual admittances
+ * differ unless phi = 0.
  * Out: Y[0..7] = Gff, Bff, Gft, Bft, Gtf, Btf, Gtt, Btt.  Returns 0, or -1 if r = x = 0. */
-int oracle_pi_model(double r, double x, double b, double tap, double *Y)
+int oracle_pi_model_shift(double r, double x, double b, double tap, double phi, double *Y)
 {
     double z2 = r * r + x * x;
     double tau = (tap == 0.0) ? 1.0 : tap;
-    double gs, bs;
+    double gs, bs, cp, sp;
     if (z2 == 0.0) return -1;
     gs = r / z2;
     bs = -x / z2;
+    cp = cos(phi);
+    sp = sin(phi);
     Y[0] = gs / (tau * tau);
     Y[1] = (bs + 0.5 * b) / (tau * tau);
-    Y[2] = -gs / tau;
-    Y[3] = -bs / tau;
-    Y[4] = -gs / tau;
-    Y[5] = -bs / tau;
+    /* -(gs + j bs)(cp + j sp) / tau */
+    Y[2] = -(gs * cp - bs * sp) / tau;
+    Y[3] = -(gs * sp + bs * cp) / tau;
+    /* -(gs + j bs)(cp - j sp) / tau */
+    Y[4] = -(gs * cp + bs * sp) / tau;
+    Y[5] = -(bs * cp - gs * sp) / tau;
     Y[6] = gs;
     Y[7] = bs + 0.5 * b;
     return 0;
+}
+
+/* The same without phase shift (phi = 0). */
+int oracle_pi_model(double r, double x, double b, double tap, double *Y)
+{
+    return oracle_pi_model_shift(r, x, b, tap, 0.0, Y);
+}
+
+static double branch_shift(const oracle_net *net, int l)
+{
+    return net->shift ? net->shift[l] : 0.0;
 }
 
 /* ---- one end of a branch, seen from its own bus u towards the other bus v ----
@@ -268,7 +290,8 @@ int oracle_eval(const oracle_net *net, const double *x, const double *lam, const
         int gidx[2][4];
         int s;
         if (fb < 0 || fb >= nb || tb < 0 || tb >= nb || fb == tb) return -1;
-        if (oracle_pi_model(net->r[l], net->x[l], net->b[l], net->tap[l], Y) != 0) return -1;
+        if (oracle_pi_model_shift(net->r[l], net->x[l], net->b[l], net->tap[l],
+                                  branch_shift(net, l), Y) != 0) return -1;
         /* from side: u = f, v = t; to side: u = t, v = f */
         side_terms(Y[0], Y[1], Y[2], Y[3], Va[fb], Va[tb], Vm[fb], Vm[tb],
                    &P[0], &Q[0], dP[0], dQ[0], HP[0], HQ[0]);
@@ -477,7 +500,8 @@ int oracle_eval_cart(const oracle_net *net, const double *x, const double *lam,
         int gidx[2][4];
         int s;
         if (fb < 0 || fb >= nb || tb < 0 || tb >= nb || fb == tb) return -1;
-        if (oracle_pi_model(net->r[l], net->x[l], net->b[l], net->tap[l], Y) != 0) return -1;
+        if (oracle_pi_model_shift(net->r[l], net->x[l], net->b[l], net->tap[l],
+                                  branch_shift(net, l), Y) != 0) return -1;
         side_terms_cart(Y[0], Y[1], Y[2], Y[3], E[fb], F[fb], E[tb], F[tb],
                         &P[0], &Q[0], dP[0], dQ[0], HP[0], HQ[0]);
         side_terms_cart(Y[6], Y[7], Y[4], Y[5], E[tb], F[tb], E[fb], F[fb],

@@ -53,9 +53,12 @@ def complex_model(g, x, mask=None, pd_scale=None):
     m = np.ones(nl) if mask is None else mask.astype(np.float64)
     ys = 1.0 / (g.r + 1j * g.x)
     tau = np.where(g.tap == 0.0, 1.0, g.tap)
-    Yff = (ys + 0.5j * g.b) / tau ** 2 * m
-    Yft = -ys / tau * m
-    Ytf = -ys / tau * m
+    # complex ratio of the from-side ideal transformer: tap and phase shift (phase-shifting
+    # transformers); the from current is the series current over conj(T)
+    T = tau * np.exp(1j * (np.zeros(nl) if getattr(g, "shift", None) is None else g.shift))
+    Yff = (ys + 0.5j * g.b) / (T * np.conj(T)) * m
+    Yft = -ys / np.conj(T) * m
+    Ytf = -ys / T * m
     Ytt = (ys + 0.5j * g.b) * m
     If = Yff * V[g.f] + Yft * V[g.t]
     It = Ytf * V[g.f] + Ytt * V[g.t]
@@ -74,7 +77,7 @@ def complex_model(g, x, mask=None, pd_scale=None):
     np.add.at(Sg, g.gbus, Pg + 1j * Qg)
     gP = Sbus.real + g.Pd * sc - Sg.real
     gQ = Sbus.imag + g.Qd * sc - Sg.imag
-    return dict(Sf=Sf, St=St, gP=gP, gQ=gQ, V=V, ys=ys, tau=tau)
+    return dict(Sf=Sf, St=St, gP=gP, gQ=gQ, V=V, ys=ys, tau=tau, T=T)
 
 
 def gh_of(oracle_mod, net, x, lam, mask=None, pd_scale=None):
@@ -151,9 +154,13 @@ def test_objective_hand_numbers(oracle_mod):
 
 # ---- independent formulation --------------------------------------------------------------------
 
-@pytest.mark.parametrize("seed,nb,nl,ng", [(21, 3, 3, 1), (22, 30, 41, 6), (23, 200, 260, 50)])
-def test_matches_complex_nodal_form(oracle_mod, seed, nb, nl, ng):
-    g = synth.make_grid(seed, nb, nl, ng, shunts=True)
+@pytest.mark.parametrize("seed,nb,nl,ng,shifters", [(21, 3, 3, 1, 0.0), (22, 30, 41, 6, 0.0),
+                                                    (23, 200, 260, 50, 0.0),
+                                                    (24, 60, 80, 12, 0.25)])
+def test_matches_complex_nodal_form(oracle_mod, seed, nb, nl, ng, shifters):
+    """The last case has phase-shifting transformers on a quarter of its branches: the nodal form
+    then carries the complex tap ratio T = tau e^{j phi} of each."""
+    g = synth.make_grid(seed, nb, nl, ng, shunts=True, shifter_frac=shifters)
     if nb == 3:
         g.tap[1] = 0.97   # 3-bus triangle with a transformer
     b = synth.random_batch(seed, g, 1, masks=True, pd_scale=True)
@@ -166,9 +173,11 @@ def test_matches_complex_nodal_form(oracle_mod, seed, nb, nl, ng):
     np.testing.assert_allclose(r["gh"][2 * nb + nl:], np.abs(c["St"]) ** 2, rtol=1e-12, atol=1e-12)
 
 
-def test_loss_invariant(oracle_mod):
-    """Net injections sum to the series losses gs |V_f e^{j Va_f}/tau - V_t e^{j Va_t}|^2 >= 0."""
-    g = synth.make_grid(31, 60, 80, 12, shunts=True)
+@pytest.mark.parametrize("shifters", [0.0, 0.3])
+def test_loss_invariant(oracle_mod, shifters):
+    """Net injections sum to the series losses gs |V_f e^{j Va_f}/T - V_t e^{j Va_t}|^2 >= 0,
+    T = tau e^{j phi} (an ideal phase-shifting transformer moves power without loss)."""
+    g = synth.make_grid(31, 60, 80, 12, shunts=True, shifter_frac=shifters)
     b = synth.random_batch(31, g, 1, masks=True)
     x, mask = b.x[0], b.mask[0]
     r = gh_of(oracle_mod, oracle_mod.OracleNet(g), x, b.lam[0], mask)
@@ -178,7 +187,8 @@ def test_loss_invariant(oracle_mod):
     V = Vm * np.exp(1j * x[:nb])
     gs = (1.0 / (g.r + 1j * g.x)).real
     tau = np.where(g.tap == 0.0, 1.0, g.tap)
-    loss = mask * gs * np.abs(V[g.f] / tau - V[g.t]) ** 2
+    T = tau * np.exp(1j * (np.zeros(g.nl) if g.shift is None else g.shift))
+    loss = mask * gs * np.abs(V[g.f] / T - V[g.t]) ** 2
     assert np.all(loss >= 0)
     assert lhs == pytest.approx(loss.sum(), rel=1e-11)
 
@@ -230,6 +240,12 @@ def test_finite_differences_sigma_zero_and_transformers(oracle_mod):
     g = synth.make_grid(43, 10, 14, 3, transformer_frac=0.5, shunts=True)
     b = synth.random_batch(43, g, 1)
     _fd_check(oracle_mod, g, b, sigma=0.0)
+
+
+def test_finite_differences_phase_shifters(oracle_mod):
+    g = synth.make_grid(44, 12, 17, 3, shunts=True, shifter_frac=0.4)
+    b = synth.random_batch(44, g, 1, masks=True, pd_scale=True)
+    _fd_check(oracle_mod, g, b, sigma=0.9)
 
 
 # ---- symmetries of the model ----------------------------------------------------------------

@@ -84,7 +84,10 @@ def change_of_variables(g, xp):
 
 @pytest.mark.parametrize("seed", [53, 54])
 def test_change_of_variables_to_polar(oracle_mod, seed):
-    g = grid_with_shunts(seed)
+    change_of_variables_check(oracle_mod, grid_with_shunts(seed), seed)
+
+
+def change_of_variables_check(oracle_mod, g, seed):
     rng = np.random.default_rng(seed)
     xp, xc = cart_state(g, rng)
     lam_p = rng.normal(size=g.m)

@@ -15,6 +15,7 @@ import test_oracle_cartesian as TK
 import test_oracle_genmask as TG
 import test_oracle_slack as TS
 import test_oracle_coupling as TC
+import test_oracle_shift as TP
 
 SRC = os.path.join(os.path.dirname(acopf.__file__), "acopf_oracle.c")
 
@@ -32,7 +33,14 @@ MUTANTS = {
     "hess_mu_factor": ("+ mu * 2.0 * (dP[a]", "+ mu * (dP[a]"),
     "to_side_swapped": ("gidx[1][0] = tb; gidx[1][1] = fb;", "gidx[1][0] = fb; gidx[1][1] = tb;"),
     "charging_not_halved": ("Y[1] = (bs + 0.5 * b) / (tau * tau);", "Y[1] = (bs + b) / (tau * tau);"),
-    "tap_square_mutual": ("Y[2] = -gs / tau;", "Y[2] = -gs / (tau * tau);"),
+    "tap_square_mutual": ("Y[2] = -(gs * cp - bs * sp) / tau;", "Y[2] = -(gs * cp - bs * sp) / (tau * tau);"),
+    "shift_ft_conjugate": ("Y[2] = -(gs * cp - bs * sp) / tau;",
+                           "Y[2] = -(gs * cp + bs * sp) / tau;"),
+    "shift_tf_sign": ("Y[5] = -(bs * cp - gs * sp) / tau;", "Y[5] = -(bs * cp + gs * sp) / tau;"),
+    "shift_ends_equal": ("Y[4] = -(gs * cp + bs * sp) / tau;", "Y[4] = -(gs * cp - bs * sp) / tau;"),
+    "shift_dropped_in_Bft": ("Y[3] = -(gs * sp + bs * cp) / tau;", "Y[3] = -(bs * cp) / tau;"),
+    "shift_ignored": ("return net->shift ? net->shift[l] : 0.0;", "return 0.0;"),
+    "shift_on_tap_magnitude": ("Y[0] = gs / (tau * tau);", "Y[0] = gs * cp / (tau * tau);"),
     "tap_on_wrong_end": ("Y[6] = gs;", "Y[6] = gs / (tau * tau);"),
     "h_jac_factor": ("2.0 * P * dP[a] + 2.0 * Q * dQ[a]", "P * dP[a] + Q * dQ[a]"),
     "cost_units": ("net->c1[k] * MW + net->c0[k]", "net->c1[k] * Pg[k] + net->c0[k]"),
@@ -98,9 +106,10 @@ PINS = [
     ("transformer", lambda om: T.test_transformer_scales_from_voltage(om)),
     ("flat_start", lambda om: T.test_flat_start(om)),
     ("objective", lambda om: T.test_objective_hand_numbers(om)),
-    ("nodal_3", lambda om: T.test_matches_complex_nodal_form(om, 21, 3, 3, 1)),
-    ("nodal_30", lambda om: T.test_matches_complex_nodal_form(om, 22, 30, 41, 6)),
-    ("loss", lambda om: T.test_loss_invariant(om)),
+    ("nodal_3", lambda om: T.test_matches_complex_nodal_form(om, 21, 3, 3, 1, 0.0)),
+    ("nodal_30", lambda om: T.test_matches_complex_nodal_form(om, 22, 30, 41, 6, 0.0)),
+    ("loss", lambda om: T.test_loss_invariant(om, 0.0)),
+    ("loss_shift", lambda om: T.test_loss_invariant(om, 0.3)),
     ("fd", lambda om: T.test_finite_differences(om, 41)),
     ("fd_sigma0", lambda om: T.test_finite_differences_sigma_zero_and_transformers(om)),
     ("mask", lambda om: T.test_mask_equals_branch_removed(om)),
@@ -113,6 +122,10 @@ PINS = [
     ("gen_out_hand", lambda om: TG.test_two_bus_generator_outage_by_hand(om)),
     ("slack_hand", lambda om: TS.test_hand_values(om)),
     ("slack_load_loss", lambda om: TS.test_load_loss_equals_lower_load(om)),
+    ("shift_closed_form", lambda om: TP.test_lossless_phase_shifter_closed_form(om)),
+    ("shift_rotation", lambda om: TP.test_shift_equals_rotated_from_angle(om, 0.02, 0.12, 0.05, 1.0, 0.35)),
+    ("shift_nodal", lambda om: T.test_matches_complex_nodal_form(om, 24, 60, 80, 12, 0.25)),
+    ("shift_cart", lambda om: TP.test_cartesian_change_of_variables_with_shifters(om)),
     ("coupling_hand", lambda om: TC.test_hand_rows(om)),
     ("coupling_hand_transpose", lambda om: TC.test_hand_transpose(om)),
     ("coupling_telescopes", lambda om: TC.test_chain_telescopes(om)),
