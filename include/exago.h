@@ -18,7 +18,8 @@
  *   P balance of bus i:  sum of branch-end injections at i + Gs_i Vm_i^2 + Pd_i s_i - sum Pg at i
  *   Q balance of bus i:  sum of branch-end injections at i - Bs_i Vm_i^2 + Qd_i s_i - sum Qg at i
  *   branch model:        pi-model, series 1/(r + jx), charging b split half per end, tap on the
- *                        from end (tap 0 means 1), no phase shift
+ *                        from end (tap 0 means 1), no phase shift (exago_net_create_shift
+ *                        adds one per branch: phase-shifting transformers)
  *   objective:           f = w * sum_k (c2_k (baseMVA Pg_k)^2 + c1_k baseMVA Pg_k + c0_k)
  *   Lagrangian Hessian:  sigma grad^2 f + sum lam_i grad^2 g_i + sum mu_l grad^2 h_l, lower
  *                        triangle, row-major CSR, ascending columns
@@ -80,6 +81,24 @@ exago_status exago_net_create(int nb, const double *Gs, const double *Bs, const 
                               const double *tap, const double *rateA, int ng, const int *gbus,
                               const double *c2, const double *c1, const double *c0,
                               double baseMVA, exago_net_t *out);
+
+/*
+ * exago_net_create for a network with phase-shifting transformers: the same arguments, plus
+ * shift[nl] (host, rad; NULL = no phase shift anywhere), the phase angle of the ideal transformer
+ * on each branch's from side.  Its complex ratio is T = tau e^{j shift} (tau = tap, 0 meaning 1),
+ * so the mutual admittances become Yft = -ys/conj(T) and Ytf = -ys/T and differ between the two
+ * ends (the textbook and MATPOWER branch model; Sec. III lists the network features the model
+ * carries).  Every evaluation entry point of both formulations honours the shifts, through the
+ * kernel variants that read each end's own mutual admittances; a net created with shift = NULL,
+ * or by exago_net_create, runs the shift-free variants.  EINVAL for a non-finite shift.
+ */
+exago_status exago_net_create_shift(int nb, const double *Gs, const double *Bs, const double *Pd,
+                                    const double *Qd, int nl, const int *f, const int *t,
+                                    const double *r, const double *x, const double *b,
+                                    const double *tap, const double *shift,
+                                    const double *rateA, int ng, const int *gbus,
+                                    const double *c2, const double *c1, const double *c0,
+                                    double baseMVA, exago_net_t *out);
 
 /*
  * Host-only planning with the same arguments and validation as exago_net_create, without

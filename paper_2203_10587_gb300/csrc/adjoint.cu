@@ -40,9 +40,8 @@ __device__ __forceinline__ void adj_branch_item(const DevNet &N, const AdjReq &A
     const double Gtt2 = __ldg(N.Gtt2 + l), Btt2 = __ldg(N.Btt2 + l);
     double s, c;
     branch_sincos(Vaf - Vat, &s, &c);
-    const double Bc = Bm * c, Bs = Bm * s;
-    const double Af = fma(G, c, Bs), Cf = fma(G, s, -Bc);
-    const double At = fma(G, c, -Bs), Ct = -fma(G, s, Bc);
+    double Af, Cf, At, Ct;
+    angle_terms<true>(N, l, G, Bm, s, c, &Af, &Cf, &At, &Ct);   // phase shifters honoured
     const double VV = Vf * Vt, Vf2 = Vf * Vf, Vt2 = Vt * Vt;
     const End ef = end_terms<true>(Gff, Bff, Gff2, Bff2, Af, Cf, Vf, Vt, Vf2, VV);
     const End et = end_terms<true>(Gtt, Btt, Gtt2, Btt2, At, Ct, Vt, Vf, Vt2, VV);

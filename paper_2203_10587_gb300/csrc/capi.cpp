@@ -202,15 +202,18 @@ exago_status do_upload(exago_net *net) {
     if ((s = upload(net, p.x, &x)) != EXAGO_OK) return s;
     if ((s = upload(net, p.b, &b)) != EXAGO_OK) return s;
     if ((s = upload(net, p.tap, &tap)) != EXAGO_OK) return s;
-    double *Y[11];
-    for (int k = 0; k < 11; k++)
+    const double *shift = nullptr;
+    if ((s = upload(net, p.shift, &shift)) != EXAGO_OK) return s;   // empty: no phase shifters
+    double *Y[13] = {};
+    for (int k = 0; k < (shift ? 13 : 11); k++)
         if ((s = alloc_dev(net, (size_t)p.nl * sizeof(double), &Y[k])) != EXAGO_OK) return s;
     d.Gff = Y[0]; d.Bff = Y[1]; d.Gtt = Y[2]; d.Btt = Y[3]; d.Gft = Y[4]; d.Bft = Y[5];
     d.Gff2 = Y[6]; d.Bff2 = Y[7]; d.Gtt2 = Y[8]; d.Btt2 = Y[9]; d.Kft = Y[10];
+    d.Gtf = Y[11]; d.Btf = Y[12];
     cudaStream_t st;
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
         return cuda_fail(e, "cudaStreamCreate");
-    int le = launch_admittance(r, x, b, tap, p.nl, Y, st);
+    int le = launch_admittance(r, x, b, tap, shift, p.nl, Y, st);
     e = cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
     if (le != 0) return cuda_fail((cudaError_t)le, "admittance kernel launch");
@@ -239,7 +242,8 @@ exago_status plan_only(int nb, const double *Gs, const double *Bs, const double 
                        const double *Qd, int nl, const int *f, const int *t, const double *r,
                        const double *x, const double *b, const double *tap, const double *rateA,
                        int ng, const int *gbus, const double *c2, const double *c1,
-                       const double *c0, double baseMVA, exago_net_t *out) {
+                       const double *c0, double baseMVA, const double *shift,
+                       exago_net_t *out) {
     if (!out) return fail(EXAGO_EINVAL, "out is NULL");
     *out = nullptr;
     exago_net *net = new (std::nothrow) exago_net();
@@ -248,7 +252,7 @@ exago_status plan_only(int nb, const double *Gs, const double *Bs, const double 
     exago_status s;
     try {
         s = build_plan(net->plan, nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng, gbus,
-                       c2, c1, c0, baseMVA, err);
+                       c2, c1, c0, baseMVA, shift, err);
     } catch (const std::bad_alloc &) {
         s = EXAGO_ENOMEM;
         err = "host allocation failed while planning";
@@ -704,7 +708,7 @@ exago_status exago_net_plan(int nb, const double *Gs, const double *Bs, const do
                             const double *c2, const double *c1, const double *c0,
                             double baseMVA, exago_net_t *out) {
     return plan_only(nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng, gbus, c2, c1, c0,
-                     baseMVA, out);
+                     baseMVA, nullptr, out);
 }
 
 exago_status exago_net_create(int nb, const double *Gs, const double *Bs, const double *Pd,
@@ -713,9 +717,20 @@ exago_status exago_net_create(int nb, const double *Gs, const double *Bs, const 
                               const double *tap, const double *rateA, int ng, const int *gbus,
                               const double *c2, const double *c1, const double *c0,
                               double baseMVA, exago_net_t *out) {
+    return exago_net_create_shift(nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, nullptr, rateA, ng,
+                                  gbus, c2, c1, c0, baseMVA, out);
+}
+
+exago_status exago_net_create_shift(int nb, const double *Gs, const double *Bs, const double *Pd,
+                                    const double *Qd, int nl, const int *f, const int *t,
+                                    const double *r, const double *x, const double *b,
+                                    const double *tap, const double *shift,
+                                    const double *rateA, int ng, const int *gbus,
+                                    const double *c2, const double *c1, const double *c0,
+                                    double baseMVA, exago_net_t *out) {
     Range range("exago_net_create");
     exago_status s = plan_only(nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng, gbus, c2,
-                               c1, c0, baseMVA, out);
+                               c1, c0, baseMVA, shift, out);
     if (s != EXAGO_OK) return s;
     s = do_upload(*out);
     if (s != EXAGO_OK) {

@@ -73,14 +73,18 @@ struct CartBranch {
     double p1t, p2t, q1t, q2t, p3t, p4t;   // to end (u = t, v = f)
 };
 
-// The admittances of one branch (network tables).
+// The admittances of one branch (network tables).  G, Bm are the from end's mutual admittance;
+// Gt, Bt the to end's, read only by the phase-shifter variants (PS; equal to G, Bm otherwise).
 struct CartY {
-    double G, Bm, Gff, Bff, Gtt, Btt, Gff2, Bff2, Gtt2, Btt2;
+    double G, Bm, Gff, Bff, Gtt, Btt, Gff2, Bff2, Gtt2, Btt2, Gt, Bt;
 };
 
+template <bool PS>
 __device__ __forceinline__ CartY cart_y(const DevNet &N, int l) {
     CartY y;
     y.G = __ldg(N.Gft + l); y.Bm = __ldg(N.Bft + l);
+    if (PS) { y.Gt = __ldg(N.Gtf + l); y.Bt = __ldg(N.Btf + l); }
+    else { y.Gt = y.G; y.Bt = y.Bm; }
     y.Gff = __ldg(N.Gff + l); y.Bff = __ldg(N.Bff + l);
     y.Gtt = __ldg(N.Gtt + l); y.Btt = __ldg(N.Btt + l);
     y.Gff2 = __ldg(N.Gff2 + l); y.Bff2 = __ldg(N.Bff2 + l);
@@ -88,6 +92,10 @@ __device__ __forceinline__ CartY cart_y(const DevNet &N, int l) {
     return y;
 }
 
+// With PS (phase-shifting transformers) the to end's terms take its own mutual admittance
+// (Gt, Bt): P_t = Gtt s_t + Gt a - Bt bf, Q_t = -Btt s_t - Gt bf - Bt a, and the to end's
+// admittance-voltage products below use Gt, Bt; without, one set of products serves both ends.
+template <bool PS>
 __device__ __forceinline__ CartBranch cart_terms(const CartY &y, double ef, double ff, double et,
                                                  double ft) {
     const double G = y.G, Bm = y.Bm, Gff = y.Gff, Bff = y.Bff, Gtt = y.Gtt, Btt = y.Btt;
@@ -100,8 +108,14 @@ __device__ __forceinline__ CartBranch cart_terms(const CartY &y, double ef, doub
     const double Ga = G * a, Ba = Bm * a, Gb = G * bf, Bb = Bm * bf;
     c.Pf = fma(Gff, sf, Ga + Bb);
     c.Qf = fma(-Bff, sf, Gb - Ba);
-    c.Pt = fma(Gtt, st, Ga - Bb);
-    c.Qt = fma(-Btt, st, -(Gb + Ba));
+    if (PS) {
+        const double Gta = y.Gt * a, Bta = y.Bt * a, Gtb = y.Gt * bf, Btb = y.Bt * bf;
+        c.Pt = fma(Gtt, st, Gta - Btb);
+        c.Qt = fma(-Btt, st, -(Gtb + Bta));
+    } else {
+        c.Pt = fma(Gtt, st, Ga - Bb);
+        c.Qt = fma(-Btt, st, -(Gb + Ba));
+    }
     // admittance-voltage products shared by both ends' derivatives
     const double Gef = G * ef, Gff_ = G * ff, Get = G * et, Gft_ = G * ft;
     const double Bef = Bm * ef, Bff_ = Bm * ff, Bet = Bm * et, Bft_ = Bm * ft;
@@ -109,10 +123,20 @@ __device__ __forceinline__ CartBranch cart_terms(const CartY &y, double ef, doub
     c.p1f = fma(Gff2, ef, u1); c.p2f = fma(Gff2, ff, u2);
     c.q1f = fma(-Bff2, ef, -u2); c.q2f = fma(-Bff2, ff, u1);
     c.p3f = Gef + Bff_; c.p4f = Gff_ - Bef;
-    const double w1 = Gef - Bff_, w2 = Gff_ + Bef;
+    double w1, w2;
+    if (PS) {
+        const double Gtef = y.Gt * ef, Gtff = y.Gt * ff, Gtet = y.Gt * et, Gtft = y.Gt * ft;
+        const double Btef = y.Bt * ef, Btff = y.Bt * ff, Btet = y.Bt * et, Btft = y.Bt * ft;
+        w1 = Gtef - Btff;
+        w2 = Gtff + Btef;
+        c.p3t = Gtet + Btft; c.p4t = Gtft - Btet;
+    } else {
+        w1 = Gef - Bff_;
+        w2 = Gff_ + Bef;
+        c.p3t = Get + Bft_; c.p4t = Gft_ - Bet;
+    }
     c.p1t = fma(Gtt2, et, w1); c.p2t = fma(Gtt2, ft, w2);
     c.q1t = fma(-Btt2, et, -w2); c.q2t = fma(-Btt2, ft, w1);
-    c.p3t = Get + Bft_; c.p4t = Gft_ - Bet;
     return c;
 }
 
@@ -129,6 +153,7 @@ struct CartHess {
     double eeft, ffft, ef_ft, ff_et; // (e_f,e_t), (f_f,f_t), (e_f,f_t), (f_f,e_t)
 };
 
+template <bool PS>
 __device__ __forceinline__ CartHess cart_hess(const CartY &y, const CartBranch &c, double lPf,
                                               double lQf, double lPt, double lQt, double muf,
                                               double mut) {
@@ -137,8 +162,14 @@ __device__ __forceinline__ CartHess cart_hess(const CartY &y, const CartBranch &
     const double wPf = fma(muf2, c.Pf, lPf), wQf = fma(muf2, c.Qf, lQf);
     const double wPt = fma(mut2, c.Pt, lPt), wQt = fma(mut2, c.Qt, lQt);
     const double df = fma(wPf, Gff2, -(wQf * Bff2)), dt = fma(wPt, Gtt2, -(wQt * Btt2));
-    const double c1 = fma(wPf + wPt, G, -((wQf + wQt) * Bm));            // c1_f + c1_t
-    const double dc = fma(wPt - wPf, Bm, (wQt - wQf) * G);               // c2_t - c2_f
+    double c1, dc;
+    if (PS) {   // each end with its own mutual admittance
+        c1 = fma(wPf, G, fma(wPt, y.Gt, -fma(wQf, Bm, wQt * y.Bt)));        // c1_f + c1_t
+        dc = fma(wPt, y.Bt, fma(wQt, y.Gt, -fma(wPf, Bm, wQf * G)));        // c2_t - c2_f
+    } else {
+        c1 = fma(wPf + wPt, G, -((wQf + wQt) * Bm));                        // c1_f + c1_t
+        dc = fma(wPt - wPf, Bm, (wQt - wQf) * G);                           // c2_t - c2_f
+    }
     // 2 mu times each end's gradient
     const double a1 = muf2 * c.p1f, a2 = muf2 * c.p2f, a3 = muf2 * c.p3f, a4 = muf2 * c.p4f;
     const double b1 = muf2 * c.q1f, b2 = muf2 * c.q2f;
@@ -161,6 +192,7 @@ __device__ __forceinline__ CartHess cart_hess(const CartY &y, const CartBranch &
 }
 
 // One (state, branch) item of the branch kernel.
+template <bool PS>
 __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq &R, int bl, int l) {
     const int b = R.b0 + bl;
     const int nb = N.nb, nl = N.nl;
@@ -181,9 +213,9 @@ __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq 
         return;
     }
     const double *xb = R.x + (size_t)b * N.n;
-    const CartY y = cart_y(N, l);
-    const CartBranch c = cart_terms(y, __ldg(xb + fb), __ldg(xb + nb + fb), __ldg(xb + tb),
-                                    __ldg(xb + nb + tb));
+    const CartY y = cart_y<PS>(N, l);
+    const CartBranch c = cart_terms<PS>(y, __ldg(xb + fb), __ldg(xb + nb + fb), __ldg(xb + tb),
+                                        __ldg(xb + nb + tb));
     if (ghb) {
         ghb[2 * nb + l] = fma(c.Pf, c.Pf, c.Qf * c.Qf);
         ghb[2 * nb + nl + l] = fma(c.Pt, c.Pt, c.Qt * c.Qt);
@@ -213,9 +245,9 @@ __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq 
     put2c(rt, CR_PEV, c.p3t, c.p4t);
     if (R.hval) {
         const double *lb = R.lam + (size_t)b * R.mc;
-        const CartHess h = cart_hess(y, c, __ldg(lb + fb), __ldg(lb + nb + fb), __ldg(lb + tb),
-                                     __ldg(lb + nb + tb), __ldg(lb + 2 * nb + l),
-                                     __ldg(lb + 2 * nb + nl + l));
+        const CartHess h = cart_hess<PS>(y, c, __ldg(lb + fb), __ldg(lb + nb + fb), __ldg(lb + tb),
+                                         __ldg(lb + nb + tb), __ldg(lb + 2 * nb + l),
+                                         __ldg(lb + 2 * nb + nl + l));
         put2c(rf, CR_HEE, h.eef, h.fef);
         put2c(rf, CR_HFF, h.fff, h.eeft);
         put2c(rf, CR_HFEV, h.ff_et, h.ffft);
@@ -227,12 +259,14 @@ __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq 
 
 // Work items (state of the chunk, block of 128 branches or buses), state-major, taken by a grid
 // of the resident CTA count so that no launch ends in a nearly empty wave.
+// PS: the net has phase-shifting transformers (N.Gtf non-null).
+template <bool PS>
 __global__ void __launch_bounds__(128) k_cart_branch(const DevNet N, const CartReq R, int nB) {
     const int per = (N.nl + 127) / 128;
     for (int it = blockIdx.x; it < nB * per; it += gridDim.x) {
         const int bl = it / per;
         const int l = (it - bl * per) * 128 + threadIdx.x;
-        if (l < N.nl) cart_branch_item(N, R, bl, l);
+        if (l < N.nl) cart_branch_item<PS>(N, R, bl, l);
     }
 }
 
@@ -408,7 +442,7 @@ struct CartAdjReq {
     double *scratch;            // [chunk][nl][4]
 };
 
-template <int MODE>
+template <int MODE, bool PS>
 __global__ void __launch_bounds__(128) k_cart_adj_branch(const DevNet N, const CartAdjReq A) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= N.nl) return;
@@ -427,9 +461,9 @@ __global__ void __launch_bounds__(128) k_cart_adj_branch(const DevNet N, const C
         return;
     }
     const double *xb = A.x + (size_t)b * N.n;
-    const CartY y = cart_y(N, l);
-    const CartBranch c = cart_terms(y, __ldg(xb + fb), __ldg(xb + nb + fb), __ldg(xb + tb),
-                                    __ldg(xb + nb + tb));
+    const CartY y = cart_y<PS>(N, l);
+    const CartBranch c = cart_terms<PS>(y, __ldg(xb + fb), __ldg(xb + nb + fb), __ldg(xb + tb),
+                                        __ldg(xb + nb + tb));
     if (MODE == CADJ_JTV) {
         const double *vb = A.v + (size_t)b * A.mc;
         const double vhf2 = twice(__ldg(vb + 2 * nb + l)), vht2 = twice(__ldg(vb + 2 * nb + nl + l));
@@ -457,9 +491,9 @@ __global__ void __launch_bounds__(128) k_cart_adj_branch(const DevNet N, const C
         ob[2 * nb + nl + l] = twice(fma(c.Pt, dPt, c.Qt * dQt));
     } else {
         const double *lb = A.lam + (size_t)b * A.mc;
-        const CartHess h = cart_hess(y, c, __ldg(lb + fb), __ldg(lb + nb + fb), __ldg(lb + tb),
-                                     __ldg(lb + nb + tb), __ldg(lb + 2 * nb + l),
-                                     __ldg(lb + 2 * nb + nl + l));
+        const CartHess h = cart_hess<PS>(y, c, __ldg(lb + fb), __ldg(lb + nb + fb), __ldg(lb + tb),
+                                         __ldg(lb + nb + tb), __ldg(lb + 2 * nb + l),
+                                         __ldg(lb + 2 * nb + nl + l));
         // rows of the block over (e_f, f_f, e_t, f_t) times u
         put2c(rf, 0, fma(h.eef, uef, fma(h.fef, uff, fma(h.eeft, uet, h.ef_ft * uft))),
               fma(h.fef, uef, fma(h.fff, uff, fma(h.ff_et, uet, h.ffft * uft))));
@@ -534,7 +568,7 @@ size_t record_bytes(const DevNet &N) { return (size_t)N.nslot * CNC * sizeof(dou
 
 // Resident CTAs of a kernel on the current device (looked up once per device and kernel).
 int resident_ctas(const void *kernel, int slot) {
-    static std::atomic<int> cache[64][2];
+    static std::atomic<int> cache[64][3];   // slots: branch, bus, branch with phase shifters
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
     int v = cache[dev][slot].load(std::memory_order_relaxed);
@@ -599,14 +633,18 @@ exago_status cart_adjoint(exago_net_t net, const exago_batch *bt, const double *
             const int nB = std::min(chunk, bt->B - b0);
             A.b0 = b0;
             const dim3 gbr((N.nl + 127) / 128, nB), gbu((N.nb + 127) / 128, nB);
+            const bool ps = N.Gtf != nullptr;   // phase-shifting transformers
             if (mode == CADJ_JVP) {
-                if (N.nl > 0) k_cart_adj_branch<CADJ_JVP><<<gbr, 128, 0, st>>>(N, A);
+                if (N.nl > 0 && ps) k_cart_adj_branch<CADJ_JVP, true><<<gbr, 128, 0, st>>>(N, A);
+                else if (N.nl > 0) k_cart_adj_branch<CADJ_JVP, false><<<gbr, 128, 0, st>>>(N, A);
                 k_cart_adj_bus<CADJ_JVP><<<gbu, 128, 0, st>>>(N, A);
             } else if (mode == CADJ_JTV) {
-                if (N.nl > 0) k_cart_adj_branch<CADJ_JTV><<<gbr, 128, 0, st>>>(N, A);
+                if (N.nl > 0 && ps) k_cart_adj_branch<CADJ_JTV, true><<<gbr, 128, 0, st>>>(N, A);
+                else if (N.nl > 0) k_cart_adj_branch<CADJ_JTV, false><<<gbr, 128, 0, st>>>(N, A);
                 k_cart_adj_bus<CADJ_JTV><<<gbu, 128, 0, st>>>(N, A);
             } else {
-                if (N.nl > 0) k_cart_adj_branch<CADJ_HVP><<<gbr, 128, 0, st>>>(N, A);
+                if (N.nl > 0 && ps) k_cart_adj_branch<CADJ_HVP, true><<<gbr, 128, 0, st>>>(N, A);
+                else if (N.nl > 0) k_cart_adj_branch<CADJ_HVP, false><<<gbr, 128, 0, st>>>(N, A);
                 k_cart_adj_bus<CADJ_HVP><<<gbu, 128, 0, st>>>(N, A);
             }
         }
@@ -708,7 +746,9 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
         R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask; R.gen_mask = bt->gen_mask;
         R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
         R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
-        const int br_ctas = resident_ctas((const void *)k_cart_branch, 0);
+        const bool ps = N.Gtf != nullptr;   // phase-shifting transformers
+        const void *kbr = ps ? (const void *)k_cart_branch<true> : (const void *)k_cart_branch<false>;
+        const int br_ctas = resident_ctas(kbr, ps ? 2 : 0);
         const int bu_ctas = resident_ctas((const void *)k_cart_bus, 1);
         // chunk k: branch kernel on `main`, then its bus kernel on `side` (after an event), so the
         // FP64-bound branch work of chunk k + 1 overlaps the latency-bound bus work of chunk k;
@@ -727,7 +767,8 @@ exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, 
                 const int br_items = nB * ((N.nl + 127) / 128), bus_items = nB * ((N.nb + 127) / 128);
                 if (pl && k >= ring) cudaStreamWaitEvent(main, pl->ev_bu[(k - ring) % (ring + 1)], 0);
                 if (N.nl > 0)
-                    k_cart_branch<<<std::min(br_items, br_ctas), 128, 0, main>>>(N, Rk, nB);
+                    if (ps) k_cart_branch<true><<<std::min(br_items, br_ctas), 128, 0, main>>>(N, Rk, nB);
+                    else k_cart_branch<false><<<std::min(br_items, br_ctas), 128, 0, main>>>(N, Rk, nB);
                 cudaStream_t bs = main;
                 if (pl) {
                     cudaEventRecord(pl->ev_br[k % (ring + 1)], main);

@@ -10,8 +10,9 @@
 namespace exago {
 
 // What an item computes: g | h values, Jacobian values, Hessian values; W_GM compiles in the
-// per-state generator mask (st_gmask), which a launch without one leaves out.
-enum : int { W_G = 1, W_J = 2, W_H = 4, W_GM = 8 };
+// per-state generator mask (st_gmask), which a launch without one leaves out; W_PS compiles in
+// phase-shifting transformers (the to end's own mutual admittances, when the net has them).
+enum : int { W_G = 1, W_J = 2, W_H = 4, W_GM = 8, W_PS = 16 };
 
 // Where state b's inputs and outputs live: row b of the batch arrays, or entry b of a gathered
 // batch's state table.
@@ -90,6 +91,28 @@ __device__ __forceinline__ void branch_sincos(double th, double *s, double *c) {
         *c = fma(v, z, 1.0);
     } else {
         sincos_wide(th, s, c);
+    }
+}
+
+// The angle terms of both ends of branch l from s = sin th, c = cos th, th = Va_f - Va_t:
+//   from end:  A_f = Gft c + Bft s,   C_f = Gft s - Bft c;
+//   to end (angle -th):  A_t = Gtf c - Btf s,   C_t = -(Gtf s + Btf c).
+// Without phase shift Gtf = Gft and Btf = Bft (G, Bm), and B c and B s serve both ends.  With PS
+// and a net that has phase-shifting transformers (N.Gtf non-null) the to end reads its own pair.
+template <bool PS>
+__device__ __forceinline__ void angle_terms(const DevNet &N, int l, double G, double Bm, double s,
+                                            double c, double *Af, double *Cf, double *At,
+                                            double *Ct) {
+    const double Bc = Bm * c, Bs = Bm * s;
+    *Af = fma(G, c, Bs);
+    *Cf = fma(G, s, -Bc);
+    if (PS && N.Gtf) {
+        const double Gt = __ldg(N.Gtf + l), Bt = __ldg(N.Btf + l);
+        *At = fma(Gt, c, -(Bt * s));
+        *Ct = -fma(Gt, s, Bt * c);
+    } else {
+        *At = fma(G, c, -Bs);
+        *Ct = -fma(G, s, Bc);
     }
 }
 
@@ -280,9 +303,8 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
 
     double s, c;
     branch_sincos(Vaf - Vat, &s, &c);
-    const double Bc = Bm * c, Bs = Bm * s;
-    const double Af = fma(G, c, Bs), Cf = fma(G, s, -Bc);      // from end, th = Va_f - Va_t
-    const double At = fma(G, c, -Bs), Ct = -fma(G, s, Bc);     // to end,   th = Va_t - Va_f
+    double Af, Cf, At, Ct;    // from end, th = Va_f - Va_t; to end, th = Va_t - Va_f
+    angle_terms<(WANT & W_PS) != 0>(N, l, G, Bm, s, c, &Af, &Cf, &At, &Ct);
     const double VV = Vf * Vt, Vf2 = Vf * Vf, Vt2 = Vt * Vt;
 
     // One end at a time, stored as soon as it is computed, so that fewer values are live at once

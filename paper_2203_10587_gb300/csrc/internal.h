@@ -42,6 +42,7 @@ struct HostPlan {
     double baseMVA = 100.0;
     std::vector<double> Gs, Bs, Pd, Qd, r, x, b, tap, rateA, c2, c1, c0;
     std::vector<double> c2g, c1g;   // 2 c2 baseMVA^2 and c1 baseMVA
+    std::vector<double> shift;      // [nl] phase shift (rad) per branch, or empty: none
     std::vector<int> f, t, gbus;
 
     std::vector<int64_t> Jrowptr, Hrowptr;
@@ -80,7 +81,9 @@ struct DevNet {
     int stage_cap_all[4];                    // buses: its row segments, or components plus rows
     double baseMVA;
     const int *f, *t;
-    const double *Gff, *Bff, *Gtt, *Btt, *Gft, *Bft;   // pi-model admittances (no phase shift: ft == tf)
+    const double *Gff, *Bff, *Gtt, *Btt, *Gft, *Bft;   // pi-model admittances (Gft, Bft: from end's)
+    const double *Gtf, *Btf;     // to end's mutual admittances where they differ (phase-shifting
+                                 // transformers), else nullptr: Gtf = Gft and Btf = Bft
     const double *Gff2, *Bff2, *Gtt2, *Btt2;            // 2 Gff, 2 Bff, 2 Gtt, 2 Btt (exact)
     const double *Kft;                                  // Gft^2 + Bft^2
     const int *slot_ptr, *slot_nbr, *slot_ref, *br_slot, *slot_bus, *slot_pos;
@@ -156,7 +159,8 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
                         const double *Qd, int nl, const int *f, const int *t, const double *r,
                         const double *x, const double *b, const double *tap,
                         const double *rateA, int ng, const int *gbus, const double *c2,
-                        const double *c1, const double *c0, double baseMVA, std::string &err);
+                        const double *c1, const double *c0, double baseMVA,
+                        const double *shift, std::string &err);
 
 // Optional per-kernel timing: an event is recorded on the launching stream before each kernel
 // and after the last one; name[i] labels the interval ev[i] .. ev[i+1].
@@ -168,9 +172,10 @@ struct ProfileHook {
 };
 
 // Kernel launchers (kernels.cu).  Each returns the launch's cudaError_t as int.
-// Y[0..10] = Gff, Bff, Gtt, Btt, Gft, Bft, 2 Gff, 2 Bff, 2 Gtt, 2 Btt, Gft^2 + Bft^2.
+// Y[0..10] = Gff, Bff, Gtt, Btt, Gft, Bft, 2 Gff, 2 Bff, 2 Gtt, 2 Btt, Gft^2 + Bft^2; with a
+// phase shift per branch (shift non-null), Y[11], Y[12] = Gtf, Btf as well.
 int launch_admittance(const double *r, const double *x, const double *b, const double *tap,
-                      int nl, double *const Y[11], void *stream);
+                      const double *shift, int nl, double *const Y[13], void *stream);
 int launch_eval(const DevNet &net, const EvalReq &req, void *stream, ProfileHook *hook = nullptr);
 int launch_eval_pipelined(const DevNet &net, const EvalReq &req, const PipeLaunch &pl,
                           void *stream, ProfileHook *hook = nullptr);

@@ -6,7 +6,8 @@
 // GPU), so the branch arithmetic, not HBM, bounds this path.  The kernels are therefore written
 // to issue as few FP64 instructions as possible:
 //   * one sincos per branch, shared by both ends; B cos and B sin serve both ends' flows and
-//     each A, C term is one fma (no phase shift: the mutual admittances are equal);
+//     each A, C term is one fma (without phase shift the mutual admittances are equal; a net
+//     with phase-shifting transformers takes the to end's own pair in the variants that allow it);
 //   * P and dP/dVm of an end come from one product Gss Vu + Vv A; the angle derivatives are
 //     products of the magnitude derivatives;
 //   * the Lagrangian Hessian block of an end, lamP grad^2 P + lamQ grad^2 Q + mu grad^2 (P^2+Q^2),
@@ -23,14 +24,17 @@ namespace exago {
 
 // ---------------------------------------------------------------------------------------------
 // pi-model admittances (once per network).  ys = 1/(r + jx); Yff = (ys + jb/2)/tau^2,
-// Yft = Ytf = -ys/tau, Ytt = ys + jb/2; tap 0 means tau = 1.
+// Ytt = ys + jb/2; tap 0 means tau = 1.  Without phase shift Yft = Ytf = -ys/tau.  A phase-shifting
+// transformer has the complex ratio T = tau e^{j phi} on the from side: Yft = -ys/conj(T) =
+// -ys e^{j phi}/tau and Ytf = -ys/T = -ys e^{-j phi}/tau (shift non-null; Y[11], Y[12] = Gtf, Btf).
 struct AdmittanceOut {
-    double *Y[11];   // Gff, Bff, Gtt, Btt, Gft, Bft, 2 Gff, 2 Bff, 2 Gtt, 2 Btt, Gft^2 + Bft^2
+    double *Y[13];   // Gff, Bff, Gtt, Btt, Gft, Bft, 2 Gff, 2 Bff, 2 Gtt, 2 Btt, Gft^2 + Bft^2,
+                     // Gtf, Btf
 };
 
 __global__ void k_admittance(const double *__restrict__ r, const double *__restrict__ x,
-                             const double *__restrict__ b, const double *__restrict__ tap, int nl,
-                             AdmittanceOut out) {
+                             const double *__restrict__ b, const double *__restrict__ tap,
+                             const double *__restrict__ shift, int nl, AdmittanceOut out) {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nl) return;
     double rl = r[l], xl = x[l];
@@ -43,10 +47,18 @@ __global__ void k_admittance(const double *__restrict__ r, const double *__restr
     out.Y[1][l] = Bff;
     out.Y[2][l] = gs;
     out.Y[3][l] = bc;
-    const double Gft = -gs / tau, Bft = -bs / tau;
+    double Gft = -gs / tau, Bft = -bs / tau;
+    if (shift) {
+        double sp, cp;
+        sincos(shift[l], &sp, &cp);
+        Gft = -(gs * cp - bs * sp) / tau;        // -(gs + j bs)(cp + j sp) / tau
+        Bft = -(gs * sp + bs * cp) / tau;
+        out.Y[11][l] = -(gs * cp + bs * sp) / tau;   // -(gs + j bs)(cp - j sp) / tau
+        out.Y[12][l] = -(bs * cp - gs * sp) / tau;
+    }
     out.Y[4][l] = Gft;
     out.Y[5][l] = Bft;
-    out.Y[10][l] = fma(Gft, Gft, Bft * Bft);
+    out.Y[10][l] = fma(Gft, Gft, Bft * Bft);     // |Yft|^2 = |Ytf|^2
     out.Y[6][l] = 2.0 * Gff;     // doubling is exact
     out.Y[7][l] = 2.0 * Bff;
     out.Y[8][l] = 2.0 * gs;
@@ -54,11 +66,11 @@ __global__ void k_admittance(const double *__restrict__ r, const double *__restr
 }
 
 int launch_admittance(const double *r, const double *x, const double *b, const double *tap,
-                      int nl, double *const Y[11], void *stream) {
+                      const double *shift, int nl, double *const Y[13], void *stream) {
     if (nl <= 0) return 0;
     AdmittanceOut out;
-    for (int k = 0; k < 11; k++) out.Y[k] = Y[k];
-    k_admittance<<<(nl + 127) / 128, 128, 0, (cudaStream_t)stream>>>(r, x, b, tap, nl, out);
+    for (int k = 0; k < 13; k++) out.Y[k] = Y[k];
+    k_admittance<<<(nl + 127) / 128, 128, 0, (cudaStream_t)stream>>>(r, x, b, tap, shift, nl, out);
     return (int)cudaGetLastError();
 }
 
@@ -68,7 +80,8 @@ template <int WANT>
 __global__ void __launch_bounds__(128) k_branch(const DevNet N, const EvalReq R, int b0) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     const int b = b0 + blockIdx.y;
-    if (l < N.nl) branch_item<WANT>(N, R, b, l, R.scratch + (size_t)(b - R.scr_b0) * N.nslot * NCOMP);
+    // this schedule always honours phase-shifting transformers (W_PS)
+    if (l < N.nl) branch_item<WANT | W_PS>(N, R, b, l, R.scratch + (size_t)(b - R.scr_b0) * N.nslot * NCOMP);
 }
 
 template <int WANT>

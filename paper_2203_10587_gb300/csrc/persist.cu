@@ -61,8 +61,8 @@ int launch_eval_persistent(const DevNet &N, const EvalReq &R, const PersistLaunc
     if (e != cudaSuccess) return (int)e;
     int grid = L.grid < P.total ? L.grid : P.total;
     int rc;
-    if (R.gen_mask || R.tab) {
-        // generator masks (a gathered batch's states may carry their own)
+    if (R.gen_mask || R.tab || N.Gtf) {
+        // generator masks (a gathered batch's states may carry their own) or phase shifters
         rc = launch_persist_gm(L.block, N, R, P, grid, L.occ_warps, st);
     } else if (L.block == 32) rc = launch_persist_nt<32, 0>(N, R, P, grid, L.occ_warps, st);
     else if (L.block == 256) rc = launch_persist_nt<256, 0>(N, R, P, grid, L.occ_warps, st);

@@ -35,7 +35,8 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
                         const double *Qd, int nl, const int *f, const int *t, const double *r,
                         const double *x, const double *b, const double *tap,
                         const double *rateA, int ng, const int *gbus, const double *c2,
-                        const double *c1, const double *c0, double baseMVA, std::string &err) {
+                        const double *c1, const double *c0, double baseMVA,
+                        const double *shift, std::string &err) {
     char msg[256];
     if (nb < 1 || nl < 0 || ng < 0) {
         err = "need nb >= 1, nl >= 0, ng >= 0";
@@ -78,6 +79,10 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
         if (!finite_all(v->data(), nb)) { err = "non-finite bus data"; return EXAGO_EINVAL; }
     for (auto *v : {&p.r, &p.x, &p.b, &p.tap, &p.rateA})
         if (!finite_all(v->data(), nl)) { err = "non-finite branch data"; return EXAGO_EINVAL; }
+    if (shift && nl > 0) {
+        p.shift.assign(shift, shift + nl);
+        if (!finite_all(p.shift.data(), nl)) { err = "non-finite phase shift"; return EXAGO_EINVAL; }
+    }
     for (auto *v : {&p.c2, &p.c1, &p.c0})
         if (!finite_all(v->data(), ng)) { err = "non-finite generator data"; return EXAGO_EINVAL; }
     for (int l = 0; l < nl; l++) {

@@ -24,7 +24,8 @@ STATUS = {0: "EXAGO_OK", 1: "EXAGO_EINVAL", 2: "EXAGO_ENOMEM", 3: "EXAGO_ECUDA",
 
 # every symbol include/exago.h declares (checked by tests/test_capi_host.py)
 EXPORTS = [
-    "exago_last_error", "exago_status_name", "exago_net_create", "exago_net_plan",
+    "exago_last_error", "exago_status_name", "exago_net_create", "exago_net_create_shift",
+    "exago_net_plan",
     "exago_net_destroy", "exago_net_dims", "exago_net_jac_pattern", "exago_net_hess_pattern",
     "exago_net_ineq_bounds", "exago_net_plan_array", "exago_eval_workspace_size",
     "exago_net_reserve", "exago_eval_obj", "exago_eval_grad", "exago_eval_cons",
@@ -88,6 +89,7 @@ def lib():
                 "exago_last_error": ([], ctypes.c_char_p),
                 "exago_status_name": ([i32], ctypes.c_char_p),
                 "exago_net_create": (net_args, i32),
+                "exago_net_create_shift": (net_args[:12] + [vp] + net_args[12:], i32),
                 "exago_net_plan": (net_args, i32),
                 "exago_net_destroy": ([vp], i32),
                 "exago_net_dims": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
@@ -201,6 +203,20 @@ def exago_net_create(nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng, gbus
     """Host numpy arrays in; returns the opaque net handle (on the current CUDA device)."""
     return _net_call(lib().exago_net_create, nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA,
                      ng, gbus, c2, c1, c0, baseMVA)
+
+
+def exago_net_create_shift(nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, shift, rateA, ng, gbus,
+                           c2, c1, c0, baseMVA):
+    """exago_net_create with a per-branch phase shift (rad) of phase-shifting transformers."""
+    d = lambda a: _np(a, np.float64)
+    i = lambda a: _np(a, np.int32)
+    keep = [d(Gs), d(Bs), d(Pd), d(Qd), i(f), i(t), d(r), d(x), d(b), d(tap),
+            None if shift is None else d(shift), d(rateA), i(gbus), d(c2), d(c1), d(c0)]
+    h = ctypes.c_void_p()
+    _check(lib().exago_net_create_shift(int(nb), *map(_hp, keep[:4]), int(nl),
+                                        *map(_hp, keep[4:12]), int(ng), *map(_hp, keep[12:]),
+                                        float(baseMVA), ctypes.byref(h)))
+    return h
 
 
 def exago_net_plan(nb, Gs, Bs, Pd, Qd, nl, f, t, r, x, b, tap, rateA, ng, gbus, c2, c1, c0,
@@ -586,7 +602,12 @@ class Net:
     """Owns a net handle built from a synth.Grid-like object (nb, Gs, ..., baseMVA)."""
 
     def __init__(self, grid, plan_only: bool = False):
-        self.h = (exago_net_plan if plan_only else exago_net_create)(*_grid_args(grid))
+        shift = getattr(grid, "shift", None)
+        if shift is not None and not plan_only:   # phase-shifting transformers
+            a = _grid_args(grid)
+            self.h = exago_net_create_shift(*a[:12], shift, *a[12:])
+        else:
+            self.h = (exago_net_plan if plan_only else exago_net_create)(*_grid_args(grid))
         self.n, self.m_eq, self.m_ineq, self.nnzJ, self.nnzH = exago_net_dims(self.h)
         self.m = self.m_eq + self.m_ineq
         self.nb, self.nl, self.ng = grid.nb, grid.nl, grid.ng

@@ -272,6 +272,23 @@ def test_create_without_gpu_fails_cleanly(L):
     assert ei.value.name in ("EXAGO_ECUDA", "EXAGO_ENOMEM")
 
 
+def test_phase_shift_validation(L):
+    """exago_net_create_shift validates the shifts on the host before any device work: a
+    non-finite shift is EINVAL (on any machine); without a GPU a valid one fails at the upload."""
+    import torch
+    g = synth.make_grid(9, 20, 26, 5, shifter_frac=0.3)
+    a = exago._grid_args(g)
+    bad = g.shift.copy()
+    bad[4] = np.nan
+    with pytest.raises(exago.ExagoError) as ei:
+        exago.exago_net_create_shift(*a[:12], bad, *a[12:])
+    assert ei.value.name == "EXAGO_EINVAL" and "phase shift" in str(ei.value)
+    if not torch.cuda.is_available():
+        with pytest.raises(exago.ExagoError) as ei:
+            exago.Net(g)
+        assert ei.value.name in ("EXAGO_ECUDA", "EXAGO_ENOMEM")
+
+
 # ---- coupling (ramp) rows: host side ---------------------------------------------------------
 
 def coupling_parents():
