@@ -544,6 +544,80 @@ def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):
                         "of records stays in L2"}
 
 
+def run_kkt(exago, synth, torch, np, dev):
+    """The interior-point KKT step (exago_kkt_solve) of the 2,000-bus x 512 N-1 batch, with the
+    batch's own Jacobian and Lagrangian Hessian (exago_eval_all), dx_i = 1 + sum_j |W_ij|,
+    dc ~ U(0.5, 2), rhs ~ N(0, 1): assembly, eliminations, the batched block L D L' and both
+    sweeps, CUDA events over back-to-back calls.  FP64-bound: the flops per state are
+    exago_kkt_info's count (its 4 x 4 block products dominate)."""
+    g = synth.grid_2000()
+    b = synth.contingency_batch(3, g, 512)
+    B = b.B
+    net = exago.Net(g)
+    td = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    bt = exago.make_batch(td(b.x, torch.float64), td(b.lam, torch.float64),
+                          td(b.mask, torch.uint8), obj_factor=1.0)
+    out = net.outputs(B, dev, f=False, grad=False, gh=False)
+    net.eval_all(bt, out)
+    # dx = 1 + the absolute row sums of W (both triangles from the lower one)
+    hp, hc = exago.exago_net_hess_pattern(net.h)
+    rows = torch.as_tensor(np.repeat(np.arange(net.n), np.diff(hp)), device=dev)
+    cols = torch.as_tensor(hc.astype(np.int64), device=dev)
+    a = out["hval"].abs()
+    dx = torch.ones(B, net.n, dtype=torch.float64, device=dev)
+    dx.index_add_(1, rows, a)
+    dx.index_add_(1, cols, a * (rows != cols).to(torch.float64))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
+    dc = 0.5 + 1.5 * torch.rand(B, net.m, dtype=torch.float64, device=dev, generator=gen)
+    rhs = torch.randn(B, net.n + net.m, dtype=torch.float64, device=dev, generator=gen)
+    sol = torch.empty_like(rhs)
+    inertia = torch.empty(B, 2, dtype=torch.int32, device=dev)
+    k = exago.exago_kkt_create(net.h)
+    info = exago.exago_kkt_info(k)
+    ws = torch.empty(exago.exago_kkt_workspace_size(k, B), dtype=torch.uint8, device=dev)
+    fn = lambda: exago.exago_kkt_solve(k, out["jval"], out["hval"], dx, dc, rhs, sol, inertia, ws)
+    ms = time_calls(torch, fn, 10, warm=2)
+    ok = bool((inertia[:, 0] == net.m).all().item() and (inertia[:, 1] == 0).all().item())
+    exago.exago_kkt_destroy(k)
+    net.close()
+    flops = info["flops"] * B
+    return {"workload": "2000-bus x 512 N-1 states: KKT [[W + Dx, J'], [J, -Dc]] step per state",
+            "ms_per_batch": ms, "states_per_s": B / (ms * 1e-3),
+            "factor_blocks": info["blocks"], "block_products_per_state": info["pairs"],
+            "levels": info["levels"], "flops_per_state": info["flops"],
+            "tflops": flops / (ms * 1e-3) / 1e12,
+            "frac_fp64_peak": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+            "inertia_all_correct": ok}
+
+
+def run_pflow(exago, synth, torch, np, dev):
+    """One power-flow Newton step (exago_pf_step: the evaluation of g and J, then the batched
+    2 x 2-block LU of J_pf and both sweeps) for 512 states of a 2,000-bus grid (light load, flat
+    start), CUDA events over back-to-back calls."""
+    g = synth.make_grid(33, 2000, 2700, 500, transformer_frac=0.2)
+    g.Pd *= 0.3
+    g.Qd *= 0.3
+    bt_ = np.ones(g.nb, np.int32)
+    bt_[g.gbus] = 2
+    bt_[g.gbus[0]] = 3
+    x0 = np.concatenate([np.zeros(g.nb), np.ones(g.nb), np.full(g.ng, g.Pd.sum() / g.ng),
+                         np.zeros(g.ng)])
+    B = 512
+    net = exago.Net(g)
+    X = torch.as_tensor(np.repeat(x0[None, :], B, axis=0), device=dev)
+    pf = exago.exago_pf_create(net.h, bt_)
+    ws = torch.empty(exago.exago_pf_workspace_size(pf, B), dtype=torch.uint8, device=dev)
+    bt = exago.make_batch(X, workspace=ws)
+    Xn = torch.empty_like(X)
+    mis = torch.empty(B, dtype=torch.float64, device=dev)
+    ms = time_calls(torch, lambda: exago.exago_pf_step(pf, bt, Xn, mis), 20, warm=2)
+    exago.exago_pf_destroy(pf)
+    net.close()
+    return {"workload": "2000-bus x 512 states: one power-flow Newton step (g, J, factor, solve)",
+            "ms_per_batch": ms, "states_per_s": B / (ms * 1e-3)}
+
+
 def run_serve(exago, synth, torch, np, dev, seconds):
     rng = np.random.default_rng(5)
     sc = ServeClients(exago, synth, torch, np, dev)
@@ -758,6 +832,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     cartesian = None if args.no_serve else run_cartesian(exago, synth, torch, np, dev, hbm_peak,
                                                          top_ms)
     slacks = None if args.no_serve else run_slacks(exago, synth, torch, np, dev, hbm_peak)
+    kkt = None if args.no_serve else run_kkt(exago, synth, torch, np, dev)
+    pflow = None if args.no_serve else run_pflow(exago, synth, torch, np, dev)
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -804,6 +880,10 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         res["cartesian"] = cartesian
     if slacks is not None:
         res["feasibility_slacks"] = slacks
+    if kkt is not None:
+        res["kkt_step"] = kkt
+    if pflow is not None:
+        res["pflow_step"] = pflow
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_evals = 256 * cores

@@ -509,6 +509,78 @@ exago_status exago_serve_stats(exago_server_t server, double *p50_ms, double *p9
 exago_status exago_serve_destroy(exago_server_t server);
 
 /*
+ * Batched interior-point KKT step (the linear solve the paper's solvers, Ipopt and HiOp, perform
+ * once per iteration, Sec. II-III; one per contingency or scenario subproblem under EMPAR,
+ * Sec. V-A, eqs. (16)-(20), and Sec. VI-A).  For every state b of a batch it solves
+ *     K_b [dx; dlam] = r_b,    K_b = [[W_b + diag(dx_b), J_b'], [J_b, -diag(dc_b)]]
+ * with W_b the Lagrangian Hessian and J_b the Jacobian of [g; h] exactly as exago_eval_all writes
+ * them (hval [B][nnzH], the lower triangle; jval [B][nnzJ]).  The flow rows and the generator
+ * variables are eliminated first (they create no fill), then the remaining 4 x 4 block per bus
+ * (Va, Vm, lamP, lamQ) is factored by a batched block L D L' without pivoting on a minimum-degree
+ * order of the bus graph computed once by exago_kkt_create.  K must be factorable without
+ * pivoting: it is whenever W + diag(dx) is positive definite and dc > 0 (a quasi-definite K;
+ * interior-point methods regularise to that), and dx of every Qg must be nonzero.
+ *   exago_kkt_create      symbolic analysis on the host (ordering, factor structure, update
+ *                         lists, levels) and upload.  On a net made by exago_net_plan it does the
+ *                         analysis alone (info and order answer; solve returns ESTATE).  The
+ *                         handle refers to the net, which must outlive it.
+ *   exago_kkt_order       host arrays [nb] (each may be NULL): perm (the bus eliminated k-th),
+ *                         parent (elimination tree over elimination indices, -1 at a root) and
+ *                         level (0 at the leaves; columns of one level are factored together).
+ *   exago_kkt_info        factor blocks, update pairs (4 x 4 block products per state), levels of
+ *                         the elimination tree, and FP64 flops of one state's factor and solve.
+ *   exago_kkt_workspace_size  scratch bytes for B states (two factor arrays of 16 blocks x 8 B x B
+ *                         per factor block, the reduced vectors and counters).
+ *   exago_kkt_solve       DEVICE pointers, row-major per state: jval [B][nnzJ], hval [B][nnzH],
+ *                         dx [B][n], dc [B][m] (> 0), rhs [B][n + m]; sol [B][n + m] receives
+ *                         [dx; dlam].  inertia [B][2] (or NULL) receives the number of negative
+ *                         pivots of the whole factorisation (m for a correct interior-point step)
+ *                         and of pivots below 1e-13 of their block (0 unless K is numerically
+ *                         singular without pivoting).  workspace: at least exago_kkt_workspace_size
+ *                         bytes, 256-byte aligned, or NULL for the handle's own (grown on demand;
+ *                         a growth synchronises the device; calls using it must be ordered).
+ *                         Asynchronous on `stream`.  EINVAL for null arguments or B too large.
+ */
+typedef struct exago_kkt *exago_kkt_t;
+exago_status exago_kkt_create(exago_net_t net, exago_kkt_t *out);
+exago_status exago_kkt_destroy(exago_kkt_t kkt);
+exago_status exago_kkt_info(exago_kkt_t kkt, int64_t *blocks, int64_t *pairs, int *levels,
+                            double *flops);
+exago_status exago_kkt_order(exago_kkt_t kkt, int *perm, int *parent, int *level);
+exago_status exago_kkt_workspace_size(exago_kkt_t kkt, int B, size_t *bytes);
+exago_status exago_kkt_solve(exago_kkt_t kkt, int B, const double *jval, const double *hval,
+                             const double *dx, const double *dc, const double *rhs, double *sol,
+                             int *inertia, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Batched power-flow Newton step (PFLOW, the paper's power-flow application; balances of Sec. III,
+ * eq. (8)).  Buses are PQ (type 1), PV (2) or slack (3); Pg, Qg and the PV and slack set points
+ * are data in x.  For every state of the batch one step solves J_pf d = -g_pf, where g_pf holds the
+ * P balances of the non-slack buses and the Q balances of the PQ buses and d the changes of Va
+ * (non-slack buses) and Vm (PQ buses), and writes x + d.  g and J are exago_eval_all's at x
+ * (batch->mask, gen_mask and pd_scale apply); J_pf is factored without pivoting on a minimum-degree
+ * order of the bus graph (2 x 2 blocks per bus, the fixed unknowns' rows replaced by identity
+ * rows, so they do not move).
+ *   exago_pf_create          validates bus_type (host [nb], values 1..3, at least one slack) and
+ *                            runs the symbolic analysis; the net must have a device and outlive
+ *                            the handle.
+ *   exago_pf_workspace_size  scratch bytes for B states (g, J, four factor arrays, vectors).
+ *   exago_pf_step            x_new [B][n] (DEVICE; may equal batch->x) = x + d, Pg and Qg copied;
+ *                            mismatch [B] (or NULL) = max |g_pf(x)| before the step.
+ *                            batch->workspace: at least exago_pf_workspace_size bytes, or NULL for
+ *                            the handle's own (grown on demand, synchronising the device; calls
+ *                            using it must be ordered); the evaluation inside uses the net's
+ *                            internal workspace.  batch->lambda is ignored.  Asynchronous on
+ *                            batch->stream.
+ */
+typedef struct exago_pf *exago_pf_t;
+exago_status exago_pf_create(exago_net_t net, const int *bus_type, exago_pf_t *out);
+exago_status exago_pf_destroy(exago_pf_t pf);
+exago_status exago_pf_workspace_size(exago_pf_t pf, int B, size_t *bytes);
+exago_status exago_pf_step(exago_pf_t pf, const exago_batch *batch, double *x_new,
+                           double *mismatch);
+
+/*
  * Testing only: the next n device allocations made by the library (network tables, workspaces,
  * serving arenas) fail as if the device were out of memory, so that callers' ENOMEM paths can be
  * exercised without exhausting a GPU.  n <= 0 clears the hook.  The paper has no counterpart.

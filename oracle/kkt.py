@@ -69,12 +69,13 @@ def pf_sets(nb: int, bus_type):
     return np.concatenate([ns, nb + pq]), np.concatenate([ns, nb + pq])
 
 
-def pf_newton_step(om, net, x, bus_type, gen_mask=None, mask=None):
+def pf_newton_step(om, net, x, bus_type, gen_mask=None, mask=None, pd_scale=None):
     """One power-flow Newton step: returns (x_new, mismatch), mismatch = max |g_pf(x)| before
-    the step.  om is oracle.acopf; g and J are its evaluation at x (multipliers irrelevant)."""
+    the step.  om is oracle.acopf; g and J are its evaluation at x (multipliers irrelevant;
+    branch mask, generator mask and load scale as in the evaluation)."""
     nb = net.nb
     lam = np.zeros(net.m)
-    r = om.evaluate(net, x, lam, mask, None, 1.0, 0.0, want_hess=False, gen_mask=gen_mask)
+    r = om.evaluate(net, x, lam, mask, pd_scale, 1.0, 0.0, want_hess=False, gen_mask=gen_mask)
     cols, rows = pf_sets(nb, bus_type)
     jp, jc, jv = r["J"]
     Js = sp.csr_matrix((jv, jc, jp), shape=(net.m, net.n))

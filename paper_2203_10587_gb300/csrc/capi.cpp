@@ -642,6 +642,12 @@ exago_status eval_locked(exago_net *net, const exago_batch *bt, double *f, doubl
 
 namespace exago {
 
+bool net_plan_view(exago_net_t net, const HostPlan **plan) {
+    if (!net) return false;
+    *plan = &net->plan;
+    return true;
+}
+
 bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **dev, int *device) {
     if (!net || !net->on_device) return false;
     *plan = &net->plan;

@@ -212,6 +212,8 @@ int bus_blocks_per_sm(size_t smem_bytes);   // k_bus blocks of 128 threads per S
 // Read-only view of a net's plan and device tables (false for NULL or a plan-only net), and the
 // thread-local error setter of the C ABI.  Used by entry points defined outside capi.cpp.
 bool net_internal_view(exago_net_t net, const HostPlan **plan, const DevNet **dev, int *device);
+// The host plan of any net, with or without a device (false for NULL).
+bool net_plan_view(exago_net_t net, const HostPlan **plan);
 exago_status set_last_error(exago_status s, const std::string &msg);
 // Shared-memory doubles of a bus tile of the multi-kernel schedule's bus kernel (128 threads),
 // within the budget that keeps its register-limited residency, as exago_eval_all launches it.

@@ -40,6 +40,10 @@ EXPORTS = [
     "exago_net_jac_pattern_cart", "exago_eval_cart_workspace_size", "exago_eval_cart",
     "exago_eval_cart_jvp", "exago_eval_cart_jtv", "exago_eval_cart_hvp", "exago_slack_create",
     "exago_slack_destroy", "exago_slack_pattern", "exago_eval_slack", "exago_eval_slack_jtv",
+    "exago_kkt_create", "exago_kkt_destroy", "exago_kkt_info", "exago_kkt_order",
+    "exago_kkt_workspace_size", "exago_pf_create", "exago_pf_destroy", "exago_pf_workspace_size",
+    "exago_pf_step",
+    "exago_kkt_solve",
 ]
 
 SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
@@ -153,6 +157,18 @@ def lib():
                 "exago_coupling_jac_pattern": ([vp, vp, vp, vp], i32),
                 "exago_eval_coupling": ([vp, vp, vp, vp], i32),
                 "exago_eval_coupling_jtv": ([vp, vp, vp, ctypes.c_int64, i32, vp], i32),
+                "exago_kkt_create": ([vp, ctypes.POINTER(vp)], i32),
+                "exago_kkt_destroy": ([vp], i32),
+                "exago_kkt_info": ([vp, i64p, i64p, ctypes.POINTER(i32),
+                                    ctypes.POINTER(ctypes.c_double)], i32),
+                "exago_kkt_order": ([vp, vp, vp, vp], i32),
+                "exago_kkt_workspace_size": ([vp, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
+                "exago_kkt_solve": ([vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp],
+                                    i32),
+                "exago_pf_create": ([vp, vp, ctypes.POINTER(vp)], i32),
+                "exago_pf_destroy": ([vp], i32),
+                "exago_pf_workspace_size": ([vp, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
+                "exago_pf_step": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -588,6 +604,78 @@ def exago_eval_coupling_jtv(h, nu, out, ldo: int, accumulate: bool = False, stre
     optr = out if isinstance(out, int) else _out(out)
     _check(lib().exago_eval_coupling_jtv(h, _dp(nu, torch.float64), optr, int(ldo),
                                          1 if accumulate else 0, _stream_ptr(stream)))
+
+
+# ---- interior-point KKT step ------------------------------------------------------------------
+
+def exago_kkt_create(net_h):
+    h = ctypes.c_void_p()
+    _check(lib().exago_kkt_create(net_h, ctypes.byref(h)))
+    return h
+
+
+def exago_kkt_destroy(h):
+    _check(lib().exago_kkt_destroy(h))
+
+
+def exago_kkt_info(h) -> dict:
+    blocks, pairs = ctypes.c_int64(), ctypes.c_int64()
+    levels, flops = ctypes.c_int(), ctypes.c_double()
+    _check(lib().exago_kkt_info(h, ctypes.byref(blocks), ctypes.byref(pairs), ctypes.byref(levels),
+                                ctypes.byref(flops)))
+    return {"blocks": blocks.value, "pairs": pairs.value, "levels": levels.value,
+            "flops": flops.value}
+
+
+def exago_kkt_order(h, nb: int):
+    """(perm, parent, level) of the KKT factorisation's elimination order (numpy int32 [nb])."""
+    perm, parent, level = (np.zeros(nb, np.int32) for _ in range(3))
+    _check(lib().exago_kkt_order(h, _hp(perm), _hp(parent), _hp(level)))
+    return perm, parent, level
+
+
+def exago_kkt_workspace_size(h, B: int) -> int:
+    v = ctypes.c_size_t()
+    _check(lib().exago_kkt_workspace_size(h, int(B), ctypes.byref(v)))
+    return v.value
+
+
+def exago_kkt_solve(h, jval, hval, dx, dc, rhs, sol, inertia=None, workspace=None, stream=None):
+    """sol [B][n + m] = K^{-1} rhs per state (CUDA float64 tensors, row-major per state);
+    inertia: CUDA int32 [B][2] or None."""
+    import torch
+    B = int(jval.shape[0])
+    ws, wb = (None, 0) if workspace is None else (_dp(workspace), workspace.numel() * workspace.element_size())
+    _check(lib().exago_kkt_solve(h, B, _dp(jval, torch.float64), _dp(hval, torch.float64),
+                                 _dp(dx, torch.float64), _dp(dc, torch.float64),
+                                 _dp(rhs, torch.float64), _out(sol),
+                                 None if inertia is None else _dp(inertia, torch.int32), ws, wb,
+                                 _stream_ptr(stream)))
+
+
+# ---- power-flow Newton step ---------------------------------------------------------------------
+
+def exago_pf_create(net_h, bus_type):
+    bt = _np(bus_type, np.int32)
+    h = ctypes.c_void_p()
+    _check(lib().exago_pf_create(net_h, _hp(bt), ctypes.byref(h)))
+    return h
+
+
+def exago_pf_destroy(h):
+    _check(lib().exago_pf_destroy(h))
+
+
+def exago_pf_workspace_size(h, B: int) -> int:
+    v = ctypes.c_size_t()
+    _check(lib().exago_pf_workspace_size(h, int(B), ctypes.byref(v)))
+    return v.value
+
+
+def exago_pf_step(h, batch: exago_batch, x_new, mismatch=None):
+    """x_new [B][n] = x + d (one Newton step per state); mismatch [B] = max |g_pf(x)|."""
+    _check(lib().exago_pf_step(h, ctypes.byref(batch), _out(x_new),
+                               None if mismatch is None else _out(mismatch)))
 
 
 # ---- convenience ------------------------------------------------------------------------------

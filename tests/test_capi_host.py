@@ -407,3 +407,60 @@ def test_slack_pattern_and_validation(L):
         with pytest.raises(exago.ExagoError) as ei:
             exago.Slack(net, kw["bus"], kw["row"], kw["sign"], kw["cost"])
         assert ei.value.name == "EXAGO_EINVAL"
+
+
+# ---- KKT step: host symbolic analysis ------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["30bus", "parallel", "300bus", "2000bus"])
+def test_kkt_symbolic_is_minimum_degree_with_its_fill(L, name):
+    """exago_kkt_create on a plan-only net runs the symbolic analysis alone.  Replaying the
+    elimination on the bus graph here: every eliminated bus had the least current degree (lowest
+    index on ties), the number of factor blocks is nb plus the fill-inclusive neighbour counts,
+    and each column's level exceeds those of its elimination-tree children."""
+    g = {"30bus": synth.grid_30bus, "parallel": parallel_grid, "2000bus": synth.grid_2000,
+         "300bus": lambda: synth.make_grid(13, 300, 389, 77)}[name]()
+    net = plan(g)
+    k = exago.exago_kkt_create(net.h)
+    try:
+        info = exago.exago_kkt_info(k)
+        perm, parent, level = exago.exago_kkt_order(k, g.nb)
+    finally:
+        exago.exago_kkt_destroy(k)
+    assert sorted(perm.tolist()) == list(range(g.nb))
+    adj = [set() for _ in range(g.nb)]
+    for f, t in zip(g.f.tolist(), g.t.tolist()):
+        if f != t:
+            adj[f].add(t)
+            adj[t].add(f)
+    alive = set(range(g.nb))
+    blocks = 0
+    iperm = np.empty(g.nb, np.int64)
+    iperm[perm] = np.arange(g.nb)
+    for kk, v in enumerate(perm.tolist()):
+        dmin = min(len(adj[u]) for u in alive)
+        assert len(adj[v]) == dmin and v == min(u for u in alive if len(adj[u]) == dmin)
+        N = adj[v]
+        blocks += 1 + len(N)
+        want_parent = min(iperm[u] for u in N) if N else -1
+        assert parent[kk] == want_parent
+        for u in N:
+            adj[u] |= N
+            adj[u].discard(u)
+            adj[u].discard(v)
+        alive.discard(v)
+        adj[v] = set()
+    assert info["blocks"] == blocks
+    for kk in range(g.nb):
+        if parent[kk] >= 0:
+            assert level[parent[kk]] > level[kk]
+    assert info["levels"] == level.max() + 1
+
+
+def test_kkt_solve_needs_a_device_net(L):
+    net = plan(synth.grid_30bus())
+    k = exago.exago_kkt_create(net.h)
+    try:
+        rc = L.exago_kkt_solve(k, 1, 8, 8, 8, 8, 8, 8, None, None, 0, None)
+        assert exago.STATUS[rc] == "EXAGO_ESTATE"
+    finally:
+        exago.exago_kkt_destroy(k)
