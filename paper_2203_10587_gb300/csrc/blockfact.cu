@@ -182,6 +182,166 @@ __global__ void __launch_bounds__(kNT) k_bf_scale(const DevSymK S, int B, const 
     }
 }
 
+// ---- split variants: the terms of one target (or one column's sweep) divided among kSlices
+// warps of a block that holds 32 states; slice w takes every kSlices-th term from the w-th, and
+// warp 0 adds the slices' partial sums in slice order.  Used where a level has few targets, so
+// that the long sums of the dense top of the elimination tree are not one thread's latency
+// chain.  The split is fixed by the structure alone (never by the batch size), so every state's
+// result is the same whatever the batch it belongs to.
+constexpr int kSlices = 8;
+
+template <int BS, bool SYM>
+__global__ void __launch_bounds__(32 * kSlices) k_bf_update_split(const DevSymK S, int B, double *T,
+                                                                  double *TU, const double *L,
+                                                                  const double *U, int t0) {
+    constexpr int BB = BS * BS, NP = SYM ? BB : 2 * BB;   // partial sums: lower (and upper)
+    __shared__ double part[kSlices][NP][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int b = blockIdx.y * 32 + lane;
+    const bool live = b < B;
+    const int t = t0 + blockIdx.x;
+    const int p = __ldg(S.tgt_blk + t);
+    const bool diag = p == __ldg(S.tgt_diag + t);
+    const int64_t q0 = __ldg(S.tptr + t), q1 = __ldg(S.tptr + t + 1);
+    if (q0 == q1) return;   // uniform over the block
+    double acc[BB], accU[BB];
+#pragma unroll
+    for (int e = 0; e < BB; e++) { acc[e] = 0.0; accU[e] = 0.0; }
+    if (live)
+        for (int64_t q = q0 + w; q < q1; q += kSlices) {
+            const int2 pr = __ldg(S.pairs + q);
+            double X[BB], Y[BB];
+            load_blk_cg<BS>(T, pr.x, B, b, X);
+            if (SYM) {
+                load_blk_cg<BS>(L, pr.y, B, b, Y);
+                sub_mul<BS, true>(acc, X, Y);
+            } else {
+                load_blk_cg<BS>(U, pr.y, B, b, Y);
+                sub_mul<BS, false>(acc, X, Y);
+                if (!diag) {
+                    load_blk_cg<BS>(T, pr.y, B, b, X);
+                    load_blk_cg<BS>(U, pr.x, B, b, Y);
+                    sub_mul<BS, false>(accU, X, Y);
+                }
+            }
+        }
+#pragma unroll
+    for (int e = 0; e < BB; e++) {
+        part[w][e][lane] = acc[e];
+        if (!SYM) part[w][(NP - BB) + e][lane] = accU[e];
+    }
+    __syncthreads();
+    if (w != 0 || !live) return;
+    load_blk_cg<BS>(T, p, B, b, acc);
+    if (!SYM && !diag) load_blk_cg<BS>(TU, p, B, b, accU);
+#pragma unroll
+    for (int e = 0; e < BB; e++) {
+        double s = part[0][e][lane];
+#pragma unroll
+        for (int v = 1; v < kSlices; v++) s += part[v][e][lane];
+        acc[e] += s;
+        if (!SYM) {
+            double su = part[0][(NP - BB) + e][lane];
+#pragma unroll
+            for (int v = 1; v < kSlices; v++) su += part[v][(NP - BB) + e][lane];
+            accU[e] += su;
+        }
+    }
+    store_blk<BS>(T, p, B, b, acc);
+    if (!SYM && !diag) store_blk<BS>(TU, p, B, b, accU);
+}
+
+// Forward sweep of one level's columns, split: y_J = r_J + (the slices' sums of -F_JK z_K);
+// z_J = D_J^-1 y_J.
+template <int BS>
+__global__ void __launch_bounds__(32 * kSlices) k_bf_forward_split(const DevSymK S, int B,
+                                                                   const double *T,
+                                                                   const double *L, double *x,
+                                                                   int c0) {
+    __shared__ double part[kSlices][BS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int b = blockIdx.y * 32 + lane;
+    const bool live = b < B;
+    const int J = __ldg(S.lvl_cols + c0 + blockIdx.x);
+    double y[BS];
+#pragma unroll
+    for (int i = 0; i < BS; i++) y[i] = 0.0;
+    const int64_t r0 = __ldg(S.rowptr + J), r1 = __ldg(S.rowptr + J + 1);
+    if (live)
+        for (int64_t r = r0 + w; r < r1; r += kSlices) {
+            const int K = __ldg(S.rowcol + r), p = __ldg(S.rowblk + r);
+            double F[BS * BS], z[BS];
+            load_blk<BS>(T, p, B, b, F);
+#pragma unroll
+            for (int i = 0; i < BS; i++) z[i] = __ldcg(x + ((size_t)K * BS + i) * B + b);
+#pragma unroll
+            for (int i = 0; i < BS; i++)
+#pragma unroll
+                for (int k = 0; k < BS; k++) y[i] = fma(-F[i * BS + k], z[k], y[i]);
+        }
+#pragma unroll
+    for (int i = 0; i < BS; i++) part[w][i][lane] = y[i];
+    __syncthreads();
+    if (w != 0 || !live) return;
+#pragma unroll
+    for (int i = 0; i < BS; i++) {
+        double s = part[0][i][lane];
+#pragma unroll
+        for (int v = 1; v < kSlices; v++) s += part[v][i][lane];
+        y[i] = __ldcg(x + ((size_t)J * BS + i) * B + b) + s;
+    }
+    double Di[BS * BS];
+    load_blk<BS>(L, __ldg(S.colptr + J), B, b, Di);
+#pragma unroll
+    for (int i = 0; i < BS; i++) {
+        double s = Di[i * BS] * y[0];
+#pragma unroll
+        for (int k = 1; k < BS; k++) s = fma(Di[i * BS + k], y[k], s);
+        x[((size_t)J * BS + i) * B + b] = s;
+    }
+}
+
+// Backward sweep of one level's columns, split: x_J = z_J + (the slices' sums of -U_JI x_I).
+template <int BS, bool SYM>
+__global__ void __launch_bounds__(32 * kSlices) k_bf_backward_split(const DevSymK S, int B,
+                                                                    const double *L,
+                                                                    const double *U, double *x,
+                                                                    int c0) {
+    __shared__ double part[kSlices][BS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int b = blockIdx.y * 32 + lane;
+    const bool live = b < B;
+    const int J = __ldg(S.lvl_cols + c0 + blockIdx.x);
+    double v[BS];
+#pragma unroll
+    for (int i = 0; i < BS; i++) v[i] = 0.0;
+    const int64_t p0 = __ldg(S.colptr + J), p1 = __ldg(S.colptr + J + 1);
+    if (live)
+        for (int64_t p = p0 + 1 + w; p < p1; p += kSlices) {
+            const int I = __ldg(S.rowidx + p);
+            double M[BS * BS], xi[BS];
+            load_blk<BS>(SYM ? L : U, p, B, b, M);
+#pragma unroll
+            for (int i = 0; i < BS; i++) xi[i] = __ldcg(x + ((size_t)I * BS + i) * B + b);
+#pragma unroll
+            for (int i = 0; i < BS; i++)
+#pragma unroll
+                for (int k = 0; k < BS; k++)
+                    v[i] = fma(-(SYM ? M[k * BS + i] : M[i * BS + k]), xi[k], v[i]);
+        }
+#pragma unroll
+    for (int i = 0; i < BS; i++) part[w][i][lane] = v[i];
+    __syncthreads();
+    if (w != 0 || !live) return;
+#pragma unroll
+    for (int i = 0; i < BS; i++) {
+        double s = part[0][i][lane];
+#pragma unroll
+        for (int u = 1; u < kSlices; u++) s += part[u][i][lane];
+        x[((size_t)J * BS + i) * B + b] = __ldcg(x + ((size_t)J * BS + i) * B + b) + s;
+    }
+}
+
 // Forward sweep of one level's columns: y_J = r_J - sum_K F_JK z_K; z_J = D_J^-1 y_J.
 template <int BS>
 __global__ void __launch_bounds__(kNT) k_bf_forward(const DevSymK S, int B, const double *T,
@@ -245,16 +405,24 @@ __global__ void __launch_bounds__(kNT) k_bf_backward(const DevSymK S, int B, con
 
 }  // namespace
 
+// A level is split when it has fewer than this many targets (factor) or columns (sweeps): a
+// property of the structure, not of the batch.
+constexpr int kSplitBelow = 64;
+
 template <int BS, bool SYM>
 int launch_block_factor(const DevSym &S, int B, double *T, double *TU, double *L, double *U,
                         int *neg, int *bad, double tiny, cudaStream_t st) {
     if (B <= 0) return 0;
-    const unsigned gy = (unsigned)((B + kNT - 1) / kNT);
+    const unsigned gy = (unsigned)((B + kNT - 1) / kNT), gy32 = (unsigned)((B + 31) / 32);
     for (int l = 0; l < S.nlevels; l++) {
         const int t0 = S.lvl_tptr[l], nt = S.lvl_tptr[l + 1] - t0;
         if (nt <= 0) continue;
         const dim3 grid((unsigned)nt, gy);
-        k_bf_update<BS, SYM><<<grid, kNT, 0, st>>>(S.k, B, T, TU, L, U, t0);
+        if (nt < kSplitBelow)
+            k_bf_update_split<BS, SYM><<<dim3((unsigned)nt, gy32), 32 * kSlices, 0, st>>>(
+                S.k, B, T, TU, L, U, t0);
+        else
+            k_bf_update<BS, SYM><<<grid, kNT, 0, st>>>(S.k, B, T, TU, L, U, t0);
         k_bf_scale<BS, SYM><<<grid, kNT, 0, st>>>(S.k, B, T, TU, L, U, neg, bad, tiny, t0);
     }
     return (int)cudaGetLastError();
@@ -264,14 +432,23 @@ template <int BS, bool SYM>
 int launch_block_solve(const DevSym &S, int B, const double *T, const double *L, const double *U,
                        double *x, cudaStream_t st) {
     if (B <= 0) return 0;
-    const unsigned gy = (unsigned)((B + kNT - 1) / kNT);
+    const unsigned gy = (unsigned)((B + kNT - 1) / kNT), gy32 = (unsigned)((B + 31) / 32);
     for (int l = 0; l < S.nlevels; l++) {
         const int c0 = S.lvl_colptr[l], nc = S.lvl_colptr[l + 1] - c0;
-        if (nc > 0) k_bf_forward<BS><<<dim3((unsigned)nc, gy), kNT, 0, st>>>(S.k, B, T, L, x, c0);
+        if (nc <= 0) continue;
+        if (nc < kSplitBelow)
+            k_bf_forward_split<BS><<<dim3((unsigned)nc, gy32), 32 * kSlices, 0, st>>>(S.k, B, T, L,
+                                                                                     x, c0);
+        else
+            k_bf_forward<BS><<<dim3((unsigned)nc, gy), kNT, 0, st>>>(S.k, B, T, L, x, c0);
     }
     for (int l = S.nlevels - 1; l >= 0; l--) {
         const int c0 = S.lvl_colptr[l], nc = S.lvl_colptr[l + 1] - c0;
-        if (nc > 0)
+        if (nc <= 0) continue;
+        if (nc < kSplitBelow)
+            k_bf_backward_split<BS, SYM><<<dim3((unsigned)nc, gy32), 32 * kSlices, 0, st>>>(
+                S.k, B, L, U, x, c0);
+        else
             k_bf_backward<BS, SYM><<<dim3((unsigned)nc, gy), kNT, 0, st>>>(S.k, B, L, U, x, c0);
     }
     return (int)cudaGetLastError();
