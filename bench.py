@@ -35,7 +35,7 @@ B_DEFAULT = 512
 N_INPUT_SETS = 4
 # FP64 work per unit with every output requested, counted from the kernel source on the fast
 # sincos path (an FMA counts 2 flops; doublings run on the integer pipe and count nothing):
-# (flops, instructions).  Per 2000-bus state they sum to 522,500 flops / 353,700 instructions.
+# (flops, instructions).  Per 2000-bus state they sum to 515,655 flops / 340,855 instructions.
 FP64_PER_BRANCH = (168, 109)   # sincos, flows, 16 derivatives, h and its J row, Hessian fold
 FP64_PER_SLOT = (7, 7)         # a branch end's record summed into its bus (all but the first)
 FP64_PER_BUS = (16, 9)         # shunt, balances (Euler, from the derivative sums), diagonal terms
@@ -188,6 +188,22 @@ def oracle_rate(grid, batch, n_evals: int, threads: int):
         runner.close()
 
 
+def bench_config(grid, B: int, world: int, n: int, m: int, nnzJ: int, nnzH: int) -> dict:
+    """The `config` object of both arms' JSON line (the same keys and values for one workload)."""
+    return {"workload": WORKLOAD, "nb": grid.nb, "nl": grid.nl, "ng": grid.ng, "B": B,
+            "n": n, "m": m, "nnzJ": nnzJ, "nnzH": nnzH,
+            "l2": "inputs rotate over 4 device copies (236 MB) and each step writes 343 MB, "
+                  "both larger than L2",
+            "parallelism": f"{world} rank(s), each its own 512 contingencies, no collective"}
+
+
+def oracle_dims(grid, batch):
+    """(n, m, nnzJ, nnzH) as the oracle's evaluation of the first state emits them."""
+    from oracle import acopf
+    r = acopf.evaluate(acopf.OracleNet(grid), batch.x[0], batch.lam[0], batch.mask[0])
+    return grid.n, grid.m, int(r["J"][0][-1]), int(r["H"][0][-1])
+
+
 def run_reference(args, rank: int):
     """--impl reference: the oracle on the host cores; each step is a bounded sample."""
     if rank != 0:
@@ -211,8 +227,8 @@ def run_reference(args, rank: int):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "nb": grid.nb, "nl": grid.nl,
-                                        "ng": grid.ng, "B": args.B},
+        "data": "synthetic (seeded 2000-bus grid and N-1 states; ACTIVSg2000 not available)",
+        "config": bench_config(grid, args.B, args.gpus, *oracle_dims(grid, batch)),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -839,11 +855,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded 2000-bus grid and N-1 states; ACTIVSg2000 not available)",
-        "config": {"workload": WORKLOAD, "nb": grid.nb, "nl": grid.nl, "ng": grid.ng, "B": B,
-                   "n": n, "m": m, "nnzJ": nnzJ, "nnzH": nnzH,
-                   "l2": "inputs rotate over 4 device copies (236 MB) and each step writes 343 MB, "
-                         "both larger than L2",
-                   "parallelism": f"{world} rank(s), each its own 512 contingencies, no collective"},
+        "config": bench_config(grid, B, world, n, m, nnzJ, nnzH),
         "latency_ms": {"p50": statistics.median(step_ms),
                        "p99": sorted(step_ms)[max(0, int(0.99 * len(step_ms)) - 1)]},
         "hbm_gbs": hbm_gbs,

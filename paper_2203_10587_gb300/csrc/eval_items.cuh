@@ -262,7 +262,7 @@ __device__ __forceinline__ void put2(double *rec, int c, double a, double b) {
 
 // One (state b, branch l) item.  scr is state b's record scratch ([nslot][NCOMP]).  The branch
 // writes its two h values and its two Jacobian h rows (four entries each, contiguous across a
-// warp), and the 96-byte record of each end at the end's slot; the bus phase assembles
+// warp), and the 80-byte record of each end at the end's slot; the bus phase assembles
 // everything else row by row.
 template <int WANT>
 __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, int b, int l,
