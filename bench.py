@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ / 1e3
 FP64_PEAK_GINSTR = SMS * FP64_FMA_PER_SM_CLK * SM_MAX_GHZ
 # dram bytes per launch of the dominant kernel from its ncu capture, by kernel name; a kernel
 # changed since its capture has no entry
-TRAFFIC_BYTES = {"persistent": 579_142_400}   # 65.9 MB read + 513.3 MB written (ncu, 2000-bus x 512)
+TRAFFIC_BYTES = {"persistent": 386_942_464}   # 63.8 MB read + 323.2 MB written (ncu, 2000-bus x 512)
 HBM_PEAK_FALLBACK_GBS = 6800.0
 
 

@@ -62,6 +62,19 @@ static __device__ bool bounded_wait(const int *p, int target, long long limit, i
 
 enum : int { ST_TIMEOUT_BUS = 1, ST_TIMEOUT_RING = 2 };
 
+// Invalidates in L2, without write-back, every whole 128-byte line of [p, q): branch-end records
+// of a ring slot that its bus tiles have consumed.  Nothing reads them again; the ring slot's
+// next writer (a branch tile of state b + ring, which waits for this tile's signal) overwrites
+// them, so writing them back to DRAM would be wasted traffic.  PTX treats a discard as a weak
+// write of indeterminate values, so the release of the tile's signal orders it before that next
+// writer.  Lines shared with a neighbouring tile's range are kept.
+// Called by the 32 lanes of one warp, which take every 32nd line.
+__device__ __forceinline__ void discard_lines(const void *p, const void *q, int lane) {
+    uintptr_t a = (((uintptr_t)p + 127) & ~(uintptr_t)127) + 128 * (uintptr_t)lane;
+    const uintptr_t e = (uintptr_t)q & ~(uintptr_t)127;
+    for (; a < e; a += 32 * 128) asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+}
+
 __device__ __forceinline__ void decode_item(const PersistParams &P, int t, bool *is_branch, int *b,
                                             int *tile) {
     const int L = P.lag, Tbr = P.Tbr, Tbu = P.Tbu;
@@ -138,7 +151,16 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
                 if (tile == 0 && R.f) obj_block<(WANT & W_GM) != 0>(N, R, b, s_part);
             }
             __syncthreads();
-            if (threadIdx.x == 0) red_release_add(done_bu + b);
+            if (threadIdx.x < 32) {
+                if (s_ok && (WANT & (W_G | W_J | W_H))) {   // this item's records are consumed
+                    const int i0 = tile * P.group * NT;
+                    const int i1 = min(N.nb, (tile + 1) * P.group * NT);
+                    discard_lines(scr + (size_t)__ldg(N.slot_ptr + i0) * NCOMP,
+                                  scr + (size_t)__ldg(N.slot_ptr + i1) * NCOMP, threadIdx.x);
+                    __syncwarp();   // the lanes' discards before lane 0's release
+                }
+                if (threadIdx.x == 0) red_release_add(done_bu + b);
+            }
         }
     }
 }
