@@ -65,6 +65,9 @@ def parse():
     p.add_argument("--config", default="", help="launch configuration instead of autotuning, "
                    "e.g. schedule=2,block=64,occupancy=16")
     p.add_argument("--serve-seconds", type=float, default=1.5, help="length of each serving phase")
+    p.add_argument("--only", default="", choices=["", "kkt", "pflow"],
+                   help="time only the KKT step or the power-flow step (--steps calls after "
+                        "--warmup) and print its object")
     return p.parse_args()
 
 
@@ -560,7 +563,7 @@ def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):
                         "of records stays in L2"}
 
 
-def run_kkt(exago, synth, torch, np, dev):
+def run_kkt(exago, synth, torch, np, dev, reps=10, warm=2):
     """The interior-point KKT step (exago_kkt_solve) of the 2,000-bus x 512 N-1 batch, with the
     batch's own Jacobian and Lagrangian Hessian (exago_eval_all), dx_i = 1 + sum_j |W_ij|,
     dc ~ U(0.5, 2), rhs ~ N(0, 1): assembly, eliminations, the batched block L D L' and both
@@ -593,7 +596,7 @@ def run_kkt(exago, synth, torch, np, dev):
     info = exago.exago_kkt_info(k)
     ws = torch.empty(exago.exago_kkt_workspace_size(k, B), dtype=torch.uint8, device=dev)
     fn = lambda: exago.exago_kkt_solve(k, out["jval"], out["hval"], dx, dc, rhs, sol, inertia, ws)
-    ms = time_calls(torch, fn, 10, warm=2)
+    ms = time_calls(torch, fn, reps, warm=warm)
     ok = bool((inertia[:, 0] == net.m).all().item() and (inertia[:, 1] == 0).all().item())
     exago.exago_kkt_destroy(k)
     net.close()
@@ -607,7 +610,7 @@ def run_kkt(exago, synth, torch, np, dev):
             "inertia_all_correct": ok}
 
 
-def run_pflow(exago, synth, torch, np, dev):
+def run_pflow(exago, synth, torch, np, dev, reps=20, warm=2):
     """One power-flow Newton step (exago_pf_step: the evaluation of g and J, then the batched
     2 x 2-block LU of J_pf and both sweeps) for 512 states of a 2,000-bus grid (light load, flat
     start), CUDA events over back-to-back calls."""
@@ -627,7 +630,7 @@ def run_pflow(exago, synth, torch, np, dev):
     bt = exago.make_batch(X, workspace=ws)
     Xn = torch.empty_like(X)
     mis = torch.empty(B, dtype=torch.float64, device=dev)
-    ms = time_calls(torch, lambda: exago.exago_pf_step(pf, bt, Xn, mis), 20, warm=2)
+    ms = time_calls(torch, lambda: exago.exago_pf_step(pf, bt, Xn, mis), reps, warm=warm)
     exago.exago_pf_destroy(pf)
     net.close()
     return {"workload": "2000-bus x 512 states: one power-flow Newton step (g, J, factor, solve)",
@@ -913,6 +916,17 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.only:   # one sub-workload alone (profiling): rank 0 of one process
+        import numpy as np
+        import torch
+        from paper_2203_10587_gb300 import build, exago, synth
+        build.build()
+        exago.lib()
+        dev = torch.device("cuda", local_rank)
+        fn = run_kkt if args.only == "kkt" else run_pflow
+        res = fn(exago, synth, torch, np, dev, reps=max(1, args.steps), warm=args.warmup)
+        print(json.dumps({("kkt_step" if args.only == "kkt" else "pflow_step"): res}), flush=True)
         return
     if world > 1:
         import torch

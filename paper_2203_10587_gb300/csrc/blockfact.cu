@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "blockfact.h"
+#include "internal.h"
 
 namespace exago {
 
@@ -452,6 +453,36 @@ int launch_block_solve(const DevSym &S, int B, const double *T, const double *L,
             k_bf_backward<BS, SYM><<<dim3((unsigned)nc, gy), kNT, 0, st>>>(S.k, B, L, U, x, c0);
     }
     return (int)cudaGetLastError();
+}
+
+int upload_block_sym(const BlockSym &S, DevSym &D, std::vector<void *> &allocs) {
+    D = DevSym();
+    D.k.nb = S.nb;
+    D.k.nlevels = D.nlevels = S.nlevels;
+    D.k.nblk = S.nblk;
+    D.k.ntgt = (int64_t)S.tgt_blk.size();
+    D.k.npairs = (int64_t)S.pairs.size();
+    D.lvl_colptr = S.lvl_colptr;
+    D.lvl_tptr = S.lvl_tptr;
+    auto up = [&](const void *src, size_t bytes, const void **dst) -> int {
+        *dst = nullptr;
+        if (bytes == 0) return 0;
+        void *p = nullptr;
+        cudaError_t e = dev_malloc(&p, bytes);
+        if (e != cudaSuccess) return (int)e;
+        allocs.push_back(p);
+        e = cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice);
+        *dst = p;
+        return (int)e;
+    };
+    int e = 0;
+#define UPV(field, vec) \
+    if (!e) e = up(S.vec.data(), S.vec.size() * sizeof(S.vec[0]), (const void **)&D.k.field)
+    UPV(colptr, colptr); UPV(rowidx, rowidx); UPV(rowptr, rowptr); UPV(rowblk, rowblk);
+    UPV(rowcol, rowcol); UPV(lvl_cols, lvl_cols); UPV(tgt_blk, tgt_blk); UPV(tgt_diag, tgt_diag);
+    UPV(tptr, tptr); UPV(pairs, pairs);
+#undef UPV
+    return e;
 }
 
 template int launch_block_factor<4, true>(const DevSym &, int, double *, double *, double *,

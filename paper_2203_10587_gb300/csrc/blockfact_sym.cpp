@@ -4,13 +4,13 @@
 // current degree (lowest index on ties) is eliminated and its neighbours become a clique; the
 // neighbour set at elimination is the block structure of its factor column.  The graphs here are
 // sparse (degree <= 8 before fill), so plain sorted adjacency vectors merged on each elimination
-// are enough.
+// are enough.  Plain host code (no CUDA calls): the host tests build it with the address and
+// undefined-behaviour sanitizers.
 #include <algorithm>
 #include <cstdio>
 #include <set>
 
 #include "blockfact.h"
-#include "internal.h"
 
 namespace exago {
 
@@ -180,36 +180,6 @@ bool build_block_sym(int nb, const int *adj_ptr, const int *adj, BlockSym &S, st
     }
     S.flops_factor_per_block = (double)S.pairs.size();
     return true;
-}
-
-int upload_block_sym(const BlockSym &S, DevSym &D, std::vector<void *> &allocs) {
-    D = DevSym();
-    D.k.nb = S.nb;
-    D.k.nlevels = D.nlevels = S.nlevels;
-    D.k.nblk = S.nblk;
-    D.k.ntgt = (int64_t)S.tgt_blk.size();
-    D.k.npairs = (int64_t)S.pairs.size();
-    D.lvl_colptr = S.lvl_colptr;
-    D.lvl_tptr = S.lvl_tptr;
-    auto up = [&](const void *src, size_t bytes, const void **dst) -> int {
-        *dst = nullptr;
-        if (bytes == 0) return 0;
-        void *p = nullptr;
-        cudaError_t e = dev_malloc(&p, bytes);
-        if (e != cudaSuccess) return (int)e;
-        allocs.push_back(p);
-        e = cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice);
-        *dst = p;
-        return (int)e;
-    };
-    int e = 0;
-#define UPV(field, vec) \
-    if (!e) e = up(S.vec.data(), S.vec.size() * sizeof(S.vec[0]), (const void **)&D.k.field)
-    UPV(colptr, colptr); UPV(rowidx, rowidx); UPV(rowptr, rowptr); UPV(rowblk, rowblk);
-    UPV(rowcol, rowcol); UPV(lvl_cols, lvl_cols); UPV(tgt_blk, tgt_blk); UPV(tgt_diag, tgt_diag);
-    UPV(tptr, tptr); UPV(pairs, pairs);
-#undef UPV
-    return e;
 }
 
 }  // namespace exago
