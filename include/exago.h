@@ -52,7 +52,8 @@ typedef enum {
     EXAGO_ECUDA = 3,     /* a CUDA runtime call failed */
     EXAGO_ETIMEOUT = 4,  /* a bounded device-side wait gave up, or a serve deadline passed */
     EXAGO_EBUSY = 5,     /* serve queue full */
-    EXAGO_ESTATE = 6     /* call not valid in the object's current state */
+    EXAGO_ESTATE = 6,    /* call not valid in the object's current state */
+    EXAGO_EDEVICE = 7    /* a device-side index check failed (library built with EXAGO_DEBUG) */
 } exago_status;
 
 typedef struct exago_net *exago_net_t;
@@ -588,10 +589,21 @@ exago_status exago_pf_step(exago_pf_t pf, const exago_batch *batch, double *x_ne
 void exago_test_fail_allocations(int n);
 
 /*
- * Waits for `stream` and returns the device status word of the net: EXAGO_OK, or EXAGO_ETIMEOUT
- * if a bounded device-side wait gave up since the last check (the word is then cleared).
+ * Waits for `stream` and returns the device status word of the net: EXAGO_OK, EXAGO_EDEVICE if a
+ * device-side index check of the debug build (EXAGO_DEBUG) failed, or EXAGO_ETIMEOUT if a bounded
+ * device-side wait gave up, since the last check (the word is then cleared).
  */
 exago_status exago_net_check(exago_net_t net, void *stream);
+
+/*
+ * Testing only: the bound on branch-end slot indices that the debug build's device-side checks
+ * compare against (normally the net's slot count, 2 nl), lowered to `slots` (clamped to
+ * [0, 2 nl]; a negative value restores it), so that the checks' failure path can be exercised
+ * while every access the kernels still make stays in bounds.  Takes effect in launches made
+ * after the call (not in CUDA graphs the net captured before).  Without EXAGO_DEBUG the checks,
+ * and this bound, are compiled out.  The paper has no counterpart.
+ */
+exago_status exago_test_debug_bounds(exago_net_t net, int slots);
 
 #ifdef __cplusplus
 }

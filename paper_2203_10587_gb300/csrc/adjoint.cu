@@ -102,9 +102,14 @@ __device__ __forceinline__ void adj_bus_item(const DevNet &N, const AdjReq &A, i
     const int nb = N.nb, ng = N.ng;
     const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
+    if (!EXAGO_DCHECK(N, s0 >= 0 && s0 <= s1 && s1 <= N.chk_nslot && g0 >= 0 && g0 <= g1 &&
+                             g1 <= ng))
+        return;
     double s0v = 0.0, s1v = 0.0;
     for (int s = s0; s < s1; s++) {
-        const double2 r = ld2(scr + 2 * (size_t)__ldg(N.slot_ref + s));
+        const int ref = __ldg(N.slot_ref + s);
+        if (!EXAGO_DCHECK(N, ref >= 0 && ref < 2 * N.nl)) continue;
+        const double2 r = ld2(scr + 2 * (size_t)ref);
         s0v += r.x;
         s1v += r.y;
     }

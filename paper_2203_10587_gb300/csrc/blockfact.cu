@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kNT) k_bf_update(const DevSymK S, int B, doubl
     if (!SYM && !diag) load_blk_cg<BS>(TU, p, B, b, accU);
     for (int64_t q = q0; q < q1; q++) {
         const int2 pr = __ldg(S.pairs + q);   // (I, K), (J, K)
+        if (!EXAGO_DCHECK(S, pr.x >= 0 && pr.x < S.nblk && pr.y >= 0 && pr.y < S.nblk)) continue;
         double X[BB], Y[BB];
         load_blk_cg<BS>(T, pr.x, B, b, X);                      // F_IK
         if (SYM) {
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(32 * kSlices) k_bf_update_split(const DevSymK 
     if (live)
         for (int64_t q = q0 + w; q < q1; q += kSlices) {
             const int2 pr = __ldg(S.pairs + q);
+            if (!EXAGO_DCHECK(S, pr.x >= 0 && pr.x < S.nblk && pr.y >= 0 && pr.y < S.nblk)) continue;
             double X[BB], Y[BB];
             load_blk_cg<BS>(T, pr.x, B, b, X);
             if (SYM) {
@@ -271,6 +273,7 @@ __global__ void __launch_bounds__(32 * kSlices) k_bf_forward_split(const DevSymK
     if (live)
         for (int64_t r = r0 + w; r < r1; r += kSlices) {
             const int K = __ldg(S.rowcol + r), p = __ldg(S.rowblk + r);
+            if (!EXAGO_DCHECK(S, K >= 0 && K < S.nb && p >= 0 && p < S.nblk)) continue;
             double F[BS * BS], z[BS];
             load_blk<BS>(T, p, B, b, F);
 #pragma unroll
@@ -320,6 +323,7 @@ __global__ void __launch_bounds__(32 * kSlices) k_bf_backward_split(const DevSym
     if (live)
         for (int64_t p = p0 + 1 + w; p < p1; p += kSlices) {
             const int I = __ldg(S.rowidx + p);
+            if (!EXAGO_DCHECK(S, I >= 0 && I < S.nb)) continue;
             double M[BS * BS], xi[BS];
             load_blk<BS>(SYM ? L : U, p, B, b, M);
 #pragma unroll
@@ -356,6 +360,7 @@ __global__ void __launch_bounds__(kNT) k_bf_forward(const DevSymK S, int B, cons
     const int64_t r0 = __ldg(S.rowptr + J), r1 = __ldg(S.rowptr + J + 1);
     for (int64_t r = r0; r < r1; r++) {
         const int K = __ldg(S.rowcol + r), p = __ldg(S.rowblk + r);
+        if (!EXAGO_DCHECK(S, K >= 0 && K < S.nb && p >= 0 && p < S.nblk)) continue;
         double F[BS * BS], z[BS];
         load_blk<BS>(T, p, B, b, F);
 #pragma unroll
@@ -390,6 +395,7 @@ __global__ void __launch_bounds__(kNT) k_bf_backward(const DevSymK S, int B, con
     const int64_t p0 = __ldg(S.colptr + J), p1 = __ldg(S.colptr + J + 1);
     for (int64_t p = p0 + 1; p < p1; p++) {
         const int I = __ldg(S.rowidx + p);
+        if (!EXAGO_DCHECK(S, I >= 0 && I < S.nb)) continue;
         double M[BS * BS], xi[BS];
         load_blk<BS>(SYM ? L : U, p, B, b, M);
 #pragma unroll

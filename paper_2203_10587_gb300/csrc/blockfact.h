@@ -74,6 +74,7 @@ struct DevSymK {
     const int *tgt_blk, *tgt_diag;
     const int64_t *tptr;
     const int2 *pairs;
+    int *status;             // the owning net's device status word (debug-build index checks)
 };
 
 // The device tables and the host copies of the launch ranges.

@@ -165,6 +165,7 @@ exago_status do_upload(exago_net *net) {
     d = DevNet{};
     d.nb = p.nb; d.nl = p.nl; d.ng = p.ng; d.n = p.n; d.m = p.m;
     d.nslot = p.nslot;
+    d.chk_nslot = p.nslot;
     d.nnzJ = p.nnzJ; d.nnzJg = p.nnzJg; d.nnzH = p.nnzH;
     d.baseMVA = p.baseMVA;
     d.hpg = p.Hrowptr[2 * p.nb];
@@ -703,6 +704,7 @@ const char *exago_status_name(exago_status s) {
         case EXAGO_ETIMEOUT: return "EXAGO_ETIMEOUT";
         case EXAGO_EBUSY: return "EXAGO_EBUSY";
         case EXAGO_ESTATE: return "EXAGO_ESTATE";
+        case EXAGO_EDEVICE: return "EXAGO_EDEVICE";
     }
     return "EXAGO_UNKNOWN";
 }
@@ -1085,9 +1087,21 @@ exago_status exago_net_check(exago_net_t net, void *stream) {
     if (v != 0) {
         *(volatile int *)net->status_host = 0;
         char msg[128];
+        if (v & ST_BOUNDS) {
+            snprintf(msg, sizeof msg, "a device-side index check failed (status %d)", v);
+            return fail(EXAGO_EDEVICE, msg);
+        }
         snprintf(msg, sizeof msg, "a bounded device-side wait gave up (code %d)", v);
         return fail(EXAGO_ETIMEOUT, msg);
     }
+    return EXAGO_OK;
+}
+
+exago_status exago_test_debug_bounds(exago_net_t net, int slots) {
+    if (!net) return fail(EXAGO_EINVAL, "net is NULL");
+    std::lock_guard<std::mutex> lk(net->mu);
+    const int n = net->plan.nslot;
+    net->dev.chk_nslot = slots < 0 ? n : std::min(slots, n);
     return EXAGO_OK;
 }
 

@@ -270,9 +270,13 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     constexpr bool DERIV = WG || WJ || WH;   // the bus balances come from derivative sums
     const int nb = N.nb, nl = N.nl;
-    double *rf = scr + (size_t)__ldg(N.br_slot + l) * NCOMP;
-    double *rt = scr + (size_t)__ldg(N.br_slot + nl + l) * NCOMP;
+    const int sf = __ldg(N.br_slot + l), sto = __ldg(N.br_slot + nl + l);
     const int fb = __ldg(N.f + l), tb = __ldg(N.t + l);
+    if (!EXAGO_DCHECK(N, l >= 0 && l < nl && sf >= 0 && sf < N.chk_nslot && sto >= 0 &&
+                             sto < N.chk_nslot && fb >= 0 && fb < nb && tb >= 0 && tb < nb))
+        return;
+    double *rf = scr + (size_t)sf * NCOMP;
+    double *rt = scr + (size_t)sto * NCOMP;
     double *Jf = WJ ? st_jval(N, R, b) + N.nnzJg + 4 * (size_t)l : nullptr;
     double *Jt = WJ ? Jf + 4 * (size_t)nl : nullptr;
     double *ghb = R.gh ? st_gh(N, R, b) : nullptr;
@@ -423,6 +427,7 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H, GM = WANT & W_GM;
     const int nb = N.nb;
     const int g0 = __ldg(N.gen_ptr + i), g1 = __ldg(N.gen_ptr + i + 1);
+    if (!EXAGO_DCHECK(N, g0 >= 0 && g0 <= g1 && g1 <= N.ng)) return;
     const double *xb = st_x(N, R, b);
     const double Vm = __ldg(xb + nb + i);
     const double Gs = __ldg(N.Gs + i), Bs = __ldg(N.Bs + i);
@@ -505,6 +510,9 @@ __device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int 
     const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
     const int k = __ldg(N.bus_k + i), nlow = __ldg(N.bus_nlow + i);
     double *JP = W.JP, *JQ = W.JQ, *HA = W.HA, *HM = W.HM;
+    if (!EXAGO_DCHECK(N, i >= 0 && i < N.nb && s0 >= 0 && s0 <= s1 && s1 <= N.chk_nslot &&
+                             nlow >= 0 && nlow < k && s1 - s0 >= k - 1))
+        return;
 
     // The first record of the bus initialises the diagonal sums and the first neighbour's entries;
     // every later record adds to the diagonal sums and starts (or, for a parallel branch, adds to)
@@ -594,6 +602,7 @@ template <int WANT>
 __device__ __forceinline__ void slot_item(const DevNet &N, int s, const double *scr, double *dg,
                                           const TileRows &T) {
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
+    if (!EXAGO_DCHECK(N, s >= 0 && s < N.chk_nslot)) return;
     Rec o = load_rec<WANT, false>(scr + (size_t)s * NCOMP);
     if (WG || WJ) { dg[0] = o.pa; dg[1] = o.pu; dg[2] = o.qa; dg[3] = o.qu; }
     if (WH) { dg[4] = o.haa; dg[5] = o.hua; dg[6] = o.huu; }

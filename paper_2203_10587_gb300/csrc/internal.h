@@ -93,7 +93,23 @@ struct DevNet {
     const double *c2, *c1, *c0;
     const double *c2g, *c1g;    // 2 c2 baseMVA^2 and c1 baseMVA (cost derivatives in p.u.)
     int *status;                // device status word (host-mapped)
+    int chk_nslot;              // bound of slot indices for the debug build's checks (nslot)
 };
+
+// Device status word bits.  The bounded waits store their timeout codes (1, 2); the debug build's
+// index checks (EXAGO_DEBUG) OR in ST_BOUNDS and skip the access they guard.
+enum : int { ST_BOUNDS = 16 };
+#if defined(__CUDACC__)
+__device__ __forceinline__ bool debug_fail(int *status) {
+    if (status) atomicOr(status, ST_BOUNDS);
+    return false;
+}
+#endif
+#ifdef EXAGO_DEBUG
+#define EXAGO_DCHECK(N, cond) ((cond) ? true : ::exago::debug_fail((N).status))
+#else
+#define EXAGO_DCHECK(N, cond) true
+#endif
 
 // One state of a gathered batch (serving: states of several requests in one launch): where its
 // inputs and outputs live.  Absent inputs are nullptr (no mask, unit load scale, weight 1).

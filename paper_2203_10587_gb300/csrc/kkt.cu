@@ -392,6 +392,7 @@ exago_status exago_kkt_create(exago_net_t net, exago_kkt_t *out) {
         }
         exago_status s = EXAGO_OK;
         if (upload_block_sym(k->S, k->D, k->allocs) != 0) s = set_last_error(EXAGO_ENOMEM, "KKT symbolic tables");
+        k->D.k.status = dev->status;   // the net's status word (debug-build index checks)
         KktDev &K = k->K;
         K.nb = nb; K.nl = nl; K.ng = ng; K.n = n; K.m = m;
         K.nnzJ = P->nnzJ; K.nnzH = P->nnzH; K.nnzJg = P->nnzJg; K.hpg = P->Hrowptr[2 * nb];

@@ -221,6 +221,7 @@ exago_status exago_pf_create(exago_net_t net, const int *bus_type, exago_pf_t *o
         for (int u = 0; u < nb; u++) active[u] = (row_active(u, 0) ? 1 : 0) | (row_active(u, 1) ? 2 : 0);
         exago_status s = EXAGO_OK;
         if (upload_block_sym(pf->S, pf->D, pf->allocs) != 0) s = set_last_error(EXAGO_ENOMEM, "power-flow symbolic tables");
+        pf->D.k.status = dev->status;   // the net's status word (debug-build index checks)
         PfDev &D = pf->P;
         D.nb = nb; D.n = P->n; D.m = P->m; D.nnzJ = P->nnzJ;
         if (P->nnzJ >= (1ll << 31)) s = set_last_error(EXAGO_EINVAL, "grid too large");

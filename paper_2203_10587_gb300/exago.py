@@ -14,13 +14,14 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIBPATH = os.path.join(HERE, "_build", "libexago_gb300.so")
+# EXAGO_LIBRARY selects another build of the library (the EXAGO_DEBUG build in its tests)
+LIBPATH = os.environ.get("EXAGO_LIBRARY") or os.path.join(HERE, "_build", "libexago_gb300.so")
 
 _lock = threading.Lock()
 _lib = None
 
 STATUS = {0: "EXAGO_OK", 1: "EXAGO_EINVAL", 2: "EXAGO_ENOMEM", 3: "EXAGO_ECUDA",
-          4: "EXAGO_ETIMEOUT", 5: "EXAGO_EBUSY", 6: "EXAGO_ESTATE"}
+          4: "EXAGO_ETIMEOUT", 5: "EXAGO_EBUSY", 6: "EXAGO_ESTATE", 7: "EXAGO_EDEVICE"}
 
 # every symbol include/exago.h declares (checked by tests/test_capi_host.py)
 EXPORTS = [
@@ -42,7 +43,7 @@ EXPORTS = [
     "exago_slack_destroy", "exago_slack_pattern", "exago_eval_slack", "exago_eval_slack_jtv",
     "exago_kkt_create", "exago_kkt_destroy", "exago_kkt_info", "exago_kkt_order",
     "exago_kkt_workspace_size", "exago_pf_create", "exago_pf_destroy", "exago_pf_workspace_size",
-    "exago_pf_step",
+    "exago_pf_step", "exago_test_debug_bounds",
     "exago_kkt_solve",
 ]
 
@@ -169,6 +170,7 @@ def lib():
                 "exago_pf_destroy": ([vp], i32),
                 "exago_pf_workspace_size": ([vp, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
                 "exago_pf_step": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
+                "exago_test_debug_bounds": ([vp, i32], i32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -433,6 +435,10 @@ def exago_serve_submit(s, net_id: int, batch: exago_batch, f=None, grad=None, gh
                                     _out(gh), _out(jval), _out(hval), float(deadline_ms),
                                     ctypes.byref(t)))
     return t.value
+
+
+def exago_test_debug_bounds(h, slots: int):
+    _check(lib().exago_test_debug_bounds(h, int(slots)))
 
 
 def exago_test_fail_allocations(n: int):
