@@ -308,77 +308,22 @@ class ServeClients:
     def run(self, rng, seconds, rate=None):
         """Closed loop (rate None: every client resubmits as soon as its request completes) or
         Poisson arrivals at `rate` requests/s, each taking a free client of a grid drawn from the
-        mix.  Returns throughput and the server's submit-to-completion latency quantiles."""
-        ex, L, ct = self.exago, self.exago.lib(), self.ct
+        mix, driven by the library's native load generator (exago_serve_drive) on a fresh
+        server.  Returns throughput and the server's submit-to-completion latency quantiles."""
+        ex = self.exago
         srv = ex.exago_serve_create(SERVE_BUDGET, SERVE_SLOTS, SERVE_STREAMS)
-        nids = [ex.exago_serve_register(srv, n.h) for n in self.nets]
-        tk = ct.c_uint64()
-        done = ct.c_int()
-        out_t = {}                      # client -> ticket
-        free = [list(ids) for ids in self.by_grid]
-        deferred = 0
-
-        def submit(c):
-            gi, _, _, bt, _, p = self.clients[c]
-            st = L.exago_serve_submit(srv, nids[gi], ct.byref(bt), p[0], p[1], p[2], p[3], p[4],
-                                      ct.c_double(0.0), ct.byref(tk))
-            if st != 0:
-                ex._check(st)
-            out_t[c] = tk.value
-
-        def finish(c):
-            ex._check(L.exago_serve_wait(srv, ct.c_uint64(out_t.pop(c)), ct.c_double(0.0)))
-            free[self.clients[c][0]].append(c)
-
-        def harvest(gi):
-            for c in [c for c in self.by_grid[gi] if c in out_t]:
-                ex._check(L.exago_serve_poll(srv, ct.c_uint64(out_t[c]), ct.byref(done)))
-                if done.value:
-                    finish(c)
-
-        t0 = time.perf_counter()
-        n_sub = 0
         try:
-            if rate is None:
-                order = list(range(len(self.clients)))
-                for c in order:
-                    submit(c)
-                    n_sub += 1
-                k = 0
-                while time.perf_counter() - t0 < seconds:
-                    c = order[k % len(order)]
-                    k += 1
-                    gi = self.clients[c][0]
-                    finish(c)
-                    free[gi].remove(c)
-                    submit(c)
-                    n_sub += 1
-            else:
-                t_next = t0
-                while True:
-                    t_next += float(rng.exponential(1.0 / rate))
-                    if t_next - t0 >= seconds or time.perf_counter() - t0 >= seconds:
-                        break
-                    while time.perf_counter() < t_next:
-                        pass
-                    gi = int(rng.choice(len(self.share), p=self.share))
-                    if not free[gi]:
-                        harvest(gi)
-                    if not free[gi]:
-                        deferred += 1
-                        oldest = min((c for c in self.by_grid[gi] if c in out_t), key=out_t.get)
-                        finish(oldest)
-                    submit(free[gi].pop())
-                    n_sub += 1
-            for c in list(out_t):
-                finish(c)
-            dt = time.perf_counter() - t0
-            p50, p99, n = ex.exago_serve_stats(srv)
+            nids = [ex.exago_serve_register(srv, n.h) for n in self.nets]
+            clients = [(nids[gi], bt, out) for gi, _, _, bt, out, _ in self.clients]
+            group = [gi for gi, *_ in self.clients]
+            r = ex.exago_serve_drive(srv, clients, group, self.share, rate or 0.0, seconds,
+                                     seed=int(rng.integers(1 << 62)))
         finally:
             ex.exago_serve_destroy(srv)
-        res = {"evals_per_s": n / dt, "p50_ms": p50, "p99_ms": p99, "requests": int(n)}
+        res = {"evals_per_s": r["completed"] / r["seconds"], "p50_ms": r["p50_ms"],
+               "p99_ms": r["p99_ms"], "requests": r["completed"]}
         if rate is not None:
-            res.update(offered_per_s=rate, deferred=deferred)
+            res.update(offered_per_s=rate, deferred=r["deferred"])
         return res
 
 
@@ -643,7 +588,7 @@ def run_serve(exago, synth, torch, np, dev, seconds):
     alone = sc.one_at_a_time(rng, 2000)
     sc.run(rng, 0.3)                                   # warm-up
     peak = sc.run(rng, seconds)
-    # the fastest arrival rate this Python client sustains (arrivals due at once, every one
+    # the fastest arrival rate the native client sustains (arrivals due at once, every one
     # submitted as soon as a client of its grid is free): offered loads stay below it
     client = sc.run(rng, min(seconds, 0.5), rate=1e9)
     ref = min(peak["evals_per_s"], client["evals_per_s"])

@@ -510,6 +510,34 @@ exago_status exago_serve_stats(exago_server_t server, double *p50_ms, double *p9
 exago_status exago_serve_destroy(exago_server_t server);
 
 /*
+ * A native load generator for a server (benchmarks and tests; the paper has no counterpart):
+ * drives `server` for `seconds` with n_clients simulated solver instances, each at most one
+ * request outstanding, from the calling thread (no interpreter in the submission loop).
+ *   clients[i]   the net id, request batch and DEVICE outputs of client i (kept valid by the
+ *                caller); group[i] its grid group, 0 .. n_groups - 1;
+ *   weight[g]    the share of arrivals that go to group g (need not sum to 1);
+ *   rate <= 0    closed loop: every client resubmits as soon as its request completes;
+ *   rate > 0     Poisson arrivals at `rate` requests/s (exponential gaps from a 64-bit Mersenne
+ *                twister seeded by `seed`) until `seconds` of arrival time or of wall time have
+ *                passed (a rate above what can be submitted falls behind the clock and still
+ *                ends on time); each takes a free client of a group drawn by weight;
+ *                when the group has none, its finished requests are collected, and failing
+ *                that the oldest outstanding one is waited for (counted as deferred).
+ *   result[5]    requests completed, seconds elapsed, server p50 and p99 latency (ms, over the
+ *                server's whole life: create one server per run) and deferred arrivals.
+ * Returns the first failing serve call's status; every request submitted is waited for.
+ */
+typedef struct {
+    int net_id;
+    const exago_batch *batch;
+    double *f, *grad, *gh, *jval, *hval;
+} exago_serve_client;
+exago_status exago_serve_drive(exago_server_t server, const exago_serve_client *clients,
+                               const int *group, int n_clients, const double *weight,
+                               int n_groups, double rate, double seconds, uint64_t seed,
+                               double *result);
+
+/*
  * Batched interior-point KKT step (the linear solve the paper's solvers, Ipopt and HiOp, perform
  * once per iteration, Sec. II-III; one per contingency or scenario subproblem under EMPAR,
  * Sec. V-A, eqs. (16)-(20), and Sec. VI-A).  For every state b of a batch it solves

@@ -185,12 +185,14 @@ __global__ void __launch_bounds__(kNT) k_bf_scale(const DevSymK S, int B, const 
 }
 
 // ---- split variants: the terms of one target (or one column's sweep) divided among kSlices
-// warps of a block that holds 32 states; slice w takes every kSlices-th term from the w-th, and
+// (kSweepSlices) warps of a block that holds 32 states; slice w takes every kSlices-th term from
+// the w-th, and
 // warp 0 adds the slices' partial sums in slice order.  Used where a level has few targets, so
 // that the long sums of the dense top of the elimination tree are not one thread's latency
 // chain.  The split is fixed by the structure alone (never by the batch size), so every state's
 // result is the same whatever the batch it belongs to.
 constexpr int kSlices = 8;
+constexpr int kSweepSlices = 32;   // the sweeps carry less per term, so they split wider
 
 template <int BS, bool SYM>
 __global__ void __launch_bounds__(32 * kSlices) k_bf_update_split(const DevSymK S, int B, double *T,
@@ -257,11 +259,11 @@ __global__ void __launch_bounds__(32 * kSlices) k_bf_update_split(const DevSymK 
 // Forward sweep of one level's columns, split: y_J = r_J + (the slices' sums of -F_JK z_K);
 // z_J = D_J^-1 y_J.
 template <int BS>
-__global__ void __launch_bounds__(32 * kSlices) k_bf_forward_split(const DevSymK S, int B,
+__global__ void __launch_bounds__(32 * kSweepSlices) k_bf_forward_split(const DevSymK S, int B,
                                                                    const double *T,
                                                                    const double *L, double *x,
                                                                    int c0) {
-    __shared__ double part[kSlices][BS][32];
+    __shared__ double part[kSweepSlices][BS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int b = blockIdx.y * 32 + lane;
     const bool live = b < B;
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(32 * kSlices) k_bf_forward_split(const DevSymK
     for (int i = 0; i < BS; i++) y[i] = 0.0;
     const int64_t r0 = __ldg(S.rowptr + J), r1 = __ldg(S.rowptr + J + 1);
     if (live)
-        for (int64_t r = r0 + w; r < r1; r += kSlices) {
+        for (int64_t r = r0 + w; r < r1; r += kSweepSlices) {
             const int K = __ldg(S.rowcol + r), p = __ldg(S.rowblk + r);
             if (!EXAGO_DCHECK(S, K >= 0 && K < S.nb && p >= 0 && p < S.nblk)) continue;
             double F[BS * BS], z[BS];
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(32 * kSlices) k_bf_forward_split(const DevSymK
     for (int i = 0; i < BS; i++) {
         double s = part[0][i][lane];
 #pragma unroll
-        for (int v = 1; v < kSlices; v++) s += part[v][i][lane];
+        for (int v = 1; v < kSweepSlices; v++) s += part[v][i][lane];
         y[i] = __ldcg(x + ((size_t)J * BS + i) * B + b) + s;
     }
     double Di[BS * BS];
@@ -307,11 +309,11 @@ __global__ void __launch_bounds__(32 * kSlices) k_bf_forward_split(const DevSymK
 
 // Backward sweep of one level's columns, split: x_J = z_J + (the slices' sums of -U_JI x_I).
 template <int BS, bool SYM>
-__global__ void __launch_bounds__(32 * kSlices) k_bf_backward_split(const DevSymK S, int B,
+__global__ void __launch_bounds__(32 * kSweepSlices) k_bf_backward_split(const DevSymK S, int B,
                                                                     const double *L,
                                                                     const double *U, double *x,
                                                                     int c0) {
-    __shared__ double part[kSlices][BS][32];
+    __shared__ double part[kSweepSlices][BS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int b = blockIdx.y * 32 + lane;
     const bool live = b < B;
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(32 * kSlices) k_bf_backward_split(const DevSym
     for (int i = 0; i < BS; i++) v[i] = 0.0;
     const int64_t p0 = __ldg(S.colptr + J), p1 = __ldg(S.colptr + J + 1);
     if (live)
-        for (int64_t p = p0 + 1 + w; p < p1; p += kSlices) {
+        for (int64_t p = p0 + 1 + w; p < p1; p += kSweepSlices) {
             const int I = __ldg(S.rowidx + p);
             if (!EXAGO_DCHECK(S, I >= 0 && I < S.nb)) continue;
             double M[BS * BS], xi[BS];
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(32 * kSlices) k_bf_backward_split(const DevSym
     for (int i = 0; i < BS; i++) {
         double s = part[0][i][lane];
 #pragma unroll
-        for (int u = 1; u < kSlices; u++) s += part[u][i][lane];
+        for (int u = 1; u < kSweepSlices; u++) s += part[u][i][lane];
         x[((size_t)J * BS + i) * B + b] = __ldcg(x + ((size_t)J * BS + i) * B + b) + s;
     }
 }
@@ -444,8 +446,8 @@ int launch_block_solve(const DevSym &S, int B, const double *T, const double *L,
         const int c0 = S.lvl_colptr[l], nc = S.lvl_colptr[l + 1] - c0;
         if (nc <= 0) continue;
         if (nc < kSplitBelow)
-            k_bf_forward_split<BS><<<dim3((unsigned)nc, gy32), 32 * kSlices, 0, st>>>(S.k, B, T, L,
-                                                                                     x, c0);
+            k_bf_forward_split<BS><<<dim3((unsigned)nc, gy32), 32 * kSweepSlices, 0, st>>>(
+                S.k, B, T, L, x, c0);
         else
             k_bf_forward<BS><<<dim3((unsigned)nc, gy), kNT, 0, st>>>(S.k, B, T, L, x, c0);
     }
@@ -453,7 +455,7 @@ int launch_block_solve(const DevSym &S, int B, const double *T, const double *L,
         const int c0 = S.lvl_colptr[l], nc = S.lvl_colptr[l + 1] - c0;
         if (nc <= 0) continue;
         if (nc < kSplitBelow)
-            k_bf_backward_split<BS, SYM><<<dim3((unsigned)nc, gy32), 32 * kSlices, 0, st>>>(
+            k_bf_backward_split<BS, SYM><<<dim3((unsigned)nc, gy32), 32 * kSweepSlices, 0, st>>>(
                 S.k, B, L, U, x, c0);
         else
             k_bf_backward<BS, SYM><<<dim3((unsigned)nc, gy), kNT, 0, st>>>(S.k, B, L, U, x, c0);

@@ -24,6 +24,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <random>
 #include <string>
 #include <thread>
 #include <vector>
@@ -533,3 +534,109 @@ exago_status exago_serve_destroy(exago_server_t S) {
 }
 
 }  // extern "C"
+
+// ---- native load generator (exago_serve_drive) ------------------------------------------------
+// The submission loop of a benchmark's simulated clients, in C++ so that the arrival process and
+// the polling are not limited by an interpreter: closed loop, or Poisson arrivals with spin-timed
+// submission.  Uses only the public serving calls.
+#include <random>
+
+extern "C" exago_status exago_serve_drive(exago_server_t S, const exago_serve_client *clients,
+                                          const int *group, int n_clients, const double *weight,
+                                          int n_groups, double rate, double seconds,
+                                          uint64_t seed, double *result) {
+    if (!S || !clients || !group || !weight || !result || n_clients < 1 || n_groups < 1 ||
+        !(seconds > 0.0))
+        return sfail(EXAGO_EINVAL, "exago_serve_drive: bad argument");
+    std::vector<std::vector<int>> members(n_groups), free_c(n_groups);
+    for (int i = 0; i < n_clients; i++) {
+        if (group[i] < 0 || group[i] >= n_groups || !clients[i].batch)
+            return sfail(EXAGO_EINVAL, "exago_serve_drive: bad client");
+        members[group[i]].push_back(i);
+    }
+    double wsum = 0.0;
+    for (int g = 0; g < n_groups; g++) {
+        if (!(weight[g] >= 0.0)) return sfail(EXAGO_EINVAL, "exago_serve_drive: bad weight");
+        if (members[g].empty() && weight[g] > 0.0)
+            return sfail(EXAGO_EINVAL, "exago_serve_drive: a weighted group has no client");
+        wsum += weight[g];
+    }
+    if (!(wsum > 0.0)) return sfail(EXAGO_EINVAL, "exago_serve_drive: weights sum to 0");
+    std::vector<uint64_t> ticket(n_clients, 0);
+    std::vector<char> busy(n_clients, 0);
+    exago_status first = EXAGO_OK;
+    auto note = [&](exago_status s) {
+        if (s != EXAGO_OK && first == EXAGO_OK) first = s;
+        return s;
+    };
+    auto submit = [&](int c) {
+        const exago_serve_client &k = clients[c];
+        exago_status s = note(exago_serve_submit(S, k.net_id, k.batch, k.f, k.grad, k.gh, k.jval,
+                                                 k.hval, 0.0, &ticket[c]));
+        busy[c] = s == EXAGO_OK;
+        return s;
+    };
+    auto finish = [&](int c) {
+        note(exago_serve_wait(S, ticket[c], 0.0));
+        busy[c] = 0;
+    };
+    double deferred = 0.0;
+    const auto t0 = Clock::now();
+    auto elapsed = [&] { return std::chrono::duration<double>(Clock::now() - t0).count(); };
+    if (rate <= 0.0) {
+        for (int c = 0; c < n_clients && first == EXAGO_OK; c++) submit(c);
+        for (int k = 0; elapsed() < seconds && first == EXAGO_OK; k++) {
+            const int c = k % n_clients;
+            if (busy[c]) finish(c);
+            if (first == EXAGO_OK) submit(c);
+        }
+    } else {
+        std::mt19937_64 rng(seed);
+        std::exponential_distribution<double> gap(rate);
+        std::discrete_distribution<int> pick(weight, weight + n_groups);
+        for (int g = 0; g < n_groups; g++) free_c[g] = members[g];
+        double t_next = 0.0;
+        while (first == EXAGO_OK) {
+            t_next += gap(rng);
+            // the run ends at `seconds` of arrival time or of wall time, whichever comes first
+            // (arrivals offered faster than they can be submitted fall behind the clock)
+            if (t_next >= seconds || elapsed() >= seconds) break;
+            while (elapsed() < t_next) {
+            }
+            const int g = pick(rng);
+            if (free_c[g].empty()) {   // collect this group's finished requests
+                for (int c : members[g]) {
+                    int done = 0;
+                    if (busy[c] && note(exago_serve_poll(S, ticket[c], &done)) == EXAGO_OK && done) {
+                        finish(c);
+                        free_c[g].push_back(c);
+                    }
+                }
+            }
+            if (free_c[g].empty()) {   // wait for the oldest outstanding one
+                deferred += 1.0;
+                int oldest = -1;
+                for (int c : members[g])
+                    if (busy[c] && (oldest < 0 || ticket[c] < ticket[oldest])) oldest = c;
+                if (oldest < 0) break;
+                finish(oldest);
+                free_c[g].push_back(oldest);
+            }
+            const int c = free_c[g].back();
+            free_c[g].pop_back();
+            submit(c);
+        }
+    }
+    for (int c = 0; c < n_clients; c++)
+        if (busy[c]) finish(c);
+    const double dt = elapsed();
+    double p50 = 0.0, p99 = 0.0;
+    uint64_t n = 0;
+    note(exago_serve_stats(S, &p50, &p99, &n));
+    result[0] = (double)n;
+    result[1] = dt;
+    result[2] = p50;
+    result[3] = p99;
+    result[4] = deferred;
+    return first;
+}

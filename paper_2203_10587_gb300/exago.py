@@ -43,7 +43,7 @@ EXPORTS = [
     "exago_slack_destroy", "exago_slack_pattern", "exago_eval_slack", "exago_eval_slack_jtv",
     "exago_kkt_create", "exago_kkt_destroy", "exago_kkt_info", "exago_kkt_order",
     "exago_kkt_workspace_size", "exago_pf_create", "exago_pf_destroy", "exago_pf_workspace_size",
-    "exago_pf_step", "exago_test_debug_bounds",
+    "exago_pf_step", "exago_test_debug_bounds", "exago_serve_drive",
     "exago_kkt_solve",
 ]
 
@@ -171,6 +171,8 @@ def lib():
                 "exago_pf_workspace_size": ([vp, i32, ctypes.POINTER(ctypes.c_size_t)], i32),
                 "exago_pf_step": ([vp, ctypes.POINTER(exago_batch), vp, vp], i32),
                 "exago_test_debug_bounds": ([vp, i32], i32),
+                "exago_serve_drive": ([vp, vp, vp, i32, vp, i32, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_uint64, vp], i32),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -439,6 +441,35 @@ def exago_serve_submit(s, net_id: int, batch: exago_batch, f=None, grad=None, gh
 
 def exago_test_debug_bounds(h, slots: int):
     _check(lib().exago_test_debug_bounds(h, int(slots)))
+
+
+class exago_serve_client(ctypes.Structure):
+    _fields_ = [("net_id", ctypes.c_int), ("batch", ctypes.POINTER(exago_batch)),
+                ("f", ctypes.c_void_p), ("grad", ctypes.c_void_p), ("gh", ctypes.c_void_p),
+                ("jval", ctypes.c_void_p), ("hval", ctypes.c_void_p)]
+
+
+def exago_serve_drive(s, clients, group, weight, rate: float, seconds: float, seed: int = 0) -> dict:
+    """Native load generator (exago_serve_drive).  clients: list of (net_id, exago_batch, outputs
+    dict of CUDA tensors or None); group: list of group ids; weight: per-group arrival share.
+    rate <= 0: closed loop.  Returns completed, seconds, p50_ms, p99_ms, deferred."""
+    n = len(clients)
+    arr = (exago_serve_client * n)()
+    keep = []
+    for i, (nid, bt, out) in enumerate(clients):
+        keep.append(bt)
+        arr[i].net_id = int(nid)
+        arr[i].batch = ctypes.pointer(bt)
+        for k in ("f", "grad", "gh", "jval", "hval"):
+            t = out.get(k)
+            setattr(arr[i], k, None if t is None else t.data_ptr())
+    g = np.ascontiguousarray(group, dtype=np.int32)
+    w = np.ascontiguousarray(weight, dtype=np.float64)
+    res = np.zeros(5)
+    _check(lib().exago_serve_drive(s, arr, _hp(g), n, _hp(w), int(w.shape[0]), float(rate),
+                                   float(seconds), int(seed), _hp(res)))
+    return {"completed": int(res[0]), "seconds": float(res[1]), "p50_ms": float(res[2]),
+            "p99_ms": float(res[3]), "deferred": int(res[4])}
 
 
 def exago_test_fail_allocations(n: int):

@@ -200,3 +200,33 @@ def test_queued_requests_merge_into_one_launch(ex):
                 np.testing.assert_array_equal(got[key], ref[key])
     finally:
         ex.exago_serve_destroy(srv)
+
+
+@pytest.mark.parametrize("rate", [0.0, 20000.0])
+def test_native_load_generator(ex, rate):
+    """exago_serve_drive, closed loop and Poisson arrivals, over clients on two grids: requests
+    complete, the server's quantiles come back, and every client's last result equals its
+    request evaluated alone."""
+    import torch
+    grids = [synth.grid_sized(9, 118), synth.grid_sized(10, 300)]
+    nets = [ex.Net(g) for g in grids]
+    reqs, group = [], []
+    for gi, g in enumerate(grids):
+        for k in range(6):
+            reqs.append(Req(ex, nets[gi], synth.random_batch(700 + 10 * gi + k, g, 1 + k % 2,
+                                                            masks=True, sigma=0.8)))
+            group.append(gi)
+    torch.cuda.synchronize()
+    srv = ex.exago_serve_create(1 << 29, max_slots=4, n_streams=2)
+    try:
+        ids = [ex.exago_serve_register(srv, n.h) for n in nets]
+        clients = [(ids[gi], r.bt, r.out) for gi, r in zip(group, reqs)]
+        res = ex.exago_serve_drive(srv, clients, group, [0.6, 0.4], rate, 0.3, seed=5)
+    finally:
+        ex.exago_serve_destroy(srv)
+    assert res["completed"] > len(reqs) and res["seconds"] > 0.25
+    assert 0.0 < res["p50_ms"] <= res["p99_ms"]
+    for gi, r in zip(group, reqs):
+        got, ref = r.host(), alone(ex, nets[gi], r)
+        for key in ref:
+            np.testing.assert_array_equal(got[key], ref[key])
