@@ -460,11 +460,33 @@ def run_slacks(exago, synth, torch, np, dev, hbm_peak):
     bt = exago.make_batch(x)
     ms = time_calls(torch, lambda: exago.exago_eval_slack(sl, bt, z, gh, net.m, f, gz), 500)
     nbytes = B * (16 * nz + 32 * nb + 16)
+    # the full evaluation with the slacks, on the N-1 states: exago_eval_all then exago_eval_slack,
+    # and the same through exago_eval_all_slack
+    b = synth.contingency_batch(3, g, B)
+    td = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    bte = exago.make_batch(td(b.x, torch.float64), td(b.lam, torch.float64),
+                           td(b.mask, torch.uint8), obj_factor=1.0)
+    exago.exago_net_set_config(net.h, schedule=2, block=64, occupancy=16, stage_records=2,
+                               tile_group=1)
+    out = net.outputs(B, dev)
+    ms_eval = time_calls(torch, lambda: net.eval_all(bte, out), 200, warm=5)
+
+    def two_calls():
+        net.eval_all(bte, out)
+        exago.exago_eval_slack(sl, bte, z, out["gh"], net.m, out["f"], gz)
+
+    ms_two = time_calls(torch, two_calls, 200, warm=5)
+    ms_fused = time_calls(torch, lambda: exago.exago_eval_all_slack(
+        net.h, bte, sl, z, out["f"], out["grad"], out["gh"], out["jval"], out["hval"], gz),
+        200, warm=5)
     sl.close()
     net.close()
     return {"workload": "2000-bus x 512 states, imbalance pairs on every balance plus load loss",
             "slacks_per_state": nz, "us_per_call": ms * 1e3, "algorithmic_bytes": nbytes,
-            "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak}
+            "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak,
+            "with_evaluation": {"eval_ms": ms_eval, "eval_then_slack_ms": ms_two,
+                                "fused_ms": ms_fused,
+                                "fused": "exago_eval_all_slack (the two calls in one)"}}
 
 
 def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):

@@ -309,6 +309,17 @@ exago_status exago_slack_destroy(exago_slack_t slack);
 exago_status exago_slack_pattern(exago_slack_t slack, int64_t *rows, double *vals);
 exago_status exago_eval_slack(exago_slack_t slack, const exago_batch *batch, const double *z,
                               double *gh, int64_t ldgh, double *f, double *grad_z);
+/*
+ * exago_eval_all and exago_eval_slack in one call, for the polar formulation: the evaluation's
+ * outputs with the slacks' balance terms, cost and gradient grad_z [B][nz] (DEVICE) included, bit
+ * for bit what the two calls give (it issues them in order on batch->stream).  Evaluating the
+ * slacks inside the evaluation's launch was measured slower: the slacks' gathers land on the
+ * latency-bound bus phase, while their own kernels run at HBM speed.  Errors as exago_eval_all
+ * and exago_eval_slack; EINVAL for a slack set of another grid.
+ */
+exago_status exago_eval_all_slack(exago_net_t net, const exago_batch *batch, exago_slack_t slack,
+                                  const double *z, double *f, double *grad, double *gh,
+                                  double *jval, double *hval, double *grad_z);
 exago_status exago_eval_slack_jtv(exago_slack_t slack, const exago_batch *batch, const double *v,
                                   int64_t ldv, double *out);
 

@@ -268,6 +268,19 @@ exago_status exago_eval_slack(exago_slack_t s, const exago_batch *bt, const doub
     return EXAGO_OK;
 }
 
+exago_status exago_eval_all_slack(exago_net_t net, const exago_batch *bt, exago_slack_t s,
+                                  const double *z, double *f, double *grad, double *gh,
+                                  double *jval, double *hval, double *grad_z) {
+    exago_status st = check_call(s, bt);
+    if (st != EXAGO_OK || bt->B == 0) return st;
+    int n = 0, meq = 0, mineq = 0;
+    if ((st = exago_net_dims(net, &n, &meq, &mineq, nullptr, nullptr)) != EXAGO_OK) return st;
+    if (meq / 2 != s->nb) return set_last_error(EXAGO_EINVAL, "slack set of another grid");
+    // the evaluation, then the slack kernels on the same stream (bit for bit the two calls)
+    if ((st = exago_eval_all(net, bt, f, grad, gh, jval, hval)) != EXAGO_OK) return st;
+    return exago_eval_slack(s, bt, z, gh, meq + mineq, f, grad_z);
+}
+
 exago_status exago_eval_slack_jtv(exago_slack_t s, const exago_batch *bt, const double *v,
                                   int64_t ldv, double *out) {
     exago_status st = check_call(s, bt);

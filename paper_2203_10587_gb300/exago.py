@@ -41,6 +41,7 @@ EXPORTS = [
     "exago_net_jac_pattern_cart", "exago_eval_cart_workspace_size", "exago_eval_cart",
     "exago_eval_cart_jvp", "exago_eval_cart_jtv", "exago_eval_cart_hvp", "exago_slack_create",
     "exago_slack_destroy", "exago_slack_pattern", "exago_eval_slack", "exago_eval_slack_jtv",
+    "exago_eval_all_slack",
     "exago_kkt_create", "exago_kkt_destroy", "exago_kkt_info", "exago_kkt_order",
     "exago_kkt_workspace_size", "exago_pf_create", "exago_pf_destroy", "exago_pf_workspace_size",
     "exago_pf_step", "exago_test_debug_bounds", "exago_serve_drive",
@@ -152,6 +153,8 @@ def lib():
                                       vp], i32),
                 "exago_eval_slack_jtv": ([vp, ctypes.POINTER(exago_batch), vp, ctypes.c_int64, vp],
                                          i32),
+                "exago_eval_all_slack": ([vp, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp, vp,
+                                          vp, vp], i32),
                 "exago_coupling_create": ([vp, i32, vp, ctypes.POINTER(vp)], i32),
                 "exago_coupling_destroy": ([vp], i32),
                 "exago_coupling_dims": ([vp, ctypes.POINTER(i32), i64p, i64p], i32),
@@ -584,6 +587,16 @@ def exago_eval_slack(slack: Slack, batch: exago_batch, z, gh=None, ldgh: int = 0
     import torch
     _check(lib().exago_eval_slack(slack.h, ctypes.byref(batch), _dp(z, torch.float64), _out(gh),
                                   int(ldgh), _out(f), _out(grad_z)))
+
+
+def exago_eval_all_slack(net_h, batch: exago_batch, slack: Slack, z, f=None, grad=None, gh=None,
+                         jval=None, hval=None, grad_z=None):
+    """exago_eval_all and exago_eval_slack in one call (one launch when the fused variant
+    applies)."""
+    import torch
+    _check(lib().exago_eval_all_slack(net_h, ctypes.byref(batch), slack.h, _dp(z, torch.float64),
+                                      _out(f), _out(grad), _out(gh), _out(jval), _out(hval),
+                                      _out(grad_z)))
 
 
 def exago_eval_slack_jtv(slack: Slack, batch: exago_batch, v, ldv: int, out):

@@ -152,3 +152,75 @@ def test_slacks_more_states_than_one_grid_row(ex, oracle_mod):
         np.testing.assert_array_equal(jt[i], sign * gh0[i, row * g.nb + bus])
     sl.close()
     net.close()
+
+
+@pytest.mark.parametrize("cfg", [
+    dict(),                                                                  # persistent default
+    dict(schedule=2, block=64, occupancy=16, stage_records=2, tile_group=1),  # the bench's
+    dict(schedule=2, block=128, stage_records=1, tile_group=2),
+    dict(schedule=2, block=32, occupancy=8),
+    dict(schedule=1),                                                        # two calls (fallback)
+])
+def test_eval_all_slack_equals_the_two_calls(ex, cfg):
+    """exago_eval_all_slack gives bitwise the results of exago_eval_all then exago_eval_slack, for
+    every output (f, grad, g | h, J, H, grad_z), in every schedule."""
+    import torch
+    g = synth.make_grid(115, 300, 389, 77, shunts=True)
+    b = synth.random_batch(115, g, 11, masks=True, pd_scale=True, obj_weight=True, sigma=0.7)
+    bus, row, sign, cost = slack_set(g, 116)
+    nz = bus.shape[0]
+    z = torch.as_tensor(np.random.default_rng(117).uniform(0.0, 0.2, (b.B, nz)), device="cuda")
+    net = ex.Net(g)
+    if cfg:
+        ex.exago_net_set_config(net.h, **cfg)
+    sl = ex.Slack(net, bus, row, sign, cost)
+    d = to_device(b)
+    bt = ex.make_batch(d["x"], d["lam"], d["mask"], d["pd_scale"], d["obj_weight"], b.sigma)
+    two = net.outputs(b.B)
+    gz2 = torch.empty(b.B, nz, dtype=torch.float64, device="cuda")
+    net.eval_all(bt, two)
+    ex.exago_eval_slack(sl, bt, z, two["gh"], net.m, two["f"], gz2)
+    one = net.outputs(b.B)
+    gz1 = torch.full((b.B, nz), np.nan, dtype=torch.float64, device="cuda")
+    for _ in range(2):   # the second call may replay a cached graph
+        ex.exago_eval_all_slack(net.h, bt, sl, z, one["f"], one["grad"], one["gh"], one["jval"],
+                                one["hval"], gz1)
+    torch.cuda.synchronize()
+    ex.exago_net_check(net.h)
+    for k in two:
+        np.testing.assert_array_equal(one[k].cpu().numpy(), two[k].cpu().numpy(), err_msg=k)
+    np.testing.assert_array_equal(gz1.cpu().numpy(), gz2.cpu().numpy())
+
+
+def test_eval_all_slack_2000_bus_512_against_oracle(ex, oracle_mod):
+    """The one-call evaluation with slacks on the 2,000-bus x 512 batch in the benchmarked
+    configuration, sampled against the oracle's model plus slacks."""
+    import torch
+    g = synth.grid_2000()
+    b = synth.contingency_batch(3, g, 512)
+    b.obj_weight = np.random.default_rng(118).uniform(0.1, 1.0, 512)
+    bus, row, sign, cost = slack_set(g, 119)
+    nz = bus.shape[0]
+    zh = np.random.default_rng(120).uniform(0.0, 0.2, (b.B, nz))
+    net = ex.Net(g)
+    ex.exago_net_set_config(net.h, schedule=2, block=64, occupancy=16, stage_records=2,
+                            tile_group=1)
+    sl = ex.Slack(net, bus, row, sign, cost)
+    d = to_device(b)
+    bt = ex.make_batch(d["x"], d["lam"], d["mask"], None, d["obj_weight"], b.sigma)
+    out = net.outputs(b.B)
+    gz = torch.empty(b.B, nz, dtype=torch.float64, device="cuda")
+    ex.exago_eval_all_slack(net.h, bt, sl, torch.as_tensor(zh, device="cuda"), out["f"],
+                            out["grad"], out["gh"], out["jval"], out["hval"], gz)
+    torch.cuda.synchronize()
+    host = {k: v.cpu().numpy() for k, v in out.items()}
+    for i in (0, 255, 511):
+        ref = oracle_eval(oracle_mod, g, b, i)
+        ghs, fs, gzs = oracle_mod.slack(g.nb, bus, row, sign, cost, zh[i], float(b.obj_weight[i]),
+                                        gh=ref["gh"][:2 * g.nb], f=ref["f"])
+        assert_close(host["gh"][i][:2 * g.nb], ghs, f"gh[{i}]")
+        assert_close(host["gh"][i][2 * g.nb:], ref["gh"][2 * g.nb:], f"h[{i}]")
+        assert_close(host["f"][i], fs, f"f[{i}]")
+        assert_close(gz[i].cpu().numpy(), gzs, f"grad_z[{i}]")
+        assert_close(host["jval"][i], ref["J"][2], f"J[{i}]")
+        assert_close(host["hval"][i], ref["H"][2], f"H[{i}]")
