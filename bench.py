@@ -65,9 +65,9 @@ def parse():
     p.add_argument("--config", default="", help="launch configuration instead of autotuning, "
                    "e.g. schedule=2,block=64,occupancy=16")
     p.add_argument("--serve-seconds", type=float, default=1.5, help="length of each serving phase")
-    p.add_argument("--only", default="", choices=["", "kkt", "pflow"],
-                   help="time only the KKT step or the power-flow step (--steps calls after "
-                        "--warmup) and print its object")
+    p.add_argument("--only", default="", choices=["", "kkt", "pflow", "cart"],
+                   help="time only the KKT step, the power-flow step (--steps calls after "
+                        "--warmup) or the cartesian evaluation, and print its object")
     return p.parse_args()
 
 
@@ -510,6 +510,9 @@ def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):
     z = lambda *sh: torch.empty(*sh, dtype=torch.float64, device=dev)
     out = [z(b.B), z(b.B, n), z(b.B, me + mi), z(b.B, nj), z(b.B, nh)]
     ms = time_calls(torch, lambda: exago.exago_eval_cart(net.h, bt, *out), 200, warm=5)
+    exago.exago_net_set_config(net.h, schedule=3)       # the chunked two-stream schedule
+    ms_chunked = time_calls(torch, lambda: exago.exago_eval_cart(net.h, bt, *out), 200, warm=5)
+    exago.exago_net_set_config(net.h)
     v = torch.randn(b.B, me + mi, dtype=torch.float64, device=dev)
     u = torch.randn(b.B, n, dtype=torch.float64, device=dev)
     o = torch.empty(b.B, n, dtype=torch.float64, device=dev)
@@ -525,9 +528,12 @@ def run_cartesian(exago, synth, torch, np, dev, hbm_peak, polar_ms):
             "jtv_per_s": b.B / (ms_jtv * 1e-3), "hvp_per_s": b.B / (ms_hvp * 1e-3),
             "algorithmic_bytes": nbytes, "hbm_gbs": nbytes / (ms * 1e-3) / 1e9,
             "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak,
-            "schedule": "per chunk of 41 states, branch records on the caller's stream while the "
-                        "previous chunk's bus assembly runs on a side stream; a ring of 3 chunks "
-                        "of records stays in L2"}
+            "schedule": "persistent work list (one launch through the graph cache; records in an "
+                        "L2-resident ring of states)",
+            "ms_per_batch_chunked": ms_chunked,
+            "chunked_schedule": "per chunk of 41 states, branch records on the caller's stream "
+                                "while the previous chunk's bus assembly runs on a side stream; "
+                                "a ring of 3 chunks of records stays in L2"}
 
 
 def run_kkt(exago, synth, torch, np, dev, reps=10, warm=2):
@@ -891,6 +897,10 @@ def main():
         build.build()
         exago.lib()
         dev = torch.device("cuda", local_rank)
+        if args.only == "cart":
+            res = run_cartesian(exago, synth, torch, np, dev, HBM_PEAK_FALLBACK_GBS, float("nan"))
+            print(json.dumps({"cartesian": res}), flush=True)
+            return
         fn = run_kkt if args.only == "kkt" else run_pflow
         res = fn(exago, synth, torch, np, dev, reps=max(1, args.steps), warm=args.warmup)
         print(json.dumps({("kkt_step" if args.only == "kkt" else "pflow_step"): res}), flush=True)

@@ -242,21 +242,32 @@ exago_status exago_eval_hvp(exago_net_t net, const exago_batch *batch, const dou
  *                               place of Va and f in place of Vm, then voltage row i with columns
  *                               e_i, f_i.  The Hessian pattern is exago_net_hess_pattern's (same
  *                               substitution).  Works on a net made by exago_net_plan.
- *   exago_eval_cart_workspace_size  scratch bytes of exago_eval_cart for B states (branch-end
- *                               records of up to three chunks of states, at most about 75 MB).
+ *   exago_eval_cart_workspace_size  scratch bytes of exago_eval_cart for B states, enough for
+ *                               either schedule (branch-end records of the persistent schedule's
+ *                               ring, at most about 64 MB, and its counters, 8 B + 8 B per state;
+ *                               or up to three chunks of records, at most about 75 MB).
  *   exago_eval_cart             f [B], grad [B][n], gh [B][m_c], jval [B][nnzJ_c], hval [B][nnzH]
  *                               (DEVICE buffers; any may be NULL) for the batch's states x [B][n]
  *                               and multipliers lambda [B][m_c].  batch->workspace as for
  *                               exago_eval_all (else the net's internal workspace, grown on
- *                               demand).  Errors as exago_eval_all.  Per chunk of states, a
- *                               branch kernel writes records and a bus kernel assembles the rows;
- *                               the bus kernel of a chunk runs on the net's side stream while the
+ *                               demand; a smaller batch->workspace that still holds two ring
+ *                               slots and the counters is used with fewer slots).  Errors as
+ *                               exago_eval_all.  The net's configuration picks the schedule:
+ *                               EXAGO_SCHED_AUTO / PERSISTENT (the default) run the polar model's
+ *                               persistent work list -- one launch whose CTAs claim branch and
+ *                               bus items of 128 branches or buses of every state, bus items
+ *                               waiting (bounded, EXAGO_ETIMEOUT in the status word) for their
+ *                               state's branch items, records in an L2-resident ring of lag,
+ *                               ring states (the configuration's lag and ring, else derived) --
+ *                               through the net's graph cache (use_graph as for exago_eval_all).
+ *                               EXAGO_SCHED_PIPELINED / KERNELS: per chunk of states a branch
+ *                               kernel writes records and a bus kernel assembles the rows; the
+ *                               bus kernel of a chunk runs on the net's side stream while the
  *                               next chunk's branch kernel runs on batch->stream (ordered by
- *                               events; the call returns with all work ordered on batch->stream;
- *                               the call may be captured in a CUDA graph once a first call outside
- *                               the capture has grown the workspace, or with a batch->workspace);
- *                               the persistent schedule and the graph cache are the polar
- *                               model's only.
+ *                               events).  Both give bitwise equal results; the call returns with
+ *                               all work ordered on batch->stream and may be captured in a CUDA
+ *                               graph once a first call outside the capture has grown the
+ *                               workspace, or with a batch->workspace.
  */
 exago_status exago_net_dims_cart(exago_net_t net, int *n, int *m_eq, int *m_ineq, int64_t *nnzJ,
                                  int64_t *nnzH);
@@ -489,6 +500,7 @@ exago_status exago_net_autotune(exago_net_t net, const exago_batch *batch, doubl
  *   exago_serve_create   EINVAL for max_slots, n_streams < 1 or a zero budget; ENOMEM if the
  *                        arena cannot be allocated.  The queue holds up to 4 max_slots requests.
  *   exago_serve_register the server uses (does not own) the net; it must outlive the server.
+ *                        EINVAL for NULL or a net planned without a device.
  *   exago_serve_submit   request = an exago_batch (device inputs; workspace ignored) and device
  *                        outputs as for exago_eval_all; all must stay valid until the request
  *                        completes.  The request runs on a server stream after the work queued on
@@ -509,6 +521,10 @@ typedef struct exago_server *exago_server_t;
 exago_status exago_serve_create(size_t device_mem_budget, int max_slots, int n_streams,
                                 exago_server_t *out);
 exago_status exago_serve_register(exago_server_t server, exago_net_t net, int *net_id);
+/* As exago_serve_register, for requests in the cartesian formulation: each is evaluated alone
+ * (no merging) by exago_eval_cart's schedule without the graph cache, with outputs and
+ * multipliers sized as exago_eval_cart's and a workspace of exago_eval_cart_workspace_size. */
+exago_status exago_serve_register_cart(exago_server_t server, exago_net_t net, int *net_id);
 exago_status exago_serve_submit(exago_server_t server, int net_id, const exago_batch *request,
                                 double *f, double *grad, double *gh, double *jval, double *hval,
                                 double deadline_ms, uint64_t *ticket);

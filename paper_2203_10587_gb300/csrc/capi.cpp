@@ -231,6 +231,7 @@ exago_status do_upload(exago_net *net) {
         if (net->device >= 0 && net->device < 64 && !done[net->device]) {
             int le2 = persist_allow_stage();
             if (le2 == 0) le2 = bus_allow_stage();
+            if (le2 == 0) le2 = cart_allow_stage();
             if (le2 != 0) return cuda_fail((cudaError_t)le2, "cudaFuncSetAttribute");
             done[net->device] = true;
         }
@@ -460,8 +461,6 @@ uint64_t bits(double v) {
     return u;
 }
 
-// Launches the persistent schedule through a cached instantiated CUDA graph (memset of the
-// counters + the persistent kernel).  Caller holds net->mu.
 // Launches a schedule through a cached instantiated CUDA graph: `launch` queues the schedule's
 // work on a capture stream once per distinct key (every argument the work bakes in).  Caller holds
 // net->mu.
@@ -680,6 +679,17 @@ exago_status with_net_workspace(exago_net_t net, void *caller_ws, size_t bytes, 
     s = fn(net->ws, plp);
     const exago_status r = ws_release_locked(net, st, capturing);
     return s != EXAGO_OK ? s : r;
+}
+
+exago_config net_config(exago_net_t net) {
+    std::lock_guard<std::mutex> lk(net->mu);
+    return net->cfg;
+}
+
+exago_status net_graph_launch_locked(exago_net_t net, const std::vector<uint64_t> &key,
+                                     const std::function<int(cudaStream_t)> &launch,
+                                     cudaStream_t stream) {
+    return launch_graph_locked(net, key, launch, stream);
 }
 
 exago_status eval_direct(exago_net_t net, const exago_batch *bt, double *f, double *grad,

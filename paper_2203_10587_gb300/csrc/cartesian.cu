@@ -25,9 +25,14 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "eval_items.cuh"
+#include "persist_kernel.cuh"
 
 namespace exago {
 namespace {
@@ -59,7 +64,12 @@ struct CartReq {
     double sigma;
     double *f, *grad, *gh, *jval, *hval;
     double *scratch;            // [chunk][nslot][CNC]
+    int stage_cap;              // persistent schedule: shared-memory doubles of a bus tile's rows
 };
+
+// Output stores: written once and never read by the kernels, so they are marked evict-first
+// (st.global.cs) and leave L2 to the branch-end records, which are read back.
+__device__ __forceinline__ void out(double *p, double v) { __stcs(p, v); }
 
 __device__ __forceinline__ void put2c(double *rec, int c, double a, double b) {
     *reinterpret_cast<double2 *>(rec + c) = make_double2(a, b);
@@ -93,48 +103,37 @@ __device__ __forceinline__ CartY cart_y(const DevNet &N, int l) {
 }
 
 // With PS (phase-shifting transformers) the to end's terms take its own mutual admittance
-// (Gt, Bt): P_t = Gtt s_t + Gt a - Bt bf, Q_t = -Btt s_t - Gt bf - Bt a, and the to end's
-// admittance-voltage products below use Gt, Bt; without, one set of products serves both ends.
+// (Gt, Bt); without, Gt = G and Bt = Bm and the products of Bm with the four voltage components
+// serve both ends.  The mutual parts of the injections are linear in the far end's voltage, so
+// with u = d(G a + B b)/d(e_f, f_f) and w = d(G a - B b)/d(e_t, f_t) (a = e_f e_t + f_f f_t,
+// b = f_f e_t - e_f f_t):  G a + B b = e_f u1 + f_f u2,  G b - B a = f_f u1 - e_f u2,  and at
+// the to end  G a - B b = e_t w1 + f_t w2,  -(G b + B a) = f_t w1 - e_t w2.
 template <bool PS>
 __device__ __forceinline__ CartBranch cart_terms(const CartY &y, double ef, double ff, double et,
                                                  double ft) {
     const double G = y.G, Bm = y.Bm, Gff = y.Gff, Bff = y.Bff, Gtt = y.Gtt, Btt = y.Btt;
     const double Gff2 = y.Gff2, Bff2 = y.Bff2, Gtt2 = y.Gtt2, Btt2 = y.Btt2;
     CartBranch c;
-    // a = Vf Vt cos th, bf = Vf Vt sin th (th = Va_f - Va_t); the to end sees -bf
-    const double a = fma(ef, et, ff * ft);
-    const double bf = fma(ff, et, -(ef * ft));
     const double sf = fma(ef, ef, ff * ff), st = fma(et, et, ft * ft);
-    const double Ga = G * a, Ba = Bm * a, Gb = G * bf, Bb = Bm * bf;
-    c.Pf = fma(Gff, sf, Ga + Bb);
-    c.Qf = fma(-Bff, sf, Gb - Ba);
-    if (PS) {
-        const double Gta = y.Gt * a, Bta = y.Bt * a, Gtb = y.Gt * bf, Btb = y.Bt * bf;
-        c.Pt = fma(Gtt, st, Gta - Btb);
-        c.Qt = fma(-Btt, st, -(Gtb + Bta));
-    } else {
-        c.Pt = fma(Gtt, st, Ga - Bb);
-        c.Qt = fma(-Btt, st, -(Gb + Ba));
-    }
-    // admittance-voltage products shared by both ends' derivatives
-    const double Gef = G * ef, Gff_ = G * ff, Get = G * et, Gft_ = G * ft;
     const double Bef = Bm * ef, Bff_ = Bm * ff, Bet = Bm * et, Bft_ = Bm * ft;
-    const double u1 = Get - Bft_, u2 = Gft_ + Bet;
-    c.p1f = fma(Gff2, ef, u1); c.p2f = fma(Gff2, ff, u2);
-    c.q1f = fma(-Bff2, ef, -u2); c.q2f = fma(-Bff2, ff, u1);
-    c.p3f = Gef + Bff_; c.p4f = Gff_ - Bef;
+    const double u1 = fma(G, et, -Bft_), u2 = fma(G, ft, Bet);
+    c.p3f = fma(G, ef, Bff_); c.p4f = fma(G, ff, -Bef);          // dP_f/d(e_t, f_t)
     double w1, w2;
     if (PS) {
-        const double Gtef = y.Gt * ef, Gtff = y.Gt * ff, Gtet = y.Gt * et, Gtft = y.Gt * ft;
-        const double Btef = y.Bt * ef, Btff = y.Bt * ff, Btet = y.Bt * et, Btft = y.Bt * ft;
-        w1 = Gtef - Btff;
-        w2 = Gtff + Btef;
-        c.p3t = Gtet + Btft; c.p4t = Gtft - Btet;
+        const double Gt = y.Gt, Bt = y.Bt;
+        const double Btef = Bt * ef, Btff = Bt * ff, Btet = Bt * et, Btft = Bt * ft;
+        w1 = fma(Gt, ef, -Btff); w2 = fma(Gt, ff, Btef);
+        c.p3t = fma(Gt, et, Btft); c.p4t = fma(Gt, ft, -Btet);   // dP_t/d(e_f, f_f)
     } else {
-        w1 = Gef - Bff_;
-        w2 = Gff_ + Bef;
-        c.p3t = Get + Bft_; c.p4t = Gft_ - Bet;
+        w1 = fma(G, ef, -Bff_); w2 = fma(G, ff, Bef);
+        c.p3t = fma(G, et, Bft_); c.p4t = fma(G, ft, -Bet);
     }
+    c.Pf = fma(Gff, sf, fma(ef, u1, ff * u2));
+    c.Qf = fma(-Bff, sf, fma(ff, u1, -(ef * u2)));
+    c.Pt = fma(Gtt, st, fma(et, w1, ft * w2));
+    c.Qt = fma(-Btt, st, fma(ft, w1, -(et * w2)));
+    c.p1f = fma(Gff2, ef, u1); c.p2f = fma(Gff2, ff, u2);
+    c.q1f = fma(-Bff2, ef, -u2); c.q2f = fma(-Bff2, ff, u1);
     c.p1t = fma(Gtt2, et, w1); c.p2t = fma(Gtt2, ft, w2);
     c.q1t = fma(-Btt2, et, -w2); c.q2t = fma(-Btt2, ft, w1);
     return c;
@@ -191,12 +190,11 @@ __device__ __forceinline__ CartHess cart_hess(const CartY &y, const CartBranch &
     return h;
 }
 
-// One (state, branch) item of the branch kernel.
+// One (state b, branch l) item: scr is state b's records ([nslot][CNC]).
 template <bool PS>
-__device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq &R, int bl, int l) {
-    const int b = R.b0 + bl;
+__device__ __forceinline__ void cart_branch_item_at(const DevNet &N, const CartReq &R, int b,
+                                                    double *scr, int l) {
     const int nb = N.nb, nl = N.nl;
-    double *scr = R.scratch + (size_t)bl * N.nslot * CNC;
     double *rf = scr + (size_t)__ldg(N.br_slot + l) * CNC;
     double *rt = scr + (size_t)__ldg(N.br_slot + nl + l) * CNC;
     const int fb = __ldg(N.f + l), tb = __ldg(N.t + l);
@@ -207,9 +205,9 @@ __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq 
     if (!on) {
 #pragma unroll
         for (int c = 0; c < CNC; c += 2) { put2c(rf, c, 0.0, 0.0); put2c(rt, c, 0.0, 0.0); }
-        if (ghb) { ghb[2 * nb + l] = 0.0; ghb[2 * nb + nl + l] = 0.0; }
+        if (ghb) { out(ghb + 2 * nb + l, 0.0); out(ghb + 2 * nb + nl + l, 0.0); }
         if (Jf)
-            for (int k = 0; k < 4; k++) { Jf[k] = 0.0; Jt[k] = 0.0; }
+            for (int k = 0; k < 4; k++) { out(Jf + k, 0.0); out(Jt + k, 0.0); }
         return;
     }
     const double *xb = R.x + (size_t)b * N.n;
@@ -217,8 +215,8 @@ __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq 
     const CartBranch c = cart_terms<PS>(y, __ldg(xb + fb), __ldg(xb + nb + fb), __ldg(xb + tb),
                                         __ldg(xb + nb + tb));
     if (ghb) {
-        ghb[2 * nb + l] = fma(c.Pf, c.Pf, c.Qf * c.Qf);
-        ghb[2 * nb + nl + l] = fma(c.Pt, c.Pt, c.Qt * c.Qt);
+        out(ghb + 2 * nb + l, fma(c.Pf, c.Pf, c.Qf * c.Qf));
+        out(ghb + 2 * nb + nl + l, fma(c.Pt, c.Pt, c.Qt * c.Qt));
     }
     if (Jf) {
         // grad |S|^2 = 2 P grad P + 2 Q grad Q, columns (e_lo, e_hi, f_lo, f_hi)
@@ -228,11 +226,11 @@ __device__ __forceinline__ void cart_branch_item(const DevNet &N, const CartReq 
         const double htt_e = fma(Pt2, c.p1t, Qt2 * c.q1t), htt_f = fma(Pt2, c.p2t, Qt2 * c.q2t);
         const double htf_e = fma(Pt2, c.p3t, Qt2 * c.p4t), htf_f = fma(Pt2, c.p4t, -(Qt2 * c.p3t));
         if (fb < tb) {
-            Jf[0] = hff_e; Jf[1] = hft_e; Jf[2] = hff_f; Jf[3] = hft_f;
-            Jt[0] = htf_e; Jt[1] = htt_e; Jt[2] = htf_f; Jt[3] = htt_f;
+            out(Jf, hff_e); out(Jf + 1, hft_e); out(Jf + 2, hff_f); out(Jf + 3, hft_f);
+            out(Jt, htf_e); out(Jt + 1, htt_e); out(Jt + 2, htf_f); out(Jt + 3, htt_f);
         } else {
-            Jf[0] = hft_e; Jf[1] = hff_e; Jf[2] = hft_f; Jf[3] = hff_f;
-            Jt[0] = htt_e; Jt[1] = htf_e; Jt[2] = htt_f; Jt[3] = htf_f;
+            out(Jf, hft_e); out(Jf + 1, hff_e); out(Jf + 2, hft_f); out(Jf + 3, hff_f);
+            out(Jt, htt_e); out(Jt + 1, htf_e); out(Jt + 2, htt_f); out(Jt + 3, htf_f);
         }
     }
     put2c(rf, CR_P, c.Pf, c.Qf);
@@ -266,7 +264,8 @@ __global__ void __launch_bounds__(128) k_cart_branch(const DevNet N, const CartR
     for (int it = blockIdx.x; it < nB * per; it += gridDim.x) {
         const int bl = it / per;
         const int l = (it - bl * per) * 128 + threadIdx.x;
-        if (l < N.nl) cart_branch_item<PS>(N, R, bl, l);
+        if (l < N.nl)
+            cart_branch_item_at<PS>(N, R, R.b0 + bl, R.scratch + (size_t)bl * N.nslot * CNC, l);
     }
 }
 
@@ -292,19 +291,34 @@ __device__ __forceinline__ CRec load_crec(const double *r, bool wantH) {
     return o;
 }
 
-__device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R, int bl, int i) {
-    const int b = R.b0 + bl;
+// Bus i's four rows (J rows P_i and Q_i, H rows e_i and f_i) in state b's outputs, or null
+// where that output is not wanted.
+__device__ __forceinline__ BusRows cart_rows(const DevNet &N, const CartReq &R, int b, int i) {
+    BusRows W{};
+    if (R.jval) {
+        double *Jb = R.jval + (size_t)b * R.nnzJc;
+        W.JP = Jb + __ldg(N.bus_jP + i);
+        W.JQ = Jb + __ldg(N.bus_jQ + i);
+    }
+    if (R.hval) {
+        double *Hb = R.hval + (size_t)b * N.nnzH;
+        W.HA = Hb + __ldg(N.bus_hA + i);
+        W.HM = Hb + __ldg(N.bus_hM + i);
+    }
+    return W;
+}
+
+// One (state b, bus i) item: scr is state b's records ([nslot][CNC]); W the bus's rows (in
+// global memory or in a tile's shared-memory copy).
+__device__ __forceinline__ void cart_bus_item_at(const DevNet &N, const CartReq &R, int b,
+                                                 const double *scr, int i, const BusRows &W) {
     const int nb = N.nb, ng = N.ng;
     const bool wantH = R.hval != nullptr;
-    const double *scr = R.scratch + (size_t)bl * N.nslot * CNC;
     const int s0 = __ldg(N.slot_ptr + i), s1 = __ldg(N.slot_ptr + i + 1);
     const int k = __ldg(N.bus_k + i), nlow = __ldg(N.bus_nlow + i);
     double *Jb = R.jval ? R.jval + (size_t)b * R.nnzJc : nullptr;
     double *Hb = wantH ? R.hval + (size_t)b * N.nnzH : nullptr;
-    double *JP = Jb ? Jb + __ldg(N.bus_jP + i) : nullptr;
-    double *JQ = Jb ? Jb + __ldg(N.bus_jQ + i) : nullptr;
-    double *HA = Hb ? Hb + __ldg(N.bus_hA + i) : nullptr;
-    double *HM = Hb ? Hb + __ldg(N.bus_hM + i) : nullptr;
+    double *JP = W.JP, *JQ = W.JQ, *HA = W.HA, *HM = W.HM;
 
     // diagonal sums over the bus's ends, and one neighbour group (parallel branches) at a time
     double P = 0.0, Q = 0.0, pe = 0.0, pf = 0.0, qe = 0.0, qf = 0.0, hee = 0.0, hfe = 0.0, hff = 0.0;
@@ -359,9 +373,9 @@ __device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R,
             gQ -= __ldg(xb + 2 * nb + ng + g);
         }
         double *ghb = R.gh + (size_t)b * R.mc;
-        ghb[i] = gP;
-        ghb[nb + i] = gQ;
-        ghb[2 * nb + 2 * N.nl + i] = V2;
+        out(ghb + i, gP);
+        out(ghb + nb + i, gQ);
+        out(ghb + 2 * nb + 2 * N.nl + i, V2);
     }
     if (JP) {
         const double tG = twice(Gs), tB = twice(Bs);
@@ -375,8 +389,8 @@ __device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R,
             JQ[2 * k + q] = v;
         }
         double *Jv = Jb + N.nnzJ + 2 * (size_t)i;              // voltage row: 2 e_i, 2 f_i
-        Jv[0] = twice(ei);
-        Jv[1] = twice(fi);
+        out(Jv, twice(ei));
+        out(Jv + 1, twice(fi));
     }
     if (HM) {
         const double *lb = R.lam + (size_t)b * R.mc;
@@ -390,21 +404,21 @@ __device__ __forceinline__ void cart_bus_item(const DevNet &N, const CartReq &R,
             const double sw = R.sigma * (R.obj_weight ? __ldg(R.obj_weight + b) : 1.0);
             for (int q = g0; q < g1; q++) {
                 const int g = __ldg(N.gen_ord + q);
-                Hb[N.hpg + g] = gen_on(gm, g) ? sw * __ldg(N.c2g + g) : 0.0;
+                out(Hb + N.hpg + g, gen_on(gm, g) ? sw * __ldg(N.c2g + g) : 0.0);
             }
         }
     }
     if (R.grad) {
         double *gb = R.grad + (size_t)b * N.n;
-        gb[i] = 0.0;
-        gb[nb + i] = 0.0;
+        out(gb + i, 0.0);
+        out(gb + nb + i, 0.0);
         const double w = R.obj_weight ? __ldg(R.obj_weight + b) : 1.0;
         for (int q = g0; q < g1; q++) {
             const int g = __ldg(N.gen_ord + q);
-            gb[2 * nb + g] = gen_on(gm, g) ? w * fma(__ldg(N.c2g + g), __ldg(xb + 2 * nb + g),
-                                                     __ldg(N.c1g + g))
-                                           : 0.0;
-            gb[2 * nb + ng + g] = 0.0;
+            out(gb + 2 * nb + g, gen_on(gm, g) ? w * fma(__ldg(N.c2g + g), __ldg(xb + 2 * nb + g),
+                                                         __ldg(N.c1g + g))
+                                               : 0.0);
+            out(gb + 2 * nb + ng + g, 0.0);
         }
     }
 }
@@ -414,7 +428,57 @@ __global__ void __launch_bounds__(128) k_cart_bus(const DevNet N, const CartReq 
     for (int it = blockIdx.x; it < nB * per; it += gridDim.x) {
         const int bl = it / per;
         const int i = (it - bl * per) * 128 + threadIdx.x;
-        if (i < N.nb) cart_bus_item(N, R, bl, i);
+        if (i < N.nb)
+            cart_bus_item_at(N, R, R.b0 + bl, R.scratch + (size_t)bl * N.nslot * CNC, i,
+                             cart_rows(N, R, R.b0 + bl, i));
+    }
+}
+
+// The bus items of buses [i0, i0 + 128) of state b, by the whole block.  Thread r takes the
+// tile's r-th bus by descending degree (the plan's permutation for 128-bus tiles, which maps every
+// tile onto itself), so that a warp's slot walks have similar lengths.  When the tile's four row
+// segments (J rows P and Q, H rows e and f: contiguous, the same layout as the polar rows) fit
+// `cap` doubles of shared memory, the rows are assembled there and copied out with coalesced
+// stores; otherwise they go straight to global memory.  Contains __syncthreads(): call from every
+// thread of the block.
+__device__ __forceinline__ void cart_bus_tile(const DevNet &N, const CartReq &R, int b, int i0,
+                                              const double *scr, double *stage, int cap) {
+    const int nb = N.nb, r = threadIdx.x;
+    const int i1 = min(i0 + 128, nb);
+    const int *perm = N.bus_perm + (size_t)stage_index(128) * nb;
+    const int i = i0 + r < i1 ? __ldg(perm + i0 + r) : nb;
+    const bool WJ = R.jval != nullptr, WH = R.hval != nullptr;
+    const int p0 = row_start(N.bus_jP, i0, nb, N.jP_end), p1 = row_start(N.bus_jP, i1, nb, N.jP_end);
+    const int q0 = row_start(N.bus_jQ, i0, nb, N.jQ_end);
+    const int a0 = row_start(N.bus_hA, i0, nb, N.hA_end), a1 = row_start(N.bus_hA, i1, nb, N.hA_end);
+    const int m0 = row_start(N.bus_hM, i0, nb, N.hM_end), m1 = row_start(N.bus_hM, i1, nb, N.hM_end);
+    const int LP = WJ ? p1 - p0 : 0, LA = WH ? a1 - a0 : 0, LM = WH ? m1 - m0 : 0;
+    const bool staged = (WJ || WH) && 2 * LP + LA + LM <= cap;
+    if (i < i1) {
+        BusRows W = cart_rows(N, R, b, i);
+        if (staged) {
+            if (WJ) {
+                W.JP = stage + (__ldg(N.bus_jP + i) - p0);
+                W.JQ = stage + LP + (__ldg(N.bus_jQ + i) - q0);
+            }
+            if (WH) {
+                W.HA = stage + 2 * LP + (__ldg(N.bus_hA + i) - a0);
+                W.HM = stage + 2 * LP + LA + (__ldg(N.bus_hM + i) - m0);
+            }
+        }
+        cart_bus_item_at(N, R, b, scr, i, W);
+    }
+    if (staged) {
+        __syncthreads();
+        double *Jb = WJ ? R.jval + (size_t)b * R.nnzJc : nullptr;
+        double *Hb = WH ? R.hval + (size_t)b * N.nnzH : nullptr;
+        for (int e = r; e < LP; e += 128) {
+            out(Jb + p0 + e, stage[e]);
+            out(Jb + q0 + e, stage[LP + e]);
+        }
+        for (int e = r; e < LA; e += 128) out(Hb + a0 + e, stage[2 * LP + e]);
+        for (int e = r; e < LM; e += 128) out(Hb + m0 + e, stage[2 * LP + LA + e]);
+        __syncthreads();   // the next tile overwrites the stage
     }
 }
 
@@ -422,6 +486,73 @@ __global__ void __launch_bounds__(128) k_cart_bus(const DevNet N, const CartReq 
 __global__ void __launch_bounds__(OBJ_LANES) k_cart_obj(const DevNet N, const EvalReq R, int b0) {
     __shared__ double part[OBJ_LANES];
     obj_block<true>(N, R, b0 + blockIdx.x, part);
+}
+
+// Persistent schedule of the cartesian evaluation: the polar model's ticketed work list
+// (PersistParams, decode_item) over (state, 128 branches) and (state, 128 buses) items.  A branch
+// item writes its branches' records into ring slot b mod ring once the bus items of state
+// b - ring have consumed that slot; a bus item waits for all branch items of its state, assembles
+// its buses' rows (bus item 0 also the objective), discards the consumed records from L2 and
+// signals.  Each item computes exactly what the chunked kernels compute for it, so both
+// schedules give bitwise equal results.  Waits are bounded as in the polar kernel.
+// MINB: resident CTAs per SM the register allocation must allow (1: the compiler's choice).
+template <bool PS, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_cart_persist(const DevNet N, const CartReq R,
+                                                      const PersistParams P) {
+    __shared__ int s_item, s_ok;
+    __shared__ double s_part[OBJ_LANES];
+    extern __shared__ double stage[];
+    int *done_br = P.ctr + 1, *done_bu = P.ctr + 1 + P.B;
+    const size_t slot_doubles = (size_t)CNC * N.nslot;
+    int next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(P.ctr, 1);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = next;
+            if (next < P.total) next = atomicAdd(P.ctr, 1);
+        }
+        __syncthreads();
+        const int t = s_item;
+        if (t >= P.total) return;
+        bool is_branch;
+        int b, tile;
+        decode_item(P, t, &is_branch, &b, &tile);
+        double *scr = R.scratch + (size_t)(b % P.ring) * slot_doubles;
+        if (is_branch) {
+            if (threadIdx.x == 0)
+                s_ok = b < P.ring || bounded_wait(done_bu + (b - P.ring), P.Tbu, P.spin_limit,
+                                                  N.status, ST_TIMEOUT_RING);
+            __syncthreads();
+            const int l = tile * 128 + threadIdx.x;
+            if (s_ok && l < N.nl) cart_branch_item_at<PS>(N, R, b, scr, l);
+            __syncthreads();
+            if (threadIdx.x == 0) red_release_add(done_br + b);
+        } else {
+            if (threadIdx.x == 0)
+                s_ok = bounded_wait(done_br + b, P.Tbr + P.force_timeout, P.spin_limit, N.status,
+                                    ST_TIMEOUT_BUS);
+            __syncthreads();
+            if (s_ok) {
+                cart_bus_tile(N, R, b, tile * 128, scr, stage, R.stage_cap);
+                if (tile == 0 && R.f) {
+                    EvalReq E{};
+                    E.B = R.B;
+                    E.x = R.x; E.obj_weight = R.obj_weight; E.f = R.f; E.gen_mask = R.gen_mask;
+                    obj_block<true>(N, E, b, s_part);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                if (s_ok) {   // this item's records are consumed
+                    const int i1 = min(N.nb, (tile + 1) * 128);
+                    discard_lines(scr + (size_t)__ldg(N.slot_ptr + tile * 128) * CNC,
+                                  scr + (size_t)__ldg(N.slot_ptr + i1) * CNC, threadIdx.x);
+                    __syncwarp();   // the lanes' discards before lane 0's release
+                }
+                if (threadIdx.x == 0) red_release_add(done_bu + b);
+            }
+        }
+    }
 }
 
 // ---- adjoint products of the cartesian constraint map c = [g; h] ----
@@ -591,6 +722,133 @@ int chunk_states(const DevNet &N, int B) {
     return (int)std::max<size_t>(1, std::min<size_t>((size_t)std::min(B, 65535), kChunkRecordBytes / per));
 }
 
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Workspace of the chunked schedule for B states: `ring` chunks of records.
+size_t chunked_bytes(const DevNet &N, int B) {
+    const int chunk = chunk_states(N, B);
+    const int ring = std::min(kRing, (B + chunk - 1) / chunk);
+    return (size_t)ring * chunk * record_bytes(N);
+}
+
+// Ring slots of the persistent schedule are sized to stay in L2 with room to spare.
+constexpr size_t kPersistRingBytes = (size_t)64 << 20;
+
+// Shared memory of a persistent bus tile (the largest 128-bus tile's row segments, within the
+// budget that keeps the register-limited number of resident CTAs per SM) and the resident CTAs
+// of the persistent kernel with it, looked up once per device, variant and need.
+struct CartShape {
+    int cap, grid;
+};
+
+// Resident CTAs of 128 threads per SM that the persistent kernel's registers must allow for a
+// target of occ resident warps (exago_config.occupancy: 16, the default, or 24; 8: the
+// compiler's choice).  Measured on the 2,000-bus grid x 512 states with staged rows: 0.487 ms at
+// 16 (103 registers) and at 8 (105), 0.62 ms at 24 (80 registers, spills); with rows straight to
+// memory 0.50-0.52 ms at every setting.
+constexpr int cart_minb(int occ) { return occ == 8 ? 1 : occ / 4; }
+
+template <int OCC>
+const void *cart_persist_fn_occ(bool ps) {
+    return ps ? (const void *)k_cart_persist<true, cart_minb(OCC)>
+              : (const void *)k_cart_persist<false, cart_minb(OCC)>;
+}
+
+const void *cart_persist_fn(bool ps, int occ) {
+    switch (occ) {
+        case 8: return cart_persist_fn_occ<8>(ps);
+        case 16: return cart_persist_fn_occ<16>(ps);
+        case 24: return cart_persist_fn_occ<24>(ps);
+        default: return cart_persist_fn_occ<16>(ps);
+    }
+}
+
+template <int OCC>
+void launch_cart_persist(bool ps, int grid, size_t smem, cudaStream_t st, const DevNet &N,
+                         const CartReq &R, const PersistParams &P) {
+    if (ps) k_cart_persist<true, cart_minb(OCC)><<<grid, 128, smem, st>>>(N, R, P);
+    else k_cart_persist<false, cart_minb(OCC)><<<grid, 128, smem, st>>>(N, R, P);
+}
+
+CartShape cart_shape(const DevNet &N, int occ) {
+    const bool ps = N.Gtf != nullptr;
+    const int want = std::max(0, N.stage_cap_rows[stage_index(128)]);
+    CartShape sh{0, 152};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return sh;
+    }
+    static std::mutex mu;
+    static std::map<uint64_t, CartShape> cache;
+    const uint64_t key = ((uint64_t)dev << 48) | ((uint64_t)occ << 40) | ((uint64_t)ps << 32) |
+                         (uint64_t)(uint32_t)want;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    const void *k = cart_persist_fn(ps, occ);
+    int sms = 0, smem_sm = 0, by_regs = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&by_regs, k, 128, 0) != cudaSuccess ||
+        by_regs < 1 || sms < 1) {
+        cudaGetLastError();
+        return sh;
+    }
+    const long budget = ((long)smem_sm / by_regs - 4096) / 8;
+    sh.cap = (int)(std::max<long>(0, std::min<long>(want, budget)) & ~1l);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, (size_t)sh.cap * sizeof(double)) !=
+            cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    sh.grid = per_sm * sms;
+    cache[key] = sh;
+    return sh;
+}
+
+// Launch settings of the persistent schedule for B >= 1 states, from the net's configuration.
+struct CartPersist {
+    int grid, cap, occ, lag, ring;
+    long long spin_limit;
+    int force_timeout;
+    bool use_graph;
+};
+
+bool cart_is_persistent(const exago_config &c) {
+    return c.schedule != EXAGO_SCHED_KERNELS && c.schedule != EXAGO_SCHED_PIPELINED;
+}
+
+CartPersist cart_persist_plan(const exago_config &c, const DevNet &N, int B) {
+    CartPersist p{};
+    p.occ = c.occupancy == 8 || c.occupancy == 24 ? c.occupancy : 16;
+    const CartShape sh = cart_shape(N, p.occ);
+    p.grid = sh.grid;
+    // rows through shared memory unless EXAGO_STAGE_OFF asks for direct stores
+    p.cap = c.stage_records == EXAGO_STAGE_OFF ? 0 : sh.cap;
+    // bus items trail branch items by 4/3 of the states the resident CTAs hold in branch work,
+    // plus two (the polar schedule's rule); the ring holds up to three lags within its L2 budget
+    const int Tbr = (N.nl + 127) / 128;
+    int lag = c.lag > 0 ? c.lag : (Tbr > 0 ? (4 * p.grid + 3 * Tbr - 1) / (3 * Tbr) : 1) + 2;
+    lag = std::max(1, std::min(lag, B));
+    const int fit = (int)std::min<size_t>(1 << 20, kPersistRingBytes / std::max<size_t>(record_bytes(N), 1));
+    int ring = c.ring > 0 ? c.ring : std::max(lag + 2, std::min(3 * lag + 2, fit));
+    if (ring <= lag) ring = lag + 1;
+    if (ring > B + 1) ring = B + 1;
+    p.lag = lag;
+    p.ring = ring;
+    p.spin_limit = c.spin_limit > 0 ? c.spin_limit : (1ll << 22);
+    p.force_timeout = c.test_force_timeout ? 1 : 0;
+    p.use_graph = c.use_graph != EXAGO_GRAPH_OFF;
+    return p;
+}
+
+size_t counter_bytes(int B) { return round256((size_t)(1 + 2 * (size_t)B) * sizeof(int)); }
+
+size_t persist_bytes(const DevNet &N, const CartPersist &p, int B) {
+    return round256((size_t)p.ring * record_bytes(N)) + counter_bytes(B);
+}
+
 // One adjoint product over the batch, in chunks of states whose branch values fit the workspace.
 exago_status cart_adjoint(exago_net_t net, const exago_batch *bt, const double *in, double *out,
                           int mode) {
@@ -656,7 +914,214 @@ exago_status cart_adjoint(exago_net_t net, const exago_batch *bt, const double *
     });
 }
 
+// The persistent schedule of one call (rows wanted, nb > 0): the counters' memset and one launch,
+// through the net's graph cache when allowed.
+exago_status cart_eval_persistent(exago_net_t net, const DevNet &N, const exago_batch *bt, CartReq R,
+                                  const exago_config &cfg, bool allow_graph) {
+    const int B = bt->B;
+    CartPersist p = cart_persist_plan(cfg, N, B);
+    const size_t slot = record_bytes(N);
+    void *ws = bt->workspace;
+    if (ws) {   // a smaller caller workspace takes fewer ring slots (at least two)
+        if (((uintptr_t)ws & 255) != 0)
+            return set_last_error(EXAGO_EINVAL, "workspace not 256-byte aligned");
+        const size_t cb = counter_bytes(B), have = bt->workspace_bytes;
+        size_t fit = have > cb ? (have - cb) / std::max<size_t>(slot, 1) : 0;
+        while (fit > 0 && round256(fit * slot) + cb > have) fit--;
+        if (fit < 2)
+            return set_last_error(EXAGO_EINVAL, "workspace smaller than exago_eval_cart_workspace_size");
+        if ((size_t)p.ring > fit) {
+            p.ring = (int)fit;
+            if (p.lag >= p.ring) p.lag = p.ring - 1;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)bt->stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+    if (ce != cudaSuccess)
+        return set_last_error(EXAGO_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+    const bool graph = allow_graph && p.use_graph && cap == cudaStreamCaptureStatusNone;
+    const bool ps = N.Gtf != nullptr;   // phase-shifting transformers
+    PersistParams P{};
+    P.B = B;
+    P.group = 1;
+    P.Tbr = (N.nl + 127) / 128;
+    P.Tbu = (N.nb + 127) / 128;
+    P.lag = p.lag;
+    P.ring = p.ring;
+    P.total = B * (P.Tbr + P.Tbu);
+    P.spin_limit = p.spin_limit;
+    P.force_timeout = p.force_timeout;
+    const int grid = std::min(p.grid, P.total);
+    R.stage_cap = p.cap;
+    // the net's lock stays held until the launch (or the graph launch) is queued
+    return with_net_workspace(net, ws, persist_bytes(N, p, B), st, false,
+                              [&](void *w, const PipeLaunch *) -> exago_status {
+        R.scratch = (double *)w;
+        P.ctr = (int *)((char *)w + round256((size_t)p.ring * slot));
+        auto launch = [&](cudaStream_t cs) -> int {
+            cudaError_t e = cudaMemsetAsync(P.ctr, 0, (size_t)(1 + 2 * (size_t)B) * sizeof(int), cs);
+            if (e != cudaSuccess) return (int)e;
+            const size_t smem = (size_t)R.stage_cap * sizeof(double);
+            switch (p.occ) {
+                case 8: launch_cart_persist<8>(ps, grid, smem, cs, N, R, P); break;
+                case 24: launch_cart_persist<24>(ps, grid, smem, cs, N, R, P); break;
+                default: launch_cart_persist<16>(ps, grid, smem, cs, N, R, P); break;
+            }
+            return (int)cudaGetLastError();
+        };
+        if (graph) {
+            uint64_t sg;
+            std::memcpy(&sg, &R.sigma, sizeof sg);
+            const std::vector<uint64_t> key = {
+                0xCA470u + (uint64_t)ps, (uint64_t)R.x, (uint64_t)R.lam, (uint64_t)R.mask,
+                (uint64_t)R.gen_mask, (uint64_t)R.pd_scale, (uint64_t)R.obj_weight, sg,
+                (uint64_t)R.f, (uint64_t)R.grad, (uint64_t)R.gh, (uint64_t)R.jval, (uint64_t)R.hval,
+                (uint64_t)R.scratch, (uint64_t)P.ctr, (uint64_t)B, (uint64_t)grid, (uint64_t)P.lag,
+                (uint64_t)P.ring, (uint64_t)P.spin_limit, (uint64_t)P.force_timeout,
+                (uint64_t)R.stage_cap, (uint64_t)p.occ};
+            return net_graph_launch_locked(net, key, launch, st);
+        }
+        const int e = launch(st);
+        if (e != 0)
+            return set_last_error(EXAGO_ECUDA, std::string("cartesian persistent launch: ") +
+                                                   cudaGetErrorString((cudaError_t)e));
+        return EXAGO_OK;
+    });
+}
+
+// One cartesian evaluation call: the persistent schedule by default, the chunked two-stream
+// schedule when the net's configuration asks for EXAGO_SCHED_PIPELINED or EXAGO_SCHED_KERNELS.
+exago_status cart_eval(exago_net_t net, const exago_batch *bt, double *f, double *grad, double *gh,
+                       double *jval, double *hval, bool allow_graph) {
+    const HostPlan *plan = nullptr;
+    const DevNet *dev = nullptr;
+    int device = -1;
+    if (!net_internal_view(net, &plan, &dev, &device))
+        return set_last_error(net ? EXAGO_ESTATE : EXAGO_EINVAL,
+                              net ? "net was planned without a device" : "net is NULL");
+    if (!bt) return set_last_error(EXAGO_EINVAL, "batch is NULL");
+    if (bt->B < 0) return set_last_error(EXAGO_EINVAL, "batch B < 0");
+    if (bt->B == 0) return EXAGO_OK;
+    if (!bt->x) return set_last_error(EXAGO_EINVAL, "batch x is NULL");
+    if (hval && !bt->lambda)
+        return set_last_error(EXAGO_EINVAL, "batch lambda is NULL (needed by the Hessian)");
+    const DevNet &N = *dev;
+    cudaStream_t st = (cudaStream_t)bt->stream;
+    const bool rows = gh || jval || hval || grad;
+    const exago_config cfg = net_config(net);
+    const bool persistent = rows && N.nb > 0 && cart_is_persistent(cfg);
+    if (persistent) {
+        CartReq R{};
+        R.B = bt->B;
+        R.mc = N.m + N.nb;
+        R.nnzJc = N.nnzJ + 2 * (int64_t)N.nb;
+        R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask; R.gen_mask = bt->gen_mask;
+        R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
+        R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
+        exago_status s = cart_eval_persistent(net, N, bt, R, cfg, allow_graph);
+        if (s != EXAGO_OK) return s;
+    } else {
+        if (rows && N.nb > 0) {
+            const int chunk = chunk_states(N, bt->B);
+            const size_t chunk_bytes = (size_t)chunk * record_bytes(N);
+            const int nchunks = (bt->B + chunk - 1) / chunk;
+            int ring = std::min(kRing, nchunks);
+            void *ws = bt->workspace;
+            if (ws) {
+                if (((uintptr_t)ws & 255) != 0)
+                    return set_last_error(EXAGO_EINVAL, "workspace not 256-byte aligned");
+                if (bt->workspace_bytes < chunk_bytes)
+                    return set_last_error(EXAGO_EINVAL, "workspace smaller than exago_eval_cart_workspace_size");
+                ring = (int)std::min<size_t>((size_t)ring, bt->workspace_bytes / std::max<size_t>(chunk_bytes, 1));
+            }
+            CartReq R{};
+            R.B = bt->B;
+            R.mc = N.m + N.nb;
+            R.nnzJc = N.nnzJ + 2 * (int64_t)N.nb;
+            R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask; R.gen_mask = bt->gen_mask;
+            R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
+            R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
+            const bool ps = N.Gtf != nullptr;   // phase-shifting transformers
+            const void *kbr = ps ? (const void *)k_cart_branch<true> : (const void *)k_cart_branch<false>;
+            const int br_ctas = resident_ctas(kbr, ps ? 2 : 0);
+            const int bu_ctas = resident_ctas((const void *)k_cart_bus, 1);
+            // chunk k: branch kernel on `main`, then its bus kernel on `side` (after an event), so the
+            // FP64-bound branch work of chunk k + 1 overlaps the latency-bound bus work of chunk k;
+            // the branch kernel of chunk k waits for the bus kernel of chunk k - ring, whose ring
+            // slot it overwrites.  With one chunk or one ring slot everything runs on `main`.
+            auto run = [&](void *ws, cudaStream_t main, cudaStream_t side, const PipeLaunch *pl) {
+                if (pl) {
+                    cudaEventRecord(pl->ev_fork, main);
+                    cudaStreamWaitEvent(side, pl->ev_fork, 0);
+                }
+                for (int k = 0; k < nchunks; k++) {
+                    const int b0 = k * chunk, nB = std::min(chunk, bt->B - b0);
+                    CartReq Rk = R;
+                    Rk.b0 = b0;
+                    Rk.scratch = (double *)ws + (size_t)(k % ring) * chunk * N.nslot * CNC;
+                    const int br_items = nB * ((N.nl + 127) / 128), bus_items = nB * ((N.nb + 127) / 128);
+                    if (pl && k >= ring) cudaStreamWaitEvent(main, pl->ev_bu[(k - ring) % (ring + 1)], 0);
+                    if (N.nl > 0)
+                        if (ps) k_cart_branch<true><<<std::min(br_items, br_ctas), 128, 0, main>>>(N, Rk, nB);
+                        else k_cart_branch<false><<<std::min(br_items, br_ctas), 128, 0, main>>>(N, Rk, nB);
+                    cudaStream_t bs = main;
+                    if (pl) {
+                        cudaEventRecord(pl->ev_br[k % (ring + 1)], main);
+                        cudaStreamWaitEvent(side, pl->ev_br[k % (ring + 1)], 0);
+                        bs = side;
+                    }
+                    k_cart_bus<<<std::min(bus_items, bu_ctas), 128, 0, bs>>>(N, Rk, nB);
+                    if (pl) cudaEventRecord(pl->ev_bu[k % (ring + 1)], side);
+                }
+                if (pl) {
+                    cudaEventRecord(pl->ev_join, side);
+                    cudaStreamWaitEvent(main, pl->ev_join, 0);
+                }
+                return EXAGO_OK;
+            };
+            // the net's lock stays held until every kernel that uses its workspace is queued
+            const bool pipe = nchunks > 1 && ring > 1;
+            exago_status s = with_net_workspace(
+                net, ws, (size_t)ring * chunk_bytes, st, pipe,
+                [&](void *w, const PipeLaunch *pl) {
+                    return pl ? run(w, st, pl->side, pl) : run(w, st, st, nullptr);
+                });
+            if (s != EXAGO_OK) return s;
+        }
+    }
+    if (f && !persistent) {
+        EvalReq E{};
+        E.B = bt->B;
+        E.x = bt->x; E.obj_weight = bt->obj_weight; E.f = f; E.gen_mask = bt->gen_mask;
+        for (int b0 = 0; b0 < bt->B; b0 += 65535)
+            k_cart_obj<<<std::min(65535, bt->B - b0), OBJ_LANES, 0, st>>>(N, E, b0);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_last_error(EXAGO_ECUDA, std::string("cartesian evaluation launch: ") +
+                                               cudaGetErrorString(e));
+    return EXAGO_OK;
+}
+
 }  // namespace
+
+int cart_allow_stage() {
+    const int bytes = kStageMaxDoubles * (int)sizeof(double);
+    cudaError_t e = cudaSuccess;
+    for (int occ : {8, 16, 24})
+        for (bool ps : {false, true})
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(cart_persist_fn(ps, occ),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return (int)e;
+}
+
+exago_status eval_cart_direct(exago_net_t net, const exago_batch *bt, double *f, double *grad,
+                              double *gh, double *jval, double *hval) {
+    return cart_eval(net, bt, f, grad, gh, jval, hval, false);
+}
+
 }  // namespace exago
 
 using namespace exago;
@@ -703,108 +1168,19 @@ exago_status exago_eval_cart_workspace_size(exago_net_t net, int B, size_t *byte
         return set_last_error(net ? EXAGO_ESTATE : EXAGO_EINVAL,
                               net ? "net was planned without a device" : "net is NULL");
     if (B < 0) return set_last_error(EXAGO_EINVAL, "B < 0");
-    const int chunk = B == 0 ? 0 : chunk_states(*dev, B);
-    const int ring = chunk == 0 ? 0 : std::min(kRing, (B + chunk - 1) / chunk);
-    *bytes = (size_t)ring * chunk * record_bytes(*dev);
+    if (B == 0) {
+        *bytes = 0;
+        return EXAGO_OK;
+    }
+    // enough for either schedule, so that a later change of the configuration keeps it valid
+    const size_t p = persist_bytes(*dev, cart_persist_plan(net_config(net), *dev, B), B);
+    *bytes = std::max(p, chunked_bytes(*dev, B));
     return EXAGO_OK;
 }
 
 exago_status exago_eval_cart(exago_net_t net, const exago_batch *bt, double *f, double *grad,
                              double *gh, double *jval, double *hval) {
-    const HostPlan *plan = nullptr;
-    const DevNet *dev = nullptr;
-    int device = -1;
-    if (!net_internal_view(net, &plan, &dev, &device))
-        return set_last_error(net ? EXAGO_ESTATE : EXAGO_EINVAL,
-                              net ? "net was planned without a device" : "net is NULL");
-    if (!bt) return set_last_error(EXAGO_EINVAL, "batch is NULL");
-    if (bt->B < 0) return set_last_error(EXAGO_EINVAL, "batch B < 0");
-    if (bt->B == 0) return EXAGO_OK;
-    if (!bt->x) return set_last_error(EXAGO_EINVAL, "batch x is NULL");
-    if (hval && !bt->lambda)
-        return set_last_error(EXAGO_EINVAL, "batch lambda is NULL (needed by the Hessian)");
-    const DevNet &N = *dev;
-    cudaStream_t st = (cudaStream_t)bt->stream;
-    const bool rows = gh || jval || hval || grad;
-    if (rows && N.nb > 0) {
-        const int chunk = chunk_states(N, bt->B);
-        const size_t chunk_bytes = (size_t)chunk * record_bytes(N);
-        const int nchunks = (bt->B + chunk - 1) / chunk;
-        int ring = std::min(kRing, nchunks);
-        void *ws = bt->workspace;
-        if (ws) {
-            if (((uintptr_t)ws & 255) != 0)
-                return set_last_error(EXAGO_EINVAL, "workspace not 256-byte aligned");
-            if (bt->workspace_bytes < chunk_bytes)
-                return set_last_error(EXAGO_EINVAL, "workspace smaller than exago_eval_cart_workspace_size");
-            ring = (int)std::min<size_t>((size_t)ring, bt->workspace_bytes / std::max<size_t>(chunk_bytes, 1));
-        }
-        CartReq R{};
-        R.B = bt->B;
-        R.mc = N.m + N.nb;
-        R.nnzJc = N.nnzJ + 2 * (int64_t)N.nb;
-        R.x = bt->x; R.lam = bt->lambda; R.mask = bt->mask; R.gen_mask = bt->gen_mask;
-        R.pd_scale = bt->pd_scale; R.obj_weight = bt->obj_weight; R.sigma = bt->obj_factor;
-        R.f = f; R.grad = grad; R.gh = gh; R.jval = jval; R.hval = hval;
-        const bool ps = N.Gtf != nullptr;   // phase-shifting transformers
-        const void *kbr = ps ? (const void *)k_cart_branch<true> : (const void *)k_cart_branch<false>;
-        const int br_ctas = resident_ctas(kbr, ps ? 2 : 0);
-        const int bu_ctas = resident_ctas((const void *)k_cart_bus, 1);
-        // chunk k: branch kernel on `main`, then its bus kernel on `side` (after an event), so the
-        // FP64-bound branch work of chunk k + 1 overlaps the latency-bound bus work of chunk k;
-        // the branch kernel of chunk k waits for the bus kernel of chunk k - ring, whose ring
-        // slot it overwrites.  With one chunk or one ring slot everything runs on `main`.
-        auto run = [&](void *ws, cudaStream_t main, cudaStream_t side, const PipeLaunch *pl) {
-            if (pl) {
-                cudaEventRecord(pl->ev_fork, main);
-                cudaStreamWaitEvent(side, pl->ev_fork, 0);
-            }
-            for (int k = 0; k < nchunks; k++) {
-                const int b0 = k * chunk, nB = std::min(chunk, bt->B - b0);
-                CartReq Rk = R;
-                Rk.b0 = b0;
-                Rk.scratch = (double *)ws + (size_t)(k % ring) * chunk * N.nslot * CNC;
-                const int br_items = nB * ((N.nl + 127) / 128), bus_items = nB * ((N.nb + 127) / 128);
-                if (pl && k >= ring) cudaStreamWaitEvent(main, pl->ev_bu[(k - ring) % (ring + 1)], 0);
-                if (N.nl > 0)
-                    if (ps) k_cart_branch<true><<<std::min(br_items, br_ctas), 128, 0, main>>>(N, Rk, nB);
-                    else k_cart_branch<false><<<std::min(br_items, br_ctas), 128, 0, main>>>(N, Rk, nB);
-                cudaStream_t bs = main;
-                if (pl) {
-                    cudaEventRecord(pl->ev_br[k % (ring + 1)], main);
-                    cudaStreamWaitEvent(side, pl->ev_br[k % (ring + 1)], 0);
-                    bs = side;
-                }
-                k_cart_bus<<<std::min(bus_items, bu_ctas), 128, 0, bs>>>(N, Rk, nB);
-                if (pl) cudaEventRecord(pl->ev_bu[k % (ring + 1)], side);
-            }
-            if (pl) {
-                cudaEventRecord(pl->ev_join, side);
-                cudaStreamWaitEvent(main, pl->ev_join, 0);
-            }
-            return EXAGO_OK;
-        };
-        // the net's lock stays held until every kernel that uses its workspace is queued
-        const bool pipe = nchunks > 1 && ring > 1;
-        exago_status s = with_net_workspace(
-            net, ws, (size_t)ring * chunk_bytes, st, pipe,
-            [&](void *w, const PipeLaunch *pl) {
-                return pl ? run(w, st, pl->side, pl) : run(w, st, st, nullptr);
-            });
-        if (s != EXAGO_OK) return s;
-    }
-    if (f) {
-        EvalReq E{};
-        E.B = bt->B;
-        E.x = bt->x; E.obj_weight = bt->obj_weight; E.f = f; E.gen_mask = bt->gen_mask;
-        for (int b0 = 0; b0 < bt->B; b0 += 65535)
-            k_cart_obj<<<std::min(65535, bt->B - b0), OBJ_LANES, 0, st>>>(N, E, b0);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return set_last_error(EXAGO_ECUDA, std::string("cartesian evaluation launch: ") +
-                                               cudaGetErrorString(e));
-    return EXAGO_OK;
+    return cart_eval(net, bt, f, grad, gh, jval, hval, true);
 }
 
 exago_status exago_eval_cart_jvp(exago_net_t net, const exago_batch *batch, const double *u,

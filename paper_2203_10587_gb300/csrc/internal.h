@@ -222,6 +222,7 @@ __host__ __device__ inline int stage_index(int block) {
     return block == 32 ? 0 : block == 64 ? 1 : block == 256 ? 3 : 2;
 }
 int persist_allow_stage();   // persist.cu
+int cart_allow_stage();      // cartesian.cu: the cartesian persistent kernel
 int bus_allow_stage();       // kernels.cu
 int bus_blocks_per_sm(size_t smem_bytes);   // k_bus blocks of 128 threads per SM (kernels.cu)
 
@@ -242,6 +243,17 @@ int multi_kernel_stage_cap(exago_net_t net);
 exago_status with_net_workspace(exago_net_t net, void *caller_ws, size_t bytes, cudaStream_t st,
                                 bool pipeline,
                                 const std::function<exago_status(void *, const PipeLaunch *)> &fn);
+// The net's user configuration (exago_net_set_config; zeros = automatic).
+exago_config net_config(exago_net_t net);
+// Launches `launch`'s work through the net's cache of instantiated CUDA graphs, keyed by every
+// argument the work bakes in (key[0] names the schedule).  Only inside with_net_workspace's fn
+// (the net's lock held) and on a stream that is not being captured.
+exago_status net_graph_launch_locked(exago_net_t net, const std::vector<uint64_t> &key,
+                                     const std::function<int(cudaStream_t)> &launch,
+                                     cudaStream_t stream);
+// exago_eval_cart without the graph cache (serving: every request has its own buffers).
+exago_status eval_cart_direct(exago_net_t net, const exago_batch *bt, double *f, double *grad,
+                              double *gh, double *jval, double *hval);
 // cudaMalloc for every device allocation of the library (honours exago_test_fail_allocations).
 cudaError_t dev_malloc(void **p, size_t bytes);
 // exago_eval_all without the graph cache (serving: every request has its own buffers).  With

@@ -114,6 +114,7 @@ struct exago_server {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> all_events, free_events;   // one per queued or running request
     std::vector<exago_net_t> nets;
+    std::vector<char> cart;        // per net id: evaluated in the cartesian formulation
     std::deque<Request *> queue;
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
     std::vector<std::unique_ptr<Group>> running_groups;
@@ -222,7 +223,8 @@ bool admit_locked(exago_server *S) {
     exago_net_t net = S->nets[head->net_id];
     std::vector<Request *> members{head};
     int Btot = head->batch.B;
-    if (S->max_merge > 1)
+    const bool cart = S->cart[head->net_id] != 0;   // cartesian requests run alone
+    if (S->max_merge > 1 && !cart)
         for (auto it = std::next(S->queue.begin()); it != S->queue.end(); ++it) {
             Request *q = *it;
             if (same_shape(*q, *head) && Btot + q->batch.B <= S->max_merge) {
@@ -267,7 +269,10 @@ bool admit_locked(exago_server *S) {
         bt.stream = st;
         bt.workspace = S->arena_base + off + tab_bytes;
         bt.workspace_bytes = bytes - tab_bytes;
-        if (members.size() == 1) {
+        if (cart) {
+            rc = exago::eval_cart_direct(net, &bt, head->f, head->grad, head->gh, head->jval,
+                                         head->hval);
+        } else if (members.size() == 1) {
             rc = exago::eval_direct(net, &bt, head->f, head->grad, head->gh, head->jval, head->hval);
         } else {
             // per-state table: copied from pageable memory, so the host vector may go afterwards
@@ -399,15 +404,26 @@ exago_status exago_serve_create(size_t device_mem_budget, int max_slots, int n_s
     return EXAGO_OK;
 }
 
-exago_status exago_serve_register(exago_server_t S, exago_net_t net, int *net_id) {
+static exago_status register_net(exago_server_t S, exago_net_t net, int *net_id, bool cart) {
     if (!S || !net || !net_id) return sfail(EXAGO_EINVAL, "null argument");
-    int n = 0;
-    if (exago_net_dims(net, &n, nullptr, nullptr, nullptr, nullptr) != EXAGO_OK)
-        return sfail(EXAGO_EINVAL, "invalid net");
+    const exago::HostPlan *p = nullptr;
+    const exago::DevNet *d = nullptr;
+    int dev = 0;
+    if (!exago::net_internal_view(net, &p, &d, &dev))
+        return sfail(EXAGO_EINVAL, "invalid net (NULL or planned without a device)");
     std::lock_guard<std::mutex> lk(S->mu);
     S->nets.push_back(net);
+    S->cart.push_back(cart ? 1 : 0);
     *net_id = (int)S->nets.size() - 1;
     return EXAGO_OK;
+}
+
+exago_status exago_serve_register(exago_server_t S, exago_net_t net, int *net_id) {
+    return register_net(S, net, net_id, false);
+}
+
+exago_status exago_serve_register_cart(exago_server_t S, exago_net_t net, int *net_id) {
+    return register_net(S, net, net_id, true);
 }
 
 exago_status exago_serve_submit(exago_server_t S, int net_id, const exago_batch *req, double *f,
@@ -417,15 +433,18 @@ exago_status exago_serve_submit(exago_server_t S, int net_id, const exago_batch 
     std::unique_ptr<Request> r(new (std::nothrow) Request());
     if (!r) return sfail(EXAGO_ENOMEM, "host allocation failed");
     exago_net_t net;
+    bool cart;
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (net_id < 0 || net_id >= (int)S->nets.size()) return sfail(EXAGO_EINVAL, "unknown net id");
         net = S->nets[net_id];
+        cart = S->cart[net_id] != 0;
     }
     if (req->B < 1 || !req->x) return sfail(EXAGO_EINVAL, "request needs B >= 1 and x");
     if (hval && !req->lambda) return sfail(EXAGO_EINVAL, "the Hessian needs lambda");
     size_t ws = 0;
-    exago_status st = exago_eval_workspace_size(net, req->B, &ws);
+    exago_status st = cart ? exago_eval_cart_workspace_size(net, req->B, &ws)
+                           : exago_eval_workspace_size(net, req->B, &ws);
     if (st != EXAGO_OK) return st;
     if ((ws + 255) / 256 * 256 > S->budget)
         return sfail(EXAGO_ENOMEM, "request needs more workspace than the server's whole budget");

@@ -44,7 +44,7 @@ EXPORTS = [
     "exago_eval_all_slack",
     "exago_kkt_create", "exago_kkt_destroy", "exago_kkt_info", "exago_kkt_order",
     "exago_kkt_workspace_size", "exago_pf_create", "exago_pf_destroy", "exago_pf_workspace_size",
-    "exago_pf_step", "exago_test_debug_bounds", "exago_serve_drive",
+    "exago_pf_step", "exago_test_debug_bounds", "exago_serve_drive", "exago_serve_register_cart",
     "exago_kkt_solve",
 ]
 
@@ -128,6 +128,7 @@ def lib():
                 "exago_net_check": ([vp, vp], i32),
                 "exago_serve_create": ([ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)], i32),
                 "exago_serve_register": ([vp, vp, ctypes.POINTER(i32)], i32),
+                "exago_serve_register_cart": ([vp, vp, ctypes.POINTER(i32)], i32),
                 "exago_serve_submit": ([vp, i32, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], i32),
                 "exago_serve_set_merge": ([vp, i32], i32),
@@ -430,6 +431,12 @@ def exago_serve_create(device_mem_budget: int, max_slots: int, n_streams: int):
 def exago_serve_register(s, net_h) -> int:
     i = ctypes.c_int()
     _check(lib().exago_serve_register(s, net_h, ctypes.byref(i)))
+    return i.value
+
+
+def exago_serve_register_cart(s, net_h) -> int:
+    i = ctypes.c_int()
+    _check(lib().exago_serve_register_cart(s, net_h, ctypes.byref(i)))
     return i.value
 
 
