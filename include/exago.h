@@ -409,8 +409,14 @@ exago_status exago_eval_all_static(exago_net_t net, const exago_batch *batch, do
  * times on batch->stream with a CUDA event recorded on that stream before every kernel launch and
  * after the last one, waits for each repetition, and returns the mean duration in milliseconds of
  * each kernel of one evaluation: names[k] (static strings: "branch", "bus", "grad", "obj" for
- * the multi-kernel schedule, "persistent" for the fused one) and ms[k] for k < *nkernels.  names and ms need room for 16 entries.  Outputs are those
- * of exago_eval_all.  EINVAL for reps < 1 or null names/ms/nkernels.
+ * the multi-kernel schedule, "persistent" for the fused one) and ms[k] for k < *nkernels.
+ * After "persistent" come the fused kernel's phases, timed on the device's global timer by the
+ * CTAs themselves (names starting "phase: "): kernel span, CTA entry to the first branch item,
+ * the branch items, the last branch end to the first bus start (the wait of a single state),
+ * the bus items, the objective, and the last bus end to the last CTA exit.  With several states
+ * the phases overlap (a span can then exceed the sum, or be negative).  names and ms need room
+ * for 16 entries.  Outputs are those of exago_eval_all.  EINVAL for reps < 1 or null
+ * names/ms/nkernels.
  */
 exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, double *f, double *grad,
                                 double *gh, double *jval, double *hval, int reps, int *nkernels,

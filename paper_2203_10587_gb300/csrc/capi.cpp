@@ -355,13 +355,20 @@ Resolved resolve(exago_net *net, int B) {
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
+// Branch-end records of one state.
 size_t slot_bytes(const exago_net *net) {
     return (size_t)NCOMP * (size_t)net->dev.nslot * sizeof(double);
 }
 
+// One ring slot of the persistent schedule: a state's records, then its objective partials.
+size_t persist_slot_bytes(const exago_net *net) {
+    return slot_bytes(net) + (size_t)kObjLanes * sizeof(double);
+}
+
 // Workspace of the persistent schedule: ring scratch, then counters.
 size_t persist_bytes(const exago_net *net, const Resolved &r, int B) {
-    return round256(r.ring * slot_bytes(net)) + round256((size_t)(1 + 2 * (size_t)B) * sizeof(int));
+    return round256(r.ring * persist_slot_bytes(net)) +
+           round256((size_t)(1 + 2 * (size_t)B) * sizeof(int));
 }
 
 size_t need_bytes(exago_net *net, int B) {
@@ -616,7 +623,7 @@ exago_status eval_locked(exago_net *net, const exago_batch *bt, double *f, doubl
     }
     char *w = (char *)ws;
     R.scratch = (double *)w;
-    w += round256(rs.ring * slot_bytes(net));
+    w += round256(rs.ring * persist_slot_bytes(net));
     PersistLaunch pl;
     pl.block = rs.block; pl.occ_warps = rs.occ_warps; pl.grid = rs.grid; pl.lag = rs.lag;
     pl.ring = rs.ring;
@@ -877,6 +884,29 @@ exago_status exago_eval_all(exago_net_t net, const exago_batch *bt, double *f, d
     return eval(net, bt, f, grad, gh, jval, hval);
 }
 
+// Phase spans reported by exago_eval_profile for the persistent kernel, from the global-timer
+// events of persist_kernel.cuh (PhaseSlot; the slot numbers are repeated here because that header
+// is device code): from the earliest or latest time of event `from` to the earliest or latest
+// time of event `to`.
+constexpr int PHASE_N = 8;
+struct PhaseSpan {
+    const char *name;
+    int from;
+    bool from_latest;
+    int to;
+    bool to_latest;
+};
+constexpr PhaseSpan kPhaseSpan[] = {
+    {"phase: first CTA entry to last CTA exit", 0, false, 7, true},
+    {"phase: first CTA entry to first branch item start", 0, false, 1, false},
+    {"phase: first to last branch item (start to end)", 1, false, 2, true},
+    {"phase: last branch item end to first bus item start", 2, true, 3, false},
+    {"phase: first to last bus item (start to end)", 3, false, 4, true},
+    {"phase: objective (first start to last end)", 5, false, 6, true},
+    {"phase: last bus item end to last CTA exit", 4, true, 7, true},
+};
+constexpr int kPhaseSpans = (int)(sizeof(kPhaseSpan) / sizeof(kPhaseSpan[0]));
+
 exago_status exago_eval_profile(exago_net_t net, const exago_batch *bt, double *f, double *grad,
                                 double *gh, double *jval, double *hval, int reps, int *nkernels,
                                 const char **names, double *ms) {
@@ -893,13 +923,27 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *bt, double *
             return cuda_fail(e, "cudaEventCreate");
         }
     }
-    double acc[ProfileHook::MAX] = {0};
+    // the persistent kernel's phase timestamps: earliest (first 8) and latest (last 8) ns
+    cudaError_t ea = dev_malloc((void **)&hk.phase, 2 * PHASE_N * sizeof(unsigned long long));
+    if (ea != cudaSuccess) {
+        for (int i = 0; i < ProfileHook::MAX; i++) cudaEventDestroy(hk.ev[i]);
+        return cuda_fail(ea, "cudaMalloc (profile phases)");
+    }
+    const cudaStream_t st = (cudaStream_t)bt->stream;
+    double acc[ProfileHook::MAX] = {0}, ph[kPhaseSpans] = {0};
+    bool seen[kPhaseSpans];
+    for (bool &v : seen) v = true;
     int nk = 0;
+    bool phases = false;
     for (int r = 0; r < reps && s == EXAGO_OK; r++) {
         hk.n = 0;
+        cudaError_t e = cudaMemsetAsync(hk.phase, 0xFF, PHASE_N * sizeof(unsigned long long), st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(hk.phase + PHASE_N, 0, PHASE_N * sizeof(unsigned long long), st);
+        if (e != cudaSuccess) { s = cuda_fail(e, "cudaMemsetAsync (profile phases)"); break; }
         s = eval(net, bt, f, grad, gh, jval, hval, &hk);
         if (s != EXAGO_OK) break;
-        cudaError_t e = cudaStreamSynchronize((cudaStream_t)bt->stream);
+        e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { s = cuda_fail(e, "cudaStreamSynchronize (profile)"); break; }
         nk = hk.n - 1;
         for (int k = 0; k < nk; k++) {
@@ -908,11 +952,32 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *bt, double *
             acc[k] += t;
             names[k] = hk.name[k];
         }
+        phases = nk == 1 && std::strcmp(hk.name[0], "persistent") == 0;
+        if (phases) {
+            unsigned long long T[2 * PHASE_N];
+            e = cudaMemcpy(T, hk.phase, sizeof T, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { s = cuda_fail(e, "cudaMemcpy (profile phases)"); break; }
+            for (int k = 0; k < kPhaseSpans; k++) {
+                const PhaseSpan &q = kPhaseSpan[k];
+                const unsigned long long a = T[(q.from_latest ? PHASE_N : 0) + q.from];
+                const unsigned long long b = T[(q.to_latest ? PHASE_N : 0) + q.to];
+                // an event that never happened (no objective wanted) keeps its initial value
+                if (T[q.from] == ~0ull || T[q.to] == ~0ull) seen[k] = false;
+                ph[k] += ((double)b - (double)a) * 1e-6;   // ns -> ms (may be negative: overlap)
+            }
+        }
     }
+    cudaFree(hk.phase);
     for (int i = 0; i < ProfileHook::MAX; i++) cudaEventDestroy(hk.ev[i]);
     if (s != EXAGO_OK) return s;
-    *nkernels = nk;
     for (int k = 0; k < nk; k++) ms[k] = acc[k] / reps;
+    if (phases)
+        for (int k = 0; k < kPhaseSpans && nk < ProfileHook::MAX; k++)
+            if (seen[k]) {
+                names[nk] = kPhaseSpan[k].name;
+                ms[nk++] = ph[k] / reps;
+            }
+    *nkernels = nk;
     return EXAGO_OK;
 }
 

@@ -485,15 +485,15 @@ __device__ __forceinline__ void cart_bus_tile(const DevNet &N, const CartReq &R,
 // Objective of each state (the polar model's: it depends on Pg only).
 __global__ void __launch_bounds__(OBJ_LANES) k_cart_obj(const DevNet N, const EvalReq R, int b0) {
     __shared__ double part[OBJ_LANES];
-    obj_block<true>(N, R, b0 + blockIdx.x, part);
+    obj_block<true, OBJ_LANES>(N, R, b0 + blockIdx.x, part);
 }
 
 // Persistent schedule of the cartesian evaluation: the polar model's ticketed work list
 // (PersistParams, decode_item) over (state, 128 branches) and (state, 128 buses) items.  A branch
 // item writes its branches' records into ring slot b mod ring once the bus items of state
-// b - ring have consumed that slot; a bus item waits for all branch items of its state, assembles
-// its buses' rows (bus item 0 also the objective), discards the consumed records from L2 and
-// signals.  Each item computes exactly what the chunked kernels compute for it, so both
+// b - ring have consumed that slot (the last branch item first computes the state's objective); a bus
+// item waits for all branch items of its state, assembles its buses' rows, discards the consumed
+// records from L2 and signals.  Each item computes exactly what the chunked kernels compute for it, so both
 // schedules give bitwise equal results.  Waits are bounded as in the polar kernel.
 // MINB: resident CTAs per SM the register allocation must allow (1: the compiler's choice).
 template <bool PS, int MINB>
@@ -518,6 +518,14 @@ __global__ void __launch_bounds__(128, MINB) k_cart_persist(const DevNet N, cons
         int b, tile;
         decode_item(P, t, &is_branch, &b, &tile);
         double *scr = R.scratch + (size_t)(b % P.ring) * slot_doubles;
+        // the objective reads x only: the state's last branch item computes it first (bus item
+        // 0 when the net has no branches)
+        if (R.f && is_branch == (P.Tbr > 0) && tile == (P.Tbr > 0 ? P.Tbr - 1 : 0)) {
+            EvalReq E{};
+            E.B = R.B;
+            E.x = R.x; E.obj_weight = R.obj_weight; E.f = R.f; E.gen_mask = R.gen_mask;
+            obj_block<true, 128>(N, E, b, s_part);
+        }
         if (is_branch) {
             if (threadIdx.x == 0)
                 s_ok = b < P.ring || bounded_wait(done_bu + (b - P.ring), P.Tbu, P.spin_limit,
@@ -532,15 +540,7 @@ __global__ void __launch_bounds__(128, MINB) k_cart_persist(const DevNet N, cons
                 s_ok = bounded_wait(done_br + b, P.Tbr + P.force_timeout, P.spin_limit, N.status,
                                     ST_TIMEOUT_BUS);
             __syncthreads();
-            if (s_ok) {
-                cart_bus_tile(N, R, b, tile * 128, scr, stage, R.stage_cap);
-                if (tile == 0 && R.f) {
-                    EvalReq E{};
-                    E.B = R.B;
-                    E.x = R.x; E.obj_weight = R.obj_weight; E.f = R.f; E.gen_mask = R.gen_mask;
-                    obj_block<true>(N, E, b, s_part);
-                }
-            }
+            if (s_ok) cart_bus_tile(N, R, b, tile * 128, scr, stage, R.stage_cap);
             __syncthreads();
             if (threadIdx.x < 32) {
                 if (s_ok) {   // this item's records are consumed
@@ -952,6 +952,7 @@ exago_status cart_eval_persistent(exago_net_t net, const DevNet &N, const exago_
     P.total = B * (P.Tbr + P.Tbu);
     P.spin_limit = p.spin_limit;
     P.force_timeout = p.force_timeout;
+    P.times = nullptr;
     const int grid = std::min(p.grid, P.total);
     R.stage_cap = p.cap;
     // the net's lock stays held until the launch (or the graph launch) is queued

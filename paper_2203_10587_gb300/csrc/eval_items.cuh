@@ -649,9 +649,9 @@ __device__ __forceinline__ void bus_sums(const DevNet &N, const EvalReq &R, int 
 // The bus items of buses [i0, i0 + G::size()) of state b, by the whole group (i0 a multiple of
 // the group size), with `stage` = cap doubles of shared memory.  The tile's slots are one
 // contiguous range [S0, S1), and its rows are four contiguous segments.
-//   * With R.stage_recs, and when the slots' diagonal components and the row segments fit, the
-//     tile runs slot-parallel: every thread takes slots (slot_item), then every thread sums its
-//     bus's components from shared memory (bus_sums).
+//   * With R.stage_recs, and when the slots' diagonal components fit, the tile runs
+//     slot-parallel: every thread takes slots (slot_item), then every thread sums its bus's
+//     components from shared memory (bus_sums).
 //   * Otherwise every thread walks its own bus's slots, reading the records through L2
 //     (bus_item).
 // When the row segments fit (after the components, if used), every row entry is written to
@@ -675,7 +675,8 @@ __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int 
     const int m0 = row_start(N.bus_hM, i0, nb, N.hM_end), m1 = row_start(N.bus_hM, i1, nb, N.hM_end);
     const int LP = WJ ? p1 - p0 : 0, LA = WH ? a1 - a0 : 0, LM = WH ? m1 - m0 : 0;
     const int LROWS = 2 * LP + LA + LM;
-    const bool slotpar = R.stage_recs && kDiagComps * (S1 - S0) + LROWS <= cap;
+    // slot-parallel whenever the components fit; the rows are staged after them when they fit too
+    const bool slotpar = R.stage_recs && kDiagComps * (S1 - S0) <= cap;
     const int LD = slotpar ? kDiagComps * (S1 - S0) : 0;
     const bool staged = (WJ || WH) && LD + LROWS <= cap;
     double *Jb = WJ ? st_jval(N, R, b) : nullptr;
@@ -729,32 +730,105 @@ __device__ __forceinline__ void grad_bus(const DevNet &N, const EvalReq &R, int 
 // Virtual lane v < 256 sums generators v, v+256, ... in order; the 256 partials are combined by
 // a fixed pairwise tree.  The result is the same for every block size.  part: 256 doubles of
 // shared memory.
-constexpr int OBJ_LANES = 256;
-template <bool GM>
+constexpr int OBJ_LANES = kObjLanes;
+// NT: the block's threads (a divisor of OBJ_LANES).
+template <bool GM, int NT>
 __device__ __forceinline__ void obj_block(const DevNet &N, const EvalReq &R, int b, double *part) {
+    static_assert(NT >= 32 && OBJ_LANES % NT == 0, "block size");
+    constexpr int LPT = OBJ_LANES / NT;   // virtual lanes per thread
     const double *Pg = st_x(N, R, b) + 2 * N.nb;
     [[maybe_unused]] const uint8_t *gm = nullptr;
     if constexpr (GM) gm = st_gmask(N, R, b);
-    for (int v = threadIdx.x; v < OBJ_LANES; v += blockDim.x) {
-        double acc = 0.0;
-        for (int k = v; k < N.ng; k += OBJ_LANES) {
-            if constexpr (GM) {
-                if (!gen_on(gm, k)) continue;                 // generator out of service
-            }
-            const double MW = N.baseMVA * __ldg(Pg + k);
-            acc += fma(fma(__ldg(N.c2 + k), MW, __ldg(N.c1 + k)), MW, __ldg(N.c0 + k));
+    // Thread r holds lanes r, r + NT, ...  Each step loads the next two generators of all of them
+    // before adding, so that one thread has many loads in flight; every lane still adds its
+    // generators in increasing order.  A missing generator (past ng, or out of service) adds
+    // +0.0, which leaves the sum unchanged: it starts at +0.0, so it is never -0.0.
+    double acc[LPT];
+#pragma unroll
+    for (int j = 0; j < LPT; j++) acc[j] = 0.0;
+    auto term = [&](int v, int r) -> double {
+        const int k = v + r * OBJ_LANES;
+        if (k >= N.ng) return 0.0;
+        if constexpr (GM) {
+            if (!gen_on(gm, k)) return 0.0;                   // generator out of service
         }
-        part[v] = acc;
+        const double MW = N.baseMVA * __ldg(Pg + k);
+        return fma(fma(__ldg(N.c2 + k), MW, __ldg(N.c1 + k)), MW, __ldg(N.c0 + k));
+    };
+    const int rounds = (N.ng + OBJ_LANES - 1) / OBJ_LANES;
+    for (int r = 0; r < rounds; r += 2) {
+        double t0[LPT], t1[LPT];
+#pragma unroll
+        for (int j = 0; j < LPT; j++) {
+            t0[j] = term(threadIdx.x + j * NT, r);
+            t1[j] = term(threadIdx.x + j * NT, r + 1);
+        }
+#pragma unroll
+        for (int j = 0; j < LPT; j++) acc[j] = (acc[j] + t0[j]) + t1[j];
     }
+#pragma unroll
+    for (int j = 0; j < LPT; j++) part[threadIdx.x + j * NT] = acc[j];
     __syncthreads();
     for (int w = OBJ_LANES / 2; w > 0; w >>= 1) {
-        for (int v = threadIdx.x; v < w; v += blockDim.x) part[v] += part[v + w];
+        for (int v = threadIdx.x; v < w; v += NT) part[v] += part[v + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) *st_f(R, b) = st_w(R, b) * part[0];
     __syncthreads();
 }
 
+
+// The objective of state b split over several CTAs (the persistent schedule): lanes
+// [q NT, (q + 1) NT) of obj_block's 256 virtual lanes, one per thread, each summing its generators
+// in increasing order exactly as obj_block does, into partials[v] (global memory).
+template <bool GM, int NT>
+__device__ __forceinline__ void obj_lanes(const DevNet &N, const EvalReq &R, int b, int q,
+                                          double *partials) {
+    const double *Pg = st_x(N, R, b) + 2 * N.nb;
+    [[maybe_unused]] const uint8_t *gm = nullptr;
+    if constexpr (GM) gm = st_gmask(N, R, b);
+    const int v = q * NT + threadIdx.x;
+    auto term = [&](int k) -> double {
+        if (k >= N.ng) return 0.0;
+        if constexpr (GM) {
+            if (!gen_on(gm, k)) return 0.0;                   // generator out of service
+        }
+        const double MW = N.baseMVA * __ldg(Pg + k);
+        return fma(fma(__ldg(N.c2 + k), MW, __ldg(N.c1 + k)), MW, __ldg(N.c0 + k));
+    };
+    // four generators' loads in flight before their terms are added in order (+0.0 for a missing
+    // one leaves the sum unchanged, as in obj_block)
+    double acc = 0.0;
+    for (int k = v; k < N.ng; k += 4 * OBJ_LANES) {
+        const double t0 = term(k), t1 = term(k + OBJ_LANES), t2 = term(k + 2 * OBJ_LANES),
+                     t3 = term(k + 3 * OBJ_LANES);
+        acc = (((acc + t0) + t1) + t2) + t3;
+    }
+    partials[v] = acc;
+}
+
+// obj_block's fixed pairwise tree over the 256 partials, by one warp (lanes 0..31 of the
+// calling warp): levels 128, 64 and 32 in registers (lane l holds lanes l + 32 j), then 16 .. 1
+// by shuffles, each level adding part[v + w] to part[v] for v < w as obj_block does, so the
+// result is bitwise obj_block's.  Writes f[b].  partials were written by other CTAs of the launch
+// (read through L2).
+__device__ __forceinline__ void obj_tree_warp(const EvalReq &R, int b, const double *partials) {
+    const int l = threadIdx.x & 31;
+    double p[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) p[j] = __ldcg(partials + l + 32 * j);
+#pragma unroll
+    for (int j = 0; j < 4; j++) p[j] += p[j + 4];
+    p[0] += p[2];
+    p[1] += p[3];
+    p[0] += p[1];
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, p[0], w);
+        if (l < w) p[0] += o;
+    }
+    if (l == 0) *st_f(R, b) = st_w(R, b) * p[0];
+}
 
 // Records an event on the launching stream before a kernel when profiling.
 static inline void mark(ProfileHook *hk, cudaStream_t st, const char *name) {

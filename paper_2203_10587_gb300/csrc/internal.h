@@ -180,11 +180,14 @@ exago_status build_plan(HostPlan &p, int nb, const double *Gs, const double *Bs,
 
 // Optional per-kernel timing: an event is recorded on the launching stream before each kernel
 // and after the last one; name[i] labels the interval ev[i] .. ev[i+1].
+// phase: a device array of 16 u64 for the persistent kernel's phase timestamps (earliest and
+// latest global-timer ns of each PhaseSlot event, persist_kernel.cuh), or null.
 struct ProfileHook {
     static constexpr int MAX = 16;
     cudaEvent_t ev[MAX];
     const char *name[MAX];
     int n = 0;
+    unsigned long long *phase = nullptr;
 };
 
 // Kernel launchers (kernels.cu).  Each returns the launch's cudaError_t as int.
@@ -217,6 +220,9 @@ int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes);
 // largest tile's need in doubles, capped at kStageMaxDoubles; a tile above the cap reads its
 // records from global memory and writes its rows directly.
 constexpr int kStageMaxDoubles = 9216;   // 72 KB
+// The persistent schedule's ring slot of one state: NCOMP x nslot doubles of branch-end records,
+// then the kObjLanes partial sums of the state's objective (256 virtual lanes).
+constexpr int kObjLanes = 256;
 constexpr int kDiagComps = 7;            // record components summed into a bus's diagonal
 __host__ __device__ inline int stage_index(int block) {
     return block == 32 ? 0 : block == 64 ? 1 : block == 256 ? 3 : 2;

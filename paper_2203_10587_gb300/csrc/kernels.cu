@@ -104,7 +104,7 @@ __global__ void k_grad(const DevNet N, const EvalReq R, int b0) {
 
 __global__ void __launch_bounds__(OBJ_LANES) k_obj(const DevNet N, const EvalReq R, int b0) {
     __shared__ double part[OBJ_LANES];
-    obj_block<true>(N, R, b0 + blockIdx.x, part);
+    obj_block<true, OBJ_LANES>(N, R, b0 + blockIdx.x, part);
 }
 
 template <int WANT>

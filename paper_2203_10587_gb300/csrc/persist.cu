@@ -54,6 +54,7 @@ int launch_eval_persistent(const DevNet &N, const EvalReq &R, const PersistLaunc
     P.ctr = L.counters;
     P.spin_limit = L.spin_limit;
     P.force_timeout = L.force_timeout;
+    P.times = hk ? hk->phase : nullptr;
     // every wait must point to a smaller ticket: ring slots must outnumber the lag
     if (P.lag < 1 || P.ring <= P.lag) return (int)cudaErrorInvalidValue;
     mark(hk, st, "persistent");

@@ -25,14 +25,49 @@ namespace exago {
 // Both wait only on items with smaller tickets, which are held by running CTAs and wait only on
 // smaller tickets still; the smallest unfinished ticket never waits, so the launch cannot
 // deadlock.  Every wait is bounded: after spin_limit polls it records a timeout in the status
-// word, skips its work and still signals, so the launch always ends.  Bus tile 0 of each state
-// also writes its objective; every bus tile writes the gradient entries of its buses.
+// word, skips its work and still signals, so the launch always ends.  The objective is split
+// over the state's last branch items, which write the partial sums of its 256 virtual lanes into
+// the ring slot (after the records), and bus tile 0 adds them up with obj_block's tree (it does
+// the whole objective on a net without branches); every bus tile writes the gradient entries of
+// its buses.
 struct PersistParams {
     int B, Tbr, Tbu, lag, ring, total, group;
     int *ctr;               // [1 + 2B]: ticket, branch tiles done per state, bus tiles done
     long long spin_limit;
     int force_timeout;      // testing: bus tiles wait for one branch tile more than exists
+    // exago_eval_profile only (else null): phase times in ns of the global timer, earliest
+    // [0 .. PH_N) and latest [PH_N .. 2 PH_N) over the launch's CTAs (PhaseSlot)
+    unsigned long long *times;
 };
+
+// Phase timestamps of a profiled persistent launch: slot k holds the earliest (times[k]) and the
+// latest (times[PH_N + k]) time that event k was reached.
+enum PhaseSlot : int {
+    PH_ENTRY = 0,      // a CTA starts
+    PH_BR_START = 1,   // a branch item starts its work (after its ring wait)
+    PH_BR_END = 2,     // a branch item has finished
+    PH_BU_START = 3,   // a bus item starts its work (after its wait for the state's branches)
+    PH_BU_END = 4,     // a bus item has finished
+    PH_OBJ_START = 5,  // the objective of a state starts
+    PH_OBJ_END = 6,    // and ends
+    PH_EXIT = 7,       // a CTA exits
+    PH_N = 8
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Thread 0 of a profiled launch records event k (earliest and latest).
+__device__ __forceinline__ void phase_mark(unsigned long long *times, int k) {
+    if (times && threadIdx.x == 0) {
+        const unsigned long long t = global_ns();
+        atomicMin(times + k, t);
+        atomicMax(times + PH_N + k, t);
+    }
+}
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
@@ -103,12 +138,15 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
     __shared__ double s_part[OBJ_LANES];
     extern __shared__ double stage[];
     int *done_br = P.ctr + 1, *done_bu = P.ctr + 1 + P.B;
-    const size_t slot_doubles = (size_t)NCOMP * N.nslot;
+    static_assert(OBJ_LANES == kObjLanes && OBJ_LANES % NT == 0, "objective lanes");
+    const size_t rec_doubles = (size_t)NCOMP * N.nslot;
+    const size_t slot_doubles = rec_doubles + kObjLanes;   // records, then objective partials
     const int cap = R.stage_cap;
     // Thread 0 claims the next ticket while the block works on the current one.  The smallest
     // unfinished ticket is always some block's current item (a block's prefetched ticket is
     // larger than its current one), so the argument above still holds.
     int next = 0;
+    phase_mark(P.times, PH_ENTRY);
     if (threadIdx.x == 0) next = atomicAdd(P.ctr, 1);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -117,7 +155,10 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
         }
         __syncthreads();
         const int t = s_item;
-        if (t >= P.total) return;
+        if (t >= P.total) {
+            phase_mark(P.times, PH_EXIT);
+            return;
+        }
         bool is_branch;
         int b, tile;
         decode_item(P, t, &is_branch, &b, &tile);
@@ -128,17 +169,30 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
                 s_ok = b < P.ring || bounded_wait(done_bu + (b - P.ring), P.Tbu, P.spin_limit,
                                                   N.status, ST_TIMEOUT_RING);
             __syncthreads();
+            phase_mark(P.times, PH_BR_START);
+            if (s_ok && R.f) {
+                // the objective's lane groups q = 0 .. 256/NT - 1, group q by the state's branch
+                // item Tbr - 1 - (q mod Tbr) (the last items, the ragged tail among them), into
+                // the slot's partials; bus item 0 adds them up
+                constexpr int G = OBJ_LANES / NT;
+                for (int q = P.Tbr - 1 - tile; q < G; q += P.Tbr) {
+                    phase_mark(P.times, PH_OBJ_START);
+                    obj_lanes<(WANT & W_GM) != 0, NT>(N, R, b, q, scr + rec_doubles);
+                }
+            }
             if (s_ok)
                 for (int l = tile * P.group * NT + threadIdx.x; l < N.nl && l < (tile + 1) * P.group * NT;
                      l += NT)
                     branch_item<WANT>(N, R, b, l, scr);
             __syncthreads();
             if (threadIdx.x == 0) red_release_add(done_br + b);
+            phase_mark(P.times, PH_BR_END);
         } else {
             if (threadIdx.x == 0)
                 s_ok = bounded_wait(done_br + b, P.Tbr + P.force_timeout, P.spin_limit, N.status,
                                     ST_TIMEOUT_BUS);
             __syncthreads();
+            phase_mark(P.times, PH_BU_START);
             if (s_ok) {
                 for (int k = 0; k < P.group; k++) {
                     const int i0 = (tile * P.group + k) * NT;
@@ -148,9 +202,17 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
                     if (i0 + (int)threadIdx.x < N.nb && R.grad)
                         grad_bus<(WANT & W_GM) != 0>(N, R, b, i0 + threadIdx.x);
                 }
-                if (tile == 0 && R.f) obj_block<(WANT & W_GM) != 0>(N, R, b, s_part);
+                if (tile == 0 && R.f) {
+                    if (P.Tbr == 0) {   // no branch items: the whole objective here
+                        obj_block<(WANT & W_GM) != 0, NT>(N, R, b, s_part);
+                    } else if (threadIdx.x < 32) {
+                        obj_tree_warp(R, b, scr + rec_doubles);
+                    }
+                    phase_mark(P.times, PH_OBJ_END);
+                }
             }
             __syncthreads();
+            phase_mark(P.times, PH_BU_END);
             if (threadIdx.x < 32) {
                 if (s_ok && (WANT & (W_G | W_J | W_H))) {   // this item's records are consumed
                     const int i0 = tile * P.group * NT;

@@ -2,7 +2,7 @@
 replayed with new inputs written into the captured buffers.  Each replay must equal, bit for bit,
 a direct call on the same inputs: the polar model on the persistent, pipelined (two streams,
 forked and joined by events inside the capture) and multi-kernel schedules, and the cartesian
-model's two-stream schedule.  A call outside the capture comes first, so that the workspace and
+model's persistent and two-stream chunked schedules.  A call outside the capture comes first, so that the workspace and
 the launch-configuration caches exist before capture (nothing may allocate while capturing).
 """
 import numpy as np
@@ -73,15 +73,17 @@ def test_polar_call_captured_in_a_graph(ex, schedule):
     net.close()
 
 
-def test_cartesian_call_captured_in_a_graph(ex):
+@pytest.mark.parametrize("schedule", [2, 3])
+def test_cartesian_call_captured_in_a_graph(ex, schedule):
     import torch
     from test_gpu_cartesian import to_cartesian
     g = synth.grid_2000()
-    b1 = synth.contingency_batch(3, g, 96)       # three chunks: the two-stream schedule
+    b1 = synth.contingency_batch(3, g, 96)       # chunked: three chunks on two streams
     b2 = synth.contingency_batch(4, g, 96)
     x1, l1 = to_cartesian(g, b1, 5)
     x2, l2 = to_cartesian(g, b2, 6)
     net = ex.Net(g)
+    ex.exago_net_set_config(net.h, schedule=schedule)
     n, me, mi, nj, nh = ex.exago_net_dims_cart(net.h)
     t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
     x, lam, mask = t(x1, torch.float64), t(l1, torch.float64), t(b1.mask, torch.uint8)

@@ -167,7 +167,21 @@ def test_profile_names_the_persistent_kernel(ex):
     ex.exago_net_set_config(net.h, schedule=2)
     prof = ex.exago_eval_profile(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"],
                                  out["hval"], reps=3)
-    assert [n for n, _ in prof] == ["persistent"] and prof[0][1] > 0
+    assert prof[0][0] == "persistent" and prof[0][1] > 0
+    ph = dict(prof[1:])
+    assert len(ph) == 7 and all(n.startswith("phase: ") for n in ph)
+    span = ph["phase: first CTA entry to last CTA exit"]
+    # the device-timed span fits inside the event-timed interval (which adds the counters'
+    # memset and the launch); phases of eight states overlap, but each lies within the span
+    assert 0 <= span <= prof[0][1] * 1.05 + 2e-3
+    for n in ("phase: first to last branch item (start to end)",
+              "phase: first to last bus item (start to end)",
+              "phase: objective (first start to last end)"):
+        assert 0 <= ph[n] <= span, n
+    # without the objective its phase is left out
+    prof = ex.exago_eval_profile(net.h, bt, None, out["grad"], out["gh"], out["jval"],
+                                 out["hval"], reps=2)
+    assert "phase: objective (first start to last end)" not in dict(prof)
     ex.exago_net_set_config(net.h, schedule=1)
     prof = ex.exago_eval_profile(net.h, bt, out["f"], out["grad"], out["gh"], out["jval"],
                                  out["hval"], reps=3)
