@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ / 1e3
 FP64_PEAK_GINSTR = SMS * FP64_FMA_PER_SM_CLK * SM_MAX_GHZ
 # dram bytes per launch of the dominant kernel from its ncu capture, by kernel name; a kernel
 # changed since its capture has no entry
-TRAFFIC_BYTES = {"persistent": 386_942_464}   # 63.8 MB read + 323.2 MB written (ncu, 2000-bus x 512)
+TRAFFIC_BYTES = {"persistent": 384_156_672}   # 63.5 MB read + 320.7 MB written (ncu, 2000-bus x 512)
 HBM_PEAK_FALLBACK_GBS = 6800.0
 
 
@@ -703,6 +703,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     # ---- per-kernel timing of the same evaluation (CUDA events on the launching stream)
     prof = exago.exago_eval_profile(net.h, batches[0], out["f"], out["grad"], out["gh"],
                                     out["jval"], out["hval"], reps=min(args.steps, 100))
+    phases = {k[len("phase: "):]: v for k, v in prof if k.startswith("phase: ")}
+    prof = [(k, v) for k, v in prof if not k.startswith("phase: ")]
     kernels_per_step = len(prof)
     total_prof = sum(ms for _, ms in prof)
     top_name, top_ms = max(prof, key=lambda kv: kv[1])
@@ -838,6 +840,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "unbatched": unbatched,
         "kernels_ms": {k: v for k, v in prof},
         "kernel_share": {k: v / total_prof for k, v in prof},
+        "phases_ms": phases,
         "roofline": {"kernel": top_name, "bound": "alu", "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                      "traffic": TRAFFIC_BYTES.get(top_name),

@@ -411,7 +411,7 @@ exago_status exago_eval_all_static(exago_net_t net, const exago_batch *batch, do
  * each kernel of one evaluation: names[k] (static strings: "branch", "bus", "grad", "obj" for
  * the multi-kernel schedule, "persistent" for the fused one) and ms[k] for k < *nkernels.
  * After "persistent" come the fused kernel's phases, timed on the device's global timer by the
- * CTAs themselves (names starting "phase: "): kernel span, CTA entry to the first branch item,
+ * CTAs themselves in `reps` further evaluations (names starting "phase: "): kernel span, CTA entry to the first branch item,
  * the branch items, the last branch end to the first bus start (the wait of a single state),
  * the bus items, the objective, and the last bus end to the last CTA exit.  With several states
  * the phases overlap (a span can then exceed the sum, or be negative).  names and ms need room

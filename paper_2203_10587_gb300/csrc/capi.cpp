@@ -935,27 +935,34 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *bt, double *
     for (bool &v : seen) v = true;
     int nk = 0;
     bool phases = false;
-    for (int r = 0; r < reps && s == EXAGO_OK; r++) {
+    // reps evaluations timed by events with the phase marks off, then (for the persistent
+    // schedule) reps more with them on, whose event times are not used
+    unsigned long long *phase_buf = hk.phase;
+    for (int r = 0; r < 2 * reps && s == EXAGO_OK; r++) {
+        const bool timed = r < reps;
+        if (!timed && !phases) break;
         hk.n = 0;
-        cudaError_t e = cudaMemsetAsync(hk.phase, 0xFF, PHASE_N * sizeof(unsigned long long), st);
+        hk.phase = timed ? nullptr : phase_buf;
+        cudaError_t e = cudaMemsetAsync(phase_buf, 0xFF, PHASE_N * sizeof(unsigned long long), st);
         if (e == cudaSuccess)
-            e = cudaMemsetAsync(hk.phase + PHASE_N, 0, PHASE_N * sizeof(unsigned long long), st);
+            e = cudaMemsetAsync(phase_buf + PHASE_N, 0, PHASE_N * sizeof(unsigned long long), st);
         if (e != cudaSuccess) { s = cuda_fail(e, "cudaMemsetAsync (profile phases)"); break; }
         s = eval(net, bt, f, grad, gh, jval, hval, &hk);
         if (s != EXAGO_OK) break;
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { s = cuda_fail(e, "cudaStreamSynchronize (profile)"); break; }
-        nk = hk.n - 1;
-        for (int k = 0; k < nk; k++) {
-            float t = 0.f;
-            cudaEventElapsedTime(&t, hk.ev[k], hk.ev[k + 1]);
-            acc[k] += t;
-            names[k] = hk.name[k];
-        }
-        phases = nk == 1 && std::strcmp(hk.name[0], "persistent") == 0;
-        if (phases) {
+        if (timed) {
+            nk = hk.n - 1;
+            for (int k = 0; k < nk; k++) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, hk.ev[k], hk.ev[k + 1]);
+                acc[k] += t;
+                names[k] = hk.name[k];
+            }
+            phases = nk == 1 && std::strcmp(hk.name[0], "persistent") == 0;
+        } else {
             unsigned long long T[2 * PHASE_N];
-            e = cudaMemcpy(T, hk.phase, sizeof T, cudaMemcpyDeviceToHost);
+            e = cudaMemcpy(T, phase_buf, sizeof T, cudaMemcpyDeviceToHost);
             if (e != cudaSuccess) { s = cuda_fail(e, "cudaMemcpy (profile phases)"); break; }
             for (int k = 0; k < kPhaseSpans; k++) {
                 const PhaseSpan &q = kPhaseSpan[k];
@@ -967,7 +974,7 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *bt, double *
             }
         }
     }
-    cudaFree(hk.phase);
+    cudaFree(phase_buf);
     for (int i = 0; i < ProfileHook::MAX; i++) cudaEventDestroy(hk.ev[i]);
     if (s != EXAGO_OK) return s;
     for (int k = 0; k < nk; k++) ms[k] = acc[k] / reps;
