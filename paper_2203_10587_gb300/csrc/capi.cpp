@@ -368,7 +368,7 @@ size_t persist_slot_bytes(const exago_net *net) {
 // Workspace of the persistent schedule: ring scratch, then counters.
 size_t persist_bytes(const exago_net *net, const Resolved &r, int B) {
     return round256(r.ring * persist_slot_bytes(net)) +
-           round256((size_t)(1 + 2 * (size_t)B) * sizeof(int));
+           round256((size_t)(1 + 2 * (size_t)B + 256) * sizeof(int));
 }
 
 size_t need_bytes(exago_net *net, int B) {
@@ -630,6 +630,7 @@ exago_status eval_locked(exago_net *net, const exago_batch *bt, double *f, doubl
     pl.group = rs.group;
     pl.spin_limit = rs.spin_limit; pl.force_timeout = rs.force_timeout;
     pl.counters = (int *)w;
+    pl.sm_count = net->sm_count;
     if (graph) {
         std::vector<uint64_t> key = req_key(R, EXAGO_SCHED_PERSISTENT);
         for (uint64_t v : {(uint64_t)pl.counters, (uint64_t)pl.block, (uint64_t)pl.grid,

@@ -199,7 +199,7 @@ int launch_eval(const DevNet &net, const EvalReq &req, void *stream, ProfileHook
 int launch_eval_pipelined(const DevNet &net, const EvalReq &req, const PipeLaunch &pl,
                           void *stream, ProfileHook *hook = nullptr);
 
-// Persistent schedule (one launch; see persist.cu).  counters: 1 + 2B ints of the workspace;
+// Persistent schedule (one launch; see persist.cu).  counters: 1 + 2B + 256 ints of the workspace;
 // req.scratch holds `ring` state slots.
 struct PersistLaunch {
     int block;              // 64, 128 or 256 threads
@@ -210,7 +210,8 @@ struct PersistLaunch {
     int group;              // tiles of one kind and state per work item
     long long spin_limit;   // polls before a bounded wait gives up
     int force_timeout;      // testing only
-    int *counters;
+    int sm_count;           // SMs of the device
+    int *counters;          // 1 + 2B + 256 ints
 };
 int launch_eval_persistent(const DevNet &net, const EvalReq &req, const PersistLaunch &pl,
                            void *stream, ProfileHook *hook = nullptr);

@@ -58,9 +58,13 @@ int launch_eval_persistent(const DevNet &N, const EvalReq &R, const PersistLaunc
     // every wait must point to a smaller ticket: ring slots must outnumber the lag
     if (P.lag < 1 || P.ring <= P.lag) return (int)cudaErrorInvalidValue;
     mark(hk, st, "persistent");
-    cudaError_t e = cudaMemsetAsync(L.counters, 0, (size_t)(1 + 2 * R.B) * sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(L.counters, 0, (size_t)(1 + 2 * R.B + kSpreadSMs) * sizeof(int),
+                                    st);
     if (e != cudaSuccess) return (int)e;
     int grid = L.grid < P.total ? L.grid : P.total;
+    // a launch of at most two items per CTA spreads its items over the SMs (PersistParams::spread):
+    // the first ceil(total / SMs) CTAs of each SM take part
+    P.spread = L.sm_count > 0 && P.total <= 2 * grid ? (P.total + L.sm_count - 1) / L.sm_count : 0;
     int rc;
     if (R.gen_mask || R.tab || N.Gtf) {
         // generator masks (a gathered batch's states may carry their own) or phase shifters

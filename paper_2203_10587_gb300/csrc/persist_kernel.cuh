@@ -38,7 +38,14 @@ struct PersistParams {
     // exago_eval_profile only (else null): phase times in ns of the global timer, earliest
     // [0 .. PH_N) and latest [PH_N .. 2 PH_N) over the launch's CTAs (PhaseSlot)
     unsigned long long *times;
+    // Small launches (a few items per SM): 0 = off.  Otherwise the CTAs rank themselves on their
+    // SM (ctr[1 + 2B + smid]); rank >= spread exits at once, and rank k claims its first item
+    // after k x kSpreadNs and claims one item at a time, so that consecutive tickets land on
+    // different SMs instead of piling onto the CTAs that start first.
+    int spread;
 };
+constexpr int kSpreadSMs = 256;        // per-SM rank counters after the per-state counters
+constexpr unsigned kSpreadNs = 400;    // a claim round: about the time all SMs' first CTAs claim
 
 // Phase timestamps of a profiled persistent launch: slot k holds the earliest (times[k]) and the
 // latest (times[PH_N + k]) time that event k was reached.
@@ -144,14 +151,34 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
     const int cap = R.stage_cap;
     // Thread 0 claims the next ticket while the block works on the current one.  The smallest
     // unfinished ticket is always some block's current item (a block's prefetched ticket is
-    // larger than its current one), so the argument above still holds.
+    // larger than its current one), so the argument above still holds.  In a spread launch a
+    // block claims one ticket at a time (and late-ranked blocks claim none): the argument holds
+    // as well, since tickets are still claimed in order by running blocks.
     int next = 0;
     phase_mark(P.times, PH_ENTRY);
-    if (threadIdx.x == 0) next = atomicAdd(P.ctr, 1);
-    for (;;) {
+    if (threadIdx.x == 0) {
+        if (P.spread > 0) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            const int k = smid < kSpreadSMs ? atomicAdd(P.ctr + 1 + 2 * P.B + smid, 1) : 0;
+            if (k >= P.spread) next = P.total;                   // enough blocks on this SM
+            else {
+                if (k > 0) __nanosleep(k * kSpreadNs);
+                next = atomicAdd(P.ctr, 1);
+            }
+        } else {
+            next = atomicAdd(P.ctr, 1);
+        }
+    }
+    for (bool first = true;; first = false) {
         if (threadIdx.x == 0) {
-            s_item = next;
-            if (next < P.total) next = atomicAdd(P.ctr, 1);
+            if (P.spread > 0) {
+                if (!first && next < P.total) next = atomicAdd(P.ctr, 1);
+                s_item = next;
+            } else {
+                s_item = next;
+                if (next < P.total) next = atomicAdd(P.ctr, 1);
+            }
         }
         __syncthreads();
         const int t = s_item;
