@@ -666,6 +666,16 @@ exago_status exago_net_check(exago_net_t net, void *stream);
  */
 exago_status exago_test_debug_bounds(exago_net_t net, int slots);
 
+/*
+ * Testing only: the persistent schedule's work list, decoded on the host by the kernels' own
+ * decoder, for B states of Tbr branch items and Tbu bus items each, bus items trailing branch
+ * items by `lag` states.  HOST arrays of B (Tbr + Tbu) entries receive, per ticket, kind
+ * (1 branch, 0 bus), state and tile.  EINVAL unless B >= 1, Tbr >= 0, Tbu >= 1, 1 <= lag <= B
+ * and B (Tbr + Tbu) fits an int.  The paper has no counterpart.
+ */
+exago_status exago_test_work_list(int B, int Tbr, int Tbu, int lag, int *kind, int *state,
+                                  int *tile);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,3 +78,25 @@ int launch_eval_persistent(const DevNet &N, const EvalReq &R, const PersistLaunc
 }
 
 }  // namespace exago
+
+extern "C" exago_status exago_test_work_list(int B, int Tbr, int Tbu, int lag, int *kind,
+                                             int *state, int *tile) {
+    if (B < 1 || Tbr < 0 || Tbu < 1 || lag < 1 || lag > B || !kind || !state || !tile ||
+        (long long)B * (Tbr + Tbu) > 2147483647ll)
+        return exago::set_last_error(EXAGO_EINVAL, "bad work-list arguments");
+    exago::PersistParams P{};
+    P.B = B;
+    P.Tbr = Tbr;
+    P.Tbu = Tbu;
+    P.lag = lag;
+    P.total = B * (Tbr + Tbu);
+    for (int t = 0; t < P.total; t++) {
+        bool br = false;
+        int b = 0, tl = 0;
+        exago::decode_item(P, t, &br, &b, &tl);
+        kind[t] = br ? 1 : 0;
+        state[t] = b;
+        tile[t] = tl;
+    }
+    return EXAGO_OK;
+}

@@ -117,8 +117,8 @@ __device__ __forceinline__ void discard_lines(const void *p, const void *q, int 
     for (; a < e; a += 32 * 128) asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
 }
 
-__device__ __forceinline__ void decode_item(const PersistParams &P, int t, bool *is_branch, int *b,
-                                            int *tile) {
+__host__ __device__ __forceinline__ void decode_item(const PersistParams &P, int t, bool *is_branch,
+                                                     int *b, int *tile) {
     const int L = P.lag, Tbr = P.Tbr, Tbu = P.Tbu;
     const int head = L * Tbr;
     if (t < head) {

@@ -45,6 +45,7 @@ EXPORTS = [
     "exago_kkt_create", "exago_kkt_destroy", "exago_kkt_info", "exago_kkt_order",
     "exago_kkt_workspace_size", "exago_pf_create", "exago_pf_destroy", "exago_pf_workspace_size",
     "exago_pf_step", "exago_test_debug_bounds", "exago_serve_drive", "exago_serve_register_cart",
+    "exago_test_work_list",
     "exago_kkt_solve",
 ]
 
@@ -129,6 +130,7 @@ def lib():
                 "exago_serve_create": ([ctypes.c_size_t, i32, i32, ctypes.POINTER(vp)], i32),
                 "exago_serve_register": ([vp, vp, ctypes.POINTER(i32)], i32),
                 "exago_serve_register_cart": ([vp, vp, ctypes.POINTER(i32)], i32),
+                "exago_test_work_list": ([i32, i32, i32, i32, vp, vp, vp], i32),
                 "exago_serve_submit": ([vp, i32, ctypes.POINTER(exago_batch), vp, vp, vp, vp, vp,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)], i32),
                 "exago_serve_set_merge": ([vp, i32], i32),
@@ -432,6 +434,16 @@ def exago_serve_register(s, net_h) -> int:
     i = ctypes.c_int()
     _check(lib().exago_serve_register(s, net_h, ctypes.byref(i)))
     return i.value
+
+
+def exago_test_work_list(B: int, Tbr: int, Tbu: int, lag: int):
+    """The persistent schedule's work list decoded on the host: (kind, state, tile) per ticket."""
+    import numpy as np
+    n = B * (Tbr + Tbu)
+    k, st, tl = (np.zeros(max(n, 1), dtype=np.int32) for _ in range(3))
+    _check(lib().exago_test_work_list(int(B), int(Tbr), int(Tbu), int(lag), _hp(k), _hp(st),
+                                      _hp(tl)))
+    return k[:n], st[:n], tl[:n]
 
 
 def exago_serve_register_cart(s, net_h) -> int:
