@@ -455,11 +455,19 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *             wait times out; the launch still ends and exago_net_check reports it.
  *   tile_group  persistent: tiles of one kind and state per work item (1 to 4; 0 = 1), which
  *             divides the items' claims, waits and signals by that number.
+ *   tiling    persistent: EXAGO_TILING_DEFAULT / THREAD: branch per thread -- each thread of a
+ *             tile takes its own branch (bus) of one state.  EXAGO_TILING_WARP: branch per warp
+ *             -- each warp takes one branch (bus) and its 32 lanes take 32 consecutive states,
+ *             so every lane of a warp walks a bus of the same degree; blocks of 64 or 128
+ *             threads, occupancy 8 or 16, tile_group branches (buses) per warp and work item,
+ *             no record staging, and lag and ring count groups of 32 states.  Both tilings
+ *             give bitwise equal outputs.  The power-balance-cartesian calls ignore it.
  */
 enum { EXAGO_SCHED_AUTO = 0, EXAGO_SCHED_KERNELS = 1, EXAGO_SCHED_PERSISTENT = 2,
        EXAGO_SCHED_PIPELINED = 3 };
 enum { EXAGO_GRAPH_DEFAULT = 0, EXAGO_GRAPH_ON = 1, EXAGO_GRAPH_OFF = 2 };
 enum { EXAGO_STAGE_DEFAULT = 0, EXAGO_STAGE_ON = 1, EXAGO_STAGE_OFF = 2 };
+enum { EXAGO_TILING_DEFAULT = 0, EXAGO_TILING_THREAD = 1, EXAGO_TILING_WARP = 2 };
 typedef struct {
     int schedule;
     int block;
@@ -472,6 +480,7 @@ typedef struct {
     long long spin_limit;
     int test_force_timeout;
     int tile_group;
+    int tiling;
 } exago_config;
 
 /* Sets the net's configuration (validated: EINVAL for unknown values or ring <= lag). */
@@ -483,7 +492,9 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg);
 /*
  * Autotuner: times the multi-kernel schedule, pipelined variants (three chunk sizes) and
  * persistent variants (block 32 / 64 / 128 / 256, occupancy 8 / 16 / 24 warps, 1 or 2 tiles per
- * work item), each with and without slot-parallel bus tiles, on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
+ * work item), each with and without slot-parallel bus tiles, and the warp-tiled persistent
+ * variants (branch per warp: block 64 / 128, occupancy 8 / 16, 1 or 2 branches per warp and
+ * item), on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
  * fastest for batches of this size (used by EXAGO_SCHED_AUTO).  Outputs are written as by
  * exago_eval_all.  *best (may be NULL) receives the choice.
  */

@@ -272,6 +272,8 @@ struct Resolved {
     int schedule;          // EXAGO_SCHED_KERNELS or EXAGO_SCHED_PERSISTENT
     int block, occ_warps, stage_recs, stage_cap, grid, lag, ring, use_graph, force_timeout;
     int group;             // persistent: tiles per work item
+    int warp_tiles;        // persistent: warp-tiled kernel (a warp per branch or bus, a lane per
+                           // state); lag and ring then count groups of 32 states
     int chunk, pipe_ring;  // pipelined schedule
     long long spin_limit;
 };
@@ -280,12 +282,16 @@ constexpr long long kDefaultSpinLimit = 1ll << 22;   // polls of ~0.4 us: about 
 
 // Resident CTAs per SM of the persistent kernel (persistent) or of the bus kernel (otherwise)
 // with `smem` bytes of dynamic shared memory, cached.
-int occupancy(exago_net *net, bool persistent, int block, int occ_warps, size_t smem) {
-    const uint64_t key = ((uint64_t)persistent << 62) | ((uint64_t)block << 48) |
-                         ((uint64_t)occ_warps << 40) | (uint64_t)smem;
+// warp: the warp-tiled persistent kernel (no dynamic shared memory).
+int occupancy(exago_net *net, bool persistent, int block, int occ_warps, size_t smem,
+              bool warp = false) {
+    const uint64_t key = ((uint64_t)persistent << 62) | ((uint64_t)warp << 61) |
+                         ((uint64_t)block << 48) | ((uint64_t)occ_warps << 40) | (uint64_t)smem;
     auto it = net->occ.find(key);
     if (it != net->occ.end()) return it->second;
-    const int o = persistent ? persist_blocks_per_sm(block, occ_warps, smem) : bus_blocks_per_sm(smem);
+    const int o = warp         ? persist_w_blocks_per_sm(block, occ_warps)
+                  : persistent ? persist_blocks_per_sm(block, occ_warps, smem)
+                               : bus_blocks_per_sm(smem);
     net->occ[key] = o;
     return o;
 }
@@ -330,10 +336,37 @@ Resolved resolve(exago_net *net, int B) {
     r.occ_warps = (c.occupancy == 8 || c.occupancy == 24) ? c.occupancy : 16;
     r.stage_recs = c.stage_records == EXAGO_STAGE_ON;
     const bool pers = r.schedule == EXAGO_SCHED_PERSISTENT;
+    r.use_graph = c.use_graph != EXAGO_GRAPH_OFF;
+    r.spin_limit = c.spin_limit > 0 ? c.spin_limit : kDefaultSpinLimit;
+    r.force_timeout = c.test_force_timeout ? 1 : 0;
+    r.group = c.tile_group >= 1 && c.tile_group <= 4 ? c.tile_group : 1;
+    if (pers && c.tiling == EXAGO_TILING_WARP) {
+        // warp-tiled: blocks of 64 or 128 threads, no shared-memory staging; the lag and the ring
+        // count groups of 32 states.  By default bus items trail by the groups the resident CTAs
+        // hold in branch work plus one, and the ring holds two more groups (a group's records are
+        // 32 x 80 bytes per branch end, so a few groups already fill a good part of L2).
+        r.warp_tiles = 1;
+        r.block = c.block == 128 ? 128 : 64;
+        r.occ_warps = c.occupancy == 8 ? 8 : 16;
+        r.stage_recs = 0;
+        r.stage_cap = 0;
+        r.grid = net->sm_count * occupancy(net, true, r.block, r.occ_warps, 0, true);
+        const int G = (B + 31) / 32;
+        const int per_item = (r.block / 32) * r.group;
+        const int Tbr = (net->plan.nl + per_item - 1) / per_item;
+        int lag = c.lag > 0 ? c.lag : (Tbr > 0 ? (r.grid + Tbr - 1) / Tbr : 1) + 1;
+        if (lag > G) lag = G;
+        if (lag < 1) lag = 1;
+        int ring = c.ring > 0 ? c.ring : lag + 2;
+        if (ring <= lag) ring = lag + 1;
+        if (ring > G + 1) ring = G + 1 > lag ? G + 1 : lag + 1;
+        r.lag = lag;
+        r.ring = ring;
+        return r;
+    }
     r.stage_cap = stage_cap(net, pers, r.block, r.occ_warps, r.stage_recs);
     r.grid = net->sm_count * occupancy(net, true, r.block, r.occ_warps,
                                        pers ? (size_t)r.stage_cap * sizeof(double) : 0);
-    r.group = c.tile_group >= 1 && c.tile_group <= 4 ? c.tile_group : 1;
     const int Tbr = (net->plan.nl + r.block * r.group - 1) / (r.block * r.group);
     // Bus tiles trail by 4/3 of the states the resident CTAs can hold in branch work, plus two,
     // and the ring holds three lags: bus tiles then seldom wait for branch tiles, nor branch
@@ -347,9 +380,6 @@ Resolved resolve(exago_net *net, int B) {
     if (ring > B + 1) ring = B + 1 > lag ? B + 1 : lag + 1;
     r.lag = lag;
     r.ring = ring;
-    r.use_graph = c.use_graph != EXAGO_GRAPH_OFF;
-    r.spin_limit = c.spin_limit > 0 ? c.spin_limit : kDefaultSpinLimit;
-    r.force_timeout = c.test_force_timeout ? 1 : 0;
     return r;
 }
 
@@ -365,9 +395,15 @@ size_t persist_slot_bytes(const exago_net *net) {
     return slot_bytes(net) + (size_t)kObjLanes * sizeof(double);
 }
 
+// Ring scratch of a persistent launch: `ring` state slots, or group slots when warp-tiled.
+size_t persist_ring_bytes(const exago_net *net, const Resolved &r) {
+    if (r.warp_tiles) return round256(r.ring * persist_w_slot_doubles(net->dev.nslot) * sizeof(double));
+    return round256(r.ring * persist_slot_bytes(net));
+}
+
 // Workspace of the persistent schedule: ring scratch, then counters.
 size_t persist_bytes(const exago_net *net, const Resolved &r, int B) {
-    return round256(r.ring * persist_slot_bytes(net)) +
+    return persist_ring_bytes(net, r) +
            round256((size_t)(1 + 2 * (size_t)B + 256) * sizeof(int));
 }
 
@@ -623,7 +659,7 @@ exago_status eval_locked(exago_net *net, const exago_batch *bt, double *f, doubl
     }
     char *w = (char *)ws;
     R.scratch = (double *)w;
-    w += round256(rs.ring * persist_slot_bytes(net));
+    w += persist_ring_bytes(net, rs);
     PersistLaunch pl;
     pl.block = rs.block; pl.occ_warps = rs.occ_warps; pl.grid = rs.grid; pl.lag = rs.lag;
     pl.ring = rs.ring;
@@ -635,13 +671,18 @@ exago_status eval_locked(exago_net *net, const exago_batch *bt, double *f, doubl
         std::vector<uint64_t> key = req_key(R, EXAGO_SCHED_PERSISTENT);
         for (uint64_t v : {(uint64_t)pl.counters, (uint64_t)pl.block, (uint64_t)pl.grid,
                            (uint64_t)pl.lag, (uint64_t)pl.ring, (uint64_t)pl.spin_limit,
-                           (uint64_t)pl.occ_warps, (uint64_t)pl.force_timeout, (uint64_t)pl.group})
+                           (uint64_t)pl.occ_warps, (uint64_t)pl.force_timeout, (uint64_t)pl.group,
+                           (uint64_t)rs.warp_tiles})
             key.push_back(v);
         const DevNet &dn = net->dev;
+        if (rs.warp_tiles)
+            return launch_graph_locked(
+                net, key, [&](cudaStream_t cs) { return launch_eval_persistent_w(dn, R, pl, cs); }, stream);
         return launch_graph_locked(
             net, key, [&](cudaStream_t cs) { return launch_eval_persistent(dn, R, pl, cs); }, stream);
     }
-    int e = launch_eval_persistent(net->dev, R, pl, stream, hook);
+    int e = rs.warp_tiles ? launch_eval_persistent_w(net->dev, R, pl, stream, hook)
+                          : launch_eval_persistent(net->dev, R, pl, stream, hook);
     if (e != 0) return cuda_fail((cudaError_t)e, "persistent kernel launch");
     return EXAGO_OK;
 }
@@ -1057,6 +1098,12 @@ exago_status exago_net_set_config(exago_net_t net, const exago_config *cfg) {
         return fail(EXAGO_EINVAL, "tile_group must be 0 to 4");
     if (cfg->schedule != EXAGO_SCHED_PIPELINED && cfg->ring > 0 && cfg->lag > 0 && cfg->ring <= cfg->lag)
         return fail(EXAGO_EINVAL, "ring must exceed lag");
+    if (cfg->tiling < EXAGO_TILING_DEFAULT || cfg->tiling > EXAGO_TILING_WARP)
+        return fail(EXAGO_EINVAL, "unknown tiling");
+    if (cfg->tiling == EXAGO_TILING_WARP && cfg->block != 0 && cfg->block != 64 && cfg->block != 128)
+        return fail(EXAGO_EINVAL, "warp tiling takes blocks of 64 or 128 threads");
+    if (cfg->tiling == EXAGO_TILING_WARP && cfg->occupancy == 24)
+        return fail(EXAGO_EINVAL, "warp tiling takes occupancy 0, 8 or 16");
     std::lock_guard<std::mutex> lk(net->mu);
     net->cfg = *cfg;
     return EXAGO_OK;
@@ -1077,6 +1124,7 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg) {
         cfg->ring = r.ring;
         cfg->use_graph = r.use_graph;
         cfg->tile_group = r.group;
+        cfg->tiling = r.warp_tiles ? EXAGO_TILING_WARP : EXAGO_TILING_THREAD;
     }
     if (r.schedule == EXAGO_SCHED_PIPELINED) {
         cfg->chunk = r.chunk;
@@ -1127,6 +1175,19 @@ exago_status exago_net_autotune(exago_net_t net, const exago_batch *bt, double *
                         cands.push_back(c);
                     }
         }
+        // warp-tiled persistent kernel: a warp per branch or bus, a lane per state
+        for (int block : {64, 128})
+            for (int occw : {8, 16})
+                for (int group : {1, 2}) {
+                    exago_config c{};
+                    c.schedule = EXAGO_SCHED_PERSISTENT;
+                    c.tiling = EXAGO_TILING_WARP;
+                    c.block = block;
+                    c.occupancy = occw;
+                    c.tile_group = group;
+                    c.use_graph = EXAGO_GRAPH_ON;
+                    cands.push_back(c);
+                }
     }
     cudaStream_t st = (cudaStream_t)bt->stream;
     cudaEvent_t e0, e1;

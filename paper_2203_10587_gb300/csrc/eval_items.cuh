@@ -255,16 +255,21 @@ __device__ __forceinline__ void store_hrow(double *Jrow, const End &e, bool self
     }
 }
 
-// Stores a pair of components of a record (16-byte aligned: records are 80 bytes).
+// Stores the pair of components (c, c + 1) of a record, c even.  PS: doubles between a record's
+// consecutive pairs -- 2 for a record of NCOMP consecutive doubles (16-byte aligned: records are
+// 80 bytes), 64 for the lane-interleaved records of the warp-tiled schedule (a slot's pair p of
+// 32 states is one 512-byte run, lane after lane).
+template <int PS = 2>
 __device__ __forceinline__ void put2(double *rec, int c, double a, double b) {
-    *reinterpret_cast<double2 *>(rec + c) = make_double2(a, b);
+    *reinterpret_cast<double2 *>(rec + (c / 2) * PS) = make_double2(a, b);
 }
 
-// One (state b, branch l) item.  scr is state b's record scratch ([nslot][NCOMP]).  The branch
-// writes its two h values and its two Jacobian h rows (four entries each, contiguous across a
-// warp), and the 80-byte record of each end at the end's slot; the bus phase assembles
+// One (state b, branch l) item.  scr is state b's record scratch ([nslot][NCOMP]), or with
+// LW = 32 (warp-tiled schedule) a group of 32 states' records ([nslot][NCOMP / 2][32][2]) offset
+// to the state's lane.  The branch writes its two h values and its two Jacobian h rows (four
+// entries each), and the record of each end at the end's slot; the bus phase assembles
 // everything else row by row.
-template <int WANT>
+template <int WANT, int LW = 1>
 __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, int b, int l,
                                             double *scr) {
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
@@ -275,8 +280,9 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     if (!EXAGO_DCHECK(N, l >= 0 && l < nl && sf >= 0 && sf < N.chk_nslot && sto >= 0 &&
                              sto < N.chk_nslot && fb >= 0 && fb < nb && tb >= 0 && tb < nb))
         return;
-    double *rf = scr + (size_t)sf * NCOMP;
-    double *rt = scr + (size_t)sto * NCOMP;
+    constexpr int PS = 2 * LW;                       // doubles between a record's pairs
+    double *rf = scr + (size_t)sf * (NCOMP * LW);
+    double *rt = scr + (size_t)sto * (NCOMP * LW);
     double *Jf = WJ ? st_jval(N, R, b) + N.nnzJg + 4 * (size_t)l : nullptr;
     double *Jt = WJ ? Jf + 4 * (size_t)nl : nullptr;
     double *ghb = R.gh ? st_gh(N, R, b) : nullptr;
@@ -287,8 +293,8 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
 #pragma unroll
         for (int e = 0; e < 2; e++) {
             double *r = e ? rt : rf;
-            if (WG || WJ) { put2(r, SC_PA, 0.0, 0.0); put2(r, SC_PV, 0.0, 0.0); put2(r, SC_QU, 0.0, 0.0); }
-            if (WH) { put2(r, SC_HAA, 0.0, 0.0); put2(r, SC_HUU, 0.0, 0.0); }
+            if (WG || WJ) { put2<PS>(r, SC_PA, 0.0, 0.0); put2<PS>(r, SC_PV, 0.0, 0.0); put2<PS>(r, SC_QU, 0.0, 0.0); }
+            if (WH) { put2<PS>(r, SC_HAA, 0.0, 0.0); put2<PS>(r, SC_HUU, 0.0, 0.0); }
         }
         if (WG && ghb) { ghb[2 * nb + l] = 0.0; ghb[2 * nb + nl + l] = 0.0; }
         if (WJ)
@@ -320,7 +326,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
         const End ef = end_terms<DERIV>(Gff, Bff, Gff2, Bff2, Af, Cf, Vf, Vt, Vf2, VV);
         if (WG && ghb) ghb[2 * nb + l] = fma(ef.P, ef.P, ef.Q * ef.Q);
         if (WG || WJ) {
-            put2(rf, SC_PA, ef.pa, ef.pu); put2(rf, SC_PV, ef.pv, ef.qa); put2(rf, SC_QU, ef.qu, ef.qv);
+            put2<PS>(rf, SC_PA, ef.pa, ef.pu); put2<PS>(rf, SC_PV, ef.pv, ef.qa); put2<PS>(rf, SC_QU, ef.qu, ef.qv);
         }
         if (WJ) store_hrow(Jf, ef, fb < tb);
         if (WH)
@@ -331,7 +337,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
         const End et = end_terms<DERIV>(Gtt, Btt, Gtt2, Btt2, At, Ct, Vt, Vf, Vt2, VV);
         if (WG && ghb) ghb[2 * nb + nl + l] = fma(et.P, et.P, et.Q * et.Q);
         if (WG || WJ) {
-            put2(rt, SC_PA, et.pa, et.pu); put2(rt, SC_PV, et.pv, et.qa); put2(rt, SC_QU, et.qu, et.qv);
+            put2<PS>(rt, SC_PA, et.pa, et.pu); put2<PS>(rt, SC_PV, et.pv, et.qa); put2<PS>(rt, SC_QU, et.qu, et.qv);
         }
         if (WJ) store_hrow(Jt, et, tb < fb);
         if (WH)
@@ -340,10 +346,10 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     }
     if (WH) {
         const BranchHess h = branch_hess(hf, ht, Vf, Vt, Vf2, Vt2, VV);
-        put2(rf, SC_HAA, h.haa, h.xf);                 // (Va_f,Va_f), (Vm_f, Va_f)
-        put2(rt, SC_HAA, h.haa, h.xt);                 // (Va_t,Va_t), (Vm_t, Va_t)
-        put2(rf, SC_HUU, h.mff, h.mft);
-        put2(rt, SC_HUU, h.mtt, h.mft);
+        put2<PS>(rf, SC_HAA, h.haa, h.xf);                 // (Va_f,Va_f), (Vm_f, Va_f)
+        put2<PS>(rt, SC_HAA, h.haa, h.xt);                 // (Va_t,Va_t), (Vm_t, Va_t)
+        put2<PS>(rf, SC_HUU, h.mff, h.mft);
+        put2<PS>(rt, SC_HUU, h.mtt, h.mft);
     }
 }
 
@@ -381,16 +387,17 @@ __device__ __forceinline__ double2 rec2(const double *p) {
     return ld2(p);
 }
 
-template <int WANT, bool SMEM>
+// PS: doubles between the record's pairs (put2).
+template <int WANT, bool SMEM, int PS = 2>
 __device__ __forceinline__ Rec load_rec(const double *rec) {
     Rec r{};
     if (WANT & (W_G | W_J)) {
-        const double2 a = rec2<SMEM>(rec + SC_PA), v = rec2<SMEM>(rec + SC_PV);
-        const double2 u = rec2<SMEM>(rec + SC_QU);
+        const double2 a = rec2<SMEM>(rec + SC_PA / 2 * PS), v = rec2<SMEM>(rec + SC_PV / 2 * PS);
+        const double2 u = rec2<SMEM>(rec + SC_QU / 2 * PS);
         r.pa = a.x; r.pu = a.y; r.pv = v.x; r.qa = v.y; r.qu = u.x; r.qv = u.y;
     }
     if (WANT & W_H) {
-        const double2 h1 = rec2<SMEM>(rec + SC_HAA), h2 = rec2<SMEM>(rec + SC_HUU);
+        const double2 h1 = rec2<SMEM>(rec + SC_HAA / 2 * PS), h2 = rec2<SMEM>(rec + SC_HUU / 2 * PS);
         r.haa = h1.x; r.hua = h1.y; r.huu = h2.x; r.huv = h2.y;
     }
     return r;
@@ -502,8 +509,9 @@ __device__ __forceinline__ void bus_tail(const DevNet &N, const EvalReq &R, int 
 // bus_tail.  Records come from the tile's shared-memory copy, or through L2 (ld.cg): in the
 // persistent schedule other CTAs wrote them during the launch.  recs + (s - sbase) * NCOMP is slot
 // s's record: the tile's shared-memory copy (SMEM) or state b's scratch in global memory
-// (sbase = 0).
-template <int WANT, bool SMEM>
+// (sbase = 0).  LW = 32: the warp-tiled schedule's lane-interleaved records (branch_item), recs
+// offset to the state's lane; every lane of a warp then walks the same bus.
+template <int WANT, bool SMEM, int LW = 1>
 __device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int b, int i,
                                          const double *recs, int sbase, const BusRows &W) {
     constexpr bool WJ = WANT & W_J, WH = WANT & W_H;
@@ -535,17 +543,17 @@ __device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int 
         }
         pos++;
     };
-    auto rec_of = [&](int s) { return recs + (size_t)(s - sbase) * NCOMP; };
+    auto rec_of = [&](int s) { return recs + (size_t)(s - sbase) * (NCOMP * LW); };
     int s = s0;
     if (s < s1) {
         int j = __ldg(N.slot_nbr + s);
-        Rec o = load_rec<WANT, SMEM>(rec_of(s));
+        Rec o = load_rec<WANT, SMEM, 2 * LW>(rec_of(s));
         D = o;
         for (;;) {
             s++;
             int jn = s < s1 ? __ldg(N.slot_nbr + s) : -1;
             while (jn == j) {                                 // parallel branch to the same bus
-                const Rec p = load_rec<WANT, SMEM>(rec_of(s));
+                const Rec p = load_rec<WANT, SMEM, 2 * LW>(rec_of(s));
                 add_group<WANT>(o, p);
                 add_diag<WANT>(D, p);
                 s++;
@@ -554,7 +562,7 @@ __device__ __forceinline__ void bus_item(const DevNet &N, const EvalReq &R, int 
             emit(j, o);
             if (s >= s1) break;
             j = jn;
-            o = load_rec<WANT, SMEM>(rec_of(s));
+            o = load_rec<WANT, SMEM, 2 * LW>(rec_of(s));
             add_diag<WANT>(D, o);
         }
     }

@@ -216,6 +216,12 @@ struct PersistLaunch {
 int launch_eval_persistent(const DevNet &net, const EvalReq &req, const PersistLaunch &pl,
                            void *stream, ProfileHook *hook = nullptr);
 int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes);
+// Warp-tiled persistent schedule (persist_warp.cu): a warp takes one branch or bus, its lanes 32
+// states.  pl.block is 64 or 128; pl.lag and pl.ring count groups of 32 states; req.scratch holds
+// `ring` group slots (persist_w_slot_doubles each); occ_warps 8 or 16.
+int launch_eval_persistent_w(const DevNet &net, const EvalReq &req, const PersistLaunch &pl,
+                             void *stream, ProfileHook *hook = nullptr);
+int persist_w_blocks_per_sm(int block, int occ_warps);
 
 // Shared memory of a bus tile (eval_items.cuh, bus_tile): its records and its row segments.  The
 // largest tile's need in doubles, capped at kStageMaxDoubles; a tile above the cap reads its
@@ -225,6 +231,9 @@ constexpr int kStageMaxDoubles = 9216;   // 72 KB
 // then the kObjLanes partial sums of the state's objective (256 virtual lanes).
 constexpr int kObjLanes = 256;
 constexpr int kDiagComps = 7;            // record components summed into a bus's diagonal
+// One ring slot of the warp-tiled schedule: 32 states' lane-interleaved records, then their
+// objective partials.
+inline size_t persist_w_slot_doubles(int nslot) { return ((size_t)NCOMP * nslot + kObjLanes) * 32; }
 __host__ __device__ inline int stage_index(int block) {
     return block == 32 ? 0 : block == 64 ? 1 : block == 256 ? 3 : 2;
 }

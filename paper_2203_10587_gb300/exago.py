@@ -52,6 +52,7 @@ EXPORTS = [
 SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
 GRAPH_DEFAULT, GRAPH_ON, GRAPH_OFF = 0, 1, 2
 STAGE_DEFAULT, STAGE_ON, STAGE_OFF = 0, 1, 2
+TILING_DEFAULT, TILING_THREAD, TILING_WARP = 0, 1, 2
 
 
 class ExagoError(RuntimeError):
@@ -66,7 +67,7 @@ class exago_config(ctypes.Structure):
                 ("occupancy", ctypes.c_int), ("stage_records", ctypes.c_int), ("lag", ctypes.c_int),
                 ("ring", ctypes.c_int), ("chunk", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("spin_limit", ctypes.c_longlong), ("test_force_timeout", ctypes.c_int),
-                ("tile_group", ctypes.c_int)]
+                ("tile_group", ctypes.c_int), ("tiling", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -396,9 +397,10 @@ def exago_eval_profile(h, batch: exago_batch, f=None, grad=None, gh=None, jval=N
 
 
 def exago_net_set_config(h, schedule=0, block=0, occupancy=0, stage_records=0, lag=0, ring=0,
-                         chunk=0, use_graph=0, spin_limit=0, test_force_timeout=0, tile_group=0):
+                         chunk=0, use_graph=0, spin_limit=0, test_force_timeout=0, tile_group=0,
+                         tiling=0):
     c = exago_config(schedule, block, occupancy, stage_records, lag, ring, chunk, use_graph,
-                     spin_limit, test_force_timeout, tile_group)
+                     spin_limit, test_force_timeout, tile_group, tiling)
     _check(lib().exago_net_set_config(h, ctypes.byref(c)))
 
 

@@ -40,6 +40,9 @@ CONFIGS = [
     dict(schedule=3, chunk=7, ring=2, stage_records=1), # ring reuse from the third chunk on
     dict(schedule=3, chunk=5, use_graph=2),             # direct launches
     dict(schedule=1, stage_records=1),
+    dict(schedule=2, tiling=2),                         # warp tiles: a warp per branch / bus
+    dict(schedule=2, tiling=2, block=128, occupancy=8, tile_group=2),
+    dict(schedule=2, tiling=2, lag=1, ring=2, use_graph=2),
 ]
 
 
