@@ -97,6 +97,7 @@ struct exago_net {
     cudaStream_t side_stream = nullptr;   // pipelined schedule: bus kernels
     cudaEvent_t pipe_ev[18] = {};
     std::map<uint64_t, int> occ;  // resident CTAs per SM by (schedule, block, occupancy, shared memory)
+    std::map<int, int> item_rows; // warp tiles: most row doubles of one bus item, by buses per item
 };
 
 namespace {
@@ -232,6 +233,7 @@ exago_status do_upload(exago_net *net) {
             int le2 = persist_allow_stage();
             if (le2 == 0) le2 = bus_allow_stage();
             if (le2 == 0) le2 = cart_allow_stage();
+            if (le2 == 0) le2 = persist_w_allow_stage();
             if (le2 != 0) return cuda_fail((cudaError_t)le2, "cudaFuncSetAttribute");
             done[net->device] = true;
         }
@@ -282,14 +284,14 @@ constexpr long long kDefaultSpinLimit = 1ll << 22;   // polls of ~0.4 us: about 
 
 // Resident CTAs per SM of the persistent kernel (persistent) or of the bus kernel (otherwise)
 // with `smem` bytes of dynamic shared memory, cached.
-// warp: the warp-tiled persistent kernel (no dynamic shared memory).
+// warp: the warp-tiled persistent kernel (smem: its lanes' staging row in doubles).
 int occupancy(exago_net *net, bool persistent, int block, int occ_warps, size_t smem,
               bool warp = false) {
     const uint64_t key = ((uint64_t)persistent << 62) | ((uint64_t)warp << 61) |
                          ((uint64_t)block << 48) | ((uint64_t)occ_warps << 40) | (uint64_t)smem;
     auto it = net->occ.find(key);
     if (it != net->occ.end()) return it->second;
-    const int o = warp         ? persist_w_blocks_per_sm(block, occ_warps)
+    const int o = warp         ? persist_w_blocks_per_sm(block, occ_warps, (int)smem)
                   : persistent ? persist_blocks_per_sm(block, occ_warps, smem)
                                : bus_blocks_per_sm(smem);
     net->occ[key] = o;
@@ -306,6 +308,26 @@ int stage_cap(exago_net *net, bool persistent, int block, int occ_warps, bool st
     const long budget = ((long)net->smem_per_sm / (by_regs > 0 ? by_regs : 1) - 4096) / 8;
     const int want = stage_recs ? net->dev.stage_cap_all[t] : net->dev.stage_cap_rows[t];
     return want > budget ? (int)(budget & ~1l) : want;
+}
+
+// The most row doubles (J rows P and Q, H rows Va and Vm) that one bus item of per_item
+// consecutive buses writes, cached per per_item.
+int item_rows_max(exago_net *net, int per_item) {
+    auto it = net->item_rows.find(per_item);
+    if (it != net->item_rows.end()) return it->second;
+    const HostPlan &p = net->plan;
+    const DevNet &d = net->dev;
+    auto at = [&](const std::vector<int> &v, int i, int end) { return i < p.nb ? v[i] : end; };
+    int mx = 0;
+    for (int i0 = 0; i0 < p.nb; i0 += per_item) {
+        const int i1 = std::min(p.nb, i0 + per_item);
+        const int L = 2 * (at(p.bus_jP, i1, d.jP_end) - p.bus_jP[i0]) +
+                      (at(p.bus_hA, i1, d.hA_end) - p.bus_hA[i0]) +
+                      (at(p.bus_hM, i1, d.hM_end) - p.bus_hM[i0]);
+        mx = std::max(mx, L);
+    }
+    net->item_rows[per_item] = mx;
+    return mx;
 }
 
 Resolved resolve(exago_net *net, int B) {
@@ -349,10 +371,21 @@ Resolved resolve(exago_net *net, int B) {
         r.block = c.block == 128 ? 128 : 64;
         r.occ_warps = c.occupancy == 8 ? 8 : 16;
         r.stage_recs = 0;
-        r.stage_cap = 0;
-        r.grid = net->sm_count * occupancy(net, true, r.block, r.occ_warps, 0, true);
         const int G = (B + 31) / 32;
         const int per_item = (r.block / 32) * r.group;
+        // Each lane stages its state's rows of one item in shared memory (odd row length: no bank
+        // conflicts when the lanes write one position each): the longest bus item's rows, and the
+        // branch items' 10 doubles per branch, within what keeps the register-limited residency.
+        const int by_regs = occupancy(net, true, r.block, r.occ_warps, 0, true);
+        const long budget = ((long)net->smem_per_sm / (by_regs > 0 ? by_regs : 1) - 1024) / (8 * 32);
+        int want = item_rows_max(net, per_item);
+        if (want < 10 * per_item) want = 10 * per_item;
+        want |= 1;
+        const int cap = (kStageMaxDoubles / 32 - 1) | 1;
+        if (want > cap) want = cap;
+        r.stage_cap = want <= budget ? want : (int)((budget - 1) | 1);
+        if (r.stage_cap < 10 * per_item) r.stage_cap = 0;   // no staging at all
+        r.grid = net->sm_count * occupancy(net, true, r.block, r.occ_warps, r.stage_cap, true);
         const int Tbr = (net->plan.nl + per_item - 1) / per_item;
         int lag = c.lag > 0 ? c.lag : (Tbr > 0 ? (r.grid + Tbr - 1) / Tbr : 1) + 1;
         if (lag > G) lag = G;

@@ -264,6 +264,13 @@ __device__ __forceinline__ void put2(double *rec, int c, double a, double b) {
     *reinterpret_cast<double2 *>(rec + (c / 2) * PS) = make_double2(a, b);
 }
 
+// Where a branch item writes its two Jacobian h rows (four entries each) and its two h values
+// instead of the state's J and g | h rows (the warp-tiled schedule's shared-memory staging); all
+// null: the state's rows.
+struct BranchOut {
+    double *Jf = nullptr, *Jt = nullptr, *hf = nullptr, *ht = nullptr;
+};
+
 // One (state b, branch l) item.  scr is state b's record scratch ([nslot][NCOMP]), or with
 // LW = 32 (warp-tiled schedule) a group of 32 states' records ([nslot][NCOMP / 2][32][2]) offset
 // to the state's lane.  The branch writes its two h values and its two Jacobian h rows (four
@@ -271,7 +278,7 @@ __device__ __forceinline__ void put2(double *rec, int c, double a, double b) {
 // everything else row by row.
 template <int WANT, int LW = 1>
 __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, int b, int l,
-                                            double *scr) {
+                                            double *scr, const BranchOut &O = BranchOut{}) {
     constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     constexpr bool DERIV = WG || WJ || WH;   // the bus balances come from derivative sums
     const int nb = N.nb, nl = N.nl;
@@ -283,9 +290,11 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     constexpr int PS = 2 * LW;                       // doubles between a record's pairs
     double *rf = scr + (size_t)sf * (NCOMP * LW);
     double *rt = scr + (size_t)sto * (NCOMP * LW);
-    double *Jf = WJ ? st_jval(N, R, b) + N.nnzJg + 4 * (size_t)l : nullptr;
-    double *Jt = WJ ? Jf + 4 * (size_t)nl : nullptr;
+    double *Jf = WJ ? (O.Jf ? O.Jf : st_jval(N, R, b) + N.nnzJg + 4 * (size_t)l) : nullptr;
+    double *Jt = WJ ? (O.Jt ? O.Jt : st_jval(N, R, b) + N.nnzJg + 4 * (size_t)(nl + l)) : nullptr;
     double *ghb = R.gh ? st_gh(N, R, b) : nullptr;
+    double *hrf = O.hf ? O.hf : ghb ? ghb + 2 * nb + l : nullptr;       // h rows of the ends
+    double *hrt = O.ht ? O.ht : ghb ? ghb + 2 * nb + nl + l : nullptr;
 
     const uint8_t *mk = st_mask(N, R, b);
     const bool on = mk == nullptr || mk[l] != 0;
@@ -296,7 +305,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
             if (WG || WJ) { put2<PS>(r, SC_PA, 0.0, 0.0); put2<PS>(r, SC_PV, 0.0, 0.0); put2<PS>(r, SC_QU, 0.0, 0.0); }
             if (WH) { put2<PS>(r, SC_HAA, 0.0, 0.0); put2<PS>(r, SC_HUU, 0.0, 0.0); }
         }
-        if (WG && ghb) { ghb[2 * nb + l] = 0.0; ghb[2 * nb + nl + l] = 0.0; }
+        if (WG && ghb) { *hrf = 0.0; *hrt = 0.0; }
         if (WJ)
             for (int k = 0; k < 4; k++) { Jf[k] = 0.0; Jt[k] = 0.0; }
         return;
@@ -324,7 +333,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     EndHess hf{}, ht{};
     {
         const End ef = end_terms<DERIV>(Gff, Bff, Gff2, Bff2, Af, Cf, Vf, Vt, Vf2, VV);
-        if (WG && ghb) ghb[2 * nb + l] = fma(ef.P, ef.P, ef.Q * ef.Q);
+        if (WG && ghb) *hrf = fma(ef.P, ef.P, ef.Q * ef.Q);
         if (WG || WJ) {
             put2<PS>(rf, SC_PA, ef.pa, ef.pu); put2<PS>(rf, SC_PV, ef.pv, ef.qa); put2<PS>(rf, SC_QU, ef.qu, ef.qv);
         }
@@ -335,7 +344,7 @@ __device__ __forceinline__ void branch_item(const DevNet &N, const EvalReq &R, i
     }
     {
         const End et = end_terms<DERIV>(Gtt, Btt, Gtt2, Btt2, At, Ct, Vt, Vf, Vt2, VV);
-        if (WG && ghb) ghb[2 * nb + nl + l] = fma(et.P, et.P, et.Q * et.Q);
+        if (WG && ghb) *hrt = fma(et.P, et.P, et.Q * et.Q);
         if (WG || WJ) {
             put2<PS>(rt, SC_PA, et.pa, et.pu); put2<PS>(rt, SC_PV, et.pv, et.qa); put2<PS>(rt, SC_QU, et.qu, et.qv);
         }

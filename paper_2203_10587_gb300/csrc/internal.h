@@ -218,10 +218,12 @@ int launch_eval_persistent(const DevNet &net, const EvalReq &req, const PersistL
 int persist_blocks_per_sm(int block, int occ_warps, size_t smem_bytes);
 // Warp-tiled persistent schedule (persist_warp.cu): a warp takes one branch or bus, its lanes 32
 // states.  pl.block is 64 or 128; pl.lag and pl.ring count groups of 32 states; req.scratch holds
-// `ring` group slots (persist_w_slot_doubles each); occ_warps 8 or 16.
+// `ring` group slots (persist_w_slot_doubles each); occ_warps 8 or 16; req.stage_cap is the
+// doubles of one lane's shared-memory staging row (odd, at most kStageMaxDoubles / 32; 0 = none).
 int launch_eval_persistent_w(const DevNet &net, const EvalReq &req, const PersistLaunch &pl,
                              void *stream, ProfileHook *hook = nullptr);
-int persist_w_blocks_per_sm(int block, int occ_warps);
+int persist_w_blocks_per_sm(int block, int occ_warps, int stage_cap);
+int persist_w_allow_stage();
 
 // Shared memory of a bus tile (eval_items.cuh, bus_tile): its records and its row segments.  The
 // largest tile's need in doubles, capped at kStageMaxDoubles; a tile above the cap reads its

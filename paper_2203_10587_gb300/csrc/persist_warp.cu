@@ -8,9 +8,17 @@
 
 namespace exago {
 
-int persist_w_blocks_per_sm(int block, int occ_warps) {
-    if (block == 128) return occupancy_w_nt<128, 0>(occ_warps);
-    return occupancy_w_nt<64, 0>(occ_warps);
+int persist_w_blocks_per_sm(int block, int occ_warps, int stage_cap) {
+    const size_t smem = persist_w_smem(stage_cap);
+    if (block == 128) return occupancy_w_nt<128, 0>(occ_warps, smem);
+    return occupancy_w_nt<64, 0>(occ_warps, smem);
+}
+
+int persist_w_allow_stage() {
+    int e = allow_stage_w_nt<64, 0>();
+    if (e == 0) e = allow_stage_w_nt<128, 0>();
+    if (e == 0) e = persist_w_allow_stage_gm();
+    return e;
 }
 
 int launch_eval_persistent_w(const DevNet &N, const EvalReq &R, const PersistLaunch &L,

@@ -57,8 +57,8 @@ __device__ __forceinline__ void obj_chunk_w(const DevNet &N, const EvalReq &R, i
 
 // obj_block's pairwise tree over the 256 partials of the lane's state (part[v * 32 + lane],
 // written by other CTAs of the launch: read through L2): levels 128, 64 and 32 as in
-// obj_tree_warp, the 32 results in tree[v * 32 + lane] (shared memory), then levels 16 .. 1
-// there.  Writes f of state b.
+// obj_tree_warp, the 32 results in tree[v * 32 + lane] (shared memory, 1024 doubles), then
+// levels 16 .. 1 there.  Writes f of state b.
 __device__ __forceinline__ void obj_tree_w(const EvalReq &R, int b, const double *part,
                                            double *tree, int lane) {
     for (int v = 0; v < 32; v++) {
@@ -93,19 +93,44 @@ __device__ __forceinline__ BusRows rows_w(const DevNet &N, const EvalReq &R, int
     return W;
 }
 
-// P.B is the number of groups here; R.B the number of states.
+// Copies the staged rows of the item's live states out of shared memory: state s (lane s) has
+// `len` doubles at stage[s * lstr ..], of which [0, n0) go to dst0 + e, then n1 to dst1, n2 to
+// dst2 and the rest to dst3 (each dstk(s) a row of state s).  Warp w takes states w, w + NW, ...,
+// its lanes consecutive doubles of one state's segments.
+template <int NW, class Dst>
+__device__ __forceinline__ void copy_out_w(const double *stage, int lstr, int nlive, int len,
+                                           int n0, int n1, int n2, const Dst &dst, int wid,
+                                           int lane) {
+    for (int s = wid; s < nlive; s += NW) {
+        const double *src = stage + (size_t)s * lstr;
+        for (int e = lane; e < len; e += 32) {
+            const double v = src[e];
+            if (e < n0) *(dst(s, 0) + e) = v;
+            else if (e < n0 + n1) *(dst(s, 1) + (e - n0)) = v;
+            else if (e < n0 + n1 + n2) *(dst(s, 2) + (e - n0 - n1)) = v;
+            else *(dst(s, 3) + (e - n0 - n1 - n2)) = v;
+        }
+    }
+}
+
+// P.B is the number of groups here; R.B the number of states.  R.stage_cap: doubles of one
+// lane's staging row (odd; 0 = no staging); the dynamic shared memory holds 32 such rows, and
+// at least the 1024 doubles of the objective tree.
 template <int WANT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_persist_w(const DevNet N, const EvalReq R,
                                                         const PersistParams P) {
     static_assert(NT % 32 == 0 && NT >= 32, "whole warps");
     constexpr int NW = NT / 32;                                  // warps: branches per tile
     constexpr bool GM = (WANT & W_GM) != 0;
+    constexpr bool WG = WANT & W_G, WJ = WANT & W_J, WH = WANT & W_H;
     __shared__ int s_item, s_ok;
-    __shared__ double s_tree[32 * kLanes];
+    extern __shared__ double wstage[];
     int *done_br = P.ctr + 1, *done_bu = P.ctr + 1 + P.B;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const size_t rec_doubles = (size_t)NCOMP * N.nslot * kLanes;
     const size_t slot_doubles = rec_doubles + (size_t)kObjLanes * kLanes;
+    const int lstr = R.stage_cap;
+    double *myrow = wstage + (size_t)lane * lstr;                // this lane's staging row
     // claiming as in k_persist: thread 0 claims the next ticket while the block works
     int next = 0;
     phase_mark(P.times, PH_ENTRY);
@@ -133,7 +158,7 @@ __global__ void __launch_bounds__(NT, MINB) k_persist_w(const DevNet N, const Ev
                 if (next < P.total) next = atomicAdd(P.ctr, 1);
             }
         }
-        __syncthreads();
+        __syncthreads();   // also: the previous item's staged rows are copied out
         const int t = s_item;
         if (t >= P.total) {
             phase_mark(P.times, PH_EXIT);
@@ -144,6 +169,7 @@ __global__ void __launch_bounds__(NT, MINB) k_persist_w(const DevNet N, const Ev
         decode_item(P, t, &is_branch, &g, &tile);
         const int b = g * kLanes + lane;                         // this lane's state
         const bool live = b < R.B;
+        const int nlive = min(kLanes, R.B - g * kLanes);
         double *scr = R.scratch + (size_t)(g % P.ring) * slot_doubles;
         const int per_item = P.group * NW;                       // branches (buses) per item
         if (is_branch) {
@@ -152,6 +178,9 @@ __global__ void __launch_bounds__(NT, MINB) k_persist_w(const DevNet N, const Ev
                                                   N.status, ST_TIMEOUT_RING);
             __syncthreads();
             phase_mark(P.times, PH_BR_START);
+            const int l0 = tile * per_item, cnt = min(N.nl, l0 + per_item) - l0;
+            // the item's h rows, staged per lane as [J from rows | J to rows | h from | h to]
+            const bool staged = (WJ || (WG && R.gh)) && 10 * per_item <= lstr;
             if (s_ok && live) {
                 if (R.f) {
                     // obj_block's 256 virtual lanes in 8 chunks of 32; chunk c by warp c mod
@@ -163,25 +192,79 @@ __global__ void __launch_bounds__(NT, MINB) k_persist_w(const DevNet N, const Ev
                 }
                 for (int k = 0; k < P.group; k++) {
                     const int l = (tile * P.group + k) * NW + wid;
-                    if (l < N.nl) branch_item<WANT, kLanes>(N, R, b, l, scr + 2 * lane);
+                    if (l >= N.nl) continue;
+                    BranchOut O{};
+                    if (staged) {
+                        const int q = l - l0;
+                        O.Jf = myrow + 4 * q;
+                        O.Jt = myrow + 4 * per_item + 4 * q;
+                        O.hf = myrow + 8 * per_item + q;
+                        O.ht = myrow + 9 * per_item + q;
+                    }
+                    branch_item<WANT, kLanes>(N, R, b, l, scr + 2 * lane, O);
                 }
             }
             __syncthreads();
             if (threadIdx.x == 0) red_release_add(done_br + g);
             phase_mark(P.times, PH_BR_END);
+            if (staged && s_ok) {
+                // rows of one lane: [4 cnt J from][4 cnt J to][cnt h from][cnt h to], compacted
+                // from the per_item-strided staging layout by the index map below
+                const int nj = WJ ? 4 * cnt : 0, nh = (WG && R.gh) ? cnt : 0;
+                const int gbase = g * kLanes;
+                for (int s = wid; s < nlive; s += NW) {
+                    const double *src = wstage + (size_t)s * lstr;
+                    for (int e = lane; e < 2 * nj + 2 * nh; e += 32) {
+                        double *dst;
+                        double v;
+                        if (e < nj) {
+                            v = src[e];
+                            dst = st_jval(N, R, gbase + s) + N.nnzJg + 4 * (size_t)l0 + e;
+                        } else if (e < 2 * nj) {
+                            v = src[4 * per_item + (e - nj)];
+                            dst = st_jval(N, R, gbase + s) + N.nnzJg + 4 * (size_t)(N.nl + l0) + (e - nj);
+                        } else if (e < 2 * nj + nh) {
+                            v = src[8 * per_item + (e - 2 * nj)];
+                            dst = st_gh(N, R, gbase + s) + 2 * N.nb + l0 + (e - 2 * nj);
+                        } else {
+                            v = src[9 * per_item + (e - 2 * nj - nh)];
+                            dst = st_gh(N, R, gbase + s) + 2 * N.nb + N.nl + l0 + (e - 2 * nj - nh);
+                        }
+                        *dst = v;
+                    }
+                }
+            }
         } else {
             if (threadIdx.x == 0)
                 s_ok = bounded_wait(done_br + g, P.Tbr + P.force_timeout, P.spin_limit, N.status,
                                     ST_TIMEOUT_BUS);
             __syncthreads();
             phase_mark(P.times, PH_BU_START);
+            const int i0 = tile * per_item, i1 = min(N.nb, i0 + per_item);
+            const int nb = N.nb;
+            const int p0 = row_start(N.bus_jP, i0, nb, N.jP_end), p1 = row_start(N.bus_jP, i1, nb, N.jP_end);
+            const int q0 = row_start(N.bus_jQ, i0, nb, N.jQ_end);
+            const int a0 = row_start(N.bus_hA, i0, nb, N.hA_end), a1 = row_start(N.bus_hA, i1, nb, N.hA_end);
+            const int m0 = row_start(N.bus_hM, i0, nb, N.hM_end), m1 = row_start(N.bus_hM, i1, nb, N.hM_end);
+            const int LP = WJ ? p1 - p0 : 0, LA = WH ? a1 - a0 : 0, LM = WH ? m1 - m0 : 0;
+            const int LROWS = 2 * LP + LA + LM;
+            const bool staged = (WJ || WH) && LROWS <= lstr;
             if (s_ok && live) {
                 for (int k = 0; k < P.group; k++) {
                     const int i = (tile * P.group + k) * NW + wid;
                     if (i >= N.nb) break;
-                    if (WANT & (W_G | W_J | W_H))
-                        bus_item<WANT, false, kLanes>(N, R, b, i, scr + 2 * lane, 0,
-                                                      rows_w<WANT>(N, R, b, i));
+                    if (WANT & (W_G | W_J | W_H)) {
+                        BusRows W;
+                        if (staged) {
+                            W.JP = myrow + (__ldg(N.bus_jP + i) - p0);
+                            W.JQ = myrow + LP + (__ldg(N.bus_jQ + i) - q0);
+                            W.HA = myrow + 2 * LP + (__ldg(N.bus_hA + i) - a0);
+                            W.HM = myrow + 2 * LP + LA + (__ldg(N.bus_hM + i) - m0);
+                        } else {
+                            W = rows_w<WANT>(N, R, b, i);
+                        }
+                        bus_item<WANT, false, kLanes>(N, R, b, i, scr + 2 * lane, 0, W);
+                    }
                     if (R.grad) grad_bus<GM>(N, R, b, i);
                 }
             }
@@ -190,17 +273,29 @@ __global__ void __launch_bounds__(NT, MINB) k_persist_w(const DevNet N, const Ev
                     if (live)
                         for (int c = wid; c < OBJ_LANES / 32; c += NW)
                             obj_chunk_w<GM>(N, R, b, c, scr + rec_doubles, lane);
-                    __syncthreads();
                 }
-                if (wid == 0 && live) obj_tree_w(R, b, scr + rec_doubles, s_tree, lane);
+            }
+            __syncthreads();
+            if (staged && s_ok) {
+                const int gbase = g * kLanes;
+                auto dst = [&](int s, int k) -> double * {
+                    return k == 0 ? st_jval(N, R, gbase + s) + p0
+                         : k == 1 ? st_jval(N, R, gbase + s) + q0
+                         : k == 2 ? st_hval(N, R, gbase + s) + a0
+                                  : st_hval(N, R, gbase + s) + m0;
+                };
+                copy_out_w<NW>(wstage, lstr, nlive, LROWS, LP, LP, LA, dst, wid, lane);
+            }
+            if (tile == 0 && R.f && s_ok) {
+                // the tree in the staging space, once the rows are out
+                if (staged) __syncthreads();
+                if (wid == 0 && live) obj_tree_w(R, b, scr + rec_doubles, wstage, lane);
                 phase_mark(P.times, PH_OBJ_END);
             }
             __syncthreads();
             phase_mark(P.times, PH_BU_END);
             if (threadIdx.x < 32) {
                 if (s_ok && (WANT & (W_G | W_J | W_H))) {   // this item's records are consumed
-                    const int i0 = tile * per_item;
-                    const int i1 = min(N.nb, (tile + 1) * per_item);
                     discard_lines(scr + (size_t)__ldg(N.slot_ptr + i0) * (NCOMP * kLanes),
                                   scr + (size_t)__ldg(N.slot_ptr + i1) * (NCOMP * kLanes), lane);
                     __syncwarp();   // the lanes' discards before lane 0's release
@@ -211,10 +306,17 @@ __global__ void __launch_bounds__(NT, MINB) k_persist_w(const DevNet N, const Ev
     }
 }
 
+// Dynamic shared memory of a launch: 32 staging rows of R.stage_cap doubles, and at least the
+// objective tree's 1024 doubles.
+inline size_t persist_w_smem(int stage_cap) {
+    const size_t d = (size_t)kLanes * (stage_cap > 0 ? stage_cap : 0);
+    return (d > 1024 ? d : 1024) * sizeof(double);
+}
+
 template <int WANT, int NT, int MINB>
 static void launch_one_w(const DevNet &N, const EvalReq &R, const PersistParams &P, int grid,
                          cudaStream_t st) {
-    k_persist_w<WANT, NT, MINB><<<grid, NT, 0, st>>>(N, R, P);
+    k_persist_w<WANT, NT, MINB><<<grid, NT, persist_w_smem(R.stage_cap), st>>>(N, R, P);
 }
 
 // Launches the warp-tiled variant for the requested outputs (plus X = 0 or W_GM | W_PS): all
@@ -240,17 +342,36 @@ static int launch_persist_w_nt(const DevNet &N, const EvalReq &R, const PersistP
 }
 
 template <int NT, int X>
-static int occupancy_w_nt(int occ_warps) {
+static int occupancy_w_nt(int occ_warps, size_t smem) {
     constexpr int ALL = W_G | W_J | W_H;
     int per_sm = 0;
     cudaError_t e = occ_warps == 16
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist_w<ALL | X, NT, minb(NT, 16)>, NT, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist_w<ALL | X, NT, 1>, NT, 0);
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist_w<ALL | X, NT, minb(NT, 16)>, NT, smem)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist_w<ALL | X, NT, 1>, NT, smem);
     return e == cudaSuccess && per_sm > 0 ? per_sm : 1;
+}
+
+// Opts every warp-tiled variant in to kStageMaxDoubles of dynamic shared memory.
+template <int NT, int X>
+static int allow_stage_w_nt() {
+    const int bytes = kStageMaxDoubles * (int)sizeof(double);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *k) {
+        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (r != cudaSuccess) e = r;
+    };
+    constexpr int ALL = W_G | W_J | W_H;
+    set((const void *)k_persist_w<X, NT, 1>); set((const void *)k_persist_w<W_G | X, NT, 1>);
+    set((const void *)k_persist_w<W_J | X, NT, 1>); set((const void *)k_persist_w<W_G | W_J | X, NT, 1>);
+    set((const void *)k_persist_w<W_H | X, NT, 1>); set((const void *)k_persist_w<W_G | W_H | X, NT, 1>);
+    set((const void *)k_persist_w<W_J | W_H | X, NT, 1>); set((const void *)k_persist_w<ALL | X, NT, 1>);
+    set((const void *)k_persist_w<ALL | X, NT, minb(NT, 16)>);
+    return (int)e;
 }
 
 // persist_warp_gm.cu: the variants with generator masks and phase shifters.
 int launch_persist_w_gm(int block, const DevNet &N, const EvalReq &R, const PersistParams &P,
                         int grid, int occ_warps, cudaStream_t st);
+int persist_w_allow_stage_gm();
 
 }  // namespace exago

@@ -13,4 +13,10 @@ int launch_persist_w_gm(int block, const DevNet &N, const EvalReq &R, const Pers
     return launch_persist_w_nt<64, W_GM | W_PS>(N, R, P, grid, occ_warps, st);
 }
 
+int persist_w_allow_stage_gm() {
+    int e = allow_stage_w_nt<64, W_GM | W_PS>();
+    if (e == 0) e = allow_stage_w_nt<128, W_GM | W_PS>();
+    return e;
+}
+
 }  // namespace exago
