@@ -343,7 +343,8 @@ def time_calls(torch, fn, reps, warm=3):
 
 def run_other_configs(exago, synth, torch, np, dev):
     """The other workloads: a 10,000-bus grid evaluated 1,000 times in sequence (one IPM run),
-    and 10,000 buses x 64 load scenarios with the adjoint products."""
+    10,000 buses x 64 load scenarios with the adjoint products, and a meshed 2,000-bus grid of
+    6,000 branches x 512 states under both tilings of the persistent schedule."""
     td = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     g = synth.grid_10k()
     net = exago.Net(g)
@@ -358,7 +359,8 @@ def run_other_configs(exago, synth, torch, np, dev):
     ms = time_calls(torch, lambda: net.eval_all(bt1, out1), 1000)
     res["10k_bus_single_x1000"] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms,
                                    "launch_config": {k: tuned1[k] for k in
-                                                     ("schedule", "block", "occupancy", "tile_group")}}
+                                                     ("schedule", "block", "occupancy", "tile_group",
+                                                      "tiling")}}
     # C4: 64 load scenarios, all outputs, then J^T v and (grad^2 L) u
     b = synth.scenario_batch(4, g, 64)
     x, lam, ps, w = (td(b.x, torch.float64), td(b.lam, torch.float64),
@@ -377,8 +379,32 @@ def run_other_configs(exago, synth, torch, np, dev):
     res["10k_bus_x64_scenarios"] = {"evals_per_s": 64e3 / ms, "ms_per_batch": ms,
                                     "jtv_per_s": 64e3 / ms_jtv, "hvp_per_s": 64e3 / ms_hvp,
                                     "launch_config": {k: tuned[k] for k in
-                                                      ("schedule", "block", "occupancy", "tile_group")}}
+                                                      ("schedule", "block", "occupancy", "tile_group",
+                                                       "tiling")}}
     net.close()
+    # a meshed grid (2,000 buses, 6,000 branches: mean degree 6, up to 16) x 512 states: the bus
+    # degrees within a warp vary more, which the branch-per-warp tiling does not mind
+    gd = synth.make_grid(7, 2000, 6000, 500, max_degree=32)
+    bd = synth.random_batch(8, gd, 512, masks=True, sigma=0.02)
+    netd = exago.Net(gd)
+    btd = exago.make_batch(td(bd.x, torch.float64), td(bd.lam, torch.float64), td(bd.mask, torch.uint8))
+    outd = netd.outputs(512, dev)
+    exago.exago_net_reserve(netd.h, 512)
+    tunedd = exago.exago_net_autotune(netd.h, btd, outd["f"], outd["grad"], outd["gh"],
+                                      outd["jval"], outd["hval"], reps=5)
+    ms_tuned = time_calls(torch, lambda: netd.eval_all(btd, outd), 100)
+    timed = {}
+    for name, cfg in (("branch_per_thread", dict(schedule=2, block=64, occupancy=16, tile_group=1)),
+                      ("branch_per_warp", dict(schedule=2, tiling=2, block=128, occupancy=16,
+                                               tile_group=1))):
+        exago.exago_net_set_config(netd.h, **cfg)
+        timed[name] = time_calls(torch, lambda: netd.eval_all(btd, outd), 100)
+    res["2000_bus_6000_branch_x512"] = {
+        "evals_per_s": 512e3 / ms_tuned, "ms_per_batch": ms_tuned,
+        "ms_per_batch_by_tiling": timed, "mean_degree": 2 * gd.nl / gd.nb,
+        "launch_config": {k: tunedd[k] for k in ("schedule", "block", "occupancy", "tile_group",
+                                                  "stage_records", "tiling")}}
+    netd.close()
     return res
 
 

@@ -37,6 +37,7 @@ def grid300():
     dict(schedule=1),                                                   # multi-kernel
     dict(schedule=1, stage_records=1),
     dict(schedule=3, chunk=2),                                          # pipelined
+    dict(schedule=2, tiling=2),                                         # branch per warp
 ])
 def test_eval_all_against_oracle(ex, oracle_mod, cfg):
     g = grid300()
