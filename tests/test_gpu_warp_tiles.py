@@ -69,6 +69,25 @@ def test_benchmark_batch_2000bus_x512(ex, oracle_mod):
         compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), "warp 2000x512")
 
 
+def test_meshed_grid_rows_beyond_the_staging_cap(ex, oracle_mod):
+    """A meshed grid (mean bus degree 10, up to about 20): some items' rows exceed the shared-
+    memory staging of either tiling and are written directly; both tilings still agree bit for
+    bit and with the oracle."""
+    g = synth.make_grid(261, 400, 2000, 100, max_degree=64, shunts=True)
+    b = synth.random_batch(262, g, 40, masks=True, pd_scale=True, sigma=0.8)
+    net = ex.Net(g)
+    ex.exago_net_set_config(net.h, schedule=2)
+    ref = gpu_eval(net, b)
+    for cfg in (dict(schedule=2, tiling=WARP, block=128, tile_group=2),
+                dict(schedule=2, tiling=WARP, block=64), dict(schedule=1)):
+        ex.exago_net_set_config(net.h, **cfg)
+        out = gpu_eval(net, b)
+        for k in ref:
+            np.testing.assert_array_equal(out[k], ref[k], err_msg=f"{cfg} {k}")
+    for i in (0, 31, 39):
+        compare_instance(ref, i, oracle_eval(oracle_mod, g, b, i), "warp meshed")
+
+
 def test_generator_outages_and_phase_shifters(ex, oracle_mod):
     """The general variant (generator masks, phase-shifting transformers)."""
     g = synth.make_grid(211, 300, 390, 75, transformer_frac=0.1, shunts=True, shifter_frac=0.2)
