@@ -458,8 +458,8 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *   tiling    persistent: EXAGO_TILING_DEFAULT / THREAD: branch per thread -- each thread of a
  *             tile takes its own branch (bus) of one state.  EXAGO_TILING_WARP: branch per warp
  *             -- each warp takes one branch (bus) and its 32 lanes take 32 consecutive states,
- *             so every lane of a warp walks a bus of the same degree; blocks of 64 or 128
- *             threads, occupancy 8 or 16, tile_group branches (buses) per warp and work item,
+ *             so every lane of a warp walks a bus of the same degree; blocks of 128 (0 = 128)
+ *             or 64 threads, occupancy 8 or 16, tile_group branches (buses) per warp and work item,
  *             no record staging, and lag and ring count groups of 32 states (a ring slot then
  *             holds 32 states' records, so exago_eval_workspace_size grows accordingly).  Both
  *             tilings give bitwise equal outputs.  The power-balance-cartesian calls ignore it.

@@ -363,12 +363,13 @@ Resolved resolve(exago_net *net, int B) {
     r.force_timeout = c.test_force_timeout ? 1 : 0;
     r.group = c.tile_group >= 1 && c.tile_group <= 4 ? c.tile_group : 1;
     if (pers && c.tiling == EXAGO_TILING_WARP) {
-        // warp-tiled: blocks of 64 or 128 threads, no shared-memory staging; the lag and the ring
-        // count groups of 32 states.  By default bus items trail by the groups the resident CTAs
-        // hold in branch work plus one, and the ring holds two more groups (a group's records are
-        // 32 x 80 bytes per branch end, so a few groups already fill a good part of L2).
+        // warp-tiled: blocks of 128 (default) or 64 threads, no record staging; the lag and the
+        // ring count groups of 32 states.  By default bus items trail by the groups the resident
+        // CTAs hold in branch work plus two, and the ring holds two lags (measured on 2000 buses
+        // x 512, 128 threads: lag 3 and ring 6 take 0.469 ms, as do larger lags and rings up to
+        // 6 / 12; lag 2 and ring 4 0.502 ms; lag 2 and ring 3 0.755 ms).
         r.warp_tiles = 1;
-        r.block = c.block == 128 ? 128 : 64;
+        r.block = c.block == 64 ? 64 : 128;
         r.occ_warps = c.occupancy == 8 ? 8 : 16;
         r.stage_recs = 0;
         const int G = (B + 31) / 32;
@@ -387,10 +388,10 @@ Resolved resolve(exago_net *net, int B) {
         if (r.stage_cap < 10 * per_item) r.stage_cap = 0;   // no staging at all
         r.grid = net->sm_count * occupancy(net, true, r.block, r.occ_warps, r.stage_cap, true);
         const int Tbr = (net->plan.nl + per_item - 1) / per_item;
-        int lag = c.lag > 0 ? c.lag : (Tbr > 0 ? (r.grid + Tbr - 1) / Tbr : 1) + 1;
+        int lag = c.lag > 0 ? c.lag : (Tbr > 0 ? (r.grid + Tbr - 1) / Tbr : 1) + 2;
         if (lag > G) lag = G;
         if (lag < 1) lag = 1;
-        int ring = c.ring > 0 ? c.ring : lag + 2;
+        int ring = c.ring > 0 ? c.ring : 2 * lag;
         if (ring <= lag) ring = lag + 1;
         if (ring > G + 1) ring = G + 1 > lag ? G + 1 : lag + 1;
         r.lag = lag;

@@ -94,21 +94,22 @@ __device__ __forceinline__ BusRows rows_w(const DevNet &N, const EvalReq &R, int
 }
 
 // Copies the staged rows of the item's live states out of shared memory: state s (lane s) has
-// `len` doubles at stage[s * lstr ..], of which [0, n0) go to dst0 + e, then n1 to dst1, n2 to
-// dst2 and the rest to dst3 (each dstk(s) a row of state s).  Warp w takes states w, w + NW, ...,
-// its lanes consecutive doubles of one state's segments.
+// `len` doubles at stage[s * lstr ..], of which [0, n0) go to dst(s, 0) + e, then n1 to dst(s, 1),
+// n2 to dst(s, 2) and the rest to dst(s, 3) (each dst(s, k) a row segment of state s, offset so
+// that element e of the staging row lands at dst + e).  Warp w takes states w, w + NW, ..., its
+// lanes consecutive doubles of one state's segments.
 template <int NW, class Dst>
 __device__ __forceinline__ void copy_out_w(const double *stage, int lstr, int nlive, int len,
                                            int n0, int n1, int n2, const Dst &dst, int wid,
                                            int lane) {
+    const int e1 = n0, e2 = n0 + n1, e3 = n0 + n1 + n2;
     for (int s = wid; s < nlive; s += NW) {
         const double *src = stage + (size_t)s * lstr;
+        double *const d0 = dst(s, 0), *const d1 = dst(s, 1), *const d2 = dst(s, 2),
+                      *const d3 = dst(s, 3);
         for (int e = lane; e < len; e += 32) {
-            const double v = src[e];
-            if (e < n0) *(dst(s, 0) + e) = v;
-            else if (e < n0 + n1) *(dst(s, 1) + (e - n0)) = v;
-            else if (e < n0 + n1 + n2) *(dst(s, 2) + (e - n0 - n1)) = v;
-            else *(dst(s, 3) + (e - n0 - n1 - n2)) = v;
+            double *d = e < e1 ? d0 : e < e2 ? d1 : e < e3 ? d2 : d3;
+            d[e] = src[e];
         }
     }
 }
@@ -208,29 +209,23 @@ __global__ void __launch_bounds__(NT, MINB) k_persist_w(const DevNet N, const Ev
             if (threadIdx.x == 0) red_release_add(done_br + g);
             phase_mark(P.times, PH_BR_END);
             if (staged && s_ok) {
-                // rows of one lane: [4 cnt J from][4 cnt J to][cnt h from][cnt h to], compacted
-                // from the per_item-strided staging layout by the index map below
+                // a lane's staging row holds [J from rows | J to rows | h from | h to] at offsets
+                // 0, 4 per_item, 8 per_item, 9 per_item; the item's 4 cnt, 4 cnt, cnt and cnt of
+                // them go to four contiguous segments of the state's rows
                 const int nj = WJ ? 4 * cnt : 0, nh = (WG && R.gh) ? cnt : 0;
                 const int gbase = g * kLanes;
                 for (int s = wid; s < nlive; s += NW) {
                     const double *src = wstage + (size_t)s * lstr;
+                    double *Jb = WJ ? st_jval(N, R, gbase + s) + N.nnzJg + 4 * (size_t)l0 : nullptr;
+                    double *hb = nh ? st_gh(N, R, gbase + s) + 2 * N.nb + l0 : nullptr;
                     for (int e = lane; e < 2 * nj + 2 * nh; e += 32) {
-                        double *dst;
-                        double v;
-                        if (e < nj) {
-                            v = src[e];
-                            dst = st_jval(N, R, gbase + s) + N.nnzJg + 4 * (size_t)l0 + e;
-                        } else if (e < 2 * nj) {
-                            v = src[4 * per_item + (e - nj)];
-                            dst = st_jval(N, R, gbase + s) + N.nnzJg + 4 * (size_t)(N.nl + l0) + (e - nj);
-                        } else if (e < 2 * nj + nh) {
-                            v = src[8 * per_item + (e - 2 * nj)];
-                            dst = st_gh(N, R, gbase + s) + 2 * N.nb + l0 + (e - 2 * nj);
-                        } else {
-                            v = src[9 * per_item + (e - 2 * nj - nh)];
-                            dst = st_gh(N, R, gbase + s) + 2 * N.nb + N.nl + l0 + (e - 2 * nj - nh);
-                        }
-                        *dst = v;
+                        double *d;
+                        int o;
+                        if (e < nj) { d = Jb + e; o = e; }
+                        else if (e < 2 * nj) { d = Jb + 4 * (size_t)N.nl + (e - nj); o = 4 * per_item + (e - nj); }
+                        else if (e < 2 * nj + nh) { d = hb + (e - 2 * nj); o = 8 * per_item + (e - 2 * nj); }
+                        else { d = hb + N.nl + (e - 2 * nj - nh); o = 9 * per_item + (e - 2 * nj - nh); }
+                        *d = src[o];
                     }
                 }
             }
@@ -278,11 +273,17 @@ __global__ void __launch_bounds__(NT, MINB) k_persist_w(const DevNet N, const Ev
             __syncthreads();
             if (staged && s_ok) {
                 const int gbase = g * kLanes;
+                // element e of a lane's staging row: P rows [0, LP), Q rows [LP, 2 LP), Va rows
+                // [2 LP, 2 LP + LA), Vm rows after; each base is offset by its segment's start
                 auto dst = [&](int s, int k) -> double * {
-                    return k == 0 ? st_jval(N, R, gbase + s) + p0
-                         : k == 1 ? st_jval(N, R, gbase + s) + q0
-                         : k == 2 ? st_hval(N, R, gbase + s) + a0
-                                  : st_hval(N, R, gbase + s) + m0;
+                    if (k < 2) {
+                        if (!WJ) return nullptr;
+                        double *Jb = st_jval(N, R, gbase + s);
+                        return k == 0 ? Jb + p0 : Jb + (q0 - LP);
+                    }
+                    if (!WH) return nullptr;
+                    double *Hb = st_hval(N, R, gbase + s);
+                    return k == 2 ? Hb + (a0 - 2 * LP) : Hb + (m0 - 2 * LP - LA);
                 };
                 copy_out_w<NW>(wstage, lstr, nlive, LROWS, LP, LP, LA, dst, wid, lane);
             }

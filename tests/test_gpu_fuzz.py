@@ -112,3 +112,31 @@ def test_random_grids_with_generator_outages_both_formulations(ex, oracle_mod, c
         compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"case {case} {cfg} [{i}]")
         ref = oracle_cart(oracle_mod, g, b, x, lam, i)
         compare_instance(cart, i, ref, f"cartesian case {case} [{i}]")
+
+
+@pytest.mark.parametrize("case", range(10))
+def test_random_irregular_grids_warp_tiles(ex, oracle_mod, case):
+    """The same irregular grids (a single bus without branches among them) under random
+    branch-per-warp configurations, with batches that end inside or on a group of 32 states:
+    bitwise equal to the branch-per-thread kernel, and sampled states against the oracle."""
+    rng = np.random.default_rng(6000 + case)
+    g = irregular_grid(rng, 6000 + case)
+    B = int(rng.choice([1, 5, 31, 32, 33, 64, 70]))
+    b = synth.random_batch(7000 + case, g, B, masks=True, pd_scale=bool(rng.integers(2)),
+                           obj_weight=bool(rng.integers(2)), sigma=float(rng.choice([0.0, 0.6, 1.0])),
+                           gen_masks=bool(rng.integers(2)))
+    net = ex.Net(g)
+    ex.exago_net_set_config(net.h, schedule=2)
+    ref = gpu_eval(net, b)
+    cfg = dict(schedule=2, tiling=2, block=int(rng.choice([64, 128])),
+               occupancy=int(rng.choice([8, 16])), tile_group=int(rng.integers(1, 5)),
+               use_graph=int(rng.choice([1, 2])))
+    if rng.integers(2):
+        lag = int(rng.integers(1, 4))
+        cfg.update(lag=lag, ring=lag + int(rng.integers(1, 4)))
+    ex.exago_net_set_config(net.h, **cfg)
+    out = gpu_eval(net, b)
+    for k in ref:
+        np.testing.assert_array_equal(out[k], ref[k], err_msg=f"case {case} {cfg} {k}")
+    for i in sorted({0, B - 1, int(rng.integers(B))}):
+        compare_instance(out, i, oracle_eval(oracle_mod, g, b, i), f"warp case {case} {cfg} [{i}]")

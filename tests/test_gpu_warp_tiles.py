@@ -88,6 +88,27 @@ def test_meshed_grid_rows_beyond_the_staging_cap(ex, oracle_mod):
         compare_instance(ref, i, oracle_eval(oracle_mod, g, b, i), "warp meshed")
 
 
+def test_net_without_branches(ex, oracle_mod):
+    """One bus, no branch: no branch items at all, so the first bus item of each group sums the
+    objective's partials itself."""
+    import dataclasses
+    g = synth.make_grid(271, 2, 1, 1, shunts=True)
+    g = dataclasses.replace(g, nb=1, Gs=g.Gs[:1], Bs=g.Bs[:1], Pd=g.Pd[:1], Qd=g.Qd[:1],
+                            f=g.f[:0], t=g.t[:0], r=g.r[:0], x=g.x[:0], b=g.b[:0], tap=g.tap[:0],
+                            rateA=g.rateA[:0], gbus=np.zeros(1, np.int32))
+    b = synth.random_batch(272, g, 45, pd_scale=True, obj_weight=True, sigma=0.7)
+    net = ex.Net(g)
+    ex.exago_net_set_config(net.h, schedule=2)
+    ref = gpu_eval(net, b)
+    for cfg in WARP_CONFIGS[:3]:
+        ex.exago_net_set_config(net.h, **cfg)
+        out = gpu_eval(net, b)
+        for k in ref:
+            np.testing.assert_array_equal(out[k], ref[k], err_msg=f"{cfg} {k}")
+    for i in (0, 44):
+        compare_instance(ref, i, oracle_eval(oracle_mod, g, b, i), "warp no branches")
+
+
 def test_generator_outages_and_phase_shifters(ex, oracle_mod):
     """The general variant (generator masks, phase-shifting transformers)."""
     g = synth.make_grid(211, 300, 390, 75, transformer_frac=0.1, shunts=True, shifter_frac=0.2)
