@@ -48,7 +48,9 @@ FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_GHZ / 1e3
 FP64_PEAK_GINSTR = SMS * FP64_FMA_PER_SM_CLK * SM_MAX_GHZ
 # dram bytes per launch of the dominant kernel from its ncu capture, by kernel name; a kernel
 # changed since its capture has no entry
-TRAFFIC_BYTES = {"persistent": 384_156_672}   # 63.5 MB read + 320.7 MB written (ncu, 2000-bus x 512)
+# (the persistent kernel's entry is the per-thread tiling's; "persistent/warp" the warp tiling's)
+TRAFFIC_BYTES = {"persistent": 385_613_568,        # 63.9 MB read + 321.7 MB written (ncu, 2000-bus x 512)
+                 "persistent/warp": 783_639_296}   # 278.2 MB read + 505.5 MB written (ncu, same workload)
 HBM_PEAK_FALLBACK_GBS = 6800.0
 
 
@@ -869,7 +871,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         "phases_ms": phases,
         "roofline": {"kernel": top_name, "bound": "alu", "achieved": achieved_tf,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": TRAFFIC_BYTES.get(top_name),
+                     "traffic": TRAFFIC_BYTES.get(
+                         top_name + ("/warp" if top_name == "persistent" and
+                                     launch_cfg.get("tiling") == exago.TILING_WARP else "")),
                      "per_unit": f"{per_unit} = {flops_state} flops ({instr_state} FP64 instructions)",
                      "units_per_launch": units, "launch_ms": top_ms,
                      "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
