@@ -2,7 +2,8 @@
 instead of trapping; the substitute for compute-sanitizer, which is closed on this machine).
 
 A child process loads the debug build (EXAGO_LIBRARY) and evaluates the same inputs as this
-process does with the release build: every schedule, an adjoint product and a KKT step.  The
+process does with the release build: every schedule (both tilings of the persistent one), an
+adjoint product and a KKT step.  The
 checks are pure comparisons, so the results must be bitwise the release build's, and the status
 word must stay clear.  Then the child lowers the bound the checks compare slot indices against
 (exago_test_debug_bounds): the checks must fire -- exago_net_check reports EXAGO_EDEVICE -- while
@@ -22,7 +23,7 @@ pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SCHEDULES = (dict(schedule=1, use_graph=2), dict(schedule=2, use_graph=2),
-             dict(schedule=3, chunk=2, use_graph=2))
+             dict(schedule=3, chunk=2, use_graph=2), dict(schedule=2, tiling=2, use_graph=2))
 
 WORK = r'''
 import numpy as np, torch
