@@ -3,9 +3,8 @@ instead of trapping; the substitute for compute-sanitizer, which is closed on th
 
 A child process loads the debug build (EXAGO_LIBRARY) and evaluates the same inputs as this
 process does with the release build: every schedule (both tilings of the persistent one), an
-adjoint product and a KKT step.  The
-checks are pure comparisons, so the results must be bitwise the release build's, and the status
-word must stay clear.  Then the child lowers the bound the checks compare slot indices against
+adjoint product and a KKT step.  The checks are pure comparisons, so the results must be bitwise
+the release build's, and the status word must stay clear.  Then the child lowers the bound the checks compare slot indices against
 (exago_test_debug_bounds): the checks must fire -- exago_net_check reports EXAGO_EDEVICE -- while
 every access the kernels still make stays in bounds (the bound only shrinks, the tables are
 untouched); with the bound restored the next evaluation is clean again.
