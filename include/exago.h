@@ -437,6 +437,9 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
  *             reads its record (coalesced) and writes the neighbour's row entries, then one
  *             thread per bus sums its ends' diagonal terms from shared memory; DEFAULT / OFF:
  *             one thread per bus walks its ends, reading the records through L2.
+ *             EXAGO_STAGE_BULK (persistent schedule, branch per thread; elsewhere OFF): one TMA
+ *             bulk copy brings a bus tile's records into shared memory, and one thread per bus
+ *             walks its ends there (tiles whose records do not fit read them through L2).
  *             EXAGO_SCHED_PIPELINED: the batch in chunks; the branch kernel of a chunk runs on
  *             the caller's stream while the bus kernel of the previous chunk runs on a
  *             high-priority net stream, ordered by events only (no device-side waits).
@@ -467,7 +470,7 @@ exago_status exago_eval_profile(exago_net_t net, const exago_batch *batch, doubl
 enum { EXAGO_SCHED_AUTO = 0, EXAGO_SCHED_KERNELS = 1, EXAGO_SCHED_PERSISTENT = 2,
        EXAGO_SCHED_PIPELINED = 3 };
 enum { EXAGO_GRAPH_DEFAULT = 0, EXAGO_GRAPH_ON = 1, EXAGO_GRAPH_OFF = 2 };
-enum { EXAGO_STAGE_DEFAULT = 0, EXAGO_STAGE_ON = 1, EXAGO_STAGE_OFF = 2 };
+enum { EXAGO_STAGE_DEFAULT = 0, EXAGO_STAGE_ON = 1, EXAGO_STAGE_OFF = 2, EXAGO_STAGE_BULK = 3 };
 enum { EXAGO_TILING_DEFAULT = 0, EXAGO_TILING_THREAD = 1, EXAGO_TILING_WARP = 2 };
 typedef struct {
     int schedule;
@@ -493,7 +496,8 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg);
 /*
  * Autotuner: times the multi-kernel schedule, pipelined variants (three chunk sizes) and
  * persistent variants (block 32 / 64 / 128 / 256, occupancy 8 / 16 / 24 warps, 1 or 2 tiles per
- * work item), each with and without slot-parallel bus tiles, and the warp-tiled persistent
+ * work item), each with and without slot-parallel bus tiles, persistent variants with bulk-copied
+ * bus tile records (block 64 / 128, occupancy 8 / 16), and the warp-tiled persistent
  * variants (branch per warp: block 64 / 128, occupancy 8 / 16, 1 or 2 branches per warp and
  * item), on this batch, `reps` evaluations each after one warm-up, on batch->stream, and records the
  * fastest for batches of this size (used by EXAGO_SCHED_AUTO).  Outputs are written as by

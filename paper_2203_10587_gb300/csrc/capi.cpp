@@ -176,17 +176,20 @@ exago_status do_upload(exago_net *net) {
     d.hM_end = (int)p.Hrowptr[2 * p.nb];
     for (int t = 0; t < 4; t++) {   // largest bus tile's rows (and components), 32 to 256 buses
         const int T = 32 << t;
-        int64_t rows = 0, all = 0;
+        int64_t rows = 0, all = 0, bulk = 0;
         for (int i0 = 0; i0 < p.nb; i0 += T) {
             const int i1 = i0 + T < p.nb ? i0 + T : p.nb;
             const int64_t r = 2 * (p.Jrowptr[i1] - p.Jrowptr[i0]) + (p.Hrowptr[i1] - p.Hrowptr[i0]) +
                               (p.Hrowptr[p.nb + i1] - p.Hrowptr[p.nb + i0]);
             const int64_t a = r + (int64_t)kDiagComps * (p.slot_ptr[i1] - p.slot_ptr[i0]);
+            const int64_t k = r + (int64_t)NCOMP * (p.slot_ptr[i1] - p.slot_ptr[i0]);
             if (r > rows) rows = r;
             if (a > all) all = a;
+            if (k > bulk) bulk = k;
         }
         d.stage_cap_rows[t] = (int)(rows < kStageMaxDoubles ? rows : kStageMaxDoubles);
         d.stage_cap_all[t] = (int)(all < kStageMaxDoubles ? all : kStageMaxDoubles);
+        d.stage_cap_bulk[t] = (int)(bulk < kStageMaxDoubles ? bulk : kStageMaxDoubles);
     }
 #define UP(field, vec) if ((s = upload(net, p.vec, &d.field)) != EXAGO_OK) return s
     UP(f, f); UP(t, t);
@@ -302,11 +305,13 @@ int occupancy(exago_net *net, bool persistent, int block, int occ_warps, size_t 
 // diagonal components), but no more than keeps the register-limited number of resident CTAs per
 // SM.  A tile that does not fit writes its rows straight to global memory (and walks its slots
 // per bus).
-int stage_cap(exago_net *net, bool persistent, int block, int occ_warps, bool stage_recs) {
+int stage_cap(exago_net *net, bool persistent, int block, int occ_warps, int stage_recs) {
     const int t = stage_index(persistent ? block : 128);
     const int by_regs = occupancy(net, persistent, block, occ_warps, 0);
     const long budget = ((long)net->smem_per_sm / (by_regs > 0 ? by_regs : 1) - 4096) / 8;
-    const int want = stage_recs ? net->dev.stage_cap_all[t] : net->dev.stage_cap_rows[t];
+    const int want = stage_recs == 2   ? net->dev.stage_cap_bulk[t]
+                     : stage_recs == 1 ? net->dev.stage_cap_all[t]
+                                       : net->dev.stage_cap_rows[t];
     return want > budget ? (int)(budget & ~1l) : want;
 }
 
@@ -356,8 +361,11 @@ Resolved resolve(exago_net *net, int B) {
     }
     r.block = (c.block == 32 || c.block == 128 || c.block == 256) ? c.block : 64;
     r.occ_warps = (c.occupancy == 8 || c.occupancy == 24) ? c.occupancy : 16;
-    r.stage_recs = c.stage_records == EXAGO_STAGE_ON;
     const bool pers = r.schedule == EXAGO_SCHED_PERSISTENT;
+    // bulk record copies only in the persistent kernel (others walk the records through L2)
+    r.stage_recs = c.stage_records == EXAGO_STAGE_ON     ? 1
+                   : c.stage_records == EXAGO_STAGE_BULK ? (pers ? 2 : 0)
+                                                         : 0;
     r.use_graph = c.use_graph != EXAGO_GRAPH_OFF;
     r.spin_limit = c.spin_limit > 0 ? c.spin_limit : kDefaultSpinLimit;
     r.force_timeout = c.test_force_timeout ? 1 : 0;
@@ -1124,7 +1132,7 @@ exago_status exago_net_set_config(exago_net_t net, const exago_config *cfg) {
         return fail(EXAGO_EINVAL, "block must be 0, 32, 64, 128 or 256");
     if (cfg->occupancy != 0 && cfg->occupancy != 8 && cfg->occupancy != 16 && cfg->occupancy != 24)
         return fail(EXAGO_EINVAL, "occupancy must be 0, 8, 16 or 24");
-    if (cfg->stage_records < EXAGO_STAGE_DEFAULT || cfg->stage_records > EXAGO_STAGE_OFF)
+    if (cfg->stage_records < EXAGO_STAGE_DEFAULT || cfg->stage_records > EXAGO_STAGE_BULK)
         return fail(EXAGO_EINVAL, "unknown stage_records value");
     if (cfg->lag < 0 || cfg->ring < 0 || cfg->spin_limit < 0)
         return fail(EXAGO_EINVAL, "negative lag, ring or spin limit");
@@ -1150,7 +1158,9 @@ exago_status exago_net_get_config(exago_net_t net, int B, exago_config *cfg) {
     const Resolved r = resolve(net, B > 0 ? B : 1);
     *cfg = net->cfg;
     cfg->schedule = r.schedule;
-    cfg->stage_records = r.stage_recs ? EXAGO_STAGE_ON : EXAGO_STAGE_OFF;
+    cfg->stage_records = r.stage_recs == 2 ? EXAGO_STAGE_BULK
+                         : r.stage_recs    ? EXAGO_STAGE_ON
+                                           : EXAGO_STAGE_OFF;
     if (r.schedule == EXAGO_SCHED_PERSISTENT) {
         cfg->block = r.block;
         cfg->occupancy = r.occ_warps;
@@ -1209,6 +1219,18 @@ exago_status exago_net_autotune(exago_net_t net, const exago_batch *bt, double *
                         cands.push_back(c);
                     }
         }
+        // persistent kernel with bus tiles' records in one bulk copy each
+        for (int block : {64, 128})
+            for (int occw : {8, 16}) {
+                exago_config c{};
+                c.schedule = EXAGO_SCHED_PERSISTENT;
+                c.block = block;
+                c.occupancy = occw;
+                c.stage_records = EXAGO_STAGE_BULK;
+                c.tile_group = 1;
+                c.use_graph = EXAGO_GRAPH_ON;
+                cands.push_back(c);
+            }
         // warp-tiled persistent kernel: a warp per branch or bus, a lane per state
         for (int block : {64, 128})
             for (int occw : {8, 16})

@@ -663,12 +663,61 @@ __device__ __forceinline__ void bus_sums(const DevNet &N, const EvalReq &R, int 
     bus_tail<WANT>(N, R, b, i, D, W);
 }
 
+// Bulk copy of a bus tile's records into shared memory (the persistent kernel): one TMA bulk
+// copy (cp.async.bulk) whose completion an mbarrier of the CTA counts.  mbar: the barrier
+// (initialised with an arrival count of 1); a wait gives up after spin_limit polls.  The parity
+// of the barrier's next completion is kept by every thread of the CTA (bus_tile's `phase`).
+struct BulkCtx {
+    unsigned long long *mbar;
+    long long spin_limit;
+};
+
+// Thread 0: the tile's records [src, src + bytes) -> dst (shared memory), both 16-byte aligned
+// and bytes a multiple of 16.  The group's earlier shared-memory accesses of dst are ordered
+// before the copy by the caller's barrier and the proxy fence here; the records were written by
+// other CTAs and acquired through the tile's wait.
+__device__ __forceinline__ void bulk_records(double *dst, const double *src, unsigned bytes,
+                                             unsigned long long *mbar) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+    asm volatile("fence.proxy.async;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(d), "l"(src), "r"(bytes), "r"(m)
+                 : "memory");
+}
+
+// Every thread: waits for the barrier's completion of the given parity; false (and a timeout
+// code in the status word) after `limit` polls.
+__device__ __forceinline__ bool bulk_wait(unsigned long long *mbar, unsigned parity,
+                                          long long limit, int *status) {
+    const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+    for (long long it = 0;; it++) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(m), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (it >= limit) {
+            if (status) *(volatile int *)status = 3;   // the records' bulk copy did not complete
+            return false;
+        }
+    }
+}
+
 // The bus items of buses [i0, i0 + G::size()) of state b, by the whole group (i0 a multiple of
 // the group size), with `stage` = cap doubles of shared memory.  The tile's slots are one
 // contiguous range [S0, S1), and its rows are four contiguous segments.
-//   * With R.stage_recs, and when the slots' diagonal components fit, the tile runs
+//   * With R.stage_recs == 1, and when the slots' diagonal components fit, the tile runs
 //     slot-parallel: every thread takes slots (slot_item), then every thread sums its bus's
 //     components from shared memory (bus_sums).
+//   * With R.stage_recs == 2, a bulk context (the persistent kernel) and when the tile's records
+//     fit, one bulk copy brings them into shared memory and every thread walks its own bus's
+//     slots there (bus_item).
 //   * Otherwise every thread walks its own bus's slots, reading the records through L2
 //     (bus_item).
 // When the row segments fit (after the components, if used), every row entry is written to
@@ -676,7 +725,8 @@ __device__ __forceinline__ void bus_sums(const DevNet &N, const EvalReq &R, int 
 // the rows go straight to global memory.  Contains G::sync(): call from every thread.
 template <int WANT, class G>
 __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int b, int i0,
-                                         const double *scr, double *stage, int cap) {
+                                         const double *scr, double *stage, int cap,
+                                         const BulkCtx *bk = nullptr, unsigned *phase = nullptr) {
     constexpr bool WJ = WANT & W_J, WH = WANT & W_H;
     const int nb = N.nb, r = G::rank(), sz = G::size();
     int i1 = i0 + sz;
@@ -692,9 +742,12 @@ __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int 
     const int m0 = row_start(N.bus_hM, i0, nb, N.hM_end), m1 = row_start(N.bus_hM, i1, nb, N.hM_end);
     const int LP = WJ ? p1 - p0 : 0, LA = WH ? a1 - a0 : 0, LM = WH ? m1 - m0 : 0;
     const int LROWS = 2 * LP + LA + LM;
-    // slot-parallel whenever the components fit; the rows are staged after them when they fit too
-    const bool slotpar = R.stage_recs && kDiagComps * (S1 - S0) <= cap;
-    const int LD = slotpar ? kDiagComps * (S1 - S0) : 0;
+    // slot-parallel whenever the components fit, or the records in bulk whenever they fit; the
+    // rows are staged after them when they fit too
+    const bool slotpar = R.stage_recs == 1 && kDiagComps * (S1 - S0) <= cap;
+    const bool bulk = bk != nullptr && phase != nullptr && R.stage_recs == 2 && S1 > S0 &&
+                      NCOMP * (S1 - S0) <= cap;
+    const int LD = slotpar ? kDiagComps * (S1 - S0) : bulk ? NCOMP * (S1 - S0) : 0;
     const bool staged = (WJ || WH) && LD + LROWS <= cap;
     double *Jb = WJ ? st_jval(N, R, b) : nullptr;
     double *Hb = WH ? st_hval(N, R, b) : nullptr;
@@ -712,6 +765,12 @@ __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int 
             slot_item<WANT>(N, s, scr, stage + (size_t)(s - S0) * kDiagComps, T);
         G::sync();
         if (i < i1) bus_sums<WANT>(N, R, b, i, S0, stage, T.template of<WANT>(N, i));
+    } else if (bulk) {
+        if (r == 0)
+            bulk_records(stage, scr + (size_t)S0 * NCOMP, (unsigned)(LD * sizeof(double)), bk->mbar);
+        const bool ok = bulk_wait(bk->mbar, *phase, bk->spin_limit, N.status);
+        *phase ^= 1u;
+        if (i < i1 && ok) bus_item<WANT, true>(N, R, b, i, stage, S0, T.template of<WANT>(N, i));
     } else if (i < i1) {
         bus_item<WANT, false>(N, R, b, i, scr, 0, T.template of<WANT>(N, i));
     }
@@ -724,8 +783,8 @@ __device__ __forceinline__ void bus_tile(const DevNet &N, const EvalReq &R, int 
         for (int e = r; e < LA; e += sz) Hb[a0 + e] = rows[2 * LP + e];
         for (int e = r; e < LM; e += sz) Hb[m0 + e] = rows[2 * LP + LA + e];
         G::sync();
-    } else if (slotpar) {
-        G::sync();   // the next tile may overwrite the components
+    } else if (slotpar || bulk) {
+        G::sync();   // the next tile may overwrite the components or records
     }
 }
 

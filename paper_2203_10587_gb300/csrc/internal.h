@@ -79,6 +79,7 @@ struct DevNet {
     int jP_end, jQ_end, hA_end, hM_end;      // ends of the four row blocks of the bus rows
     int stage_cap_rows[4];                   // shared-memory doubles of a bus tile of 32/64/128/256
     int stage_cap_all[4];                    // buses: its row segments, or components plus rows
+    int stage_cap_bulk[4];                   // ... or its whole records plus rows
     double baseMVA;
     const int *f, *t;
     const double *Gff, *Bff, *Gtt, *Btt, *Gft, *Bft;   // pi-model admittances (Gft, Bft: from end's)
@@ -133,7 +134,8 @@ struct EvalReq {
     double *scratch;            // [B][nslot][NCOMP] branch-end records (or ring slots)
     int scr_b0;                 // state b's records are at scratch + (b - scr_b0) * nslot * NCOMP
                                 // in the multi-kernel and pipelined schedules
-    int stage_recs;             // bus tiles read their records slot-parallel into shared memory
+    int stage_recs;             // 1: bus tiles read their records slot-parallel into shared
+                                // memory; 2: in one bulk copy (persistent kernel)
     int stage_cap;              // shared-memory doubles of one bus tile (records and rows)
     int B;
     const StateTab *tab;        // device table of B states, or nullptr

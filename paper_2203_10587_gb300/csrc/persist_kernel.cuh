@@ -102,6 +102,7 @@ static __device__ bool bounded_wait(const int *p, int target, long long limit, i
     return true;
 }
 
+// (code 3: a bus tile's bulk copy of its records did not complete, bulk_wait in eval_items.cuh)
 enum : int { ST_TIMEOUT_BUS = 1, ST_TIMEOUT_RING = 2 };
 
 // Invalidates in L2, without write-back, every whole 128-byte line of [p, q): branch-end records
@@ -143,7 +144,8 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
                                                       const PersistParams P) {
     __shared__ int s_item, s_ok;
     __shared__ double s_part[OBJ_LANES];
-    extern __shared__ double stage[];
+    __shared__ unsigned long long s_mbar;   // bulk copies of bus tiles' records (stage_recs 2)
+    extern __shared__ __align__(16) double stage[];
     int *done_br = P.ctr + 1, *done_bu = P.ctr + 1 + P.B;
     static_assert(OBJ_LANES == kObjLanes && OBJ_LANES % NT == 0, "objective lanes");
     const size_t rec_doubles = (size_t)NCOMP * N.nslot;
@@ -155,6 +157,13 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
     // block claims one ticket at a time (and late-ranked blocks claim none): the argument holds
     // as well, since tickets are still claimed in order by running blocks.
     int next = 0;
+    unsigned bulk_phase = 0;
+    const BulkCtx bk{&s_mbar, P.spin_limit};
+    if (R.stage_recs == 2 && threadIdx.x == 0) {
+        const unsigned m = (unsigned)__cvta_generic_to_shared(&s_mbar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(m) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     phase_mark(P.times, PH_ENTRY);
     if (threadIdx.x == 0) {
         if (P.spread > 0) {
@@ -225,7 +234,8 @@ __global__ void __launch_bounds__(NT, MINB) k_persist(const DevNet N, const Eval
                     const int i0 = (tile * P.group + k) * NT;
                     if (i0 >= N.nb) break;
                     if (WANT & (W_G | W_J | W_H))
-                        bus_tile<WANT, BlockGroup>(N, R, b, i0, scr, stage, cap);
+                        bus_tile<WANT, BlockGroup>(N, R, b, i0, scr, stage, cap,
+                                                   R.stage_recs == 2 ? &bk : nullptr, &bulk_phase);
                     if (i0 + (int)threadIdx.x < N.nb && R.grad)
                         grad_bus<(WANT & W_GM) != 0>(N, R, b, i0 + threadIdx.x);
                 }

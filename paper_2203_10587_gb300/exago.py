@@ -51,7 +51,7 @@ EXPORTS = [
 
 SCHED_AUTO, SCHED_KERNELS, SCHED_PERSISTENT, SCHED_PIPELINED = 0, 1, 2, 3
 GRAPH_DEFAULT, GRAPH_ON, GRAPH_OFF = 0, 1, 2
-STAGE_DEFAULT, STAGE_ON, STAGE_OFF = 0, 1, 2
+STAGE_DEFAULT, STAGE_ON, STAGE_OFF, STAGE_BULK = 0, 1, 2, 3
 TILING_DEFAULT, TILING_THREAD, TILING_WARP = 0, 1, 2
 
 

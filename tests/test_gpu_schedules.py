@@ -43,6 +43,10 @@ CONFIGS = [
     dict(schedule=2, tiling=2),                         # warp tiles: a warp per branch / bus
     dict(schedule=2, tiling=2, block=128, occupancy=8, tile_group=2),
     dict(schedule=2, tiling=2, lag=1, ring=2, use_graph=2),
+    dict(schedule=2, stage_records=3),                  # bus tiles' records in one bulk copy each
+    dict(schedule=2, block=128, stage_records=3, tile_group=2, lag=1, ring=2, use_graph=2),
+    dict(schedule=2, block=32, occupancy=8, stage_records=3),
+    dict(schedule=1, stage_records=3),                  # bulk copies only persistent: plain walk
 ]
 
 
@@ -70,6 +74,28 @@ def test_schedules_bitwise_equal_and_match_oracle(ex, oracle_mod, name):
             np.testing.assert_array_equal(o[k], outs[0][k], err_msg=k)
     for i in (0, B // 2, B - 1):
         compare_instance(outs[0], i, oracle_eval(oracle_mod, g, b, i), name)
+
+
+@pytest.mark.parametrize("cfg", [dict(block=64, occupancy=16), dict(block=128, occupancy=16),
+                                 dict(block=64, occupancy=8, tile_group=3),
+                                 dict(block=256, occupancy=16)])
+def test_bulk_record_copies_on_the_benchmark_and_a_meshed_grid(ex, oracle_mod, cfg):
+    """stage_records = BULK: each bus tile's records come into shared memory in one TMA bulk
+    copy (tiles whose records do not fit walk them through L2).  On the 2,000-bus x 512 batch and
+    on a meshed grid (larger tiles, some above the cap) every output equals the default
+    schedule's bit for bit."""
+    for g, b in ((synth.grid_2000(), None), (synth.make_grid(281, 500, 2500, 125, max_degree=64), None)):
+        b = synth.contingency_batch(3, g, 512) if g.nb == 2000 else synth.random_batch(282, g, 70, masks=True)
+        net = ex.Net(g)
+        ex.exago_net_set_config(net.h, schedule=2, **cfg)
+        ref = gpu_eval(net, b)
+        ex.exago_net_set_config(net.h, schedule=2, stage_records=3, **cfg)
+        assert ex.exago_net_get_config(net.h, b.B)["stage_records"] == 3
+        for _ in range(2):
+            out = gpu_eval(net, b)
+            for key in ref:
+                np.testing.assert_array_equal(out[key], ref[key], err_msg=f"{cfg} {g.nb} {key}")
+        compare_instance(out, b.B - 1, oracle_eval(oracle_mod, g, b, b.B - 1), f"bulk {cfg} {g.nb}")
 
 
 def test_graph_cache_under_many_argument_sets(ex):
