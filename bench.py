@@ -362,7 +362,7 @@ def run_other_configs(exago, synth, torch, np, dev):
     res["10k_bus_single_x1000"] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms,
                                    "launch_config": {k: tuned1[k] for k in
                                                      ("schedule", "block", "occupancy", "tile_group",
-                                                      "tiling")}}
+                                                      "stage_records", "tiling")}}
     # C4: 64 load scenarios, all outputs, then J^T v and (grad^2 L) u
     b = synth.scenario_batch(4, g, 64)
     x, lam, ps, w = (td(b.x, torch.float64), td(b.lam, torch.float64),
@@ -382,7 +382,7 @@ def run_other_configs(exago, synth, torch, np, dev):
                                     "jtv_per_s": 64e3 / ms_jtv, "hvp_per_s": 64e3 / ms_hvp,
                                     "launch_config": {k: tuned[k] for k in
                                                       ("schedule", "block", "occupancy", "tile_group",
-                                                       "tiling")}}
+                                                       "stage_records", "tiling")}}
     net.close()
     # a meshed grid (2,000 buses, 6,000 branches: mean degree 6, up to 16) x 512 states: the bus
     # degrees within a warp vary more, which the branch-per-warp tiling does not mind
