@@ -49,7 +49,7 @@ FP64_PEAK_GINSTR = SMS * FP64_FMA_PER_SM_CLK * SM_MAX_GHZ
 # dram bytes per launch of the dominant kernel from its ncu capture, by kernel name; a kernel
 # changed since its capture has no entry
 # (the persistent kernel's entry is the per-thread tiling's; "persistent/warp" the warp tiling's)
-TRAFFIC_BYTES = {"persistent": 385_613_568,        # 63.9 MB read + 321.7 MB written (ncu, 2000-bus x 512)
+TRAFFIC_BYTES = {"persistent": 384_794_624,        # 63.7 MB read + 321.1 MB written (ncu, 2000-bus x 512)
                  "persistent/warp": 783_639_296}   # 278.2 MB read + 505.5 MB written (ncu, same workload)
 HBM_PEAK_FALLBACK_GBS = 6800.0
 
