@@ -35,6 +35,25 @@ def test_exports_every_declared_symbol(L):
     assert sorted(exago.EXPORTS) == syms
 
 
+def test_binding_structs_and_enums_match_the_header():
+    """The ctypes mirrors of the header's structs list the same fields in the same order with
+    the same C types, and the binding's enum constants have the header's values."""
+    src = open(os.path.join(ROOT, "include", "exago.h")).read()
+    ctype = {"int": ctypes.c_int, "long long": ctypes.c_longlong, "double": ctypes.c_double,
+             "size_t": ctypes.c_size_t}
+    for name, mirror in (("exago_config", exago.exago_config),):
+        body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + ";", src).group(1)
+        fields = re.findall(r"^\s*([a-z ]+?)\s+(\w+);", body, re.M)
+        assert [f for _, f in fields] == [f for f, _ in mirror._fields_], name
+        for (ct, f), (mf, mt) in zip(fields, mirror._fields_):
+            assert ctypes.sizeof(ctype[ct.strip()]) == ctypes.sizeof(mt), (name, f)
+    enums = {f"{a}_{b}": int(v) for a, b, v in
+             re.findall(r"\bEXAGO_(SCHED|GRAPH|STAGE|TILING)_(\w+)\s*=\s*(\d+)", src)}
+    assert len(enums) == 14
+    for k, v in enums.items():
+        assert getattr(exago, k) == v, k
+
+
 def plan(grid):
     return exago.Net(grid, plan_only=True)
 
