@@ -54,6 +54,35 @@ def test_binding_structs_and_enums_match_the_header():
         assert getattr(exago, k) == v, k
 
 
+def test_binding_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every ctypes mirror of a header struct has the size and field offsets that the host C
+    compiler gives the header's struct (compiled here with gcc)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    mirrors = {"exago_config": exago.exago_config, "exago_batch": exago.exago_batch,
+               "exago_serve_client": exago.exago_serve_client}
+    cfield = {"lambda_": "lambda"}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "exago.h"', "int main(void) {"]
+    for name, m in mirrors.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in m._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {cfield.get(f, f)}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for name, m in mirrors.items():
+        assert int(out[name]) == ctypes.sizeof(m), name
+        for f, _ in m._fields_:
+            assert int(out[f"{name}.{f}"]) == getattr(m, f).offset, f"{name}.{f}"
+
+
 def plan(grid):
     return exago.Net(grid, plan_only=True)
 
